@@ -1,0 +1,248 @@
+"""The H-LU factorisation as the paper states it (test infrastructure only).
+
+Recursion (Sec. 3.1, operation sequence O1.1-O5.5; the same five steps at
+every partitioned diagonal block):
+
+    lu(A):   A dense -> unpivoted LU in place                          (O1.1)
+             else    lu(A00); trsm_l(A00, A01); trsm_u(A00, A10);      (O1.1-O1.3)
+                     addmul(A11, -1, A10, A01); lu(A11)                (O1.4, O1.5)
+
+Triangular solves on a target X (Sec. 3.1 "Low-rank blocks", and the
+decomposition of O2 into O2.1-O2.6 in Sec. 5.2):
+    X low rank  -> solve only on its factor (U for L^{-1} X, V for X U^{-1});
+    X dense     -> forward / backward substitution through the H-structure of L or U;
+    X partitioned -> X0j := L00^{-1} X0j; X1j -= L10 X0j; X1j := L11^{-1} X1j.
+
+Products and additions (Sec. 3.1): a product with a low-rank factor stays
+factorised, Z (U V^T) = (Z U) V^T and (U V^T) Z = U (Z^T V)^T.  Adding to a
+low-rank target is rounded addition: stack the factors, take the SVD of the
+sum and drop the small singular values; a dense contribution to a low-rank
+target is converted the same way.
+
+Readings where the paper is silent (each one is listed in the design notes):
+  * truncation rule: keep sigma_i > eps * sigma_1 (strict), rank 0 if sigma_1 = 0;
+  * one truncation per (addmul call, low-rank target leaf): addmul recurses while
+    C, A and B are all partitioned; otherwise the exact product A B is formed
+    (factorised when A or B is low rank, dense otherwise), restricted to each
+    leaf of C, and added once;
+  * the factor Sigma of a truncated block is kept in U (U <- Q_u X Sigma, V <- Q_v Y).
+"""
+from __future__ import annotations
+
+import collections
+
+import numpy as np
+
+from .dense import lu_nopiv, solve_unit_lower, solve_upper_right
+from .hmatrix import build_hmatrix, densify, hmul, hmul_t
+
+
+class Counters:
+    """Model flop counts (standard operation counts) and event statistics."""
+
+    def __init__(self):
+        self.flops = collections.Counter()
+        self.events = collections.Counter()
+        self.trunc_K = collections.Counter()
+        self.trunc_rank = collections.Counter()
+        self.min_pivot = np.inf
+
+    def total(self):
+        return float(sum(self.flops.values()))
+
+
+class HLUOracle:
+    """Plain FP64 H-LU of a shared-input problem.  After factor(), self.A holds
+    L (strictly below the diagonal, unit diagonal implied) and U (on and above)
+    in the block structure of the input."""
+
+    def __init__(self, problem, eps, hm=None):
+        self.problem = problem
+        self.eps = float(eps)
+        self.A = build_hmatrix(problem) if hm is None else hm
+        self.c = Counters()
+
+    # ----------------------------------------------------------- recursion
+    def factor(self):
+        self.lu(self.A)
+        return self
+
+    def lu(self, b):
+        if b.kind == "dense":
+            m = b.m
+            piv = lu_nopiv(b.D)
+            self.c.flops["getrf"] += 2.0 * m ** 3 / 3.0
+            self.c.events["getrf"] += 1
+            if not np.all(np.isfinite(piv)) or np.any(piv == 0.0):
+                raise FloatingPointError(f"zero or non-finite pivot in leaf {b.leaf_id}")
+            self.c.min_pivot = min(self.c.min_pivot, float(np.min(piv)))
+            return
+        if b.kind != "part":
+            raise ValueError("low-rank diagonal block")
+        (a00, a01), (a10, a11) = b.sons
+        self.lu(a00)                     # O1.1
+        self.trsm_l(a00, a01)            # O1.2
+        self.trsm_u(a00, a10)            # O1.3
+        self.addmul(a11, -1.0, a10, a01)  # O1.4
+        self.lu(a11)                     # O1.5
+
+    # ------------------------------------------------ triangular solves
+    def trsm_l(self, L, X):
+        """X := L^{-1} X, L the unit lower part of the factored diagonal block."""
+        if X.kind == "lowrank":
+            self.trsm_l_panel(L, X.U)
+        elif X.kind == "dense":
+            self.trsm_l_panel(L, X.D)
+        else:
+            (l00, _), (l10, l11) = L.sons
+            for j in (0, 1):
+                self.trsm_l(l00, X.sons[0][j])                      # O2.1, O2.2
+            for j in (0, 1):
+                self.addmul(X.sons[1][j], -1.0, l10, X.sons[0][j])  # O2.3, O2.4
+            for j in (0, 1):
+                self.trsm_l(l11, X.sons[1][j])                      # O2.5, O2.6
+
+    def trsm_u(self, U, X):
+        """X := X U^{-1}, U the upper part of the factored diagonal block."""
+        if X.kind == "lowrank":
+            self.trsm_u_panel(U, X.V.T)  # (U_x V_x^T) U^{-1} = U_x (V_x^T U^{-1})
+        elif X.kind == "dense":
+            self.trsm_u_panel(U, X.D)
+        else:
+            (u00, u01), (_, u11) = U.sons
+            for i in (0, 1):
+                self.trsm_u(u00, X.sons[i][0])
+            for i in (0, 1):
+                self.addmul(X.sons[i][1], -1.0, X.sons[i][0], u01)
+            for i in (0, 1):
+                self.trsm_u(u11, X.sons[i][1])
+
+    def trsm_l_panel(self, L, P):
+        """P := L^{-1} P for a dense panel P (rows = L's rows), in place."""
+        if L.kind == "dense":
+            solve_unit_lower(L.D, P)
+            self.c.flops["trsm"] += float(L.m) ** 2 * (P.shape[1] if P.ndim > 1 else 1)
+            self.c.events["trsm"] += 1
+            return
+        (l00, _), (l10, l11) = L.sons
+        m0 = l00.m
+        self.trsm_l_panel(l00, P[:m0])
+        P[m0:] -= self._hmul(l10, P[:m0])
+        self.trsm_l_panel(l11, P[m0:])
+
+    def trsm_u_panel(self, U, P):
+        """P := P U^{-1} for a dense panel P (columns = U's columns), in place."""
+        if U.kind == "dense":
+            solve_upper_right(U.D, P)
+            self.c.flops["trsm"] += float(U.m) ** 2 * P.shape[0]
+            self.c.events["trsm"] += 1
+            return
+        (u00, u01), (_, u11) = U.sons
+        n0 = u00.n
+        self.trsm_u_panel(u00, P[:, :n0])
+        P[:, n0:] -= self._hmul_t(u01, P[:, :n0].T).T
+        self.trsm_u_panel(u11, P[:, n0:])
+
+    # ---------------------------------------------------------- products
+    def _hmul(self, b, x):
+        self._count_hmul(b, x.shape[1] if x.ndim > 1 else 1)
+        return hmul(b, x)
+
+    def _hmul_t(self, b, x):
+        self._count_hmul(b, x.shape[1] if x.ndim > 1 else 1)
+        return hmul_t(b, x)
+
+    def _count_hmul(self, b, p):
+        for leaf in b.leaves():
+            if leaf.kind == "dense":
+                self.c.flops["gemm"] += 2.0 * leaf.m * leaf.n * p
+            else:
+                self.c.flops["lrmul"] += 2.0 * (leaf.m + leaf.n) * leaf.rank * p
+
+    def product(self, A, B):
+        """Exact A B for aligned blocks: ('lr', U, V) or ('dense', D)."""
+        if A.kind == "lowrank":
+            self.c.events["prod_lr_left"] += 1
+            return "lr", A.U, self._hmul_t(B, A.V)
+        if B.kind == "lowrank":
+            self.c.events["prod_lr_right"] += 1
+            return "lr", self._hmul(A, B.U), B.V
+        if A.kind == "dense":
+            self.c.events["prod_dense_left"] += 1
+            return "dense", self._hmul_t(B, A.D.T).T
+        if B.kind == "dense":
+            self.c.events["prod_dense_right"] += 1
+            return "dense", self._hmul(A, B.D)
+        self.c.events["prod_part_part"] += 1
+        self.c.flops["gemm"] += 2.0 * A.m * A.n * B.n
+        return "dense", densify(A) @ densify(B)
+
+    def addmul(self, C, alpha, A, B):
+        """C := C + alpha A B with truncation at low-rank leaves of C."""
+        if C.kind == "part" and A.kind == "part" and B.kind == "part":
+            for i in (0, 1):
+                for j in (0, 1):
+                    for k in (0, 1):
+                        self.addmul(C.sons[i][j], alpha, A.sons[i][k], B.sons[k][j])
+            return
+        P = self.product(A, B)
+        self.add_into(C, alpha, P, 0, 0)
+
+    def add_into(self, C, alpha, P, r, c):
+        """Add alpha * P[r:r+C.m, c:c+C.n] to C (exact product restricted to C)."""
+        kind, X, Y = (P[0], P[1], P[2]) if P[0] == "lr" else (P[0], P[1], None)
+        if C.kind == "part":
+            for row in C.sons:
+                for s in row:
+                    self.add_into(s, alpha, P, r + s.r0 - C.r0, c + s.c0 - C.c0)
+            return
+        if kind == "lr":
+            Up = X[r:r + C.m]
+            Vp = Y[c:c + C.n]
+            if C.kind == "dense":
+                C.D += alpha * (Up @ Vp.T)
+                self.c.flops["lrexpand"] += 2.0 * C.m * C.n * Up.shape[1]
+                self.c.events["add_dense"] += 1
+            else:
+                C.U, C.V = self.rounded_add(np.hstack([C.U, alpha * Up]), np.hstack([C.V, Vp]))
+        else:
+            D = X[r:r + C.m, c:c + C.n]
+            if C.kind == "dense":
+                C.D += alpha * D
+                self.c.events["add_dense"] += 1
+            else:
+                C.U, C.V = self.truncate_dense(C.U @ C.V.T + alpha * D)
+
+    # ------------------------------------------------ rounded addition
+    def _keep(self, sig):
+        if sig.size == 0 or sig[0] == 0.0:
+            return 0
+        return int(np.count_nonzero(sig > self.eps * sig[0]))
+
+    def rounded_add(self, Us, Vs):
+        """Truncated SVD of Us Vs^T from the stacked factors (Sec. 3.1):
+        QR of both stacks, SVD of the small core R_u R_v^T, drop sigma_i <= eps*sigma_1."""
+        m, K = Us.shape
+        n = Vs.shape[0]
+        qu, ru = np.linalg.qr(Us)
+        qv, rv = np.linalg.qr(Vs)
+        x, sig, yt = np.linalg.svd(ru @ rv.T)
+        k = self._keep(sig)
+        ku, kv = ru.shape[0], rv.shape[0]
+        self.c.flops["qr"] += (2.0 * m * K * K - 2.0 * K ** 3 / 3.0) + (2.0 * n * K * K - 2.0 * K ** 3 / 3.0)
+        self.c.flops["svd"] += 21.0 * max(ku, kv) ** 3
+        self.c.flops["qx"] += 2.0 * (m * ku + n * kv) * k
+        self.c.events["rounded_add"] += 1
+        self.c.trunc_K[K] += 1
+        self.c.trunc_rank[k] += 1
+        return qu @ (x[:, :k] * sig[:k]), qv @ yt[:k].T
+
+    def truncate_dense(self, X):
+        """Dense -> low-rank conversion by the same truncated SVD (Sec. 3.1)."""
+        m, n = X.shape
+        x, sig, yt = np.linalg.svd(X, full_matrices=False)
+        k = self._keep(sig)
+        self.c.flops["svd_dense"] += 21.0 * m * n * min(m, n)
+        self.c.events["truncate_dense"] += 1
+        self.c.trunc_rank[k] += 1
+        return x[:, :k] * sig[:k], yt[:k].T.copy()

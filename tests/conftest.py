@@ -1,0 +1,25 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a) and the built library")
+    config.addinivalue_line("markers", "slow: longer CPU test")
+
+
+@pytest.fixture(scope="session")
+def prob320():
+    from bem_inputs import build_problem
+    return build_problem(2, 32, 2.0, 1e-4, nrhs=2)
+
+
+@pytest.fixture(scope="session")
+def prob1280():
+    from bem_inputs import build_problem
+    return build_problem(3, 32, 2.0, 1e-4, nrhs=1)
