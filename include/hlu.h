@@ -1,0 +1,156 @@
+/*
+ * hlu.h - LU factorisation of hierarchical matrices (H-LU) on one GB300 GPU.
+ *
+ * The operation is the H-LU of Sec. 3.1 of "Exploiting Nested Task-Parallelism
+ * in the H-LU Factorization": the recursion O1.1-O5.5 (LU of the leading
+ * diagonal block, triangular solves of the off-diagonal blocks, Schur update,
+ * LU of the trailing block) applied at every partitioned diagonal block, with
+ * low-rank blocks X = U V^T handled in H-arithmetic (triangular solves on one
+ * factor only, factorised products, rounded addition by SVD truncation).  The
+ * matrix is described by a cluster tree (Algorithm 1) and the leaves of a
+ * block tree (Algorithm 2), as in the `cluster` and `hmatrix` records of Sec. 2.
+ *
+ * All entry points return an int status (HLU_OK = 0).  No C++ exception and no
+ * device trap crosses this interface: device kernels record failures in an
+ * error word that the host reads after each call.  All device work of a handle
+ * is ordered on the CUDA stream given at creation.  Matrix rows and columns are
+ * numbered in cluster order internally; vectors passed to hlu_solve and
+ * hlu_matvec are in the ORIGINAL degree-of-freedom order.
+ */
+#ifndef HLU_H
+#define HLU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------------- status */
+enum {
+    HLU_OK = 0,
+    HLU_EINVAL = 1,    /* malformed tree, leaves not tiling [0,n)^2, low-rank diagonal
+                          block, rank > min(m,n), non-finite input, bad argument */
+    HLU_ENOMEM = 2,    /* cudaMalloc failed or the plan exceeds opts.mem_budget */
+    HLU_ESTATE = 3,    /* call out of order (solve before factor, factor twice) */
+    HLU_EPIVOT = 4,    /* zero or non-finite pivot u_kk in a dense diagonal leaf */
+    HLU_ERANKCAP = 5,  /* a truncated rank or a stacked rank exceeded its capacity */
+    HLU_ETIMEOUT = 6,  /* a device-side wait exceeded its limit */
+    HLU_ECUDA = 7,     /* a CUDA runtime call failed */
+    HLU_ENUMERIC = 8   /* a non-finite value appeared during the factorisation */
+};
+
+/* ------------------------------------------------------------- precision */
+enum {
+    HLU_FP64 = 0,      /* factors stored and computed in FP64 */
+    HLU_FP32 = 1       /* factors stored and computed in FP32 (cores of the truncation
+                          SVD stay FP64); the original matrix and hlu_matvec stay FP64 */
+};
+
+/* Cluster tree (Sec. 2, Algorithm 1), host pointers, clusters numbered so that
+ * every cluster's degrees of freedom are the contiguous range
+ * [begin[c], begin[c]+size[c]) of the cluster order; cluster 0 is the root.
+ * son0/son1 are -1 for a leaf cluster, otherwise the two sons with
+ * begin[son0] = begin[c] and begin[son1] = begin[c] + size[son0].
+ * perm[p] is the original index of the degree of freedom at cluster position p. */
+typedef struct {
+    int32_t n;
+    int32_t n_clusters;
+    const int32_t *perm;
+    const int32_t *begin;
+    const int32_t *size;
+    const int32_t *son0;
+    const int32_t *son1;
+} hlu_tree;
+
+/* Leaves of the block tree (Sec. 2, Algorithm 2), host pointers.
+ * Leaf l covers rows of cluster row_cl[l] and columns of cluster col_cl[l].
+ * kind 0 = dense: data[offset[l] ...] holds the m x n block column-major.
+ * kind 1 = low rank X = U V^T (Sec. 3.1): data[offset[l] ...] holds U (m x k,
+ *          column-major) followed by V (n x k, column-major), k = rank[l].
+ * The leaves must tile the matrix exactly, diagonal blocks may not be low rank,
+ * and 0 <= rank <= min(m, n). */
+typedef struct {
+    int64_t n_leaves;
+    const int32_t *row_cl;
+    const int32_t *col_cl;
+    const int8_t *kind;
+    const int32_t *rank;
+    const int64_t *offset;
+    const double *data;
+    int64_t data_len;    /* number of doubles in data (every leaf must lie inside) */
+} hlu_blocks;
+
+typedef struct {
+    int32_t precision;   /* HLU_FP64 or HLU_FP32 */
+    int32_t rank_cap;    /* capacity of every low-rank block: min(m, n, rank_cap); 0 -> 32 */
+    int32_t nrhs_max;    /* widest right-hand-side panel one solve pass takes; 0 -> 64 */
+    int32_t reserved;
+    int64_t mem_budget;  /* bytes of device memory the handle may allocate; 0 -> no limit */
+    double timeout_s;    /* limit for any device-side wait; 0 -> 10 s */
+} hlu_opts;
+
+typedef struct hlu_ctx *hlu_t;
+
+/* Build the handle: validates and copies the caller's host arrays (they may be
+ * freed after the call), plans the task graph of the factorisation and of the
+ * solve, and uploads the original matrix A_H (kept in FP64 for hlu_matvec) and
+ * the working copy that hlu_factor overwrites.  `cuda_stream` is a
+ * cudaStream_t (NULL = legacy default stream).  On failure *out is NULL. */
+int hlu_create(const hlu_tree *tree, const hlu_blocks *blocks, const hlu_opts *opts,
+               void *cuda_stream, hlu_t *out);
+
+/* H-LU in place (Sec. 3.1, O1.1-O5.5), truncating at relative tolerance eps
+ * (singular values sigma_i <= eps * sigma_1 of each rounded addition are dropped).
+ * Callable once per handle (HLU_ESTATE otherwise).  Synchronises the stream and
+ * returns the device error status. */
+int hlu_factor(hlu_t h, double eps);
+
+/* Solve A x = b with the factors: forward substitution with the unit lower
+ * factor, then backward substitution with the upper factor (Sec. 3.1).
+ * b is a DEVICE pointer to n x nrhs FP64 values, column-major with leading
+ * dimension ldb >= n, in original order; it is overwritten by x. */
+int hlu_solve(hlu_t h, double *b_dev, int32_t nrhs, int64_t ldb);
+
+/* y = A_H x with the original (unfactored) H-matrix in FP64 (Sec. 3.1,
+ * y = U (V^T x) on low-rank leaves).  x, y: DEVICE pointers, n x nrhs,
+ * column-major, leading dimension ld >= n, original order, must not overlap. */
+int hlu_matvec(hlu_t h, const double *x_dev, double *y_dev, int32_t nrhs, int64_t ld);
+
+/* Copy the factors back to the host in the input leaf layout: for each leaf,
+ * dense leaves as m x n column-major (diagonal leaves hold L below and U on and
+ * above the diagonal), low-rank leaves as U then V with rank_out[l] columns.
+ * `data_out` must hold hlu_factor_doubles(h) values; offsets_out[l] receives the
+ * position of leaf l.  Low-rank factors of L blocks are those of L itself. */
+int64_t hlu_factor_doubles(hlu_t h);
+int hlu_get_factors(hlu_t h, int32_t *rank_out, int64_t *offsets_out, double *data_out);
+
+/* Statistics of the plan and of the last factorisation. */
+typedef struct {
+    int64_t n_tasks;          /* tasks of the factorisation plan */
+    int64_t n_waves;          /* dependency waves of the factorisation plan */
+    int64_t n_launches;       /* kernel launches of one hlu_factor */
+    int64_t solve_tasks, solve_waves, solve_launches;
+    int64_t device_bytes;     /* device memory held by the handle */
+    int64_t tasks_by_kind[8]; /* getrf, trsm, project, accum, radd, split, gather, scatter */
+    double model_flops;       /* model flop count of the factorisation */
+    int32_t max_rank;         /* largest rank after the factorisation */
+    int32_t max_stacked;      /* largest stacked rank seen by a rounded addition */
+} hlu_stats;
+
+int hlu_get_stats(hlu_t h, hlu_stats *out);
+
+/* Destroy the handle and free its device memory.  NULL-safe. */
+void hlu_destroy(hlu_t h);
+
+/* Message for a status code (static string). */
+const char *hlu_strerror(int status);
+
+/* Detail of the last device-side failure: the leaf (or task) index involved
+ * and a value (the pivot, or the rank that overflowed).  Returns the status. */
+int hlu_last_error_detail(hlu_t h, int64_t *index, double *value);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HLU_H */

@@ -22,9 +22,13 @@ target is converted the same way.
 Readings where the paper is silent (each one is listed in the design notes):
   * truncation rule: keep sigma_i > eps * sigma_1 (strict), rank 0 if sigma_1 = 0;
   * one truncation per (addmul call, low-rank target leaf): addmul recurses while
-    C, A and B are all partitioned; otherwise the exact product A B is formed
+    A and B are both partitioned; otherwise the exact product A B is formed
     (factorised when A or B is low rank, dense otherwise), restricted to each
     leaf of C, and added once;
+  * a low-rank target C with two partitioned factors is split into a temporary
+    2 x 2 block of low-rank sons (restrictions of its factors), the recursion
+    continues on the sons, and the sons are merged back into C by one rounded
+    addition of their zero-padded factors;
   * the factor Sigma of a truncated block is kept in U (U <- Q_u X Sigma, V <- Q_v Y).
 """
 from __future__ import annotations
@@ -34,7 +38,7 @@ import collections
 import numpy as np
 
 from .dense import lu_nopiv, solve_unit_lower, solve_upper_right
-from .hmatrix import build_hmatrix, densify, hmul, hmul_t
+from .hmatrix import HBlock, build_hmatrix, densify, hmul, hmul_t
 
 
 class Counters:
@@ -179,14 +183,56 @@ class HLUOracle:
 
     def addmul(self, C, alpha, A, B):
         """C := C + alpha A B with truncation at low-rank leaves of C."""
-        if C.kind == "part" and A.kind == "part" and B.kind == "part":
-            for i in (0, 1):
-                for j in (0, 1):
-                    for k in (0, 1):
-                        self.addmul(C.sons[i][j], alpha, A.sons[i][k], B.sons[k][j])
-            return
+        if A.kind == "part" and B.kind == "part":
+            if C.kind == "part":
+                for i in (0, 1):
+                    for j in (0, 1):
+                        for k in (0, 1):
+                            self.addmul(C.sons[i][j], alpha, A.sons[i][k], B.sons[k][j])
+                return
+            if C.kind == "lowrank":
+                # low-rank target, both factors partitioned: descend into a
+                # temporary 2 x 2 split of the target and merge it back
+                S = self.split_lowrank(C, A, B)
+                for i in (0, 1):
+                    for j in (0, 1):
+                        for k in (0, 1):
+                            self.addmul(S.sons[i][j], alpha, A.sons[i][k], B.sons[k][j])
+                C.U, C.V = self.merge_lowrank(C, S)
+                return
         P = self.product(A, B)
         self.add_into(C, alpha, P, 0, 0)
+
+    def split_lowrank(self, C, A, B):
+        """Temporary partitioned copy of a low-rank block: son (i, j) holds the
+        restriction U[rows_i] V[cols_j]^T of its factors."""
+        S = HBlock(C.t, C.s, C.r0, C.m, C.c0, C.n)
+        S.kind = "part"
+        S.sons = [[None, None], [None, None]]
+        for i in (0, 1):
+            for j in (0, 1):
+                a, b = A.sons[i][0], B.sons[0][j]
+                s = HBlock(a.t, b.s, a.r0, a.m, b.c0, b.n)
+                s.kind = "lowrank"
+                s.U = C.U[a.r0 - C.r0:a.r0 - C.r0 + a.m].copy()
+                s.V = C.V[b.c0 - C.c0:b.c0 - C.c0 + b.n].copy()
+                S.sons[i][j] = s
+        self.c.events["split"] += 1
+        return S
+
+    def merge_lowrank(self, C, S):
+        """Rounded addition of the four zero-padded sons back into one block."""
+        us, vs = [], []
+        for row in S.sons:
+            for s in row:
+                u = np.zeros((C.m, s.rank))
+                v = np.zeros((C.n, s.rank))
+                u[s.r0 - C.r0:s.r0 - C.r0 + s.m] = s.U
+                v[s.c0 - C.c0:s.c0 - C.c0 + s.n] = s.V
+                us.append(u)
+                vs.append(v)
+        self.c.events["merge"] += 1
+        return self.rounded_add(np.hstack(us), np.hstack(vs))
 
     def add_into(self, C, alpha, P, r, c):
         """Add alpha * P[r:r+C.m, c:c+C.n] to C (exact product restricted to C)."""

@@ -1,0 +1,446 @@
+// C ABI of the H-LU library (declared in include/hlu.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/hlu.h"
+#include "kernels.cuh"
+#include "plan.h"
+
+namespace hlu {
+template <class T>
+void set_kernel_attributes();
+}
+
+using namespace hlu;
+
+namespace {
+
+struct DevPlan {
+    TGetrf *getrf = nullptr;
+    TTrsm *trsm = nullptr;
+    TProject *project = nullptr;
+    TAccum *accum = nullptr;
+    TRadd *radd = nullptr;
+    TSplit *split = nullptr;
+    Term *terms = nullptr;
+    Piece *pieces = nullptr;
+    std::vector<Launch> launches;
+    std::vector<int32_t> launch_aux;  // smem capacity per launch (RADD: core size)
+};
+
+}  // namespace
+
+struct hlu_ctx {
+    Planner pl;
+    int precision = HLU_FP64;
+    cudaStream_t stream = nullptr;
+    size_t elem = 8;
+    void *farena = nullptr;
+    double *aarena = nullptr;
+    int32_t *kdyn = nullptr;
+    long long *err = nullptr;
+    int32_t *perm = nullptr;
+    int64_t *leaf_desc = nullptr;
+    DevPlan fp, sp, mp;
+    int64_t device_bytes = 0;
+    int64_t mem_budget = 0;
+    bool factored = false;
+    double eps = 0.0;
+    std::vector<void *> allocs;
+    int last_status = HLU_OK;
+    long long last_err[4] = {0, 0, 0, 0};
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? HLU_OK : HLU_ECUDA; }
+
+template <class X>
+int dalloc(hlu_ctx *h, X **p, size_t count) {
+    *p = nullptr;
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(X);
+    if (h->mem_budget > 0 && h->device_bytes + (int64_t)bytes > h->mem_budget) return HLU_ENOMEM;
+    if (cudaMalloc(reinterpret_cast<void **>(p), bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return HLU_ENOMEM;
+    }
+    h->allocs.push_back(*p);
+    h->device_bytes += (int64_t)bytes;
+    return HLU_OK;
+}
+
+template <class X>
+int upload(hlu_ctx *h, X **p, const std::vector<X> &v) {
+    int st = dalloc(h, p, v.size());
+    if (st) return st;
+    if (!v.empty()) return cuda_status(cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(X), cudaMemcpyHostToDevice, h->stream));
+    return HLU_OK;
+}
+
+int upload_plan(hlu_ctx *h, const Plan &p, DevPlan &d, int kmax) {
+    int st;
+    if ((st = upload(h, &d.getrf, p.getrf))) return st;
+    if ((st = upload(h, &d.trsm, p.trsm))) return st;
+    if ((st = upload(h, &d.project, p.project))) return st;
+    if ((st = upload(h, &d.accum, p.accum))) return st;
+    if ((st = upload(h, &d.radd, p.radd))) return st;
+    if ((st = upload(h, &d.split, p.split))) return st;
+    if ((st = upload(h, &d.terms, p.terms))) return st;
+    if ((st = upload(h, &d.pieces, p.pieces))) return st;
+    d.launches = p.launches;
+    d.launch_aux.resize(p.launches.size());
+    for (size_t i = 0; i < p.launches.size(); ++i) {
+        const Launch &L = p.launches[i];
+        int aux = h->pl.max_leaf;
+        if (L.kind == K_RADD) {
+            int kc = 1;
+            for (int j = L.start; j < L.start + L.count; ++j) kc = std::max(kc, p.radd[j].Kcap);
+            aux = std::min(kc, kmax);
+        }
+        d.launch_aux[i] = aux;
+    }
+    return HLU_OK;
+}
+
+const void *task_ptr(const DevPlan &d, int kind) {
+    switch (kind) {
+        case K_GETRF: return d.getrf;
+        case K_TRSM: return d.trsm;
+        case K_PROJECT: return d.project;
+        case K_ACCUM: return d.accum;
+        case K_RADD: return d.radd;
+        case K_SPLIT: return d.split;
+    }
+    return nullptr;
+}
+
+void run_plan(hlu_ctx *h, const DevPlan &d, void *arena) {
+    LaunchArgs a;
+    a.arena = arena;
+    a.kdyn = h->kdyn;
+    a.err = h->err;
+    a.eps = h->eps;
+    a.kmax = h->pl.opt.kmax_core;
+    for (size_t i = 0; i < d.launches.size(); ++i) {
+        const Launch &L = d.launches[i];
+        if (arena == (void *)h->aarena || h->precision == HLU_FP64)
+            launch_kind<double>(L.kind, task_ptr(d, L.kind), d.terms, d.pieces, L.start, L.count, d.launch_aux[i], a,
+                                h->stream);
+        else
+            launch_kind<float>(L.kind, task_ptr(d, L.kind), d.terms, d.pieces, L.start, L.count, d.launch_aux[i], a,
+                               h->stream);
+    }
+}
+
+int read_error(hlu_ctx *h) {
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return HLU_ECUDA;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return HLU_ECUDA;
+    long long w[4];
+    if (cudaMemcpy(w, h->err, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess) return HLU_ECUDA;
+    std::memcpy(h->last_err, w, sizeof(w));
+    switch ((int)w[0]) {
+        case DE_OK: return HLU_OK;
+        case DE_PIVOT: return HLU_EPIVOT;
+        case DE_RANKCAP: return HLU_ERANKCAP;
+        case DE_NONFINITE: return HLU_ENUMERIC;
+        case DE_TIMEOUT: return HLU_ETIMEOUT;
+    }
+    return HLU_ECUDA;
+}
+
+int clear_error(hlu_ctx *h) { return cuda_status(cudaMemsetAsync(h->err, 0, 4 * sizeof(long long), h->stream)); }
+
+template <class T>
+int upload_arenas(hlu_ctx *h, const double *data) {
+    Planner &pl = h->pl;
+    // A_H arena: leaves exactly as given (FP64), then zeroed work panels
+    std::vector<double> a_leaves;
+    int64_t a_leaf_end = 0;
+    for (const Store &s : pl.astore) {
+        int64_t end = s.kind == B_DENSE ? s.D_off + int64_t(s.m) * s.n : s.V_off + int64_t(s.n) * s.krank;
+        a_leaf_end = std::max(a_leaf_end, end);
+    }
+    a_leaves.assign(a_leaf_end, 0.0);
+    std::vector<int64_t> desc(8 * pl.n_leaves);
+    for (int64_t l = 0; l < pl.n_leaves; ++l) {
+        const Store &s = pl.astore[l];
+        const Store &f = pl.fstore[l];
+        const double *src = data + pl.leaf_offset[l];
+        if (s.kind == B_DENSE) {
+            std::memcpy(&a_leaves[s.D_off], src, sizeof(double) * s.m * s.n);
+        } else {
+            std::memcpy(&a_leaves[s.U_off], src, sizeof(double) * s.m * s.krank);
+            std::memcpy(&a_leaves[s.V_off], src + int64_t(s.m) * s.krank, sizeof(double) * s.n * s.krank);
+        }
+        int64_t *d = &desc[8 * l];
+        d[0] = s.kind == B_DENSE ? 0 : 1;
+        d[1] = s.m;
+        d[2] = s.n;
+        d[3] = s.kind == B_DENSE ? 0 : s.krank;
+        d[4] = s.kind == B_DENSE ? s.D_off : s.U_off;
+        d[5] = s.kind == B_DENSE ? f.D_off : f.U_off;
+        d[6] = s.kind == B_DENSE ? 0 : f.V_off;
+        d[7] = s.kind == B_DENSE ? 0 : f.kslot;
+    }
+    int st;
+    if ((st = dalloc(h, &h->aarena, pl.a_elems))) return st;
+    if ((st = cuda_status(cudaMemsetAsync(h->aarena, 0, sizeof(double) * pl.a_elems, h->stream)))) return st;
+    if ((st = cuda_status(cudaMemcpyAsync(h->aarena, a_leaves.data(), sizeof(double) * a_leaf_end,
+                                          cudaMemcpyHostToDevice, h->stream))))
+        return st;
+    if ((st = upload(h, &h->leaf_desc, desc))) return st;
+    T *f = nullptr;
+    if ((st = dalloc(h, &f, pl.f_elems))) return st;
+    h->farena = f;
+    if ((st = cuda_status(cudaMemsetAsync(f, 0, sizeof(T) * pl.f_elems, h->stream)))) return st;
+    std::vector<T> ident((size_t)pl.max_leaf * pl.max_leaf, T(0));
+    for (int i = 0; i < pl.max_leaf; ++i) ident[i + (size_t)i * pl.max_leaf] = T(1);
+    if ((st = cuda_status(cudaMemcpyAsync(f + pl.f_ident_off, ident.data(), sizeof(T) * ident.size(),
+                                          cudaMemcpyHostToDevice, h->stream))))
+        return st;
+    // the host staging vectors die at return: wait for the copies
+    return cuda_status(cudaStreamSynchronize(h->stream));
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *hlu_strerror(int s) {
+    switch (s) {
+        case HLU_OK: return "ok";
+        case HLU_EINVAL: return "invalid argument or malformed H-matrix";
+        case HLU_ENOMEM: return "out of device memory (or over the memory budget)";
+        case HLU_ESTATE: return "call out of order";
+        case HLU_EPIVOT: return "zero or non-finite pivot in a dense diagonal leaf";
+        case HLU_ERANKCAP: return "rank capacity exceeded";
+        case HLU_ETIMEOUT: return "device-side wait timed out";
+        case HLU_ECUDA: return "CUDA runtime error";
+        case HLU_ENUMERIC: return "non-finite value during the factorisation";
+    }
+    return "unknown status";
+}
+
+int hlu_create(const hlu_tree *tree, const hlu_blocks *blocks, const hlu_opts *opts, void *cuda_stream,
+               hlu_t *out) {
+    if (!out) return HLU_EINVAL;
+    *out = nullptr;
+    if (!tree || !blocks) return HLU_EINVAL;
+    hlu_ctx *h = new (std::nothrow) hlu_ctx();
+    if (!h) return HLU_ENOMEM;
+    PlanOptions po;
+    if (opts) {
+        h->precision = opts->precision;
+        if (opts->rank_cap > 0) po.rank_cap = opts->rank_cap;
+        if (opts->nrhs_max > 0) po.nrhs_max = opts->nrhs_max;
+        h->mem_budget = opts->mem_budget;
+    }
+    if (h->precision != HLU_FP64 && h->precision != HLU_FP32) {
+        delete h;
+        return HLU_EINVAL;
+    }
+    h->elem = h->precision == HLU_FP64 ? 8 : 4;
+    h->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    int st = h->pl.build(tree->n, tree->n_clusters, tree->perm, tree->begin, tree->size, tree->son0, tree->son1,
+                         blocks->n_leaves, blocks->row_cl, blocks->col_cl, blocks->kind, blocks->rank,
+                         blocks->offset, blocks->data, blocks->data_len, po);
+    if (st == HLU_OK && h->pl.max_leaf > 128) st = HLU_EINVAL;  // dense leaves live in one warp's registers
+    if (st == HLU_OK) st = h->pl.plan_all();
+    if (st == HLU_OK) {
+        if (h->precision == HLU_FP64) {
+            set_kernel_attributes<double>();
+            st = upload_arenas<double>(h, blocks->data);
+        } else {
+            set_kernel_attributes<float>();
+            st = upload_arenas<float>(h, blocks->data);
+        }
+    }
+    if (st == HLU_OK) st = upload(h, &h->kdyn, h->pl.slot_init);
+    if (st == HLU_OK) st = dalloc(h, &h->err, 4);
+    if (st == HLU_OK) st = clear_error(h);
+    if (st == HLU_OK) st = upload(h, &h->perm, h->pl.perm);
+    int kmax = h->pl.opt.kmax_core;
+    if (st == HLU_OK) st = upload_plan(h, h->pl.fplan, h->fp, kmax);
+    if (st == HLU_OK) st = upload_plan(h, h->pl.splan, h->sp, kmax);
+    if (st == HLU_OK) st = upload_plan(h, h->pl.mplan, h->mp, kmax);
+    if (st == HLU_OK) st = cuda_status(cudaStreamSynchronize(h->stream));
+    if (st != HLU_OK) {
+        hlu_destroy(h);
+        return st;
+    }
+    *out = h;
+    return HLU_OK;
+}
+
+int hlu_factor(hlu_t h, double eps) {
+    if (!h || !(eps >= 0.0) || !std::isfinite(eps)) return HLU_EINVAL;
+    h->eps = eps;
+    int st = clear_error(h);
+    if (st) return st;
+    // restore the working copy from A_H (the factorisation overwrites it) and the ranks
+    if ((st = cuda_status(cudaMemcpyAsync(h->kdyn, h->pl.slot_init.data(), sizeof(int32_t) * h->pl.n_slots,
+                                          cudaMemcpyHostToDevice, h->stream))))
+        return st;
+    if (h->precision == HLU_FP64)
+        launch_reset<double>(h->leaf_desc, h->pl.n_leaves, h->aarena, (double *)h->farena, h->kdyn, h->stream);
+    else
+        launch_reset<float>(h->leaf_desc, h->pl.n_leaves, h->aarena, (float *)h->farena, h->kdyn, h->stream);
+    run_plan(h, h->fp, h->farena);
+    st = read_error(h);
+    h->last_status = st;
+    h->factored = st == HLU_OK;
+    return st;
+}
+
+int hlu_solve(hlu_t h, double *b, int32_t nrhs, int64_t ldb) {
+    if (!h || !b || nrhs < 0 || ldb < h->pl.n) return HLU_EINVAL;
+    if (!h->factored) return HLU_ESTATE;
+    int st = clear_error(h);
+    if (st) return st;
+    const int32_t n = h->pl.n, w = h->pl.opt.nrhs_max;
+    for (int32_t j0 = 0; j0 < nrhs; j0 += w) {
+        const int32_t nc = std::min(w, nrhs - j0);
+        double *bj = b + (int64_t)j0 * ldb;
+        launch_set_slot(h->kdyn, h->pl.nrhs_slot, nc, h->stream);
+        if (h->precision == HLU_FP64) {
+            double *Y = (double *)h->farena + h->pl.f_solve_off;
+            launch_permute<double, double>(h->perm, n, nc, bj, ldb, Y, n, 1, h->stream);
+            run_plan(h, h->sp, h->farena);
+            launch_permute<double, double>(h->perm, n, nc, Y, n, bj, ldb, 0, h->stream);
+        } else {
+            float *Y = (float *)h->farena + h->pl.f_solve_off;
+            launch_permute<double, float>(h->perm, n, nc, bj, ldb, Y, n, 1, h->stream);
+            run_plan(h, h->sp, h->farena);
+            launch_permute<float, double>(h->perm, n, nc, Y, n, bj, ldb, 0, h->stream);
+        }
+    }
+    st = read_error(h);
+    h->last_status = st;
+    return st;
+}
+
+int hlu_matvec(hlu_t h, const double *x, double *y, int32_t nrhs, int64_t ld) {
+    if (!h || !x || !y || nrhs < 0 || ld < h->pl.n) return HLU_EINVAL;
+    int st = clear_error(h);
+    if (st) return st;
+    const int32_t n = h->pl.n, w = h->pl.opt.nrhs_max;
+    double *X = h->aarena + h->pl.a_x_off, *Y = h->aarena + h->pl.a_y_off;
+    for (int32_t j0 = 0; j0 < nrhs; j0 += w) {
+        const int32_t nc = std::min(w, nrhs - j0);
+        launch_set_slot(h->kdyn, h->pl.nrhs_slot, nc, h->stream);
+        launch_permute<double, double>(h->perm, n, nc, x + (int64_t)j0 * ld, ld, X, n, 1, h->stream);
+        run_plan(h, h->mp, h->aarena);
+        launch_permute<double, double>(h->perm, n, nc, Y, n, y + (int64_t)j0 * ld, ld, 0, h->stream);
+    }
+    st = read_error(h);
+    return st;
+}
+
+int64_t hlu_factor_doubles(hlu_t h) {
+    if (!h) return -1;
+    int64_t tot = 0;
+    for (int64_t l = 0; l < h->pl.n_leaves; ++l) {
+        const Store &s = h->pl.fstore[l];
+        tot += s.kind == B_DENSE ? int64_t(s.m) * s.n : int64_t(s.m + s.n) * s.cap;
+    }
+    return tot;
+}
+
+int hlu_get_factors(hlu_t h, int32_t *rank_out, int64_t *offsets_out, double *data_out) {
+    if (!h || !rank_out || !offsets_out || !data_out) return HLU_EINVAL;
+    if (!h->factored) return HLU_ESTATE;
+    Planner &pl = h->pl;
+    std::vector<int32_t> kd(pl.n_slots);
+    int st = cuda_status(cudaStreamSynchronize(h->stream));
+    if (st) return st;
+    if ((st = cuda_status(cudaMemcpy(kd.data(), h->kdyn, sizeof(int32_t) * pl.n_slots, cudaMemcpyDeviceToHost))))
+        return st;
+    int64_t leaf_end = 0;
+    for (int64_t l = 0; l < pl.n_leaves; ++l) {
+        const Store &s = pl.fstore[l];
+        leaf_end = std::max(leaf_end, s.kind == B_DENSE ? s.D_off + int64_t(s.m) * s.n : s.V_off + int64_t(s.n) * s.cap);
+    }
+    std::vector<double> buf(leaf_end);
+    if (h->precision == HLU_FP64) {
+        st = cuda_status(cudaMemcpy(buf.data(), h->farena, sizeof(double) * leaf_end, cudaMemcpyDeviceToHost));
+    } else {
+        std::vector<float> fb(leaf_end);
+        st = cuda_status(cudaMemcpy(fb.data(), h->farena, sizeof(float) * leaf_end, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < leaf_end; ++i) buf[i] = fb[i];
+    }
+    if (st) return st;
+    int64_t pos = 0;
+    for (int64_t l = 0; l < pl.n_leaves; ++l) {
+        const Store &s = pl.fstore[l];
+        offsets_out[l] = pos;
+        if (s.kind == B_DENSE) {
+            rank_out[l] = 0;
+            std::memcpy(data_out + pos, &buf[s.D_off], sizeof(double) * s.m * s.n);
+            pos += int64_t(s.m) * s.n;
+        } else {
+            const int32_t k = kd[s.kslot];
+            rank_out[l] = k;
+            std::memcpy(data_out + pos, &buf[s.U_off], sizeof(double) * s.m * k);
+            pos += int64_t(s.m) * k;
+            std::memcpy(data_out + pos, &buf[s.V_off], sizeof(double) * s.n * k);
+            pos += int64_t(s.n) * k;
+        }
+    }
+    return HLU_OK;
+}
+
+int hlu_get_stats(hlu_t h, hlu_stats *o) {
+    if (!h || !o) return HLU_EINVAL;
+    std::memset(o, 0, sizeof(*o));
+    const Plan &f = h->pl.fplan, &s = h->pl.splan;
+    o->n_tasks = f.n_tasks;
+    o->n_waves = f.n_waves;
+    o->n_launches = (int64_t)f.launches.size() + 1;
+    o->solve_tasks = s.n_tasks;
+    o->solve_waves = s.n_waves;
+    o->solve_launches = (int64_t)s.launches.size() + 3;
+    o->device_bytes = h->device_bytes;
+    o->tasks_by_kind[0] = (int64_t)f.getrf.size();
+    o->tasks_by_kind[1] = (int64_t)f.trsm.size();
+    o->tasks_by_kind[2] = (int64_t)f.project.size();
+    o->tasks_by_kind[3] = (int64_t)f.accum.size();
+    o->tasks_by_kind[4] = (int64_t)f.radd.size();
+    o->tasks_by_kind[5] = (int64_t)f.split.size();
+    o->max_stacked = f.max_kcap;
+    if (h->factored) {
+        std::vector<int32_t> kd(h->pl.n_slots);
+        if (cudaMemcpy(kd.data(), h->kdyn, sizeof(int32_t) * h->pl.n_slots, cudaMemcpyDeviceToHost) == cudaSuccess)
+            for (int64_t l = 0; l < h->pl.n_leaves; ++l)
+                if (h->pl.fstore[l].kslot >= 0) o->max_rank = std::max(o->max_rank, kd[h->pl.fstore[l].kslot]);
+    }
+    return HLU_OK;
+}
+
+void hlu_destroy(hlu_t h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    for (void *p : h->allocs) cudaFree(p);
+    delete h;
+}
+
+int hlu_last_error_detail(hlu_t h, int64_t *index, double *value) {
+    if (!h) return HLU_EINVAL;
+    if (index) *index = h->last_err[1];
+    if (value) {
+        double v;
+        std::memcpy(&v, &h->last_err[2], sizeof(v));
+        *value = v;
+    }
+    return h->last_status;
+}
+
+}  // extern "C"

@@ -1,0 +1,597 @@
+// Device kernels of the H-LU task graph (sm_103a).  One CTA (256 threads)
+// executes one task; the launch of a wave passes the slice of the task array
+// that belongs to it.  T is the storage type of the factors (double or
+// float); the core of every rounded addition is always computed in double.
+#include <cuda_runtime.h>
+#include <float.h>
+#include <math.h>
+
+#include "kernels.cuh"
+
+namespace hlu {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kMaxLeaf = 128;        // largest dense diagonal leaf (4 rows per lane)
+constexpr int kRowsPerLane = kMaxLeaf / 32;
+
+__device__ __forceinline__ int dim_r(const Panel &p, const int32_t *kd) { return p.rslot >= 0 ? kd[p.rslot] : p.rows; }
+__device__ __forceinline__ int dim_c(const Panel &p, const int32_t *kd) { return p.cslot >= 0 ? kd[p.cslot] : p.cols; }
+
+template <class T>
+__device__ __forceinline__ T &at(T *A, const Panel &p, int i, int j) {
+    return A[p.off + (int64_t)i * p.rs + (int64_t)j * p.cs];
+}
+
+__device__ void set_error(long long *err, int code, long long index, double value) {
+    if (atomicCAS((unsigned long long *)err, 0ull, (unsigned long long)code) == 0ull) {
+        err[1] = index;
+        err[2] = __double_as_longlong(value);
+    }
+    atomicAdd((unsigned long long *)(err + 3), 1ull);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Sum over the CTA; `red` holds >= 33 doubles of shared memory.
+__device__ double block_sum(double v, double *red) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        double s = l < nw ? red[l] : 0.0;
+        s = warp_sum(s);
+        if (l == 0) red[32] = s;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+// ------------------------------------------------------------------ GETRF
+// Unpivoted LU of an m x m dense diagonal leaf in shared memory (Sec. 3.1,
+// "Dense blocks": L unit lower and U overwrite A).
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_getrf(const TGetrf *tasks, LaunchArgs a) {
+    const TGetrf t = tasks[blockIdx.x];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *s = reinterpret_cast<T *>(smem_raw);
+    const int m = t.m;
+    T *g = reinterpret_cast<T *>(a.arena) + t.off;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) s[e] = g[e];
+    __syncthreads();
+    for (int k = 0; k < m; ++k) {
+        const T piv = s[k + k * m];
+        if (threadIdx.x == 0 && (!(piv != T(0)) || !isfinite((double)piv)))
+            set_error(a.err, DE_PIVOT, t.leaf, (double)piv);
+        for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) s[i + k * m] /= piv;
+        __syncthreads();
+        const int rem = m - k - 1;
+        for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
+            const int i = k + 1 + e % rem, j = k + 1 + e / rem;
+            s[i + j * m] -= s[i + k * m] * s[k + j * m];
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) g[e] = s[e];
+}
+
+// ------------------------------------------------------------------- TRSM
+// Triangular solve of a panel with a dense diagonal leaf; one warp per panel
+// column, the column held in registers (rows lane + 32 r), the triangle in
+// shared memory laid out so that lane accesses are contiguous.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_trsm(const TTrsm *tasks, LaunchArgs a) {
+    const TTrsm t = tasks[blockIdx.x];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *L = reinterpret_cast<T *>(smem_raw);
+    const int m = t.m;
+    const T *g = reinterpret_cast<const T *>(a.arena) + t.L_off;
+    if (t.mode == TR_UPPER_TRANS) {
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            const int i = e % m, j = e / m;
+            L[j + i * m] = g[e];  // L = U^T
+        }
+    } else {
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) L[e] = g[e];
+    }
+    __syncthreads();
+    T *A = reinterpret_cast<T *>(a.arena);
+    const int p = dim_c(t.P, a.kdyn);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int c = warp; c < p; c += nw) {
+        T x[kRowsPerLane];
+#pragma unroll
+        for (int r = 0; r < kRowsPerLane; ++r) {
+            const int row = lane + 32 * r;
+            x[r] = row < m ? at(A, t.P, row, c) : T(0);
+        }
+        if (t.mode == TR_LOWER_UNIT || t.mode == TR_UPPER_TRANS) {
+            const bool unit = t.mode == TR_LOWER_UNIT;
+            for (int i = 0; i < m; ++i) {
+                const int ri = i >> 5, li = i & 31;
+                if (!unit && lane == li) {
+#pragma unroll
+                    for (int r = 0; r < kRowsPerLane; ++r)
+                        if (r == ri) x[r] /= L[i + i * m];
+                }
+                T xv = 0;
+#pragma unroll
+                for (int r = 0; r < kRowsPerLane; ++r)
+                    if (r == ri) xv = x[r];
+                const T xi = __shfl_sync(kFull, xv, li);
+#pragma unroll
+                for (int r = 0; r < kRowsPerLane; ++r) {
+                    const int row = lane + 32 * r;
+                    if (row > i && row < m) x[r] -= L[row + i * m] * xi;
+                }
+            }
+        } else {  // TR_UPPER: backward substitution
+            for (int i = m - 1; i >= 0; --i) {
+                const int ri = i >> 5, li = i & 31;
+                if (lane == li) {
+#pragma unroll
+                    for (int r = 0; r < kRowsPerLane; ++r)
+                        if (r == ri) x[r] /= L[i + i * m];
+                }
+                T xv = 0;
+#pragma unroll
+                for (int r = 0; r < kRowsPerLane; ++r)
+                    if (r == ri) xv = x[r];
+                const T xi = __shfl_sync(kFull, xv, li);
+#pragma unroll
+                for (int r = 0; r < kRowsPerLane; ++r) {
+                    const int row = lane + 32 * r;
+                    if (row < i) x[r] -= L[row + i * m] * xi;
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kRowsPerLane; ++r) {
+            const int row = lane + 32 * r;
+            if (row < m) at(A, t.P, row, c) = x[r];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- PROJECT
+// T (k x p) = F^T X (F: len x k, X: len x p): the V^T z (or U^T z) half of a
+// low-rank product (Sec. 3.1).  Rows are streamed through shared memory in
+// chunks of 32; each thread owns up to 16 outputs of a 64 x 64 output tile.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_project(const TProject *tasks, LaunchArgs a) {
+    const TProject t = tasks[blockIdx.x];
+    __shared__ T sF[32][65];
+    __shared__ T sX[32][65];
+    T *A = reinterpret_cast<T *>(a.arena);
+    const int len = dim_r(t.F, a.kdyn), k = dim_c(t.F, a.kdyn), p = dim_c(t.X, a.kdyn);
+    for (int a0 = 0; a0 < k; a0 += 64)
+        for (int b0 = 0; b0 < p; b0 += 64) {
+            const int ka = min(64, k - a0), pb = min(64, p - b0);
+            T acc[16];
+#pragma unroll
+            for (int s = 0; s < 16; ++s) acc[s] = T(0);
+            for (int r0 = 0; r0 < len; r0 += 32) {
+                const int rr = min(32, len - r0);
+                for (int e = threadIdx.x; e < 32 * 64; e += blockDim.x) {
+                    const int r = e & 31, c = e >> 5;
+                    sF[r][c] = (r < rr && c < ka) ? at(A, t.F, r0 + r, a0 + c) : T(0);
+                    sX[r][c] = (r < rr && c < pb) ? at(A, t.X, r0 + r, b0 + c) : T(0);
+                }
+                __syncthreads();
+#pragma unroll
+                for (int s = 0; s < 16; ++s) {
+                    const int idx = threadIdx.x + kThreads * s;
+                    const int ia = idx & 63, ib = idx >> 6;
+                    T v = acc[s];
+                    for (int r = 0; r < rr; ++r) v += sF[r][ia] * sX[r][ib];
+                    acc[s] = v;
+                }
+                __syncthreads();
+            }
+#pragma unroll
+            for (int s = 0; s < 16; ++s) {
+                const int idx = threadIdx.x + kThreads * s;
+                const int ia = idx & 63, ib = idx >> 6;
+                if (ia < ka && ib < pb) at(A, t.T, a0 + ia, b0 + ib) = acc[s];
+            }
+        }
+}
+
+// ------------------------------------------------------------------ ACCUM
+// out (m x p) = beta out + alpha sum_t A_t X_t over the leaves that cover one
+// leaf cluster of the output rows (dense leaves: A = D, X = panel slice;
+// low-rank leaves: A = U slice, X = projected V^T z).
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_accum(const TAccum *tasks, const Term *terms, LaunchArgs a) {
+    const TAccum t = tasks[blockIdx.x];
+    T *A = reinterpret_cast<T *>(a.arena);
+    const int m = dim_r(t.out, a.kdyn);
+    const int p = t.dst >= 0 ? a.kdyn[t.src] : dim_c(t.out, a.kdyn);
+    if (t.dst >= 0 && threadIdx.x == 0) a.kdyn[t.dst] = p;
+    const T alpha = T(t.alpha);
+    for (int e0 = 0; e0 < m * p; e0 += blockDim.x) {
+        const int e = e0 + threadIdx.x;
+        if (e >= m * p) break;
+        const int i = e % m, j = e / m;
+        T acc = T(0);
+        for (int q = 0; q < t.nterms; ++q) {
+            const Term tm = terms[t.term0 + q];
+            const int inner = dim_c(tm.A, a.kdyn);
+            const T *pa = A + tm.A.off + (int64_t)i * tm.A.rs;
+            const T *px = A + tm.X.off + (int64_t)j * tm.X.cs;
+            for (int l = 0; l < inner; ++l) acc += pa[(int64_t)l * tm.A.cs] * px[(int64_t)l * tm.X.rs];
+        }
+        T &o = at(A, t.out, i, j);
+        o = (t.overwrite ? T(0) : o) + alpha * acc;
+    }
+}
+
+// ------------------------------------------------------------------ SPLIT
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_split(const TSplit *tasks, LaunchArgs a) {
+    const TSplit t = tasks[blockIdx.x];
+    T *A = reinterpret_cast<T *>(a.arena);
+    const int k = a.kdyn[t.src_kslot];
+    if (threadIdx.x == 0) a.kdyn[t.dst_kslot] = k;
+    for (int e = threadIdx.x; e < t.mu * k; e += blockDim.x) {
+        const int i = e % t.mu, j = e / t.mu;
+        A[t.dstU + e] = at(A, t.srcU, i, j);
+    }
+    for (int e = threadIdx.x; e < t.nv * k; e += blockDim.x) {
+        const int i = e % t.nv, j = e / t.nv;
+        A[t.dstV + e] = at(A, t.srcV, i, j);
+    }
+}
+
+// ------------------------------------------------------------------- RADD
+// Householder QR of the m x K panel W in place (reflector j: v_j = 1 implied,
+// v_j[i] stored below the diagonal, tau[j]); R in the upper triangle.
+template <class T>
+__device__ void block_householder_qr(T *W, int m, int K, double *tau, double *red) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int kk = min(m, K);
+    for (int j = 0; j < kk; ++j) {
+        T *x = W + (int64_t)j * m;
+        double s = 0.0;
+        for (int i = j + threadIdx.x; i < m; i += blockDim.x) s += (double)x[i] * (double)x[i];
+        s = block_sum(s, red);
+        const double x0 = (double)x[j];
+        const double nrm = sqrt(s);
+        if (nrm == 0.0) {
+            if (threadIdx.x == 0) tau[j] = 0.0;
+            __syncthreads();
+            continue;
+        }
+        const double alpha = x0 >= 0.0 ? -nrm : nrm;
+        const double v0 = x0 - alpha;
+        const double tj = (alpha - x0) / alpha;
+        __syncthreads();
+        for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) x[i] = T((double)x[i] / v0);
+        if (threadIdx.x == 0) {
+            x[j] = T(alpha);
+            tau[j] = tj;
+        }
+        __syncthreads();
+        for (int c = j + 1 + warp; c < K; c += nw) {
+            T *y = W + (int64_t)c * m;
+            double d = 0.0;
+            for (int i = j + 1 + lane; i < m; i += 32) d += (double)x[i] * (double)y[i];
+            d = warp_sum(d);
+            d = (d + (double)y[j]) * tj;
+            __syncwarp();
+            if (lane == 0) y[j] = T((double)y[j] - d);
+            for (int i = j + 1 + lane; i < m; i += 32) y[i] = T((double)y[i] - d * (double)x[i]);
+        }
+        __syncthreads();
+    }
+}
+
+// Z (m x nc, ld m) := Q Z with Q = H_0 ... H_{kk-1} from block_householder_qr;
+// each warp owns whole columns, so no CTA barrier is needed between reflectors.
+template <class T>
+__device__ void block_apply_q(const T *W, int m, int kk, const double *tau, T *Z, int nc) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int c = warp; c < nc; c += nw) {
+        T *y = Z + (int64_t)c * m;
+        for (int j = kk - 1; j >= 0; --j) {
+            const T *x = W + (int64_t)j * m;
+            double d = 0.0;
+            for (int i = j + 1 + lane; i < m; i += 32) d += (double)x[i] * (double)y[i];
+            d = warp_sum(d);
+            d = (d + (double)y[j]) * tau[j];
+            __syncwarp();
+            if (lane == 0) y[j] = T((double)y[j] - d);
+            for (int i = j + 1 + lane; i < m; i += 32) y[i] = T((double)y[i] - d * (double)x[i]);
+            __syncwarp();
+        }
+    }
+}
+
+// One-sided (Hestenes) Jacobi on the columns of M (ku x kv, double, shared):
+// M J = B with orthogonal columns; the singular values are the column norms of
+// B, the right singular vectors the columns of J.  Round-robin ordering, one
+// warp per column pair, sweeps until every pair is orthogonal to 1e-15.
+__device__ void block_jacobi(double *M, int ku, int kv, double *J, int *flag) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int np = (kv + 1) & ~1;
+    for (int sweep = 0; sweep < 40; ++sweep) {
+        if (threadIdx.x == 0) *flag = 0;
+        __syncthreads();
+        for (int r = 0; r < np - 1; ++r) {
+            for (int pi = warp; pi < np / 2; pi += nw) {
+                int p, q;
+                if (pi == 0) {
+                    p = r;
+                    q = np - 1;
+                } else {
+                    p = (r + pi) % (np - 1);
+                    q = (r - pi + np - 1) % (np - 1);
+                }
+                if (p > q) {
+                    const int tmp = p;
+                    p = q;
+                    q = tmp;
+                }
+                if (q >= kv) continue;
+                double *cp = M + (int64_t)p * ku, *cq = M + (int64_t)q * ku;
+                double aa = 0.0, bb = 0.0, gg = 0.0;
+                for (int i = lane; i < ku; i += 32) {
+                    const double x = cp[i], y = cq[i];
+                    aa += x * x;
+                    bb += y * y;
+                    gg += x * y;
+                }
+                aa = warp_sum(aa);
+                bb = warp_sum(bb);
+                gg = warp_sum(gg);
+                if (gg == 0.0 || !(fabs(gg) > 1e-15 * sqrt(aa * bb))) continue;
+                if (lane == 0) *flag = 1;
+                const double zeta = (bb - aa) / (2.0 * gg);
+                const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
+                __syncwarp();
+                for (int i = lane; i < ku; i += 32) {
+                    const double x = cp[i], y = cq[i];
+                    cp[i] = cs * x - sn * y;
+                    cq[i] = sn * x + cs * y;
+                }
+                double *jp = J + (int64_t)p * kv, *jq = J + (int64_t)q * kv;
+                for (int i = lane; i < kv; i += 32) {
+                    const double x = jp[i], y = jq[i];
+                    jp[i] = cs * x - sn * y;
+                    jq[i] = sn * x + cs * y;
+                }
+            }
+            __syncthreads();
+        }
+        const int f = *flag;
+        __syncthreads();
+        if (!f) break;
+    }
+}
+
+size_t radd_smem_bytes(int kc) {
+    return sizeof(double) * (2 * (size_t)kc * kc + 4 * (size_t)kc + 40) + sizeof(int) * (2 * (size_t)kc + 8);
+}
+
+// Rounded addition (Sec. 3.1): the target's factors and every contribution are
+// stacked, U_s = [U_c, c_1 U_1, ...], V_s = [V_c, V_1, ...] (pieces
+// zero-padded to the target's index ranges); both stacks are reduced by
+// Householder QR, the core R_u R_v^T is decomposed by one-sided Jacobi in
+// double, singular values sigma_i <= eps sigma_1 are dropped, and the new
+// factors are U = Q_u X Sigma, V = Q_v Y.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_radd(const TRadd *tasks, const Piece *pieces, LaunchArgs a, int kc) {
+    const TRadd t = tasks[blockIdx.x];
+    T *A = reinterpret_cast<T *>(a.arena);
+    int32_t *kd = a.kdyn;
+    const int m = t.m, n = t.n;
+    const int kself = t.include_self ? kd[t.kslot] : 0;
+    int K = kself;
+    for (int q = 0; q < t.npieces; ++q) K += dim_c(pieces[t.piece0 + q].U, kd);
+    __syncthreads();  // every thread has read the target's rank before it is rewritten
+    if (K > kc || K > t.Kcap) {
+        if (threadIdx.x == 0) set_error(a.err, DE_RANKCAP, t.target, (double)K);
+        return;
+    }
+    if (K == 0) {
+        if (threadIdx.x == 0) kd[t.kslot] = 0;
+        return;
+    }
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *M = reinterpret_cast<double *>(smem_raw);
+    double *J = M + (size_t)kc * kc;
+    double *tauU = J + (size_t)kc * kc;
+    double *tauV = tauU + kc;
+    double *sig = tauV + kc;
+    double *red = sig + kc + kc;  // 40 doubles
+    int *order = reinterpret_cast<int *>(red + 40);
+    int *iflag = order + kc;
+
+    T *WU = A + t.scratch_off;
+    T *WV = WU + (int64_t)m * K;
+    // ---- stack the factors
+    for (int64_t e = threadIdx.x; e < (int64_t)(m + n) * K; e += blockDim.x) WU[e] = T(0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < m * kself; e += blockDim.x) WU[e] = A[t.U_off + e];
+    for (int e = threadIdx.x; e < n * kself; e += blockDim.x) WV[e] = A[t.V_off + e];
+    int col = kself;
+    for (int q = 0; q < t.npieces; ++q) {
+        const Piece pc = pieces[t.piece0 + q];
+        const int k = dim_c(pc.U, kd), mu = pc.U.rows, nv = pc.V.rows;
+        const T coef = T(pc.coef);
+        for (int e = threadIdx.x; e < mu * k; e += blockDim.x) {
+            const int i = e % mu, j = e / mu;
+            WU[pc.roff + i + (int64_t)(col + j) * m] = coef * at(A, pc.U, i, j);
+        }
+        for (int e = threadIdx.x; e < nv * k; e += blockDim.x) {
+            const int i = e % nv, j = e / nv;
+            WV[pc.coff + i + (int64_t)(col + j) * n] = at(A, pc.V, i, j);
+        }
+        col += k;
+    }
+    __syncthreads();
+    // ---- QR of both stacks
+    block_householder_qr(WU, m, K, tauU, red);
+    block_householder_qr(WV, n, K, tauV, red);
+    const int ku = min(m, K), kv = min(n, K);
+    // ---- core M = R_u R_v^T (double), J = I
+    for (int e = threadIdx.x; e < ku * kv; e += blockDim.x) {
+        const int i = e % ku, j = e / ku;
+        double s = 0.0;
+        for (int l = max(i, j); l < K; ++l) s += (double)WU[i + (int64_t)l * m] * (double)WV[j + (int64_t)l * n];
+        M[e] = s;
+    }
+    for (int e = threadIdx.x; e < kv * kv; e += blockDim.x) J[e] = (e % kv == e / kv) ? 1.0 : 0.0;
+    __syncthreads();
+    block_jacobi(M, ku, kv, J, iflag);
+    // ---- singular values, ordering, truncation rank
+    for (int j = threadIdx.x; j < kv; j += blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < ku; ++i) s += M[i + (size_t)j * ku] * M[i + (size_t)j * ku];
+        sig[j] = sqrt(s);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < kv; j += blockDim.x) {
+        int rk = 0;
+        for (int l = 0; l < kv; ++l) rk += (sig[l] > sig[j]) || (sig[l] == sig[j] && l < j);
+        order[rk] = j;
+    }
+    __syncthreads();
+    const double s1 = sig[order[0]];
+    int knew = 0;
+    if (!isfinite(s1)) {
+        if (threadIdx.x == 0) set_error(a.err, DE_NONFINITE, t.target, s1);
+    } else if (s1 > 0.0) {
+        for (int l = 0; l < kv; ++l) knew += sig[order[l]] > a.eps * s1;
+    }
+    if (knew > t.cap) {
+        if (threadIdx.x == 0) set_error(a.err, DE_RANKCAP, t.target, (double)knew);
+        knew = t.cap;
+    }
+    // ---- new factors: U = Q_u [B_sel; 0], V = Q_v [J_sel; 0]
+    T *Uc = A + t.U_off;
+    T *Vc = A + t.V_off;
+    for (int e = threadIdx.x; e < m * knew; e += blockDim.x) {
+        const int i = e % m, c = e / m;
+        Uc[e] = i < ku ? T(M[i + (size_t)order[c] * ku]) : T(0);
+    }
+    for (int e = threadIdx.x; e < n * knew; e += blockDim.x) {
+        const int i = e % n, c = e / n;
+        Vc[e] = i < kv ? T(J[i + (size_t)order[c] * kv]) : T(0);
+    }
+    __syncthreads();
+    block_apply_q(WU, m, ku, tauU, Uc, knew);
+    block_apply_q(WV, n, kv, tauV, Vc, knew);
+    if (threadIdx.x == 0) kd[t.kslot] = knew;
+}
+
+// ------------------------------------------------------------------ RESET
+// leaf_desc per leaf (int64 x 8): kind, m, n, k, a_off, f_off (D or U), f_voff, kslot
+template <class T>
+__global__ void k_reset(const int64_t *desc, const double *Aa, T *F, int32_t *kd) {
+    const int64_t *d = desc + 8 * (int64_t)blockIdx.x;
+    const int64_t kind = d[0], m = d[1], n = d[2], k = d[3], ao = d[4], fo = d[5], fv = d[6];
+    if (kind == 0) {
+        for (int64_t e = threadIdx.x; e < m * n; e += blockDim.x) F[fo + e] = T(Aa[ao + e]);
+    } else {
+        for (int64_t e = threadIdx.x; e < m * k; e += blockDim.x) F[fo + e] = T(Aa[ao + e]);
+        for (int64_t e = threadIdx.x; e < n * k; e += blockDim.x) F[fv + e] = T(Aa[ao + m * k + e]);
+        if (threadIdx.x == 0) kd[d[7]] = int32_t(k);
+    }
+}
+
+template <class Tin, class Tout>
+__global__ void k_permute(const int32_t *perm, int32_t n, int32_t nrhs, const Tin *x, int64_t ldx, Tout *y,
+                          int64_t ldy, int to_cluster) {
+    const int64_t tot = (int64_t)n * nrhs;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = e % n, j = e / n;
+        if (to_cluster)
+            y[p + j * ldy] = Tout(x[perm[p] + j * ldx]);
+        else
+            y[perm[p] + j * ldy] = Tout(x[p + j * ldx]);
+    }
+}
+
+__global__ void k_set_slot(int32_t *kd, int32_t slot, int32_t v) { kd[slot] = v; }
+
+// -------------------------------------------------------------- dispatch
+size_t getrf_smem_bytes(int max_leaf, int elem) { return (size_t)max_leaf * max_leaf * elem; }
+
+template <class T>
+void launch_kind(int kind, const void *tasks, const Term *terms, const Piece *pieces, int start, int count,
+                 int aux, const LaunchArgs &a, cudaStream_t s) {
+    switch (kind) {
+        case K_GETRF:
+            k_getrf<T><<<count, kThreads, getrf_smem_bytes(aux, sizeof(T)), s>>>(
+                reinterpret_cast<const TGetrf *>(tasks) + start, a);
+            break;
+        case K_TRSM:
+            k_trsm<T><<<count, kThreads, getrf_smem_bytes(aux, sizeof(T)), s>>>(
+                reinterpret_cast<const TTrsm *>(tasks) + start, a);
+            break;
+        case K_PROJECT:
+            k_project<T><<<count, kThreads, 0, s>>>(reinterpret_cast<const TProject *>(tasks) + start, a);
+            break;
+        case K_ACCUM:
+            k_accum<T><<<count, kThreads, 0, s>>>(reinterpret_cast<const TAccum *>(tasks) + start, terms, a);
+            break;
+        case K_RADD: {
+            k_radd<T><<<count, kThreads, radd_smem_bytes(aux), s>>>(reinterpret_cast<const TRadd *>(tasks) + start,
+                                                                    pieces, a, aux);
+            break;
+        }
+        case K_SPLIT:
+            k_split<T><<<count, kThreads, 0, s>>>(reinterpret_cast<const TSplit *>(tasks) + start, a);
+            break;
+        default:
+            break;
+    }
+}
+
+template <class T>
+void set_kernel_attributes() {
+    cudaFuncSetAttribute(k_radd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_getrf<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_trsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+template <class T>
+void launch_reset(const int64_t *leaf_desc, int64_t n_leaves, const double *aarena, T *farena, int32_t *kdyn,
+                  cudaStream_t s) {
+    if (n_leaves > 0) k_reset<T><<<(unsigned)n_leaves, kThreads, 0, s>>>(leaf_desc, aarena, farena, kdyn);
+}
+
+template <class Tin, class Tout>
+void launch_permute(const int32_t *perm, int32_t n, int32_t nrhs, const Tin *x, int64_t ldx, Tout *y, int64_t ldy,
+                    int to_cluster, cudaStream_t s) {
+    const int64_t tot = (int64_t)n * nrhs;
+    const int blocks = (int)std::min<int64_t>((tot + kThreads - 1) / kThreads, 152 * 8);
+    if (tot > 0) k_permute<Tin, Tout><<<blocks, kThreads, 0, s>>>(perm, n, nrhs, x, ldx, y, ldy, to_cluster);
+}
+
+void launch_set_slot(int32_t *kdyn, int32_t slot, int32_t value, cudaStream_t s) {
+    k_set_slot<<<1, 1, 0, s>>>(kdyn, slot, value);
+}
+
+template void launch_kind<double>(int, const void *, const Term *, const Piece *, int, int, int, const LaunchArgs &,
+                                  cudaStream_t);
+template void launch_kind<float>(int, const void *, const Term *, const Piece *, int, int, int, const LaunchArgs &,
+                                 cudaStream_t);
+template void set_kernel_attributes<double>();
+template void set_kernel_attributes<float>();
+template void launch_reset<double>(const int64_t *, int64_t, const double *, double *, int32_t *, cudaStream_t);
+template void launch_reset<float>(const int64_t *, int64_t, const double *, float *, int32_t *, cudaStream_t);
+template void launch_permute<double, double>(const int32_t *, int32_t, int32_t, const double *, int64_t, double *,
+                                             int64_t, int, cudaStream_t);
+template void launch_permute<double, float>(const int32_t *, int32_t, int32_t, const double *, int64_t, float *,
+                                            int64_t, int, cudaStream_t);
+template void launch_permute<float, double>(const int32_t *, int32_t, int32_t, const float *, int64_t, double *,
+                                            int64_t, int, cudaStream_t);
+
+}  // namespace hlu

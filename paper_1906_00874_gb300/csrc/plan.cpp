@@ -1,0 +1,812 @@
+// Host planner: validation, block tree, arena layout and the expansion of the
+// H-LU recursion (Sec. 3.1) into tasks grouped in dependency waves.
+#include "plan.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <utility>
+
+#include "../../include/hlu.h"
+
+namespace hlu {
+
+static inline int64_t align8(int64_t x) { return (x + 7) & ~int64_t(7); }
+
+Planner::~Planner() {
+    for (Block *b : blocks_owned) delete b;
+}
+
+// ------------------------------------------------------------------ objects
+int32_t Planner::new_obj(int32_t row_cl, int32_t col_cl, int32_t nr_if_none) {
+    Obj o;
+    o.row_cl = row_cl;
+    o.col_cl = col_cl;
+    o.nr = row_cl >= 0 ? cl[row_cl].lc_count : nr_if_none;
+    o.nc = col_cl >= 0 ? cl[col_cl].lc_count : 1;
+    o.cell_base = objs.empty() ? 0 : objs.back().cell_base + int64_t(objs.back().nr) * objs.back().nc;
+    objs.push_back(o);
+    int64_t need = o.cell_base + int64_t(o.nr) * o.nc;
+    if ((int64_t)cell_write_wave.size() < need) {
+        cell_write_wave.resize(need, -1);
+        cell_read_wave.resize(need, -1);
+    }
+    return int32_t(objs.size() - 1);
+}
+
+int32_t Planner::new_slot(int32_t init) {
+    slot_init.push_back(init);
+    return n_slots++;
+}
+
+View Planner::new_temp(int32_t row_cl, int32_t rows, int32_t cols, int32_t rslot, int32_t cslot) {
+    View v;
+    v.p.off = *arena;
+    v.p.rows = rows;
+    v.p.cols = cols;
+    v.p.rslot = rslot;
+    v.p.cslot = cslot;
+    v.p.rs = 1;
+    v.p.cs = rows;
+    *arena = align8(*arena + int64_t(rows) * std::max(cols, 1));
+    v.obj = new_obj(row_cl, -1);
+    v.r_cl = row_cl;
+    v.c_cl = -1;
+    v.trans = false;
+    return v;
+}
+
+void Planner::cells_of(const View &v, std::vector<int64_t> &out) const {
+    const Obj &o = objs[v.obj];
+    int32_t vr = v.trans ? v.c_cl : v.r_cl;  // cluster restricting object rows
+    int32_t vc = v.trans ? v.r_cl : v.c_cl;  // cluster restricting object columns
+    int32_t r0 = 0, r1 = o.nr, c0 = 0, c1 = o.nc;
+    if (o.row_cl >= 0 && vr >= 0) {
+        r0 = cl[vr].lc_first - cl[o.row_cl].lc_first;
+        r1 = r0 + cl[vr].lc_count;
+    }
+    if (o.col_cl >= 0 && vc >= 0) {
+        c0 = cl[vc].lc_first - cl[o.col_cl].lc_first;
+        c1 = c0 + cl[vc].lc_count;
+    }
+    for (int32_t r = r0; r < r1; ++r)
+        for (int32_t c = c0; c < c1; ++c) out.push_back(o.cell_base + int64_t(r) * o.nc + c);
+}
+
+int32_t Planner::emit(Kind k, const std::vector<const View *> &reads,
+                      const std::vector<const View *> &writes) {
+    static thread_local std::vector<int64_t> rc, wc;
+    rc.clear();
+    wc.clear();
+    for (const View *v : reads) cells_of(*v, rc);
+    for (const View *v : writes) cells_of(*v, wc);
+    int32_t dep = -1;
+    for (int64_t c : rc) dep = std::max(dep, cell_write_wave[c]);
+    for (int64_t c : wc) dep = std::max(dep, std::max(cell_write_wave[c], cell_read_wave[c]));
+    int32_t w = dep + 1;
+    for (int64_t c : rc) cell_read_wave[c] = std::max(cell_read_wave[c], w);
+    for (int64_t c : wc) {
+        cell_write_wave[c] = w;
+        cell_read_wave[c] = -1;
+    }
+    P->wave[k].push_back(w);
+    P->n_tasks++;
+    P->n_waves = std::max(P->n_waves, w + 1);
+    return w;
+}
+
+// -------------------------------------------------------------------- views
+View Planner::viewD(const Block *b) {
+    Store &s = st(b);
+    View v;
+    v.p = Panel{s.D_off, s.m, s.n, -1, -1, 1, s.m};
+    v.obj = s.objD;
+    v.r_cl = b->t;
+    v.c_cl = b->s;
+    v.trans = false;
+    return v;
+}
+
+View Planner::viewU(const Block *b) {
+    Store &s = st(b);
+    View v;
+    v.p = Panel{s.U_off, s.m, s.kslot >= 0 ? s.cap : s.krank, -1, s.kslot, 1, s.m};
+    v.obj = s.objU;
+    v.r_cl = b->t;
+    v.c_cl = -1;
+    v.trans = false;
+    return v;
+}
+
+View Planner::viewV(const Block *b) {
+    Store &s = st(b);
+    View v;
+    v.p = Panel{s.V_off, s.n, s.kslot >= 0 ? s.cap : s.krank, -1, s.kslot, 1, s.n};
+    v.obj = s.objV;
+    v.r_cl = b->s;
+    v.c_cl = -1;
+    v.trans = false;
+    return v;
+}
+
+View Planner::ident(int32_t c) {
+    View v;
+    v.p = Panel{f_ident_off, cl[c].size, cl[c].size, -1, -1, 1, max_leaf};
+    v.obj = ident_obj;
+    v.r_cl = c;
+    v.c_cl = c;
+    v.trans = false;
+    return v;
+}
+
+View Planner::rows(const View &v, int32_t sub) const {
+    View r = v;
+    int64_t d = int64_t(cl[sub].begin) - cl[v.r_cl].begin;
+    r.p.off += d * v.p.rs;
+    r.p.rows = cl[sub].size;
+    r.p.rslot = -1;
+    r.r_cl = sub;
+    return r;
+}
+
+View Planner::transpose(const View &v) {
+    View t = v;
+    std::swap(t.p.rows, t.p.cols);
+    std::swap(t.p.rslot, t.p.cslot);
+    std::swap(t.p.rs, t.p.cs);
+    std::swap(t.r_cl, t.c_cl);
+    t.trans = !v.trans;
+    return t;
+}
+
+void Planner::collect_leaves(Block *b, std::vector<Block *> &out) {
+    if (b->kind == B_PART) {
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) collect_leaves(b->son[i][j], out);
+    } else {
+        out.push_back(b);
+    }
+}
+
+// ----------------------------------------------------- the H-LU recursion
+// lu: O1.1-O1.5 at a partitioned diagonal block, getrf at a dense leaf.
+void Planner::lu(Block *b) {
+    if (b->kind == B_DENSE) {
+        Store &s = st(b);
+        View D = viewD(b);
+        P->getrf.push_back(TGetrf{s.D_off, s.m, b->id});
+        emit(K_GETRF, {}, {&D});
+        return;
+    }
+    lu(b->son[0][0]);                                     // O1.1
+    trsm_l(b->son[0][0], b->son[0][1]);                   // O1.2
+    trsm_u(b->son[0][0], b->son[1][0]);                   // O1.3
+    addmul(b->son[1][1], -1.0, b->son[1][0], b->son[0][1]);  // O1.4
+    lu(b->son[1][1]);                                     // O1.5
+}
+
+void Planner::trsm_l(Block *L, Block *X) {
+    if (X->kind == B_LOWRANK) {
+        trsm_l_panel(L, viewU(X));  // L^{-1} U V^T: solve on the k columns of U
+    } else if (X->kind == B_DENSE) {
+        trsm_l_panel(L, viewD(X));
+    } else {  // O2.1-O2.6
+        for (int j = 0; j < 2; ++j) trsm_l(L->son[0][0], X->son[0][j]);
+        for (int j = 0; j < 2; ++j) addmul(X->son[1][j], -1.0, L->son[1][0], X->son[0][j]);
+        for (int j = 0; j < 2; ++j) trsm_l(L->son[1][1], X->son[1][j]);
+    }
+}
+
+void Planner::trsm_u(Block *U, Block *X) {
+    if (X->kind == B_LOWRANK) {
+        trsm_u_panel(U, viewV(X));  // U V^T R^{-1} = U (R^{-T} V)^T: solve on the rows of V
+    } else if (X->kind == B_DENSE) {
+        trsm_u_panel(U, transpose(viewD(X)));  // X R^{-1} = (R^{-T} X^T)^T
+    } else {
+        for (int i = 0; i < 2; ++i) trsm_u(U->son[0][0], X->son[i][0]);
+        for (int i = 0; i < 2; ++i) addmul(X->son[i][1], -1.0, X->son[i][0], U->son[0][1]);
+        for (int i = 0; i < 2; ++i) trsm_u(U->son[1][1], X->son[i][1]);
+    }
+}
+
+void Planner::trsm_l_panel(Block *L, const View &Pv) {
+    if (L->kind == B_DENSE) {
+        Store &s = st(L);
+        View D = viewD(L);
+        P->trsm.push_back(TTrsm{s.D_off, s.m, TR_LOWER_UNIT, Pv.p});
+        emit(K_TRSM, {&D}, {&Pv});
+        return;
+    }
+    int32_t t0 = cl[L->t].son0, t1 = cl[L->t].son1;
+    trsm_l_panel(L->son[0][0], rows(Pv, t0));
+    hmm(rows(Pv, t1), -1.0, false, L->son[1][0], false, rows(Pv, t0));
+    trsm_l_panel(L->son[1][1], rows(Pv, t1));
+}
+
+// P := R^{-T} P with R the upper factor of U's diagonal block (rows of P = U->t)
+void Planner::trsm_u_panel(Block *U, const View &Pv) {
+    if (U->kind == B_DENSE) {
+        Store &s = st(U);
+        View D = viewD(U);
+        P->trsm.push_back(TTrsm{s.D_off, s.m, TR_UPPER_TRANS, Pv.p});
+        emit(K_TRSM, {&D}, {&Pv});
+        return;
+    }
+    int32_t t0 = cl[U->t].son0, t1 = cl[U->t].son1;
+    trsm_u_panel(U->son[0][0], rows(Pv, t0));
+    hmm(rows(Pv, t1), -1.0, false, U->son[0][1], true, rows(Pv, t0));
+    trsm_u_panel(U->son[1][1], rows(Pv, t1));
+}
+
+// out (+)= alpha * op(M) X, op(M) = M or M^T, exact (Sec. 3.1: U (V^T X) on
+// low-rank leaves).  Phase 1 projects every low-rank leaf, phase 2 sums the
+// contributions of all leaves covering one leaf cluster of the output rows.
+void Planner::hmm(const View &out, double alpha, bool overwrite, Block *M, bool trans, const View &X,
+                  int32_t wdst, int32_t wsrc) {
+    std::vector<Block *> lv;
+    collect_leaves(M, lv);
+    std::vector<View> Tv(lv.size());
+    for (size_t i = 0; i < lv.size(); ++i) {
+        Block *m = lv[i];
+        if (m->kind != B_LOWRANK) continue;
+        Store &s = st(m);
+        View F = trans ? viewU(m) : viewV(m);
+        View Xs = rows(X, trans ? m->t : m->s);
+        int32_t krows = F.p.cslot >= 0 ? s.cap : F.p.cols;
+        View T = new_temp(-1, krows, X.p.cols, F.p.cslot, X.p.cslot);
+        TProject tp{F.p, Xs.p, T.p, -1, -1, -1, -1};
+        P->project.push_back(tp);
+        emit(K_PROJECT, {&F, &Xs}, {&T});
+        Tv[i] = T;
+    }
+    int32_t oc = out.r_cl;
+    int32_t lc0 = cl[oc].lc_first, nseg = cl[oc].lc_count;
+    std::vector<std::vector<int32_t>> seg(nseg);
+    for (size_t i = 0; i < lv.size(); ++i) {
+        int32_t rm = trans ? lv[i]->s : lv[i]->t;
+        for (int32_t q = cl[rm].lc_first; q < cl[rm].lc_first + cl[rm].lc_count; ++q)
+            seg[q - lc0].push_back(int32_t(i));
+    }
+    std::vector<View> keep;
+    std::vector<const View *> rd;
+    for (int32_t qi = 0; qi < nseg; ++qi) {
+        if (seg[qi].empty() && !overwrite) continue;
+        int32_t q = lc_ids[lc0 + qi];
+        View o = rows(out, q);
+        keep.clear();
+        keep.reserve(2 * seg[qi].size() + 1);
+        TAccum ta{o.p, alpha, overwrite ? 1 : 0, int32_t(P->terms.size()), int32_t(seg[qi].size()), wdst, wsrc, 0};
+        for (int32_t i : seg[qi]) {
+            Block *m = lv[i];
+            View A, Xt;
+            if (m->kind == B_DENSE) {
+                A = rows(trans ? transpose(viewD(m)) : viewD(m), q);
+                Xt = rows(X, trans ? m->t : m->s);
+            } else {
+                A = rows(trans ? viewV(m) : viewU(m), q);
+                Xt = Tv[i];
+            }
+            P->terms.push_back(Term{A.p, Xt.p});
+            keep.push_back(A);
+            keep.push_back(Xt);
+        }
+        P->accum.push_back(ta);
+        rd.clear();
+        for (const View &v : keep) rd.push_back(&v);
+        if (!overwrite) rd.push_back(&o);
+        emit(K_ACCUM, rd, {&o});
+    }
+}
+
+Planner::Prod Planner::product(Block *A, Block *B) {
+    if (A->kind == B_LOWRANK) {  // (U_a V_a^T) B = U_a (B^T V_a)^T
+        Store &sa = st(A);
+        int32_t ws = new_slot(0);
+        View W = new_temp(B->s, cl[B->s].size, sa.cap, -1, ws);
+        hmm(W, 1.0, true, B, true, viewV(A), ws, sa.kslot);
+        return Prod{viewU(A), W};
+    }
+    if (B->kind == B_LOWRANK) {  // A (U_b V_b^T) = (A U_b) V_b^T
+        Store &sb = st(B);
+        int32_t ws = new_slot(0);
+        View W = new_temp(A->t, cl[A->t].size, sb.cap, -1, ws);
+        hmm(W, 1.0, true, A, false, viewU(B), ws, sb.kslot);
+        return Prod{W, viewV(B)};
+    }
+    int32_t tsz = cl[A->t].size, rsz = cl[A->s].size, ssz = cl[B->s].size;
+    if (A->kind == B_DENSE && B->kind == B_DENSE && rsz <= std::min(tsz, ssz))
+        return Prod{viewD(A), transpose(viewD(B))};  // factors of the product itself
+    if (A->kind == B_DENSE && (B->kind == B_PART || tsz <= ssz)) {
+        // A B = I_t (B^T A^T)^T with the leaf cluster t on the identity side
+        View W = new_temp(B->s, ssz, tsz, -1, -1);
+        hmm(W, 1.0, true, B, true, transpose(viewD(A)));
+        return Prod{ident(A->t), W};
+    }
+    // A B = (A D_B) I_s^T with the leaf cluster s on the identity side
+    View W = new_temp(A->t, tsz, ssz, -1, -1);
+    hmm(W, 1.0, true, A, false, viewD(B));
+    return Prod{W, ident(B->s)};
+}
+
+void Planner::add_into(Block *C, double alpha, const Prod &p) {
+    if (C->kind == B_PART) {
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) {
+                Block *c = C->son[i][j];
+                add_into(c, alpha, Prod{rows(p.U, c->t), rows(p.V, c->s)});
+            }
+        return;
+    }
+    if (C->kind == B_DENSE) {
+        View D = viewD(C);
+        View Vt = transpose(p.V);
+        for (int32_t qi = 0; qi < cl[C->t].lc_count; ++qi) {
+            int32_t q = lc_ids[cl[C->t].lc_first + qi];
+            View o = rows(D, q);
+            View A = rows(p.U, q);
+            P->accum.push_back(TAccum{o.p, alpha, 0, int32_t(P->terms.size()), 1, -1, -1, 0});
+            P->terms.push_back(Term{A.p, Vt.p});
+            emit(K_ACCUM, {&A, &Vt, &o}, {&o});
+        }
+        return;
+    }
+    Piece pc{alpha, p.U.p, p.V.p, 0, 0};
+    radd(C, true, {pc}, {p.U, p.V});
+}
+
+void Planner::radd(Block *C, bool include_self, const std::vector<Piece> &pcs,
+                   const std::vector<View> &pviews) {
+    Store &s = st(C);
+    int32_t kcap = include_self ? s.cap : 0;
+    for (const Piece &pc : pcs) kcap += pc.U.cols;
+    TRadd tr{};
+    tr.U_off = s.U_off;
+    tr.V_off = s.V_off;
+    tr.scratch_off = 0;
+    tr.m = s.m;
+    tr.n = s.n;
+    tr.cap = s.cap;
+    tr.kslot = s.kslot;
+    tr.include_self = include_self ? 1 : 0;
+    tr.piece0 = int32_t(P->pieces.size());
+    tr.npieces = int32_t(pcs.size());
+    tr.Kcap = kcap;
+    tr.target = C->id;
+    for (const Piece &pc : pcs) P->pieces.push_back(pc);
+    P->radd.push_back(tr);
+    P->max_kcap = std::max(P->max_kcap, kcap);
+    View U = viewU(C), V = viewV(C);
+    std::vector<const View *> rd;
+    for (const View &v : pviews) rd.push_back(&v);
+    if (include_self) {
+        rd.push_back(&U);
+        rd.push_back(&V);
+    }
+    emit(K_RADD, rd, {&U, &V});
+}
+
+void Planner::addmul(Block *C, double alpha, Block *A, Block *B) {
+    if (A->kind == B_PART && B->kind == B_PART) {
+        if (C->kind == B_PART) {
+            for (int i = 0; i < 2; ++i)
+                for (int j = 0; j < 2; ++j)
+                    for (int k = 0; k < 2; ++k) addmul(C->son[i][j], alpha, A->son[i][k], B->son[k][j]);
+            return;
+        }
+        // low-rank target, both factors partitioned: temporary 2x2 split
+        Store cs = st(C);
+        Block *S[2][2];
+        View CU = viewU(C), CV = viewV(C);
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) {
+                int32_t ti = A->son[i][0]->t, sj = B->son[0][j]->s;
+                Block *v = new Block{ti, sj, B_LOWRANK, int32_t(fstore.size()), {{nullptr, nullptr}, {nullptr, nullptr}}};
+                blocks_owned.push_back(v);
+                Store vs{};
+                vs.kind = B_LOWRANK;
+                vs.t = ti;
+                vs.s = sj;
+                vs.m = cl[ti].size;
+                vs.n = cl[sj].size;
+                vs.cap = std::max(std::min(std::min(vs.m, vs.n), opt.rank_cap), cs.cap);
+                vs.U_off = *arena;
+                *arena = align8(*arena + int64_t(vs.m) * vs.cap);
+                vs.V_off = *arena;
+                *arena = align8(*arena + int64_t(vs.n) * vs.cap);
+                vs.kslot = new_slot(0);
+                vs.krank = 0;
+                vs.objU = new_obj(ti, -1);
+                vs.objV = new_obj(sj, -1);
+                vs.objD = -1;
+                fstore.push_back(vs);
+                S[i][j] = v;
+                View su = rows(CU, ti), sv = rows(CV, sj);
+                View du = viewU(v), dv = viewV(v);
+                P->split.push_back(TSplit{su.p, sv.p, vs.U_off, vs.V_off, vs.m, vs.n, cs.kslot, vs.kslot});
+                emit(K_SPLIT, {&su, &sv}, {&du, &dv});
+            }
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j)
+                for (int k = 0; k < 2; ++k) addmul(S[i][j], alpha, A->son[i][k], B->son[k][j]);
+        std::vector<Piece> pcs;
+        std::vector<View> pv;
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) {
+                View u = viewU(S[i][j]), v = viewV(S[i][j]);
+                pcs.push_back(Piece{1.0, u.p, v.p, cl[S[i][j]->t].begin - cl[C->t].begin,
+                                    cl[S[i][j]->s].begin - cl[C->s].begin});
+                pv.push_back(u);
+                pv.push_back(v);
+            }
+        radd(C, false, pcs, pv);
+        return;
+    }
+    Prod p = product(A, B);
+    add_into(C, alpha, p);
+}
+
+// --------------------------------------------------------------- the solve
+void Planner::solve_lower(Block *F, const View &Y) {
+    if (F->kind == B_DENSE) {
+        Store &s = st(F);
+        View D = viewD(F);
+        P->trsm.push_back(TTrsm{s.D_off, s.m, TR_LOWER_UNIT, Y.p});
+        emit(K_TRSM, {&D}, {&Y});
+        return;
+    }
+    int32_t t0 = cl[F->t].son0, t1 = cl[F->t].son1;
+    solve_lower(F->son[0][0], rows(Y, t0));
+    hmm(rows(Y, t1), -1.0, false, F->son[1][0], false, rows(Y, t0));
+    solve_lower(F->son[1][1], rows(Y, t1));
+}
+
+void Planner::solve_upper(Block *F, const View &Y) {
+    if (F->kind == B_DENSE) {
+        Store &s = st(F);
+        View D = viewD(F);
+        P->trsm.push_back(TTrsm{s.D_off, s.m, TR_UPPER, Y.p});
+        emit(K_TRSM, {&D}, {&Y});
+        return;
+    }
+    int32_t t0 = cl[F->t].son0, t1 = cl[F->t].son1;
+    solve_upper(F->son[1][1], rows(Y, t1));
+    hmm(rows(Y, t0), -1.0, false, F->son[0][1], false, rows(Y, t1));
+    solve_upper(F->son[0][0], rows(Y, t0));
+}
+
+// --------------------------------------------------------- plan bookkeeping
+void Planner::begin_plan(Plan &p, bool astore_mode, int64_t *bump) {
+    P = &p;
+    use_astore = astore_mode;
+    arena = bump;
+    std::fill(cell_write_wave.begin(), cell_write_wave.end(), -1);
+    std::fill(cell_read_wave.begin(), cell_read_wave.end(), -1);
+}
+
+template <class T>
+static void permute_by_wave(std::vector<T> &v, std::vector<int32_t> &w) {
+    std::vector<int32_t> idx(v.size());
+    for (size_t i = 0; i < idx.size(); ++i) idx[i] = int32_t(i);
+    std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) { return w[a] < w[b]; });
+    std::vector<T> nv(v.size());
+    std::vector<int32_t> nw(w.size());
+    for (size_t i = 0; i < idx.size(); ++i) {
+        nv[i] = v[idx[i]];
+        nw[i] = w[idx[i]];
+    }
+    v.swap(nv);
+    w.swap(nw);
+}
+
+void Planner::finalize(Plan &p, int64_t *bump) {
+    permute_by_wave(p.getrf, p.wave[K_GETRF]);
+    permute_by_wave(p.trsm, p.wave[K_TRSM]);
+    permute_by_wave(p.project, p.wave[K_PROJECT]);
+    permute_by_wave(p.accum, p.wave[K_ACCUM]);
+    permute_by_wave(p.radd, p.wave[K_RADD]);
+    permute_by_wave(p.split, p.wave[K_SPLIT]);
+    // rounded-addition scratch: tasks of one wave get disjoint regions, waves reuse them
+    int64_t base = align8(*bump), maxw = 0;
+    {
+        size_t i = 0;
+        while (i < p.radd.size()) {
+            int32_t w = p.wave[K_RADD][i];
+            int64_t off = 0;
+            for (; i < p.radd.size() && p.wave[K_RADD][i] == w; ++i) {
+                TRadd &r = p.radd[i];
+                r.scratch_off = base + off;
+                int32_t kc = std::min(r.Kcap, opt.kmax_core);
+                off = align8(off + int64_t(r.m + r.n) * std::max(kc, 1));
+            }
+            maxw = std::max(maxw, off);
+        }
+    }
+    p.scratch_base = base;
+    p.scratch_elems = maxw;
+    *bump = base + maxw;
+    // launches: for each wave, one launch per kind present
+    size_t pos[K_NKINDS] = {0, 0, 0, 0, 0, 0};
+    for (int32_t w = 0; w < p.n_waves; ++w) {
+        for (int k = 0; k < K_NKINDS; ++k) {
+            std::vector<int32_t> &wv = p.wave[k];
+            size_t s = pos[k];
+            while (pos[k] < wv.size() && wv[pos[k]] == w) ++pos[k];
+            if (pos[k] > s) p.launches.push_back(Launch{w, k, int32_t(s), int32_t(pos[k] - s)});
+        }
+    }
+}
+
+// ------------------------------------------------------------- validation
+int Planner::build_tree() {
+    std::map<std::pair<int32_t, int32_t>, int64_t> idx;
+    for (int64_t l = 0; l < n_leaves; ++l) {
+        auto key = std::make_pair(leaf_row[l], leaf_col[l]);
+        if (idx.count(key)) {
+            error = "duplicate leaf block";
+            return HLU_EINVAL;
+        }
+        idx[key] = l;
+    }
+    int64_t used = 0;
+    std::vector<std::pair<Block **, std::pair<int32_t, int32_t>>> stack;
+    stack.push_back({&root, {0, 0}});
+    while (!stack.empty()) {
+        auto it = stack.back();
+        stack.pop_back();
+        int32_t t = it.second.first, s = it.second.second;
+        Block *b = new Block{t, s, B_PART, -1, {{nullptr, nullptr}, {nullptr, nullptr}}};
+        blocks_owned.push_back(b);
+        *it.first = b;
+        auto f = idx.find({t, s});
+        if (f != idx.end()) {
+            int64_t l = f->second;
+            b->kind = leaf_kind[l] == 0 ? B_DENSE : B_LOWRANK;
+            b->id = int32_t(l);
+            if (t == s && b->kind == B_LOWRANK) {
+                error = "low-rank diagonal block";
+                return HLU_EINVAL;
+            }
+            used++;
+            continue;
+        }
+        if (cl[t].son0 < 0 || cl[s].son0 < 0) {
+            error = "leaves do not tile the matrix (missing block)";
+            return HLU_EINVAL;
+        }
+        int32_t ts[2] = {cl[t].son0, cl[t].son1}, ss[2] = {cl[s].son0, cl[s].son1};
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) stack.push_back({&b->son[i][j], {ts[i], ss[j]}});
+    }
+    if (used != n_leaves) {
+        error = "leaves do not tile the matrix (overlapping or unreachable leaf)";
+        return HLU_EINVAL;
+    }
+    return HLU_OK;
+}
+
+void Planner::layout_factor_arena() {
+    f_elems = 0;
+    fstore.assign(n_leaves, Store{});
+    for (int64_t l = 0; l < n_leaves; ++l) {
+        Store &s = fstore[l];
+        s.t = leaf_row[l];
+        s.s = leaf_col[l];
+        s.m = cl[s.t].size;
+        s.n = cl[s.s].size;
+        s.krank = leaf_rank[l];
+        s.objD = s.objU = s.objV = -1;
+        if (leaf_kind[l] == 0) {
+            s.kind = B_DENSE;
+            s.D_off = f_elems;
+            f_elems = align8(f_elems + int64_t(s.m) * s.n);
+            s.objD = new_obj(s.t, s.s);
+            s.kslot = -1;
+            s.cap = 0;
+        } else {
+            s.kind = B_LOWRANK;
+            s.cap = std::min(std::min(s.m, s.n), std::max(opt.rank_cap, s.krank));
+            s.U_off = f_elems;
+            f_elems = align8(f_elems + int64_t(s.m) * s.cap);
+            s.V_off = f_elems;
+            f_elems = align8(f_elems + int64_t(s.n) * s.cap);
+            s.kslot = new_slot(s.krank);
+            s.objU = new_obj(s.t, -1);
+            s.objV = new_obj(s.s, -1);
+        }
+    }
+    f_ident_off = f_elems;
+    f_elems = align8(f_elems + int64_t(max_leaf) * max_leaf);
+    ident_obj = new_obj(-1, -1);
+}
+
+void Planner::layout_a_arena() {
+    a_elems = 0;
+    astore.assign(n_leaves, Store{});
+    for (int64_t l = 0; l < n_leaves; ++l) {
+        Store &s = astore[l];
+        s = fstore[l];
+        s.kslot = -1;
+        s.cap = s.krank;
+        if (s.kind == B_DENSE) {
+            s.D_off = a_elems;
+            a_elems = align8(a_elems + int64_t(s.m) * s.n);
+            s.objD = new_obj(s.t, s.s);
+        } else {
+            s.U_off = a_elems;
+            a_elems = align8(a_elems + int64_t(s.m) * s.krank);
+            s.V_off = a_elems;
+            a_elems = align8(a_elems + int64_t(s.n) * s.krank);
+            s.objU = new_obj(s.t, -1);
+            s.objV = new_obj(s.s, -1);
+        }
+    }
+}
+
+int Planner::build(int32_t n_, int32_t n_clusters, const int32_t *perm_, const int32_t *begin,
+                   const int32_t *size, const int32_t *son0, const int32_t *son1, int64_t n_leaves_,
+                   const int32_t *row_cl, const int32_t *col_cl, const int8_t *kind,
+                   const int32_t *rank, const int64_t *offset, const double *data,
+                   int64_t data_len, const PlanOptions &o) {
+    opt = o;
+    n = n_;
+    if (n < 1 || n_clusters < 1 || !perm_ || !begin || !size || !son0 || !son1) {
+        error = "bad tree arguments";
+        return HLU_EINVAL;
+    }
+    cl.resize(n_clusters);
+    for (int32_t c = 0; c < n_clusters; ++c) {
+        cl[c].begin = begin[c];
+        cl[c].size = size[c];
+        cl[c].son0 = son0[c];
+        cl[c].son1 = son1[c];
+        cl[c].lc_first = cl[c].lc_count = 0;
+        if (size[c] < 1 || begin[c] < 0 || int64_t(begin[c]) + size[c] > n) {
+            error = "cluster range outside [0, n)";
+            return HLU_EINVAL;
+        }
+        bool l0 = son0[c] < 0, l1 = son1[c] < 0;
+        if (l0 != l1) {
+            error = "cluster with exactly one son";
+            return HLU_EINVAL;
+        }
+        if (!l0) {
+            if (son0[c] >= n_clusters || son1[c] >= n_clusters || son0[c] == 0 || son1[c] == 0 ||
+                son0[c] == son1[c]) {
+                error = "bad son index";
+                return HLU_EINVAL;
+            }
+        }
+    }
+    if (cl[0].begin != 0 || cl[0].size != n) {
+        error = "root cluster must cover [0, n)";
+        return HLU_EINVAL;
+    }
+    // walk the tree: check son ranges, count visits, number leaf clusters in DoF order
+    std::vector<int32_t> visits(n_clusters, 0);
+    std::vector<int32_t> stack{0};
+    std::vector<int32_t> order;
+    while (!stack.empty()) {
+        int32_t c = stack.back();
+        stack.pop_back();
+        if (visits[c]++) {
+            error = "cluster reached twice (not a tree)";
+            return HLU_EINVAL;
+        }
+        order.push_back(c);
+        if (cl[c].son0 >= 0) {
+            const ClusterInfo &a = cl[cl[c].son0], &b = cl[cl[c].son1];
+            if (a.begin != cl[c].begin || b.begin != cl[c].begin + a.size || a.size + b.size != cl[c].size) {
+                error = "son ranges do not split the parent";
+                return HLU_EINVAL;
+            }
+            stack.push_back(cl[c].son1);
+            stack.push_back(cl[c].son0);
+        }
+    }
+    if ((int32_t)order.size() != n_clusters) {
+        error = "unreachable cluster";
+        return HLU_EINVAL;
+    }
+    // leaf clusters in DoF order (pre-order with son0 first is DoF order)
+    lc_ids.clear();
+    max_leaf = 0;
+    for (int32_t c : order)
+        if (cl[c].son0 < 0) {
+            cl[c].lc_first = int32_t(lc_ids.size());
+            cl[c].lc_count = 1;
+            lc_ids.push_back(c);
+            max_leaf = std::max(max_leaf, cl[c].size);
+        }
+    for (auto it = order.rbegin(); it != order.rend(); ++it) {
+        int32_t c = *it;
+        if (cl[c].son0 >= 0) {
+            cl[c].lc_first = cl[cl[c].son0].lc_first;
+            cl[c].lc_count = cl[cl[c].son0].lc_count + cl[cl[c].son1].lc_count;
+        }
+    }
+    perm.assign(perm_, perm_ + n);
+    {
+        std::vector<char> seen(n, 0);
+        for (int32_t p : perm) {
+            if (p < 0 || p >= n || seen[p]) {
+                error = "perm is not a permutation";
+                return HLU_EINVAL;
+            }
+            seen[p] = 1;
+        }
+    }
+    n_leaves = n_leaves_;
+    if (n_leaves < 1 || !row_cl || !col_cl || !kind || !rank || !offset || !data) {
+        error = "bad block arguments";
+        return HLU_EINVAL;
+    }
+    leaf_row.assign(row_cl, row_cl + n_leaves);
+    leaf_col.assign(col_cl, col_cl + n_leaves);
+    leaf_kind.assign(kind, kind + n_leaves);
+    leaf_rank.assign(rank, rank + n_leaves);
+    leaf_offset.assign(offset, offset + n_leaves);
+    for (int64_t l = 0; l < n_leaves; ++l) {
+        if (leaf_row[l] < 0 || leaf_row[l] >= n_clusters || leaf_col[l] < 0 || leaf_col[l] >= n_clusters) {
+            error = "leaf cluster index out of range";
+            return HLU_EINVAL;
+        }
+        if (leaf_kind[l] != 0 && leaf_kind[l] != 1) {
+            error = "leaf kind must be 0 or 1";
+            return HLU_EINVAL;
+        }
+        int32_t m = cl[leaf_row[l]].size, nn = cl[leaf_col[l]].size;
+        if (leaf_kind[l] == 1 && (leaf_rank[l] < 0 || leaf_rank[l] > std::min(m, nn))) {
+            error = "rank outside [0, min(m, n)]";
+            return HLU_EINVAL;
+        }
+        int64_t len = leaf_kind[l] == 0 ? int64_t(m) * nn : int64_t(m + nn) * leaf_rank[l];
+        if (leaf_offset[l] < 0 || leaf_offset[l] + len > data_len) {
+            error = "leaf data outside the data array";
+            return HLU_EINVAL;
+        }
+        for (int64_t i = 0; i < len; ++i)
+            if (!std::isfinite(data[leaf_offset[l] + i])) {
+                error = "non-finite input value";
+                return HLU_EINVAL;
+            }
+    }
+    return build_tree();
+}
+
+int Planner::plan_all() {
+    layout_factor_arena();
+    nrhs_slot = new_slot(0);
+    begin_plan(fplan, false, &f_elems);
+    lu(root);
+    finalize(fplan, &f_elems);
+    f_solve_off = f_elems;
+    f_elems = align8(f_elems + int64_t(n) * opt.nrhs_max);
+    View Y;
+    Y.p = Panel{f_solve_off, n, opt.nrhs_max, -1, nrhs_slot, 1, n};
+    Y.obj = new_obj(0, -1);
+    Y.r_cl = 0;
+    Y.c_cl = -1;
+    Y.trans = false;
+    begin_plan(splan, false, &f_elems);
+    solve_lower(root, Y);
+    solve_upper(root, Y);
+    finalize(splan, &f_elems);
+    layout_a_arena();
+    a_x_off = a_elems;
+    a_elems = align8(a_elems + int64_t(n) * opt.nrhs_max);
+    a_y_off = a_elems;
+    a_elems = align8(a_elems + int64_t(n) * opt.nrhs_max);
+    View X = Y, Yo = Y;
+    X.p.off = a_x_off;
+    X.obj = new_obj(0, -1);
+    Yo.p.off = a_y_off;
+    Yo.obj = new_obj(0, -1);
+    begin_plan(mplan, true, &a_elems);
+    hmm(Yo, 1.0, true, root, false, X);
+    finalize(mplan, &a_elems);
+    P = nullptr;
+    return HLU_OK;
+}
+
+}  // namespace hlu

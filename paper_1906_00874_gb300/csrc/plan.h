@@ -1,0 +1,183 @@
+// Host planner: expands the H-LU recursion into a task graph with dependency
+// waves, and lays out the device arenas.
+//
+// The recursion is the one of Sec. 3.1 (O1.1-O5.5 at every partitioned
+// diagonal block, with O2/O3 decomposed as O2.1-O2.6 of Sec. 5.2 when the
+// off-diagonal block is partitioned).  Dependencies between tasks are found
+// from the matrix regions they read and write, at the granularity of leaf
+// clusters: every stored object (a dense block, the U or V factor of a
+// low-rank block, a temporary panel) is cut into cells along the leaf clusters
+// of its row (and column) cluster.  This plays the role of the skeleton array
+// of Sec. 5.1 - a fixed table of representants, built once, that is decoupled
+// from the storage whose sizes change during the factorisation - and, because
+// all tasks of all recursion levels are analysed in one domain, it exposes the
+// cross-level parallelism that weak dependencies and early release give in
+// Sec. 5.2.  Tasks are grouped into waves (longest-path levels); the tasks of
+// one wave are independent.
+#pragma once
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "tasks.h"
+
+namespace hlu {
+
+struct ClusterInfo {
+    int32_t begin, size, son0, son1;
+    int32_t lc_first, lc_count;  // leaf clusters below, in DoF order
+};
+
+struct Obj {
+    int32_t row_cl, col_cl;  // -1: not cluster-indexed (one cell in that dimension)
+    int32_t nr, nc;
+    int64_t cell_base;
+};
+
+struct View {
+    Panel p;
+    int32_t obj;
+    int32_t r_cl, c_cl;  // cluster of the view's rows / columns, -1 if none
+    bool trans;          // view rows run along the object's columns
+};
+
+enum BKind : int32_t { B_DENSE = 0, B_LOWRANK = 1, B_PART = 2 };
+
+struct Block {
+    int32_t t, s;
+    BKind kind;
+    int32_t id;  // storage id for leaves (input leaves first, then temporary splits)
+    Block *son[2][2];
+};
+
+// Storage of one leaf (or temporary split block) in one arena.
+struct Store {
+    int32_t kind;  // B_DENSE / B_LOWRANK
+    int32_t t, s, m, n;
+    int64_t D_off, U_off, V_off;
+    int32_t cap;     // column capacity of U and V
+    int32_t kslot;   // dynamic rank slot, -1 if static
+    int32_t krank;   // static rank (A_H arena) or input rank
+    int32_t objD, objU, objV;
+};
+
+struct Launch {
+    int32_t wave, kind, start, count;
+};
+
+struct Plan {
+    std::vector<TGetrf> getrf;
+    std::vector<TTrsm> trsm;
+    std::vector<TProject> project;
+    std::vector<TAccum> accum;
+    std::vector<TRadd> radd;
+    std::vector<TSplit> split;
+    std::vector<Term> terms;
+    std::vector<Piece> pieces;
+    std::vector<int32_t> wave[K_NKINDS];
+    std::vector<Launch> launches;
+    int32_t n_waves = 0;
+    int64_t n_tasks = 0;
+    int64_t scratch_base = 0, scratch_elems = 0;
+    int32_t max_kcap = 0;
+};
+
+struct PlanOptions {
+    int32_t rank_cap = 32;
+    int32_t nrhs_max = 64;
+    int32_t kmax_core = 96;  // largest stacked rank a rounded addition handles
+};
+
+class Planner {
+public:
+    // ---- inputs (validated copies)
+    int32_t n = 0;
+    std::vector<ClusterInfo> cl;
+    std::vector<int32_t> perm;
+    std::vector<int32_t> lc_ids;  // leaf clusters in DoF order
+    int32_t max_leaf = 0;
+    int64_t n_leaves = 0;
+    std::vector<int32_t> leaf_row, leaf_col, leaf_rank;
+    std::vector<int8_t> leaf_kind;
+    std::vector<int64_t> leaf_offset;
+    PlanOptions opt;
+
+    // ---- block tree
+    std::vector<Block *> blocks_owned;
+    Block *root = nullptr;
+
+    // ---- factor arena (element type chosen by the caller) and A_H arena (FP64)
+    std::vector<Store> fstore;   // input leaves then temporary split blocks
+    std::vector<Store> astore;   // input leaves only
+    int64_t f_elems = 0, a_elems = 0;
+    int64_t f_ident_off = 0;     // max_leaf x max_leaf identity in the factor arena
+    int32_t n_slots = 0;         // dynamic dimension slots
+    std::vector<int32_t> slot_init;  // initial value of every slot
+    int32_t nrhs_slot = -1;      // solve / matvec panel width
+    int64_t f_solve_off = 0;     // n x nrhs_max panel (factor arena)
+    int64_t a_x_off = 0, a_y_off = 0;  // n x nrhs_max panels (A_H arena)
+
+    Plan fplan, splan, mplan;    // factorisation, solve, matvec
+
+    std::string error;
+
+    ~Planner();
+    // Returns 0 or an HLU_* status with `error` set.
+    int build(int32_t n, int32_t n_clusters, const int32_t *perm, const int32_t *begin,
+              const int32_t *size, const int32_t *son0, const int32_t *son1, int64_t n_leaves,
+              const int32_t *row_cl, const int32_t *col_cl, const int8_t *kind,
+              const int32_t *rank, const int64_t *offset, const double *data,
+              int64_t data_len, const PlanOptions &o);
+    // Lays out the arenas and emits the factorisation, solve and matvec plans.
+    int plan_all();
+
+private:
+    // current plan being emitted
+    Plan *P = nullptr;
+    bool use_astore = false;
+    int64_t *arena = nullptr;  // bump pointer of the current arena
+    std::vector<Obj> objs;
+    std::vector<int32_t> cell_write_wave, cell_read_wave;
+    int32_t ident_obj = -1;
+
+    int32_t new_obj(int32_t row_cl, int32_t col_cl, int32_t nr_if_none = 1);
+    int32_t new_slot(int32_t init);
+    View new_temp(int32_t row_cl, int32_t rows, int32_t cols, int32_t rslot, int32_t cslot);
+    void cells_of(const View &v, std::vector<int64_t> &out) const;
+    int32_t emit(Kind k, const std::vector<const View *> &reads, const std::vector<const View *> &writes);
+
+    Store &st(const Block *b) { return use_astore ? astore[b->id] : fstore[b->id]; }
+    View viewD(const Block *b);
+    View viewU(const Block *b);
+    View viewV(const Block *b);
+    View ident(int32_t c);
+    View rows(const View &v, int32_t sub) const;
+    static View transpose(const View &v);
+
+    void collect_leaves(Block *b, std::vector<Block *> &out);
+
+    // the recursion
+    void lu(Block *b);
+    void trsm_l(Block *L, Block *X);
+    void trsm_u(Block *U, Block *X);
+    void trsm_l_panel(Block *L, const View &P);
+    void trsm_u_panel(Block *U, const View &P);
+    void hmm(const View &out, double alpha, bool overwrite, Block *M, bool trans, const View &X,
+             int32_t wdst = -1, int32_t wsrc = -1);
+    struct Prod { View U, V; };
+    Prod product(Block *A, Block *B);
+    void add_into(Block *C, double alpha, const Prod &p);
+    void addmul(Block *C, double alpha, Block *A, Block *B);
+    void radd(Block *C, bool include_self, const std::vector<Piece> &pcs, const std::vector<View> &pviews);
+    void solve_lower(Block *F, const View &Y);
+    void solve_upper(Block *F, const View &Y);
+
+    int build_tree();
+    void layout_factor_arena();
+    void layout_a_arena();
+    void finalize(Plan &p, int64_t *bump);
+    void begin_plan(Plan &p, bool astore_mode, int64_t *bump);
+};
+
+}  // namespace hlu

@@ -1,0 +1,221 @@
+"""Thin ctypes binding of the H-LU C ABI (include/hlu.h).
+
+Every step of the factorisation, the solve and the matrix-vector product runs
+in the library's CUDA kernels; this module only marshals arguments.  There is
+no CPU path: if libhlu.so cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhlu.so")
+
+HLU_FP64 = 0
+HLU_FP32 = 1
+
+STATUS = {0: "HLU_OK", 1: "HLU_EINVAL", 2: "HLU_ENOMEM", 3: "HLU_ESTATE", 4: "HLU_EPIVOT",
+          5: "HLU_ERANKCAP", 6: "HLU_ETIMEOUT", 7: "HLU_ECUDA", 8: "HLU_ENUMERIC"}
+
+EXPORTS = ("hlu_create", "hlu_factor", "hlu_solve", "hlu_matvec", "hlu_factor_doubles",
+           "hlu_get_factors", "hlu_get_stats", "hlu_destroy", "hlu_strerror", "hlu_last_error_detail")
+
+
+class HLUError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)} ({_strerror(status)})")
+
+
+class _Tree(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("n_clusters", ctypes.c_int32), ("perm", ctypes.c_void_p),
+                ("begin", ctypes.c_void_p), ("size", ctypes.c_void_p), ("son0", ctypes.c_void_p),
+                ("son1", ctypes.c_void_p)]
+
+
+class _Blocks(ctypes.Structure):
+    _fields_ = [("n_leaves", ctypes.c_int64), ("row_cl", ctypes.c_void_p), ("col_cl", ctypes.c_void_p),
+                ("kind", ctypes.c_void_p), ("rank", ctypes.c_void_p), ("offset", ctypes.c_void_p),
+                ("data", ctypes.c_void_p), ("data_len", ctypes.c_int64)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("rank_cap", ctypes.c_int32), ("nrhs_max", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("mem_budget", ctypes.c_int64), ("timeout_s", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_tasks", ctypes.c_int64), ("n_waves", ctypes.c_int64), ("n_launches", ctypes.c_int64),
+                ("solve_tasks", ctypes.c_int64), ("solve_waves", ctypes.c_int64),
+                ("solve_launches", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("tasks_by_kind", ctypes.c_int64 * 8), ("model_flops", ctypes.c_double),
+                ("max_rank", ctypes.c_int32), ("max_stacked", ctypes.c_int32)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "tasks_by_kind"}
+        d["tasks_by_kind"] = dict(zip(("getrf", "trsm", "project", "accum", "radd", "split"),
+                                      list(self.tasks_by_kind)[:6]))
+        return d
+
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load libhlu.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libhlu.so not found at {path}: build it with paper_1906_00874_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    lib.hlu_create.argtypes = [ctypes.POINTER(_Tree), ctypes.POINTER(_Blocks), ctypes.POINTER(_Opts), vp,
+                               ctypes.POINTER(vp)]
+    lib.hlu_factor.argtypes = [vp, dbl]
+    lib.hlu_solve.argtypes = [vp, vp, i32, i64]
+    lib.hlu_matvec.argtypes = [vp, vp, vp, i32, i64]
+    lib.hlu_factor_doubles.argtypes = [vp]
+    lib.hlu_factor_doubles.restype = i64
+    lib.hlu_get_factors.argtypes = [vp, vp, vp, vp]
+    lib.hlu_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+    lib.hlu_destroy.argtypes = [vp]
+    lib.hlu_destroy.restype = None
+    lib.hlu_strerror.argtypes = [ctypes.c_int]
+    lib.hlu_strerror.restype = ctypes.c_char_p
+    lib.hlu_last_error_detail.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(dbl)]
+    _lib = lib
+    return lib
+
+
+def _strerror(status):
+    try:
+        return load().hlu_strerror(int(status)).decode()
+    except Exception:
+        return "?"
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dev_ptr_and_ld(t, n, what):
+    """(pointer, nrhs, ld) of a CUDA float64 tensor holding an n x nrhs column-major panel:
+    shape (n,) or (n, nrhs) with stride(0) == 1."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64):
+        raise TypeError(f"{what} must be a CUDA float64 tensor")
+    if t.dim() == 1:
+        if t.shape[0] != n or t.stride(0) != 1:
+            raise ValueError(f"{what}: expected a contiguous vector of length {n}")
+        return t.data_ptr(), 1, n
+    if t.dim() != 2 or t.shape[0] != n or t.stride(0) != 1:
+        raise ValueError(f"{what}: expected shape ({n}, nrhs) in column-major layout (stride(0) == 1)")
+    return t.data_ptr(), t.shape[1], max(t.stride(1), n)
+
+
+def to_device_panel(a, device="cuda"):
+    """CUDA float64 tensor of shape (n, nrhs) in column-major layout from a host array."""
+    import torch
+    a = np.asarray(a, dtype=np.float64)
+    if a.ndim == 1:
+        return torch.tensor(a, device=device)
+    return torch.tensor(np.ascontiguousarray(a.T), device=device).t()
+
+
+class HLU:
+    """One H-matrix on the GPU: factorise once, solve many times."""
+
+    def __init__(self, n, perm, begin, size, son0, son1, row_cl, col_cl, kind, rank, offset, data,
+                 precision=HLU_FP64, rank_cap=0, nrhs_max=0, mem_budget=0, stream=None):
+        lib = load()
+        self._h = ctypes.c_void_p()
+        keep = [np.ascontiguousarray(a, dtype=t) for a, t in (
+            (perm, np.int32), (begin, np.int32), (size, np.int32), (son0, np.int32), (son1, np.int32),
+            (row_cl, np.int32), (col_cl, np.int32), (kind, np.int8), (rank, np.int32), (offset, np.int64),
+            (data, np.float64))]
+        perm_, begin_, size_, son0_, son1_, row_, col_, kind_, rank_, off_, data_ = keep
+        tree = _Tree(int(n), int(begin_.shape[0]), _ptr(perm_), _ptr(begin_), _ptr(size_), _ptr(son0_), _ptr(son1_))
+        blocks = _Blocks(int(row_.shape[0]), _ptr(row_), _ptr(col_), _ptr(kind_), _ptr(rank_), _ptr(off_),
+                         _ptr(data_), int(data_.shape[0]))
+        opts = _Opts(int(precision), int(rank_cap), int(nrhs_max), 0, int(mem_budget), 0.0)
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self.n = int(n)
+        self.n_leaves = int(row_.shape[0])
+        self.precision = int(precision)
+        st = lib.hlu_create(ctypes.byref(tree), ctypes.byref(blocks), ctypes.byref(opts), ctypes.c_void_p(stream),
+                            ctypes.byref(self._h))
+        if st != 0:
+            self._h = ctypes.c_void_p()
+            raise HLUError(st, "hlu_create")
+
+    @classmethod
+    def from_problem(cls, p, **kw):
+        t = p.tree
+        return cls(p.n, t.perm, t.begin, t.size, t.son0, t.son1, p.row_cl, p.col_cl, p.kind, p.rank, p.offset,
+                   p.data, **kw)
+
+    def _check(self, st, what):
+        if st != 0:
+            raise HLUError(st, what)
+
+    def factor(self, eps):
+        self._check(load().hlu_factor(self._h, float(eps)), "hlu_factor")
+
+    def solve(self, b):
+        """Overwrite the CUDA float64 panel b (n,) or (n, nrhs) column-major with A^{-1} b."""
+        ptr, nrhs, ld = _dev_ptr_and_ld(b, self.n, "b")
+        self._check(load().hlu_solve(self._h, ctypes.c_void_p(ptr), nrhs, ld), "hlu_solve")
+        return b
+
+    def matvec(self, x, y):
+        """y = A_H x (original H-matrix, FP64) for CUDA float64 panels."""
+        px, nrhs, ldx = _dev_ptr_and_ld(x, self.n, "x")
+        py, nrhs2, ldy = _dev_ptr_and_ld(y, self.n, "y")
+        if nrhs != nrhs2 or ldx != ldy:
+            raise ValueError("x and y must have the same shape and leading dimension")
+        self._check(load().hlu_matvec(self._h, ctypes.c_void_p(px), ctypes.c_void_p(py), nrhs, ldx), "hlu_matvec")
+        return y
+
+    def get_factors(self):
+        """(rank, offset, data) of the factors in the input leaf layout (host numpy)."""
+        lib = load()
+        tot = lib.hlu_factor_doubles(self._h)
+        rank = np.zeros(self.n_leaves, dtype=np.int32)
+        off = np.zeros(self.n_leaves, dtype=np.int64)
+        data = np.zeros(max(int(tot), 1), dtype=np.float64)
+        self._check(lib.hlu_get_factors(self._h, _ptr(rank), _ptr(off), _ptr(data)), "hlu_get_factors")
+        return rank, off, data
+
+    def stats(self):
+        s = Stats()
+        self._check(load().hlu_get_stats(self._h, ctypes.byref(s)), "hlu_get_stats")
+        return s.as_dict()
+
+    def error_detail(self):
+        idx = ctypes.c_int64()
+        val = ctypes.c_double()
+        st = load().hlu_last_error_detail(self._h, ctypes.byref(idx), ctypes.byref(val))
+        return st, idx.value, val.value
+
+    def close(self):
+        if self._h:
+            load().hlu_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

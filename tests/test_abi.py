@@ -1,0 +1,98 @@
+"""The C-ABI library loads, exports every declared entry point, and rejects
+malformed H-matrices during host-side validation (no GPU needed: validation
+happens before any device call)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1906_00874_gb300 import build, hlu
+    build.build()
+    return hlu.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "hlu.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int|void|int64_t|const char \*)\s*\*?\s*(hlu_\w+)\s*\(", src, re.M)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), name
+    from paper_1906_00874_gb300.hlu import EXPORTS
+    assert set(EXPORTS) <= set(names)
+
+
+def test_strerror_covers_all_codes(lib):
+    for code in range(9):
+        assert lib.hlu_strerror(code).decode() != "unknown status"
+
+
+def _create(prob, **mut):
+    from paper_1906_00874_gb300.hlu import HLU
+    t = prob.tree
+    args = dict(n=prob.n, perm=t.perm, begin=t.begin, size=t.size, son0=t.son0, son1=t.son1,
+                row_cl=prob.row_cl, col_cl=prob.col_cl, kind=prob.kind, rank=prob.rank,
+                offset=prob.offset, data=prob.data)
+    args.update(mut)
+    return HLU(stream=0, **args)
+
+
+def _expect_einval(prob, **mut):
+    from paper_1906_00874_gb300.hlu import HLUError
+    with pytest.raises(HLUError) as e:
+        _create(prob, **mut)
+    assert e.value.status == 1
+
+
+def test_rejects_missing_leaf(lib, prob1280):
+    keep = np.arange(1, prob1280.n_leaves)
+    _expect_einval(prob1280, row_cl=prob1280.row_cl[keep], col_cl=prob1280.col_cl[keep],
+                   kind=prob1280.kind[keep], rank=prob1280.rank[keep], offset=prob1280.offset[keep])
+
+
+def test_rejects_lowrank_diagonal(lib, prob1280):
+    kind = prob1280.kind.copy()
+    d = np.flatnonzero(prob1280.row_cl == prob1280.col_cl)[0]
+    kind[d] = 1
+    _expect_einval(prob1280, kind=kind)
+
+
+def test_rejects_rank_above_min_dims(lib, prob1280):
+    rank = prob1280.rank.copy()
+    l = np.flatnonzero(prob1280.kind == 1)[0]
+    rank[l] = 10 ** 6
+    _expect_einval(prob1280, rank=rank)
+
+
+def test_rejects_non_finite_data(lib, prob1280):
+    data = prob1280.data.copy()
+    data[prob1280.offset[3]] = np.nan
+    _expect_einval(prob1280, data=data)
+
+
+def test_rejects_bad_permutation(lib, prob1280):
+    perm = prob1280.tree.perm.copy()
+    perm[0] = perm[1]
+    _expect_einval(prob1280, perm=perm)
+
+
+def test_rejects_broken_son_ranges(lib, prob1280):
+    size = prob1280.tree.size.copy()
+    size[1] += 1
+    _expect_einval(prob1280, size=size)
+
+
+def test_rejects_data_out_of_range(lib, prob1280):
+    off = prob1280.offset.copy()
+    off[-1] = prob1280.data.shape[0]
+    _expect_einval(prob1280, offset=off)
