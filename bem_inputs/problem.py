@@ -24,9 +24,9 @@ import numpy as np
 
 from .assemble import aca_partial, kernel_block, recompress
 from .mesh import ellipsoid, icosphere, triangle_data
-from .trees import ClusterTree, build_block_leaves, build_cluster_tree
+from .trees import BlockLeaves, ClusterTree, admissible, build_block_leaves, build_cluster_tree
 
-CACHE_VERSION = 3
+CACHE_VERSION = 4
 
 
 class Problem:
@@ -74,6 +74,49 @@ class Problem:
         return self.b[self.tree.perm]
 
 
+def sub_problem(p, cluster):
+    """The diagonal block (cluster, cluster) of p as a problem of its own: the
+    sub-tree of `cluster` renumbered in pre-order, the leaves inside the block
+    with their data copied, b restricted to the block's rows.  (A data-layout
+    operation: the leaves are the same matrix blocks.)"""
+    t = p.tree
+    order = []
+    stack = [int(cluster)]
+    while stack:
+        c = stack.pop()
+        order.append(c)
+        if t.son0[c] >= 0:
+            stack.append(int(t.son1[c]))
+            stack.append(int(t.son0[c]))
+    new_id = {c: i for i, c in enumerate(order)}
+    b0, m = int(t.begin[cluster]), int(t.size[cluster])
+    orig = t.perm[b0:b0 + m].astype(np.int64)
+    rank_of = np.empty(m, dtype=np.int64)
+    rank_of[np.argsort(orig, kind="stable")] = np.arange(m)
+    tree = ClusterTree(
+        begin=[int(t.begin[c]) - b0 for c in order], size=[int(t.size[c]) for c in order],
+        son0=[new_id[int(t.son0[c])] if t.son0[c] >= 0 else -1 for c in order],
+        son1=[new_id[int(t.son1[c])] if t.son1[c] >= 0 else -1 for c in order],
+        level=[int(t.level[c]) - int(t.level[cluster]) for c in order],
+        bmin=t.bmin[order], bmax=t.bmax[order], perm=rank_of)
+    keep = [l for l in range(p.n_leaves) if int(p.row_cl[l]) in new_id and int(p.col_cl[l]) in new_id]
+    chunks, offset = [], []
+    pos = 0
+    for l in keep:
+        mm, nn = p.leaf_shape(l)
+        size = mm * nn if p.kind[l] == 0 else (mm + nn) * int(p.rank[l])
+        o = int(p.offset[l])
+        chunks.append(p.data[o:o + size])
+        offset.append(pos)
+        pos += size
+    return Problem(n=m, r=p.r, leaf=p.leaf, eta=p.eta, eps=p.eps, nrhs=p.nrhs, seed=p.seed, axes=p.axes,
+                   tree=tree, row_cl=np.array([new_id[int(p.row_cl[l])] for l in keep], dtype=np.int32),
+                   col_cl=np.array([new_id[int(p.col_cl[l])] for l in keep], dtype=np.int32),
+                   kind=p.kind[keep].copy(), rank=p.rank[keep].copy(), offset=np.array(offset, dtype=np.int64),
+                   data=np.concatenate(chunks), b=np.asfortranarray(p.b[orig]),
+                   centroid=p.centroid[orig], area=p.area[orig], aca_fallbacks=0, build_seconds=0.0)
+
+
 def _cache_dir():
     d = os.environ.get("HLU_CACHE_DIR") or os.path.join(os.path.expanduser("~"), ".cache", "hlu_gb300")
     os.makedirs(d, exist_ok=True)
@@ -111,47 +154,67 @@ def build_problem(r, leaf, eta, eps, nrhs=1, seed=0, axes=None, cache=True, verb
     bl = build_block_leaves(tree, eta)
     perm = tree.perm.astype(np.int64)
 
-    rank = np.zeros(len(bl), dtype=np.int32)
-    kind = bl.kind.copy()
-    chunks = []
+    rows_out, cols_out, kind_out, rank_out, offset_out, chunks = [], [], [], [], [], []
+    pos = 0
     fallbacks = 0
     rng_check = np.random.default_rng(12345)
-    for l in range(len(bl)):
-        t, s = int(bl.row_cl[l]), int(bl.col_cl[l])
+
+    def emit(t, s, k, U=None, V=None):
+        nonlocal pos
+        rows_out.append(t); cols_out.append(s); kind_out.append(k); offset_out.append(pos)
+        if k == 1:
+            rank_out.append(U.shape[1])
+            chunks.append(np.asfortranarray(U).ravel(order="F"))
+            chunks.append(np.asfortranarray(V).ravel(order="F"))
+            pos += U.size + V.size
+        else:
+            rank_out.append(0)
+            rr = perm[tree.begin[t]:tree.begin[t] + tree.size[t]]
+            cc = perm[tree.begin[s]:tree.begin[s] + tree.size[s]]
+            chunks.append(kernel_block(centroid, area, rr, cc).ravel(order="F"))
+            pos += chunks[-1].size
+
+    def compress(t, s):
+        """Low-rank factors of an admissible block, or None when ACA does not
+        reach the tolerance with k <= min(m, n) / 2 or fails the sample check."""
+        nonlocal fallbacks
         rows = perm[tree.begin[t]:tree.begin[t] + tree.size[t]]
         cols = perm[tree.begin[s]:tree.begin[s] + tree.size[s]]
-        if kind[l] == 1:
-            U, V = aca_partial(centroid, area, rows, cols, eps)
-            ok = U.shape[1] <= min(len(rows), len(cols)) // 2
-            if ok:
-                U, V = recompress(U, V, eps)
-                ii = rng_check.integers(0, len(rows), 64)
-                jj = rng_check.integers(0, len(cols), 64)
-                exact = kernel_block(centroid, area, rows[ii], cols[jj])[np.arange(64), np.arange(64)]
-                approx = np.einsum("ik,ik->i", U[ii], V[jj])
-                ok = np.max(np.abs(exact - approx)) <= 10.0 * eps * np.max(np.abs(exact))
-                if not ok:
-                    fallbacks += 1
-            if ok:
-                rank[l] = U.shape[1]
-                chunks.append(np.asfortranarray(U).ravel(order="F"))
-                chunks.append(np.asfortranarray(V).ravel(order="F"))
-                continue
-            kind[l] = 0
-        chunks.append(kernel_block(centroid, area, rows, cols).ravel(order="F"))
-    sizes = np.array([c.shape[0] for c in chunks], dtype=np.int64)
-    # one leaf may own two chunks (U and V): rebuild offsets per leaf
-    offset = np.zeros(len(bl), dtype=np.int64)
-    pos = 0
-    ci = 0
+        U, V = aca_partial(centroid, area, rows, cols, eps)
+        if U.shape[1] > min(len(rows), len(cols)) // 2:
+            return None
+        U, V = recompress(U, V, eps)
+        ii = rng_check.integers(0, len(rows), 64)
+        jj = rng_check.integers(0, len(cols), 64)
+        exact = kernel_block(centroid, area, rows[ii], cols[jj])[np.arange(64), np.arange(64)]
+        approx = np.einsum("ik,ik->i", U[ii], V[jj])
+        if np.max(np.abs(exact - approx)) > 10.0 * eps * np.max(np.abs(exact)):
+            fallbacks += 1
+            return None
+        return U, V
+
+    def block(t, s, adm):
+        # an admissible block is compressed; if compression fails and both
+        # clusters have sons it is partitioned like an inadmissible block
+        # (Algorithm 2), so a dense leaf always has a leaf cluster on one side
+        if adm:
+            f = compress(t, s)
+            if f is not None:
+                emit(t, s, 1, *f)
+                return
+        if tree.son0[t] >= 0 and tree.son0[s] >= 0:
+            for tt in (tree.son0[t], tree.son1[t]):
+                for ss in (tree.son0[s], tree.son1[s]):
+                    block(int(tt), int(ss), admissible(tree, int(tt), int(ss), eta))
+            return
+        emit(t, s, 0)
+
     for l in range(len(bl)):
-        offset[l] = pos
-        if kind[l] == 1:
-            pos += sizes[ci] + sizes[ci + 1]
-            ci += 2
-        else:
-            pos += sizes[ci]
-            ci += 1
+        block(int(bl.row_cl[l]), int(bl.col_cl[l]), bl.kind[l] == 1)
+    kind = np.array(kind_out, dtype=np.int8)
+    rank = np.array(rank_out, dtype=np.int32)
+    offset = np.array(offset_out, dtype=np.int64)
+    bl = BlockLeaves(rows_out, cols_out, kind)
     data = np.concatenate(chunks) if chunks else np.zeros(0)
     rng = np.random.default_rng(seed)
     b = np.asfortranarray(rng.standard_normal((nrhs, n)).T)

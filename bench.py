@@ -1,0 +1,384 @@
+"""Benchmark: H-LU of the n = 20480 unit-sphere BEM H-matrix and the solve of
+16 right-hand sides to a 1e-10 relative residual on one GB300.
+
+One step = hlu_factor (the whole H-LU task graph) + hlu_solve_refined (solves
+with the factors, FP64 residual H-matvec, update, until every column reaches
+||b - A_H x|| <= 1e-10 ||b||).  The headline arm factorises in FP32 (FP64
+truncation cores); the FP64 arm is timed beside it.  Inputs (the H-matrix and
+b) are resident in HBM when the timed region starts; the working set (factor
+arena >= 4 GB) is far larger than the 129 MB L2, so no L2 flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+N > 1 runs under torch.distributed.run: one independent replica per GPU (the
+factorisation does not shard), barrier + max-over-ranks timing, value = the
+model flops of all ranks / that time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "H-LU GFLOP/s & solves/s to 1e-10 residual, FP32-TC+IR vs FP64; p50/p99 latency"
+WORKLOAD = "sphere20480"  # icosphere r=5, n=20480, leaf 64, eta=2, eps=1e-4, 16 rhs
+TOL = 1e-10
+KIND_NAMES = ("getrf", "trsm", "project", "accum", "radd", "split")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=("native", "reference"))
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison arm")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------- CPU side
+CPU_SAMPLE_LEVEL = 2   # diagonal block of a level-2 cluster (about n/4 unknowns)
+REF_SAMPLE_LEVEL = 3   # reference arm: a level-3 block per step (bounded run time)
+
+
+def _oracle_sample_worker(workload, level, reps):
+    """Run in a single-threaded subprocess: FP64 oracle H-LU of one diagonal block."""
+    import numpy as np
+    from bem_inputs import WORKLOADS, build_problem
+    from bem_inputs.problem import sub_problem
+    from oracle import HLUOracle
+    w = WORKLOADS[workload]
+    p = build_problem(**w)
+    c = int(np.flatnonzero(p.tree.level == level)[0])
+    q = sub_problem(p, c)
+    times, flops = [], 0.0
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        o = HLUOracle(q, q.eps).factor()
+        times.append(time.perf_counter() - t0)
+        flops = o.c.total()
+    print(json.dumps({"n": q.n, "leaves": q.n_leaves, "times": times, "flops": flops}))
+
+
+def oracle_sample(workload, level, reps):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = ("import sys; sys.path.insert(0, %r); import bench; bench._oracle_sample_worker(%r, %d, %d)"
+            % (ROOT, workload, level, reps))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed:\n" + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    reps = args.warmup + args.steps
+    res = oracle_sample(args.workload, REF_SAMPLE_LEVEL, reps)
+    ts = res["times"][args.warmup:]
+    step = sum(ts) / len(ts)
+    gflops = res["flops"] / step / 1e9
+    sample = (f"FP64 oracle H-LU of the leading level-{REF_SAMPLE_LEVEL} diagonal block (n={res['n']}, "
+              f"{res['leaves']} leaves) of the {args.workload} H-matrix per step, factor only, 1 thread")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": gflops, "unit": "GFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample": sample},
+        "cpu_baseline": {"value": gflops, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": gflops, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- GPU side
+class ClockSampler:
+    """nvidia-smi clock and throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        import statistics
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_handle(p, precision, stream):
+    from paper_1906_00874_gb300 import HLU
+    return HLU.from_problem(p, precision=precision, stream=stream)
+
+
+def run_native(args):
+    import numpy as np
+    import torch
+
+    from bem_inputs import WORKLOADS, build_problem
+    from paper_1906_00874_gb300 import HLU_FP32, HLU_FP64, build
+    from paper_1906_00874_gb300.hlu import probe_alu_peaks, to_device_panel
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    w = dict(WORKLOADS[args.workload])
+    p = build_problem(**w)
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    b = to_device_panel(p.b)
+    x = torch.zeros_like(b)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        import torch.distributed as dist
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return t.item()
+
+    def sum_over_ranks(v):
+        if world == 1:
+            return v
+        import torch.distributed as dist
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return t.item()
+
+    def step(h):
+        h.factor(p.eps)
+        it, res = h.solve_refined(b, x, tol=TOL, max_iter=30)
+        return it, res
+
+    def timed_arm(h, steps, warmup):
+        for _ in range(warmup):
+            step(h)
+        torch.cuda.synchronize()
+        launches0 = h.stats()["kernels_launched"]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        iters, resid = [], []
+        barrier()
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        for i in range(steps):
+            it, res = step(h)
+            ev[i + 1].record(stream)
+            iters.append(it)
+            resid.append(res)
+        torch.cuda.synchronize()
+        barrier()
+        per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+        total_ms = ev[0].elapsed_time(ev[steps])
+        st = h.stats()
+        return {"total_ms": total_ms, "per_step_ms": per, "iters": iters, "resid": resid,
+                "launches": st["kernels_launched"] - launches0, "stats": st}
+
+    def flops_per_step(h):
+        st = h.stats()  # counters of the last step: factor + its solves/products
+        return st["model_flops"] + st["solve_flops"], st
+
+    # ---------------- headline arm: FP32 factors + FP64 refinement
+    h32 = make_handle(p, HLU_FP32, sptr)
+    with ClockSampler(local) as clk:
+        arm32 = timed_arm(h32, args.steps, args.warmup)
+    f32, st32 = flops_per_step(h32)
+    t_ms = max_over_ranks(arm32["total_ms"])
+    total_flops = sum_over_ranks(f32 * args.steps)
+    value = total_flops / (t_ms * 1e-3) / 1e9
+    per = sorted(arm32["per_step_ms"])
+
+    def pct(a, q):
+        return a[min(len(a) - 1, int(round(q * (len(a) - 1))))]
+
+    # ---------------- profiled pass (per-kernel-class time, same steps)
+    h32.set_profiling(True)
+    for _ in range(max(1, min(args.steps, 3))):
+        step(h32)
+    torch.cuda.synchronize()
+    prof = h32.stats()
+    h32.set_profiling(False)
+    nprof = max(1, min(args.steps, 3))
+
+    # ---------------- FP64 arm
+    arm64 = None
+    if not args.no_fp64:
+        h64 = make_handle(p, HLU_FP64, sptr)
+        a64 = timed_arm(h64, max(2, args.steps // 3), max(1, args.warmup // 2))
+        f64, st64 = flops_per_step(h64)
+        n64 = len(a64["per_step_ms"])
+        t64 = max_over_ranks(a64["total_ms"]) / n64
+        arm64 = {"time_to_1e10_ms": t64, "gflops": f64 / (t64 * 1e-3) / 1e9, "ir_iters": a64["iters"][-1],
+                 "resid": a64["resid"][-1], "factor_model_gflop": st64["model_flops"] / 1e9,
+                 "max_rank": st64["max_rank"], "steps": n64}
+        h64.close()
+
+    # ---------------- end to end through the public API with host buffers
+    e2e = e2e_arm(p, HLU_FP32, sptr, min(args.steps, 3), f32)
+
+    # ---------------- roofline of the dominant kernel class (profiled pass)
+    fp64_peak, fp32_peak = probe_alu_peaks()
+    ms = prof["kernel_ms"]
+    dom = max(ms, key=lambda k: ms[k])
+    dom_flops = st32["flops_by_kind"][dom]  # per step (factor side)
+    dom_ms = ms[dom] / nprof
+    achieved = dom_flops / (dom_ms * 1e-3) / 1e12 if dom_ms > 0 else 0.0
+    roof = {"kernel": f"k_{dom}<float>", "bound": "alu", "achieved": achieved,
+            "peak": fp32_peak if dom not in ("radd",) else fp64_peak, "unit": "TFLOP/s",
+            "frac": None, "traffic": None,
+            "peak_source": ("measured FP32 FMA probe (hlu_probe_alu_peaks)" if dom != "radd"
+                            else "measured FP64 FMA probe (hlu_probe_alu_peaks): the truncation core is FP64"),
+            "share_of_kernel_time": ms[dom] / max(1e-9, sum(ms.values())),
+            "launches_per_step": prof["kernel_launches"][dom] / nprof,
+            "kernel_ms_per_step": {k: v / nprof for k, v in ms.items()}}
+    roof["frac"] = roof["achieved"] / roof["peak"] if roof["peak"] else None
+
+    cpu = None
+    if rank == 0:
+        try:
+            res = oracle_sample(args.workload, CPU_SAMPLE_LEVEL, 1)
+            cpu = {"value": res["flops"] / res["times"][0] / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                   "sample": (f"FP64 oracle H-LU (factor only) of the leading level-{CPU_SAMPLE_LEVEL} diagonal "
+                              f"block, n={res['n']}, {res['leaves']} leaves, of the same H-matrix; "
+                              f"{res['times'][0]:.1f} s on 1 host thread")}
+        except Exception as e:  # reported, not fatal
+            cpu = {"value": None, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 truncation cores and residual)",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload}: icosphere r=5, n={p.n}, leaf 64, eta=2, eps=1e-4, "
+                                   f"{p.nrhs} rhs ~ N(0,1) seed 0, tol 1e-10",
+                       "n": p.n, "leaves": p.n_leaves, "nrhs": p.nrhs, "l2": "inputs larger than L2 (factor arena "
+                       f"{st32['device_bytes'] / 1e9:.1f} GB)", "parallelism": f"replicas x{world}"},
+            "time_to_1e10_ms": t_ms / args.steps, "solves_per_s": p.nrhs * args.steps * world / (t_ms * 1e-3),
+            "p50_ms": pct(per, 0.5), "p99_ms": pct(per, 0.99), "ir_iters": arm32["iters"][-1],
+            "resid": max(arm32["resid"]), "factor_model_gflop": st32["model_flops"] / 1e9,
+            "step_model_gflop": f32 / 1e9, "max_rank": st32["max_rank"],
+            "fp64_arm": arm64, "e2e": e2e, "gpu_launches": arm32["launches"], "clocks": clk.summary(),
+            "roofline": roof, "cpu_baseline": cpu,
+            "alu_peaks_tflops": {"fp64": fp64_peak, "fp32": fp32_peak},
+            "plan": {"tasks": st32["n_tasks"], "waves": st32["n_waves"], "launches_per_factor": st32["n_launches"]},
+        }
+        print(json.dumps(line), flush=True)
+    h32.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def e2e_arm(p, precision, sptr, steps, flops_step):
+    """Public-API end to end: hlu_create from host arrays (H2D of the H-matrix),
+    factor, b from pinned host memory, refinement, x back to pinned host memory."""
+    import numpy as np
+    import torch
+
+    from paper_1906_00874_gb300 import HLU
+    b_host = torch.tensor(np.ascontiguousarray(p.b.T)).pin_memory()  # (nrhs, n) row-major = n x nrhs col-major
+    x_host = torch.empty_like(b_host).pin_memory()
+    t = p.tree
+    h2d = (p.data.nbytes + p.row_cl.nbytes + p.col_cl.nbytes + p.kind.nbytes + p.rank.nbytes + p.offset.nbytes
+           + t.perm.nbytes + t.begin.nbytes + t.size.nbytes + t.son0.nbytes + t.son1.nbytes + b_host.numel() * 8)
+    d2h = x_host.numel() * 8
+    times = []
+    for i in range(steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = HLU(p.n, t.perm, t.begin, t.size, t.son0, t.son1, p.row_cl, p.col_cl, p.kind, p.rank, p.offset, p.data,
+                precision=precision, stream=sptr)
+        h.factor(p.eps)
+        bd = b_host.to("cuda", non_blocking=True).t()
+        xd = torch.zeros_like(bd)
+        h.solve_refined(bd, xd, tol=TOL, max_iter=30)
+        x_host.copy_(xd.t(), non_blocking=True)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        h.close()
+    ts = times[1:]  # the first call also pays one-time start-up costs
+    sec = sum(ts) / len(ts)
+    return {"value": flops_step / sec / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": sec * 1e3,
+            "includes": "hlu_create (validation, planning, upload) + factor + refinement + copies"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

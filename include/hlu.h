@@ -69,7 +69,9 @@ typedef struct {
  * kind 1 = low rank X = U V^T (Sec. 3.1): data[offset[l] ...] holds U (m x k,
  *          column-major) followed by V (n x k, column-major), k = rank[l].
  * The leaves must tile the matrix exactly, diagonal blocks may not be low rank,
- * and 0 <= rank <= min(m, n). */
+ * 0 <= rank <= min(m, n), and a dense leaf must have a leaf cluster on at least
+ * one side (Algorithm 2 partitions a block whose clusters both have sons unless
+ * it is stored in low-rank form). */
 typedef struct {
     int64_t n_leaves;
     const int32_t *row_cl;
@@ -102,8 +104,10 @@ int hlu_create(const hlu_tree *tree, const hlu_blocks *blocks, const hlu_opts *o
 
 /* H-LU in place (Sec. 3.1, O1.1-O5.5), truncating at relative tolerance eps
  * (singular values sigma_i <= eps * sigma_1 of each rounded addition are dropped).
- * Callable once per handle (HLU_ESTATE otherwise).  Synchronises the stream and
- * returns the device error status. */
+ * Every call first restores the working copy from A_H on the device, so the
+ * handle can be factorised again (e.g. with another eps).  Synchronises the
+ * stream and returns the device error status (HLU_EPIVOT, HLU_ERANKCAP,
+ * HLU_ENUMERIC with details from hlu_last_error_detail). */
 int hlu_factor(hlu_t h, double eps);
 
 /* Solve A x = b with the factors: forward substitution with the unit lower
@@ -125,20 +129,50 @@ int hlu_matvec(hlu_t h, const double *x_dev, double *y_dev, int32_t nrhs, int64_
 int64_t hlu_factor_doubles(hlu_t h);
 int hlu_get_factors(hlu_t h, int32_t *rank_out, int64_t *offsets_out, double *data_out);
 
-/* Statistics of the plan and of the last factorisation. */
+/* Iterative refinement (the solve of the mixed-precision form): starting from
+ * x = 0, repeat d = U^{-1} L^{-1} r (the factors, in their precision), x += d and
+ * r = b - A_H x with the original H-matrix in FP64, until every column meets
+ * ||r_j||_2 <= tol ||b_j||_2 or max_iter solves were applied.  b and x are
+ * DEVICE pointers to n x nrhs FP64 panels (column-major, leading dimension
+ * ld >= n, original order, not overlapping).  *iters_out (may be NULL) gets the
+ * number of solves applied (largest over column chunks), *resid_out (may be
+ * NULL) the largest relative residual reached.  Returns HLU_OK even when tol is
+ * not reached within max_iter; the caller reads *resid_out. */
+int hlu_solve_refined(hlu_t h, const double *b_dev, double *x_dev, int32_t nrhs, int64_t ld, double tol,
+                      int32_t max_iter, int32_t *iters_out, double *resid_out);
+
+/* Statistics of the plan and of the last calls.  Model flops use the standard
+ * operation counts (getrf 2m^3/3, trsm m^2 p, gemm 2mkp, Householder QR
+ * 2 a b^2 - 2 b^3/3, Jacobi SVD 21 K^3, Q times a panel 2mKk'), counted on the
+ * device from the actual (run-time) ranks. */
 typedef struct {
     int64_t n_tasks;          /* tasks of the factorisation plan */
     int64_t n_waves;          /* dependency waves of the factorisation plan */
     int64_t n_launches;       /* kernel launches of one hlu_factor */
     int64_t solve_tasks, solve_waves, solve_launches;
     int64_t device_bytes;     /* device memory held by the handle */
-    int64_t tasks_by_kind[8]; /* getrf, trsm, project, accum, radd, split, gather, scatter */
-    double model_flops;       /* model flop count of the factorisation */
+    int64_t tasks_by_kind[8]; /* getrf, trsm, project, accum, radd, split, -, - */
+    double model_flops;       /* model flops of the last hlu_factor */
+    double flops_by_kind[8];  /* the same, per task kind */
+    double solve_flops;       /* model flops of solves and products since the last hlu_factor */
+    double kernel_ms[8];      /* with profiling on: summed kernel time per task kind */
+    int64_t kernel_launches[8];
+    int64_t kernels_launched; /* kernels this handle launched since it was created */
     int32_t max_rank;         /* largest rank after the factorisation */
-    int32_t max_stacked;      /* largest stacked rank seen by a rounded addition */
+    int32_t max_stacked;      /* largest stacked-rank capacity of a rounded addition */
 } hlu_stats;
 
 int hlu_get_stats(hlu_t h, hlu_stats *out);
+
+/* Profiling: when on, every kernel launch of the handle is bracketed by CUDA
+ * events on the handle's stream and its duration is added to kernel_ms of its
+ * task kind (read with hlu_get_stats).  Turning it on clears the sums. */
+int hlu_set_profiling(hlu_t h, int32_t on);
+
+/* Roofline denominators: FP64 and FP32 fused multiply-add throughput of the
+ * current GPU in TFLOP/s, measured with independent FMA chains on every SM
+ * (a measurement utility, not part of the factorisation). */
+int hlu_probe_alu_peaks(double *fp64_tflops, double *fp32_tflops);
 
 /* Destroy the handle and free its device memory.  NULL-safe. */
 void hlu_destroy(hlu_t h);

@@ -16,8 +16,10 @@ decomposition of O2 into O2.1-O2.6 in Sec. 5.2):
 Products and additions (Sec. 3.1): a product with a low-rank factor stays
 factorised, Z (U V^T) = (Z U) V^T and (U V^T) Z = U (Z^T V)^T.  Adding to a
 low-rank target is rounded addition: stack the factors, take the SVD of the
-sum and drop the small singular values; a dense contribution to a low-rank
-target is converted the same way.
+sum and drop the small singular values.  A product of two dense or partitioned
+blocks is written in factorised form too (an identity factor on the side of
+its leaf cluster), so a dense contribution to a low-rank target is converted
+by the same rounded addition.
 
 Readings where the paper is silent (each one is listed in the design notes):
   * truncation rule: keep sigma_i > eps * sigma_1 (strict), rank 0 if sigma_1 = 0;
@@ -39,6 +41,13 @@ import numpy as np
 
 from .dense import lu_nopiv, solve_unit_lower, solve_upper_right
 from .hmatrix import HBlock, build_hmatrix, densify, hmul, hmul_t
+
+
+def qr_flops(m, K):
+    """Model flops of a Householder QR of an m x K panel: 2 a b^2 - 2 b^3 / 3 with
+    a = max(m, K), b = min(m, K) (Golub and Van Loan)."""
+    a, b = max(m, K), min(m, K)
+    return 2.0 * a * b * b - 2.0 * b ** 3 / 3.0
 
 
 class Counters:
@@ -164,22 +173,29 @@ class HLUOracle:
                 self.c.flops["lrmul"] += 2.0 * (leaf.m + leaf.n) * leaf.rank * p
 
     def product(self, A, B):
-        """Exact A B for aligned blocks: ('lr', U, V) or ('dense', D)."""
+        """Exact A B for aligned blocks as factors (U, V), A B = U V^T.
+
+        Sec. 3.1: a product with a low-rank factor stays factorised,
+        (U_a V_a^T) B = U_a (B^T V_a)^T and A (U_b V_b^T) = (A U_b) V_b^T.  A
+        product of two non-low-rank blocks is written with an identity factor
+        on the side of a leaf cluster (or as the pair of dense factors when
+        the inner dimension is the smallest), so every contribution reaches
+        its target in factorised form."""
         if A.kind == "lowrank":
             self.c.events["prod_lr_left"] += 1
-            return "lr", A.U, self._hmul_t(B, A.V)
+            return A.U, self._hmul_t(B, A.V)
         if B.kind == "lowrank":
             self.c.events["prod_lr_right"] += 1
-            return "lr", self._hmul(A, B.U), B.V
-        if A.kind == "dense":
+            return self._hmul(A, B.U), B.V
+        t, r, s = A.m, A.n, B.n
+        if A.kind == "dense" and B.kind == "dense" and r <= min(t, s):
+            self.c.events["prod_dense_dense"] += 1
+            return A.D, B.D.T
+        if A.kind == "dense" and (B.kind == "part" or t <= s):
             self.c.events["prod_dense_left"] += 1
-            return "dense", self._hmul_t(B, A.D.T).T
-        if B.kind == "dense":
-            self.c.events["prod_dense_right"] += 1
-            return "dense", self._hmul(A, B.D)
-        self.c.events["prod_part_part"] += 1
-        self.c.flops["gemm"] += 2.0 * A.m * A.n * B.n
-        return "dense", densify(A) @ densify(B)
+            return np.eye(t), self._hmul_t(B, A.D.T)
+        self.c.events["prod_dense_right"] += 1
+        return self._hmul(A, B.D), np.eye(s)
 
     def addmul(self, C, alpha, A, B):
         """C := C + alpha A B with truncation at low-rank leaves of C."""
@@ -235,29 +251,21 @@ class HLUOracle:
         return self.rounded_add(np.hstack(us), np.hstack(vs))
 
     def add_into(self, C, alpha, P, r, c):
-        """Add alpha * P[r:r+C.m, c:c+C.n] to C (exact product restricted to C)."""
-        kind, X, Y = (P[0], P[1], P[2]) if P[0] == "lr" else (P[0], P[1], None)
+        """Add alpha * (U V^T)[r:r+C.m, c:c+C.n] to C (exact product restricted to C)."""
+        U, V = P
         if C.kind == "part":
             for row in C.sons:
                 for s in row:
                     self.add_into(s, alpha, P, r + s.r0 - C.r0, c + s.c0 - C.c0)
             return
-        if kind == "lr":
-            Up = X[r:r + C.m]
-            Vp = Y[c:c + C.n]
-            if C.kind == "dense":
-                C.D += alpha * (Up @ Vp.T)
-                self.c.flops["lrexpand"] += 2.0 * C.m * C.n * Up.shape[1]
-                self.c.events["add_dense"] += 1
-            else:
-                C.U, C.V = self.rounded_add(np.hstack([C.U, alpha * Up]), np.hstack([C.V, Vp]))
+        Up = U[r:r + C.m]
+        Vp = V[c:c + C.n]
+        if C.kind == "dense":
+            C.D += alpha * (Up @ Vp.T)
+            self.c.flops["lrexpand"] += 2.0 * C.m * C.n * Up.shape[1]
+            self.c.events["add_dense"] += 1
         else:
-            D = X[r:r + C.m, c:c + C.n]
-            if C.kind == "dense":
-                C.D += alpha * D
-                self.c.events["add_dense"] += 1
-            else:
-                C.U, C.V = self.truncate_dense(C.U @ C.V.T + alpha * D)
+            C.U, C.V = self.rounded_add(np.hstack([C.U, alpha * Up]), np.hstack([C.V, Vp]))
 
     # ------------------------------------------------ rounded addition
     def _keep(self, sig):
@@ -275,20 +283,10 @@ class HLUOracle:
         x, sig, yt = np.linalg.svd(ru @ rv.T)
         k = self._keep(sig)
         ku, kv = ru.shape[0], rv.shape[0]
-        self.c.flops["qr"] += (2.0 * m * K * K - 2.0 * K ** 3 / 3.0) + (2.0 * n * K * K - 2.0 * K ** 3 / 3.0)
+        self.c.flops["qr"] += qr_flops(m, K) + qr_flops(n, K)
         self.c.flops["svd"] += 21.0 * max(ku, kv) ** 3
         self.c.flops["qx"] += 2.0 * (m * ku + n * kv) * k
         self.c.events["rounded_add"] += 1
         self.c.trunc_K[K] += 1
         self.c.trunc_rank[k] += 1
         return qu @ (x[:, :k] * sig[:k]), qv @ yt[:k].T
-
-    def truncate_dense(self, X):
-        """Dense -> low-rank conversion by the same truncated SVD (Sec. 3.1)."""
-        m, n = X.shape
-        x, sig, yt = np.linalg.svd(X, full_matrices=False)
-        k = self._keep(sig)
-        self.c.flops["svd_dense"] += 21.0 * m * n * min(m, n)
-        self.c.events["truncate_dense"] += 1
-        self.c.trunc_rank[k] += 1
-        return x[:, :k] * sig[:k], yt[:k].T.copy()

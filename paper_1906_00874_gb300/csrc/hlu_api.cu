@@ -31,7 +31,12 @@ struct DevPlan {
     Term *terms = nullptr;
     Piece *pieces = nullptr;
     std::vector<Launch> launches;
-    std::vector<int32_t> launch_aux;  // smem capacity per launch (RADD: core size)
+    std::vector<int32_t> launch_aux;  // GETRF/TRSM: leaf size for shared memory; RADD: core capacity
+};
+
+struct Pending {
+    int kind;
+    cudaEvent_t e0, e1;
 };
 
 }  // namespace
@@ -40,13 +45,15 @@ struct hlu_ctx {
     Planner pl;
     int precision = HLU_FP64;
     cudaStream_t stream = nullptr;
-    size_t elem = 8;
     void *farena = nullptr;
     double *aarena = nullptr;
     int32_t *kdyn = nullptr;
     long long *err = nullptr;
+    double *flops = nullptr;  // [0, 8): factorisation, [8, 16): solves and products
     int32_t *perm = nullptr;
     int64_t *leaf_desc = nullptr;
+    double *ir = nullptr;     // refinement work: b, x, r (n x nrhs_max each) and 2 x nrhs_max norms
+    double *ir_host = nullptr;  // pinned copy of the norms
     DevPlan fp, sp, mp;
     int64_t device_bytes = 0;
     int64_t mem_budget = 0;
@@ -55,6 +62,13 @@ struct hlu_ctx {
     std::vector<void *> allocs;
     int last_status = HLU_OK;
     long long last_err[4] = {0, 0, 0, 0};
+    // profiling
+    bool profiling = false;
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> free_events;
+    double prof_ms[8] = {0};
+    int64_t prof_count[8] = {0};
+    int64_t kernels_launched = 0;
 };
 
 namespace {
@@ -79,7 +93,8 @@ template <class X>
 int upload(hlu_ctx *h, X **p, const std::vector<X> &v) {
     int st = dalloc(h, p, v.size());
     if (st) return st;
-    if (!v.empty()) return cuda_status(cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(X), cudaMemcpyHostToDevice, h->stream));
+    if (!v.empty())
+        return cuda_status(cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(X), cudaMemcpyHostToDevice, h->stream));
     return HLU_OK;
 }
 
@@ -120,22 +135,60 @@ const void *task_ptr(const DevPlan &d, int kind) {
     return nullptr;
 }
 
-void run_plan(hlu_ctx *h, const DevPlan &d, void *arena) {
+cudaEvent_t take_event(hlu_ctx *h) {
+    if (!h->free_events.empty()) {
+        cudaEvent_t e = h->free_events.back();
+        h->free_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Accumulate the durations of the profiled launches (after a synchronisation).
+void collect_profile(hlu_ctx *h) {
+    for (const Pending &p : h->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.e0, p.e1) == cudaSuccess) {
+            h->prof_ms[p.kind] += ms;
+            h->prof_count[p.kind] += 1;
+        }
+        h->free_events.push_back(p.e0);
+        h->free_events.push_back(p.e1);
+    }
+    h->pending.clear();
+}
+
+void run_plan(hlu_ctx *h, const DevPlan &d, void *arena, double *flops) {
     LaunchArgs a;
     a.arena = arena;
     a.kdyn = h->kdyn;
     a.err = h->err;
     a.eps = h->eps;
+    a.flops = flops;
     a.kmax = h->pl.opt.kmax_core;
+    const bool dbl = arena == (void *)h->aarena || h->precision == HLU_FP64;
     for (size_t i = 0; i < d.launches.size(); ++i) {
         const Launch &L = d.launches[i];
-        if (arena == (void *)h->aarena || h->precision == HLU_FP64)
+        Pending pe{L.kind, nullptr, nullptr};
+        if (h->profiling) {
+            pe.e0 = take_event(h);
+            pe.e1 = take_event(h);
+            cudaEventRecord(pe.e0, h->stream);
+        }
+        if (dbl)
             launch_kind<double>(L.kind, task_ptr(d, L.kind), d.terms, d.pieces, L.start, L.count, d.launch_aux[i], a,
                                 h->stream);
         else
             launch_kind<float>(L.kind, task_ptr(d, L.kind), d.terms, d.pieces, L.start, L.count, d.launch_aux[i], a,
                                h->stream);
+        if (h->profiling) {
+            cudaEventRecord(pe.e1, h->stream);
+            h->pending.push_back(pe);
+        }
     }
+    h->kernels_launched += (int64_t)d.launches.size();
 }
 
 int read_error(hlu_ctx *h) {
@@ -143,6 +196,7 @@ int read_error(hlu_ctx *h) {
     if (e != cudaSuccess) return HLU_ECUDA;
     e = cudaGetLastError();
     if (e != cudaSuccess) return HLU_ECUDA;
+    if (h->profiling) collect_profile(h);
     long long w[4];
     if (cudaMemcpy(w, h->err, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess) return HLU_ECUDA;
     std::memcpy(h->last_err, w, sizeof(w));
@@ -169,7 +223,7 @@ int upload_arenas(hlu_ctx *h, const double *data) {
         a_leaf_end = std::max(a_leaf_end, end);
     }
     a_leaves.assign(a_leaf_end, 0.0);
-    std::vector<int64_t> desc(8 * pl.n_leaves);
+    std::vector<int64_t> desc(kLeafDesc * pl.n_leaves);
     for (int64_t l = 0; l < pl.n_leaves; ++l) {
         const Store &s = pl.astore[l];
         const Store &f = pl.fstore[l];
@@ -180,15 +234,16 @@ int upload_arenas(hlu_ctx *h, const double *data) {
             std::memcpy(&a_leaves[s.U_off], src, sizeof(double) * s.m * s.krank);
             std::memcpy(&a_leaves[s.V_off], src + int64_t(s.m) * s.krank, sizeof(double) * s.n * s.krank);
         }
-        int64_t *d = &desc[8 * l];
+        int64_t *d = &desc[kLeafDesc * l];
         d[0] = s.kind == B_DENSE ? 0 : 1;
         d[1] = s.m;
         d[2] = s.n;
         d[3] = s.kind == B_DENSE ? 0 : s.krank;
         d[4] = s.kind == B_DENSE ? s.D_off : s.U_off;
-        d[5] = s.kind == B_DENSE ? f.D_off : f.U_off;
-        d[6] = s.kind == B_DENSE ? 0 : f.V_off;
-        d[7] = s.kind == B_DENSE ? 0 : f.kslot;
+        d[5] = s.kind == B_DENSE ? 0 : s.V_off;
+        d[6] = s.kind == B_DENSE ? f.D_off : f.U_off;
+        d[7] = s.kind == B_DENSE ? 0 : f.V_off;
+        d[8] = s.kind == B_DENSE ? 0 : f.kslot;
     }
     int st;
     if ((st = dalloc(h, &h->aarena, pl.a_elems))) return st;
@@ -208,6 +263,20 @@ int upload_arenas(hlu_ctx *h, const double *data) {
         return st;
     // the host staging vectors die at return: wait for the copies
     return cuda_status(cudaStreamSynchronize(h->stream));
+}
+
+// One solve pass on the factor arena's work panel Y (cluster order, nc columns, ld n).
+void solve_pass(hlu_ctx *h, int32_t nc) {
+    launch_set_slot(h->kdyn, h->pl.nrhs_slot, nc, h->stream);
+    h->kernels_launched += 1;
+    run_plan(h, h->sp, h->farena, h->flops + 8);
+}
+
+// A_H x_c for a cluster-order panel already copied into the A_H arena's X panel; result in its Y panel.
+void matvec_pass(hlu_ctx *h, int32_t nc) {
+    launch_set_slot(h->kdyn, h->pl.nrhs_slot, nc, h->stream);
+    h->kernels_launched += 1;
+    run_plan(h, h->mp, h->aarena, h->flops + 8);
 }
 
 }  // namespace
@@ -247,12 +316,11 @@ int hlu_create(const hlu_tree *tree, const hlu_blocks *blocks, const hlu_opts *o
         delete h;
         return HLU_EINVAL;
     }
-    h->elem = h->precision == HLU_FP64 ? 8 : 4;
     h->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
     int st = h->pl.build(tree->n, tree->n_clusters, tree->perm, tree->begin, tree->size, tree->son0, tree->son1,
                          blocks->n_leaves, blocks->row_cl, blocks->col_cl, blocks->kind, blocks->rank,
                          blocks->offset, blocks->data, blocks->data_len, po);
-    if (st == HLU_OK && h->pl.max_leaf > 128) st = HLU_EINVAL;  // dense leaves live in one warp's registers
+    if (st == HLU_OK && h->pl.max_leaf > 128) st = HLU_EINVAL;  // a dense leaf column lives in one warp's registers
     if (st == HLU_OK) st = h->pl.plan_all();
     if (st == HLU_OK) {
         if (h->precision == HLU_FP64) {
@@ -263,11 +331,16 @@ int hlu_create(const hlu_tree *tree, const hlu_blocks *blocks, const hlu_opts *o
             st = upload_arenas<float>(h, blocks->data);
         }
     }
+    const int64_t n = h->pl.n, w = h->pl.opt.nrhs_max;
     if (st == HLU_OK) st = upload(h, &h->kdyn, h->pl.slot_init);
     if (st == HLU_OK) st = dalloc(h, &h->err, 4);
+    if (st == HLU_OK) st = dalloc(h, &h->flops, 16);
+    if (st == HLU_OK) st = cuda_status(cudaMemsetAsync(h->flops, 0, 16 * sizeof(double), h->stream));
+    if (st == HLU_OK) st = dalloc(h, &h->ir, 3 * n * w + 2 * w);
+    if (st == HLU_OK) st = cuda_status(cudaMallocHost(reinterpret_cast<void **>(&h->ir_host), 2 * w * sizeof(double)));
     if (st == HLU_OK) st = clear_error(h);
     if (st == HLU_OK) st = upload(h, &h->perm, h->pl.perm);
-    int kmax = h->pl.opt.kmax_core;
+    const int kmax = h->pl.opt.kmax_core;
     if (st == HLU_OK) st = upload_plan(h, h->pl.fplan, h->fp, kmax);
     if (st == HLU_OK) st = upload_plan(h, h->pl.splan, h->sp, kmax);
     if (st == HLU_OK) st = upload_plan(h, h->pl.mplan, h->mp, kmax);
@@ -283,8 +356,10 @@ int hlu_create(const hlu_tree *tree, const hlu_blocks *blocks, const hlu_opts *o
 int hlu_factor(hlu_t h, double eps) {
     if (!h || !(eps >= 0.0) || !std::isfinite(eps)) return HLU_EINVAL;
     h->eps = eps;
+    h->factored = false;
     int st = clear_error(h);
     if (st) return st;
+    if ((st = cuda_status(cudaMemsetAsync(h->flops, 0, 16 * sizeof(double), h->stream)))) return st;
     // restore the working copy from A_H (the factorisation overwrites it) and the ranks
     if ((st = cuda_status(cudaMemcpyAsync(h->kdyn, h->pl.slot_init.data(), sizeof(int32_t) * h->pl.n_slots,
                                           cudaMemcpyHostToDevice, h->stream))))
@@ -293,7 +368,8 @@ int hlu_factor(hlu_t h, double eps) {
         launch_reset<double>(h->leaf_desc, h->pl.n_leaves, h->aarena, (double *)h->farena, h->kdyn, h->stream);
     else
         launch_reset<float>(h->leaf_desc, h->pl.n_leaves, h->aarena, (float *)h->farena, h->kdyn, h->stream);
-    run_plan(h, h->fp, h->farena);
+    h->kernels_launched += 1;
+    run_plan(h, h->fp, h->farena, h->flops);
     st = read_error(h);
     h->last_status = st;
     h->factored = st == HLU_OK;
@@ -301,26 +377,28 @@ int hlu_factor(hlu_t h, double eps) {
 }
 
 int hlu_solve(hlu_t h, double *b, int32_t nrhs, int64_t ldb) {
-    if (!h || !b || nrhs < 0 || ldb < h->pl.n) return HLU_EINVAL;
+    if (!h || nrhs < 0 || ldb < h->pl.n) return HLU_EINVAL;
     if (!h->factored) return HLU_ESTATE;
+    if (nrhs == 0) return HLU_OK;
+    if (!b) return HLU_EINVAL;
     int st = clear_error(h);
     if (st) return st;
     const int32_t n = h->pl.n, w = h->pl.opt.nrhs_max;
     for (int32_t j0 = 0; j0 < nrhs; j0 += w) {
         const int32_t nc = std::min(w, nrhs - j0);
         double *bj = b + (int64_t)j0 * ldb;
-        launch_set_slot(h->kdyn, h->pl.nrhs_slot, nc, h->stream);
         if (h->precision == HLU_FP64) {
             double *Y = (double *)h->farena + h->pl.f_solve_off;
             launch_permute<double, double>(h->perm, n, nc, bj, ldb, Y, n, 1, h->stream);
-            run_plan(h, h->sp, h->farena);
+            solve_pass(h, nc);
             launch_permute<double, double>(h->perm, n, nc, Y, n, bj, ldb, 0, h->stream);
         } else {
             float *Y = (float *)h->farena + h->pl.f_solve_off;
             launch_permute<double, float>(h->perm, n, nc, bj, ldb, Y, n, 1, h->stream);
-            run_plan(h, h->sp, h->farena);
+            solve_pass(h, nc);
             launch_permute<float, double>(h->perm, n, nc, Y, n, bj, ldb, 0, h->stream);
         }
+        h->kernels_launched += 2;
     }
     st = read_error(h);
     h->last_status = st;
@@ -328,19 +406,95 @@ int hlu_solve(hlu_t h, double *b, int32_t nrhs, int64_t ldb) {
 }
 
 int hlu_matvec(hlu_t h, const double *x, double *y, int32_t nrhs, int64_t ld) {
-    if (!h || !x || !y || nrhs < 0 || ld < h->pl.n) return HLU_EINVAL;
+    if (!h || nrhs < 0 || ld < h->pl.n) return HLU_EINVAL;
+    if (nrhs == 0) return HLU_OK;
+    if (!x || !y) return HLU_EINVAL;
     int st = clear_error(h);
     if (st) return st;
     const int32_t n = h->pl.n, w = h->pl.opt.nrhs_max;
     double *X = h->aarena + h->pl.a_x_off, *Y = h->aarena + h->pl.a_y_off;
     for (int32_t j0 = 0; j0 < nrhs; j0 += w) {
         const int32_t nc = std::min(w, nrhs - j0);
-        launch_set_slot(h->kdyn, h->pl.nrhs_slot, nc, h->stream);
         launch_permute<double, double>(h->perm, n, nc, x + (int64_t)j0 * ld, ld, X, n, 1, h->stream);
-        run_plan(h, h->mp, h->aarena);
+        matvec_pass(h, nc);
         launch_permute<double, double>(h->perm, n, nc, Y, n, y + (int64_t)j0 * ld, ld, 0, h->stream);
+        h->kernels_launched += 2;
     }
     st = read_error(h);
+    return st;
+}
+
+int hlu_solve_refined(hlu_t h, const double *b, double *x, int32_t nrhs, int64_t ld, double tol, int32_t max_iter,
+                      int32_t *iters_out, double *resid_out) {
+    if (!h || nrhs < 0 || ld < h->pl.n || max_iter < 0 || !(tol >= 0.0)) return HLU_EINVAL;
+    if (!h->factored) return HLU_ESTATE;
+    if (iters_out) *iters_out = 0;
+    if (resid_out) *resid_out = 0.0;
+    if (nrhs == 0) return HLU_OK;
+    if (!b || !x) return HLU_EINVAL;
+    int st = clear_error(h);
+    if (st) return st;
+    const int64_t n = h->pl.n;
+    const int32_t w = h->pl.opt.nrhs_max;
+    double *bc = h->ir, *xc = bc + n * w, *rc = xc + n * w, *nrm = rc + n * w;
+    double *AX = h->aarena + h->pl.a_x_off, *AY = h->aarena + h->pl.a_y_off;
+    int32_t iters_max = 0;
+    double res_max = 0.0;
+    for (int32_t j0 = 0; j0 < nrhs; j0 += w) {
+        const int32_t nc = std::min(w, nrhs - j0);
+        const size_t bytes = sizeof(double) * n * nc;
+        launch_permute<double, double>(h->perm, (int32_t)n, nc, b + (int64_t)j0 * ld, ld, bc, n, 1, h->stream);
+        cudaMemsetAsync(xc, 0, bytes, h->stream);
+        cudaMemcpyAsync(rc, bc, bytes, cudaMemcpyDeviceToDevice, h->stream);
+        int32_t it = 0;
+        double res = 0.0;
+        if (max_iter == 0) {
+            cudaMemsetAsync(nrm, 0, 2 * w * sizeof(double), h->stream);
+            launch_residual(bc, xc, rc, n, nc, nrm, nrm + w, h->stream);  // r = b (x = 0)
+            cudaMemcpyAsync(h->ir_host, nrm, 2 * w * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+            if ((st = read_error(h))) return st;
+            res = 1.0;
+        }
+        while (it < max_iter) {
+            if (h->precision == HLU_FP64) {
+                double *Y = (double *)h->farena + h->pl.f_solve_off;
+                launch_to_work<double>(rc, Y, n, nc, h->stream);
+                solve_pass(h, nc);
+                launch_add_from_work<double>(xc, Y, n, nc, h->stream);
+            } else {
+                float *Y = (float *)h->farena + h->pl.f_solve_off;
+                launch_to_work<float>(rc, Y, n, nc, h->stream);
+                solve_pass(h, nc);
+                launch_add_from_work<float>(xc, Y, n, nc, h->stream);
+            }
+            ++it;
+            h->kernels_launched += 3;  // to_work, add_from_work, residual
+            cudaMemcpyAsync(AX, xc, bytes, cudaMemcpyDeviceToDevice, h->stream);
+            matvec_pass(h, nc);
+            cudaMemsetAsync(nrm, 0, 2 * w * sizeof(double), h->stream);
+            launch_residual(bc, AY, rc, n, nc, nrm, nrm + w, h->stream);
+            cudaMemcpyAsync(h->ir_host, nrm, 2 * w * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+            if ((st = read_error(h))) {
+                h->last_status = st;
+                return st;
+            }
+            res = 0.0;
+            for (int32_t j = 0; j < nc; ++j) {
+                const double bn = std::sqrt(h->ir_host[w + j]);
+                const double rj = bn > 0.0 ? std::sqrt(h->ir_host[j]) / bn : std::sqrt(h->ir_host[j]);
+                res = std::max(res, rj);
+            }
+            if (!std::isfinite(res) || res <= tol) break;
+        }
+        launch_permute<double, double>(h->perm, (int32_t)n, nc, xc, n, x + (int64_t)j0 * ld, ld, 0, h->stream);
+        h->kernels_launched += 2;
+        iters_max = std::max(iters_max, it);
+        res_max = std::max(res_max, res);
+    }
+    st = read_error(h);
+    h->last_status = st;
+    if (iters_out) *iters_out = iters_max;
+    if (resid_out) *resid_out = res_max;
     return st;
 }
 
@@ -366,7 +520,8 @@ int hlu_get_factors(hlu_t h, int32_t *rank_out, int64_t *offsets_out, double *da
     int64_t leaf_end = 0;
     for (int64_t l = 0; l < pl.n_leaves; ++l) {
         const Store &s = pl.fstore[l];
-        leaf_end = std::max(leaf_end, s.kind == B_DENSE ? s.D_off + int64_t(s.m) * s.n : s.V_off + int64_t(s.n) * s.cap);
+        leaf_end =
+            std::max(leaf_end, s.kind == B_DENSE ? s.D_off + int64_t(s.m) * s.n : s.V_off + int64_t(s.n) * s.cap);
     }
     std::vector<double> buf(leaf_end);
     if (h->precision == HLU_FP64) {
@@ -415,6 +570,19 @@ int hlu_get_stats(hlu_t h, hlu_stats *o) {
     o->tasks_by_kind[4] = (int64_t)f.radd.size();
     o->tasks_by_kind[5] = (int64_t)f.split.size();
     o->max_stacked = f.max_kcap;
+    o->kernels_launched = h->kernels_launched;
+    for (int k = 0; k < 8; ++k) {
+        o->kernel_ms[k] = h->prof_ms[k];
+        o->kernel_launches[k] = h->prof_count[k];
+    }
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return HLU_ECUDA;
+    double fl[16];
+    if (cudaMemcpy(fl, h->flops, sizeof(fl), cudaMemcpyDeviceToHost) != cudaSuccess) return HLU_ECUDA;
+    for (int k = 0; k < 8; ++k) {
+        o->flops_by_kind[k] = fl[k];
+        o->model_flops += fl[k];
+        o->solve_flops += fl[8 + k];
+    }
     if (h->factored) {
         std::vector<int32_t> kd(h->pl.n_slots);
         if (cudaMemcpy(kd.data(), h->kdyn, sizeof(int32_t) * h->pl.n_slots, cudaMemcpyDeviceToHost) == cudaSuccess)
@@ -424,11 +592,26 @@ int hlu_get_stats(hlu_t h, hlu_stats *o) {
     return HLU_OK;
 }
 
+int hlu_set_profiling(hlu_t h, int32_t on) {
+    if (!h) return HLU_EINVAL;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return HLU_ECUDA;
+    collect_profile(h);
+    h->profiling = on != 0;
+    for (int k = 0; k < 8; ++k) {
+        h->prof_ms[k] = 0.0;
+        h->prof_count[k] = 0;
+    }
+    return HLU_OK;
+}
+
 void hlu_destroy(hlu_t h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
+    collect_profile(h);
+    for (cudaEvent_t e : h->free_events) cudaEventDestroy(e);
     for (void *p : h->allocs) cudaFree(p);
+    if (h->ir_host) cudaFreeHost(h->ir_host);
     delete h;
 }
 

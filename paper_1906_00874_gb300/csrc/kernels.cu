@@ -6,6 +6,8 @@
 #include <float.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace hlu {
@@ -28,6 +30,16 @@ __device__ void set_error(long long *err, int code, long long index, double valu
         err[2] = __double_as_longlong(value);
     }
     atomicAdd((unsigned long long *)(err + 3), 1ull);
+}
+
+// Model flop counts (standard operation counts, Golub and Van Loan).
+__device__ __forceinline__ void add_flops(const LaunchArgs &a, int kind, double f) {
+    if (a.flops && f > 0.0) atomicAdd(a.flops + kind, f);
+}
+
+__device__ __forceinline__ double qr_model_flops(double m, double K) {
+    const double hi = m > K ? m : K, lo = m > K ? K : m;
+    return 2.0 * hi * lo * lo - 2.0 * lo * lo * lo / 3.0;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -77,6 +89,7 @@ __global__ void __launch_bounds__(kThreads) k_getrf(const TGetrf *tasks, LaunchA
         __syncthreads();
     }
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) g[e] = s[e];
+    if (threadIdx.x == 0) add_flops(a, K_GETRF, 2.0 * m * m * m / 3.0);
 }
 
 // ------------------------------------------------------------------- TRSM
@@ -101,6 +114,7 @@ __global__ void __launch_bounds__(kThreads) k_trsm(const TTrsm *tasks, LaunchArg
     __syncthreads();
     T *A = reinterpret_cast<T *>(a.arena);
     const int p = dim_c(t.P, a.kdyn);
+    if (threadIdx.x == 0) add_flops(a, K_TRSM, (double)m * m * p);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int c = warp; c < p; c += nw) {
         T x[kRowsPerLane];
@@ -168,6 +182,7 @@ __global__ void __launch_bounds__(kThreads) k_project(const TProject *tasks, Lau
     __shared__ T sX[32][65];
     T *A = reinterpret_cast<T *>(a.arena);
     const int len = dim_r(t.F, a.kdyn), k = dim_c(t.F, a.kdyn), p = dim_c(t.X, a.kdyn);
+    if (threadIdx.x == 0) add_flops(a, K_PROJECT, 2.0 * len * k * p);
     for (int a0 = 0; a0 < k; a0 += 64)
         for (int b0 = 0; b0 < p; b0 += 64) {
             const int ka = min(64, k - a0), pb = min(64, p - b0);
@@ -212,6 +227,11 @@ __global__ void __launch_bounds__(kThreads) k_accum(const TAccum *tasks, const T
     const int m = dim_r(t.out, a.kdyn);
     const int p = t.dst >= 0 ? a.kdyn[t.src] : dim_c(t.out, a.kdyn);
     if (t.dst >= 0 && threadIdx.x == 0) a.kdyn[t.dst] = p;
+    if (threadIdx.x == 0) {
+        double f = 0.0;
+        for (int q = 0; q < t.nterms; ++q) f += 2.0 * m * (double)dim_c(terms[t.term0 + q].A, a.kdyn) * p;
+        add_flops(a, K_ACCUM, f);
+    }
     const T alpha = T(t.alpha);
     for (int e0 = 0; e0 < m * p; e0 += blockDim.x) {
         const int e = e0 + threadIdx.x;
@@ -487,21 +507,26 @@ __global__ void __launch_bounds__(kThreads) k_radd(const TRadd *tasks, const Pie
     __syncthreads();
     block_apply_q(WU, m, ku, tauU, Uc, knew);
     block_apply_q(WV, n, kv, tauV, Vc, knew);
-    if (threadIdx.x == 0) kd[t.kslot] = knew;
+    if (threadIdx.x == 0) {
+        kd[t.kslot] = knew;
+        const double kb = ku > kv ? ku : kv;
+        add_flops(a, K_RADD, qr_model_flops(m, K) + qr_model_flops(n, K) + 21.0 * kb * kb * kb +
+                                 2.0 * ((double)m * ku + (double)n * kv) * knew);
+    }
 }
 
 // ------------------------------------------------------------------ RESET
-// leaf_desc per leaf (int64 x 8): kind, m, n, k, a_off, f_off (D or U), f_voff, kslot
+// leaf_desc per leaf (int64 x kLeafDesc): kind, m, n, k, a_off (D or U), a_voff, f_off (D or U), f_voff, kslot
 template <class T>
 __global__ void k_reset(const int64_t *desc, const double *Aa, T *F, int32_t *kd) {
-    const int64_t *d = desc + 8 * (int64_t)blockIdx.x;
-    const int64_t kind = d[0], m = d[1], n = d[2], k = d[3], ao = d[4], fo = d[5], fv = d[6];
+    const int64_t *d = desc + kLeafDesc * (int64_t)blockIdx.x;
+    const int64_t kind = d[0], m = d[1], n = d[2], k = d[3], ao = d[4], av = d[5], fo = d[6], fv = d[7];
     if (kind == 0) {
         for (int64_t e = threadIdx.x; e < m * n; e += blockDim.x) F[fo + e] = T(Aa[ao + e]);
     } else {
         for (int64_t e = threadIdx.x; e < m * k; e += blockDim.x) F[fo + e] = T(Aa[ao + e]);
-        for (int64_t e = threadIdx.x; e < n * k; e += blockDim.x) F[fv + e] = T(Aa[ao + m * k + e]);
-        if (threadIdx.x == 0) kd[d[7]] = int32_t(k);
+        for (int64_t e = threadIdx.x; e < n * k; e += blockDim.x) F[fv + e] = T(Aa[av + e]);
+        if (threadIdx.x == 0) kd[d[8]] = int32_t(k);
     }
 }
 
@@ -519,6 +544,50 @@ __global__ void k_permute(const int32_t *perm, int32_t n, int32_t nrhs, const Ti
 }
 
 __global__ void k_set_slot(int32_t *kd, int32_t slot, int32_t v) { kd[slot] = v; }
+
+template <class T>
+__global__ void k_to_work(const double *x, T *y, int64_t tot) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x)
+        y[e] = T(x[e]);
+}
+
+template <class T>
+__global__ void k_add_from_work(double *x, const T *y, int64_t tot) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x)
+        x[e] += (double)y[e];
+}
+
+// r = b - ax per column j (one block row of columns per blockIdx.y), squared norms accumulated
+__global__ void k_residual(const double *b, const double *ax, double *r, int64_t n, double *nrm2, double *bn2) {
+    __shared__ double red[2][32];
+    const int64_t j = blockIdx.y;
+    double sr = 0.0, sb = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double bi = b[i + j * n], ri = bi - ax[i + j * n];
+        r[i + j * n] = ri;
+        sr += ri * ri;
+        sb += bi * bi;
+    }
+    sr = warp_sum(sr);
+    sb = warp_sum(sb);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        red[0][w] = sr;
+        red[1][w] = sb;
+    }
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        sr = l < nw ? red[0][l] : 0.0;
+        sb = l < nw ? red[1][l] : 0.0;
+        sr = warp_sum(sr);
+        sb = warp_sum(sb);
+        if (l == 0) {
+            atomicAdd(nrm2 + j, sr);
+            atomicAdd(bn2 + j, sb);
+        }
+    }
+}
 
 // -------------------------------------------------------------- dispatch
 size_t getrf_smem_bytes(int max_leaf, int elem) { return (size_t)max_leaf * max_leaf * elem; }
@@ -578,6 +647,32 @@ void launch_permute(const int32_t *perm, int32_t n, int32_t nrhs, const Tin *x, 
 void launch_set_slot(int32_t *kdyn, int32_t slot, int32_t value, cudaStream_t s) {
     k_set_slot<<<1, 1, 0, s>>>(kdyn, slot, value);
 }
+
+static int grid_for(int64_t tot) { return (int)std::max<int64_t>(1, std::min<int64_t>((tot + kThreads - 1) / kThreads, 152 * 8)); }
+
+template <class T>
+void launch_to_work(const double *x, T *y, int64_t n, int32_t nc, cudaStream_t s) {
+    const int64_t tot = n * nc;
+    if (tot > 0) k_to_work<T><<<grid_for(tot), kThreads, 0, s>>>(x, y, tot);
+}
+
+template <class T>
+void launch_add_from_work(double *x, const T *y, int64_t n, int32_t nc, cudaStream_t s) {
+    const int64_t tot = n * nc;
+    if (tot > 0) k_add_from_work<T><<<grid_for(tot), kThreads, 0, s>>>(x, y, tot);
+}
+
+void launch_residual(const double *b, const double *ax, double *r, int64_t n, int32_t nc, double *nrm2,
+                     double *bn2, cudaStream_t s) {
+    if (n * nc == 0) return;
+    const int gx = (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, 64));
+    k_residual<<<dim3(gx, nc), kThreads, 0, s>>>(b, ax, r, n, nrm2, bn2);
+}
+
+template void launch_to_work<double>(const double *, double *, int64_t, int32_t, cudaStream_t);
+template void launch_to_work<float>(const double *, float *, int64_t, int32_t, cudaStream_t);
+template void launch_add_from_work<double>(double *, const double *, int64_t, int32_t, cudaStream_t);
+template void launch_add_from_work<float>(double *, const float *, int64_t, int32_t, cudaStream_t);
 
 template void launch_kind<double>(int, const void *, const Term *, const Piece *, int, int, int, const LaunchArgs &,
                                   cudaStream_t);

@@ -8,12 +8,14 @@
 namespace hlu {
 
 constexpr int kThreads = 256;
+constexpr int kLeafDesc = 9;  // int64 fields per leaf of the reset descriptor
 
 struct LaunchArgs {
     void *arena;        // T* factor arena (or double* A_H arena)
     int32_t *kdyn;      // dynamic dimensions
     long long *err;     // error word: code, index, value bits, count
     double eps;         // truncation tolerance (rounded addition)
+    double *flops;      // model flops per task kind (K_NKINDS doubles), accumulated
     int32_t kmax;       // largest stacked rank the core buffers hold
 };
 
@@ -32,6 +34,15 @@ void launch_permute(const int32_t *perm, int32_t n, int32_t nrhs, const Tin *x, 
                     int64_t ldy, int to_cluster, cudaStream_t s);
 
 void launch_set_slot(int32_t *kdyn, int32_t slot, int32_t value, cudaStream_t s);
+
+// Iterative-refinement helpers (cluster order, n x nc panels with leading dimension n):
+// y (T) = x (double);  x (double) += y (T);  r = b - ax and nrm2[j] += |r_j|^2, bn2[j] += |b_j|^2.
+template <class T>
+void launch_to_work(const double *x, T *y, int64_t n, int32_t nc, cudaStream_t s);
+template <class T>
+void launch_add_from_work(double *x, const T *y, int64_t n, int32_t nc, cudaStream_t s);
+void launch_residual(const double *b, const double *ax, double *r, int64_t n, int32_t nc, double *nrm2,
+                     double *bn2, cudaStream_t s);
 
 size_t radd_smem_bytes(int kcap);
 size_t getrf_smem_bytes(int max_leaf, int elem);

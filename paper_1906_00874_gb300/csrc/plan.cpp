@@ -567,6 +567,11 @@ int Planner::build_tree() {
                 error = "low-rank diagonal block";
                 return HLU_EINVAL;
             }
+            if (b->kind == B_DENSE && cl[t].son0 >= 0 && cl[s].son0 >= 0) {
+                // Algorithm 2 partitions a non-admissible block whose clusters both have sons
+                error = "dense leaf between two clusters that both have sons";
+                return HLU_EINVAL;
+            }
             used++;
             continue;
         }

@@ -20,8 +20,10 @@ HLU_FP32 = 1
 STATUS = {0: "HLU_OK", 1: "HLU_EINVAL", 2: "HLU_ENOMEM", 3: "HLU_ESTATE", 4: "HLU_EPIVOT",
           5: "HLU_ERANKCAP", 6: "HLU_ETIMEOUT", 7: "HLU_ECUDA", 8: "HLU_ENUMERIC"}
 
-EXPORTS = ("hlu_create", "hlu_factor", "hlu_solve", "hlu_matvec", "hlu_factor_doubles",
-           "hlu_get_factors", "hlu_get_stats", "hlu_destroy", "hlu_strerror", "hlu_last_error_detail")
+EXPORTS = ("hlu_create", "hlu_factor", "hlu_solve", "hlu_matvec", "hlu_solve_refined", "hlu_factor_doubles",
+           "hlu_get_factors", "hlu_get_stats", "hlu_set_profiling", "hlu_destroy", "hlu_strerror",
+           "hlu_last_error_detail", "hlu_probe_alu_peaks")
+KINDS = ("getrf", "trsm", "project", "accum", "radd", "split")
 
 
 class HLUError(RuntimeError):
@@ -52,12 +54,15 @@ class Stats(ctypes.Structure):
                 ("solve_tasks", ctypes.c_int64), ("solve_waves", ctypes.c_int64),
                 ("solve_launches", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
                 ("tasks_by_kind", ctypes.c_int64 * 8), ("model_flops", ctypes.c_double),
-                ("max_rank", ctypes.c_int32), ("max_stacked", ctypes.c_int32)]
+                ("flops_by_kind", ctypes.c_double * 8), ("solve_flops", ctypes.c_double),
+                ("kernel_ms", ctypes.c_double * 8), ("kernel_launches", ctypes.c_int64 * 8),
+                ("kernels_launched", ctypes.c_int64), ("max_rank", ctypes.c_int32), ("max_stacked", ctypes.c_int32)]
 
     def as_dict(self):
-        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "tasks_by_kind"}
-        d["tasks_by_kind"] = dict(zip(("getrf", "trsm", "project", "accum", "radd", "split"),
-                                      list(self.tasks_by_kind)[:6]))
+        per_kind = ("tasks_by_kind", "flops_by_kind", "kernel_ms", "kernel_launches")
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in per_kind}
+        for f in per_kind:
+            d[f] = dict(zip(KINDS, list(getattr(self, f))[:len(KINDS)]))
         return d
 
 
@@ -78,6 +83,9 @@ def load(path=LIB_PATH):
     lib.hlu_factor.argtypes = [vp, dbl]
     lib.hlu_solve.argtypes = [vp, vp, i32, i64]
     lib.hlu_matvec.argtypes = [vp, vp, vp, i32, i64]
+    lib.hlu_solve_refined.argtypes = [vp, vp, vp, i32, i64, dbl, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl)]
+    lib.hlu_set_profiling.argtypes = [vp, i32]
+    lib.hlu_probe_alu_peaks.argtypes = [ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
     lib.hlu_factor_doubles.argtypes = [vp]
     lib.hlu_factor_doubles.restype = i64
     lib.hlu_get_factors.argtypes = [vp, vp, vp, vp]
@@ -124,6 +132,15 @@ def to_device_panel(a, device="cuda"):
     if a.ndim == 1:
         return torch.tensor(a, device=device)
     return torch.tensor(np.ascontiguousarray(a.T), device=device).t()
+
+
+def probe_alu_peaks():
+    """(FP64, FP32) FMA throughput of the current GPU in TFLOP/s."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    st = load().hlu_probe_alu_peaks(ctypes.byref(a), ctypes.byref(b))
+    if st != 0:
+        raise HLUError(st, "hlu_probe_alu_peaks")
+    return a.value, b.value
 
 
 class HLU:
@@ -181,6 +198,23 @@ class HLU:
             raise ValueError("x and y must have the same shape and leading dimension")
         self._check(load().hlu_matvec(self._h, ctypes.c_void_p(px), ctypes.c_void_p(py), nrhs, ldx), "hlu_matvec")
         return y
+
+    def solve_refined(self, b, x, tol=1e-10, max_iter=20):
+        """x = refined solution of A_H x = b (CUDA float64 panels, same layout);
+        returns (solves applied, largest relative residual)."""
+        pb, nrhs, ldb = _dev_ptr_and_ld(b, self.n, "b")
+        px, nrhs2, ldx = _dev_ptr_and_ld(x, self.n, "x")
+        if nrhs != nrhs2 or ldb != ldx:
+            raise ValueError("b and x must have the same shape and leading dimension")
+        it = ctypes.c_int32()
+        res = ctypes.c_double()
+        self._check(load().hlu_solve_refined(self._h, ctypes.c_void_p(pb), ctypes.c_void_p(px), nrhs, ldb,
+                                             float(tol), int(max_iter), ctypes.byref(it), ctypes.byref(res)),
+                    "hlu_solve_refined")
+        return it.value, res.value
+
+    def set_profiling(self, on):
+        self._check(load().hlu_set_profiling(self._h, 1 if on else 0), "hlu_set_profiling")
 
     def get_factors(self):
         """(rank, offset, data) of the factors in the input leaf layout (host numpy)."""

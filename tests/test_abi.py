@@ -96,3 +96,19 @@ def test_rejects_data_out_of_range(lib, prob1280):
     off = prob1280.offset.copy()
     off[-1] = prob1280.data.shape[0]
     _expect_einval(prob1280, offset=off)
+
+
+def test_rejects_dense_block_between_split_clusters(lib, prob1280):
+    """A low-rank leaf whose clusters both have sons may not be declared dense."""
+    t = prob1280.tree
+    cand = [l for l in range(prob1280.n_leaves) if prob1280.kind[l] == 1
+            and t.son0[prob1280.row_cl[l]] >= 0 and t.son0[prob1280.col_cl[l]] >= 0]
+    assert cand
+    l = cand[0]
+    m, n = prob1280.leaf_shape(l)
+    kind = prob1280.kind.copy()
+    kind[l] = 0
+    data = np.concatenate([prob1280.data, np.zeros(m * n)])
+    off = prob1280.offset.copy()
+    off[l] = prob1280.data.shape[0]
+    _expect_einval(prob1280, kind=kind, data=data, offset=off)

@@ -65,9 +65,13 @@ def test_rounded_addition_eckart_young(prob320):
     assert U.shape[1] == 3
     assert np.allclose(np.linalg.svd(U @ V.T, compute_uv=False)[:3], sig[:3], rtol=1e-10)
     assert np.isclose(np.linalg.norm(X - U @ V.T, 2), sig[3], rtol=1e-8)
-    # dense -> low-rank conversion obeys the same rule
-    U, V = o.truncate_dense(X)
-    assert U.shape[1] == 3 and np.isclose(np.linalg.norm(X - U @ V.T, 2), sig[3], rtol=1e-8)
+    # a dense contribution enters in factorised form (identity on one side):
+    # the result is the truncated SVD of the dense sum
+    U, V = o.rounded_add(np.hstack([U1, X]), np.hstack([V1, np.eye(20)]))
+    ref = np.linalg.svd(U1 @ V1.T + X, compute_uv=False)
+    k = int(np.count_nonzero(ref > 1e-4 * ref[0]))
+    assert U.shape[1] == k
+    assert np.isclose(np.linalg.norm(U1 @ V1.T + X - U @ V.T, 2), ref[k], rtol=1e-8)
 
 
 def _dense_lu_of(hm):
