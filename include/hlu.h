@@ -83,13 +83,21 @@ typedef struct {
     int64_t data_len;    /* number of doubles in data (every leaf must lie inside) */
 } hlu_blocks;
 
+/* ------------------------------------------------------------ schedule */
+enum {
+    HLU_SCHED_DATAFLOW = 0, /* one persistent launch executes the task graph: a task
+                               starts as soon as its own predecessors are done */
+    HLU_SCHED_WAVES = 1     /* one launch per dependency level and task kind */
+};
+
 typedef struct {
     int32_t precision;   /* HLU_FP64 or HLU_FP32 */
     int32_t rank_cap;    /* capacity of every low-rank block: min(m, n, rank_cap); 0 -> 32 */
     int32_t nrhs_max;    /* widest right-hand-side panel one solve pass takes; 0 -> 64 */
-    int32_t reserved;
+    int32_t schedule;    /* HLU_SCHED_DATAFLOW (default) or HLU_SCHED_WAVES */
     int64_t mem_budget;  /* bytes of device memory the handle may allocate; 0 -> no limit */
-    double timeout_s;    /* limit for any device-side wait; 0 -> 10 s */
+    double timeout_s;    /* limit for any device-side wait; 0 -> 10 s.  On expiry the
+                            call returns HLU_ETIMEOUT and the device is left usable */
 } hlu_opts;
 
 typedef struct hlu_ctx *hlu_t;
@@ -179,6 +187,10 @@ void hlu_destroy(hlu_t h);
 
 /* Message for a status code (static string). */
 const char *hlu_strerror(int status);
+
+/* Message of the CUDA runtime error behind the last HLU_ECUDA of this handle
+ * (static string; "no CUDA error" if there was none). */
+const char *hlu_last_cuda_error(hlu_t h);
 
 /* Detail of the last device-side failure: the leaf (or task) index involved
  * and a value (the pivot, or the rank that overflowed).  Returns the status. */

@@ -14,7 +14,7 @@
 
 namespace hlu {
 template <class T>
-void set_kernel_attributes();
+bool set_kernel_attributes();
 }
 
 using namespace hlu;
@@ -32,6 +32,14 @@ struct DevPlan {
     Piece *pieces = nullptr;
     std::vector<Launch> launches;
     std::vector<int32_t> launch_aux;  // GETRF/TRSM: leaf size for shared memory; RADD: core capacity
+    // data-flow execution
+    int32_t *code = nullptr, *succ_ptr = nullptr, *succ_idx = nullptr;
+    int32_t *indeg0 = nullptr, *indeg = nullptr, *queue = nullptr, *roots = nullptr, *counters = nullptr;
+    int32_t n_tasks = 0, n_roots = 0, kc = 1;
+    void *scratch = nullptr;
+    int64_t scratch_stride = 0;
+    int workers = 0;
+    size_t smem = 0;
 };
 
 struct Pending {
@@ -44,6 +52,8 @@ struct Pending {
 struct hlu_ctx {
     Planner pl;
     int precision = HLU_FP64;
+    int schedule = HLU_SCHED_DATAFLOW;
+    unsigned long long timeout_ns = 10000000000ull;
     cudaStream_t stream = nullptr;
     void *farena = nullptr;
     double *aarena = nullptr;
@@ -69,6 +79,7 @@ struct hlu_ctx {
     double prof_ms[8] = {0};
     int64_t prof_count[8] = {0};
     int64_t kernels_launched = 0;
+    cudaError_t last_cuda = cudaSuccess;
 };
 
 namespace {
@@ -120,6 +131,36 @@ int upload_plan(hlu_ctx *h, const Plan &p, DevPlan &d, int kmax) {
         }
         d.launch_aux[i] = aux;
     }
+    // data-flow graph and per-worker workspace
+    d.n_tasks = (int32_t)p.n_tasks;
+    d.n_roots = (int32_t)p.roots.size();
+    if ((st = upload(h, &d.code, p.task_code))) return st;
+    if ((st = upload(h, &d.succ_ptr, p.succ_ptr))) return st;
+    if ((st = upload(h, &d.succ_idx, p.succ_idx))) return st;
+    if ((st = upload(h, &d.indeg0, p.indeg))) return st;
+    if ((st = upload(h, &d.roots, p.roots))) return st;
+    if ((st = dalloc(h, &d.indeg, p.indeg.size()))) return st;
+    if ((st = dalloc(h, &d.queue, p.indeg.size()))) return st;
+    if ((st = dalloc(h, &d.counters, 2))) return st;
+    int kc = 1;
+    int64_t stride = 1;
+    for (const TRadd &r : p.radd) {
+        const int k = std::min(r.Kcap, kmax);
+        kc = std::max(kc, k);
+        stride = std::max<int64_t>(stride, int64_t(r.m + r.n) * std::max(k, 1));
+    }
+    d.kc = kc;
+    d.scratch_stride = (stride + 31) & ~int64_t(31);
+    const int elem = h->precision == HLU_FP64 ? 8 : 4;
+    const bool dbl = &d == &h->mp || h->precision == HLU_FP64;
+    d.smem = dataflow_smem_bytes(h->pl.max_leaf, dbl ? 8 : elem, kc);
+    d.workers = dbl ? dataflow_workers<double>(d.smem) : dataflow_workers<float>(d.smem);
+    if (!p.radd.empty()) {
+        const size_t bytes = size_t(d.workers) * d.scratch_stride * (dbl ? 8 : elem);
+        char *sp = nullptr;
+        if ((st = dalloc(h, &sp, bytes))) return st;
+        d.scratch = sp;
+    }
     return HLU_OK;
 }
 
@@ -169,6 +210,49 @@ void run_plan(hlu_ctx *h, const DevPlan &d, void *arena, double *flops) {
     a.flops = flops;
     a.kmax = h->pl.opt.kmax_core;
     const bool dbl = arena == (void *)h->aarena || h->precision == HLU_FP64;
+    if (h->schedule == HLU_SCHED_DATAFLOW && d.n_tasks > 0) {
+        FlowArgs f;
+        f.code = d.code;
+        f.succ_ptr = d.succ_ptr;
+        f.succ_idx = d.succ_idx;
+        f.indeg = d.indeg;
+        f.queue = d.queue;
+        f.counters = d.counters;
+        f.n_tasks = d.n_tasks;
+        f.kc = d.kc;
+        f.getrf = d.getrf;
+        f.trsm = d.trsm;
+        f.project = d.project;
+        f.accum = d.accum;
+        f.radd = d.radd;
+        f.split = d.split;
+        f.terms = d.terms;
+        f.pieces = d.pieces;
+        f.scratch = d.scratch;
+        f.scratch_stride = d.scratch_stride;
+        f.timeout_ns = h->timeout_ns;
+        cudaMemcpyAsync(d.indeg, d.indeg0, sizeof(int32_t) * d.n_tasks, cudaMemcpyDeviceToDevice, h->stream);
+        cudaMemsetAsync(d.queue, 0xff, sizeof(int32_t) * d.n_tasks, h->stream);
+        cudaMemcpyAsync(d.queue, d.roots, sizeof(int32_t) * d.n_roots, cudaMemcpyDeviceToDevice, h->stream);
+        cudaMemsetAsync(d.counters, 0, 2 * sizeof(int32_t), h->stream);
+        launch_set_slot(d.counters, 1, d.n_roots, h->stream);
+        Pending pe{K_NKINDS, nullptr, nullptr};
+        if (h->profiling) {
+            pe.e0 = take_event(h);
+            pe.e1 = take_event(h);
+            cudaEventRecord(pe.e0, h->stream);
+        }
+        if (dbl)
+            launch_dataflow<double>(f, a, d.workers, d.smem, h->stream);
+        else
+            launch_dataflow<float>(f, a, d.workers, d.smem, h->stream);
+        if (h->profiling) {
+            cudaEventRecord(pe.e1, h->stream);
+            h->pending.push_back(pe);
+        }
+        h->kernels_launched += 2;
+        return;
+    }
     for (size_t i = 0; i < d.launches.size(); ++i) {
         const Launch &L = d.launches[i];
         Pending pe{L.kind, nullptr, nullptr};
@@ -192,10 +276,12 @@ void run_plan(hlu_ctx *h, const DevPlan &d, void *arena, double *flops) {
 }
 
 int read_error(hlu_ctx *h) {
-    cudaError_t e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) return HLU_ECUDA;
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return HLU_ECUDA;
+    cudaError_t e = cudaGetLastError();  // launch-time errors first
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        h->last_cuda = e;
+        return HLU_ECUDA;
+    }
     if (h->profiling) collect_profile(h);
     long long w[4];
     if (cudaMemcpy(w, h->err, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess) return HLU_ECUDA;
@@ -311,8 +397,11 @@ int hlu_create(const hlu_tree *tree, const hlu_blocks *blocks, const hlu_opts *o
         if (opts->rank_cap > 0) po.rank_cap = opts->rank_cap;
         if (opts->nrhs_max > 0) po.nrhs_max = opts->nrhs_max;
         h->mem_budget = opts->mem_budget;
+        h->schedule = opts->schedule;
+        if (opts->timeout_s > 0.0) h->timeout_ns = (unsigned long long)(opts->timeout_s * 1e9);
     }
-    if (h->precision != HLU_FP64 && h->precision != HLU_FP32) {
+    if ((h->precision != HLU_FP64 && h->precision != HLU_FP32) ||
+        (h->schedule != HLU_SCHED_DATAFLOW && h->schedule != HLU_SCHED_WAVES)) {
         delete h;
         return HLU_EINVAL;
     }
@@ -323,13 +412,15 @@ int hlu_create(const hlu_tree *tree, const hlu_blocks *blocks, const hlu_opts *o
     if (st == HLU_OK && h->pl.max_leaf > 128) st = HLU_EINVAL;  // a dense leaf column lives in one warp's registers
     if (st == HLU_OK) st = h->pl.plan_all();
     if (st == HLU_OK) {
-        if (h->precision == HLU_FP64) {
-            set_kernel_attributes<double>();
+        // the FP64 kernels always run the matrix-vector product on A_H
+        const bool attrs = set_kernel_attributes<double>() &&
+                           (h->precision == HLU_FP64 || set_kernel_attributes<float>());
+        if (!attrs)
+            st = HLU_ECUDA;
+        else if (h->precision == HLU_FP64)
             st = upload_arenas<double>(h, blocks->data);
-        } else {
-            set_kernel_attributes<float>();
+        else
             st = upload_arenas<float>(h, blocks->data);
-        }
     }
     const int64_t n = h->pl.n, w = h->pl.opt.nrhs_max;
     if (st == HLU_OK) st = upload(h, &h->kdyn, h->pl.slot_init);
@@ -613,6 +704,11 @@ void hlu_destroy(hlu_t h) {
     for (void *p : h->allocs) cudaFree(p);
     if (h->ir_host) cudaFreeHost(h->ir_host);
     delete h;
+}
+
+const char *hlu_last_cuda_error(hlu_t h) {
+    if (!h || h->last_cuda == cudaSuccess) return "no CUDA error";
+    return cudaGetErrorString(h->last_cuda);
 }
 
 int hlu_last_error_detail(hlu_t h, int64_t *index, double *value) {

@@ -67,9 +67,7 @@ __device__ double block_sum(double v, double *red) {
 // Unpivoted LU of an m x m dense diagonal leaf in shared memory (Sec. 3.1,
 // "Dense blocks": L unit lower and U overwrite A).
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_getrf(const TGetrf *tasks, LaunchArgs a) {
-    const TGetrf t = tasks[blockIdx.x];
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ void dev_getrf(const TGetrf &t, const LaunchArgs &a, unsigned char *smem_raw) {
     T *s = reinterpret_cast<T *>(smem_raw);
     const int m = t.m;
     T *g = reinterpret_cast<T *>(a.arena) + t.off;
@@ -97,9 +95,7 @@ __global__ void __launch_bounds__(kThreads) k_getrf(const TGetrf *tasks, LaunchA
 // column, the column held in registers (rows lane + 32 r), the triangle in
 // shared memory laid out so that lane accesses are contiguous.
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_trsm(const TTrsm *tasks, LaunchArgs a) {
-    const TTrsm t = tasks[blockIdx.x];
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ void dev_trsm(const TTrsm &t, const LaunchArgs &a, unsigned char *smem_raw) {
     T *L = reinterpret_cast<T *>(smem_raw);
     const int m = t.m;
     const T *g = reinterpret_cast<const T *>(a.arena) + t.L_off;
@@ -176,10 +172,9 @@ __global__ void __launch_bounds__(kThreads) k_trsm(const TTrsm *tasks, LaunchArg
 // low-rank product (Sec. 3.1).  Rows are streamed through shared memory in
 // chunks of 32; each thread owns up to 16 outputs of a 64 x 64 output tile.
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_project(const TProject *tasks, LaunchArgs a) {
-    const TProject t = tasks[blockIdx.x];
-    __shared__ T sF[32][65];
-    __shared__ T sX[32][65];
+__device__ void dev_project(const TProject &t, const LaunchArgs &a, unsigned char *smem_raw) {
+    T(*sF)[65] = reinterpret_cast<T(*)[65]>(smem_raw);
+    T(*sX)[65] = sF + 32;
     T *A = reinterpret_cast<T *>(a.arena);
     const int len = dim_r(t.F, a.kdyn), k = dim_c(t.F, a.kdyn), p = dim_c(t.X, a.kdyn);
     if (threadIdx.x == 0) add_flops(a, K_PROJECT, 2.0 * len * k * p);
@@ -221,8 +216,7 @@ __global__ void __launch_bounds__(kThreads) k_project(const TProject *tasks, Lau
 // leaf cluster of the output rows (dense leaves: A = D, X = panel slice;
 // low-rank leaves: A = U slice, X = projected V^T z).
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_accum(const TAccum *tasks, const Term *terms, LaunchArgs a) {
-    const TAccum t = tasks[blockIdx.x];
+__device__ void dev_accum(const TAccum &t, const Term *terms, const LaunchArgs &a) {
     T *A = reinterpret_cast<T *>(a.arena);
     const int m = dim_r(t.out, a.kdyn);
     const int p = t.dst >= 0 ? a.kdyn[t.src] : dim_c(t.out, a.kdyn);
@@ -252,8 +246,7 @@ __global__ void __launch_bounds__(kThreads) k_accum(const TAccum *tasks, const T
 
 // ------------------------------------------------------------------ SPLIT
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_split(const TSplit *tasks, LaunchArgs a) {
-    const TSplit t = tasks[blockIdx.x];
+__device__ void dev_split(const TSplit &t, const LaunchArgs &a) {
     T *A = reinterpret_cast<T *>(a.arena);
     const int k = a.kdyn[t.src_kslot];
     if (threadIdx.x == 0) a.kdyn[t.dst_kslot] = k;
@@ -268,50 +261,67 @@ __global__ void __launch_bounds__(kThreads) k_split(const TSplit *tasks, LaunchA
 }
 
 // ------------------------------------------------------------------- RADD
-// Householder QR of the m x K panel W in place (reflector j: v_j = 1 implied,
-// v_j[i] stored below the diagonal, tau[j]); R in the upper triangle.
+template <class R>
+__device__ __forceinline__ R warp_sum_t(R v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Householder QR of the m x K panel W in place, in the panel's own precision T
+// (reflector j: v_j = 1 implied, v_j[i] stored below the diagonal, tau[j]);
+// R in the upper triangle.
 template <class T>
 __device__ void block_householder_qr(T *W, int m, int K, double *tau, double *red) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int kk = min(m, K);
     for (int j = 0; j < kk; ++j) {
         T *x = W + (int64_t)j * m;
-        double s = 0.0;
-        for (int i = j + threadIdx.x; i < m; i += blockDim.x) s += (double)x[i] * (double)x[i];
-        s = block_sum(s, red);
-        const double x0 = (double)x[j];
-        const double nrm = sqrt(s);
-        if (nrm == 0.0) {
+        T s = T(0);
+        for (int i = j + threadIdx.x; i < m; i += blockDim.x) s += x[i] * x[i];
+        s = warp_sum_t(s);
+        __syncthreads();
+        if (lane == 0) red[warp] = (double)s;
+        __syncthreads();
+        if (warp == 0) {
+            double q = lane < nw ? red[lane] : 0.0;
+            q = warp_sum(q);
+            if (lane == 0) red[32] = q;
+        }
+        __syncthreads();
+        const T x0 = x[j];
+        const T nrm = T(sqrt(red[32]));
+        if (nrm == T(0)) {
             if (threadIdx.x == 0) tau[j] = 0.0;
             __syncthreads();
             continue;
         }
-        const double alpha = x0 >= 0.0 ? -nrm : nrm;
-        const double v0 = x0 - alpha;
-        const double tj = (alpha - x0) / alpha;
+        const T alpha = x0 >= T(0) ? -nrm : nrm;
+        const T v0 = x0 - alpha;
+        const T tj = (alpha - x0) / alpha;
         __syncthreads();
-        for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) x[i] = T((double)x[i] / v0);
+        for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) x[i] = x[i] / v0;
         if (threadIdx.x == 0) {
-            x[j] = T(alpha);
-            tau[j] = tj;
+            x[j] = alpha;
+            tau[j] = (double)tj;
         }
         __syncthreads();
         for (int c = j + 1 + warp; c < K; c += nw) {
             T *y = W + (int64_t)c * m;
-            double d = 0.0;
-            for (int i = j + 1 + lane; i < m; i += 32) d += (double)x[i] * (double)y[i];
-            d = warp_sum(d);
-            d = (d + (double)y[j]) * tj;
+            T d = T(0);
+            for (int i = j + 1 + lane; i < m; i += 32) d += x[i] * y[i];
+            d = warp_sum_t(d);
+            d = (d + y[j]) * tj;
             __syncwarp();
-            if (lane == 0) y[j] = T((double)y[j] - d);
-            for (int i = j + 1 + lane; i < m; i += 32) y[i] = T((double)y[i] - d * (double)x[i]);
+            if (lane == 0) y[j] -= d;
+            for (int i = j + 1 + lane; i < m; i += 32) y[i] -= d * x[i];
         }
         __syncthreads();
     }
 }
 
-// Z (m x nc, ld m) := Q Z with Q = H_0 ... H_{kk-1} from block_householder_qr;
-// each warp owns whole columns, so no CTA barrier is needed between reflectors.
+// Z (m x nc, ld m) := Q Z with Q = H_0 ... H_{kk-1} from block_householder_qr,
+// in precision T; each warp owns whole columns, so no CTA barrier is needed
+// between reflectors.
 template <class T>
 __device__ void block_apply_q(const T *W, int m, int kk, const double *tau, T *Z, int nc) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -319,13 +329,13 @@ __device__ void block_apply_q(const T *W, int m, int kk, const double *tau, T *Z
         T *y = Z + (int64_t)c * m;
         for (int j = kk - 1; j >= 0; --j) {
             const T *x = W + (int64_t)j * m;
-            double d = 0.0;
-            for (int i = j + 1 + lane; i < m; i += 32) d += (double)x[i] * (double)y[i];
-            d = warp_sum(d);
-            d = (d + (double)y[j]) * tau[j];
+            T d = T(0);
+            for (int i = j + 1 + lane; i < m; i += 32) d += x[i] * y[i];
+            d = warp_sum_t(d);
+            d = (d + y[j]) * T(tau[j]);
             __syncwarp();
-            if (lane == 0) y[j] = T((double)y[j] - d);
-            for (int i = j + 1 + lane; i < m; i += 32) y[i] = T((double)y[i] - d * (double)x[i]);
+            if (lane == 0) y[j] -= d;
+            for (int i = j + 1 + lane; i < m; i += 32) y[i] -= d * x[i];
             __syncwarp();
         }
     }
@@ -395,18 +405,146 @@ __device__ void block_jacobi(double *M, int ku, int kv, double *J, int *flag) {
 }
 
 size_t radd_smem_bytes(int kc) {
-    return sizeof(double) * (2 * (size_t)kc * kc + 4 * (size_t)kc + 40) + sizeof(int) * (2 * (size_t)kc + 8);
+    return sizeof(double) * (3 * (size_t)kc * kc + 5 * (size_t)kc + 40) + sizeof(int) * (2 * (size_t)kc + 8);
+}
+
+// QR with column pivoting of the ku x kv core M (double, shared memory, column
+// major), stopped at the first step whose largest remaining column norm is at
+// most delta times the first pivot's (the neglected block is at the level of
+// double rounding): M P = Q [R'; ~0] with R' of r rows.  Reflectors are kept
+// below the diagonal of M (v_j = 1 implied), tau[j]; perm holds P.  The pivot
+// is the largest column norm, lowest index on ties.
+__device__ int block_qrcp(double *M, int ku, int kv, double *tau, double *cn, int *perm, double delta,
+                          double *red, int *iflag) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int j = threadIdx.x; j < kv; j += blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < ku; ++i) s += M[i + (size_t)j * ku] * M[i + (size_t)j * ku];
+        cn[j] = s;
+        perm[j] = j;
+    }
+    __syncthreads();
+    double n0 = 0.0;
+    int r = 0;
+    const int kk = min(ku, kv);
+    for (int j = 0; j < kk; ++j) {
+        if (warp == 0) {
+            double bv = -1.0;
+            int bi = j;
+            for (int c = j + lane; c < kv; c += 32)
+                if (cn[c] > bv) {
+                    bv = cn[c];
+                    bi = c;
+                }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_xor_sync(kFull, bv, o);
+                const int oi = __shfl_xor_sync(kFull, bi, o);
+                if (ov > bv || (ov == bv && oi < bi)) {
+                    bv = ov;
+                    bi = oi;
+                }
+            }
+            if (lane == 0) {
+                iflag[1] = bi;
+                red[36] = bv;
+            }
+        }
+        __syncthreads();
+        const int p = iflag[1];
+        const double pv = red[36];
+        if (j == 0) n0 = pv;
+        if (!(pv > delta * delta * n0)) break;
+        __syncthreads();
+        if (p != j) {
+            for (int i = threadIdx.x; i < ku; i += blockDim.x) {
+                const double tmp = M[i + (size_t)j * ku];
+                M[i + (size_t)j * ku] = M[i + (size_t)p * ku];
+                M[i + (size_t)p * ku] = tmp;
+            }
+            if (threadIdx.x == 0) {
+                const double tc = cn[j];
+                cn[j] = cn[p];
+                cn[p] = tc;
+                const int tp = perm[j];
+                perm[j] = perm[p];
+                perm[p] = tp;
+            }
+        }
+        __syncthreads();
+        double *x = M + (size_t)j * ku;
+        if (warp == 0) {
+            double s = 0.0;
+            for (int i = j + lane; i < ku; i += 32) s += x[i] * x[i];
+            s = warp_sum(s);
+            const double x0 = x[j];
+            const double nrm = sqrt(s);
+            double tj = 0.0;
+            __syncwarp();
+            if (nrm > 0.0) {
+                const double alpha = x0 >= 0.0 ? -nrm : nrm;
+                const double v0 = x0 - alpha;
+                for (int i = j + 1 + lane; i < ku; i += 32) x[i] /= v0;
+                tj = (alpha - x0) / alpha;
+                __syncwarp();
+                if (lane == 0) x[j] = alpha;
+            }
+            if (lane == 0) tau[j] = tj;
+        }
+        __syncthreads();
+        const double tj = tau[j];
+        for (int c = j + 1 + warp; c < kv; c += nw) {
+            double *y = M + (size_t)c * ku;
+            double d = 0.0;
+            for (int i = j + 1 + lane; i < ku; i += 32) d += x[i] * y[i];
+            d = warp_sum(d);
+            d = (d + y[j]) * tj;
+            __syncwarp();
+            if (lane == 0) y[j] -= d;
+            double t2 = 0.0;
+            for (int i = j + 1 + lane; i < ku; i += 32) {
+                y[i] -= d * x[i];
+                t2 += y[i] * y[i];
+            }
+            t2 = warp_sum(t2);
+            if (lane == 0) cn[c] = t2;
+        }
+        __syncthreads();
+        r = j + 1;
+    }
+    return r;
+}
+
+// Z (ku x nc in shared memory, leading dimension ku) := Q Z with the r
+// reflectors of block_qrcp; one warp per column.
+__device__ void block_apply_qcp(const double *M, int ku, int r, const double *tau, double *Z, int nc) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int c = warp; c < nc; c += nw) {
+        double *y = Z + (size_t)c * ku;
+        for (int j = r - 1; j >= 0; --j) {
+            const double *x = M + (size_t)j * ku;
+            double d = 0.0;
+            for (int i = j + 1 + lane; i < ku; i += 32) d += x[i] * y[i];
+            d = warp_sum(d);
+            d = (d + y[j]) * tau[j];
+            __syncwarp();
+            if (lane == 0) y[j] -= d;
+            for (int i = j + 1 + lane; i < ku; i += 32) y[i] -= d * x[i];
+            __syncwarp();
+        }
+    }
 }
 
 // Rounded addition (Sec. 3.1): the target's factors and every contribution are
 // stacked, U_s = [U_c, c_1 U_1, ...], V_s = [V_c, V_1, ...] (pieces
 // zero-padded to the target's index ranges); both stacks are reduced by
-// Householder QR, the core R_u R_v^T is decomposed by one-sided Jacobi in
-// double, singular values sigma_i <= eps sigma_1 are dropped, and the new
-// factors are U = Q_u X Sigma, V = Q_v Y.
+// Householder QR, and the core M = R_u R_v^T (double) is decomposed: a QR with
+// column pivoting M P = Q_M [R'; ~0] (stopped at double-rounding level)
+// followed by one-sided Jacobi on R'^T gives M = X Sigma Y^T with X = Q_M [J; 0]
+// and Y = P W Sigma^{-1}; singular values sigma_i <= eps sigma_1 are dropped and
+// the new factors are U = Q_u [X Sigma; 0], V = Q_v [Y; 0].
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_radd(const TRadd *tasks, const Piece *pieces, LaunchArgs a, int kc) {
-    const TRadd t = tasks[blockIdx.x];
+__device__ void dev_radd(const TRadd &t, const Piece *pieces, const LaunchArgs &a, int kc, unsigned char *smem_raw,
+                         T *scratch) {
     T *A = reinterpret_cast<T *>(a.arena);
     int32_t *kd = a.kdyn;
     const int m = t.m, n = t.n;
@@ -422,17 +560,20 @@ __global__ void __launch_bounds__(kThreads) k_radd(const TRadd *tasks, const Pie
         if (threadIdx.x == 0) kd[t.kslot] = 0;
         return;
     }
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    double *M = reinterpret_cast<double *>(smem_raw);
-    double *J = M + (size_t)kc * kc;
+    double *M = reinterpret_cast<double *>(smem_raw);   // core, then QRCP reflectors
+    double *C = M + (size_t)kc * kc;                       // R'^T (kv x r), later Q_M [J Sigma; 0]
+    double *J = C + (size_t)kc * kc;                       // Jacobi rotations (r x r)
     double *tauU = J + (size_t)kc * kc;
     double *tauV = tauU + kc;
-    double *sig = tauV + kc;
-    double *red = sig + kc + kc;  // 40 doubles
+    double *tauM = tauV + kc;
+    double *sig = tauM + kc;
+    double *cn = sig + kc;
+    double *red = cn + kc;  // 40 doubles
     int *order = reinterpret_cast<int *>(red + 40);
-    int *iflag = order + kc;
+    int *perm = order + kc;
+    int *iflag = perm + kc;  // 8 ints
 
-    T *WU = A + t.scratch_off;
+    T *WU = scratch;
     T *WV = WU + (int64_t)m * K;
     // ---- stack the factors
     for (int64_t e = threadIdx.x; e < (int64_t)(m + n) * K; e += blockDim.x) WU[e] = T(0);
@@ -459,59 +600,230 @@ __global__ void __launch_bounds__(kThreads) k_radd(const TRadd *tasks, const Pie
     block_householder_qr(WU, m, K, tauU, red);
     block_householder_qr(WV, n, K, tauV, red);
     const int ku = min(m, K), kv = min(n, K);
-    // ---- core M = R_u R_v^T (double), J = I
+    // ---- core M = R_u R_v^T (double)
     for (int e = threadIdx.x; e < ku * kv; e += blockDim.x) {
         const int i = e % ku, j = e / ku;
         double s = 0.0;
         for (int l = max(i, j); l < K; ++l) s += (double)WU[i + (int64_t)l * m] * (double)WV[j + (int64_t)l * n];
         M[e] = s;
     }
-    for (int e = threadIdx.x; e < kv * kv; e += blockDim.x) J[e] = (e % kv == e / kv) ? 1.0 : 0.0;
     __syncthreads();
-    block_jacobi(M, ku, kv, J, iflag);
+    // ---- M P = Q_M [R'; ~0], then one-sided Jacobi on C = R'^T (kv x r)
+    const int r = block_qrcp(M, ku, kv, tauM, cn, perm, 1e-13, red, iflag);
+    for (int e = threadIdx.x; e < kv * r; e += blockDim.x) {
+        const int c = e % kv, i = e / kv;
+        C[e] = c >= i ? M[i + (size_t)c * ku] : 0.0;
+    }
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) J[e] = (e % r == e / r) ? 1.0 : 0.0;
+    __syncthreads();
+    block_jacobi(C, kv, r, J, iflag);
     // ---- singular values, ordering, truncation rank
-    for (int j = threadIdx.x; j < kv; j += blockDim.x) {
+    for (int j = threadIdx.x; j < r; j += blockDim.x) {
         double s = 0.0;
-        for (int i = 0; i < ku; ++i) s += M[i + (size_t)j * ku] * M[i + (size_t)j * ku];
+        for (int i = 0; i < kv; ++i) s += C[i + (size_t)j * kv] * C[i + (size_t)j * kv];
         sig[j] = sqrt(s);
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < kv; j += blockDim.x) {
+    for (int j = threadIdx.x; j < r; j += blockDim.x) {
         int rk = 0;
-        for (int l = 0; l < kv; ++l) rk += (sig[l] > sig[j]) || (sig[l] == sig[j] && l < j);
+        for (int l = 0; l < r; ++l) rk += (sig[l] > sig[j]) || (sig[l] == sig[j] && l < j);
         order[rk] = j;
     }
     __syncthreads();
-    const double s1 = sig[order[0]];
+    const double s1 = r > 0 ? sig[order[0]] : 0.0;
     int knew = 0;
     if (!isfinite(s1)) {
         if (threadIdx.x == 0) set_error(a.err, DE_NONFINITE, t.target, s1);
     } else if (s1 > 0.0) {
-        for (int l = 0; l < kv; ++l) knew += sig[order[l]] > a.eps * s1;
+        for (int l = 0; l < r; ++l) knew += sig[order[l]] > a.eps * s1;
     }
     if (knew > t.cap) {
         if (threadIdx.x == 0) set_error(a.err, DE_RANKCAP, t.target, (double)knew);
         knew = t.cap;
     }
-    // ---- new factors: U = Q_u [B_sel; 0], V = Q_v [J_sel; 0]
     T *Uc = A + t.U_off;
     T *Vc = A + t.V_off;
+    // ---- V = Q_v [P W_sel Sigma^{-1}; 0]
+    for (int e = threadIdx.x; e < n * knew; e += blockDim.x) Vc[e] = T(0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kv * knew; e += blockDim.x) {
+        const int i = e % kv, c = e / kv;
+        const int j = order[c];
+        Vc[perm[i] + (int64_t)c * n] = T(C[i + (size_t)j * kv] / sig[j]);
+    }
+    __syncthreads();
+    // ---- U = Q_u [Q_M [J_sel Sigma; 0]; 0] (C now holds the ku x knew product)
+    for (int e = threadIdx.x; e < ku * knew; e += blockDim.x) {
+        const int i = e % ku, c = e / ku;
+        const int j = order[c];
+        C[e] = i < r ? J[i + (size_t)j * r] * sig[j] : 0.0;
+    }
+    __syncthreads();
+    block_apply_qcp(M, ku, r, tauM, C, knew);
+    __syncthreads();
     for (int e = threadIdx.x; e < m * knew; e += blockDim.x) {
         const int i = e % m, c = e / m;
-        Uc[e] = i < ku ? T(M[i + (size_t)order[c] * ku]) : T(0);
-    }
-    for (int e = threadIdx.x; e < n * knew; e += blockDim.x) {
-        const int i = e % n, c = e / n;
-        Vc[e] = i < kv ? T(J[i + (size_t)order[c] * kv]) : T(0);
+        Uc[e] = i < ku ? T(C[i + (size_t)c * ku]) : T(0);
     }
     __syncthreads();
     block_apply_q(WU, m, ku, tauU, Uc, knew);
     block_apply_q(WV, n, kv, tauV, Vc, knew);
     if (threadIdx.x == 0) {
         kd[t.kslot] = knew;
-        const double kb = ku > kv ? ku : kv;
+        const double kb = ku > kv ? ku : kv;  // model: Jacobi SVD of the stacked core
         add_flops(a, K_RADD, qr_model_flops(m, K) + qr_model_flops(n, K) + 21.0 * kb * kb * kb +
                                  2.0 * ((double)m * ku + (double)n * kv) * knew);
+    }
+}
+
+// ------------------------------------------------------------ wave kernels
+// One launch per (wave, kind): CTA b executes task b of the launch's slice.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_getrf(const TGetrf *tasks, LaunchArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const TGetrf t = tasks[blockIdx.x];
+    dev_getrf<T>(t, a, smem_raw);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_trsm(const TTrsm *tasks, LaunchArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const TTrsm t = tasks[blockIdx.x];
+    dev_trsm<T>(t, a, smem_raw);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_project(const TProject *tasks, LaunchArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const TProject t = tasks[blockIdx.x];
+    dev_project<T>(t, a, smem_raw);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_accum(const TAccum *tasks, const Term *terms, LaunchArgs a) {
+    const TAccum t = tasks[blockIdx.x];
+    dev_accum<T>(t, terms, a);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_split(const TSplit *tasks, LaunchArgs a) {
+    const TSplit t = tasks[blockIdx.x];
+    dev_split<T>(t, a);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_radd(const TRadd *tasks, const Piece *pieces, LaunchArgs a, int kc) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const TRadd t = tasks[blockIdx.x];
+    dev_radd<T>(t, pieces, a, kc, smem_raw, reinterpret_cast<T *>(a.arena) + t.scratch_off);
+}
+
+// -------------------------------------------------------- data-flow kernel
+// One persistent launch executes the whole task graph.  Worker CTAs claim
+// queue slots in order (atomic head); a slot holds the id of a ready task once
+// the last predecessor of that task has finished and pushed it (atomic tail).
+// A finished task releases its successors: the last one to decrement a
+// successor's in-degree pushes it.  Writes of a task are published with a
+// device-scope fence before the release; the consumer reads the slot with an
+// acquire load.  Every wait has a deadline (%globaltimer): on expiry, or when
+// another worker has recorded an error, the worker records DE_TIMEOUT (first
+// error wins) and leaves, so the launch always ends.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int *p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_dataflow(FlowArgs f, LaunchArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_task;
+    T *scratch = reinterpret_cast<T *>(f.scratch) + (int64_t)blockIdx.x * f.scratch_stride;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int slot = atomicAdd(f.counters, 1);
+            int g = -1;
+            if (slot < f.n_tasks) {
+                const unsigned long long deadline = global_ns() + f.timeout_ns;
+                for (;;) {
+                    g = ld_acquire(f.queue + slot);
+                    if (g >= 0) break;
+                    if (*(volatile long long *)a.err != 0) {
+                        g = -2;
+                        break;
+                    }
+                    if (global_ns() > deadline) {
+                        set_error(a.err, DE_TIMEOUT, slot, 0.0);
+                        g = -2;
+                        break;
+                    }
+                    __nanosleep(100);
+                }
+            }
+            s_task = g;
+        }
+        __syncthreads();
+        const int g = s_task;
+        if (g < 0) break;
+        const int code = f.code[g];
+        const int kind = code >> kCodeShift, idx = code & kCodeMask;
+        switch (kind) {
+            case K_GETRF: {
+                const TGetrf t = f.getrf[idx];
+                dev_getrf<T>(t, a, smem_raw);
+                break;
+            }
+            case K_TRSM: {
+                const TTrsm t = f.trsm[idx];
+                dev_trsm<T>(t, a, smem_raw);
+                break;
+            }
+            case K_PROJECT: {
+                const TProject t = f.project[idx];
+                dev_project<T>(t, a, smem_raw);
+                break;
+            }
+            case K_ACCUM: {
+                const TAccum t = f.accum[idx];
+                dev_accum<T>(t, f.terms, a);
+                break;
+            }
+            case K_RADD: {
+                const TRadd t = f.radd[idx];
+                dev_radd<T>(t, f.pieces, a, f.kc, smem_raw, scratch);
+                break;
+            }
+            case K_SPLIT: {
+                const TSplit t = f.split[idx];
+                dev_split<T>(t, a);
+                break;
+            }
+            default:
+                break;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            for (int e = f.succ_ptr[g]; e < f.succ_ptr[g + 1]; ++e) {
+                const int s = f.succ_idx[e];
+                if (atomicSub(f.indeg + s, 1) == 1) {
+                    __threadfence();
+                    const int pos = atomicAdd(f.counters + 1, 1);
+                    st_release(f.queue + pos, s);
+                }
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -605,7 +917,8 @@ void launch_kind(int kind, const void *tasks, const Term *terms, const Piece *pi
                 reinterpret_cast<const TTrsm *>(tasks) + start, a);
             break;
         case K_PROJECT:
-            k_project<T><<<count, kThreads, 0, s>>>(reinterpret_cast<const TProject *>(tasks) + start, a);
+            k_project<T><<<count, kThreads, 2 * 32 * 65 * sizeof(T), s>>>(
+                reinterpret_cast<const TProject *>(tasks) + start, a);
             break;
         case K_ACCUM:
             k_accum<T><<<count, kThreads, 0, s>>>(reinterpret_cast<const TAccum *>(tasks) + start, terms, a);
@@ -623,12 +936,55 @@ void launch_kind(int kind, const void *tasks, const Term *terms, const Piece *pi
     }
 }
 
-template <class T>
-void set_kernel_attributes() {
-    cudaFuncSetAttribute(k_radd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_getrf<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_trsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+// Lets a kernel use all of the opt-in shared memory beside its static share.
+template <class K>
+static bool allow_dynamic_smem(K kernel, int optin) {
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return false;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin - (int)fa.sharedSizeBytes) == cudaSuccess;
 }
+
+template <class T>
+bool set_kernel_attributes() {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    bool ok = allow_dynamic_smem(k_radd<T>, optin);
+    ok = allow_dynamic_smem(k_getrf<T>, optin) && ok;
+    ok = allow_dynamic_smem(k_trsm<T>, optin) && ok;
+    ok = allow_dynamic_smem(k_project<T>, optin) && ok;
+    ok = allow_dynamic_smem(k_dataflow<T>, optin) && ok;
+    cudaGetLastError();  // a failure is reported through the return value, not left pending
+    return ok;
+}
+
+size_t dataflow_smem_bytes(int max_leaf, int elem, int kc) {
+    size_t s = getrf_smem_bytes(max_leaf, elem);
+    s = std::max(s, (size_t)2 * 32 * 65 * elem);
+    s = std::max(s, radd_smem_bytes(kc));
+    return s;
+}
+
+template <class T>
+int dataflow_workers(size_t smem) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_dataflow<T>, kThreads, smem) != cudaSuccess || per < 1)
+        per = 1;
+    return sms * per;
+}
+
+template <class T>
+void launch_dataflow(const FlowArgs &f, const LaunchArgs &a, int grid, size_t smem, cudaStream_t s) {
+    k_dataflow<T><<<grid, kThreads, smem, s>>>(f, a);
+}
+
+template int dataflow_workers<double>(size_t);
+template int dataflow_workers<float>(size_t);
+template void launch_dataflow<double>(const FlowArgs &, const LaunchArgs &, int, size_t, cudaStream_t);
+template void launch_dataflow<float>(const FlowArgs &, const LaunchArgs &, int, size_t, cudaStream_t);
 
 template <class T>
 void launch_reset(const int64_t *leaf_desc, int64_t n_leaves, const double *aarena, T *farena, int32_t *kdyn,
@@ -678,8 +1034,8 @@ template void launch_kind<double>(int, const void *, const Term *, const Piece *
                                   cudaStream_t);
 template void launch_kind<float>(int, const void *, const Term *, const Piece *, int, int, int, const LaunchArgs &,
                                  cudaStream_t);
-template void set_kernel_attributes<double>();
-template void set_kernel_attributes<float>();
+template bool set_kernel_attributes<double>();
+template bool set_kernel_attributes<float>();
 template void launch_reset<double>(const int64_t *, int64_t, const double *, double *, int32_t *, cudaStream_t);
 template void launch_reset<float>(const int64_t *, int64_t, const double *, float *, int32_t *, cudaStream_t);
 template void launch_permute<double, double>(const int32_t *, int32_t, int32_t, const double *, int64_t, double *,

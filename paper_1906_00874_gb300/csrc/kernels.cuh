@@ -23,6 +23,35 @@ template <class T>
 void launch_kind(int kind, const void *tasks, const Term *terms, const Piece *pieces, int start,
                  int count, int kcap, const LaunchArgs &a, cudaStream_t s);
 
+// Persistent data-flow execution of a whole plan (one launch).
+struct FlowArgs {
+    const int32_t *code;       // per task: (kind << kCodeShift) | index in the kind's array
+    const int32_t *succ_ptr;   // successors, CSR
+    const int32_t *succ_idx;
+    int32_t *indeg;            // working in-degrees (reset before every launch)
+    int32_t *queue;            // n_tasks slots, -1 = empty
+    int32_t *counters;         // [0] head (next slot to claim), [1] tail (next slot to fill)
+    int32_t n_tasks;
+    int32_t kc;                // core capacity of rounded additions (shared memory)
+    const TGetrf *getrf;
+    const TTrsm *trsm;
+    const TProject *project;
+    const TAccum *accum;
+    const TRadd *radd;
+    const TSplit *split;
+    const Term *terms;
+    const Piece *pieces;
+    void *scratch;             // per-worker rounded-addition workspace (T elements)
+    int64_t scratch_stride;    // elements per worker
+    unsigned long long timeout_ns;  // limit of any single wait for a ready task
+};
+
+size_t dataflow_smem_bytes(int max_leaf, int elem, int kc);
+template <class T>
+int dataflow_workers(size_t smem);
+template <class T>
+void launch_dataflow(const FlowArgs &f, const LaunchArgs &a, int grid, size_t smem, cudaStream_t s);
+
 // Restore the factor arena from the original matrix (the factorisation works in place).
 template <class T>
 void launch_reset(const int64_t *leaf_desc, int64_t n_leaves, const double *aarena, T *farena,

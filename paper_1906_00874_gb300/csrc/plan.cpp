@@ -31,6 +31,8 @@ int32_t Planner::new_obj(int32_t row_cl, int32_t col_cl, int32_t nr_if_none) {
     if ((int64_t)cell_write_wave.size() < need) {
         cell_write_wave.resize(need, -1);
         cell_read_wave.resize(need, -1);
+        cell_writer.resize(need, -1);
+        cell_rhead.resize(need, -1);
     }
     return int32_t(objs.size() - 1);
 }
@@ -90,6 +92,32 @@ int32_t Planner::emit(Kind k, const std::vector<const View *> &reads,
         cell_write_wave[c] = w;
         cell_read_wave[c] = -1;
     }
+    // explicit edges: read-after-write, write-after-write, write-after-read
+    const int32_t g = int32_t(P->n_tasks);
+    static thread_local std::vector<int32_t> pr;
+    pr.clear();
+    for (int64_t c : rc)
+        if (cell_writer[c] >= 0) pr.push_back(cell_writer[c]);
+    for (int64_t c : wc) {
+        if (cell_writer[c] >= 0) pr.push_back(cell_writer[c]);
+        for (int32_t e = cell_rhead[c]; e >= 0; e = rpool_next[e])
+            if (rpool_task[e] != g) pr.push_back(rpool_task[e]);
+    }
+    std::sort(pr.begin(), pr.end());
+    pr.erase(std::unique(pr.begin(), pr.end()), pr.end());
+    if (P->pred_ptr.empty()) P->pred_ptr.push_back(0);
+    P->pred_idx.insert(P->pred_idx.end(), pr.begin(), pr.end());
+    P->pred_ptr.push_back(int32_t(P->pred_idx.size()));
+    for (int64_t c : rc) {
+        rpool_task.push_back(g);
+        rpool_next.push_back(cell_rhead[c]);
+        cell_rhead[c] = int32_t(rpool_task.size() - 1);
+    }
+    for (int64_t c : wc) {
+        cell_writer[c] = g;
+        cell_rhead[c] = -1;
+    }
+    P->task_code.push_back((int32_t(k) << kCodeShift) | int32_t(P->wave[k].size()));
     P->wave[k].push_back(w);
     P->n_tasks++;
     P->n_waves = std::max(P->n_waves, w + 1);
@@ -482,30 +510,62 @@ void Planner::begin_plan(Plan &p, bool astore_mode, int64_t *bump) {
     arena = bump;
     std::fill(cell_write_wave.begin(), cell_write_wave.end(), -1);
     std::fill(cell_read_wave.begin(), cell_read_wave.end(), -1);
+    std::fill(cell_writer.begin(), cell_writer.end(), -1);
+    std::fill(cell_rhead.begin(), cell_rhead.end(), -1);
+    rpool_task.clear();
+    rpool_next.clear();
 }
 
+// Sorts a kind's tasks by wave (stable); returns new position of every old index.
 template <class T>
-static void permute_by_wave(std::vector<T> &v, std::vector<int32_t> &w) {
+static std::vector<int32_t> permute_by_wave(std::vector<T> &v, std::vector<int32_t> &w) {
     std::vector<int32_t> idx(v.size());
     for (size_t i = 0; i < idx.size(); ++i) idx[i] = int32_t(i);
     std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) { return w[a] < w[b]; });
     std::vector<T> nv(v.size());
-    std::vector<int32_t> nw(w.size());
+    std::vector<int32_t> nw(w.size()), where(v.size());
     for (size_t i = 0; i < idx.size(); ++i) {
         nv[i] = v[idx[i]];
         nw[i] = w[idx[i]];
+        where[idx[i]] = int32_t(i);
     }
     v.swap(nv);
     w.swap(nw);
+    return where;
 }
 
 void Planner::finalize(Plan &p, int64_t *bump) {
-    permute_by_wave(p.getrf, p.wave[K_GETRF]);
-    permute_by_wave(p.trsm, p.wave[K_TRSM]);
-    permute_by_wave(p.project, p.wave[K_PROJECT]);
-    permute_by_wave(p.accum, p.wave[K_ACCUM]);
-    permute_by_wave(p.radd, p.wave[K_RADD]);
-    permute_by_wave(p.split, p.wave[K_SPLIT]);
+    std::vector<int32_t> where[K_NKINDS];
+    where[K_GETRF] = permute_by_wave(p.getrf, p.wave[K_GETRF]);
+    where[K_TRSM] = permute_by_wave(p.trsm, p.wave[K_TRSM]);
+    where[K_PROJECT] = permute_by_wave(p.project, p.wave[K_PROJECT]);
+    where[K_ACCUM] = permute_by_wave(p.accum, p.wave[K_ACCUM]);
+    where[K_RADD] = permute_by_wave(p.radd, p.wave[K_RADD]);
+    where[K_SPLIT] = permute_by_wave(p.split, p.wave[K_SPLIT]);
+    // task codes follow the permutation; successors from the predecessor lists
+    for (int32_t &c : p.task_code) {
+        const int32_t k = c >> kCodeShift, i = c & kCodeMask;
+        c = (k << kCodeShift) | where[k][i];
+    }
+    const int64_t nt = p.n_tasks;
+    if (p.pred_ptr.empty()) p.pred_ptr.push_back(0);
+    p.indeg.assign(nt, 0);
+    p.succ_ptr.assign(nt + 1, 0);
+    for (int64_t g = 0; g < nt; ++g) {
+        p.indeg[g] = p.pred_ptr[g + 1] - p.pred_ptr[g];
+        for (int32_t e = p.pred_ptr[g]; e < p.pred_ptr[g + 1]; ++e) p.succ_ptr[p.pred_idx[e] + 1]++;
+    }
+    for (int64_t g = 0; g < nt; ++g) p.succ_ptr[g + 1] += p.succ_ptr[g];
+    p.succ_idx.assign(p.pred_idx.size(), 0);
+    {
+        std::vector<int32_t> fill(p.succ_ptr.begin(), p.succ_ptr.end() - 1);
+        for (int64_t g = 0; g < nt; ++g)
+            for (int32_t e = p.pred_ptr[g]; e < p.pred_ptr[g + 1]; ++e) p.succ_idx[fill[p.pred_idx[e]]++] = int32_t(g);
+    }
+    p.n_edges = (int64_t)p.pred_idx.size();
+    p.roots.clear();
+    for (int64_t g = 0; g < nt; ++g)
+        if (p.indeg[g] == 0) p.roots.push_back(int32_t(g));
     // rounded-addition scratch: tasks of one wave get disjoint regions, waves reuse them
     int64_t base = align8(*bump), maxw = 0;
     {

@@ -79,6 +79,12 @@ struct Plan {
     std::vector<Launch> launches;
     int32_t n_waves = 0;
     int64_t n_tasks = 0;
+    // explicit dependency graph over all tasks, numbered in emission order
+    std::vector<int32_t> task_code;           // (kind << kCodeShift) | index into the kind's (wave-sorted) array
+    std::vector<int32_t> pred_ptr, pred_idx;  // predecessors (CSR), built during emission
+    std::vector<int32_t> succ_ptr, succ_idx;  // successors (CSR), built by finalize
+    std::vector<int32_t> indeg, roots;
+    int64_t n_edges = 0;
     int64_t scratch_base = 0, scratch_elems = 0;
     int32_t max_kcap = 0;
 };
@@ -139,6 +145,9 @@ private:
     int64_t *arena = nullptr;  // bump pointer of the current arena
     std::vector<Obj> objs;
     std::vector<int32_t> cell_write_wave, cell_read_wave;
+    // per cell: last writer and the readers since (singly linked lists in a pool)
+    std::vector<int32_t> cell_writer, cell_rhead;
+    std::vector<int32_t> rpool_task, rpool_next;
     int32_t ident_obj = -1;
 
     int32_t new_obj(int32_t row_cl, int32_t col_cl, int32_t nr_if_none = 1);

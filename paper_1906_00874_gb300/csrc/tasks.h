@@ -29,6 +29,10 @@ enum Kind : int32_t {
     K_NKINDS = 6
 };
 
+// A task of the data-flow graph is coded as (kind << kCodeShift) | index.
+constexpr int kCodeShift = 28;
+constexpr int32_t kCodeMask = (1 << kCodeShift) - 1;
+
 enum TrsmMode : int32_t {
     TR_LOWER_UNIT = 0,   // P := L^{-1} P, L unit lower (strict lower part of the leaf)
     TR_UPPER_TRANS = 1,  // P := U^{-T} P, U upper part of the leaf (X U^{-1} on X^T)

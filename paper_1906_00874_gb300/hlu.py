@@ -16,14 +16,16 @@ LIB_PATH = os.path.join(_PKG, "libhlu.so")
 
 HLU_FP64 = 0
 HLU_FP32 = 1
+SCHED_DATAFLOW = 0
+SCHED_WAVES = 1
 
 STATUS = {0: "HLU_OK", 1: "HLU_EINVAL", 2: "HLU_ENOMEM", 3: "HLU_ESTATE", 4: "HLU_EPIVOT",
           5: "HLU_ERANKCAP", 6: "HLU_ETIMEOUT", 7: "HLU_ECUDA", 8: "HLU_ENUMERIC"}
 
 EXPORTS = ("hlu_create", "hlu_factor", "hlu_solve", "hlu_matvec", "hlu_solve_refined", "hlu_factor_doubles",
            "hlu_get_factors", "hlu_get_stats", "hlu_set_profiling", "hlu_destroy", "hlu_strerror",
-           "hlu_last_error_detail", "hlu_probe_alu_peaks")
-KINDS = ("getrf", "trsm", "project", "accum", "radd", "split")
+           "hlu_last_error_detail", "hlu_last_cuda_error", "hlu_probe_alu_peaks")
+KINDS = ("getrf", "trsm", "project", "accum", "radd", "split", "dataflow")
 
 
 class HLUError(RuntimeError):
@@ -46,7 +48,7 @@ class _Blocks(ctypes.Structure):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("rank_cap", ctypes.c_int32), ("nrhs_max", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("mem_budget", ctypes.c_int64), ("timeout_s", ctypes.c_double)]
+                ("schedule", ctypes.c_int32), ("mem_budget", ctypes.c_int64), ("timeout_s", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -95,6 +97,8 @@ def load(path=LIB_PATH):
     lib.hlu_strerror.argtypes = [ctypes.c_int]
     lib.hlu_strerror.restype = ctypes.c_char_p
     lib.hlu_last_error_detail.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(dbl)]
+    lib.hlu_last_cuda_error.argtypes = [vp]
+    lib.hlu_last_cuda_error.restype = ctypes.c_char_p
     _lib = lib
     return lib
 
@@ -147,7 +151,8 @@ class HLU:
     """One H-matrix on the GPU: factorise once, solve many times."""
 
     def __init__(self, n, perm, begin, size, son0, son1, row_cl, col_cl, kind, rank, offset, data,
-                 precision=HLU_FP64, rank_cap=0, nrhs_max=0, mem_budget=0, stream=None):
+                 precision=HLU_FP64, rank_cap=0, nrhs_max=0, mem_budget=0, stream=None,
+                 schedule=SCHED_DATAFLOW, timeout_s=0.0):
         lib = load()
         self._h = ctypes.c_void_p()
         keep = [np.ascontiguousarray(a, dtype=t) for a, t in (
@@ -158,7 +163,7 @@ class HLU:
         tree = _Tree(int(n), int(begin_.shape[0]), _ptr(perm_), _ptr(begin_), _ptr(size_), _ptr(son0_), _ptr(son1_))
         blocks = _Blocks(int(row_.shape[0]), _ptr(row_), _ptr(col_), _ptr(kind_), _ptr(rank_), _ptr(off_),
                          _ptr(data_), int(data_.shape[0]))
-        opts = _Opts(int(precision), int(rank_cap), int(nrhs_max), 0, int(mem_budget), 0.0)
+        opts = _Opts(int(precision), int(rank_cap), int(nrhs_max), int(schedule), int(mem_budget), float(timeout_s))
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
@@ -179,6 +184,8 @@ class HLU:
 
     def _check(self, st, what):
         if st != 0:
+            if st == 7:  # HLU_ECUDA: say which CUDA error
+                what = f"{what} [{load().hlu_last_cuda_error(self._h).decode()}]"
             raise HLUError(st, what)
 
     def factor(self, eps):
