@@ -167,6 +167,14 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
 def make_handle(p, precision, stream):
     from paper_1906_00874_gb300 import HLU
     return HLU.from_problem(p, precision=precision, stream=stream)
@@ -284,22 +292,39 @@ def run_native(args):
     # ---------------- end to end through the public API with host buffers
     e2e = e2e_arm(p, HLU_FP32, sptr, min(args.steps, 3), f32)
 
-    # ---------------- roofline of the dominant kernel class (profiled pass)
+    # ---------------- roofline of the dominant kernel (profiled pass, CUDA events on the stream)
     fp64_peak, fp32_peak = probe_alu_peaks()
     ms = prof["kernel_ms"]
     dom = max(ms, key=lambda k: ms[k])
-    dom_flops = st32["flops_by_kind"][dom]  # per step (factor side)
     dom_ms = ms[dom] / nprof
+    launches = prof["kernel_launches"][dom] / nprof
+    if dom == "dataflow_factor":
+        # one persistent launch runs the whole factorisation task graph
+        dom_flops = st32["model_flops"]
+        kname = "k_dataflow<float> (factorisation)"
+    elif dom == "dataflow_solve":
+        dom_flops = st32["solve_flops"]
+        kname = "k_dataflow (solves and FP64 products)"
+    else:
+        dom_flops = st32["flops_by_kind"][dom]
+        kname = f"k_{dom}<float>"
     achieved = dom_flops / (dom_ms * 1e-3) / 1e12 if dom_ms > 0 else 0.0
-    roof = {"kernel": f"k_{dom}<float>", "bound": "alu", "achieved": achieved,
-            "peak": fp32_peak if dom not in ("radd",) else fp64_peak, "unit": "TFLOP/s",
-            "frac": None, "traffic": None,
-            "peak_source": ("measured FP32 FMA probe (hlu_probe_alu_peaks)" if dom != "radd"
-                            else "measured FP64 FMA probe (hlu_probe_alu_peaks): the truncation core is FP64"),
+    # algorithmic bytes of the factorisation: read A_H once (FP64) and write the factors once (FP32)
+    alg_bytes = 1.5 * p.data.nbytes if dom == "dataflow_factor" else None
+    hbm_peak = measured_peaks().get("hbm_gbs", 6800.0)
+    roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak if fp32_peak else None, "traffic": None,
+            "peak_source": "measured FP32 FMA probe (hlu_probe_alu_peaks), of measured",
+            "model_gflop_per_launch": dom_flops / 1e9 / max(launches, 1e-9),
+            "avg_launch_ms": dom_ms / max(launches, 1e-9), "launches_per_step": launches,
             "share_of_kernel_time": ms[dom] / max(1e-9, sum(ms.values())),
-            "launches_per_step": prof["kernel_launches"][dom] / nprof,
-            "kernel_ms_per_step": {k: v / nprof for k, v in ms.items()}}
-    roof["frac"] = roof["achieved"] / roof["peak"] if roof["peak"] else None
+            "hbm_view": None if alg_bytes is None else {
+                "alg_bytes_per_launch": alg_bytes,
+                "achieved_gbs": alg_bytes / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else 0.0,
+                "peak_gbs": hbm_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (fallback 6800)"},
+            "kernel_ms_per_step": {k: v / nprof for k, v in ms.items()},
+            "task_busy_ms_per_factor": {k: v / nprof for k, v in prof["task_busy_ms"].items() if v},
+            "tasks_per_factor": {k: v // nprof for k, v in prof["task_count"].items() if v}}
 
     cpu = None
     if rank == 0:

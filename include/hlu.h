@@ -163,8 +163,12 @@ typedef struct {
     double model_flops;       /* model flops of the last hlu_factor */
     double flops_by_kind[8];  /* the same, per task kind */
     double solve_flops;       /* model flops of solves and products since the last hlu_factor */
-    double kernel_ms[8];      /* with profiling on: summed kernel time per task kind */
+    double kernel_ms[8];      /* with profiling on: summed kernel time per task kind; slots 6 / 7
+                                 hold the data-flow launches of factorisations / of solves */
     int64_t kernel_launches[8];
+    double task_busy_ms[8];   /* with profiling on, data-flow factorisations: summed time of the
+                                 tasks of each kind (concurrent tasks add up) */
+    int64_t task_count[8];
     int64_t kernels_launched; /* kernels this handle launched since it was created */
     int32_t max_rank;         /* largest rank after the factorisation */
     int32_t max_stacked;      /* largest stacked-rank capacity of a rounded addition */

@@ -80,6 +80,7 @@ struct hlu_ctx {
     int64_t prof_count[8] = {0};
     int64_t kernels_launched = 0;
     cudaError_t last_cuda = cudaSuccess;
+    unsigned long long *busy = nullptr;  // per-kind task time inside the data-flow kernel (profiling)
 };
 
 namespace {
@@ -231,12 +232,14 @@ void run_plan(hlu_ctx *h, const DevPlan &d, void *arena, double *flops) {
         f.scratch = d.scratch;
         f.scratch_stride = d.scratch_stride;
         f.timeout_ns = h->timeout_ns;
+        f.busy = (h->profiling && &d == &h->fp) ? h->busy : nullptr;
         cudaMemcpyAsync(d.indeg, d.indeg0, sizeof(int32_t) * d.n_tasks, cudaMemcpyDeviceToDevice, h->stream);
         cudaMemsetAsync(d.queue, 0xff, sizeof(int32_t) * d.n_tasks, h->stream);
         cudaMemcpyAsync(d.queue, d.roots, sizeof(int32_t) * d.n_roots, cudaMemcpyDeviceToDevice, h->stream);
         cudaMemsetAsync(d.counters, 0, 2 * sizeof(int32_t), h->stream);
         launch_set_slot(d.counters, 1, d.n_roots, h->stream);
-        Pending pe{K_NKINDS, nullptr, nullptr};
+        // profiling slots 6 / 7: the data-flow launch of a factorisation / of a solve or product
+        Pending pe{&d == &h->fp ? K_NKINDS : K_NKINDS + 1, nullptr, nullptr};
         if (h->profiling) {
             pe.e0 = take_event(h);
             pe.e1 = take_event(h);
@@ -426,6 +429,8 @@ int hlu_create(const hlu_tree *tree, const hlu_blocks *blocks, const hlu_opts *o
     if (st == HLU_OK) st = upload(h, &h->kdyn, h->pl.slot_init);
     if (st == HLU_OK) st = dalloc(h, &h->err, 4);
     if (st == HLU_OK) st = dalloc(h, &h->flops, 16);
+    if (st == HLU_OK) st = dalloc(h, &h->busy, 16);
+    if (st == HLU_OK) st = cuda_status(cudaMemsetAsync(h->busy, 0, 16 * sizeof(unsigned long long), h->stream));
     if (st == HLU_OK) st = cuda_status(cudaMemsetAsync(h->flops, 0, 16 * sizeof(double), h->stream));
     if (st == HLU_OK) st = dalloc(h, &h->ir, 3 * n * w + 2 * w);
     if (st == HLU_OK) st = cuda_status(cudaMallocHost(reinterpret_cast<void **>(&h->ir_host), 2 * w * sizeof(double)));
@@ -674,6 +679,12 @@ int hlu_get_stats(hlu_t h, hlu_stats *o) {
         o->model_flops += fl[k];
         o->solve_flops += fl[8 + k];
     }
+    unsigned long long bz[16];
+    if (cudaMemcpy(bz, h->busy, sizeof(bz), cudaMemcpyDeviceToHost) != cudaSuccess) return HLU_ECUDA;
+    for (int k = 0; k < 8; ++k) {
+        o->task_busy_ms[k] = bz[k] * 1e-6;
+        o->task_count[k] = (int64_t)bz[8 + k];
+    }
     if (h->factored) {
         std::vector<int32_t> kd(h->pl.n_slots);
         if (cudaMemcpy(kd.data(), h->kdyn, sizeof(int32_t) * h->pl.n_slots, cudaMemcpyDeviceToHost) == cudaSuccess)
@@ -692,6 +703,7 @@ int hlu_set_profiling(hlu_t h, int32_t on) {
         h->prof_ms[k] = 0.0;
         h->prof_count[k] = 0;
     }
+    if (cudaMemset(h->busy, 0, 16 * sizeof(unsigned long long)) != cudaSuccess) return HLU_ECUDA;
     return HLU_OK;
 }
 

@@ -777,6 +777,7 @@ __global__ void __launch_bounds__(kThreads) k_dataflow(FlowArgs f, LaunchArgs a)
         if (g < 0) break;
         const int code = f.code[g];
         const int kind = code >> kCodeShift, idx = code & kCodeMask;
+        const unsigned long long t_start = (f.busy && threadIdx.x == 0) ? global_ns() : 0ull;
         switch (kind) {
             case K_GETRF: {
                 const TGetrf t = f.getrf[idx];
@@ -813,6 +814,10 @@ __global__ void __launch_bounds__(kThreads) k_dataflow(FlowArgs f, LaunchArgs a)
         }
         __syncthreads();
         if (threadIdx.x == 0) {
+            if (f.busy) {
+                atomicAdd(f.busy + kind, global_ns() - t_start);
+                atomicAdd(f.busy + 8 + kind, 1ull);
+            }
             __threadfence();
             for (int e = f.succ_ptr[g]; e < f.succ_ptr[g + 1]; ++e) {
                 const int s = f.succ_idx[e];

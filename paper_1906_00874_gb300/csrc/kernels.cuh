@@ -44,6 +44,7 @@ struct FlowArgs {
     void *scratch;             // per-worker rounded-addition workspace (T elements)
     int64_t scratch_stride;    // elements per worker
     unsigned long long timeout_ns;  // limit of any single wait for a ready task
+    unsigned long long *busy;  // when profiling: [kind] task nanoseconds, [8 + kind] task count; else null
 };
 
 size_t dataflow_smem_bytes(int max_leaf, int elem, int kc);

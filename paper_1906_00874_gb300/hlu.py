@@ -25,7 +25,7 @@ STATUS = {0: "HLU_OK", 1: "HLU_EINVAL", 2: "HLU_ENOMEM", 3: "HLU_ESTATE", 4: "HL
 EXPORTS = ("hlu_create", "hlu_factor", "hlu_solve", "hlu_matvec", "hlu_solve_refined", "hlu_factor_doubles",
            "hlu_get_factors", "hlu_get_stats", "hlu_set_profiling", "hlu_destroy", "hlu_strerror",
            "hlu_last_error_detail", "hlu_last_cuda_error", "hlu_probe_alu_peaks")
-KINDS = ("getrf", "trsm", "project", "accum", "radd", "split", "dataflow")
+KINDS = ("getrf", "trsm", "project", "accum", "radd", "split", "dataflow_factor", "dataflow_solve")
 
 
 class HLUError(RuntimeError):
@@ -58,10 +58,11 @@ class Stats(ctypes.Structure):
                 ("tasks_by_kind", ctypes.c_int64 * 8), ("model_flops", ctypes.c_double),
                 ("flops_by_kind", ctypes.c_double * 8), ("solve_flops", ctypes.c_double),
                 ("kernel_ms", ctypes.c_double * 8), ("kernel_launches", ctypes.c_int64 * 8),
+                ("task_busy_ms", ctypes.c_double * 8), ("task_count", ctypes.c_int64 * 8),
                 ("kernels_launched", ctypes.c_int64), ("max_rank", ctypes.c_int32), ("max_stacked", ctypes.c_int32)]
 
     def as_dict(self):
-        per_kind = ("tasks_by_kind", "flops_by_kind", "kernel_ms", "kernel_launches")
+        per_kind = ("tasks_by_kind", "flops_by_kind", "kernel_ms", "kernel_launches", "task_busy_ms", "task_count")
         d = {f: getattr(self, f) for f, _ in self._fields_ if f not in per_kind}
         for f in per_kind:
             d[f] = dict(zip(KINDS, list(getattr(self, f))[:len(KINDS)]))
