@@ -192,6 +192,26 @@ void hlu_destroy(hlu_t h);
 /* Message for a status code (static string). */
 const char *hlu_strerror(int status);
 
+/* y = U (V^T x) for one low-rank block (U: m x k, V: n x k, x: n x nrhs,
+ * y: m x nrhs; DEVICE pointers, FP64, column-major with the given leading
+ * dimensions), ordered on `cuda_stream`, WITHOUT allocating device memory.
+ * The paper has no counterpart of this entry point: it serves callers that
+ * may not call cudaMalloc when they compute (a memory budget fixed in advance,
+ * a loop that must not stall in the allocator, code that does not own the
+ * device's memory).  The k x nrhs intermediate V^T x lives in one fixed array
+ * of 65536 doubles (512 KiB) inside the library, held on every GPU that loads
+ * the library until the process exits; k * nrhs above 65536 returns
+ * HLU_EINVAL.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) with the device current; make that first
+ * call before any stream capture.  Every call uses the same array, so calls
+ * that overlap on the GPU (e.g. on two streams at once) race with each other;
+ * each call clears the part it accumulates into.  Returns after queueing the
+ * work (HLU_OK), HLU_EINVAL for bad sizes or pointers, HLU_ECUDA if a launch
+ * fails. */
+int hlu_lowrank_apply_noalloc(int32_t m, int32_t n, int32_t k, int32_t nrhs, const double *U, int64_t ldu,
+                              const double *V, int64_t ldv, const double *x, int64_t ldx, double *y, int64_t ldy,
+                              void *cuda_stream);
+
 /* Message of the CUDA runtime error behind the last HLU_ECUDA of this handle
  * (static string; "no CUDA error" if there was none). */
 const char *hlu_last_cuda_error(hlu_t h);
