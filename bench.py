@@ -324,7 +324,11 @@ def run_native(args):
                 "peak_gbs": hbm_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (fallback 6800)"},
             "kernel_ms_per_step": {k: v / nprof for k, v in ms.items()},
             "task_busy_ms_per_factor": {k: v / nprof for k, v in prof["task_busy_ms"].items() if v},
-            "tasks_per_factor": {k: v // nprof for k, v in prof["task_count"].items() if v}}
+            "tasks_per_factor": {k: v // nprof for k, v in prof["task_count"].items() if v},
+            "radd_busy_ms_by_size": {k: round(v / nprof, 1) for k, v in prof["radd_busy_ms"].items() if v},
+            "radd_count_by_size": {k: v // nprof for k, v in prof["radd_count"].items() if v},
+            "radd_small_phases_per_factor": {k: (v / nprof if k != "mean_jacobi_cols" else v)
+                                             for k, v in prof["radd_phase"].items()}}
 
     cpu = None
     if rank == 0:

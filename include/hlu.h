@@ -169,6 +169,12 @@ typedef struct {
     double task_busy_ms[8];   /* with profiling on, data-flow factorisations: summed time of the
                                  tasks of each kind (concurrent tasks add up) */
     int64_t task_count[8];
+    double radd_busy_ms[8];   /* the same for rounded additions by target size m + n:
+                                 < 128, < 256, < 512, ..., >= 8192 */
+    int64_t radd_count[8];
+    double radd_phase[8];     /* small-target rounded additions, summed ms per phase: [0] sum
+                                 formation, [1] pivoted QR, [2] Jacobi, [3] ordering, [4] new
+                                 factors; [6] sum of Jacobi column counts, [7] number of tasks */
     int64_t kernels_launched; /* kernels this handle launched since it was created */
     int32_t max_rank;         /* largest rank after the factorisation */
     int32_t max_stacked;      /* largest stacked-rank capacity of a rounded addition */

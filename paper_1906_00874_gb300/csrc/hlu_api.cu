@@ -38,9 +38,19 @@ struct DevPlan {
     int32_t n_tasks = 0, n_roots = 0, kc = 1;
     void *scratch = nullptr;
     int64_t scratch_stride = 0;
+    void *core_scratch = nullptr;  // cores of rounded additions above kSmemCore (global)
+    int64_t core_stride = 0;
     int workers = 0;
     size_t smem = 0;
 };
+
+// Profiling counters: [0, 32) task times and counts (see FlowArgs::busy), [32, 40)
+// rounded-addition phases (see LaunchArgs::phase).
+constexpr int kBusyWords = 40;
+
+// Largest stacked rank whose rounded-addition core the data-flow kernel keeps in
+// shared memory: sized so that two 256-thread workers fit on one SM.
+constexpr int kSmemCore = 64;
 
 struct Pending {
     int kind;
@@ -154,13 +164,19 @@ int upload_plan(hlu_ctx *h, const Plan &p, DevPlan &d, int kmax) {
     d.scratch_stride = (stride + 31) & ~int64_t(31);
     const int elem = h->precision == HLU_FP64 ? 8 : 4;
     const bool dbl = &d == &h->mp || h->precision == HLU_FP64;
-    d.smem = dataflow_smem_bytes(h->pl.max_leaf, dbl ? 8 : elem, kc);
+    d.smem = dataflow_smem_bytes(h->pl.max_leaf, dbl ? 8 : elem, std::min(kc, kSmemCore));
     d.workers = dbl ? dataflow_workers<double>(d.smem) : dataflow_workers<float>(d.smem);
     if (!p.radd.empty()) {
         const size_t bytes = size_t(d.workers) * d.scratch_stride * (dbl ? 8 : elem);
         char *sp = nullptr;
         if ((st = dalloc(h, &sp, bytes))) return st;
         d.scratch = sp;
+        if (kc > kSmemCore) {
+            d.core_stride = (int64_t)((radd_smem_bytes(kc) + 255) & ~size_t(255));
+            char *cp = nullptr;
+            if ((st = dalloc(h, &cp, size_t(d.workers) * d.core_stride))) return st;
+            d.core_scratch = cp;
+        }
     }
     return HLU_OK;
 }
@@ -209,6 +225,7 @@ void run_plan(hlu_ctx *h, const DevPlan &d, void *arena, double *flops) {
     a.err = h->err;
     a.eps = h->eps;
     a.flops = flops;
+    a.phase = (h->profiling && &d == &h->fp) ? h->busy + 32 : nullptr;
     a.kmax = h->pl.opt.kmax_core;
     const bool dbl = arena == (void *)h->aarena || h->precision == HLU_FP64;
     if (h->schedule == HLU_SCHED_DATAFLOW && d.n_tasks > 0) {
@@ -229,6 +246,9 @@ void run_plan(hlu_ctx *h, const DevPlan &d, void *arena, double *flops) {
         f.split = d.split;
         f.terms = d.terms;
         f.pieces = d.pieces;
+        f.smem_bytes = d.smem;
+        f.core_scratch = d.core_scratch;
+        f.core_stride = d.core_stride;
         f.scratch = d.scratch;
         f.scratch_stride = d.scratch_stride;
         f.timeout_ns = h->timeout_ns;
@@ -429,8 +449,9 @@ int hlu_create(const hlu_tree *tree, const hlu_blocks *blocks, const hlu_opts *o
     if (st == HLU_OK) st = upload(h, &h->kdyn, h->pl.slot_init);
     if (st == HLU_OK) st = dalloc(h, &h->err, 4);
     if (st == HLU_OK) st = dalloc(h, &h->flops, 16);
-    if (st == HLU_OK) st = dalloc(h, &h->busy, 16);
-    if (st == HLU_OK) st = cuda_status(cudaMemsetAsync(h->busy, 0, 16 * sizeof(unsigned long long), h->stream));
+    if (st == HLU_OK) st = dalloc(h, &h->busy, kBusyWords);
+    if (st == HLU_OK)
+        st = cuda_status(cudaMemsetAsync(h->busy, 0, kBusyWords * sizeof(unsigned long long), h->stream));
     if (st == HLU_OK) st = cuda_status(cudaMemsetAsync(h->flops, 0, 16 * sizeof(double), h->stream));
     if (st == HLU_OK) st = dalloc(h, &h->ir, 3 * n * w + 2 * w);
     if (st == HLU_OK) st = cuda_status(cudaMallocHost(reinterpret_cast<void **>(&h->ir_host), 2 * w * sizeof(double)));
@@ -679,11 +700,14 @@ int hlu_get_stats(hlu_t h, hlu_stats *o) {
         o->model_flops += fl[k];
         o->solve_flops += fl[8 + k];
     }
-    unsigned long long bz[16];
+    unsigned long long bz[kBusyWords];
     if (cudaMemcpy(bz, h->busy, sizeof(bz), cudaMemcpyDeviceToHost) != cudaSuccess) return HLU_ECUDA;
     for (int k = 0; k < 8; ++k) {
         o->task_busy_ms[k] = bz[k] * 1e-6;
         o->task_count[k] = (int64_t)bz[8 + k];
+        o->radd_busy_ms[k] = bz[16 + k] * 1e-6;
+        o->radd_count[k] = (int64_t)bz[24 + k];
+        o->radd_phase[k] = k < 6 ? bz[32 + k] * 1e-6 : (double)bz[32 + k];
     }
     if (h->factored) {
         std::vector<int32_t> kd(h->pl.n_slots);
@@ -703,7 +727,7 @@ int hlu_set_profiling(hlu_t h, int32_t on) {
         h->prof_ms[k] = 0.0;
         h->prof_count[k] = 0;
     }
-    if (cudaMemset(h->busy, 0, 16 * sizeof(unsigned long long)) != cudaSuccess) return HLU_ECUDA;
+    if (cudaMemset(h->busy, 0, kBusyWords * sizeof(unsigned long long)) != cudaSuccess) return HLU_ECUDA;
     return HLU_OK;
 }
 

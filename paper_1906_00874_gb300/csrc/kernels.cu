@@ -32,6 +32,16 @@ __device__ void set_error(long long *err, int code, long long index, double valu
     atomicAdd((unsigned long long *)(err + 3), 1ull);
 }
 
+// Profiling of rounded-addition phases (only when a.phase is set): thread 0
+// adds the time since `t` to slot `s` and returns the new time stamp.
+__device__ __forceinline__ unsigned long long phase_mark(const LaunchArgs &a, int s, unsigned long long t) {
+    if (!a.phase || threadIdx.x != 0) return 0ull;
+    unsigned long long now;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+    if (t) atomicAdd(a.phase + s, now - t);
+    return now;
+}
+
 // Model flop counts (standard operation counts, Golub and Van Loan).
 __device__ __forceinline__ void add_flops(const LaunchArgs &a, int kind, double f) {
     if (a.flops && f > 0.0) atomicAdd(a.flops + kind, f);
@@ -40,6 +50,14 @@ __device__ __forceinline__ void add_flops(const LaunchArgs &a, int kind, double 
 __device__ __forceinline__ double qr_model_flops(double m, double K) {
     const double hi = m > K ? m : K, lo = m > K ? K : m;
     return 2.0 * hi * lo * lo - 2.0 * lo * lo * lo / 3.0;
+}
+
+// Model flops of one rounded addition (the oracle's count, whichever route the
+// kernel takes): QR of both stacks, Jacobi SVD of the K x K core, Q times the
+// kept vectors.
+__device__ __forceinline__ double radd_model_flops(int m, int n, int K, int knew) {
+    const double ku = m < K ? m : K, kv = n < K ? n : K, kb = ku > kv ? ku : kv;
+    return qr_model_flops(m, K) + qr_model_flops(n, K) + 21.0 * kb * kb * kb + 2.0 * (m * ku + n * kv) * knew;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -344,11 +362,15 @@ __device__ void block_apply_q(const T *W, int m, int kk, const double *tau, T *Z
 // One-sided (Hestenes) Jacobi on the columns of M (ku x kv, double, shared):
 // M J = B with orthogonal columns; the singular values are the column norms of
 // B, the right singular vectors the columns of J.  Round-robin ordering, one
-// warp per column pair, sweeps until every pair is orthogonal to 1e-15.
+// warp per column pair.  A pair is rotated while |x.y| > tol |x||y| with
+// tol = 4 ku eps_double, the rounding level of the dot product itself (a
+// smaller tolerance is never met reliably and only burns sweeps); at most 30
+// sweeps.
 __device__ void block_jacobi(double *M, int ku, int kv, double *J, int *flag) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int np = (kv + 1) & ~1;
-    for (int sweep = 0; sweep < 40; ++sweep) {
+    const double tol = 4.0 * ku * DBL_EPSILON;
+    for (int sweep = 0; sweep < 30; ++sweep) {
         if (threadIdx.x == 0) *flag = 0;
         __syncthreads();
         for (int r = 0; r < np - 1; ++r) {
@@ -378,7 +400,7 @@ __device__ void block_jacobi(double *M, int ku, int kv, double *J, int *flag) {
                 aa = warp_sum(aa);
                 bb = warp_sum(bb);
                 gg = warp_sum(gg);
-                if (gg == 0.0 || !(fabs(gg) > 1e-15 * sqrt(aa * bb))) continue;
+                if (gg == 0.0 || !(fabs(gg) > tol * sqrt(aa * bb))) continue;
                 if (lane == 0) *flag = 1;
                 const double zeta = (bb - aa) / (2.0 * gg);
                 const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
@@ -404,9 +426,12 @@ __device__ void block_jacobi(double *M, int ku, int kv, double *J, int *flag) {
     }
 }
 
-size_t radd_smem_bytes(int kc) {
-    return sizeof(double) * (3 * (size_t)kc * kc + 5 * (size_t)kc + 40) + sizeof(int) * (2 * (size_t)kc + 8);
+// FP64 core buffers of a rounded addition with stacked rank K (see dev_radd).
+__host__ __device__ size_t radd_core_bytes(int K) {
+    return sizeof(double) * (3 * (size_t)K * K + 5 * (size_t)K + 40) + sizeof(int) * (2 * (size_t)K + 8);
 }
+
+size_t radd_smem_bytes(int kc) { return radd_core_bytes(kc); }
 
 // QR with column pivoting of the ku x kv core M (double, shared memory, column
 // major), stopped at the first step whose largest remaining column norm is at
@@ -424,10 +449,12 @@ __device__ int block_qrcp(double *M, int ku, int kv, double *tau, double *cn, in
         perm[j] = j;
     }
     __syncthreads();
-    double n0 = 0.0;
+    double n0 = 0.0;  // first pivot norm (kept by warp 0)
     int r = 0;
     const int kk = min(ku, kv);
     for (int j = 0; j < kk; ++j) {
+        double *x = M + (size_t)j * ku;
+        // warp 0: pivot, stopping test, column swap and reflector; one barrier
         if (warp == 0) {
             double bv = -1.0;
             int bi = j;
@@ -444,53 +471,47 @@ __device__ int block_qrcp(double *M, int ku, int kv, double *tau, double *cn, in
                     bi = oi;
                 }
             }
-            if (lane == 0) {
-                iflag[1] = bi;
-                red[36] = bv;
-            }
-        }
-        __syncthreads();
-        const int p = iflag[1];
-        const double pv = red[36];
-        if (j == 0) n0 = pv;
-        if (!(pv > delta * delta * n0)) break;
-        __syncthreads();
-        if (p != j) {
-            for (int i = threadIdx.x; i < ku; i += blockDim.x) {
-                const double tmp = M[i + (size_t)j * ku];
-                M[i + (size_t)j * ku] = M[i + (size_t)p * ku];
-                M[i + (size_t)p * ku] = tmp;
-            }
-            if (threadIdx.x == 0) {
-                const double tc = cn[j];
-                cn[j] = cn[p];
-                cn[p] = tc;
-                const int tp = perm[j];
-                perm[j] = perm[p];
-                perm[p] = tp;
-            }
-        }
-        __syncthreads();
-        double *x = M + (size_t)j * ku;
-        if (warp == 0) {
-            double s = 0.0;
-            for (int i = j + lane; i < ku; i += 32) s += x[i] * x[i];
-            s = warp_sum(s);
-            const double x0 = x[j];
-            const double nrm = sqrt(s);
-            double tj = 0.0;
-            __syncwarp();
-            if (nrm > 0.0) {
-                const double alpha = x0 >= 0.0 ? -nrm : nrm;
-                const double v0 = x0 - alpha;
-                for (int i = j + 1 + lane; i < ku; i += 32) x[i] /= v0;
-                tj = (alpha - x0) / alpha;
+            if (j == 0) n0 = bv;
+            const bool stop = !(bv > delta * delta * n0);
+            if (lane == 0) iflag[1] = stop ? -1 : bi;
+            if (!stop) {
+                const int p = bi;
+                if (p != j) {
+                    for (int i = lane; i < ku; i += 32) {
+                        const double tmp = x[i];
+                        x[i] = M[i + (size_t)p * ku];
+                        M[i + (size_t)p * ku] = tmp;
+                    }
+                    if (lane == 0) {
+                        const double tc = cn[j];
+                        cn[j] = cn[p];
+                        cn[p] = tc;
+                        const int tp = perm[j];
+                        perm[j] = perm[p];
+                        perm[p] = tp;
+                    }
+                    __syncwarp();
+                }
+                double s = 0.0;
+                for (int i = j + lane; i < ku; i += 32) s += x[i] * x[i];
+                s = warp_sum(s);
+                const double x0 = x[j];
+                const double nrm = sqrt(s);
+                double tj = 0.0;
                 __syncwarp();
-                if (lane == 0) x[j] = alpha;
+                if (nrm > 0.0) {
+                    const double alpha = x0 >= 0.0 ? -nrm : nrm;
+                    const double v0 = x0 - alpha;
+                    for (int i = j + 1 + lane; i < ku; i += 32) x[i] /= v0;
+                    tj = (alpha - x0) / alpha;
+                    __syncwarp();
+                    if (lane == 0) x[j] = alpha;
+                }
+                if (lane == 0) tau[j] = tj;
             }
-            if (lane == 0) tau[j] = tj;
         }
         __syncthreads();
+        if (iflag[1] < 0) break;  // uniform: every thread reads the same flag
         const double tj = tau[j];
         for (int c = j + 1 + warp; c < kv; c += nw) {
             double *y = M + (size_t)c * ku;
@@ -542,9 +563,131 @@ __device__ void block_apply_qcp(const double *M, int ku, int r, const double *ta
 // followed by one-sided Jacobi on R'^T gives M = X Sigma Y^T with X = Q_M [J; 0]
 // and Y = P W Sigma^{-1}; singular values sigma_i <= eps sigma_1 are dropped and
 // the new factors are U = Q_u [X Sigma; 0], V = Q_v [Y; 0].
+//
+// Shared memory is carved by the task's own stacked rank K: the FP64 core
+// buffers first (radd_smem_bytes(K)), then, when they fit in the rest of the
+// CTA's `smem_bytes`, the stacked panels themselves; larger panels stay in
+// the global `scratch`.  The pivoted QR of the core stops at delta times the
+// first pivot: 1e-13 for FP64 factors (double rounding level) and 1e-6 for
+// FP32 factors (an order above the FP32 rounding of the stacked panels, two
+// below the relative tolerances eps the method uses).
+// Small targets (m n <= kSmallTarget, m, n <= 128): the sum X = U_c V_c^T + sum_i c_i U_i V_i^T
+// is formed densely (in the factor precision) and its truncated SVD is taken
+// directly - pivoted QR of X (double) and one-sided Jacobi on the reduced
+// factor - which is the same T_eps of the same sum without the two stacked
+// QRs.  Returns false (before touching anything) when X and its buffers do
+// not fit in `smem_bytes`.
+constexpr int kSmallTarget = 4096;
+
+template <class T>
+__device__ bool radd_small(const TRadd &t, const Piece *pieces, const LaunchArgs &a, int kself,
+                           unsigned char *smem_raw, size_t smem_bytes, double delta) {
+    const int m = t.m, n = t.n, mn = min(m, n), mx = max(m, n);
+    const size_t need = sizeof(double) * ((size_t)m * n + (size_t)mx * mn + (size_t)mn * mn + 2 * mn + n + 40) +
+                        sizeof(int) * ((size_t)mn + n + 8);
+    // every launch provides radd_smem_bytes(64) >= the largest `need` of a target
+    // with m n <= kSmallTarget and m, n <= 128 (100704 bytes at m = n = 64), so
+    // the choice depends on the task alone
+    if ((int64_t)m * n > kSmallTarget || mx > 128 || need > smem_bytes) return false;
+    T *A = reinterpret_cast<T *>(a.arena);
+    int32_t *kd = a.kdyn;
+    double *X = reinterpret_cast<double *>(smem_raw);
+    double *C = X + (size_t)m * n;  // n x r, later m x knew
+    double *J = C + (size_t)mx * mn;
+    double *tau = J + (size_t)mn * mn;
+    double *sig = tau + mn;
+    double *cn = sig + mn;
+    double *red = cn + n;
+    int *order = reinterpret_cast<int *>(red + 40);
+    int *perm = order + mn;
+    int *iflag = perm + n;
+    unsigned long long ph = phase_mark(a, 0, 0ull);
+    // ---- X = U_c V_c^T + sum of the zero-padded contributions
+    for (int e = threadIdx.x; e < m * n; e += blockDim.x) {
+        const int i = e % m, j = e / m;
+        T acc = T(0);
+        for (int c = 0; c < kself; ++c) acc += A[t.U_off + i + (int64_t)c * m] * A[t.V_off + j + (int64_t)c * n];
+        for (int q = 0; q < t.npieces; ++q) {
+            const Piece &pc = pieces[t.piece0 + q];
+            const int ii = i - pc.roff, jj = j - pc.coff;
+            if (ii < 0 || ii >= pc.U.rows || jj < 0 || jj >= pc.V.rows) continue;
+            const int k = dim_c(pc.U, kd);
+            T s = T(0);
+            for (int l = 0; l < k; ++l) s += at(A, pc.U, ii, l) * at(A, pc.V, jj, l);
+            acc += T(pc.coef) * s;
+        }
+        X[e] = (double)acc;
+    }
+    __syncthreads();
+    ph = phase_mark(a, 0, ph);
+    // ---- X P = Q [R'; ~0], one-sided Jacobi on C = R'^T (n x r)
+    const int r = block_qrcp(X, m, n, tau, cn, perm, delta, red, iflag);
+    ph = phase_mark(a, 1, ph);
+    for (int e = threadIdx.x; e < n * r; e += blockDim.x) {
+        const int c = e % n, i = e / n;
+        C[e] = c >= i ? X[i + (size_t)c * m] : 0.0;
+    }
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) J[e] = (e % r == e / r) ? 1.0 : 0.0;
+    __syncthreads();
+    block_jacobi(C, n, r, J, iflag);
+    ph = phase_mark(a, 2, ph);
+    for (int j = threadIdx.x; j < r; j += blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += C[i + (size_t)j * n] * C[i + (size_t)j * n];
+        sig[j] = sqrt(s);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < r; j += blockDim.x) {
+        int rk = 0;
+        for (int l = 0; l < r; ++l) rk += (sig[l] > sig[j]) || (sig[l] == sig[j] && l < j);
+        order[rk] = j;
+    }
+    __syncthreads();
+    const double s1 = r > 0 ? sig[order[0]] : 0.0;
+    int knew = 0;
+    if (!isfinite(s1)) {
+        if (threadIdx.x == 0) set_error(a.err, DE_NONFINITE, t.target, s1);
+    } else if (s1 > 0.0) {
+        for (int l = 0; l < r; ++l) knew += sig[order[l]] > a.eps * s1;
+    }
+    if (knew > t.cap) {
+        if (threadIdx.x == 0) set_error(a.err, DE_RANKCAP, t.target, (double)knew);
+        knew = t.cap;
+    }
+    ph = phase_mark(a, 3, ph);
+    if (a.phase && threadIdx.x == 0) {  // Jacobi problem size: columns, rows
+        atomicAdd(a.phase + 6, (unsigned long long)r);
+        atomicAdd(a.phase + 7, 1ull);
+    }
+    // ---- V = P W_sel Sigma^{-1} (every row of V is covered by the permutation)
+    T *Uc = A + t.U_off;
+    T *Vc = A + t.V_off;
+    for (int e = threadIdx.x; e < n * knew; e += blockDim.x) {
+        const int i = e % n, c = e / n;
+        const int j = order[c];
+        Vc[perm[i] + (int64_t)c * n] = T(C[i + (size_t)j * n] / sig[j]);
+    }
+    __syncthreads();
+    // ---- U = Q [J_sel Sigma; 0] (C reused for the m x knew product)
+    for (int e = threadIdx.x; e < m * knew; e += blockDim.x) {
+        const int i = e % m, c = e / m;
+        const int j = order[c];
+        C[e] = i < r ? J[i + (size_t)j * r] * sig[j] : 0.0;
+    }
+    __syncthreads();
+    block_apply_qcp(X, m, r, tau, C, knew);
+    __syncthreads();
+    for (int e = threadIdx.x; e < m * knew; e += blockDim.x) Uc[e] = T(C[e]);
+    if (threadIdx.x == 0) kd[t.kslot] = knew;
+    phase_mark(a, 4, ph);
+    return true;
+}
+
+// When even the core does not fit (K above the CTA's shared-memory capacity),
+// it is placed in `core_scratch` (global, radd_core_bytes(K) bytes).
 template <class T>
 __device__ void dev_radd(const TRadd &t, const Piece *pieces, const LaunchArgs &a, int kc, unsigned char *smem_raw,
-                         T *scratch) {
+                         T *scratch, size_t smem_bytes, unsigned char *core_scratch) {
     T *A = reinterpret_cast<T *>(a.arena);
     int32_t *kd = a.kdyn;
     const int m = t.m, n = t.n;
@@ -552,7 +695,7 @@ __device__ void dev_radd(const TRadd &t, const Piece *pieces, const LaunchArgs &
     int K = kself;
     for (int q = 0; q < t.npieces; ++q) K += dim_c(pieces[t.piece0 + q].U, kd);
     __syncthreads();  // every thread has read the target's rank before it is rewritten
-    if (K > kc || K > t.Kcap) {
+    if (K > t.Kcap) {
         if (threadIdx.x == 0) set_error(a.err, DE_RANKCAP, t.target, (double)K);
         return;
     }
@@ -560,20 +703,33 @@ __device__ void dev_radd(const TRadd &t, const Piece *pieces, const LaunchArgs &
         if (threadIdx.x == 0) kd[t.kslot] = 0;
         return;
     }
-    double *M = reinterpret_cast<double *>(smem_raw);   // core, then QRCP reflectors
-    double *C = M + (size_t)kc * kc;                       // R'^T (kv x r), later Q_M [J Sigma; 0]
-    double *J = C + (size_t)kc * kc;                       // Jacobi rotations (r x r)
-    double *tauU = J + (size_t)kc * kc;
-    double *tauV = tauU + kc;
-    double *tauM = tauV + kc;
-    double *sig = tauM + kc;
-    double *cn = sig + kc;
-    double *red = cn + kc;  // 40 doubles
+    const double delta = sizeof(T) == 8 ? 1e-13 : 1e-6;
+    if (radd_small<T>(t, pieces, a, kself, smem_raw, smem_bytes, delta)) {
+        if (threadIdx.x == 0) add_flops(a, K_RADD, radd_model_flops(m, n, K, kd[t.kslot]));
+        return;
+    }
+    if (K > kc) {
+        if (threadIdx.x == 0) set_error(a.err, DE_RANKCAP, t.target, (double)K);
+        return;
+    }
+    const size_t core_bytes = (radd_core_bytes(K) + 15) & ~size_t(15);
+    const bool core_in_smem = core_bytes <= smem_bytes;
+    unsigned char *core = core_in_smem ? smem_raw : core_scratch;
+    double *M = reinterpret_cast<double *>(core);  // core, then QRCP reflectors
+    double *C = M + (size_t)K * K;                        // R'^T (kv x r), later Q_M [J Sigma; 0]
+    double *J = C + (size_t)K * K;                        // Jacobi rotations (r x r)
+    double *tauU = J + (size_t)K * K;
+    double *tauV = tauU + K;
+    double *tauM = tauV + K;
+    double *sig = tauM + K;
+    double *cn = sig + K;
+    double *red = cn + K;  // 40 doubles
     int *order = reinterpret_cast<int *>(red + 40);
-    int *perm = order + kc;
-    int *iflag = perm + kc;  // 8 ints
-
-    T *WU = scratch;
+    int *perm = order + K;
+    int *iflag = perm + K;  // 8 ints
+    const size_t panel_bytes = (size_t)(m + n) * K * sizeof(T);
+    T *WU = core_in_smem && core_bytes + panel_bytes <= smem_bytes ? reinterpret_cast<T *>(smem_raw + core_bytes)
+                                                                    : scratch;
     T *WV = WU + (int64_t)m * K;
     // ---- stack the factors
     for (int64_t e = threadIdx.x; e < (int64_t)(m + n) * K; e += blockDim.x) WU[e] = T(0);
@@ -609,7 +765,7 @@ __device__ void dev_radd(const TRadd &t, const Piece *pieces, const LaunchArgs &
     }
     __syncthreads();
     // ---- M P = Q_M [R'; ~0], then one-sided Jacobi on C = R'^T (kv x r)
-    const int r = block_qrcp(M, ku, kv, tauM, cn, perm, 1e-13, red, iflag);
+    const int r = block_qrcp(M, ku, kv, tauM, cn, perm, delta, red, iflag);
     for (int e = threadIdx.x; e < kv * r; e += blockDim.x) {
         const int c = e % kv, i = e / kv;
         C[e] = c >= i ? M[i + (size_t)c * ku] : 0.0;
@@ -670,9 +826,7 @@ __device__ void dev_radd(const TRadd &t, const Piece *pieces, const LaunchArgs &
     block_apply_q(WV, n, kv, tauV, Vc, knew);
     if (threadIdx.x == 0) {
         kd[t.kslot] = knew;
-        const double kb = ku > kv ? ku : kv;  // model: Jacobi SVD of the stacked core
-        add_flops(a, K_RADD, qr_model_flops(m, K) + qr_model_flops(n, K) + 21.0 * kb * kb * kb +
-                                 2.0 * ((double)m * ku + (double)n * kv) * knew);
+        add_flops(a, K_RADD, radd_model_flops(m, n, K, knew));
     }
 }
 
@@ -712,10 +866,11 @@ __global__ void __launch_bounds__(kThreads) k_split(const TSplit *tasks, LaunchA
 }
 
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_radd(const TRadd *tasks, const Piece *pieces, LaunchArgs a, int kc) {
+__global__ void __launch_bounds__(kThreads) k_radd(const TRadd *tasks, const Piece *pieces, LaunchArgs a, int kc,
+                                                   size_t smem_bytes) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const TRadd t = tasks[blockIdx.x];
-    dev_radd<T>(t, pieces, a, kc, smem_raw, reinterpret_cast<T *>(a.arena) + t.scratch_off);
+    dev_radd<T>(t, pieces, a, kc, smem_raw, reinterpret_cast<T *>(a.arena) + t.scratch_off, smem_bytes, nullptr);
 }
 
 // -------------------------------------------------------- data-flow kernel
@@ -801,7 +956,9 @@ __global__ void __launch_bounds__(kThreads) k_dataflow(FlowArgs f, LaunchArgs a)
             }
             case K_RADD: {
                 const TRadd t = f.radd[idx];
-                dev_radd<T>(t, f.pieces, a, f.kc, smem_raw, scratch);
+                dev_radd<T>(t, f.pieces, a, f.kc, smem_raw, scratch, f.smem_bytes,
+                            reinterpret_cast<unsigned char *>(f.core_scratch) +
+                                (int64_t)blockIdx.x * f.core_stride);
                 break;
             }
             case K_SPLIT: {
@@ -815,8 +972,16 @@ __global__ void __launch_bounds__(kThreads) k_dataflow(FlowArgs f, LaunchArgs a)
         __syncthreads();
         if (threadIdx.x == 0) {
             if (f.busy) {
-                atomicAdd(f.busy + kind, global_ns() - t_start);
+                const unsigned long long dt = global_ns() - t_start;
+                atomicAdd(f.busy + kind, dt);
                 atomicAdd(f.busy + 8 + kind, 1ull);
+                if (kind == K_RADD) {  // rounded additions by size m + n: < 128, < 256, ..., >= 8192
+                    const TRadd &t = f.radd[idx];
+                    int b = 0;
+                    for (int s = t.m + t.n; s >= 128 && b < 7; s >>= 1) ++b;
+                    atomicAdd(f.busy + 16 + b, dt);
+                    atomicAdd(f.busy + 24 + b, 1ull);
+                }
             }
             __threadfence();
             for (int e = f.succ_ptr[g]; e < f.succ_ptr[g + 1]; ++e) {
@@ -929,8 +1094,11 @@ void launch_kind(int kind, const void *tasks, const Term *terms, const Piece *pi
             k_accum<T><<<count, kThreads, 0, s>>>(reinterpret_cast<const TAccum *>(tasks) + start, terms, a);
             break;
         case K_RADD: {
-            k_radd<T><<<count, kThreads, radd_smem_bytes(aux), s>>>(reinterpret_cast<const TRadd *>(tasks) + start,
-                                                                    pieces, a, aux);
+            // at least the dense route's worst case (m n <= kSmallTarget) so that the
+            // route a task takes does not depend on the schedule
+            const size_t smem = std::max(radd_smem_bytes(aux), radd_smem_bytes(64));
+            k_radd<T><<<count, kThreads, smem, s>>>(reinterpret_cast<const TRadd *>(tasks) + start, pieces, a, aux,
+                                                    smem);
             break;
         }
         case K_SPLIT:

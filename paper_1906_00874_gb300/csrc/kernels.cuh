@@ -16,6 +16,7 @@ struct LaunchArgs {
     long long *err;     // error word: code, index, value bits, count
     double eps;         // truncation tolerance (rounded addition)
     double *flops;      // model flops per task kind (K_NKINDS doubles), accumulated
+    unsigned long long *phase;  // when profiling: nanoseconds per rounded-addition phase (8), else null
     int32_t kmax;       // largest stacked rank the core buffers hold
 };
 
@@ -41,10 +42,14 @@ struct FlowArgs {
     const TSplit *split;
     const Term *terms;
     const Piece *pieces;
+    size_t smem_bytes;         // dynamic shared memory of a worker
+    void *core_scratch;        // per-worker global space for rounded-addition cores too big for smem
+    int64_t core_stride;       // bytes per worker
     void *scratch;             // per-worker rounded-addition workspace (T elements)
     int64_t scratch_stride;    // elements per worker
     unsigned long long timeout_ns;  // limit of any single wait for a ready task
-    unsigned long long *busy;  // when profiling: [kind] task nanoseconds, [8 + kind] task count; else null
+    unsigned long long *busy;  // when profiling: [kind] task nanoseconds, [8 + kind] task count,
+                               // [16 + b] / [24 + b] the same for rounded additions of size class b; else null
 };
 
 size_t dataflow_smem_bytes(int max_leaf, int elem, int kc);

@@ -59,13 +59,22 @@ class Stats(ctypes.Structure):
                 ("flops_by_kind", ctypes.c_double * 8), ("solve_flops", ctypes.c_double),
                 ("kernel_ms", ctypes.c_double * 8), ("kernel_launches", ctypes.c_int64 * 8),
                 ("task_busy_ms", ctypes.c_double * 8), ("task_count", ctypes.c_int64 * 8),
+                ("radd_busy_ms", ctypes.c_double * 8), ("radd_count", ctypes.c_int64 * 8),
+                ("radd_phase", ctypes.c_double * 8),
                 ("kernels_launched", ctypes.c_int64), ("max_rank", ctypes.c_int32), ("max_stacked", ctypes.c_int32)]
 
     def as_dict(self):
         per_kind = ("tasks_by_kind", "flops_by_kind", "kernel_ms", "kernel_launches", "task_busy_ms", "task_count")
-        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in per_kind}
+        per_size = ("radd_busy_ms", "radd_count")
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in per_kind + per_size + ("radd_phase",)}
+        ph = list(self.radd_phase)
+        d["radd_phase"] = {"form_ms": ph[0], "qrcp_ms": ph[1], "jacobi_ms": ph[2], "order_ms": ph[3],
+                           "factors_ms": ph[4], "mean_jacobi_cols": ph[6] / max(ph[7], 1), "tasks": ph[7]}
         for f in per_kind:
             d[f] = dict(zip(KINDS, list(getattr(self, f))[:len(KINDS)]))
+        sizes = ("<128", "<256", "<512", "<1024", "<2048", "<4096", "<8192", ">=8192")
+        for f in per_size:
+            d[f] = dict(zip(sizes, list(getattr(self, f))))
         return d
 
 
