@@ -302,9 +302,9 @@ def run_native(args):
         # one persistent launch runs the whole factorisation task graph
         dom_flops = st32["model_flops"]
         kname = "k_dataflow<float> (factorisation)"
-    elif dom == "dataflow_solve":
-        dom_flops = st32["solve_flops"]
-        kname = "k_dataflow (solves and FP64 products)"
+    elif dom in ("dataflow_solve", "dataflow_matvec"):
+        dom_flops = st32["solve_flops"] * ms[dom] / max(1e-9, ms["dataflow_solve"] + ms["dataflow_matvec"])
+        kname = "k_dataflow<float> (H-solves)" if dom == "dataflow_solve" else "k_dataflow<double> (H-matvec)"
     else:
         dom_flops = st32["flops_by_kind"][dom]
         kname = f"k_{dom}<float>"
@@ -327,8 +327,9 @@ def run_native(args):
             "tasks_per_factor": {k: v // nprof for k, v in prof["task_count"].items() if v},
             "radd_busy_ms_by_size": {k: round(v / nprof, 1) for k, v in prof["radd_busy_ms"].items() if v},
             "radd_count_by_size": {k: v // nprof for k, v in prof["radd_count"].items() if v},
-            "radd_small_phases_per_factor": {k: (v / nprof if k != "mean_jacobi_cols" else v)
-                                             for k, v in prof["radd_phase"].items()}}
+            "radd_phases_per_factor": {route: {k: (v if k.startswith("mean_") else v / nprof)
+                                               for k, v in ph.items()}
+                                       for route, ph in prof["radd_phase"].items()}}
 
     cpu = None
     if rank == 0:

@@ -30,7 +30,8 @@ extern "C" {
 enum {
     HLU_OK = 0,
     HLU_EINVAL = 1,    /* malformed tree, leaves not tiling [0,n)^2, low-rank diagonal
-                          block, rank > min(m,n), non-finite input, bad argument */
+                          block, rank > min(m,n), leaf cluster above 128 indices,
+                          non-finite input, bad argument */
     HLU_ENOMEM = 2,    /* cudaMalloc failed or the plan exceeds opts.mem_budget */
     HLU_ESTATE = 3,    /* call out of order (solve before factor, factor twice) */
     HLU_EPIVOT = 4,    /* zero or non-finite pivot u_kk in a dense diagonal leaf */
@@ -163,18 +164,24 @@ typedef struct {
     double model_flops;       /* model flops of the last hlu_factor */
     double flops_by_kind[8];  /* the same, per task kind */
     double solve_flops;       /* model flops of solves and products since the last hlu_factor */
-    double kernel_ms[8];      /* with profiling on: summed kernel time per task kind; slots 6 / 7
-                                 hold the data-flow launches of factorisations / of solves */
-    int64_t kernel_launches[8];
+    double kernel_ms[10];     /* with profiling on: summed kernel time per task kind; slots 6 / 7 / 8
+                                 hold the data-flow launches of factorisations / of solves / of
+                                 H-matrix products */
+    int64_t kernel_launches[10];
     double task_busy_ms[8];   /* with profiling on, data-flow factorisations: summed time of the
                                  tasks of each kind (concurrent tasks add up) */
     int64_t task_count[8];
     double radd_busy_ms[8];   /* the same for rounded additions by target size m + n:
                                  < 128, < 256, < 512, ..., >= 8192 */
     int64_t radd_count[8];
-    double radd_phase[8];     /* small-target rounded additions, summed ms per phase: [0] sum
-                                 formation, [1] pivoted QR, [2] Jacobi, [3] ordering, [4] new
-                                 factors; [6] sum of Jacobi column counts, [7] number of tasks */
+    double solve_busy_ms[8];  /* with profiling on, data-flow solves: summed task time per kind */
+    int64_t solve_task_count[8];
+    double radd_phase[16];    /* rounded additions, summed ms per phase; [0, 8) dense route
+                                 (small targets), [8, 16) stacked route: [0] sum formation or
+                                 stacking, [1] QR of the stacks and core product, [2] pivoted
+                                 QR of the core, [3] Jacobi SVD and truncation, [5] new
+                                 factors; counts: [4] Jacobi sweeps, [6] Jacobi sizes r,
+                                 [7] tasks */
     int64_t kernels_launched; /* kernels this handle launched since it was created */
     int32_t max_rank;         /* largest rank after the factorisation */
     int32_t max_stacked;      /* largest stacked-rank capacity of a rounded addition */

@@ -44,9 +44,13 @@ struct DevPlan {
     size_t smem = 0;
 };
 
-// Profiling counters: [0, 32) task times and counts (see FlowArgs::busy), [32, 40)
-// rounded-addition phases (see LaunchArgs::phase).
-constexpr int kBusyWords = 40;
+// Profiling counters: [0, 32) task times and counts of factorisations (see
+// FlowArgs::busy), [32, 48) rounded-addition phases (see LaunchArgs::phase),
+// [48, 64) task times and counts of solves.
+constexpr int kBusyWords = 64;
+// Launch-time slots: task kinds (wave schedule), then the data-flow launches of
+// factorisations, solves and H-matrix products.
+constexpr int kProfSlots = 10;
 
 // Largest stacked rank whose rounded-addition core the data-flow kernel keeps in
 // shared memory: sized so that two 256-thread workers fit on one SM.
@@ -86,8 +90,8 @@ struct hlu_ctx {
     bool profiling = false;
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> free_events;
-    double prof_ms[8] = {0};
-    int64_t prof_count[8] = {0};
+    double prof_ms[kProfSlots] = {0};
+    int64_t prof_count[kProfSlots] = {0};
     int64_t kernels_launched = 0;
     cudaError_t last_cuda = cudaSuccess;
     unsigned long long *busy = nullptr;  // per-kind task time inside the data-flow kernel (profiling)
@@ -172,7 +176,7 @@ int upload_plan(hlu_ctx *h, const Plan &p, DevPlan &d, int kmax) {
         if ((st = dalloc(h, &sp, bytes))) return st;
         d.scratch = sp;
         if (kc > kSmemCore) {
-            d.core_stride = (int64_t)((radd_smem_bytes(kc) + 255) & ~size_t(255));
+            d.core_stride = (int64_t)((radd_smem_bytes(kc, dbl ? 8 : elem) + 255) & ~size_t(255));
             char *cp = nullptr;
             if ((st = dalloc(h, &cp, size_t(d.workers) * d.core_stride))) return st;
             d.core_scratch = cp;
@@ -252,14 +256,14 @@ void run_plan(hlu_ctx *h, const DevPlan &d, void *arena, double *flops) {
         f.scratch = d.scratch;
         f.scratch_stride = d.scratch_stride;
         f.timeout_ns = h->timeout_ns;
-        f.busy = (h->profiling && &d == &h->fp) ? h->busy : nullptr;
+        f.busy = !h->profiling ? nullptr : &d == &h->fp ? h->busy : &d == &h->sp ? h->busy + 48 : nullptr;
         cudaMemcpyAsync(d.indeg, d.indeg0, sizeof(int32_t) * d.n_tasks, cudaMemcpyDeviceToDevice, h->stream);
         cudaMemsetAsync(d.queue, 0xff, sizeof(int32_t) * d.n_tasks, h->stream);
         cudaMemcpyAsync(d.queue, d.roots, sizeof(int32_t) * d.n_roots, cudaMemcpyDeviceToDevice, h->stream);
         cudaMemsetAsync(d.counters, 0, 2 * sizeof(int32_t), h->stream);
         launch_set_slot(d.counters, 1, d.n_roots, h->stream);
-        // profiling slots 6 / 7: the data-flow launch of a factorisation / of a solve or product
-        Pending pe{&d == &h->fp ? K_NKINDS : K_NKINDS + 1, nullptr, nullptr};
+        // profiling slots 6 / 7 / 8: the data-flow launch of a factorisation / a solve / a product
+        Pending pe{&d == &h->fp ? K_NKINDS : &d == &h->sp ? K_NKINDS + 1 : K_NKINDS + 2, nullptr, nullptr};
         if (h->profiling) {
             pe.e0 = take_event(h);
             pe.e1 = take_event(h);
@@ -688,7 +692,7 @@ int hlu_get_stats(hlu_t h, hlu_stats *o) {
     o->tasks_by_kind[5] = (int64_t)f.split.size();
     o->max_stacked = f.max_kcap;
     o->kernels_launched = h->kernels_launched;
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < kProfSlots; ++k) {
         o->kernel_ms[k] = h->prof_ms[k];
         o->kernel_launches[k] = h->prof_count[k];
     }
@@ -707,7 +711,12 @@ int hlu_get_stats(hlu_t h, hlu_stats *o) {
         o->task_count[k] = (int64_t)bz[8 + k];
         o->radd_busy_ms[k] = bz[16 + k] * 1e-6;
         o->radd_count[k] = (int64_t)bz[24 + k];
-        o->radd_phase[k] = k < 6 ? bz[32 + k] * 1e-6 : (double)bz[32 + k];
+        o->solve_busy_ms[k] = bz[48 + k] * 1e-6;
+        o->solve_task_count[k] = (int64_t)bz[56 + k];
+    }
+    for (int k = 0; k < 16; ++k) {
+        const int s = k & 7;
+        o->radd_phase[k] = (s == 4 || s >= 6) ? (double)bz[32 + k] : bz[32 + k] * 1e-6;
     }
     if (h->factored) {
         std::vector<int32_t> kd(h->pl.n_slots);
@@ -723,7 +732,7 @@ int hlu_set_profiling(hlu_t h, int32_t on) {
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return HLU_ECUDA;
     collect_profile(h);
     h->profiling = on != 0;
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < kProfSlots; ++k) {
         h->prof_ms[k] = 0.0;
         h->prof_count[k] = 0;
     }

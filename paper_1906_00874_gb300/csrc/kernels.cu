@@ -1,7 +1,8 @@
 // Device kernels of the H-LU task graph (sm_103a).  One CTA (256 threads)
 // executes one task; the launch of a wave passes the slice of the task array
 // that belongs to it.  T is the storage type of the factors (double or
-// float); the core of every rounded addition is always computed in double.
+// float); the Jacobi SVD inside every rounded addition is always computed in
+// double.
 #include <cuda_runtime.h>
 #include <float.h>
 #include <math.h>
@@ -13,8 +14,6 @@
 namespace hlu {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kMaxLeaf = 128;        // largest dense diagonal leaf (4 rows per lane)
-constexpr int kRowsPerLane = kMaxLeaf / 32;
 
 __device__ __forceinline__ int dim_r(const Panel &p, const int32_t *kd) { return p.rslot >= 0 ? kd[p.rslot] : p.rows; }
 __device__ __forceinline__ int dim_c(const Panel &p, const int32_t *kd) { return p.cslot >= 0 ? kd[p.cslot] : p.cols; }
@@ -65,20 +64,17 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Sum over the CTA; `red` holds >= 33 doubles of shared memory.
-__device__ double block_sum(double v, double *red) {
-    v = warp_sum(v);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
-    __syncthreads();
-    if (l == 0) red[w] = v;
-    __syncthreads();
-    if (w == 0) {
-        double s = l < nw ? red[l] : 0.0;
-        s = warp_sum(s);
-        if (l == 0) red[32] = s;
-    }
-    __syncthreads();
-    return red[32];
+template <class R>
+__device__ __forceinline__ R warp_sum_t(R v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Cooperative copy of n elements: element e is read by src(e) and written by
+// dst(e, v), one element per thread and step.
+template <class T, class Src, class Dst>
+__device__ __forceinline__ void block_copy(int n, Src src, Dst dst) {
+    for (int e = threadIdx.x; e < n; e += blockDim.x) dst(e, src(e));
 }
 
 // ------------------------------------------------------------------ GETRF
@@ -89,7 +85,7 @@ __device__ void dev_getrf(const TGetrf &t, const LaunchArgs &a, unsigned char *s
     T *s = reinterpret_cast<T *>(smem_raw);
     const int m = t.m;
     T *g = reinterpret_cast<T *>(a.arena) + t.off;
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) s[e] = g[e];
+    block_copy<T>(m * m, [&](int e) { return g[e]; }, [&](int e, T v) { s[e] = v; });
     __syncthreads();
     for (int k = 0; k < m; ++k) {
         const T piv = s[k + k * m];
@@ -109,156 +105,352 @@ __device__ void dev_getrf(const TGetrf &t, const LaunchArgs &a, unsigned char *s
 }
 
 // ------------------------------------------------------------------- TRSM
-// Triangular solve of a panel with a dense diagonal leaf; one warp per panel
-// column, the column held in registers (rows lane + 32 r), the triangle in
-// shared memory laid out so that lane accesses are contiguous.
-template <class T>
-__device__ void dev_trsm(const TTrsm &t, const LaunchArgs &a, unsigned char *smem_raw) {
-    T *L = reinterpret_cast<T *>(smem_raw);
-    const int m = t.m;
-    const T *g = reinterpret_cast<const T *>(a.arena) + t.L_off;
-    if (t.mode == TR_UPPER_TRANS) {
-        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-            const int i = e % m, j = e / m;
-            L[j + i * m] = g[e];  // L = U^T
+// Triangular solve of an m x p panel with a dense diagonal leaf (m <= 128).
+// The triangle is staged in shared memory (transposed for TR_UPPER_TRANS, so
+// that every mode reads a column of L per step) with the reciprocals of its
+// diagonal (ones for the unit lower factor).  Every panel column is solved by
+// a group of 16 lanes, each holding R rows (lane + 16 r) in registers, 16
+// columns at a time; the steps i are fully unrolled, so that the lane that
+// owns x_i and the rows a step updates are known at compile time: step i
+// scales x_i by the reciprocal pivot, broadcasts it within the group and
+// subtracts its multiple of column i from the rows below (forward) or above
+// (backward) it.
+constexpr int kTrsmSlack = 128;  // zeroed elements after the triangle (reads past the last column)
+
+size_t trsm_smem_bytes(int max_leaf, int elem) {
+    return (size_t)(max_leaf * max_leaf + kTrsmSlack + max_leaf) * elem;
+}
+
+template <class T, int R>
+__device__ __forceinline__ void trsm_group16(const T *L, const T *dinv, T *A, const Panel &P, int m, int p,
+                                             bool forward) {
+    constexpr int GS = 16;
+    const int lane = threadIdx.x & (GS - 1), grp = threadIdx.x / GS, per_pass = blockDim.x / GS;
+    for (int c0 = 0; c0 < p; c0 += per_pass) {
+        const int c = c0 + grp;
+        const bool live = c < p;  // dead groups still take part in the shuffles
+        T *col_p = A + P.off + (int64_t)(live ? c : 0) * P.cs;
+        T x[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int row = lane + GS * r;
+            x[r] = (live && row < m) ? col_p[(int64_t)row * P.rs] : T(0);
         }
-    } else {
-        for (int e = threadIdx.x; e < m * m; e += blockDim.x) L[e] = g[e];
-    }
-    __syncthreads();
-    T *A = reinterpret_cast<T *>(a.arena);
-    const int p = dim_c(t.P, a.kdyn);
-    if (threadIdx.x == 0) add_flops(a, K_TRSM, (double)m * m * p);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int c = warp; c < p; c += nw) {
-        T x[kRowsPerLane];
+        if (forward) {
 #pragma unroll
-        for (int r = 0; r < kRowsPerLane; ++r) {
-            const int row = lane + 32 * r;
-            x[r] = row < m ? at(A, t.P, row, c) : T(0);
+            for (int ri = 0; ri < R; ++ri)
+#pragma unroll
+                for (int li = 0; li < GS; ++li) {
+                    const int i = ri * GS + li;
+                    if (i < m) {
+                        if (lane == li) x[ri] *= dinv[i];
+                        const T xi = __shfl_sync(kFull, x[ri], li, GS);
+                        const T *col = L + i * m + lane;
+                        if (lane > li) x[ri] -= col[GS * ri] * xi;
+#pragma unroll
+                        for (int r = ri + 1; r < R; ++r) x[r] -= col[GS * r] * xi;
+                    }
+                }
+        } else {
+#pragma unroll
+            for (int ri = R - 1; ri >= 0; --ri)
+#pragma unroll
+                for (int li = GS - 1; li >= 0; --li) {
+                    const int i = ri * GS + li;
+                    if (i < m) {
+                        if (lane == li) x[ri] *= dinv[i];
+                        const T xi = __shfl_sync(kFull, x[ri], li, GS);
+                        const T *col = L + i * m + lane;
+                        if (lane < li) x[ri] -= col[GS * ri] * xi;
+#pragma unroll
+                        for (int r = 0; r < ri; ++r) x[r] -= col[GS * r] * xi;
+                    }
+                }
         }
-        if (t.mode == TR_LOWER_UNIT || t.mode == TR_UPPER_TRANS) {
-            const bool unit = t.mode == TR_LOWER_UNIT;
-            for (int i = 0; i < m; ++i) {
-                const int ri = i >> 5, li = i & 31;
-                if (!unit && lane == li) {
+        if (live) {
 #pragma unroll
-                    for (int r = 0; r < kRowsPerLane; ++r)
-                        if (r == ri) x[r] /= L[i + i * m];
-                }
-                T xv = 0;
-#pragma unroll
-                for (int r = 0; r < kRowsPerLane; ++r)
-                    if (r == ri) xv = x[r];
-                const T xi = __shfl_sync(kFull, xv, li);
-#pragma unroll
-                for (int r = 0; r < kRowsPerLane; ++r) {
-                    const int row = lane + 32 * r;
-                    if (row > i && row < m) x[r] -= L[row + i * m] * xi;
-                }
+            for (int r = 0; r < R; ++r) {
+                const int row = lane + GS * r;
+                if (row < m) col_p[(int64_t)row * P.rs] = x[r];
             }
-        } else {  // TR_UPPER: backward substitution
-            for (int i = m - 1; i >= 0; --i) {
-                const int ri = i >> 5, li = i & 31;
-                if (lane == li) {
-#pragma unroll
-                    for (int r = 0; r < kRowsPerLane; ++r)
-                        if (r == ri) x[r] /= L[i + i * m];
-                }
-                T xv = 0;
-#pragma unroll
-                for (int r = 0; r < kRowsPerLane; ++r)
-                    if (r == ri) xv = x[r];
-                const T xi = __shfl_sync(kFull, xv, li);
-#pragma unroll
-                for (int r = 0; r < kRowsPerLane; ++r) {
-                    const int row = lane + 32 * r;
-                    if (row < i) x[r] -= L[row + i * m] * xi;
-                }
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < kRowsPerLane; ++r) {
-            const int row = lane + 32 * r;
-            if (row < m) at(A, t.P, row, c) = x[r];
         }
     }
 }
 
+template <class T>
+__device__ void dev_trsm(const TTrsm &t, const LaunchArgs &a, unsigned char *smem_raw) {
+    const int m = t.m, mm = m * m;
+    T *L = reinterpret_cast<T *>(smem_raw);
+    T *dinv = L + mm + kTrsmSlack;
+    const T *g = reinterpret_cast<const T *>(a.arena) + t.L_off;
+    if (t.mode == TR_UPPER_TRANS)  // L = U^T
+        block_copy<T>(mm, [&](int e) { return g[e]; }, [&](int e, T v) {
+            const int j = e / m;
+            L[j + (e - j * m) * m] = v;
+        });
+    else
+        block_copy<T>(mm, [&](int e) { return g[e]; }, [&](int e, T v) { L[e] = v; });
+    for (int e = mm + threadIdx.x; e < mm + kTrsmSlack; e += blockDim.x) L[e] = T(0);
+    __syncthreads();
+    const bool unit = t.mode == TR_LOWER_UNIT;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) dinv[i] = unit ? T(1) : T(1) / L[i + i * m];
+    T *A = reinterpret_cast<T *>(a.arena);
+    const int p = dim_c(t.P, a.kdyn);
+    if (threadIdx.x == 0) add_flops(a, K_TRSM, (double)m * m * p);
+    const bool forward = t.mode != TR_UPPER;
+    __syncthreads();
+    if (m <= 32)
+        trsm_group16<T, 2>(L, dinv, A, t.P, m, p, forward);
+    else if (m <= 64)
+        trsm_group16<T, 4>(L, dinv, A, t.P, m, p, forward);
+    else
+        trsm_group16<T, 8>(L, dinv, A, t.P, m, p, forward);
+}
+
 // ---------------------------------------------------------------- PROJECT
 // T (k x p) = F^T X (F: len x k, X: len x p): the V^T z (or U^T z) half of a
-// low-rank product (Sec. 3.1).  Rows are streamed through shared memory in
-// chunks of 32; each thread owns up to 16 outputs of a 64 x 64 output tile.
+// low-rank product (Sec. 3.1).  The output is cut into 4 x 4 tiles held in
+// registers; the lanes of a warp take consecutive rows (coalesced loads of
+// the 4 + 4 columns of the tile), kU rows per lane in flight at a time, and
+// the 32 lane partials are added by shuffles.  With fewer tiles than warps,
+// G warps share a tile (row groups) and their partials meet in shared memory.
+size_t project_smem_bytes(int elem) { return (size_t)(kThreads / 32) * 16 * elem; }
+
 template <class T>
 __device__ void dev_project(const TProject &t, const LaunchArgs &a, unsigned char *smem_raw) {
-    T(*sF)[65] = reinterpret_cast<T(*)[65]>(smem_raw);
-    T(*sX)[65] = sF + 32;
+    constexpr int kU = sizeof(T) == 8 ? 2 : 4;
     T *A = reinterpret_cast<T *>(a.arena);
+    T *red = reinterpret_cast<T *>(smem_raw);
     const int len = dim_r(t.F, a.kdyn), k = dim_c(t.F, a.kdyn), p = dim_c(t.X, a.kdyn);
     if (threadIdx.x == 0) add_flops(a, K_PROJECT, 2.0 * len * k * p);
-    for (int a0 = 0; a0 < k; a0 += 64)
-        for (int b0 = 0; b0 < p; b0 += 64) {
-            const int ka = min(64, k - a0), pb = min(64, p - b0);
-            T acc[16];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int ta = (k + 3) >> 2, tb = (p + 3) >> 2, ntile = ta * tb;
+    if (ntile == 0) return;
+    const int G = ntile >= nw ? 1 : nw / ntile, per = nw / G;
+    const int64_t frs = t.F.rs, xrs = t.X.rs;
+    for (int tile0 = 0; tile0 < ntile; tile0 += per) {
+        const int tile = tile0 + warp / G, g = warp % G;
+        const bool live = warp / G < per && tile < ntile;
+        const int ia = (tile % ta) * 4, ib = (tile / ta) * 4;
+        T acc[16];
 #pragma unroll
-            for (int s = 0; s < 16; ++s) acc[s] = T(0);
-            for (int r0 = 0; r0 < len; r0 += 32) {
-                const int rr = min(32, len - r0);
-                for (int e = threadIdx.x; e < 32 * 64; e += blockDim.x) {
-                    const int r = e & 31, c = e >> 5;
-                    sF[r][c] = (r < rr && c < ka) ? at(A, t.F, r0 + r, a0 + c) : T(0);
-                    sX[r][c] = (r < rr && c < pb) ? at(A, t.X, r0 + r, b0 + c) : T(0);
-                }
-                __syncthreads();
+        for (int s = 0; s < 16; ++s) acc[s] = T(0);
+        int na = 0, nb = 0;
+        if (live) {
+            na = min(4, k - ia);
+            nb = min(4, p - ib);
+            const T *pf[4], *px[4];
 #pragma unroll
-                for (int s = 0; s < 16; ++s) {
-                    const int idx = threadIdx.x + kThreads * s;
-                    const int ia = idx & 63, ib = idx >> 6;
-                    T v = acc[s];
-                    for (int r = 0; r < rr; ++r) v += sF[r][ia] * sX[r][ib];
-                    acc[s] = v;
-                }
-                __syncthreads();
+            for (int u = 0; u < 4; ++u) {
+                pf[u] = A + t.F.off + (int64_t)(ia + min(u, na - 1)) * t.F.cs;
+                px[u] = A + t.X.off + (int64_t)(ib + min(u, nb - 1)) * t.X.cs;
             }
+            const int step = G * 32;
+            int r = g * 32 + lane;
+            for (; r + (kU - 1) * step < len; r += kU * step) {
+                T f[kU][4], x[kU][4];
 #pragma unroll
-            for (int s = 0; s < 16; ++s) {
-                const int idx = threadIdx.x + kThreads * s;
-                const int ia = idx & 63, ib = idx >> 6;
-                if (ia < ka && ib < pb) at(A, t.T, a0 + ia, b0 + ib) = acc[s];
+                for (int q = 0; q < kU; ++q)
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        f[q][u] = pf[u][(int64_t)(r + q * step) * frs];
+                        x[q][u] = px[u][(int64_t)(r + q * step) * xrs];
+                    }
+#pragma unroll
+                for (int q = 0; q < kU; ++q)
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) acc[u * 4 + v] += f[q][u] * x[q][v];
+            }
+            for (; r < len; r += step) {
+                T f[4], x[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    f[u] = pf[u][(int64_t)r * frs];
+                    x[u] = px[u][(int64_t)r * xrs];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u * 4 + v] += f[u] * x[v];
             }
         }
+#pragma unroll
+        for (int s = 0; s < 16; ++s) acc[s] = warp_sum_t(acc[s]);
+        if (G > 1) {
+            __syncthreads();
+            if (lane == 0)
+#pragma unroll
+                for (int s = 0; s < 16; ++s) red[warp * 16 + s] = acc[s];
+            __syncthreads();
+            if (live && g == 0 && lane < 16) {
+                T v = T(0);
+                for (int q = 0; q < G; ++q) v += red[(warp + q) * 16 + lane];
+                const int u = lane >> 2, w = lane & 3;
+                if (u < na && w < nb) at(A, t.T, ia + u, ib + w) = v;
+            }
+        } else if (live && lane == 0) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int w = 0; w < 4; ++w)
+                    if (u < na && w < nb) at(A, t.T, ia + u, ib + w) = acc[u * 4 + w];
+        }
+    }
 }
 
 // ------------------------------------------------------------------ ACCUM
 // out (m x p) = beta out + alpha sum_t A_t X_t over the leaves that cover one
 // leaf cluster of the output rows (dense leaves: A = D, X = panel slice;
-// low-rank leaves: A = U slice, X = projected V^T z).
+// low-rank leaves: A = U slice, X = projected V^T z).  The term descriptors
+// and their inner sizes are read in parallel into a shared table (at most
+// kAccTerms at a time) with the exclusive prefix of the inner sizes.  The
+// inner columns of all terms are then packed, as many as the CTA's shared
+// memory holds, into an m x L matrix sA and an L x p matrix sX: a warp takes
+// one packed column at a time and its lanes issue asynchronous global-to-
+// shared copies (cp.async) of that column's rows, so that all copies of a
+// batch are in flight together; one wait, then the batch is consumed as a
+// small GEMM from shared memory, every thread owning up to 4 outputs of a row.
+constexpr int kAccTerms = 64, kAccCols = 1024;
+
+__host__ __device__ constexpr size_t accum_header_bytes() {
+    return (kAccTerms * sizeof(Term) + sizeof(int) * (kAccTerms + 1 + kAccCols) + 15) & ~size_t(15);
+}
+
+size_t accum_smem_bytes(int elem) { return accum_header_bytes() + (size_t)12288 * elem; }
+
 template <class T>
-__device__ void dev_accum(const TAccum &t, const Term *terms, const LaunchArgs &a) {
+__device__ __forceinline__ void cp_async_el(T *dst_smem, const T *src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst_smem);
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <class T>
+__device__ void dev_accum(const TAccum &t, const Term *terms, const LaunchArgs &a, unsigned char *smem_raw,
+                          size_t smem_bytes) {
     T *A = reinterpret_cast<T *>(a.arena);
+    Term *sT = reinterpret_cast<Term *>(smem_raw);
+    int *sP = reinterpret_cast<int *>(sT + kAccTerms);  // exclusive prefix of the inner sizes
+    int *sC = sP + kAccTerms + 1;                      // packed column -> (term << 16) | column
+    T *sm = reinterpret_cast<T *>(smem_raw + accum_header_bytes());
+    const int data = (int)((smem_bytes - accum_header_bytes()) / sizeof(T));
     const int m = dim_r(t.out, a.kdyn);
     const int p = t.dst >= 0 ? a.kdyn[t.src] : dim_c(t.out, a.kdyn);
     if (t.dst >= 0 && threadIdx.x == 0) a.kdyn[t.dst] = p;
-    if (threadIdx.x == 0) {
-        double f = 0.0;
-        for (int q = 0; q < t.nterms; ++q) f += 2.0 * m * (double)dim_c(terms[t.term0 + q].A, a.kdyn) * p;
-        add_flops(a, K_ACCUM, f);
-    }
+    if (m == 0 || p == 0) return;
     const T alpha = T(t.alpha);
-    for (int e0 = 0; e0 < m * p; e0 += blockDim.x) {
-        const int e = e0 + threadIdx.x;
-        if (e >= m * p) break;
-        const int i = e % m, j = e / m;
-        T acc = T(0);
-        for (int q = 0; q < t.nterms; ++q) {
-            const Term tm = terms[t.term0 + q];
-            const int inner = dim_c(tm.A, a.kdyn);
-            const T *pa = A + tm.A.off + (int64_t)i * tm.A.rs;
-            const T *px = A + tm.X.off + (int64_t)j * tm.X.cs;
-            for (int l = 0; l < inner; ++l) acc += pa[(int64_t)l * tm.A.cs] * px[(int64_t)l * tm.X.rs];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    constexpr int kSlots = 4;  // (row, 4-column block) outputs per thread
+    // output column tiles of pb columns: m * ceil(pb / 4) <= kSlots * blockDim
+    const int pbmax = max(4, min((p + 3) & ~3, 4 * (kSlots * (int)blockDim.x / m)));
+    for (int b0 = 0; b0 < p; b0 += pbmax) {
+        const int pb = min(pbmax, p - b0);
+        const int Lcap = min(kAccCols, data / (m + pb));  // >= 1
+        T *sA = sm, *sX = sm + m * Lcap;                 // sA: m x Lcap (ld m); sX: Lcap x pb (ld Lcap)
+        const int work = m * ((pb + 3) >> 2);
+        T acc[kSlots][4];
+#pragma unroll
+        for (int s = 0; s < kSlots; ++s)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[s][u] = T(0);
+        for (int q0 = 0; q0 < t.nterms; q0 += kAccTerms) {
+            const int nq = min(kAccTerms, t.nterms - q0);
+            __syncthreads();  // the previous table and batch are no longer read
+            if ((int)threadIdx.x < nq) {
+                const Term tm = terms[t.term0 + q0 + threadIdx.x];
+                sT[threadIdx.x] = tm;
+                sP[threadIdx.x + 1] = dim_c(tm.A, a.kdyn);
+            }
+            __syncthreads();
+            if (warp == 0) {  // inclusive scan of the inner sizes
+                int carry = 0;
+                for (int base = 0; base < nq; base += 32) {
+                    const int q = base + lane;
+                    int v = q < nq ? sP[q + 1] : 0;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(kFull, v, o);
+                        if (lane >= o) v += y;
+                    }
+                    if (q < nq) sP[q + 1] = v + carry;
+                    carry += __shfl_sync(kFull, v, 31);
+                }
+                if (lane == 0) sP[0] = 0;
+            }
+            __syncthreads();
+            const int Ltot = sP[nq];
+            if (b0 == 0 && threadIdx.x == 0) add_flops(a, K_ACCUM, 2.0 * m * (double)Ltot * p);
+            for (int c0 = 0; c0 < Ltot; c0 += Lcap) {
+                const int L = min(Lcap, Ltot - c0);
+                if (c0 > 0) __syncthreads();  // the previous batch is consumed
+                for (int lb = threadIdx.x; lb < L; lb += blockDim.x) {
+                    const int gc = c0 + lb;
+                    int lo = 0, hi = nq - 1;  // largest q with sP[q] <= gc (a non-empty term)
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (sP[mid] <= gc)
+                            lo = mid;
+                        else
+                            hi = mid - 1;
+                    }
+                    sC[lb] = (lo << 16) | (gc - sP[lo]);
+                }
+                __syncthreads();
+                for (int lb = warp; lb < L; lb += nw) {
+                    const int c = sC[lb], q = c >> 16, l = c & 0xffff;
+                    const Panel &PA = sT[q].A;
+                    const T *ca = A + PA.off + (int64_t)l * PA.cs;
+                    for (int i = lane; i < m; i += 32) cp_async_el(sA + lb * m + i, ca + (int64_t)i * PA.rs);
+                    const Panel &PX = sT[q].X;
+                    const T *cx = A + PX.off + (int64_t)l * PX.rs + (int64_t)b0 * PX.cs;
+                    for (int j = lane; j < pb; j += 32) cp_async_el(sX + lb + j * Lcap, cx + (int64_t)j * PX.cs);
+                }
+                cp_async_wait_all();
+                __syncthreads();
+#pragma unroll
+                for (int s = 0; s < kSlots; ++s) {
+                    const int w = threadIdx.x + s * blockDim.x;
+                    if (w < work) {
+                        const int jb = w / m, i = w - jb * m, j0 = jb * 4;
+                        const T *pa = sA + i;
+                        const T *px = sX + j0 * Lcap;
+                        const int x1 = min(1, pb - 1 - j0) * Lcap, x2 = min(2, pb - 1 - j0) * Lcap,
+                                  x3 = min(3, pb - 1 - j0) * Lcap;
+                        T a0 = acc[s][0], a1 = acc[s][1], a2 = acc[s][2], a3 = acc[s][3];
+                        for (int lb = 0; lb < L; ++lb) {
+                            const T av = pa[lb * m];
+                            a0 += av * px[lb];
+                            a1 += av * px[lb + x1];
+                            a2 += av * px[lb + x2];
+                            a3 += av * px[lb + x3];
+                        }
+                        acc[s][0] = a0;
+                        acc[s][1] = a1;
+                        acc[s][2] = a2;
+                        acc[s][3] = a3;
+                    }
+                }
+            }
         }
-        T &o = at(A, t.out, i, j);
-        o = (t.overwrite ? T(0) : o) + alpha * acc;
+        // outputs of the tile (also without terms: an overwrite clears them)
+#pragma unroll
+        for (int s = 0; s < kSlots; ++s) {
+            const int w = threadIdx.x + s * blockDim.x;
+            if (w < work) {
+                const int jb = w / m, i = w - jb * m, j0 = jb * 4;
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (j0 + u < pb) {
+                        T &o = at(A, t.out, i, b0 + j0 + u);
+                        o = (t.overwrite ? T(0) : o) + alpha * acc[s][u];
+                    }
+            }
+        }
     }
 }
 
@@ -268,203 +460,248 @@ __device__ void dev_split(const TSplit &t, const LaunchArgs &a) {
     T *A = reinterpret_cast<T *>(a.arena);
     const int k = a.kdyn[t.src_kslot];
     if (threadIdx.x == 0) a.kdyn[t.dst_kslot] = k;
-    for (int e = threadIdx.x; e < t.mu * k; e += blockDim.x) {
-        const int i = e % t.mu, j = e / t.mu;
-        A[t.dstU + e] = at(A, t.srcU, i, j);
-    }
-    for (int e = threadIdx.x; e < t.nv * k; e += blockDim.x) {
-        const int i = e % t.nv, j = e / t.nv;
-        A[t.dstV + e] = at(A, t.srcV, i, j);
-    }
+    block_copy<T>(
+        t.mu * k, [&](int e) { return at(A, t.srcU, e % t.mu, e / t.mu); },
+        [&](int e, T v) { A[t.dstU + e] = v; });
+    block_copy<T>(
+        t.nv * k, [&](int e) { return at(A, t.srcV, e % t.nv, e / t.nv); },
+        [&](int e, T v) { A[t.dstV + e] = v; });
 }
 
 // ------------------------------------------------------------------- RADD
-template <class R>
-__device__ __forceinline__ R warp_sum_t(R v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
+
+// Named barrier over `count` threads (a multiple of 32); id 0 with the whole
+// CTA is __syncthreads.
+__device__ __forceinline__ void bar_sync(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
-// Householder QR of the m x K panel W in place, in the panel's own precision T
-// (reflector j: v_j = 1 implied, v_j[i] stored below the diagonal, tau[j]);
-// R in the upper triangle.
+// Householder QR of the m x K panel W (column major, leading dimension m) in
+// place, in precision T, by the nw warps [w0, w0 + nw) of the CTA, which
+// synchronise on named barrier `bar`.  Reflector j is H_j = I - tau_j v_j
+// v_j^T with v_j[j] = 1 implied and v_j[i > j] stored below the diagonal; R
+// is left in the upper triangle.  One barrier per column: in step j every
+// warp forms the scalars of reflector j itself from the squared norm of
+// column j below row j - 1 (left in nrm[j] by the warp that updated that
+// column in step j - 1) and applies it to its own columns with v_j[i] =
+// x[i] / v0 taken on the fly; after the barrier the warp j mod nw writes v_j
+// back.  nrm holds min(m, K) entries.
 template <class T>
-__device__ void block_householder_qr(T *W, int m, int K, double *tau, double *red) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+__device__ void group_householder_qr(T *W, int m, int K, T *tau, T *nrm, int w0, int nw, int bar) {
+    const int warp = (int)(threadIdx.x >> 5) - w0, lane = threadIdx.x & 31, nthr = nw * 32;
     const int kk = min(m, K);
+    if (kk == 0) return;  // uniform over the group
+    if (warp == 0) {
+        T s = T(0);
+        for (int i = lane; i < m; i += 32) s += W[i] * W[i];
+        s = warp_sum_t(s);
+        if (lane == 0) nrm[0] = s;
+    }
+    bar_sync(bar, nthr);
     for (int j = 0; j < kk; ++j) {
         T *x = W + (int64_t)j * m;
-        T s = T(0);
-        for (int i = j + threadIdx.x; i < m; i += blockDim.x) s += x[i] * x[i];
-        s = warp_sum_t(s);
-        __syncthreads();
-        if (lane == 0) red[warp] = (double)s;
-        __syncthreads();
-        if (warp == 0) {
-            double q = lane < nw ? red[lane] : 0.0;
-            q = warp_sum(q);
-            if (lane == 0) red[32] = q;
-        }
-        __syncthreads();
+        const T nr = sqrt(nrm[j]);
         const T x0 = x[j];
-        const T nrm = T(sqrt(red[32]));
-        if (nrm == T(0)) {
-            if (threadIdx.x == 0) tau[j] = 0.0;
-            __syncthreads();
-            continue;
+        T alpha = T(0), inv = T(0), tj = T(0);
+        if (nr > T(0)) {
+            alpha = x0 >= T(0) ? -nr : nr;
+            inv = T(1) / (x0 - alpha);
+            tj = (alpha - x0) / alpha;
         }
-        const T alpha = x0 >= T(0) ? -nrm : nrm;
-        const T v0 = x0 - alpha;
-        const T tj = (alpha - x0) / alpha;
-        __syncthreads();
-        for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) x[i] = x[i] / v0;
-        if (threadIdx.x == 0) {
-            x[j] = alpha;
-            tau[j] = (double)tj;
-        }
-        __syncthreads();
         for (int c = j + 1 + warp; c < K; c += nw) {
             T *y = W + (int64_t)c * m;
             T d = T(0);
-            for (int i = j + 1 + lane; i < m; i += 32) d += x[i] * y[i];
+            for (int i = j + 1 + lane; i < m; i += 32) d += (x[i] * inv) * y[i];
             d = warp_sum_t(d);
             d = (d + y[j]) * tj;
             __syncwarp();
             if (lane == 0) y[j] -= d;
-            for (int i = j + 1 + lane; i < m; i += 32) y[i] -= d * x[i];
+            if (c == j + 1 && c < kk) {  // next pivot column: leave its norm below row j
+                T t2 = T(0);
+                for (int i = j + 1 + lane; i < m; i += 32) {
+                    const T yi = y[i] - d * (x[i] * inv);
+                    y[i] = yi;
+                    t2 += yi * yi;
+                }
+                t2 = warp_sum_t(t2);
+                if (lane == 0) nrm[c] = t2;
+            } else {
+                for (int i = j + 1 + lane; i < m; i += 32) y[i] -= d * (x[i] * inv);
+            }
         }
-        __syncthreads();
+        bar_sync(bar, nthr);
+        if (warp == j % nw) {
+            for (int i = j + 1 + lane; i < m; i += 32) x[i] = x[i] * inv;
+            if (lane == 0) {
+                x[j] = alpha;
+                tau[j] = tj;
+            }
+        }
     }
+    bar_sync(bar, nthr);
 }
 
-// Z (m x nc, ld m) := Q Z with Q = H_0 ... H_{kk-1} from block_householder_qr,
-// in precision T; each warp owns whole columns, so no CTA barrier is needed
-// between reflectors.
+// y := Q y for one column y (length m) with Q = H_0 ... H_{kk-1} from
+// group_householder_qr; executed by one warp.
 template <class T>
-__device__ void block_apply_q(const T *W, int m, int kk, const double *tau, T *Z, int nc) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int c = warp; c < nc; c += nw) {
-        T *y = Z + (int64_t)c * m;
-        for (int j = kk - 1; j >= 0; --j) {
-            const T *x = W + (int64_t)j * m;
-            T d = T(0);
-            for (int i = j + 1 + lane; i < m; i += 32) d += x[i] * y[i];
-            d = warp_sum_t(d);
-            d = (d + y[j]) * T(tau[j]);
-            __syncwarp();
-            if (lane == 0) y[j] -= d;
-            for (int i = j + 1 + lane; i < m; i += 32) y[i] -= d * x[i];
-            __syncwarp();
-        }
+__device__ void warp_apply_q(const T *W, int m, int kk, const T *tau, T *y) {
+    const int lane = threadIdx.x & 31;
+    for (int j = kk - 1; j >= 0; --j) {
+        const T *x = W + (int64_t)j * m;
+        T d = T(0);
+        for (int i = j + 1 + lane; i < m; i += 32) d += x[i] * y[i];
+        d = warp_sum_t(d);
+        d = (d + y[j]) * tau[j];
+        __syncwarp();
+        if (lane == 0) y[j] -= d;
+        for (int i = j + 1 + lane; i < m; i += 32) y[i] -= d * x[i];
+        __syncwarp();
     }
 }
 
-// One-sided (Hestenes) Jacobi on the columns of M (ku x kv, double, shared):
-// M J = B with orthogonal columns; the singular values are the column norms of
-// B, the right singular vectors the columns of J.  Round-robin ordering, one
-// warp per column pair.  A pair is rotated while |x.y| > tol |x||y| with
-// tol = 4 ku eps_double, the rounding level of the dot product itself (a
-// smaller tolerance is never met reliably and only burns sweeps); at most 30
-// sweeps.
-__device__ void block_jacobi(double *M, int ku, int kv, double *J, int *flag) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const int np = (kv + 1) & ~1;
-    const double tol = 4.0 * ku * DBL_EPSILON;
-    for (int sweep = 0; sweep < 30; ++sweep) {
+// Jacobi rotation (c, s) that makes columns x, y with x.x = aa, y.y = bb,
+// x.y = gg orthogonal: t = tan(theta) is the smaller root of
+// t^2 + 2 zeta t - 1 = 0, zeta = (bb - aa) / (2 gg) (Rutishauser's form), and
+// c = 1 / sqrt(1 + t^2), s = c t.  The angle is evaluated in single precision
+// (zeta from a power-of-two scaling of both operands, so that it neither
+// overflows nor underflows), then (c, s) is renormalised in double by the
+// series 1 / sqrt(1 + d) = 1 - d / 2 + 3 d^2 / 8 + O(d^3), d = c^2 + s^2 - 1
+// (|d| ~ 1e-7, so the neglected term is below double rounding): the rotation
+// is orthogonal to double precision, and only its angle is single-precision
+// accurate, which the convergence test on the double dot products absorbs.
+__device__ __forceinline__ void jacobi_rotation(double aa, double bb, double gg, double &c, double &s) {
+    const double p = 2.0 * gg, q = bb - aa;
+    int e = (int)((__double2hiint(p) >> 20) & 0x7ff) - 1023;  // binary exponent of p
+    e = max(-1000, min(1000, e));
+    const double sc = __hiloint2double((1023 - e) << 20, 0);  // 2^-e, exact
+    const float pf = (float)(p * sc), qf = (float)(q * sc);
+    const float z = qf / pf, az = fabsf(z);
+    float t;
+    if (!(az < 1e15f))
+        t = isinf(z) ? 0.0f : 0.5f / z;  // t ~ 1 / (2 zeta); z = +-inf: a negligible angle
+    else
+        t = copysignf(1.0f, z) / (az + sqrtf(fmaf(z, z, 1.0f)));
+    const float cf = rsqrtf(fmaf(t, t, 1.0f));
+    const double cd = (double)cf, sd = (double)(cf * t);
+    const double d = fma(cd, cd, fma(sd, sd, -1.0));
+    const double f = fma(d, fma(0.375, d, -0.5), 1.0);
+    c = cd * f;
+    s = sd * f;
+}
+
+// One-sided (Hestenes) Jacobi on the columns of D (r x r, double, shared
+// memory, leading dimension ld), in place: D W = B with orthogonal columns
+// (W is not formed); the singular values of D are the column norms of B and
+// B = U_D Sigma holds its left singular vectors.  Round-robin ordering; the r/2 pairs of a round are
+// taken by groups of g lanes (g a power of two: the largest that is useful
+// for r rows and fits the CTA), each lane holding rows i = lane, lane + g, ...
+// of both columns; when all groups fit in one warp, the rounds run in that
+// warp alone with warp barriers.  A pair is rotated while
+// |x.y|^2 > tol^2 |x|^2 |y|^2 with tol = 4 r eps_double, the rounding level of
+// the dot product itself; at most 30 sweeps.  Returns the number of sweeps.
+__device__ int block_jacobi(double *D, int r, int ld, int *flag) {
+    if (r < 2) return 0;
+    const int np = (r + 1) & ~1, P = np / 2;
+    int g = 32;
+    while (g > 1 && g * P > (int)blockDim.x) g >>= 1;
+    while (g > 1 && (g >> 1) >= r) g >>= 1;
+    const bool one_warp = g * P <= 32;
+    const int gid = threadIdx.x / g, gl = threadIdx.x % g;
+    const double tol = 4.0 * r * DBL_EPSILON, tol2 = tol * tol;
+    int sweep = 0;
+    while (sweep < 30) {
+        ++sweep;
         if (threadIdx.x == 0) *flag = 0;
         __syncthreads();
-        for (int r = 0; r < np - 1; ++r) {
-            for (int pi = warp; pi < np / 2; pi += nw) {
+        if (!one_warp || threadIdx.x < 32) {  // uniform per warp
+            for (int rd = 0; rd < np - 1; ++rd) {
                 int p, q;
-                if (pi == 0) {
-                    p = r;
+                if (gid == 0) {
+                    p = rd;
                     q = np - 1;
                 } else {
-                    p = (r + pi) % (np - 1);
-                    q = (r - pi + np - 1) % (np - 1);
+                    p = (rd + gid) % (np - 1);
+                    q = (rd - gid + np - 1) % (np - 1);
                 }
                 if (p > q) {
                     const int tmp = p;
                     p = q;
                     q = tmp;
                 }
-                if (q >= kv) continue;
-                double *cp = M + (int64_t)p * ku, *cq = M + (int64_t)q * ku;
+                const bool active = gid < P && q < r;
+                double *cp = D + (int64_t)p * ld, *cq = D + (int64_t)q * ld;
                 double aa = 0.0, bb = 0.0, gg = 0.0;
-                for (int i = lane; i < ku; i += 32) {
-                    const double x = cp[i], y = cq[i];
-                    aa += x * x;
-                    bb += y * y;
-                    gg += x * y;
+                if (active)
+                    for (int i = gl; i < r; i += g) {
+                        const double x = cp[i], y = cq[i];
+                        aa = fma(x, x, aa);
+                        bb = fma(y, y, bb);
+                        gg = fma(x, y, gg);
+                    }
+                for (int o = g >> 1; o > 0; o >>= 1) {  // every lane of the warp takes part
+                    aa += __shfl_xor_sync(kFull, aa, o);
+                    bb += __shfl_xor_sync(kFull, bb, o);
+                    gg += __shfl_xor_sync(kFull, gg, o);
                 }
-                aa = warp_sum(aa);
-                bb = warp_sum(bb);
-                gg = warp_sum(gg);
-                if (gg == 0.0 || !(fabs(gg) > tol * sqrt(aa * bb))) continue;
-                if (lane == 0) *flag = 1;
-                const double zeta = (bb - aa) / (2.0 * gg);
-                const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
-                __syncwarp();
-                for (int i = lane; i < ku; i += 32) {
-                    const double x = cp[i], y = cq[i];
-                    cp[i] = cs * x - sn * y;
-                    cq[i] = sn * x + cs * y;
+                // the butterfly leaves identical sums in every lane of a group
+                if (active && gg * gg > tol2 * aa * bb) {
+                    if (gl == 0) *flag = 1;
+                    double cs, sn;
+                    jacobi_rotation(aa, bb, gg, cs, sn);
+                    for (int i = gl; i < r; i += g) {
+                        const double x = cp[i], y = cq[i];
+                        cp[i] = cs * x - sn * y;
+                        cq[i] = sn * x + cs * y;
+                    }
                 }
-                double *jp = J + (int64_t)p * kv, *jq = J + (int64_t)q * kv;
-                for (int i = lane; i < kv; i += 32) {
-                    const double x = jp[i], y = jq[i];
-                    jp[i] = cs * x - sn * y;
-                    jq[i] = sn * x + cs * y;
-                }
+                if (one_warp)
+                    __syncwarp();
+                else
+                    __syncthreads();
             }
-            __syncthreads();
         }
+        __syncthreads();
         const int f = *flag;
         __syncthreads();
         if (!f) break;
     }
+    return sweep;
 }
 
-// FP64 core buffers of a rounded addition with stacked rank K (see dev_radd).
-__host__ __device__ size_t radd_core_bytes(int K) {
-    return sizeof(double) * (3 * (size_t)K * K + 5 * (size_t)K + 40) + sizeof(int) * (2 * (size_t)K + 8);
-}
-
-size_t radd_smem_bytes(int kc) { return radd_core_bytes(kc); }
-
-// QR with column pivoting of the ku x kv core M (double, shared memory, column
-// major), stopped at the first step whose largest remaining column norm is at
-// most delta times the first pivot's (the neglected block is at the level of
-// double rounding): M P = Q [R'; ~0] with R' of r rows.  Reflectors are kept
-// below the diagonal of M (v_j = 1 implied), tau[j]; perm holds P.  The pivot
-// is the largest column norm, lowest index on ties.
-__device__ int block_qrcp(double *M, int ku, int kv, double *tau, double *cn, int *perm, double delta,
-                          double *red, int *iflag) {
+// QR with column pivoting of the mr x nc core M (precision R, shared memory,
+// column major), stopped at the first step whose largest remaining column
+// norm is at most delta times the first pivot's: M P = Q [R'; ~0] with R' of
+// r rows.  Reflectors are kept below the diagonal of M (v_j = 1 implied),
+// tau[j]; R' stays in rows < r; perm holds P.  The pivot is the largest
+// column norm, lowest index on ties; the norms of the remaining columns are
+// recomputed (not downdated) after every step.
+template <class R>
+__device__ int block_qrcp(R *M, int mr, int nc, R *tau, R *cn, int *perm, double delta, int *iflag) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int j = threadIdx.x; j < kv; j += blockDim.x) {
-        double s = 0.0;
-        for (int i = 0; i < ku; ++i) s += M[i + (size_t)j * ku] * M[i + (size_t)j * ku];
+    for (int j = threadIdx.x; j < nc; j += blockDim.x) {
+        R s = R(0);
+        for (int i = 0; i < mr; ++i) s += M[i + (size_t)j * mr] * M[i + (size_t)j * mr];
         cn[j] = s;
         perm[j] = j;
     }
     __syncthreads();
-    double n0 = 0.0;  // first pivot norm (kept by warp 0)
+    const R d2 = R(delta * delta);
+    R n0 = R(0);  // first pivot norm (kept by warp 0)
     int r = 0;
-    const int kk = min(ku, kv);
+    const int kk = min(mr, nc);
     for (int j = 0; j < kk; ++j) {
-        double *x = M + (size_t)j * ku;
+        R *x = M + (size_t)j * mr;
         // warp 0: pivot, stopping test, column swap and reflector; one barrier
         if (warp == 0) {
-            double bv = -1.0;
+            R bv = R(-1);
             int bi = j;
-            for (int c = j + lane; c < kv; c += 32)
+            for (int c = j + lane; c < nc; c += 32)
                 if (cn[c] > bv) {
                     bv = cn[c];
                     bi = c;
                 }
             for (int o = 16; o > 0; o >>= 1) {
-                const double ov = __shfl_xor_sync(kFull, bv, o);
+                const R ov = __shfl_xor_sync(kFull, bv, o);
                 const int oi = __shfl_xor_sync(kFull, bi, o);
                 if (ov > bv || (ov == bv && oi < bi)) {
                     bv = ov;
@@ -472,18 +709,18 @@ __device__ int block_qrcp(double *M, int ku, int kv, double *tau, double *cn, in
                 }
             }
             if (j == 0) n0 = bv;
-            const bool stop = !(bv > delta * delta * n0);
+            const bool stop = !(bv > d2 * n0);
             if (lane == 0) iflag[1] = stop ? -1 : bi;
             if (!stop) {
                 const int p = bi;
                 if (p != j) {
-                    for (int i = lane; i < ku; i += 32) {
-                        const double tmp = x[i];
-                        x[i] = M[i + (size_t)p * ku];
-                        M[i + (size_t)p * ku] = tmp;
+                    for (int i = lane; i < mr; i += 32) {
+                        const R tmp = x[i];
+                        x[i] = M[i + (size_t)p * mr];
+                        M[i + (size_t)p * mr] = tmp;
                     }
                     if (lane == 0) {
-                        const double tc = cn[j];
+                        const R tc = cn[j];
                         cn[j] = cn[p];
                         cn[p] = tc;
                         const int tp = perm[j];
@@ -492,17 +729,17 @@ __device__ int block_qrcp(double *M, int ku, int kv, double *tau, double *cn, in
                     }
                     __syncwarp();
                 }
-                double s = 0.0;
-                for (int i = j + lane; i < ku; i += 32) s += x[i] * x[i];
-                s = warp_sum(s);
-                const double x0 = x[j];
-                const double nrm = sqrt(s);
-                double tj = 0.0;
+                R s = R(0);
+                for (int i = j + lane; i < mr; i += 32) s += x[i] * x[i];
+                s = warp_sum_t(s);
+                const R x0 = x[j];
+                const R nrm = sqrt(s);
+                R tj = R(0);
                 __syncwarp();
-                if (nrm > 0.0) {
-                    const double alpha = x0 >= 0.0 ? -nrm : nrm;
-                    const double v0 = x0 - alpha;
-                    for (int i = j + 1 + lane; i < ku; i += 32) x[i] /= v0;
+                if (nrm > R(0)) {
+                    const R alpha = x0 >= R(0) ? -nrm : nrm;
+                    const R v0 = x0 - alpha;
+                    for (int i = j + 1 + lane; i < mr; i += 32) x[i] /= v0;
                     tj = (alpha - x0) / alpha;
                     __syncwarp();
                     if (lane == 0) x[j] = alpha;
@@ -512,21 +749,21 @@ __device__ int block_qrcp(double *M, int ku, int kv, double *tau, double *cn, in
         }
         __syncthreads();
         if (iflag[1] < 0) break;  // uniform: every thread reads the same flag
-        const double tj = tau[j];
-        for (int c = j + 1 + warp; c < kv; c += nw) {
-            double *y = M + (size_t)c * ku;
-            double d = 0.0;
-            for (int i = j + 1 + lane; i < ku; i += 32) d += x[i] * y[i];
-            d = warp_sum(d);
+        const R tj = tau[j];
+        for (int c = j + 1 + warp; c < nc; c += nw) {
+            R *y = M + (size_t)c * mr;
+            R d = R(0);
+            for (int i = j + 1 + lane; i < mr; i += 32) d += x[i] * y[i];
+            d = warp_sum_t(d);
             d = (d + y[j]) * tj;
             __syncwarp();
             if (lane == 0) y[j] -= d;
-            double t2 = 0.0;
-            for (int i = j + 1 + lane; i < ku; i += 32) {
+            R t2 = R(0);
+            for (int i = j + 1 + lane; i < mr; i += 32) {
                 y[i] -= d * x[i];
                 t2 += y[i] * y[i];
             }
-            t2 = warp_sum(t2);
+            t2 = warp_sum_t(t2);
             if (lane == 0) cn[c] = t2;
         }
         __syncthreads();
@@ -535,72 +772,191 @@ __device__ int block_qrcp(double *M, int ku, int kv, double *tau, double *cn, in
     return r;
 }
 
-// Z (ku x nc in shared memory, leading dimension ku) := Q Z with the r
-// reflectors of block_qrcp; one warp per column.
-__device__ void block_apply_qcp(const double *M, int ku, int r, const double *tau, double *Z, int nc) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int c = warp; c < nc; c += nw) {
-        double *y = Z + (size_t)c * ku;
-        for (int j = r - 1; j >= 0; --j) {
-            const double *x = M + (size_t)j * ku;
-            double d = 0.0;
-            for (int i = j + 1 + lane; i < ku; i += 32) d += x[i] * y[i];
-            d = warp_sum(d);
-            d = (d + y[j]) * tau[j];
-            __syncwarp();
-            if (lane == 0) y[j] -= d;
-            for (int i = j + 1 + lane; i < ku; i += 32) y[i] -= d * x[i];
-            __syncwarp();
-        }
+// Shared buffers of the truncated SVD of an mr x nc core (core_truncate),
+// carved from one byte range: double arrays first, then arrays of the core
+// precision R, then ints.  With `stacked`, the reflector scalars and column
+// norms of the two stacked QRs (mr and nc of each) come along.
+template <class R>
+struct CoreBufs {
+    double *D, *sig;                       // Jacobi factor (rc x rc), singular values
+    R *M, *C, *cn, *tauM, *tauC, *B, *isg;  // B: D in precision R (aliases D when R is double)
+    R *tauU, *tauV, *nrmU, *nrmV;
+    int *order, *perm, *iflag;
+};
+
+template <class R>
+__host__ __device__ inline size_t core_bytes(int mr, int nc, bool stacked) {
+    const size_t rc = mr < nc ? mr : nc, mx = mr > nc ? mr : nc;
+    const size_t nr = (size_t)mr * nc + mx * rc + nc + 3 * rc + (sizeof(R) == 8 ? 0 : rc * rc) +
+                      (stacked ? 2 * ((size_t)mr + nc) : 0);
+    return 8 * (rc * rc + rc) + sizeof(R) * nr + 4 * (rc + nc + 8);
+}
+
+template <class R>
+__device__ CoreBufs<R> carve_core(unsigned char *base, int mr, int nc, bool stacked) {
+    const int rc = min(mr, nc), mx = max(mr, nc);
+    CoreBufs<R> b;
+    b.D = reinterpret_cast<double *>(base);
+    b.sig = b.D + rc * rc;
+    R *x = reinterpret_cast<R *>(b.sig + rc);
+    b.M = x;
+    x += (size_t)mr * nc;
+    b.C = x;
+    x += (size_t)mx * rc;
+    b.cn = x;
+    x += nc;
+    b.tauM = x;
+    b.tauC = x + rc;
+    b.isg = x + 2 * rc;
+    x += 3 * rc;
+    if constexpr (sizeof(R) == 8) {
+        b.B = b.D;
+    } else {
+        b.B = x;
+        x += rc * rc;
     }
+    b.tauU = b.tauV = b.nrmU = b.nrmV = nullptr;
+    if (stacked) {
+        b.tauU = x;
+        b.nrmU = x + mr;
+        x += 2 * mr;
+        b.tauV = x;
+        b.nrmV = x + nc;
+        x += 2 * nc;
+    }
+    int *ip = reinterpret_cast<int *>(x);
+    b.order = ip;
+    b.perm = ip + rc;
+    b.iflag = ip + rc + nc;
+    return b;
+}
+
+// Truncated SVD (T_eps of Sec. 3.1) of the mr x nc core M held in b.M, with
+// the two QR preconditioning steps of Drmac and Veselic (2008):
+//   M P = Q_M [R'; ~0]        pivoted QR in the core precision R, r rows
+//   R'^T = Q_C R_C            Householder QR of the nc x r factor, in R
+//   R_C^T W = B               one-sided Jacobi in double on the r x r lower
+//                             triangular X = R_C^T; sigma_j = |B_j|
+// so that M = (Q_M [B; 0]) (P Q_C W)^T, and since M^T Q_M [B; 0] = P R'^T B,
+// the right factor is P R'^T B Sigma^{-2}: neither Q_C nor W is formed.
+// Singular values sigma_i <= eps sigma_1 are dropped.  Returns the kept rank
+// (order[0..knew) lists the kept columns of B by decreasing sigma, lowest
+// index on ties) and r through r_out; leaves B in precision R (b.B) and
+// 1 / sigma (b.isg).  Phase counters (profiling only) go to slots pb + 2 ...
+// pb + 7.
+template <class R>
+__device__ int core_truncate(const CoreBufs<R> &b, int mr, int nc, double delta, const TRadd &t,
+                             const LaunchArgs &a, int *r_out, int pb, unsigned long long &ph) {
+    const int r = block_qrcp<R>(b.M, mr, nc, b.tauM, b.cn, b.perm, delta, b.iflag);
+    ph = phase_mark(a, pb + 2, ph);
+    for (int e = threadIdx.x; e < nc * r; e += blockDim.x) {
+        const int c = e % nc, i = e / nc;
+        b.C[e] = c >= i ? b.M[i + (size_t)c * mr] : R(0);
+    }
+    __syncthreads();
+    group_householder_qr<R>(b.C, nc, r, b.tauC, b.cn, 0, blockDim.x >> 5, 0);
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {  // X = R_C^T
+        const int i = e % r, j = e / r;
+        b.D[e] = i >= j ? (double)b.C[j + (size_t)i * nc] : 0.0;
+    }
+    __syncthreads();
+    const int sweeps = block_jacobi(b.D, r, r, b.iflag);
+    for (int j = threadIdx.x; j < r; j += blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < r; ++i) s += b.D[i + (size_t)j * r] * b.D[i + (size_t)j * r];
+        b.sig[j] = sqrt(s);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < r; j += blockDim.x) {
+        int rk = 0;
+        for (int l = 0; l < r; ++l) rk += (b.sig[l] > b.sig[j]) || (b.sig[l] == b.sig[j] && l < j);
+        b.order[rk] = j;
+        b.isg[j] = b.sig[j] > 0.0 ? R(1.0 / b.sig[j]) : R(0);
+    }
+    if constexpr (sizeof(R) != 8)
+        for (int e = threadIdx.x; e < r * r; e += blockDim.x) b.B[e] = R(b.D[e]);
+    __syncthreads();
+    const double s1 = r > 0 ? b.sig[b.order[0]] : 0.0;
+    int knew = 0;
+    if (!isfinite(s1)) {
+        if (threadIdx.x == 0) set_error(a.err, DE_NONFINITE, t.target, s1);
+    } else if (s1 > 0.0) {
+        for (int l = 0; l < r; ++l) knew += b.sig[b.order[l]] > a.eps * s1;
+    }
+    if (knew > t.cap) {
+        if (threadIdx.x == 0) set_error(a.err, DE_RANKCAP, t.target, (double)knew);
+        knew = t.cap;
+    }
+    ph = phase_mark(a, pb + 3, ph);
+    if (a.phase && threadIdx.x == 0) {  // Jacobi sweeps, problem size and task count
+        atomicAdd(a.phase + pb + 4, (unsigned long long)sweeps);
+        atomicAdd(a.phase + pb + 6, (unsigned long long)r);
+        atomicAdd(a.phase + pb + 7, 1ull);
+    }
+    *r_out = r;
+    return knew;
+}
+
+// Right factor of the truncated core: V[perm[i], c] = (R'^T B)[i, order[c]] /
+// sigma^2 for the nc rows of the core (V of type T, leading dimension ldv).
+template <class R, class T>
+__device__ void core_write_v(const CoreBufs<R> &b, int mr, int nc, int r, int knew, T *V, int64_t ldv) {
+    for (int e = threadIdx.x; e < nc * knew; e += blockDim.x) {
+        const int c = e % knew, i = e / knew;
+        const int j = b.order[c];
+        const int lmax = min(i, r - 1);
+        const R *bj = b.B + (size_t)j * r;
+        R s = R(0);
+        for (int l = 0; l <= lmax; ++l) s += b.M[l + (size_t)i * mr] * bj[l];
+        V[b.perm[i] + (int64_t)c * ldv] = T((s * b.isg[j]) * b.isg[j]);
+    }
+}
+
+// Left factor of the truncated core: b.C (mr x knew) := Q_M [B_sel; 0].
+// Ends with a barrier.
+template <class R>
+__device__ void core_form_u(const CoreBufs<R> &b, int mr, int r, int knew) {
+    for (int e = threadIdx.x; e < mr * knew; e += blockDim.x) {
+        const int i = e % mr, c = e / mr;
+        b.C[e] = i < r ? b.B[i + (size_t)b.order[c] * r] : R(0);
+    }
+    __syncthreads();
+    for (int c = threadIdx.x >> 5; c < knew; c += blockDim.x >> 5)
+        warp_apply_q<R>(b.M, mr, r, b.tauM, b.C + (size_t)c * mr);
+    __syncthreads();
 }
 
 // Rounded addition (Sec. 3.1): the target's factors and every contribution are
 // stacked, U_s = [U_c, c_1 U_1, ...], V_s = [V_c, V_1, ...] (pieces
 // zero-padded to the target's index ranges); both stacks are reduced by
-// Householder QR, and the core M = R_u R_v^T (double) is decomposed: a QR with
-// column pivoting M P = Q_M [R'; ~0] (stopped at double-rounding level)
-// followed by one-sided Jacobi on R'^T gives M = X Sigma Y^T with X = Q_M [J; 0]
-// and Y = P W Sigma^{-1}; singular values sigma_i <= eps sigma_1 are dropped and
-// the new factors are U = Q_u [X Sigma; 0], V = Q_v [Y; 0].
+// Householder QR (concurrently, one half of the CTA each), and the core
+// M = R_u R_v^T is truncated by core_truncate; the new factors are
+// U = Q_u [Q_M [B_sel; 0]; 0], V = Q_v [P R'^T B_sel Sigma^{-2}; 0].
+// Everything but the Jacobi SVD of the r x r factor runs in the precision T
+// of the factors; the Jacobi SVD runs in double.
 //
-// Shared memory is carved by the task's own stacked rank K: the FP64 core
-// buffers first (radd_smem_bytes(K)), then, when they fit in the rest of the
-// CTA's `smem_bytes`, the stacked panels themselves; larger panels stay in
-// the global `scratch`.  The pivoted QR of the core stops at delta times the
-// first pivot: 1e-13 for FP64 factors (double rounding level) and 1e-6 for
-// FP32 factors (an order above the FP32 rounding of the stacked panels, two
-// below the relative tolerances eps the method uses).
-// Small targets (m n <= kSmallTarget, m, n <= 128): the sum X = U_c V_c^T + sum_i c_i U_i V_i^T
-// is formed densely (in the factor precision) and its truncated SVD is taken
-// directly - pivoted QR of X (double) and one-sided Jacobi on the reduced
-// factor - which is the same T_eps of the same sum without the two stacked
-// QRs.  Returns false (before touching anything) when X and its buffers do
-// not fit in `smem_bytes`.
+// Shared memory is carved by the task's own core size: the core buffers first
+// (core_bytes), then, when they fit in the rest of the CTA's `smem_bytes`,
+// the stacked panels themselves; larger panels stay in the global `scratch`.
+// The pivoted QR of the core stops at delta times the first pivot: 1e-13 for
+// FP64 factors (double rounding level) and 1e-6 for FP32 factors (an order
+// above the FP32 rounding of the stacked panels, two below the relative
+// tolerances eps the method uses).
+// Small targets (m n <= kSmallTarget, m, n <= 128): the sum X = U_c V_c^T +
+// sum_i c_i U_i V_i^T is formed densely and truncated by core_truncate
+// directly, which is the same T_eps of the same sum without the two stacked
+// QRs.  Every launch provides at least radd_small_floor bytes, so the route
+// depends on the task alone.
 constexpr int kSmallTarget = 4096;
 
 template <class T>
 __device__ bool radd_small(const TRadd &t, const Piece *pieces, const LaunchArgs &a, int kself,
                            unsigned char *smem_raw, size_t smem_bytes, double delta) {
-    const int m = t.m, n = t.n, mn = min(m, n), mx = max(m, n);
-    const size_t need = sizeof(double) * ((size_t)m * n + (size_t)mx * mn + (size_t)mn * mn + 2 * mn + n + 40) +
-                        sizeof(int) * ((size_t)mn + n + 8);
-    // every launch provides radd_smem_bytes(64) >= the largest `need` of a target
-    // with m n <= kSmallTarget and m, n <= 128 (100704 bytes at m = n = 64), so
-    // the choice depends on the task alone
-    if ((int64_t)m * n > kSmallTarget || mx > 128 || need > smem_bytes) return false;
+    const int m = t.m, n = t.n;
+    if ((int64_t)m * n > kSmallTarget || max(m, n) > 128 || core_bytes<T>(m, n, false) > smem_bytes) return false;
     T *A = reinterpret_cast<T *>(a.arena);
     int32_t *kd = a.kdyn;
-    double *X = reinterpret_cast<double *>(smem_raw);
-    double *C = X + (size_t)m * n;  // n x r, later m x knew
-    double *J = C + (size_t)mx * mn;
-    double *tau = J + (size_t)mn * mn;
-    double *sig = tau + mn;
-    double *cn = sig + mn;
-    double *red = cn + n;
-    int *order = reinterpret_cast<int *>(red + 40);
-    int *perm = order + mn;
-    int *iflag = perm + n;
+    const CoreBufs<T> b = carve_core<T>(smem_raw, m, n, false);
     unsigned long long ph = phase_mark(a, 0, 0ull);
     // ---- X = U_c V_c^T + sum of the zero-padded contributions
     for (int e = threadIdx.x; e < m * n; e += blockDim.x) {
@@ -616,75 +972,23 @@ __device__ bool radd_small(const TRadd &t, const Piece *pieces, const LaunchArgs
             for (int l = 0; l < k; ++l) s += at(A, pc.U, ii, l) * at(A, pc.V, jj, l);
             acc += T(pc.coef) * s;
         }
-        X[e] = (double)acc;
+        b.M[e] = acc;
     }
     __syncthreads();
     ph = phase_mark(a, 0, ph);
-    // ---- X P = Q [R'; ~0], one-sided Jacobi on C = R'^T (n x r)
-    const int r = block_qrcp(X, m, n, tau, cn, perm, delta, red, iflag);
-    ph = phase_mark(a, 1, ph);
-    for (int e = threadIdx.x; e < n * r; e += blockDim.x) {
-        const int c = e % n, i = e / n;
-        C[e] = c >= i ? X[i + (size_t)c * m] : 0.0;
-    }
-    for (int e = threadIdx.x; e < r * r; e += blockDim.x) J[e] = (e % r == e / r) ? 1.0 : 0.0;
-    __syncthreads();
-    block_jacobi(C, n, r, J, iflag);
-    ph = phase_mark(a, 2, ph);
-    for (int j = threadIdx.x; j < r; j += blockDim.x) {
-        double s = 0.0;
-        for (int i = 0; i < n; ++i) s += C[i + (size_t)j * n] * C[i + (size_t)j * n];
-        sig[j] = sqrt(s);
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < r; j += blockDim.x) {
-        int rk = 0;
-        for (int l = 0; l < r; ++l) rk += (sig[l] > sig[j]) || (sig[l] == sig[j] && l < j);
-        order[rk] = j;
-    }
-    __syncthreads();
-    const double s1 = r > 0 ? sig[order[0]] : 0.0;
-    int knew = 0;
-    if (!isfinite(s1)) {
-        if (threadIdx.x == 0) set_error(a.err, DE_NONFINITE, t.target, s1);
-    } else if (s1 > 0.0) {
-        for (int l = 0; l < r; ++l) knew += sig[order[l]] > a.eps * s1;
-    }
-    if (knew > t.cap) {
-        if (threadIdx.x == 0) set_error(a.err, DE_RANKCAP, t.target, (double)knew);
-        knew = t.cap;
-    }
-    ph = phase_mark(a, 3, ph);
-    if (a.phase && threadIdx.x == 0) {  // Jacobi problem size: columns, rows
-        atomicAdd(a.phase + 6, (unsigned long long)r);
-        atomicAdd(a.phase + 7, 1ull);
-    }
-    // ---- V = P W_sel Sigma^{-1} (every row of V is covered by the permutation)
-    T *Uc = A + t.U_off;
-    T *Vc = A + t.V_off;
-    for (int e = threadIdx.x; e < n * knew; e += blockDim.x) {
-        const int i = e % n, c = e / n;
-        const int j = order[c];
-        Vc[perm[i] + (int64_t)c * n] = T(C[i + (size_t)j * n] / sig[j]);
-    }
-    __syncthreads();
-    // ---- U = Q [J_sel Sigma; 0] (C reused for the m x knew product)
-    for (int e = threadIdx.x; e < m * knew; e += blockDim.x) {
-        const int i = e % m, c = e / m;
-        const int j = order[c];
-        C[e] = i < r ? J[i + (size_t)j * r] * sig[j] : 0.0;
-    }
-    __syncthreads();
-    block_apply_qcp(X, m, r, tau, C, knew);
-    __syncthreads();
-    for (int e = threadIdx.x; e < m * knew; e += blockDim.x) Uc[e] = T(C[e]);
+    int r = 0;
+    const int knew = core_truncate<T>(b, m, n, delta, t, a, &r, 0, ph);
+    // the target's own factors were read above; every row of V is covered by P
+    core_write_v<T, T>(b, m, n, r, knew, A + t.V_off, n);
+    core_form_u<T>(b, m, r, knew);
+    for (int e = threadIdx.x; e < m * knew; e += blockDim.x) A[t.U_off + e] = b.C[e];
     if (threadIdx.x == 0) kd[t.kslot] = knew;
-    phase_mark(a, 4, ph);
+    phase_mark(a, 5, ph);
     return true;
 }
 
 // When even the core does not fit (K above the CTA's shared-memory capacity),
-// it is placed in `core_scratch` (global, radd_core_bytes(K) bytes).
+// it is placed in `core_scratch` (global, radd_smem_bytes(K) bytes).
 template <class T>
 __device__ void dev_radd(const TRadd &t, const Piece *pieces, const LaunchArgs &a, int kc, unsigned char *smem_raw,
                          T *scratch, size_t smem_bytes, unsigned char *core_scratch) {
@@ -712,122 +1016,93 @@ __device__ void dev_radd(const TRadd &t, const Piece *pieces, const LaunchArgs &
         if (threadIdx.x == 0) set_error(a.err, DE_RANKCAP, t.target, (double)K);
         return;
     }
-    const size_t core_bytes = (radd_core_bytes(K) + 15) & ~size_t(15);
-    const bool core_in_smem = core_bytes <= smem_bytes;
-    unsigned char *core = core_in_smem ? smem_raw : core_scratch;
-    double *M = reinterpret_cast<double *>(core);  // core, then QRCP reflectors
-    double *C = M + (size_t)K * K;                        // R'^T (kv x r), later Q_M [J Sigma; 0]
-    double *J = C + (size_t)K * K;                        // Jacobi rotations (r x r)
-    double *tauU = J + (size_t)K * K;
-    double *tauV = tauU + K;
-    double *tauM = tauV + K;
-    double *sig = tauM + K;
-    double *cn = sig + K;
-    double *red = cn + K;  // 40 doubles
-    int *order = reinterpret_cast<int *>(red + 40);
-    int *perm = order + K;
-    int *iflag = perm + K;  // 8 ints
+    const int ku = min(m, K), kv = min(n, K);
+    const size_t cbytes = (core_bytes<T>(ku, kv, true) + 15) & ~size_t(15);
+    const bool core_in_smem = cbytes <= smem_bytes;
     const size_t panel_bytes = (size_t)(m + n) * K * sizeof(T);
-    T *WU = core_in_smem && core_bytes + panel_bytes <= smem_bytes ? reinterpret_cast<T *>(smem_raw + core_bytes)
-                                                                    : scratch;
+    T *WU = core_in_smem && cbytes + panel_bytes <= smem_bytes ? reinterpret_cast<T *>(smem_raw + cbytes) : scratch;
     T *WV = WU + (int64_t)m * K;
+    unsigned long long ph = phase_mark(a, 8, 0ull);
     // ---- stack the factors
     for (int64_t e = threadIdx.x; e < (int64_t)(m + n) * K; e += blockDim.x) WU[e] = T(0);
     __syncthreads();
-    for (int e = threadIdx.x; e < m * kself; e += blockDim.x) WU[e] = A[t.U_off + e];
-    for (int e = threadIdx.x; e < n * kself; e += blockDim.x) WV[e] = A[t.V_off + e];
+    block_copy<T>(m * kself, [&](int e) { return A[t.U_off + e]; }, [&](int e, T v) { WU[e] = v; });
+    block_copy<T>(n * kself, [&](int e) { return A[t.V_off + e]; }, [&](int e, T v) { WV[e] = v; });
     int col = kself;
     for (int q = 0; q < t.npieces; ++q) {
         const Piece pc = pieces[t.piece0 + q];
         const int k = dim_c(pc.U, kd), mu = pc.U.rows, nv = pc.V.rows;
         const T coef = T(pc.coef);
-        for (int e = threadIdx.x; e < mu * k; e += blockDim.x) {
-            const int i = e % mu, j = e / mu;
-            WU[pc.roff + i + (int64_t)(col + j) * m] = coef * at(A, pc.U, i, j);
-        }
-        for (int e = threadIdx.x; e < nv * k; e += blockDim.x) {
-            const int i = e % nv, j = e / nv;
-            WV[pc.coff + i + (int64_t)(col + j) * n] = at(A, pc.V, i, j);
-        }
+        block_copy<T>(
+            mu * k, [&](int e) { return coef * at(A, pc.U, e % mu, e / mu); },
+            [&](int e, T v) { WU[pc.roff + e % mu + (int64_t)(col + e / mu) * m] = v; });
+        block_copy<T>(
+            nv * k, [&](int e) { return at(A, pc.V, e % nv, e / nv); },
+            [&](int e, T v) { WV[pc.coff + e % nv + (int64_t)(col + e / nv) * n] = v; });
         col += k;
     }
     __syncthreads();
-    // ---- QR of both stacks
-    block_householder_qr(WU, m, K, tauU, red);
-    block_householder_qr(WV, n, K, tauV, red);
-    const int ku = min(m, K), kv = min(n, K);
-    // ---- core M = R_u R_v^T (double)
+    ph = phase_mark(a, 8, ph);
+    const CoreBufs<T> b = carve_core<T>(core_in_smem ? smem_raw : core_scratch, ku, kv, true);
+    // ---- QR of both stacks (one half of the CTA each), core M = R_u R_v^T
+    const int half = (blockDim.x >> 5) / 2;
+    if ((int)(threadIdx.x >> 5) < half)
+        group_householder_qr(WU, m, K, b.tauU, b.nrmU, 0, half, 1);
+    else
+        group_householder_qr(WV, n, K, b.tauV, b.nrmV, half, half, 2);
+    __syncthreads();
     for (int e = threadIdx.x; e < ku * kv; e += blockDim.x) {
         const int i = e % ku, j = e / ku;
-        double s = 0.0;
-        for (int l = max(i, j); l < K; ++l) s += (double)WU[i + (int64_t)l * m] * (double)WV[j + (int64_t)l * n];
-        M[e] = s;
+        T s = T(0);
+        for (int l = max(i, j); l < K; ++l) s += WU[i + (int64_t)l * m] * WV[j + (int64_t)l * n];
+        b.M[e] = s;
     }
     __syncthreads();
-    // ---- M P = Q_M [R'; ~0], then one-sided Jacobi on C = R'^T (kv x r)
-    const int r = block_qrcp(M, ku, kv, tauM, cn, perm, delta, red, iflag);
-    for (int e = threadIdx.x; e < kv * r; e += blockDim.x) {
-        const int c = e % kv, i = e / kv;
-        C[e] = c >= i ? M[i + (size_t)c * ku] : 0.0;
-    }
-    for (int e = threadIdx.x; e < r * r; e += blockDim.x) J[e] = (e % r == e / r) ? 1.0 : 0.0;
-    __syncthreads();
-    block_jacobi(C, kv, r, J, iflag);
-    // ---- singular values, ordering, truncation rank
-    for (int j = threadIdx.x; j < r; j += blockDim.x) {
-        double s = 0.0;
-        for (int i = 0; i < kv; ++i) s += C[i + (size_t)j * kv] * C[i + (size_t)j * kv];
-        sig[j] = sqrt(s);
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < r; j += blockDim.x) {
-        int rk = 0;
-        for (int l = 0; l < r; ++l) rk += (sig[l] > sig[j]) || (sig[l] == sig[j] && l < j);
-        order[rk] = j;
-    }
-    __syncthreads();
-    const double s1 = r > 0 ? sig[order[0]] : 0.0;
-    int knew = 0;
-    if (!isfinite(s1)) {
-        if (threadIdx.x == 0) set_error(a.err, DE_NONFINITE, t.target, s1);
-    } else if (s1 > 0.0) {
-        for (int l = 0; l < r; ++l) knew += sig[order[l]] > a.eps * s1;
-    }
-    if (knew > t.cap) {
-        if (threadIdx.x == 0) set_error(a.err, DE_RANKCAP, t.target, (double)knew);
-        knew = t.cap;
-    }
+    ph = phase_mark(a, 9, ph);
+    int r = 0;
+    const int knew = core_truncate<T>(b, ku, kv, delta, t, a, &r, 8, ph);
     T *Uc = A + t.U_off;
     T *Vc = A + t.V_off;
-    // ---- V = Q_v [P W_sel Sigma^{-1}; 0]
-    for (int e = threadIdx.x; e < n * knew; e += blockDim.x) Vc[e] = T(0);
-    __syncthreads();
-    for (int e = threadIdx.x; e < kv * knew; e += blockDim.x) {
-        const int i = e % kv, c = e / kv;
-        const int j = order[c];
-        Vc[perm[i] + (int64_t)c * n] = T(C[i + (size_t)j * kv] / sig[j]);
+    // ---- V = Q_v [P R'^T B_sel Sigma^{-2}; 0]
+    core_write_v<T, T>(b, ku, kv, r, knew, Vc, n);
+    for (int e = threadIdx.x; e < (n - kv) * knew; e += blockDim.x) {
+        const int i = kv + e % (n - kv), c = e / (n - kv);
+        Vc[i + (int64_t)c * n] = T(0);
     }
-    __syncthreads();
-    // ---- U = Q_u [Q_M [J_sel Sigma; 0]; 0] (C now holds the ku x knew product)
-    for (int e = threadIdx.x; e < ku * knew; e += blockDim.x) {
-        const int i = e % ku, c = e / ku;
-        const int j = order[c];
-        C[e] = i < r ? J[i + (size_t)j * r] * sig[j] : 0.0;
-    }
-    __syncthreads();
-    block_apply_qcp(M, ku, r, tauM, C, knew);
-    __syncthreads();
+    // ---- U = Q_u [Q_M [B_sel; 0]; 0]
+    core_form_u<T>(b, ku, r, knew);
     for (int e = threadIdx.x; e < m * knew; e += blockDim.x) {
         const int i = e % m, c = e / m;
-        Uc[e] = i < ku ? T(C[i + (size_t)c * ku]) : T(0);
+        Uc[e] = i < ku ? b.C[i + (size_t)c * ku] : T(0);
     }
     __syncthreads();
-    block_apply_q(WU, m, ku, tauU, Uc, knew);
-    block_apply_q(WV, n, kv, tauV, Vc, knew);
+    for (int c = threadIdx.x >> 5; c < 2 * knew; c += blockDim.x >> 5) {  // U and V columns together
+        if (c < knew)
+            warp_apply_q(WU, m, ku, b.tauU, Uc + (int64_t)c * m);
+        else
+            warp_apply_q(WV, n, kv, b.tauV, Vc + (int64_t)(c - knew) * n);
+    }
     if (threadIdx.x == 0) {
         kd[t.kslot] = knew;
         add_flops(a, K_RADD, radd_model_flops(m, n, K, knew));
     }
+    phase_mark(a, 13, ph);
+}
+
+// Shared memory that every rounded-addition launch provides: the dense route's
+// worst case over m n <= kSmallTarget, m, n <= 128.
+template <class R>
+size_t radd_small_floor() {
+    static size_t s = 0;
+    if (s == 0)
+        for (int m = 1; m <= 128; ++m)
+            for (int n = 1; n <= 128 && m * n <= kSmallTarget; ++n) s = std::max(s, core_bytes<R>(m, n, false));
+    return s;
+}
+
+size_t radd_smem_bytes(int kc, int elem) {
+    if (elem == 8) return std::max(core_bytes<double>(kc, kc, true), radd_small_floor<double>());
+    return std::max(core_bytes<float>(kc, kc, true), radd_small_floor<float>());
 }
 
 // ------------------------------------------------------------ wave kernels
@@ -854,9 +1129,11 @@ __global__ void __launch_bounds__(kThreads) k_project(const TProject *tasks, Lau
 }
 
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_accum(const TAccum *tasks, const Term *terms, LaunchArgs a) {
+__global__ void __launch_bounds__(kThreads) k_accum(const TAccum *tasks, const Term *terms, LaunchArgs a,
+                                                    size_t smem_bytes) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const TAccum t = tasks[blockIdx.x];
-    dev_accum<T>(t, terms, a);
+    dev_accum<T>(t, terms, a, smem_raw, smem_bytes);
 }
 
 template <class T>
@@ -900,7 +1177,7 @@ __device__ __forceinline__ void st_release(int *p, int v) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_dataflow(FlowArgs f, LaunchArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) k_dataflow(FlowArgs f, LaunchArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_task;
     T *scratch = reinterpret_cast<T *>(f.scratch) + (int64_t)blockIdx.x * f.scratch_stride;
@@ -951,7 +1228,7 @@ __global__ void __launch_bounds__(kThreads) k_dataflow(FlowArgs f, LaunchArgs a)
             }
             case K_ACCUM: {
                 const TAccum t = f.accum[idx];
-                dev_accum<T>(t, f.terms, a);
+                dev_accum<T>(t, f.terms, a, smem_raw, f.smem_bytes);
                 break;
             }
             case K_RADD: {
@@ -1083,20 +1360,21 @@ void launch_kind(int kind, const void *tasks, const Term *terms, const Piece *pi
                 reinterpret_cast<const TGetrf *>(tasks) + start, a);
             break;
         case K_TRSM:
-            k_trsm<T><<<count, kThreads, getrf_smem_bytes(aux, sizeof(T)), s>>>(
+            k_trsm<T><<<count, kThreads, trsm_smem_bytes(aux, sizeof(T)), s>>>(
                 reinterpret_cast<const TTrsm *>(tasks) + start, a);
             break;
         case K_PROJECT:
-            k_project<T><<<count, kThreads, 2 * 32 * 65 * sizeof(T), s>>>(
+            k_project<T><<<count, kThreads, project_smem_bytes(sizeof(T)), s>>>(
                 reinterpret_cast<const TProject *>(tasks) + start, a);
             break;
         case K_ACCUM:
-            k_accum<T><<<count, kThreads, 0, s>>>(reinterpret_cast<const TAccum *>(tasks) + start, terms, a);
+            k_accum<T><<<count, kThreads, accum_smem_bytes(sizeof(T)), s>>>(reinterpret_cast<const TAccum *>(tasks) + start,
+                                                                          terms, a, accum_smem_bytes(sizeof(T)));
             break;
         case K_RADD: {
-            // at least the dense route's worst case (m n <= kSmallTarget) so that the
+            // includes the dense route's worst case (radd_small_floor), so that the
             // route a task takes does not depend on the schedule
-            const size_t smem = std::max(radd_smem_bytes(aux), radd_smem_bytes(64));
+            const size_t smem = radd_smem_bytes(aux, sizeof(T));
             k_radd<T><<<count, kThreads, smem, s>>>(reinterpret_cast<const TRadd *>(tasks) + start, pieces, a, aux,
                                                     smem);
             break;
@@ -1127,6 +1405,7 @@ bool set_kernel_attributes() {
     ok = allow_dynamic_smem(k_getrf<T>, optin) && ok;
     ok = allow_dynamic_smem(k_trsm<T>, optin) && ok;
     ok = allow_dynamic_smem(k_project<T>, optin) && ok;
+    ok = allow_dynamic_smem(k_accum<T>, optin) && ok;
     ok = allow_dynamic_smem(k_dataflow<T>, optin) && ok;
     cudaGetLastError();  // a failure is reported through the return value, not left pending
     return ok;
@@ -1134,8 +1413,10 @@ bool set_kernel_attributes() {
 
 size_t dataflow_smem_bytes(int max_leaf, int elem, int kc) {
     size_t s = getrf_smem_bytes(max_leaf, elem);
-    s = std::max(s, (size_t)2 * 32 * 65 * elem);
-    s = std::max(s, radd_smem_bytes(kc));
+    s = std::max(s, trsm_smem_bytes(max_leaf, elem));
+    s = std::max(s, project_smem_bytes(elem));
+    s = std::max(s, accum_smem_bytes(elem));
+    s = std::max(s, radd_smem_bytes(kc, elem));
     return s;
 }
 

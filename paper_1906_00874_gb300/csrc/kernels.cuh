@@ -16,7 +16,7 @@ struct LaunchArgs {
     long long *err;     // error word: code, index, value bits, count
     double eps;         // truncation tolerance (rounded addition)
     double *flops;      // model flops per task kind (K_NKINDS doubles), accumulated
-    unsigned long long *phase;  // when profiling: nanoseconds per rounded-addition phase (8), else null
+    unsigned long long *phase;  // when profiling: rounded-addition phase counters (16), else null
     int32_t kmax;       // largest stacked rank the core buffers hold
 };
 
@@ -79,7 +79,9 @@ void launch_add_from_work(double *x, const T *y, int64_t n, int32_t nc, cudaStre
 void launch_residual(const double *b, const double *ax, double *r, int64_t n, int32_t nc, double *nrm2,
                      double *bn2, cudaStream_t s);
 
-size_t radd_smem_bytes(int kcap);
+// Shared memory of a rounded addition whose stacked rank is at most kcap, with
+// factors of elem bytes (also the dense route's worst case).
+size_t radd_smem_bytes(int kcap, int elem);
 size_t getrf_smem_bytes(int max_leaf, int elem);
 
 }  // namespace hlu

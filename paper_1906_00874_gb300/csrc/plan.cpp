@@ -783,6 +783,10 @@ int Planner::build(int32_t n_, int32_t n_clusters, const int32_t *perm_, const i
             lc_ids.push_back(c);
             max_leaf = std::max(max_leaf, cl[c].size);
         }
+    if (max_leaf > kMaxLeafRows) {
+        error = "leaf cluster larger than 128 indices";
+        return HLU_EINVAL;
+    }
     for (auto it = order.rbegin(); it != order.rend(); ++it) {
         int32_t c = *it;
         if (cl[c].son0 >= 0) {

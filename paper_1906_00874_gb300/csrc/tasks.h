@@ -19,6 +19,9 @@ struct Panel {
     int32_t rs, cs;
 };
 
+// Largest leaf cluster (rows of a dense diagonal leaf) the kernels handle.
+constexpr int32_t kMaxLeafRows = 128;
+
 enum Kind : int32_t {
     K_GETRF = 0,    // unpivoted LU of a dense diagonal leaf (O1.1, Sec. 3.1 "Dense blocks")
     K_TRSM = 1,     // triangular solve of a panel with a dense diagonal leaf (O1.2/O1.3)

@@ -25,7 +25,8 @@ STATUS = {0: "HLU_OK", 1: "HLU_EINVAL", 2: "HLU_ENOMEM", 3: "HLU_ESTATE", 4: "HL
 EXPORTS = ("hlu_create", "hlu_factor", "hlu_solve", "hlu_matvec", "hlu_solve_refined", "hlu_factor_doubles",
            "hlu_get_factors", "hlu_get_stats", "hlu_set_profiling", "hlu_destroy", "hlu_strerror",
            "hlu_last_error_detail", "hlu_last_cuda_error", "hlu_probe_alu_peaks")
-KINDS = ("getrf", "trsm", "project", "accum", "radd", "split", "dataflow_factor", "dataflow_solve")
+KINDS = ("getrf", "trsm", "project", "accum", "radd", "split", "dataflow_factor", "dataflow_solve",
+         "dataflow_matvec")
 
 
 class HLUError(RuntimeError):
@@ -57,19 +58,25 @@ class Stats(ctypes.Structure):
                 ("solve_launches", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
                 ("tasks_by_kind", ctypes.c_int64 * 8), ("model_flops", ctypes.c_double),
                 ("flops_by_kind", ctypes.c_double * 8), ("solve_flops", ctypes.c_double),
-                ("kernel_ms", ctypes.c_double * 8), ("kernel_launches", ctypes.c_int64 * 8),
+                ("kernel_ms", ctypes.c_double * 10), ("kernel_launches", ctypes.c_int64 * 10),
                 ("task_busy_ms", ctypes.c_double * 8), ("task_count", ctypes.c_int64 * 8),
                 ("radd_busy_ms", ctypes.c_double * 8), ("radd_count", ctypes.c_int64 * 8),
-                ("radd_phase", ctypes.c_double * 8),
+                ("solve_busy_ms", ctypes.c_double * 8), ("solve_task_count", ctypes.c_int64 * 8),
+                ("radd_phase", ctypes.c_double * 16),
                 ("kernels_launched", ctypes.c_int64), ("max_rank", ctypes.c_int32), ("max_stacked", ctypes.c_int32)]
 
     def as_dict(self):
-        per_kind = ("tasks_by_kind", "flops_by_kind", "kernel_ms", "kernel_launches", "task_busy_ms", "task_count")
+        per_kind = ("tasks_by_kind", "flops_by_kind", "kernel_ms", "kernel_launches", "task_busy_ms", "task_count",
+                    "solve_busy_ms", "solve_task_count")
         per_size = ("radd_busy_ms", "radd_count")
         d = {f: getattr(self, f) for f, _ in self._fields_ if f not in per_kind + per_size + ("radd_phase",)}
         ph = list(self.radd_phase)
-        d["radd_phase"] = {"form_ms": ph[0], "qrcp_ms": ph[1], "jacobi_ms": ph[2], "order_ms": ph[3],
-                           "factors_ms": ph[4], "mean_jacobi_cols": ph[6] / max(ph[7], 1), "tasks": ph[7]}
+        d["radd_phase"] = {}
+        for route, b in (("dense", 0), ("stacked", 8)):
+            d["radd_phase"][route] = {"form_ms": ph[b], "stack_qr_ms": ph[b + 1], "qrcp_ms": ph[b + 2],
+                                      "jacobi_ms": ph[b + 3], "factors_ms": ph[b + 5],
+                                      "mean_jacobi_sweeps": ph[b + 4] / max(ph[b + 7], 1),
+                                      "mean_jacobi_r": ph[b + 6] / max(ph[b + 7], 1), "tasks": ph[b + 7]}
         for f in per_kind:
             d[f] = dict(zip(KINDS, list(getattr(self, f))[:len(KINDS)]))
         sizes = ("<128", "<256", "<512", "<1024", "<2048", "<4096", "<8192", ">=8192")

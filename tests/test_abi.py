@@ -112,3 +112,12 @@ def test_rejects_dense_block_between_split_clusters(lib, prob1280):
     off = prob1280.offset.copy()
     off[l] = prob1280.data.shape[0]
     _expect_einval(prob1280, kind=kind, data=data, offset=off)
+
+
+def test_rejects_leaf_cluster_above_128(lib):
+    """One dense 200 x 200 leaf: the leaf kernels handle at most 128 rows."""
+    from paper_1906_00874_gb300.hlu import HLU, HLUError
+    n = 200
+    with pytest.raises(HLUError) as e:
+        HLU(n, np.arange(n), [0], [n], [-1], [-1], [0], [0], [0], [0], [0], np.eye(n).ravel(order="F"), stream=0)
+    assert e.value.status == 1
