@@ -167,6 +167,26 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def recorded_traffic(dom, a_h_bytes):
+    """DRAM bytes per launch of the factorisation kernel from the committed ncu summary
+    (profiles/traffic.json), scaled by A_H bytes; None when the kernel source changed since."""
+    import hashlib
+    here = os.path.dirname(os.path.abspath(__file__))
+    try:
+        rec = json.load(open(os.path.join(here, "profiles", "traffic.json")))
+        src = open(os.path.join(here, rec["source"]), "rb").read()
+    except (OSError, ValueError, KeyError):
+        return None, "no ncu record"
+    if dom != "dataflow_factor":
+        return None, "ncu record is for the factorisation kernel"
+    if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
+        return None, "kernel source changed since the ncu capture"
+    dram = rec["dram_bytes_read"] + rec["dram_bytes_write"]
+    scale = a_h_bytes / rec["captured_a_h_bytes"]
+    return dram * scale, (f"ncu dram bytes of one launch on {rec['captured_workload']} x {scale:.3f} "
+                          f"(A_H bytes ratio), {rec['summary']}")
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -312,8 +332,10 @@ def run_native(args):
     # algorithmic bytes of the factorisation: read A_H once (FP64) and write the factors once (FP32)
     alg_bytes = 1.5 * p.data.nbytes if dom == "dataflow_factor" else None
     hbm_peak = measured_peaks().get("hbm_gbs", 6800.0)
+    traffic, traffic_note = recorded_traffic(dom, p.data.nbytes)
     roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp32_peak if fp32_peak else None, "traffic": None,
+            "frac": achieved / fp32_peak if fp32_peak else None, "traffic": traffic,
+            "traffic_source": traffic_note,
             "peak_source": "measured FP32 FMA probe (hlu_probe_alu_peaks), of measured",
             "model_gflop_per_launch": dom_flops / 1e9 / max(launches, 1e-9),
             "avg_launch_ms": dom_ms / max(launches, 1e-9), "launches_per_step": launches,
@@ -348,8 +370,8 @@ def run_native(args):
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 truncation cores and residual)",
             "data": "synthetic",
-            "config": {"workload": f"{args.workload}: icosphere r=5, n={p.n}, leaf 64, eta=2, eps=1e-4, "
-                                   f"{p.nrhs} rhs ~ N(0,1) seed 0, tol 1e-10",
+            "config": {"workload": f"{args.workload}: icosphere r={w['r']}, n={p.n}, leaf {w['leaf']}, "
+                                   f"eta={w['eta']:g}, eps={w['eps']:g}, {p.nrhs} rhs ~ N(0,1) seed 0, tol 1e-10",
                        "n": p.n, "leaves": p.n_leaves, "nrhs": p.nrhs, "l2": "inputs larger than L2 (factor arena "
                        f"{st32['device_bytes'] / 1e9:.1f} GB)", "parallelism": f"replicas x{world}"},
             "time_to_1e10_ms": t_ms / args.steps, "solves_per_s": p.nrhs * args.steps * world / (t_ms * 1e-3),
