@@ -150,6 +150,26 @@ int hlu_get_factors(hlu_t h, int32_t *rank_out, int64_t *offsets_out, double *da
 int hlu_solve_refined(hlu_t h, const double *b_dev, double *x_dev, int32_t nrhs, int64_t ld, double tol,
                       int32_t max_iter, int32_t *iters_out, double *resid_out);
 
+/* Restarted GMRES(m) (Saad and Schultz 1986) in FP64 on A_H x = b with the
+ * original H-matrix, right-preconditioned by the factorisation: the Krylov
+ * space is built from A_H U^{-1} L^{-1} (the factors in their precision, the
+ * solve of Sec. 3.1), orthogonalised by two classical Gram-Schmidt passes, and
+ * x = U^{-1} L^{-1} V y with y from the Givens-reduced Hessenberg system.  All
+ * columns advance in lockstep from x = 0; a cycle stops after `restart` steps
+ * or when every column's residual estimate meets tol ||b_j||_2; each cycle
+ * starts from the true FP64 residual.  The preconditioning in the mixed form
+ * is the paper's factorisation used for the "GMRES" configuration of the
+ * mixed-precision variant (no counterpart in the paper itself, which solves
+ * directly).  b and x are DEVICE pointers to n x nrhs FP64 panels (column-major,
+ * leading dimension ld >= n, original order, not overlapping); 1 <= restart <= 256.
+ * *iters_out (may be NULL) gets the number of Arnoldi steps (one solve and one
+ * H-matvec each; largest over column chunks), *resid_out (may be NULL) the largest
+ * true relative residual at the end.  The first call allocates the Krylov bases,
+ * 2 (restart + 1) n nrhs_max doubles (HLU_ENOMEM beyond opts.mem_budget).
+ * Returns HLU_OK even when tol is not reached within max_iter steps. */
+int hlu_solve_gmres(hlu_t h, const double *b_dev, double *x_dev, int32_t nrhs, int64_t ld, double tol,
+                    int32_t restart, int32_t max_iter, int32_t *iters_out, double *resid_out);
+
 /* Statistics of the plan and of the last calls.  Model flops use the standard
  * operation counts (getrf 2m^3/3, trsm m^2 p, gemm 2mkp, Householder QR
  * 2 a b^2 - 2 b^3/3, Jacobi SVD 21 K^3, Q times a panel 2mKk'), counted on the

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/hlu.h"
+#include "gmres.cuh"
 #include "kernels.cuh"
 #include "plan.h"
 
@@ -78,6 +79,9 @@ struct hlu_ctx {
     int64_t *leaf_desc = nullptr;
     double *ir = nullptr;     // refinement work: b, x, r (n x nrhs_max each) and 2 x nrhs_max norms
     double *ir_host = nullptr;  // pinned copy of the norms
+    // GMRES: Krylov bases V ((m + 1) panels) and Z = M^{-1} V (m panels) of n x nrhs_max, small state
+    int gm_m = 0;
+    double *gm_V = nullptr, *gm_Z = nullptr, *gm_small = nullptr, *gm_host = nullptr;
     DevPlan fp, sp, mp;
     int64_t device_bytes = 0;
     int64_t mem_budget = 0;
@@ -619,6 +623,133 @@ int hlu_solve_refined(hlu_t h, const double *b, double *x, int32_t nrhs, int64_t
     return st;
 }
 
+int hlu_solve_gmres(hlu_t h, const double *b, double *x, int32_t nrhs, int64_t ld, double tol, int32_t restart,
+                    int32_t max_iter, int32_t *iters_out, double *resid_out) {
+    if (!h || nrhs < 0 || ld < h->pl.n || max_iter < 0 || !(tol >= 0.0) || restart < 1 || restart > 256)
+        return HLU_EINVAL;
+    if (!h->factored) return HLU_ESTATE;
+    if (iters_out) *iters_out = 0;
+    if (resid_out) *resid_out = 0.0;
+    if (nrhs == 0) return HLU_OK;
+    if (!b || !x) return HLU_EINVAL;
+    int st = clear_error(h);
+    if (st) return st;
+    const int64_t n = h->pl.n;
+    const int32_t w = h->pl.opt.nrhs_max, m = restart;
+    if (h->gm_m < m) {  // Krylov bases and the small per-column state, kept for later calls
+        const int64_t small = int64_t(w) * ((m + 1) * m + 2 * m + 4 * (m + 1) + 4);
+        if ((st = dalloc(h, &h->gm_V, size_t(m + 1) * n * w))) return st;
+        if ((st = dalloc(h, &h->gm_Z, size_t(m) * n * w))) return st;
+        if ((st = dalloc(h, &h->gm_small, size_t(small)))) return st;
+        if (!h->gm_host &&
+            (st = cuda_status(cudaMallocHost(reinterpret_cast<void **>(&h->gm_host), 2 * w * sizeof(double)))))
+            return st;
+        h->gm_m = m;
+    }
+    const int64_t vs = n * w;  // stride between basis panels
+    GmState gs;
+    gs.m = m;
+    gs.H = h->gm_small;
+    gs.cs = gs.H + int64_t(w) * (m + 1) * m;
+    gs.sn = gs.cs + int64_t(w) * m;
+    gs.g = gs.sn + int64_t(w) * m;
+    gs.inv = gs.g + int64_t(w) * (m + 1);
+    gs.est = gs.inv + w;
+    double *t1 = gs.est + w, *t2 = t1 + int64_t(w) * (m + 1), *nrmd = t2 + int64_t(w) * (m + 1);
+    double *bc = h->ir, *xc = bc + n * w, *rc = xc + n * w, *nrm = rc + n * w;
+    double *AX = h->aarena + h->pl.a_x_off, *AY = h->aarena + h->pl.a_y_off;
+    int32_t it_max = 0;
+    double res_max = 0.0;
+    for (int32_t j0 = 0; j0 < nrhs; j0 += w) {
+        const int32_t nc = std::min(w, nrhs - j0);
+        const size_t bytes = sizeof(double) * n * nc;
+        launch_permute<double, double>(h->perm, (int32_t)n, nc, b + (int64_t)j0 * ld, ld, bc, n, 1, h->stream);
+        cudaMemsetAsync(xc, 0, bytes, h->stream);
+        int32_t it = 0;
+        double res = 0.0;
+        std::vector<double> bn(nc, 0.0);
+        for (;;) {
+            // true residual r = b - A_H x of the cycle's start
+            cudaMemcpyAsync(AX, xc, bytes, cudaMemcpyDeviceToDevice, h->stream);
+            matvec_pass(h, nc);
+            cudaMemsetAsync(nrm, 0, 2 * w * sizeof(double), h->stream);
+            launch_residual(bc, AY, rc, n, nc, nrm, nrm + w, h->stream);
+            cudaMemcpyAsync(h->ir_host, nrm, 2 * w * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+            if ((st = read_error(h))) {
+                h->last_status = st;
+                return st;
+            }
+            res = 0.0;
+            for (int32_t j = 0; j < nc; ++j) {
+                bn[j] = std::sqrt(h->ir_host[w + j]);
+                const double rj = bn[j] > 0.0 ? std::sqrt(h->ir_host[j]) / bn[j] : std::sqrt(h->ir_host[j]);
+                res = std::max(res, rj);
+            }
+            if (!std::isfinite(res) || res <= tol || it >= max_iter) break;
+            // v_0 = r / |r|, g = |r| e_1
+            gm_dots(rc, 0, 1, rc, n, nc, nrmd, 1, h->stream);
+            gm_start(nrmd, gs, nc, h->stream);
+            gm_scale(rc, gs.inv, h->gm_V, n, nc, h->stream);
+            int k = 0;
+            for (int j = 0; j < m && it < max_iter; ++j) {
+                double *Vj = h->gm_V + j * vs, *Zj = h->gm_Z + j * vs;
+                // z_j = U^{-1} L^{-1} v_j (the factors in their precision)
+                if (h->precision == HLU_FP64) {
+                    double *Y = (double *)h->farena + h->pl.f_solve_off;
+                    launch_to_work<double>(Vj, Y, n, nc, h->stream);
+                    solve_pass(h, nc);
+                    cudaMemsetAsync(Zj, 0, bytes, h->stream);
+                    launch_add_from_work<double>(Zj, Y, n, nc, h->stream);
+                } else {
+                    float *Y = (float *)h->farena + h->pl.f_solve_off;
+                    launch_to_work<float>(Vj, Y, n, nc, h->stream);
+                    solve_pass(h, nc);
+                    cudaMemsetAsync(Zj, 0, bytes, h->stream);
+                    launch_add_from_work<float>(Zj, Y, n, nc, h->stream);
+                }
+                // w = A_H z_j, orthogonalised against v_0 .. v_j (two classical Gram-Schmidt passes)
+                cudaMemcpyAsync(AX, Zj, bytes, cudaMemcpyDeviceToDevice, h->stream);
+                matvec_pass(h, nc);
+                gm_dots(h->gm_V, vs, j + 1, AY, n, nc, t1, m + 1, h->stream);
+                gm_axpy(h->gm_V, vs, j + 1, t1, m + 1, -1.0, AY, n, nc, h->stream);
+                gm_dots(h->gm_V, vs, j + 1, AY, n, nc, t2, m + 1, h->stream);
+                gm_axpy(h->gm_V, vs, j + 1, t2, m + 1, -1.0, AY, n, nc, h->stream);
+                gm_dots(AY, 0, 1, AY, n, nc, nrmd, 1, h->stream);
+                gm_arnoldi(t1, t2, nrmd, gs, j, nc, h->stream);
+                gm_scale(AY, gs.inv, h->gm_V + (j + 1) * vs, n, nc, h->stream);
+                h->kernels_launched += 11;
+                ++it;
+                k = j + 1;
+                cudaMemcpyAsync(h->gm_host, gs.est, nc * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+                if ((st = read_error(h))) {
+                    h->last_status = st;
+                    return st;
+                }
+                bool done = true;
+                for (int32_t c = 0; c < nc; ++c) {
+                    const double e = h->gm_host[c];
+                    if (!std::isfinite(e)) done = true;
+                    else if (e > tol * bn[c]) done = false;
+                }
+                if (done) break;
+            }
+            // x += Z y, y = R^{-1} g
+            gm_hsolve(gs, k, t1, nc, h->stream);
+            gm_axpy(h->gm_Z, vs, k, t1, m + 1, 1.0, xc, n, nc, h->stream);
+            h->kernels_launched += 6;
+        }
+        launch_permute<double, double>(h->perm, (int32_t)n, nc, xc, n, x + (int64_t)j0 * ld, ld, 0, h->stream);
+        h->kernels_launched += 2;
+        it_max = std::max(it_max, it);
+        res_max = std::max(res_max, res);
+    }
+    st = read_error(h);
+    h->last_status = st;
+    if (iters_out) *iters_out = it_max;
+    if (resid_out) *resid_out = res_max;
+    return st;
+}
+
 int64_t hlu_factor_doubles(hlu_t h) {
     if (!h) return -1;
     int64_t tot = 0;
@@ -748,6 +879,7 @@ void hlu_destroy(hlu_t h) {
     for (cudaEvent_t e : h->free_events) cudaEventDestroy(e);
     for (void *p : h->allocs) cudaFree(p);
     if (h->ir_host) cudaFreeHost(h->ir_host);
+    if (h->gm_host) cudaFreeHost(h->gm_host);
     delete h;
 }
 

@@ -22,7 +22,8 @@ SCHED_WAVES = 1
 STATUS = {0: "HLU_OK", 1: "HLU_EINVAL", 2: "HLU_ENOMEM", 3: "HLU_ESTATE", 4: "HLU_EPIVOT",
           5: "HLU_ERANKCAP", 6: "HLU_ETIMEOUT", 7: "HLU_ECUDA", 8: "HLU_ENUMERIC"}
 
-EXPORTS = ("hlu_create", "hlu_factor", "hlu_solve", "hlu_matvec", "hlu_solve_refined", "hlu_factor_doubles",
+EXPORTS = ("hlu_create", "hlu_factor", "hlu_solve", "hlu_matvec", "hlu_solve_refined", "hlu_solve_gmres",
+           "hlu_factor_doubles",
            "hlu_get_factors", "hlu_get_stats", "hlu_set_profiling", "hlu_destroy", "hlu_strerror",
            "hlu_last_error_detail", "hlu_last_cuda_error", "hlu_probe_alu_peaks")
 KINDS = ("getrf", "trsm", "project", "accum", "radd", "split", "dataflow_factor", "dataflow_solve",
@@ -103,6 +104,7 @@ def load(path=LIB_PATH):
     lib.hlu_solve.argtypes = [vp, vp, i32, i64]
     lib.hlu_matvec.argtypes = [vp, vp, vp, i32, i64]
     lib.hlu_solve_refined.argtypes = [vp, vp, vp, i32, i64, dbl, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl)]
+    lib.hlu_solve_gmres.argtypes = [vp, vp, vp, i32, i64, dbl, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl)]
     lib.hlu_set_profiling.argtypes = [vp, i32]
     lib.hlu_probe_alu_peaks.argtypes = [ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
     lib.hlu_factor_doubles.argtypes = [vp]
@@ -235,6 +237,20 @@ class HLU:
         self._check(load().hlu_solve_refined(self._h, ctypes.c_void_p(pb), ctypes.c_void_p(px), nrhs, ldb,
                                              float(tol), int(max_iter), ctypes.byref(it), ctypes.byref(res)),
                     "hlu_solve_refined")
+        return it.value, res.value
+
+    def solve_gmres(self, b, x, tol=1e-10, restart=30, max_iter=300):
+        """x = GMRES(restart) solution of A_H x = b in FP64, right-preconditioned by the factors
+        (CUDA float64 panels, same layout); returns (Arnoldi steps, largest relative residual)."""
+        pb, nrhs, ldb = _dev_ptr_and_ld(b, self.n, "b")
+        px, nrhs2, ldx = _dev_ptr_and_ld(x, self.n, "x")
+        if nrhs != nrhs2 or ldb != ldx:
+            raise ValueError("b and x must have the same shape and leading dimension")
+        it = ctypes.c_int32()
+        res = ctypes.c_double()
+        self._check(load().hlu_solve_gmres(self._h, ctypes.c_void_p(pb), ctypes.c_void_p(px), nrhs, ldb,
+                                           float(tol), int(restart), int(max_iter), ctypes.byref(it),
+                                           ctypes.byref(res)), "hlu_solve_gmres")
         return it.value, res.value
 
     def set_profiling(self, on):
