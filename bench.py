@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--impl", default="native", choices=("native", "reference"))
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison arm")
+    ap.add_argument("--solver", default="ir", choices=("ir", "gmres"),
+                    help="FP64 iteration preconditioned by the factors: refinement or GMRES(restart)")
+    ap.add_argument("--restart", type=int, default=30)
     return ap.parse_args()
 
 
@@ -53,8 +56,14 @@ def dist_env():
 
 
 # ----------------------------------------------------------------- CPU side
-CPU_SAMPLE_LEVEL = 2   # diagonal block of a level-2 cluster (about n/4 unknowns)
-REF_SAMPLE_LEVEL = 3   # reference arm: a level-3 block per step (bounded run time)
+CPU_SAMPLE_N = 5120    # CPU baseline: the leading diagonal block of about this many unknowns
+REF_SAMPLE_N = 2560    # reference arm: a smaller block per step (bounded run time)
+
+
+def sample_level(n, target):
+    """Cluster-tree level whose leading block has about `target` unknowns (bisection halves n)."""
+    import math
+    return max(0, int(round(math.log2(max(n, 1) / target))))
 
 
 def _oracle_sample_worker(workload, level, reps):
@@ -92,11 +101,13 @@ def run_reference(args):
     if rank != 0:
         return
     reps = args.warmup + args.steps
-    res = oracle_sample(args.workload, REF_SAMPLE_LEVEL, reps)
+    from bem_inputs import WORKLOADS
+    level = sample_level(20 * 4 ** WORKLOADS[args.workload]["r"], REF_SAMPLE_N)
+    res = oracle_sample(args.workload, level, reps)
     ts = res["times"][args.warmup:]
     step = sum(ts) / len(ts)
     gflops = res["flops"] / step / 1e9
-    sample = (f"FP64 oracle H-LU of the leading level-{REF_SAMPLE_LEVEL} diagonal block (n={res['n']}, "
+    sample = (f"FP64 oracle H-LU of the leading level-{level} diagonal block (n={res['n']}, "
               f"{res['leaves']} leaves) of the {args.workload} H-matrix per step, factor only, 1 thread")
     line = {
         "impl": "reference", "metric": METRIC, "value": gflops, "unit": "GFLOP/s", "n_gpus": args.gpus,
@@ -167,9 +178,10 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def recorded_traffic(dom, a_h_bytes):
+def recorded_traffic(dom, a_h_bytes, eps, leaf):
     """DRAM bytes per launch of the factorisation kernel from the committed ncu summary
-    (profiles/traffic.json), scaled by A_H bytes; None when the kernel source changed since."""
+    (profiles/traffic.json), scaled by A_H bytes; None when the kernel source changed since or
+    the workload's truncation tolerance or leaf size differs from the captured one."""
     import hashlib
     here = os.path.dirname(os.path.abspath(__file__))
     try:
@@ -181,10 +193,39 @@ def recorded_traffic(dom, a_h_bytes):
         return None, "ncu record is for the factorisation kernel"
     if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
         return None, "kernel source changed since the ncu capture"
+    if eps != rec["captured_eps"] or leaf != rec["captured_leaf"]:
+        return None, "ncu record taken at another truncation tolerance or leaf size"
     dram = rec["dram_bytes_read"] + rec["dram_bytes_write"]
     scale = a_h_bytes / rec["captured_a_h_bytes"]
     return dram * scale, (f"ncu dram bytes of one launch on {rec['captured_workload']} x {scale:.3f} "
                           f"(A_H bytes ratio), {rec['summary']}")
+
+
+def class_roofline(st, prof, nprof, fp32_peak):
+    """Per task class of the factorisation: model flops over the summed task time (the rate of one
+    worker CTA while it runs that class) against one worker's share of the FP32 FMA peak
+    (two worker CTAs per SM)."""
+    import torch
+    workers = 2 * torch.cuda.get_device_properties(0).multi_processor_count
+    per_worker = fp32_peak * 1e12 / workers
+    out = {}
+    for k, busy in prof["task_busy_ms"].items():
+        fl = st["flops_by_kind"].get(k, 0.0)
+        if busy <= 0 or fl <= 0:
+            continue
+        rate = fl / (busy / nprof * 1e-3)
+        out[k] = {"model_gflop": fl / 1e9, "busy_ms": busy / nprof, "gflops_per_worker": rate / 1e9,
+                  "frac_of_worker_fp32_peak": rate / per_worker}
+    return out
+
+
+def rank_hist(st):
+    """Ranks of the low-rank leaves of L and U after the factorisation: {rank: count}, '>32' last."""
+    h = list(st.get("rank_hist", []))
+    out = {str(k): int(v) for k, v in enumerate(h[:33]) if v}
+    if len(h) > 33 and h[33]:
+        out[">32"] = int(h[33])
+    return out
 
 
 def measured_peaks():
@@ -244,7 +285,10 @@ def run_native(args):
 
     def step(h):
         h.factor(p.eps)
-        it, res = h.solve_refined(b, x, tol=TOL, max_iter=30)
+        if args.solver == "gmres":
+            it, res = h.solve_gmres(b, x, tol=TOL, restart=args.restart, max_iter=300)
+        else:
+            it, res = h.solve_refined(b, x, tol=TOL, max_iter=30)
         return it, res
 
     def timed_arm(h, steps, warmup):
@@ -310,7 +354,7 @@ def run_native(args):
         h64.close()
 
     # ---------------- end to end through the public API with host buffers
-    e2e = e2e_arm(p, HLU_FP32, sptr, min(args.steps, 3), f32)
+    e2e = e2e_arm(p, HLU_FP32, sptr, min(args.steps, 3), f32, args.solver, args.restart)
 
     # ---------------- roofline of the dominant kernel (profiled pass, CUDA events on the stream)
     fp64_peak, fp32_peak = probe_alu_peaks()
@@ -332,7 +376,7 @@ def run_native(args):
     # algorithmic bytes of the factorisation: read A_H once (FP64) and write the factors once (FP32)
     alg_bytes = 1.5 * p.data.nbytes if dom == "dataflow_factor" else None
     hbm_peak = measured_peaks().get("hbm_gbs", 6800.0)
-    traffic, traffic_note = recorded_traffic(dom, p.data.nbytes)
+    traffic, traffic_note = recorded_traffic(dom, p.data.nbytes, p.eps, w["leaf"])
     roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": achieved / fp32_peak if fp32_peak else None, "traffic": traffic,
             "traffic_source": traffic_note,
@@ -346,6 +390,7 @@ def run_native(args):
                 "peak_gbs": hbm_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (fallback 6800)"},
             "kernel_ms_per_step": {k: v / nprof for k, v in ms.items()},
             "task_busy_ms_per_factor": {k: v / nprof for k, v in prof["task_busy_ms"].items() if v},
+            "classes": class_roofline(st32, prof, nprof, fp32_peak),
             "tasks_per_factor": {k: v // nprof for k, v in prof["task_count"].items() if v},
             "radd_busy_ms_by_size": {k: round(v / nprof, 1) for k, v in prof["radd_busy_ms"].items() if v},
             "radd_count_by_size": {k: v // nprof for k, v in prof["radd_count"].items() if v},
@@ -356,9 +401,10 @@ def run_native(args):
     cpu = None
     if rank == 0:
         try:
-            res = oracle_sample(args.workload, CPU_SAMPLE_LEVEL, 1)
+            level = sample_level(p.n, CPU_SAMPLE_N)
+            res = oracle_sample(args.workload, level, 1)
             cpu = {"value": res["flops"] / res["times"][0] / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-                   "sample": (f"FP64 oracle H-LU (factor only) of the leading level-{CPU_SAMPLE_LEVEL} diagonal "
+                   "sample": (f"FP64 oracle H-LU (factor only) of the leading level-{level} diagonal "
                               f"block, n={res['n']}, {res['leaves']} leaves, of the same H-matrix; "
                               f"{res['times'][0]:.1f} s on 1 host thread")}
         except Exception as e:  # reported, not fatal
@@ -373,9 +419,11 @@ def run_native(args):
             "config": {"workload": f"{args.workload}: icosphere r={w['r']}, n={p.n}, leaf {w['leaf']}, "
                                    f"eta={w['eta']:g}, eps={w['eps']:g}, {p.nrhs} rhs ~ N(0,1) seed 0, tol 1e-10",
                        "n": p.n, "leaves": p.n_leaves, "nrhs": p.nrhs, "l2": "inputs larger than L2 (factor arena "
-                       f"{st32['device_bytes'] / 1e9:.1f} GB)", "parallelism": f"replicas x{world}"},
+                       f"{st32['device_bytes'] / 1e9:.1f} GB)", "parallelism": f"replicas x{world}",
+                       "solver": f"GMRES({args.restart})" if args.solver == "gmres" else "iterative refinement"},
             "time_to_1e10_ms": t_ms / args.steps, "solves_per_s": p.nrhs * args.steps * world / (t_ms * 1e-3),
             "p50_ms": pct(per, 0.5), "p99_ms": pct(per, 0.99), "ir_iters": arm32["iters"][-1],
+            "rank_hist": rank_hist(st32),
             "resid": max(arm32["resid"]), "factor_model_gflop": st32["model_flops"] / 1e9,
             "step_model_gflop": f32 / 1e9, "max_rank": st32["max_rank"],
             "fp64_arm": arm64, "e2e": e2e, "gpu_launches": arm32["launches"], "clocks": clk.summary(),
@@ -390,7 +438,7 @@ def run_native(args):
         dist.destroy_process_group()
 
 
-def e2e_arm(p, precision, sptr, steps, flops_step):
+def e2e_arm(p, precision, sptr, steps, flops_step, solver="ir", restart=30):
     """Public-API end to end: hlu_create from host arrays (H2D of the H-matrix),
     factor, b from pinned host memory, refinement, x back to pinned host memory."""
     import numpy as np
@@ -412,7 +460,10 @@ def e2e_arm(p, precision, sptr, steps, flops_step):
         h.factor(p.eps)
         bd = b_host.to("cuda", non_blocking=True).t()
         xd = torch.zeros_like(bd)
-        h.solve_refined(bd, xd, tol=TOL, max_iter=30)
+        if solver == "gmres":
+            h.solve_gmres(bd, xd, tol=TOL, restart=restart, max_iter=300)
+        else:
+            h.solve_refined(bd, xd, tol=TOL, max_iter=30)
         x_host.copy_(xd.t(), non_blocking=True)
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
@@ -421,7 +472,8 @@ def e2e_arm(p, precision, sptr, steps, flops_step):
     sec = sum(ts) / len(ts)
     return {"value": flops_step / sec / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": sec * 1e3,
-            "includes": "hlu_create (validation, planning, upload) + factor + refinement + copies"}
+            "includes": f"hlu_create (validation, planning, upload) + factor + "
+                        f"{'GMRES' if solver == 'gmres' else 'refinement'} + copies"}
 
 
 def main():

@@ -205,6 +205,8 @@ typedef struct {
     int64_t kernels_launched; /* kernels this handle launched since it was created */
     int32_t max_rank;         /* largest rank after the factorisation */
     int32_t max_stacked;      /* largest stacked-rank capacity of a rounded addition */
+    int64_t rank_hist[34];    /* low-rank leaves of L and U by rank after the factorisation:
+                                 [k] for k = 0 .. 32, [33] for ranks above 32 */
 } hlu_stats;
 
 int hlu_get_stats(hlu_t h, hlu_stats *out);

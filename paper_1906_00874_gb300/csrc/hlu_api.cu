@@ -853,7 +853,11 @@ int hlu_get_stats(hlu_t h, hlu_stats *o) {
         std::vector<int32_t> kd(h->pl.n_slots);
         if (cudaMemcpy(kd.data(), h->kdyn, sizeof(int32_t) * h->pl.n_slots, cudaMemcpyDeviceToHost) == cudaSuccess)
             for (int64_t l = 0; l < h->pl.n_leaves; ++l)
-                if (h->pl.fstore[l].kslot >= 0) o->max_rank = std::max(o->max_rank, kd[h->pl.fstore[l].kslot]);
+                if (h->pl.fstore[l].kslot >= 0) {
+                    const int32_t k = kd[h->pl.fstore[l].kslot];
+                    o->max_rank = std::max(o->max_rank, k);
+                    o->rank_hist[std::min(std::max(k, 0), 33)] += 1;
+                }
     }
     return HLU_OK;
 }
