@@ -844,11 +844,11 @@ __device__ CoreBufs<R> carve_core(unsigned char *base, int mr, int nc, bool stac
 // index on ties) and r through r_out; leaves B in precision R (b.B) and
 // 1 / sigma (b.isg).  Phase counters (profiling only) go to slots pb + 2 ...
 // pb + 7.
+// The steps of core_truncate after the pivoted QR (rank r known): the QR of R'^T, the Jacobi SVD,
+// ordering and truncation.  Returns the kept rank.
 template <class R>
-__device__ int core_truncate(const CoreBufs<R> &b, int mr, int nc, double delta, const TRadd &t,
-                             const LaunchArgs &a, int *r_out, int pb, unsigned long long &ph) {
-    const int r = block_qrcp<R>(b.M, mr, nc, b.tauM, b.cn, b.perm, delta, b.iflag);
-    ph = phase_mark(a, pb + 2, ph);
+__device__ int core_finish(const CoreBufs<R> &b, int mr, int nc, int r, const TRadd &t, const LaunchArgs &a,
+                           int pb, unsigned long long &ph) {
     for (int e = threadIdx.x; e < nc * r; e += blockDim.x) {
         const int c = e % nc, i = e / nc;
         b.C[e] = c >= i ? b.M[i + (size_t)c * mr] : R(0);
@@ -893,8 +893,16 @@ __device__ int core_truncate(const CoreBufs<R> &b, int mr, int nc, double delta,
         atomicAdd(a.phase + pb + 6, (unsigned long long)r);
         atomicAdd(a.phase + pb + 7, 1ull);
     }
-    *r_out = r;
     return knew;
+}
+
+template <class R>
+__device__ int core_truncate(const CoreBufs<R> &b, int mr, int nc, double delta, const TRadd &t,
+                             const LaunchArgs &a, int *r_out, int pb, unsigned long long &ph) {
+    const int r = block_qrcp<R>(b.M, mr, nc, b.tauM, b.cn, b.perm, delta, b.iflag);
+    ph = phase_mark(a, pb + 2, ph);
+    *r_out = r;
+    return core_finish<R>(b, mr, nc, r, t, a, pb, ph);
 }
 
 // Right factor of the truncated core: V[perm[i], c] = (R'^T B)[i, order[c]] /
@@ -942,21 +950,50 @@ __device__ void core_form_u(const CoreBufs<R> &b, int mr, int r, int knew) {
 // FP64 factors (double rounding level) and 1e-6 for FP32 factors (an order
 // above the FP32 rounding of the stacked panels, two below the relative
 // tolerances eps the method uses).
-// Small targets (m n <= kSmallTarget, m, n <= 128): the sum X = U_c V_c^T +
-// sum_i c_i U_i V_i^T is formed densely and truncated by core_truncate
-// directly, which is the same T_eps of the same sum without the two stacked
-// QRs.  Every launch provides at least radd_small_floor bytes, so the route
-// depends on the task alone.
-constexpr int kSmallTarget = 4096;
+// Dense route (targets with m, n <= 128 and m n <= dense_max = 4096; larger dense sums cost more in the
+// pivoted QR than the two stacked QRs they replace, measured at n = 20480):
+// the sum X = U_c V_c^T + sum_i c_i U_i V_i^T is formed densely and truncated
+// by the same core steps, which is the same T_eps of the same sum without the
+// two stacked QRs.  Shared memory is carved in two steps: X and the pivoted-QR
+// bookkeeping, then, with the rank r of the pivoted QR known, the rank-r
+// buffers; when those exceed kDensePost bytes the task falls back to the
+// stacked route (nothing outside shared memory has been written yet).  Every
+// launch provides at least radd_dense_floor bytes, so the route depends on the
+// task alone.
+template <class R>
+__host__ __device__ constexpr int dense_max() {
+    return 4096;
+}
+
+constexpr size_t kDensePost = 24576;
+
+template <class R>
+__host__ __device__ inline size_t dense_pre_bytes(int m, int n) {
+    const size_t rc = m < n ? m : n;
+    return (sizeof(R) * ((size_t)m * n + n + rc) + sizeof(int) * ((size_t)n + 8) + 15) & ~size_t(15);
+}
+
+template <class R>
+__host__ __device__ inline size_t dense_post_bytes(int m, int n, int r) {
+    const size_t mx = m > n ? m : n;
+    return 8 * ((size_t)r * r + r) + sizeof(R) * (mx * r + 2 * (size_t)r + (sizeof(R) == 8 ? 0 : (size_t)r * r)) +
+           sizeof(int) * (size_t)r;
+}
 
 template <class T>
 __device__ bool radd_small(const TRadd &t, const Piece *pieces, const LaunchArgs &a, int kself,
                            unsigned char *smem_raw, size_t smem_bytes, double delta) {
-    const int m = t.m, n = t.n;
-    if ((int64_t)m * n > kSmallTarget || max(m, n) > 128 || core_bytes<T>(m, n, false) > smem_bytes) return false;
+    const int m = t.m, n = t.n, rc = min(m, n);
+    if (max(m, n) > 128 || (int64_t)m * n > dense_max<T>()) return false;
     T *A = reinterpret_cast<T *>(a.arena);
     int32_t *kd = a.kdyn;
-    const CoreBufs<T> b = carve_core<T>(smem_raw, m, n, false);
+    CoreBufs<T> b;
+    b.M = reinterpret_cast<T *>(smem_raw);
+    b.cn = b.M + (size_t)m * n;
+    b.tauM = b.cn + n;
+    b.perm = reinterpret_cast<int *>(b.tauM + rc);
+    b.iflag = b.perm + n;
+    b.tauU = b.tauV = b.nrmU = b.nrmV = nullptr;
     unsigned long long ph = phase_mark(a, 0, 0ull);
     // ---- X = U_c V_c^T + sum of the zero-padded contributions
     for (int e = threadIdx.x; e < m * n; e += blockDim.x) {
@@ -976,8 +1013,23 @@ __device__ bool radd_small(const TRadd &t, const Piece *pieces, const LaunchArgs
     }
     __syncthreads();
     ph = phase_mark(a, 0, ph);
-    int r = 0;
-    const int knew = core_truncate<T>(b, m, n, delta, t, a, &r, 0, ph);
+    const int r = block_qrcp<T>(b.M, m, n, b.tauM, b.cn, b.perm, delta, b.iflag);
+    ph = phase_mark(a, 2, ph);
+    if (dense_post_bytes<T>(m, n, r) > kDensePost) return false;  // uniform over the CTA
+    // rank-r buffers after X and the pivot bookkeeping
+    b.D = reinterpret_cast<double *>(smem_raw + dense_pre_bytes<T>(m, n));
+    b.sig = b.D + r * r;
+    b.C = reinterpret_cast<T *>(b.sig + r);
+    b.tauC = b.C + (size_t)max(m, n) * r;
+    b.isg = b.tauC + r;
+    if constexpr (sizeof(T) == 8) {
+        b.B = b.D;
+        b.order = reinterpret_cast<int *>(b.isg + r);
+    } else {
+        b.B = b.isg + r;
+        b.order = reinterpret_cast<int *>(b.B + r * r);
+    }
+    const int knew = core_finish<T>(b, m, n, r, t, a, 0, ph);
     // the target's own factors were read above; every row of V is covered by P
     core_write_v<T, T>(b, m, n, r, knew, A + t.V_off, n);
     core_form_u<T>(b, m, r, knew);
@@ -1090,19 +1142,20 @@ __device__ void dev_radd(const TRadd &t, const Piece *pieces, const LaunchArgs &
 }
 
 // Shared memory that every rounded-addition launch provides: the dense route's
-// worst case over m n <= kSmallTarget, m, n <= 128.
+// worst case over m, n <= 128, m n <= dense_max, plus its rank-r budget.
 template <class R>
-size_t radd_small_floor() {
+size_t radd_dense_floor() {
     static size_t s = 0;
     if (s == 0)
         for (int m = 1; m <= 128; ++m)
-            for (int n = 1; n <= 128 && m * n <= kSmallTarget; ++n) s = std::max(s, core_bytes<R>(m, n, false));
+            for (int n = 1; n <= 128 && m * n <= dense_max<R>(); ++n)
+                s = std::max(s, dense_pre_bytes<R>(m, n) + kDensePost);
     return s;
 }
 
 size_t radd_smem_bytes(int kc, int elem) {
-    if (elem == 8) return std::max(core_bytes<double>(kc, kc, true), radd_small_floor<double>());
-    return std::max(core_bytes<float>(kc, kc, true), radd_small_floor<float>());
+    if (elem == 8) return std::max(core_bytes<double>(kc, kc, true), radd_dense_floor<double>());
+    return std::max(core_bytes<float>(kc, kc, true), radd_dense_floor<float>());
 }
 
 // ------------------------------------------------------------ wave kernels
@@ -1372,7 +1425,7 @@ void launch_kind(int kind, const void *tasks, const Term *terms, const Piece *pi
                                                                           terms, a, accum_smem_bytes(sizeof(T)));
             break;
         case K_RADD: {
-            // includes the dense route's worst case (radd_small_floor), so that the
+            // includes the dense route's worst case (radd_dense_floor), so that the
             // route a task takes does not depend on the schedule
             const size_t smem = radd_smem_bytes(aux, sizeof(T));
             k_radd<T><<<count, kThreads, smem, s>>>(reinterpret_cast<const TRadd *>(tasks) + start, pieces, a, aux,
