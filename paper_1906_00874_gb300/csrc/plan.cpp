@@ -298,32 +298,57 @@ void Planner::hmm(const View &out, double alpha, bool overwrite, Block *M, bool 
     }
     std::vector<View> keep;
     std::vector<const View *> rd;
+    std::vector<int32_t> depth, group;
+    std::vector<int64_t> cells;
     for (int32_t qi = 0; qi < nseg; ++qi) {
         if (seg[qi].empty() && !overwrite) continue;
         int32_t q = lc_ids[lc0 + qi];
         View o = rows(out, q);
-        keep.clear();
-        keep.reserve(2 * seg[qi].size() + 1);
-        TAccum ta{o.p, alpha, overwrite ? 1 : 0, int32_t(P->terms.size()), int32_t(seg[qi].size()), wdst, wsrc, 0};
-        for (int32_t i : seg[qi]) {
-            Block *m = lv[i];
-            View A, Xt;
+        const size_t nt = seg[qi].size();
+        keep.assign(2 * nt, View{});
+        depth.assign(nt, -1);
+        for (size_t ti = 0; ti < nt; ++ti) {
+            Block *m = lv[seg[qi][ti]];
             if (m->kind == B_DENSE) {
-                A = rows(trans ? transpose(viewD(m)) : viewD(m), q);
-                Xt = rows(X, trans ? m->t : m->s);
+                keep[2 * ti] = rows(trans ? transpose(viewD(m)) : viewD(m), q);
+                keep[2 * ti + 1] = rows(X, trans ? m->t : m->s);
             } else {
-                A = rows(trans ? viewV(m) : viewU(m), q);
-                Xt = Tv[i];
+                keep[2 * ti] = rows(trans ? viewV(m) : viewU(m), q);
+                keep[2 * ti + 1] = Tv[seg[qi][ti]];
             }
-            P->terms.push_back(Term{A.p, Xt.p});
-            keep.push_back(A);
-            keep.push_back(Xt);
+            // depth of the term: the latest dependency level among the cells it reads
+            cells.clear();
+            cells_of(keep[2 * ti], cells);
+            cells_of(keep[2 * ti + 1], cells);
+            for (int64_t c : cells) depth[ti] = std::max(depth[ti], cell_write_wave[c]);
         }
-        P->accum.push_back(ta);
-        rd.clear();
-        for (const View &v : keep) rd.push_back(&v);
-        if (!overwrite) rd.push_back(&o);
-        emit(K_ACCUM, rd, {&o});
+        // In the solve, the terms whose inputs are ready at the deepest level (the part of the
+        // update that waits on the latest solved segment) get their own ACCUM; the others are
+        // summed first, off that path.  Both sums go into the same output in the same order
+        // of terms within each group.
+        group.clear();
+        const int32_t dmax = nt ? *std::max_element(depth.begin(), depth.end()) : -1;
+        bool split = false;
+        if (split_accum && nt > 1)
+            for (size_t ti = 0; ti < nt; ++ti) split = split || depth[ti] < dmax;
+        for (int pass = 0; pass < (split ? 2 : 1); ++pass) {
+            const bool late = split && pass == 1;
+            const bool first = pass == 0;
+            int32_t cnt = 0;
+            const int32_t t0 = int32_t(P->terms.size());
+            rd.clear();
+            for (size_t ti = 0; ti < nt; ++ti) {
+                if (split && ((depth[ti] == dmax) != late)) continue;
+                P->terms.push_back(Term{keep[2 * ti].p, keep[2 * ti + 1].p});
+                rd.push_back(&keep[2 * ti]);
+                rd.push_back(&keep[2 * ti + 1]);
+                ++cnt;
+            }
+            const bool ow = overwrite && first;
+            P->accum.push_back(TAccum{o.p, alpha, ow ? 1 : 0, t0, cnt, wdst, wsrc, 0});
+            if (!ow) rd.push_back(&o);
+            emit(K_ACCUM, rd, {&o});
+        }
     }
 }
 
@@ -858,8 +883,10 @@ int Planner::plan_all() {
     Y.c_cl = -1;
     Y.trans = false;
     begin_plan(splan, false, &f_elems);
+    split_accum = true;
     solve_lower(root, Y);
     solve_upper(root, Y);
+    split_accum = false;
     finalize(splan, &f_elems);
     layout_a_arena();
     a_x_off = a_elems;

@@ -142,6 +142,7 @@ private:
     // current plan being emitted
     Plan *P = nullptr;
     bool use_astore = false;
+    bool split_accum = false;  // solve plan: split each ACCUM into its early and its latest terms
     int64_t *arena = nullptr;  // bump pointer of the current arena
     std::vector<Obj> objs;
     std::vector<int32_t> cell_write_wave, cell_read_wave;
