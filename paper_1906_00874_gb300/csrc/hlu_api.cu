@@ -160,7 +160,7 @@ int upload_plan(hlu_ctx *h, const Plan &p, DevPlan &d, int kmax) {
     if ((st = upload(h, &d.roots, p.roots))) return st;
     if ((st = dalloc(h, &d.indeg, p.indeg.size()))) return st;
     if ((st = dalloc(h, &d.queue, p.indeg.size()))) return st;
-    if ((st = dalloc(h, &d.counters, 2))) return st;
+    if ((st = dalloc(h, &d.counters, 3))) return st;
     int kc = 1;
     int64_t stride = 1;
     for (const TRadd &r : p.radd) {
@@ -264,7 +264,7 @@ void run_plan(hlu_ctx *h, const DevPlan &d, void *arena, double *flops) {
         cudaMemcpyAsync(d.indeg, d.indeg0, sizeof(int32_t) * d.n_tasks, cudaMemcpyDeviceToDevice, h->stream);
         cudaMemsetAsync(d.queue, 0xff, sizeof(int32_t) * d.n_tasks, h->stream);
         cudaMemcpyAsync(d.queue, d.roots, sizeof(int32_t) * d.n_roots, cudaMemcpyDeviceToDevice, h->stream);
-        cudaMemsetAsync(d.counters, 0, 2 * sizeof(int32_t), h->stream);
+        cudaMemsetAsync(d.counters, 0, 3 * sizeof(int32_t), h->stream);
         launch_set_slot(d.counters, 1, d.n_roots, h->stream);
         // profiling slots 6 / 7 / 8: the data-flow launch of a factorisation / a solve / a product
         Pending pe{&d == &h->fp ? K_NKINDS : &d == &h->sp ? K_NKINDS + 1 : K_NKINDS + 2, nullptr, nullptr};

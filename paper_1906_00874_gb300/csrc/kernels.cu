@@ -1208,11 +1208,22 @@ __global__ void __launch_bounds__(kThreads) k_radd(const TRadd *tasks, const Pie
 // queue slots in order (atomic head); a slot holds the id of a ready task once
 // the last predecessor of that task has finished and pushed it (atomic tail).
 // A finished task releases its successors: the last one to decrement a
-// successor's in-degree pushes it.  Writes of a task are published with a
+// successor's in-degree makes it ready.  The first successor it makes ready
+// the worker runs itself next (no queue round trip, its inputs are in this
+// SM's cache); the others are pushed.  Writes of a task are published with a
 // device-scope fence before the release; the consumer reads the slot with an
-// acquire load.  Every wait has a deadline (%globaltimer): on expiry, or when
-// another worker has recorded an error, the worker records DE_TIMEOUT (first
-// error wins) and leaves, so the launch always ends.
+// acquire load, and a worker that makes a task ready itself fences before
+// running it.  Successor lists come with the successor on the longest
+// remaining path first (the planner's priority), so that is the one run next
+// whenever it becomes ready here.  Successors are released in parallel, one
+// thread each.  The worker that completes the last
+// task writes an end mark into every queue slot a worker may be waiting on
+// (slots that inlining left unfilled).  Every wait has a deadline
+// (%globaltimer): on expiry, or when another worker has recorded an error,
+// the worker records DE_TIMEOUT (first error wins) and leaves, so the launch
+// always ends.
+constexpr int kQueueEnd = -3;  // queue slot value: no task will come
+
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -1232,27 +1243,34 @@ __device__ __forceinline__ void st_release(int *p, int v) {
 template <class T>
 __global__ void __launch_bounds__(kThreads, 2) k_dataflow(FlowArgs f, LaunchArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_task;
+    __shared__ int s_task, s_next, s_first;
     T *scratch = reinterpret_cast<T *>(f.scratch) + (int64_t)blockIdx.x * f.scratch_stride;
+    if (threadIdx.x == 0) s_next = -1;
     for (;;) {
         if (threadIdx.x == 0) {
-            const int slot = atomicAdd(f.counters, 1);
-            int g = -1;
-            if (slot < f.n_tasks) {
-                const unsigned long long deadline = global_ns() + f.timeout_ns;
-                for (;;) {
-                    g = ld_acquire(f.queue + slot);
-                    if (g >= 0) break;
-                    if (*(volatile long long *)a.err != 0) {
-                        g = -2;
-                        break;
+            int g = s_next;
+            if (g < 0) {
+                const int slot = atomicAdd(f.counters, 1);
+                if (slot < f.n_tasks) {
+                    const unsigned long long deadline = global_ns() + f.timeout_ns;
+                    for (;;) {
+                        g = ld_acquire(f.queue + slot);
+                        if (g >= 0) break;
+                        if (g == kQueueEnd) {  // every task has completed
+                            g = -1;
+                            break;
+                        }
+                        if (*(volatile long long *)a.err != 0) {
+                            g = -2;
+                            break;
+                        }
+                        if (global_ns() > deadline) {
+                            set_error(a.err, DE_TIMEOUT, slot, 0.0);
+                            g = -2;
+                            break;
+                        }
+                        __nanosleep(100);
                     }
-                    if (global_ns() > deadline) {
-                        set_error(a.err, DE_TIMEOUT, slot, 0.0);
-                        g = -2;
-                        break;
-                    }
-                    __nanosleep(100);
                 }
             }
             s_task = g;
@@ -1313,14 +1331,40 @@ __global__ void __launch_bounds__(kThreads, 2) k_dataflow(FlowArgs f, LaunchArgs
                     atomicAdd(f.busy + 24 + b, 1ull);
                 }
             }
-            __threadfence();
-            for (int e = f.succ_ptr[g]; e < f.succ_ptr[g + 1]; ++e) {
-                const int s = f.succ_idx[e];
-                if (atomicSub(f.indeg + s, 1) == 1) {
+            s_first = INT_MAX;
+        }
+        __syncthreads();
+        // release the successors in parallel, one thread each: the task's writes (ordered before
+        // this point by the barrier) are published by each thread's fence before its decrement
+        const int e0 = f.succ_ptr[g], ns = f.succ_ptr[g + 1] - e0;
+        for (int c0 = 0; c0 < ns; c0 += blockDim.x) {
+            const int e = c0 + threadIdx.x;
+            bool ready = false;
+            if (e < ns) {
+                __threadfence();
+                ready = atomicSub(f.indeg + f.succ_idx[e0 + e], 1) == 1;
+                if (ready) {
                     __threadfence();
-                    const int pos = atomicAdd(f.counters + 1, 1);
-                    st_release(f.queue + pos, s);
+                    atomicMin(&s_first, e);
                 }
+            }
+            __syncthreads();
+            // the first ready successor in priority order runs here next; the others are queued
+            if (ready && e != s_first) {
+                const int pos = atomicAdd(f.counters + 1, 1);
+                st_release(f.queue + pos, f.succ_idx[e0 + e]);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_next = s_first < ns ? f.succ_idx[e0 + s_first] : -1;
+            if (atomicAdd(f.counters + 2, 1) == f.n_tasks - 1) {
+                // the last task: wake the workers waiting on slots that will stay empty, and
+                // those that still claim one (each worker claims at most one more slot)
+                __threadfence();
+                const int tail = atomicAdd(f.counters + 1, 0), head = atomicAdd(f.counters, 0);
+                const int end = min(f.n_tasks, head + (int)gridDim.x);
+                for (int pos = tail; pos < end; ++pos) st_release(f.queue + pos, kQueueEnd);
             }
         }
         __syncthreads();

@@ -31,7 +31,8 @@ struct FlowArgs {
     const int32_t *succ_idx;
     int32_t *indeg;            // working in-degrees (reset before every launch)
     int32_t *queue;            // n_tasks slots, -1 = empty
-    int32_t *counters;         // [0] head (next slot to claim), [1] tail (next slot to fill)
+    int32_t *counters;         // [0] head (next slot to claim), [1] tail (next slot to fill),
+                               // [2] completed tasks
     int32_t n_tasks;
     int32_t kc;                // core capacity of rounded additions (shared memory)
     const TGetrf *getrf;

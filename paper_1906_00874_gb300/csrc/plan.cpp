@@ -92,21 +92,22 @@ int32_t Planner::emit(Kind k, const std::vector<const View *> &reads,
         cell_write_wave[c] = w;
         cell_read_wave[c] = -1;
     }
-    // explicit edges: read-after-write, write-after-write, write-after-read
+    // explicit edges: read-after-write, write-after-write, write-after-read; each predecessor is
+    // listed once (pred_mark[t] == g once t is in this task's list), in the order first met
     const int32_t g = int32_t(P->n_tasks);
-    static thread_local std::vector<int32_t> pr;
-    pr.clear();
-    for (int64_t c : rc)
-        if (cell_writer[c] >= 0) pr.push_back(cell_writer[c]);
-    for (int64_t c : wc) {
-        if (cell_writer[c] >= 0) pr.push_back(cell_writer[c]);
-        for (int32_t e = cell_rhead[c]; e >= 0; e = rpool_next[e])
-            if (rpool_task[e] != g) pr.push_back(rpool_task[e]);
-    }
-    std::sort(pr.begin(), pr.end());
-    pr.erase(std::unique(pr.begin(), pr.end()), pr.end());
     if (P->pred_ptr.empty()) P->pred_ptr.push_back(0);
-    P->pred_idx.insert(P->pred_idx.end(), pr.begin(), pr.end());
+    if ((int64_t)pred_mark.size() < (int64_t)g + 1) pred_mark.resize(std::max<int64_t>(2 * (int64_t)g, 1024), -1);
+    auto add = [&](int32_t t) {
+        if (t >= 0 && t != g && pred_mark[t] != g) {
+            pred_mark[t] = g;
+            P->pred_idx.push_back(t);
+        }
+    };
+    for (int64_t c : rc) add(cell_writer[c]);
+    for (int64_t c : wc) {
+        add(cell_writer[c]);
+        for (int32_t e = cell_rhead[c]; e >= 0; e = rpool_next[e]) add(rpool_task[e]);
+    }
     P->pred_ptr.push_back(int32_t(P->pred_idx.size()));
     for (int64_t c : rc) {
         rpool_task.push_back(g);
@@ -530,6 +531,7 @@ void Planner::solve_upper(Block *F, const View &Y) {
 
 // --------------------------------------------------------- plan bookkeeping
 void Planner::begin_plan(Plan &p, bool astore_mode, int64_t *bump) {
+    pred_mark.clear();
     P = &p;
     use_astore = astore_mode;
     arena = bump;
@@ -588,9 +590,30 @@ void Planner::finalize(Plan &p, int64_t *bump) {
             for (int32_t e = p.pred_ptr[g]; e < p.pred_ptr[g + 1]; ++e) p.succ_idx[fill[p.pred_idx[e]]++] = int32_t(g);
     }
     p.n_edges = (int64_t)p.pred_idx.size();
-    p.roots.clear();
-    for (int64_t g = 0; g < nt; ++g)
-        if (p.indeg[g] == 0) p.roots.push_back(int32_t(g));
+    // priorities: bottom level (longest path to the end of the graph) with per-kind task latencies
+    // measured on the GPU (microseconds: GETRF 27, TRSM 7, PROJECT 3, ACCUM 7, RADD 95, SPLIT 3).
+    // The successor on the longest remaining path goes first in every successor list (the
+    // data-flow executor prefers the first ready successor), and the roots are sorted by it.
+    {
+        static const float kLatency[K_NKINDS] = {27.f, 7.f, 3.f, 7.f, 95.f, 3.f};
+        std::vector<float> bl(nt, 0.f);
+        for (int64_t g = nt - 1; g >= 0; --g) {
+            float m = 0.f;
+            int32_t best = -1;
+            for (int32_t e = p.succ_ptr[g]; e < p.succ_ptr[g + 1]; ++e)
+                if (best < 0 || bl[p.succ_idx[e]] > m) {
+                    m = bl[p.succ_idx[e]];
+                    best = e;
+                }
+            if (best > p.succ_ptr[g]) std::swap(p.succ_idx[best], p.succ_idx[p.succ_ptr[g]]);
+            bl[g] = m + kLatency[p.task_code[g] >> kCodeShift];
+        }
+        auto by_priority = [&](int32_t x, int32_t y) { return bl[x] > bl[y] || (bl[x] == bl[y] && x < y); };
+        p.roots.clear();
+        for (int64_t g = 0; g < nt; ++g)
+            if (p.indeg[g] == 0) p.roots.push_back(int32_t(g));
+        std::sort(p.roots.begin(), p.roots.end(), by_priority);
+    }
     // rounded-addition scratch: tasks of one wave get disjoint regions, waves reuse them
     int64_t base = align8(*bump), maxw = 0;
     {

@@ -148,6 +148,7 @@ private:
     std::vector<int32_t> cell_write_wave, cell_read_wave;
     // per cell: last writer and the readers since (singly linked lists in a pool)
     std::vector<int32_t> cell_writer, cell_rhead;
+    std::vector<int32_t> pred_mark;  // per task: the last task that listed it as a predecessor
     std::vector<int32_t> rpool_task, rpool_next;
     int32_t ident_obj = -1;
 
