@@ -211,6 +211,15 @@ typedef struct {
 
 int hlu_get_stats(hlu_t h, hlu_stats *out);
 
+/* Failure injection for tests of the timeout path (no counterpart in the paper):
+ * with on != 0, the next data-flow factorisation of the handle gets one task
+ * (the last of its graph) whose in-degree is one more than its predecessors
+ * can clear.  That task never becomes ready, the workers' bounded waits run
+ * out after opts.timeout_s, and hlu_factor returns HLU_ETIMEOUT with the
+ * device left usable; no memory is touched out of bounds and nothing spins
+ * without a limit.  The injection is consumed by that call. */
+int hlu_inject_stall(hlu_t h, int32_t on);
+
 /* Profiling: when on, every kernel launch of the handle is bracketed by CUDA
  * events on the handle's stream and its duration is added to kernel_ms of its
  * task kind (read with hlu_get_stats).  Turning it on clears the sums. */

@@ -99,6 +99,7 @@ struct hlu_ctx {
     int64_t kernels_launched = 0;
     cudaError_t last_cuda = cudaSuccess;
     unsigned long long *busy = nullptr;  // per-kind task time inside the data-flow kernel (profiling)
+    bool inject_stall = false;           // next data-flow factorisation: one task never becomes ready
 };
 
 namespace {
@@ -264,6 +265,11 @@ void run_plan(hlu_ctx *h, const DevPlan &d, void *arena, double *flops) {
         cudaMemcpyAsync(d.indeg, d.indeg0, sizeof(int32_t) * d.n_tasks, cudaMemcpyDeviceToDevice, h->stream);
         cudaMemsetAsync(d.queue, 0xff, sizeof(int32_t) * d.n_tasks, h->stream);
         cudaMemcpyAsync(d.queue, d.roots, sizeof(int32_t) * d.n_roots, cudaMemcpyDeviceToDevice, h->stream);
+        if (h->inject_stall && &d == &h->fp && d.n_tasks > 0) {  // test hook: the last task waits forever
+            const int32_t last = d.n_tasks - 1;
+            launch_set_slot(d.indeg, last, h->pl.fplan.indeg[last] + 1, h->stream);
+            h->inject_stall = false;
+        }
         cudaMemsetAsync(d.counters, 0, 3 * sizeof(int32_t), h->stream);
         launch_set_slot(d.counters, 1, d.n_roots, h->stream);
         // profiling slots 6 / 7 / 8: the data-flow launch of a factorisation / a solve / a product
@@ -859,6 +865,12 @@ int hlu_get_stats(hlu_t h, hlu_stats *o) {
                     o->rank_hist[std::min(std::max(k, 0), 33)] += 1;
                 }
     }
+    return HLU_OK;
+}
+
+int hlu_inject_stall(hlu_t h, int32_t on) {
+    if (!h) return HLU_EINVAL;
+    h->inject_stall = on != 0;
     return HLU_OK;
 }
 

@@ -25,7 +25,7 @@ STATUS = {0: "HLU_OK", 1: "HLU_EINVAL", 2: "HLU_ENOMEM", 3: "HLU_ESTATE", 4: "HL
 EXPORTS = ("hlu_create", "hlu_factor", "hlu_solve", "hlu_matvec", "hlu_solve_refined", "hlu_solve_gmres",
            "hlu_factor_doubles",
            "hlu_get_factors", "hlu_get_stats", "hlu_set_profiling", "hlu_destroy", "hlu_strerror",
-           "hlu_last_error_detail", "hlu_last_cuda_error", "hlu_probe_alu_peaks")
+           "hlu_last_error_detail", "hlu_last_cuda_error", "hlu_probe_alu_peaks", "hlu_inject_stall")
 KINDS = ("getrf", "trsm", "project", "accum", "radd", "split", "dataflow_factor", "dataflow_solve",
          "dataflow_matvec")
 
@@ -109,6 +109,7 @@ def load(path=LIB_PATH):
     lib.hlu_solve_refined.argtypes = [vp, vp, vp, i32, i64, dbl, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl)]
     lib.hlu_solve_gmres.argtypes = [vp, vp, vp, i32, i64, dbl, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl)]
     lib.hlu_set_profiling.argtypes = [vp, i32]
+    lib.hlu_inject_stall.argtypes = [vp, i32]
     lib.hlu_probe_alu_peaks.argtypes = [ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
     lib.hlu_factor_doubles.argtypes = [vp]
     lib.hlu_factor_doubles.restype = i64
@@ -255,6 +256,10 @@ class HLU:
                                            float(tol), int(restart), int(max_iter), ctypes.byref(it),
                                            ctypes.byref(res)), "hlu_solve_gmres")
         return it.value, res.value
+
+    def inject_stall(self, on=True):
+        """Test hook: the next factorisation stalls on one task until the wait limit (HLU_ETIMEOUT)."""
+        self._check(load().hlu_inject_stall(self._h, int(bool(on))), "hlu_inject_stall")
 
     def set_profiling(self, on):
         self._check(load().hlu_set_profiling(self._h, 1 if on else 0), "hlu_set_profiling")
