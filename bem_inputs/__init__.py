@@ -15,3 +15,25 @@ WORKLOADS = {
     "sphere20480": dict(r=5, leaf=64, eta=2.0, eps=1e-4, nrhs=16),
     "sphere81920": dict(r=6, leaf=64, eta=2.0, eps=1e-6, nrhs=64),
 }
+
+# Batches of independent problems: `count` ellipsoids, instance i drawn from seed i.
+BATCHES = {
+    "ellipsoids64": dict(count=64, levels=(3, 4), eps=(1e-4, 1e-6), leaf=32, eta=2.0),
+}
+
+
+def batch_specs(count, levels=(3, 4), eps=(1e-4, 1e-6), leaf=32, eta=2.0):
+    """Keyword arguments of build_problem for each instance of a batch.
+
+    Instance i uses default_rng(i): refinement r uniform in `levels`, tolerance
+    uniform in `eps`, ellipsoid axes (1, a, b) with a, b uniform in [0.4, 1],
+    one right-hand side drawn from seed i."""
+    import numpy as np
+    out = []
+    for i in range(count):
+        g = np.random.default_rng(i)
+        r = int(g.choice(levels))
+        e = float(g.choice(eps))
+        a, b = (float(v) for v in g.uniform(0.4, 1.0, 2))
+        out.append(dict(r=r, leaf=leaf, eta=eta, eps=e, nrhs=1, seed=i, axes=(1.0, round(a, 6), round(b, 6))))
+    return out

@@ -119,6 +119,30 @@ int hlu_create(const hlu_tree *tree, const hlu_blocks *blocks, const hlu_opts *o
  * HLU_ENUMERIC with details from hlu_last_error_detail). */
 int hlu_factor(hlu_t h, double eps);
 
+/* Batched H-LU: `count` independent problems in one handle.  trees[i] and
+ * blocks[i] describe problem i exactly as for hlu_create (indices local to the
+ * problem, host pointers).  The handle holds the block-diagonal matrix
+ * diag(A_0, ..., A_{count-1}) of order sum n_i: a balanced binary tree of
+ * count - 1 clusters joins the problems' roots, and blocks that couple two
+ * problems are structurally zero (no leaves, no tasks, no dependencies), so
+ * the factorisation and the solve of all problems run in the same launches and
+ * no task of one problem waits on another.  Rows and right-hand-side rows of
+ * problem i follow those of problems 0..i-1 (offsets sum_{j<i} n_j); every
+ * other call (hlu_factor, hlu_solve, hlu_solve_refined, hlu_solve_gmres,
+ * hlu_matvec, hlu_get_factors) sees the stacked system of that order.
+ * count >= 1; on failure *out is NULL. */
+int hlu_create_batch(int32_t count, const hlu_tree *trees, const hlu_blocks *blocks,
+                     const hlu_opts *opts, void *cuda_stream, hlu_t *out);
+
+/* hlu_factor with a tolerance per problem: eps[i] (host array of
+ * hlu_batch_count(h) values, each finite and >= 0) truncates the rounded
+ * additions of problem i.  On a handle from hlu_create it takes eps[0]. */
+int hlu_factor_batch(hlu_t h, const double *eps);
+
+/* Number of problems in the handle: count of hlu_create_batch, 1 for
+ * hlu_create, 0 for a NULL handle. */
+int hlu_batch_count(hlu_t h);
+
 /* Solve A x = b with the factors: forward substitution with the unit lower
  * factor, then backward substitution with the upper factor (Sec. 3.1).
  * b is a DEVICE pointer to n x nrhs FP64 values, column-major with leading

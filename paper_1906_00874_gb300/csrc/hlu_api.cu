@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -100,6 +101,8 @@ struct hlu_ctx {
     cudaError_t last_cuda = cudaSuccess;
     unsigned long long *busy = nullptr;  // per-kind task time inside the data-flow kernel (profiling)
     bool inject_stall = false;           // next data-flow factorisation: one task never becomes ready
+    double *eps_inst = nullptr;          // per-instance tolerances of a batch (device), used when eps_each
+    bool eps_each = false;
 };
 
 namespace {
@@ -233,6 +236,7 @@ void run_plan(hlu_ctx *h, const DevPlan &d, void *arena, double *flops) {
     a.kdyn = h->kdyn;
     a.err = h->err;
     a.eps = h->eps;
+    a.eps_inst = h->eps_each ? h->eps_inst : nullptr;
     a.flops = flops;
     a.phase = (h->profiling && &d == &h->fp) ? h->busy + 32 : nullptr;
     a.kmax = h->pl.opt.kmax_core;
@@ -404,6 +408,10 @@ void matvec_pass(hlu_ctx *h, int32_t nc) {
 
 }  // namespace
 
+namespace {
+int factor_impl(hlu_ctx *h);
+}  // namespace
+
 extern "C" {
 
 const char *hlu_strerror(int s) {
@@ -421,8 +429,8 @@ const char *hlu_strerror(int s) {
     return "unknown status";
 }
 
-int hlu_create(const hlu_tree *tree, const hlu_blocks *blocks, const hlu_opts *opts, void *cuda_stream,
-               hlu_t *out) {
+static int create_impl(const hlu_tree *tree, const hlu_blocks *blocks, const hlu_opts *opts, void *cuda_stream,
+                       hlu_t *out, const int32_t *inst, int32_t n_inst) {
     if (!out) return HLU_EINVAL;
     *out = nullptr;
     if (!tree || !blocks) return HLU_EINVAL;
@@ -445,7 +453,7 @@ int hlu_create(const hlu_tree *tree, const hlu_blocks *blocks, const hlu_opts *o
     h->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
     int st = h->pl.build(tree->n, tree->n_clusters, tree->perm, tree->begin, tree->size, tree->son0, tree->son1,
                          blocks->n_leaves, blocks->row_cl, blocks->col_cl, blocks->kind, blocks->rank,
-                         blocks->offset, blocks->data, blocks->data_len, po);
+                         blocks->offset, blocks->data, blocks->data_len, po, inst, n_inst);
     if (st == HLU_OK && h->pl.max_leaf > 128) st = HLU_EINVAL;  // a dense leaf column lives in one warp's registers
     if (st == HLU_OK) st = h->pl.plan_all();
     if (st == HLU_OK) {
@@ -484,9 +492,109 @@ int hlu_create(const hlu_tree *tree, const hlu_blocks *blocks, const hlu_opts *o
     return HLU_OK;
 }
 
+int hlu_create(const hlu_tree *tree, const hlu_blocks *blocks, const hlu_opts *opts, void *cuda_stream,
+               hlu_t *out) {
+    return create_impl(tree, blocks, opts, cuda_stream, out, nullptr, 0);
+}
+
+int hlu_create_batch(int32_t count, const hlu_tree *trees, const hlu_blocks *blocks, const hlu_opts *opts,
+                     void *cuda_stream, hlu_t *out) {
+    if (!out) return HLU_EINVAL;
+    *out = nullptr;
+    if (count < 1 || !trees || !blocks) return HLU_EINVAL;
+    int64_t N = 0, ncl = count - 1, nl = 0, dl = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        const hlu_tree &t = trees[i];
+        const hlu_blocks &b = blocks[i];
+        if (t.n < 1 || t.n_clusters < 1 || !t.perm || !t.begin || !t.size || !t.son0 || !t.son1 || b.n_leaves < 1 ||
+            !b.row_cl || !b.col_cl || !b.kind || !b.rank || !b.offset || !b.data || b.data_len < 0)
+            return HLU_EINVAL;
+        N += t.n;
+        ncl += t.n_clusters;
+        nl += b.n_leaves;
+        dl += b.data_len;
+    }
+    if (N > INT32_MAX || ncl > INT32_MAX) return HLU_EINVAL;
+    // clusters: count - 1 clusters above the instances first (cluster 0 is the root), then every
+    // instance's own clusters, indices and ranges shifted; leaves, offsets and data concatenated
+    std::vector<int32_t> perm(N), begin(ncl), size(ncl), son0(ncl), son1(ncl), inst(ncl, -1);
+    std::vector<int32_t> rc(nl), cc(nl), rk(nl);
+    std::vector<int8_t> kd(nl);
+    std::vector<int64_t> off(nl), cl_off(count);
+    std::vector<double> data(dl);
+    int64_t no = 0, co = count - 1, lo = 0, dof = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        const hlu_tree &t = trees[i];
+        const hlu_blocks &b = blocks[i];
+        cl_off[i] = co;
+        for (int32_t c = 0; c < t.n_clusters; ++c) {
+            begin[co + c] = int32_t(t.begin[c] + no);
+            size[co + c] = t.size[c];
+            son0[co + c] = t.son0[c] >= 0 ? int32_t(t.son0[c] + co) : -1;
+            son1[co + c] = t.son1[c] >= 0 ? int32_t(t.son1[c] + co) : -1;
+            inst[co + c] = i;
+        }
+        for (int32_t k = 0; k < t.n; ++k) perm[no + k] = int32_t(t.perm[k] + no);
+        for (int64_t l = 0; l < b.n_leaves; ++l) {
+            rc[lo + l] = int32_t(b.row_cl[l] + co);
+            cc[lo + l] = int32_t(b.col_cl[l] + co);
+            kd[lo + l] = b.kind[l];
+            rk[lo + l] = b.rank[l];
+            off[lo + l] = b.offset[l] + dof;
+        }
+        std::memcpy(data.data() + dof, b.data, sizeof(double) * b.data_len);
+        no += t.n;
+        co += t.n_clusters;
+        lo += b.n_leaves;
+        dof += b.data_len;
+    }
+    // a balanced binary tree of clusters over the instances, numbered from 0 (the root)
+    int32_t next_v = 0;
+    std::function<int32_t(int32_t, int32_t)> make = [&](int32_t i0, int32_t i1) -> int32_t {
+        if (i1 - i0 == 1) return int32_t(cl_off[i0]);
+        const int32_t v = next_v++, mid = (i0 + i1) / 2;
+        const int32_t a = make(i0, mid), b = make(mid, i1);
+        begin[v] = begin[a];
+        size[v] = size[a] + size[b];
+        son0[v] = a;
+        son1[v] = b;
+        return v;
+    };
+    make(0, count);
+    const hlu_tree t{int32_t(N), int32_t(ncl), perm.data(), begin.data(), size.data(), son0.data(), son1.data()};
+    const hlu_blocks b{nl, rc.data(), cc.data(), kd.data(), rk.data(), off.data(), data.data(), dl};
+    return create_impl(&t, &b, opts, cuda_stream, out, inst.data(), count);
+}
+
 int hlu_factor(hlu_t h, double eps) {
     if (!h || !(eps >= 0.0) || !std::isfinite(eps)) return HLU_EINVAL;
     h->eps = eps;
+    h->eps_each = false;
+    return factor_impl(h);
+}
+
+int hlu_factor_batch(hlu_t h, const double *eps) {
+    if (!h || !eps) return HLU_EINVAL;
+    const int32_t ni = h->pl.n_inst;
+    for (int32_t i = 0; i < ni; ++i)
+        if (!(eps[i] >= 0.0) || !std::isfinite(eps[i])) return HLU_EINVAL;
+    int st = HLU_OK;
+    if (!h->eps_inst && (st = dalloc(h, &h->eps_inst, ni))) return st;
+    if ((st = cuda_status(cudaMemcpyAsync(h->eps_inst, eps, sizeof(double) * ni, cudaMemcpyHostToDevice, h->stream))))
+        return st;
+    if ((st = cuda_status(cudaStreamSynchronize(h->stream)))) return st;  // eps is the caller's memory
+    h->eps = eps[0];
+    h->eps_each = true;
+    return factor_impl(h);
+}
+
+int hlu_batch_count(hlu_t h) { return h ? h->pl.n_inst : 0; }
+
+}  // extern "C"
+
+namespace {
+
+int factor_impl(hlu_ctx *h) {
     h->factored = false;
     int st = clear_error(h);
     if (st) return st;
@@ -506,6 +614,10 @@ int hlu_factor(hlu_t h, double eps) {
     h->factored = st == HLU_OK;
     return st;
 }
+
+}  // namespace
+
+extern "C" {
 
 int hlu_solve(hlu_t h, double *b, int32_t nrhs, int64_t ldb) {
     if (!h || nrhs < 0 || ldb < h->pl.n) return HLU_EINVAL;

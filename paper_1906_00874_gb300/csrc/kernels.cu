@@ -881,7 +881,8 @@ __device__ int core_finish(const CoreBufs<R> &b, int mr, int nc, int r, const TR
     if (!isfinite(s1)) {
         if (threadIdx.x == 0) set_error(a.err, DE_NONFINITE, t.target, s1);
     } else if (s1 > 0.0) {
-        for (int l = 0; l < r; ++l) knew += b.sig[b.order[l]] > a.eps * s1;
+        const double eps = a.eps_inst ? a.eps_inst[t.inst] : a.eps;
+        for (int l = 0; l < r; ++l) knew += b.sig[b.order[l]] > eps * s1;
     }
     if (knew > t.cap) {
         if (threadIdx.x == 0) set_error(a.err, DE_RANKCAP, t.target, (double)knew);

@@ -15,6 +15,7 @@ struct LaunchArgs {
     int32_t *kdyn;      // dynamic dimensions
     long long *err;     // error word: code, index, value bits, count
     double eps;         // truncation tolerance (rounded addition)
+    const double *eps_inst;  // per instance of a batch (device array), else null: eps for all
     double *flops;      // model flops per task kind (K_NKINDS doubles), accumulated
     unsigned long long *phase;  // when profiling: rounded-addition phase counters (16), else null
     int32_t kmax;       // largest stacked rank the core buffers hold

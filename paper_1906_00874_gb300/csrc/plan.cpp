@@ -190,6 +190,7 @@ View Planner::transpose(const View &v) {
 }
 
 void Planner::collect_leaves(Block *b, std::vector<Block *> &out) {
+    if (b->kind == B_ZERO) return;
     if (b->kind == B_PART) {
         for (int i = 0; i < 2; ++i)
             for (int j = 0; j < 2; ++j) collect_leaves(b->son[i][j], out);
@@ -216,6 +217,7 @@ void Planner::lu(Block *b) {
 }
 
 void Planner::trsm_l(Block *L, Block *X) {
+    if (X->kind == B_ZERO) return;
     if (X->kind == B_LOWRANK) {
         trsm_l_panel(L, viewU(X));  // L^{-1} U V^T: solve on the k columns of U
     } else if (X->kind == B_DENSE) {
@@ -228,6 +230,7 @@ void Planner::trsm_l(Block *L, Block *X) {
 }
 
 void Planner::trsm_u(Block *U, Block *X) {
+    if (X->kind == B_ZERO) return;
     if (X->kind == B_LOWRANK) {
         trsm_u_panel(U, viewV(X));  // U V^T R^{-1} = U (R^{-T} V)^T: solve on the rows of V
     } else if (X->kind == B_DENSE) {
@@ -427,6 +430,7 @@ void Planner::radd(Block *C, bool include_self, const std::vector<Piece> &pcs,
     tr.npieces = int32_t(pcs.size());
     tr.Kcap = kcap;
     tr.target = C->id;
+    tr.inst = inst.empty() ? 0 : std::max(0, inst[C->t]);
     for (const Piece &pc : pcs) P->pieces.push_back(pc);
     P->radd.push_back(tr);
     P->max_kcap = std::max(P->max_kcap, kcap);
@@ -441,6 +445,7 @@ void Planner::radd(Block *C, bool include_self, const std::vector<Piece> &pcs,
 }
 
 void Planner::addmul(Block *C, double alpha, Block *A, Block *B) {
+    if (C->kind == B_ZERO || A->kind == B_ZERO || B->kind == B_ZERO) return;  // no coupling between instances
     if (A->kind == B_PART && B->kind == B_PART) {
         if (C->kind == B_PART) {
             for (int i = 0; i < 2; ++i)
@@ -683,6 +688,10 @@ int Planner::build_tree() {
             used++;
             continue;
         }
+        if (!inst.empty() && (inst[t] != inst[s] || (t != s && inst[t] < 0))) {
+            b->kind = B_ZERO;  // between two instances of a batch
+            continue;
+        }
         if (cl[t].son0 < 0 || cl[s].son0 < 0) {
             error = "leaves do not tile the matrix (missing block)";
             return HLU_EINVAL;
@@ -760,9 +769,24 @@ int Planner::build(int32_t n_, int32_t n_clusters, const int32_t *perm_, const i
                    const int32_t *size, const int32_t *son0, const int32_t *son1, int64_t n_leaves_,
                    const int32_t *row_cl, const int32_t *col_cl, const int8_t *kind,
                    const int32_t *rank, const int64_t *offset, const double *data,
-                   int64_t data_len, const PlanOptions &o) {
+                   int64_t data_len, const PlanOptions &o, const int32_t *inst_, int32_t n_inst_) {
     opt = o;
     n = n_;
+    inst.clear();
+    n_inst = 1;
+    if (inst_) {
+        if (n_inst_ < 1) {
+            error = "bad instance count";
+            return HLU_EINVAL;
+        }
+        inst.assign(inst_, inst_ + n_clusters);
+        for (int32_t v : inst)
+            if (v < -1 || v >= n_inst_) {
+                error = "bad instance index";
+                return HLU_EINVAL;
+            }
+        n_inst = n_inst_;
+    }
     if (n < 1 || n_clusters < 1 || !perm_ || !begin || !size || !son0 || !son1) {
         error = "bad tree arguments";
         return HLU_EINVAL;

@@ -42,7 +42,8 @@ struct View {
     bool trans;          // view rows run along the object's columns
 };
 
-enum BKind : int32_t { B_DENSE = 0, B_LOWRANK = 1, B_PART = 2 };
+// B_ZERO: a block between two different instances of a batch (structurally zero: no leaf, no task).
+enum BKind : int32_t { B_DENSE = 0, B_LOWRANK = 1, B_PART = 2, B_ZERO = 3 };
 
 struct Block {
     int32_t t, s;
@@ -100,6 +101,10 @@ public:
     // ---- inputs (validated copies)
     int32_t n = 0;
     std::vector<ClusterInfo> cl;
+    // batch of independent H-matrices: instance of every cluster (-1 for the clusters above the
+    // instances' roots); empty for a single H-matrix
+    std::vector<int32_t> inst;
+    int32_t n_inst = 1;
     std::vector<int32_t> perm;
     std::vector<int32_t> lc_ids;  // leaf clusters in DoF order
     int32_t max_leaf = 0;
@@ -134,7 +139,7 @@ public:
               const int32_t *size, const int32_t *son0, const int32_t *son1, int64_t n_leaves,
               const int32_t *row_cl, const int32_t *col_cl, const int8_t *kind,
               const int32_t *rank, const int64_t *offset, const double *data,
-              int64_t data_len, const PlanOptions &o);
+              int64_t data_len, const PlanOptions &o, const int32_t *inst = nullptr, int32_t n_inst = 0);
     // Lays out the arenas and emits the factorisation, solve and matvec plans.
     int plan_all();
 

@@ -90,7 +90,7 @@ struct TRadd {
     int32_t piece0, npieces;
     int32_t Kcap;
     int32_t target;        // block id for error reports
-    int32_t pad_;
+    int32_t inst;          // instance of a batch (index into the per-instance tolerances), else 0
 };
 
 struct Piece {

@@ -25,7 +25,8 @@ STATUS = {0: "HLU_OK", 1: "HLU_EINVAL", 2: "HLU_ENOMEM", 3: "HLU_ESTATE", 4: "HL
 EXPORTS = ("hlu_create", "hlu_factor", "hlu_solve", "hlu_matvec", "hlu_solve_refined", "hlu_solve_gmres",
            "hlu_factor_doubles",
            "hlu_get_factors", "hlu_get_stats", "hlu_set_profiling", "hlu_destroy", "hlu_strerror",
-           "hlu_last_error_detail", "hlu_last_cuda_error", "hlu_probe_alu_peaks", "hlu_inject_stall")
+           "hlu_last_error_detail", "hlu_last_cuda_error", "hlu_probe_alu_peaks", "hlu_inject_stall",
+           "hlu_create_batch", "hlu_factor_batch", "hlu_batch_count")
 KINDS = ("getrf", "trsm", "project", "accum", "radd", "split", "dataflow_factor", "dataflow_solve",
          "dataflow_matvec")
 
@@ -104,6 +105,10 @@ def load(path=LIB_PATH):
     lib.hlu_create.argtypes = [ctypes.POINTER(_Tree), ctypes.POINTER(_Blocks), ctypes.POINTER(_Opts), vp,
                                ctypes.POINTER(vp)]
     lib.hlu_factor.argtypes = [vp, dbl]
+    lib.hlu_create_batch.argtypes = [i32, ctypes.POINTER(_Tree), ctypes.POINTER(_Blocks), ctypes.POINTER(_Opts), vp,
+                                     ctypes.POINTER(vp)]
+    lib.hlu_factor_batch.argtypes = [vp, ctypes.POINTER(dbl)]
+    lib.hlu_batch_count.argtypes = [vp]
     lib.hlu_solve.argtypes = [vp, vp, i32, i64]
     lib.hlu_matvec.argtypes = [vp, vp, vp, i32, i64]
     lib.hlu_solve_refined.argtypes = [vp, vp, vp, i32, i64, dbl, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl)]
@@ -161,6 +166,19 @@ def to_device_panel(a, device="cuda"):
     return torch.tensor(np.ascontiguousarray(a.T), device=device).t()
 
 
+def _describe(n, perm, begin, size, son0, son1, row_cl, col_cl, kind, rank, offset, data):
+    """(_Tree, _Blocks, arrays they point into) of one problem; the arrays must outlive the structs."""
+    keep = [np.ascontiguousarray(a, dtype=t) for a, t in (
+        (perm, np.int32), (begin, np.int32), (size, np.int32), (son0, np.int32), (son1, np.int32),
+        (row_cl, np.int32), (col_cl, np.int32), (kind, np.int8), (rank, np.int32), (offset, np.int64),
+        (data, np.float64))]
+    perm_, begin_, size_, son0_, son1_, row_, col_, kind_, rank_, off_, data_ = keep
+    tree = _Tree(int(n), int(begin_.shape[0]), _ptr(perm_), _ptr(begin_), _ptr(size_), _ptr(son0_), _ptr(son1_))
+    blocks = _Blocks(int(row_.shape[0]), _ptr(row_), _ptr(col_), _ptr(kind_), _ptr(rank_), _ptr(off_),
+                     _ptr(data_), int(data_.shape[0]))
+    return tree, blocks, keep
+
+
 def probe_alu_peaks():
     """(FP64, FP32) FMA throughput of the current GPU in TFLOP/s."""
     a, b = ctypes.c_double(), ctypes.c_double()
@@ -176,28 +194,51 @@ class HLU:
     def __init__(self, n, perm, begin, size, son0, son1, row_cl, col_cl, kind, rank, offset, data,
                  precision=HLU_FP64, rank_cap=0, nrhs_max=0, mem_budget=0, stream=None,
                  schedule=SCHED_DATAFLOW, timeout_s=0.0):
+        tree, blocks, keep = _describe(n, perm, begin, size, son0, son1, row_cl, col_cl, kind, rank, offset, data)
+        self._open(1, ctypes.byref(tree), ctypes.byref(blocks), [int(n)], int(blocks.n_leaves), precision, rank_cap,
+                   nrhs_max, mem_budget, stream, schedule, timeout_s)
+
+    def _open(self, count, trees, blocks, sizes, n_leaves, precision, rank_cap, nrhs_max, mem_budget, stream,
+              schedule, timeout_s):
         lib = load()
         self._h = ctypes.c_void_p()
-        keep = [np.ascontiguousarray(a, dtype=t) for a, t in (
-            (perm, np.int32), (begin, np.int32), (size, np.int32), (son0, np.int32), (son1, np.int32),
-            (row_cl, np.int32), (col_cl, np.int32), (kind, np.int8), (rank, np.int32), (offset, np.int64),
-            (data, np.float64))]
-        perm_, begin_, size_, son0_, son1_, row_, col_, kind_, rank_, off_, data_ = keep
-        tree = _Tree(int(n), int(begin_.shape[0]), _ptr(perm_), _ptr(begin_), _ptr(size_), _ptr(son0_), _ptr(son1_))
-        blocks = _Blocks(int(row_.shape[0]), _ptr(row_), _ptr(col_), _ptr(kind_), _ptr(rank_), _ptr(off_),
-                         _ptr(data_), int(data_.shape[0]))
         opts = _Opts(int(precision), int(rank_cap), int(nrhs_max), int(schedule), int(mem_budget), float(timeout_s))
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
-        self.n = int(n)
-        self.n_leaves = int(row_.shape[0])
+        self.n = int(sum(sizes))
+        self.sizes = tuple(sizes)
+        self.n_leaves = n_leaves
         self.precision = int(precision)
-        st = lib.hlu_create(ctypes.byref(tree), ctypes.byref(blocks), ctypes.byref(opts), ctypes.c_void_p(stream),
-                            ctypes.byref(self._h))
+        if count == 1:
+            st = lib.hlu_create(trees, blocks, ctypes.byref(opts), ctypes.c_void_p(stream), ctypes.byref(self._h))
+        else:
+            st = lib.hlu_create_batch(count, trees, blocks, ctypes.byref(opts), ctypes.c_void_p(stream),
+                                      ctypes.byref(self._h))
         if st != 0:
             self._h = ctypes.c_void_p()
-            raise HLUError(st, "hlu_create")
+            raise HLUError(st, "hlu_create" if count == 1 else "hlu_create_batch")
+
+    @classmethod
+    def batch(cls, problems, precision=HLU_FP64, rank_cap=0, nrhs_max=0, mem_budget=0, stream=None,
+              schedule=SCHED_DATAFLOW, timeout_s=0.0):
+        """One handle for several independent problems (hlu_create_batch): the block-diagonal
+        system whose rows are the problems' rows in turn (offsets of self.sizes)."""
+        descs = [_describe(p.n, p.tree.perm, p.tree.begin, p.tree.size, p.tree.son0, p.tree.son1, p.row_cl,
+                           p.col_cl, p.kind, p.rank, p.offset, p.data) for p in problems]
+        if not descs:
+            raise ValueError("batch needs at least one problem")
+        trees = (_Tree * len(descs))(*[d[0] for d in descs])
+        blocks = (_Blocks * len(descs))(*[d[1] for d in descs])
+        self = cls.__new__(cls)
+        self._open(len(descs), trees, blocks, [p.n for p in problems], sum(int(d[1].n_leaves) for d in descs),
+                   precision, rank_cap, nrhs_max, mem_budget, stream, schedule, timeout_s)
+        return self
+
+    @property
+    def count(self):
+        """Number of problems in the handle (hlu_batch_count)."""
+        return load().hlu_batch_count(self._h)
 
     @classmethod
     def from_problem(cls, p, **kw):
@@ -212,7 +253,15 @@ class HLU:
             raise HLUError(st, what)
 
     def factor(self, eps):
-        self._check(load().hlu_factor(self._h, float(eps)), "hlu_factor")
+        """H-LU with tolerance eps; a sequence gives one tolerance per problem of a batch."""
+        if np.ndim(eps) == 0:
+            self._check(load().hlu_factor(self._h, float(eps)), "hlu_factor")
+            return
+        e = np.ascontiguousarray(eps, dtype=np.float64)
+        if e.shape != (self.count,):
+            raise ValueError(f"expected {self.count} tolerances, got shape {e.shape}")
+        self._check(load().hlu_factor_batch(self._h, e.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+                    "hlu_factor_batch")
 
     def solve(self, b):
         """Overwrite the CUDA float64 panel b (n,) or (n, nrhs) column-major with A^{-1} b."""

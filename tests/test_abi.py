@@ -1,6 +1,7 @@
 """The C-ABI library loads, exports every declared entry point, and rejects
 malformed H-matrices during host-side validation (no GPU needed: validation
 happens before any device call)."""
+import copy
 import ctypes
 import os
 import re
@@ -120,4 +121,22 @@ def test_rejects_leaf_cluster_above_128(lib):
     n = 200
     with pytest.raises(HLUError) as e:
         HLU(n, np.arange(n), [0], [n], [-1], [-1], [0], [0], [0], [0], [0], np.eye(n).ravel(order="F"), stream=0)
+    assert e.value.status == 1
+
+
+def test_batch_rejects_bad_count_and_bad_problem(lib, prob1280):
+    """hlu_create_batch validates every problem of the batch (and count >= 1)
+    before any device call."""
+    from paper_1906_00874_gb300.hlu import HLU, HLUError, _Blocks, _Opts, _Tree
+    h = ctypes.c_void_p(1)
+    st = lib.hlu_create_batch(0, ctypes.POINTER(_Tree)(), ctypes.POINTER(_Blocks)(), ctypes.byref(_Opts()),
+                              ctypes.c_void_p(0), ctypes.byref(h))
+    assert st == 1 and not h.value
+    assert lib.hlu_batch_count(None) == 0
+    bad = copy.copy(prob1280)
+    keep = np.arange(1, prob1280.n_leaves)
+    bad.row_cl, bad.col_cl = prob1280.row_cl[keep], prob1280.col_cl[keep]
+    bad.kind, bad.rank, bad.offset = prob1280.kind[keep], prob1280.rank[keep], prob1280.offset[keep]
+    with pytest.raises(HLUError) as e:
+        HLU.batch([prob1280, bad], stream=0)
     assert e.value.status == 1
