@@ -231,6 +231,8 @@ typedef struct {
     int32_t max_stacked;      /* largest stacked-rank capacity of a rounded addition */
     int64_t rank_hist[34];    /* low-rank leaves of L and U by rank after the factorisation:
                                  [k] for k = 0 .. 32, [33] for ranks above 32 */
+    double create_ms[2];      /* host time of hlu_create: [0] validation and planning of the task
+                                 graphs, [1] device allocation, upload and kernel set-up */
 } hlu_stats;
 
 int hlu_get_stats(hlu_t h, hlu_stats *out);

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <functional>
 #include <cmath>
 #include <cstring>
@@ -103,6 +104,7 @@ struct hlu_ctx {
     bool inject_stall = false;           // next data-flow factorisation: one task never becomes ready
     double *eps_inst = nullptr;          // per-instance tolerances of a batch (device), used when eps_each
     bool eps_each = false;
+    double create_ms[2] = {0.0, 0.0};    // host time of hlu_create: validation + planning, device set-up
 };
 
 namespace {
@@ -434,6 +436,7 @@ static int create_impl(const hlu_tree *tree, const hlu_blocks *blocks, const hlu
     if (!out) return HLU_EINVAL;
     *out = nullptr;
     if (!tree || !blocks) return HLU_EINVAL;
+    const auto t0 = std::chrono::steady_clock::now();
     hlu_ctx *h = new (std::nothrow) hlu_ctx();
     if (!h) return HLU_ENOMEM;
     PlanOptions po;
@@ -456,6 +459,7 @@ static int create_impl(const hlu_tree *tree, const hlu_blocks *blocks, const hlu
                          blocks->offset, blocks->data, blocks->data_len, po, inst, n_inst);
     if (st == HLU_OK && h->pl.max_leaf > 128) st = HLU_EINVAL;  // a dense leaf column lives in one warp's registers
     if (st == HLU_OK) st = h->pl.plan_all();
+    const auto t1 = std::chrono::steady_clock::now();
     if (st == HLU_OK) {
         // the FP64 kernels always run the matrix-vector product on A_H
         const bool attrs = set_kernel_attributes<double>() &&
@@ -488,6 +492,9 @@ static int create_impl(const hlu_tree *tree, const hlu_blocks *blocks, const hlu
         hlu_destroy(h);
         return st;
     }
+    const auto t2 = std::chrono::steady_clock::now();
+    h->create_ms[0] = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    h->create_ms[1] = std::chrono::duration<double, std::milli>(t2 - t1).count();
     *out = h;
     return HLU_OK;
 }
@@ -941,6 +948,8 @@ int hlu_get_stats(hlu_t h, hlu_stats *o) {
     o->tasks_by_kind[5] = (int64_t)f.split.size();
     o->max_stacked = f.max_kcap;
     o->kernels_launched = h->kernels_launched;
+    o->create_ms[0] = h->create_ms[0];
+    o->create_ms[1] = h->create_ms[1];
     for (int k = 0; k < kProfSlots; ++k) {
         o->kernel_ms[k] = h->prof_ms[k];
         o->kernel_launches[k] = h->prof_count[k];

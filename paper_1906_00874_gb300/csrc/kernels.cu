@@ -70,6 +70,15 @@ __device__ __forceinline__ R warp_sum_t(R v) {
     return v;
 }
 
+__device__ __forceinline__ float warp_max_f(float v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+// Largest column count of a truncation core: the dense route takes n <= 128,
+// the stacked route kv <= the stacked-rank limit (96).
+constexpr int kVRows = 128;
+
 // Cooperative copy of n elements: element e is read by src(e) and written by
 // dst(e, v), one element per thread and step.
 template <class T, class Src, class Dst>
@@ -668,6 +677,96 @@ __device__ int block_jacobi(double *D, int r, int ld, int *flag) {
     return sweep;
 }
 
+// The same rotation entirely in single precision, for cores whose data are
+// single precision (their singular values are only known to that level).
+__device__ __forceinline__ void jacobi_rotation_f(float aa, float bb, float gg, float &c, float &s) {
+    const float z = (bb - aa) / (2.0f * gg), az = fabsf(z);
+    float t;
+    if (!(az < 1e15f))
+        t = isinf(z) ? 0.0f : 0.5f / z;
+    else
+        t = copysignf(1.0f, z) / (az + sqrtf(fmaf(z, z, 1.0f)));
+    c = rsqrtf(fmaf(t, t, 1.0f));
+    s = c * t;
+}
+
+// One-sided Jacobi in single precision on the columns of X (r x r, shared
+// memory, leading dimension r), in place, with the rotations accumulated in W
+// (r x r, W = I on entry): X_in W = X_out = B with orthogonal columns, W
+// orthogonal.  Same round-robin ordering and lane groups as block_jacobi; a
+// pair is rotated while |x.y| > tol |x| |y|, tol = 4 r eps_single.  X should
+// be scaled so that its largest entry is near 1 (no overflow of the squared
+// norms).  Returns the number of sweeps (at most 30).
+__device__ int block_jacobi_f(float *X, float *W, int r, int *flag) {
+    if (r < 2) return 0;
+    const int np = (r + 1) & ~1, P = np / 2;
+    int g = 32;
+    while (g > 1 && g * P > (int)blockDim.x) g >>= 1;
+    while (g > 1 && (g >> 1) >= r) g >>= 1;
+    const bool one_warp = g * P <= 32;
+    const int gid = threadIdx.x / g, gl = threadIdx.x % g;
+    const float tol = 4.0f * r * FLT_EPSILON;
+    int sweep = 0;
+    while (sweep < 30) {
+        ++sweep;
+        if (threadIdx.x == 0) *flag = 0;
+        __syncthreads();
+        if (!one_warp || threadIdx.x < 32) {  // uniform per warp
+            for (int rd = 0; rd < np - 1; ++rd) {
+                int p, q;
+                if (gid == 0) {
+                    p = rd;
+                    q = np - 1;
+                } else {
+                    p = (rd + gid) % (np - 1);
+                    q = (rd - gid + np - 1) % (np - 1);
+                }
+                if (p > q) {
+                    const int tmp = p;
+                    p = q;
+                    q = tmp;
+                }
+                const bool active = gid < P && q < r;
+                float *cp = X + p * r, *cq = X + q * r, *wp = W + p * r, *wq = W + q * r;
+                float aa = 0.0f, bb = 0.0f, gg = 0.0f;
+                if (active)
+                    for (int i = gl; i < r; i += g) {
+                        const float x = cp[i], y = cq[i];
+                        aa = fmaf(x, x, aa);
+                        bb = fmaf(y, y, bb);
+                        gg = fmaf(x, y, gg);
+                    }
+                for (int o = g >> 1; o > 0; o >>= 1) {
+                    aa += __shfl_xor_sync(kFull, aa, o);
+                    bb += __shfl_xor_sync(kFull, bb, o);
+                    gg += __shfl_xor_sync(kFull, gg, o);
+                }
+                if (active && fabsf(gg) > tol * sqrtf(aa) * sqrtf(bb)) {
+                    if (gl == 0) *flag = 1;
+                    float cs, sn;
+                    jacobi_rotation_f(aa, bb, gg, cs, sn);
+                    for (int i = gl; i < r; i += g) {
+                        const float x = cp[i], y = cq[i], u = wp[i], v = wq[i];
+                        cp[i] = cs * x - sn * y;
+                        cq[i] = sn * x + cs * y;
+                        wp[i] = cs * u - sn * v;
+                        wq[i] = sn * u + cs * v;
+                    }
+                }
+                if (one_warp)
+                    __syncwarp();
+                else
+                    __syncthreads();
+            }
+        }
+        __syncthreads();
+        const int f = *flag;
+        __syncthreads();
+        if (!f) break;
+    }
+    return sweep;
+}
+
 // QR with column pivoting of the mr x nc core M (precision R, shared memory,
 // column major), stopped at the first step whose largest remaining column
 // norm is at most delta times the first pivot's: M P = Q [R'; ~0] with R' of
@@ -780,6 +879,7 @@ template <class R>
 struct CoreBufs {
     double *D, *sig;                       // Jacobi factor (rc x rc), singular values
     R *M, *C, *cn, *tauM, *tauC, *B, *isg;  // B: D in precision R (aliases D when R is double)
+    R *W;                                   // single precision: accumulated rotations (in D's space)
     R *tauU, *tauV, *nrmU, *nrmV;
     int *order, *perm, *iflag;
 };
@@ -811,9 +911,11 @@ __device__ CoreBufs<R> carve_core(unsigned char *base, int mr, int nc, bool stac
     x += 3 * rc;
     if constexpr (sizeof(R) == 8) {
         b.B = b.D;
+        b.W = nullptr;
     } else {
         b.B = x;
         x += rc * rc;
+        b.W = reinterpret_cast<R *>(b.D);  // r x r floats fit in the rc x rc doubles of D
     }
     b.tauU = b.tauV = b.nrmU = b.nrmV = nullptr;
     if (stacked) {
@@ -835,10 +937,14 @@ __device__ CoreBufs<R> carve_core(unsigned char *base, int mr, int nc, bool stac
 // the two QR preconditioning steps of Drmac and Veselic (2008):
 //   M P = Q_M [R'; ~0]        pivoted QR in the core precision R, r rows
 //   R'^T = Q_C R_C            Householder QR of the nc x r factor, in R
-//   R_C^T W = B               one-sided Jacobi in double on the r x r lower
+//   R_C^T W = B               one-sided Jacobi on the r x r lower
 //                             triangular X = R_C^T; sigma_j = |B_j|
-// so that M = (Q_M [B; 0]) (P Q_C W)^T, and since M^T Q_M [B; 0] = P R'^T B,
-// the right factor is P R'^T B Sigma^{-2}: neither Q_C nor W is formed.
+// so that M = (Q_M [B; 0]) (P Q_C W)^T.  Double-precision cores (R = double)
+// run the Jacobi in double without forming W: since M^T Q_M [B; 0] = P R'^T B,
+// the right factor is P R'^T B Sigma^{-2}.  Single-precision cores run it in
+// single precision with W accumulated, and the right factor is P Q_C [W; 0]
+// (Sigma^{-2} would amplify the single-precision error of B in the columns
+// of small sigma).
 // Singular values sigma_i <= eps sigma_1 are dropped.  Returns the kept rank
 // (order[0..knew) lists the kept columns of B by decreasing sigma, lowest
 // index on ties) and r through r_out; leaves B in precision R (b.B) and
@@ -853,18 +959,52 @@ __device__ int core_finish(const CoreBufs<R> &b, int mr, int nc, int r, const TR
         const int c = e % nc, i = e / nc;
         b.C[e] = c >= i ? b.M[i + (size_t)c * mr] : R(0);
     }
+    if (threadIdx.x == 0) b.iflag[2] = 0;  // [0]: Jacobi flag, [1]: pivoted-QR flag
     __syncthreads();
     group_householder_qr<R>(b.C, nc, r, b.tauC, b.cn, 0, blockDim.x >> 5, 0);
-    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {  // X = R_C^T
-        const int i = e % r, j = e / r;
-        b.D[e] = i >= j ? (double)b.C[j + (size_t)i * nc] : 0.0;
-    }
-    __syncthreads();
-    const int sweeps = block_jacobi(b.D, r, r, b.iflag);
-    for (int j = threadIdx.x; j < r; j += blockDim.x) {
-        double s = 0.0;
-        for (int i = 0; i < r; ++i) s += b.D[i + (size_t)j * r] * b.D[i + (size_t)j * r];
-        b.sig[j] = sqrt(s);
+    int sweeps;
+    if constexpr (sizeof(R) == 8) {
+        for (int e = threadIdx.x; e < r * r; e += blockDim.x) {  // X = R_C^T
+            const int i = e % r, j = e / r;
+            b.D[e] = i >= j ? b.C[j + (size_t)i * nc] : 0.0;
+        }
+        __syncthreads();
+        sweeps = block_jacobi(b.D, r, r, b.iflag);
+        for (int j = threadIdx.x; j < r; j += blockDim.x) {
+            double s = 0.0;
+            for (int i = 0; i < r; ++i) s += b.D[i + (size_t)j * r] * b.D[i + (size_t)j * r];
+            b.sig[j] = sqrt(s);
+        }
+    } else {
+        // X = R_C^T and W = I; X is scaled by a power of two 2^-e (exact) that brings its largest
+        // entry into [1, 2), so the single-precision squared norms neither overflow nor underflow
+        float mx = 0.0f;
+        for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+            const int i = e % r, j = e / r;
+            const float v = i >= j ? b.C[j + (size_t)i * nc] : 0.0f;
+            b.B[e] = v;
+            b.W[e] = i == j ? 1.0f : 0.0f;
+            mx = fmaxf(mx, fabsf(v));
+        }
+        mx = warp_max_f(mx);
+        if ((threadIdx.x & 31) == 0 && mx > 0.0f) atomicMax(b.iflag + 2, __float_as_int(mx));
+        __syncthreads();
+        const float amax = __int_as_float(b.iflag[2]);
+        const int ex = (amax > 0.0f && amax <= FLT_MAX) ? ((__float_as_int(amax) >> 23) & 0xff) - 127 : 0;
+        const float down = __int_as_float((127 - max(-126, min(126, ex))) << 23);  // 2^-ex
+        const float up = __int_as_float((127 + max(-126, min(126, ex))) << 23);    // 2^ex
+        if (ex != 0)
+            for (int e = threadIdx.x; e < r * r; e += blockDim.x) b.B[e] *= down;
+        __syncthreads();
+        sweeps = block_jacobi_f(b.B, b.W, r, b.iflag);
+        for (int j = threadIdx.x; j < r; j += blockDim.x) {
+            float s = 0.0f;
+            for (int i = 0; i < r; ++i) s = fmaf(b.B[i + j * r], b.B[i + j * r], s);
+            b.sig[j] = (double)sqrtf(s) * (double)up;
+        }
+        __syncthreads();
+        if (ex != 0)
+            for (int e = threadIdx.x; e < r * r; e += blockDim.x) b.B[e] *= up;
     }
     __syncthreads();
     for (int j = threadIdx.x; j < r; j += blockDim.x) {
@@ -873,8 +1013,6 @@ __device__ int core_finish(const CoreBufs<R> &b, int mr, int nc, int r, const TR
         b.order[rk] = j;
         b.isg[j] = b.sig[j] > 0.0 ? R(1.0 / b.sig[j]) : R(0);
     }
-    if constexpr (sizeof(R) != 8)
-        for (int e = threadIdx.x; e < r * r; e += blockDim.x) b.B[e] = R(b.D[e]);
     __syncthreads();
     const double s1 = r > 0 ? b.sig[b.order[0]] : 0.0;
     int knew = 0;
@@ -910,14 +1048,54 @@ __device__ int core_truncate(const CoreBufs<R> &b, int mr, int nc, double delta,
 // sigma^2 for the nc rows of the core (V of type T, leading dimension ldv).
 template <class R, class T>
 __device__ void core_write_v(const CoreBufs<R> &b, int mr, int nc, int r, int knew, T *V, int64_t ldv) {
-    for (int e = threadIdx.x; e < nc * knew; e += blockDim.x) {
-        const int c = e % knew, i = e / knew;
-        const int j = b.order[c];
-        const int lmax = min(i, r - 1);
-        const R *bj = b.B + (size_t)j * r;
-        R s = R(0);
-        for (int l = 0; l <= lmax; ++l) s += b.M[l + (size_t)i * mr] * bj[l];
-        V[b.perm[i] + (int64_t)c * ldv] = T((s * b.isg[j]) * b.isg[j]);
+    if constexpr (sizeof(R) == 8) {
+        for (int e = threadIdx.x; e < nc * knew; e += blockDim.x) {
+            const int c = e % knew, i = e / knew;
+            const int j = b.order[c];
+            const int lmax = min(i, r - 1);
+            const R *bj = b.B + (size_t)j * r;
+            R s = R(0);
+            for (int l = 0; l <= lmax; ++l) s += b.M[l + (size_t)i * mr] * bj[l];
+            V[b.perm[i] + (int64_t)c * ldv] = T((s * b.isg[j]) * b.isg[j]);
+        }
+    } else {
+        // V[perm[i], c] = (Q_C [W_sel; 0])[i, c]: the rotations were accumulated in single precision,
+        // so the right factor is formed from them (orthonormal columns) rather than through
+        // Sigma^{-2}, which would amplify their single-precision error.  One warp per column, the
+        // nc <= kVRows entries of y in registers; ends with a barrier (b.C is overwritten next).
+        const int lane = threadIdx.x & 31;
+        for (int c = threadIdx.x >> 5; c < knew; c += blockDim.x >> 5) {
+            const R *wj = b.W + (size_t)b.order[c] * r;
+            R y[kVRows / 32];
+#pragma unroll
+            for (int k = 0; k < kVRows / 32; ++k) {
+                const int i = lane + 32 * k;
+                y[k] = i < r ? wj[i] : R(0);
+            }
+            for (int q = r - 1; q >= 0; --q) {  // y := H_q y, H_q = I - tau_q v_q v_q^T, v_q[q] = 1
+                const R *v = b.C + (size_t)q * nc;
+                R d = R(0);
+#pragma unroll
+                for (int k = 0; k < kVRows / 32; ++k) {
+                    const int i = lane + 32 * k;
+                    if (i > q && i < nc) d += v[i] * y[k];
+                    if (i == q) d += y[k];
+                }
+                d = warp_sum_t(d) * b.tauC[q];
+#pragma unroll
+                for (int k = 0; k < kVRows / 32; ++k) {
+                    const int i = lane + 32 * k;
+                    if (i > q && i < nc) y[k] -= d * v[i];
+                    if (i == q) y[k] -= d;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < kVRows / 32; ++k) {
+                const int i = lane + 32 * k;
+                if (i < nc) V[b.perm[i] + (int64_t)c * ldv] = T(y[k]);
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -940,9 +1118,9 @@ __device__ void core_form_u(const CoreBufs<R> &b, int mr, int r, int knew) {
 // zero-padded to the target's index ranges); both stacks are reduced by
 // Householder QR (concurrently, one half of the CTA each), and the core
 // M = R_u R_v^T is truncated by core_truncate; the new factors are
-// U = Q_u [Q_M [B_sel; 0]; 0], V = Q_v [P R'^T B_sel Sigma^{-2}; 0].
-// Everything but the Jacobi SVD of the r x r factor runs in the precision T
-// of the factors; the Jacobi SVD runs in double.
+// U = Q_u [Q_M [B_sel; 0]; 0], V = Q_v [P R'^T B_sel Sigma^{-2}; 0] (double
+// factors) or V = Q_v [P Q_C W_sel; 0] (single-precision factors).
+// Everything runs in the precision T of the factors.
 //
 // Shared memory is carved by the task's own core size: the core buffers first
 // (core_bytes), then, when they fit in the rest of the CTA's `smem_bytes`,
@@ -1025,9 +1203,11 @@ __device__ bool radd_small(const TRadd &t, const Piece *pieces, const LaunchArgs
     b.isg = b.tauC + r;
     if constexpr (sizeof(T) == 8) {
         b.B = b.D;
+        b.W = nullptr;
         b.order = reinterpret_cast<int *>(b.isg + r);
     } else {
         b.B = b.isg + r;
+        b.W = reinterpret_cast<T *>(b.D);  // r x r floats in the r x r doubles of D
         b.order = reinterpret_cast<int *>(b.B + r * r);
     }
     const int knew = core_finish<T>(b, m, n, r, t, a, 0, ph);

@@ -93,7 +93,8 @@ struct Plan {
 struct PlanOptions {
     int32_t rank_cap = 32;
     int32_t nrhs_max = 64;
-    int32_t kmax_core = 96;  // largest stacked rank a rounded addition handles
+    int32_t kmax_core = 96;  // largest stacked rank a rounded addition handles (at most 128: the
+                             // truncation core keeps a column of its right factor in one warp)
 };
 
 class Planner {

@@ -66,15 +66,16 @@ class Stats(ctypes.Structure):
                 ("solve_busy_ms", ctypes.c_double * 8), ("solve_task_count", ctypes.c_int64 * 8),
                 ("radd_phase", ctypes.c_double * 16),
                 ("kernels_launched", ctypes.c_int64), ("max_rank", ctypes.c_int32), ("max_stacked", ctypes.c_int32),
-                ("rank_hist", ctypes.c_int64 * 34)]
+                ("rank_hist", ctypes.c_int64 * 34), ("create_ms", ctypes.c_double * 2)]
 
     def as_dict(self):
         per_kind = ("tasks_by_kind", "flops_by_kind", "kernel_ms", "kernel_launches", "task_busy_ms", "task_count",
                     "solve_busy_ms", "solve_task_count")
         per_size = ("radd_busy_ms", "radd_count")
         d = {f: getattr(self, f) for f, _ in self._fields_
-             if f not in per_kind + per_size + ("radd_phase", "rank_hist")}
+             if f not in per_kind + per_size + ("radd_phase", "rank_hist", "create_ms")}
         d["rank_hist"] = list(self.rank_hist)
+        d["create_ms"] = {"plan": self.create_ms[0], "device_setup": self.create_ms[1]}
         ph = list(self.radd_phase)
         d["radd_phase"] = {}
         for route, b in (("dense", 0), ("stacked", 8)):
