@@ -37,3 +37,26 @@ def batch_specs(count, levels=(3, 4), eps=(1e-4, 1e-6), leaf=32, eta=2.0):
         a, b = (float(v) for v in g.uniform(0.4, 1.0, 2))
         out.append(dict(r=r, leaf=leaf, eta=eta, eps=e, nrhs=1, seed=i, axes=(1.0, round(a, 6), round(b, 6))))
     return out
+
+
+# Request streams for the serving loop.
+STREAMS = {
+    "serve64": dict(requests=64, repeat=0.3, nrhs=(1, 64), levels=(3, 4), eps=(1e-4, 1e-6), leaf=32, eta=2.0),
+}
+
+
+def stream_specs(requests, repeat=0.3, nrhs=(1, 64), seed=0, **batch_kw):
+    """A seeded request stream: a list of (problem index, nrhs, rhs seed) and the build_problem
+    keyword arguments of every distinct problem.  Each request repeats an earlier problem with
+    probability `repeat` (uniform over those seen), else names a new one (problem i of
+    batch_specs); nrhs is uniform in the closed range `nrhs`.  Arrival times are the caller's."""
+    import numpy as np
+    g = np.random.default_rng(seed)
+    reqs, n_prob = [], 0
+    for i in range(requests):
+        if n_prob and g.random() < repeat:
+            k = int(g.integers(n_prob))
+        else:
+            k, n_prob = n_prob, n_prob + 1
+        reqs.append((k, int(g.integers(nrhs[0], nrhs[1] + 1)), 1000 + i))
+    return reqs, batch_specs(n_prob, **batch_kw)

@@ -1,0 +1,122 @@
+"""Host logic of the serving loop (paper_1906_00874_gb300.serve) on the CPU:
+request packing into the stacked block-diagonal system, the stacked
+tolerance, admission under the device-memory budget and LRU eviction.
+
+The handle is a dense stand-in with the library's interface (no GPU): each
+problem is a small dense matrix, the stacked solve is an exact dense solve
+of the block-diagonal system, and creation fails with the library's ENOMEM
+status when it would exceed the handle's memory budget."""
+import numpy as np
+import pytest
+
+from paper_1906_00874_gb300.hlu import HLUError
+from paper_1906_00874_gb300.serve import Request, Server
+
+
+class _Prob:
+    def __init__(self, n, seed, eps=1e-4):
+        g = np.random.default_rng(seed)
+        self.n, self.eps = n, eps
+        self.A = g.standard_normal((n, n)) + n * np.eye(n)
+
+
+class _FakeHLU:
+    created = []
+
+    def __init__(self, probs, mem_budget):
+        self.probs = probs
+        self.bytes = sum(8 * p.n * p.n for p in probs)
+        if mem_budget and self.bytes > mem_budget:
+            raise HLUError(2, "fake: over budget")
+        self.factored = None
+        self.solve_tols = []
+        _FakeHLU.created.append(self)
+
+    @classmethod
+    def batch(cls, probs, precision=None, mem_budget=0, stream=None):
+        return cls(list(probs), mem_budget)
+
+    @classmethod
+    def from_problem(cls, p, precision=None, mem_budget=0, stream=None):
+        return cls([p], mem_budget)
+
+    def stats(self):
+        return {"device_bytes": self.bytes}
+
+    def factor(self, eps):
+        self.factored = list(np.atleast_1d(eps))
+
+    def solve_refined(self, b, x, tol=1e-10, max_iter=20):
+        import scipy.linalg
+        self.solve_tols.append(tol)
+        A = scipy.linalg.block_diag(*[p.A for p in self.probs])
+        import torch
+        x.copy_(torch.from_numpy(np.linalg.solve(A, b.numpy())))
+        return 1, 0.0
+
+    def close(self):
+        self.closed = True
+
+
+def _server(budget=1e9, **kw):
+    _FakeHLU.created = []
+    return Server(mem_budget=budget, device="cpu", handle_type=_FakeHLU, **kw)
+
+
+def test_packing_repeats_and_per_problem_eps():
+    probs = {k: _Prob(n, k, eps=10.0 ** -(3 + k)) for k, n in enumerate((5, 7, 4))}
+    g = np.random.default_rng(9)
+    reqs = [Request(k, probs[k], g.standard_normal((probs[k].n, c)), rid=i)
+            for i, (k, c) in enumerate([(0, 2), (1, 1), (0, 3), (2, 2), (1, 1)])]
+    s = _server()
+    for r in reqs:
+        s.submit(r)
+    out = s.step(now=0.0)
+    assert len(out) == 5 and len(_FakeHLU.created) == 1
+    h = _FakeHLU.created[0]
+    assert h.factored == [probs[k].eps for k in (0, 1, 2)]  # one group, one eps per problem
+    for r in reqs:
+        assert np.allclose(probs[r.key].A @ r.x, r.b, atol=1e-10)
+    # the stacked tolerance bounds every request's own relative residual
+    assert h.solve_tols[-1] <= 1e-10
+    # repeats of resident problems are solved, not factorised again
+    r2 = Request(1, None, g.standard_normal((7, 4)), rid=9)
+    s.submit(r2)
+    s.step(now=1.0)
+    assert len(_FakeHLU.created) == 1 and s.stats["factorised_problems"] == 3
+    assert np.allclose(probs[1].A @ r2.x, r2.b, atol=1e-10)
+
+
+def test_only_arrived_requests_are_served():
+    p = _Prob(3, 0)
+    s = _server()
+    s.submit(Request("a", p, np.ones((3, 1)), arrival=5.0))
+    assert s.step(now=1.0) == []
+    assert len(s.step(now=5.0)) == 1
+
+
+def test_budget_evicts_least_recently_used_group():
+    probs = {k: _Prob(10, k) for k in range(3)}   # 800 bytes each
+    s = _server(budget=1700)                      # room for two problems
+    for t, k in enumerate([0, 1, 0, 2]):          # 1 is the least recently used when 2 arrives
+        s.submit(Request(k, probs[k], np.ones((10, 1)), arrival=float(t), rid=t))
+        s.step(now=float(t))
+    assert s.resident(0) and s.resident(2) and not s.resident(1)
+    assert s.stats["evicted_groups"] == 1 and s.resident_bytes <= 1700
+    r = Request(1, probs[1], np.ones((10, 1)), arrival=9.0, rid=9)
+    s.submit(r)
+    s.step(now=9.0)
+    assert r.refactored and np.allclose(probs[1].A @ r.x, r.b)
+
+
+def test_group_too_large_is_split_and_hopeless_problem_raises():
+    probs = {k: _Prob(10, k) for k in range(4)}
+    s = _server(budget=1700)
+    for k in range(2):
+        s.submit(Request(k, probs[k], np.ones((10, 1)), rid=k))
+    s.step(now=0.0)
+    assert s.resident(0) and s.resident(1)
+    big = _Prob(20, 7)                            # 3200 bytes: over the budget on its own
+    s.submit(Request("big", big, np.ones((20, 1)), rid=5))
+    with pytest.raises(HLUError):
+        s.step(now=1.0)
