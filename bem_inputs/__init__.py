@@ -14,6 +14,15 @@ WORKLOADS = {
     "sphere5120": dict(r=4, leaf=32, eta=2.0, eps=1e-4, nrhs=1),
     "sphere20480": dict(r=5, leaf=64, eta=2.0, eps=1e-4, nrhs=16),
     "sphere81920": dict(r=6, leaf=64, eta=2.0, eps=1e-6, nrhs=64),
+    # variants of Table 1 (Sec. 6.3): other eta values, the d = 1, 2 log kernels, and the
+    # dense-only recursive structure of Sec. 6.2 (eta = 0: no admissible block)
+    "sphere20480_eta1": dict(r=5, leaf=64, eta=1.0, eps=1e-4, nrhs=16),
+    "sphere20480_eta0.5": dict(r=5, leaf=64, eta=0.5, eps=1e-4, nrhs=16),
+    "line20480_eta0.5": dict(r=5, leaf=64, eta=0.5, eps=1e-4, nrhs=16, dim=1),
+    "line20480_eta0.25": dict(r=5, leaf=64, eta=0.25, eps=1e-4, nrhs=16, dim=1),
+    "circle20480_eta1": dict(r=5, leaf=64, eta=1.0, eps=1e-4, nrhs=16, dim=2),
+    "circle20480_eta0.25": dict(r=5, leaf=64, eta=0.25, eps=1e-4, nrhs=16, dim=2),
+    "dense5120": dict(r=4, leaf=64, eta=0.0, eps=1e-4, nrhs=16),
 }
 
 # Batches of independent problems: `count` ellipsoids, instance i drawn from seed i.

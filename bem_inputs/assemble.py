@@ -1,12 +1,17 @@
 """Matrix entries and leaf data of the BEM H-matrix.
 
-Kernel: the d = 3 Laplace kernel g(x, y) = 1 / (4 pi |x - y|) of Sec. 6.1, used
-here in collocation form on flat triangles (one centroid c_i and area a_i per
-degree of freedom):
+Kernels: the Laplace kernels of Sec. 6.1 in collocation form, one element
+(centroid c_i, size a_i: area of a flat triangle in d = 3, length of a cell or
+straight panel in d = 1, 2) per degree of freedom:
 
-    A_ij = a_j / (4 pi |c_i - c_j|)   (i != j),
-    A_ii = sqrt(a_i / pi) / 2         (potential at the centre of a flat disc of
-                                        area a_i carrying unit density).
+    A_ij = a_j g(c_i, c_j)   (i != j),   g = 1 / (4 pi |x - y|)      (d = 3)
+                                         g = -log|x - y|             (d = 1)
+                                         g = -log|x - y| / (2 pi)    (d = 2)
+
+and the self-term A_ii = the potential at c_i of the element itself with unit
+density: sqrt(a_i / pi) / 2 for d = 3 (a flat disc of area a_i), and
+a_i (1 - log(a_i / 2)) (d = 1) or that over 2 pi (d = 2), the exact integral of
+-log|t| over |t| <= a_i / 2 (a straight element of length a_i centred at c_i).
 
 Low-rank leaves (Sec. 3.1, "Low-rank blocks": X = A B^*): built by adaptive
 cross approximation with partial pivoting and then recompressed by an SVD of
@@ -25,30 +30,49 @@ import numpy as np
 FOUR_PI = 4.0 * np.pi
 
 
-def kernel_block(centroid, area, rows, cols):
+def _g(r, dim):
+    """Kernel value at distance r > 0."""
+    if dim == 3:
+        return 1.0 / (FOUR_PI * r)
+    if dim == 1:
+        return -np.log(r)
+    if dim == 2:
+        return -np.log(r) / (2.0 * np.pi)
+    raise ValueError(f"dim must be 1, 2 or 3, got {dim}")
+
+
+def self_term(a, dim):
+    """A_ii for elements of size a (see the module docstring)."""
+    if dim == 3:
+        return np.sqrt(a / np.pi) / 2.0
+    s = a * (1.0 - np.log(0.5 * a))
+    return s if dim == 1 else s / (2.0 * np.pi)
+
+
+def kernel_block(centroid, area, rows, cols, dim=3):
     """Dense kernel block A[rows][:, cols] (original DoF indices)."""
     d = centroid[rows][:, None, :] - centroid[cols][None, :, :]
     r = np.sqrt(np.einsum("ijk,ijk->ij", d, d))
     same = rows[:, None] == cols[None, :]
-    with np.errstate(divide="ignore"):
-        out = area[cols][None, :] / (FOUR_PI * r)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        out = area[cols][None, :] * _g(r, dim)
     if same.any():
         ii, jj = np.nonzero(same)
-        out[ii, jj] = np.sqrt(area[rows[ii]] / np.pi) / 2.0
+        out[ii, jj] = self_term(area[rows[ii]], dim)
     return out
 
 
-def _kernel_row(centroid, area, i, cols):
+def _kernel_row(centroid, area, i, cols, dim=3):
     d = centroid[cols] - centroid[i]
-    return area[cols] / (FOUR_PI * np.sqrt(np.einsum("ij,ij->i", d, d)))
+    return area[cols] * _g(np.sqrt(np.einsum("ij,ij->i", d, d)), dim)
 
 
-def _kernel_col(centroid, area, rows, j):
+def _kernel_col(centroid, area, rows, j, dim=3):
     d = centroid[rows] - centroid[j]
-    return area[j] / (FOUR_PI * np.sqrt(np.einsum("ij,ij->i", d, d)))
+    return area[j] * _g(np.sqrt(np.einsum("ij,ij->i", d, d)), dim)
 
 
-def aca_partial(centroid, area, rows, cols, eps):
+def aca_partial(centroid, area, rows, cols, eps, dim=3):
     """ACA with partial pivoting on an admissible block (rows, cols disjoint).
 
     Start row: local row 0.  Column pivot: argmax |residual row| (lowest index
@@ -65,7 +89,7 @@ def aca_partial(centroid, area, rows, cols, eps):
     k = 0
     s2 = 0.0
     while k < kmax:
-        row = _kernel_row(centroid, area, rows[i], cols)
+        row = _kernel_row(centroid, area, rows[i], cols, dim)
         if k:
             row -= V[:, :k] @ U[i, :k]
         used[i] = True
@@ -77,7 +101,7 @@ def aca_partial(centroid, area, rows, cols, eps):
             i = int(free[0])
             continue
         v = row / row[j]
-        u = _kernel_col(centroid, area, rows, cols[j])
+        u = _kernel_col(centroid, area, rows, cols[j], dim)
         if k:
             u -= U[:, :k] @ V[j, :k]
             s2 += 2.0 * float(np.dot(U[:, :k].T @ u, V[:, :k].T @ v))

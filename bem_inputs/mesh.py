@@ -104,3 +104,25 @@ def triangle_data(v, f):
     lo = np.minimum(np.minimum(p0, p1), p2)
     hi = np.maximum(np.maximum(p0, p1), p2)
     return centroid, area, lo, hi
+
+
+def interval_cells(n):
+    """The interval [0, 1] cut into n equal cells (the d = 1 problems of Sec. 6.1), embedded in
+    R^3 on the x axis: (midpoints (n,3), lengths (n,), cell bbox lo/hi (n,3))."""
+    x = np.linspace(0.0, 1.0, n + 1)
+    z = np.zeros(n)
+    lo = np.stack([x[:-1], z, z], axis=1)
+    hi = np.stack([x[1:], z, z], axis=1)
+    return 0.5 * (lo + hi), np.diff(x), lo, hi
+
+
+def ellipse_panels(n, axes=(0.5, 0.5)):
+    """A closed curve for the d = 2 problems of Sec. 6.1: the ellipse with semi-axes `axes`,
+    cut into n straight panels between the points at angles 2 pi i / n, embedded in R^3 in the
+    z = 0 plane: (panel midpoints (n,3), panel lengths (n,), panel bbox lo/hi (n,3)).  The
+    default circle of radius 1/2 has logarithmic capacity 1/2 < 1, so the single-layer
+    operator with kernel -log|x - y| / (2 pi) is positive definite on it."""
+    t = 2.0 * np.pi * np.arange(n + 1) / n
+    p = np.stack([axes[0] * np.cos(t), axes[1] * np.sin(t), np.zeros(n + 1)], axis=1)
+    a, b = p[:-1], p[1:]
+    return 0.5 * (a + b), np.linalg.norm(b - a, axis=1), np.minimum(a, b), np.maximum(a, b)

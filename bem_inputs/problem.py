@@ -23,13 +23,14 @@ import time
 import numpy as np
 
 from .assemble import aca_partial, kernel_block, recompress
-from .mesh import ellipsoid, icosphere, triangle_data
+from .mesh import ellipse_panels, ellipsoid, icosphere, interval_cells, triangle_data
 from .trees import BlockLeaves, ClusterTree, admissible, build_block_leaves, build_cluster_tree
 
 CACHE_VERSION = 4
 
 
 class Problem:
+    dim = 3  # problems cached before the d = 1, 2 kernels existed are d = 3
     def __init__(self, **kw):
         self.__dict__.update(kw)
 
@@ -128,18 +129,24 @@ def _key(**kw):
     return hashlib.sha1(s.encode()).hexdigest()[:16]
 
 
-def build_problem(r, leaf, eta, eps, nrhs=1, seed=0, axes=None, cache=True, verbose=False):
+def build_problem(r, leaf, eta, eps, nrhs=1, seed=0, axes=None, cache=True, verbose=False, dim=3):
     """Build (or load from the on-disk cache) the seeded BEM H-matrix problem.
 
-    r     refinement steps of the icosahedron (n = 20 * 4**r)
+    r     size: n = 20 * 4**r (refinement steps of the icosahedron for dim = 3)
     leaf  C_lf, the cluster-tree leaf size
-    eta   admissibility parameter
+    eta   admissibility parameter (0: no admissible block, every leaf dense)
     eps   ACA / recompression tolerance
     nrhs  number of right-hand sides, b = default_rng(seed).standard_normal((nrhs, n)).T
-    axes  None for the unit sphere, else ellipsoid axes (ax, ay, az)
+    axes  dim 3: None for the unit sphere, else ellipsoid axes (ax, ay, az);
+          dim 2: the ellipse's semi-axes (default (0.5, 0.5)); dim 1: unused
+    dim   3: surface of a sphere or ellipsoid, kernel 1 / (4 pi |x - y|);
+          2: closed curve, kernel -log|x - y| / (2 pi); 1: interval [0, 1], kernel -log|x - y|
     """
-    key = _key(r=r, leaf=leaf, eta=float(eta), eps=float(eps), nrhs=nrhs, seed=seed,
-               axes=None if axes is None else tuple(float(a) for a in axes))
+    kw = dict(r=r, leaf=leaf, eta=float(eta), eps=float(eps), nrhs=nrhs, seed=seed,
+              axes=None if axes is None else tuple(float(a) for a in axes))
+    if dim != 3:
+        kw["dim"] = int(dim)
+    key = _key(**kw)
     path = os.path.join(_cache_dir(), f"hmat_{key}.npz") if cache else None
     if path and os.path.exists(path):
         try:
@@ -147,8 +154,15 @@ def build_problem(r, leaf, eta, eps, nrhs=1, seed=0, axes=None, cache=True, verb
         except Exception:
             pass
     t0 = time.time()
-    v, f = icosphere(r) if axes is None else ellipsoid(r, axes)
-    centroid, area, lo, hi = triangle_data(v, f)
+    if dim == 3:
+        v, f = icosphere(r) if axes is None else ellipsoid(r, axes)
+        centroid, area, lo, hi = triangle_data(v, f)
+    elif dim == 2:
+        centroid, area, lo, hi = ellipse_panels(20 * 4 ** r, (0.5, 0.5) if axes is None else axes)
+    elif dim == 1:
+        centroid, area, lo, hi = interval_cells(20 * 4 ** r)
+    else:
+        raise ValueError(f"dim must be 1, 2 or 3, got {dim}")
     n = centroid.shape[0]
     tree = build_cluster_tree(centroid, lo, hi, leaf)
     bl = build_block_leaves(tree, eta)
@@ -171,7 +185,7 @@ def build_problem(r, leaf, eta, eps, nrhs=1, seed=0, axes=None, cache=True, verb
             rank_out.append(0)
             rr = perm[tree.begin[t]:tree.begin[t] + tree.size[t]]
             cc = perm[tree.begin[s]:tree.begin[s] + tree.size[s]]
-            chunks.append(kernel_block(centroid, area, rr, cc).ravel(order="F"))
+            chunks.append(kernel_block(centroid, area, rr, cc, dim).ravel(order="F"))
             pos += chunks[-1].size
 
     def compress(t, s):
@@ -180,13 +194,13 @@ def build_problem(r, leaf, eta, eps, nrhs=1, seed=0, axes=None, cache=True, verb
         nonlocal fallbacks
         rows = perm[tree.begin[t]:tree.begin[t] + tree.size[t]]
         cols = perm[tree.begin[s]:tree.begin[s] + tree.size[s]]
-        U, V = aca_partial(centroid, area, rows, cols, eps)
+        U, V = aca_partial(centroid, area, rows, cols, eps, dim)
         if U.shape[1] > min(len(rows), len(cols)) // 2:
             return None
         U, V = recompress(U, V, eps)
         ii = rng_check.integers(0, len(rows), 64)
         jj = rng_check.integers(0, len(cols), 64)
-        exact = kernel_block(centroid, area, rows[ii], cols[jj])[np.arange(64), np.arange(64)]
+        exact = kernel_block(centroid, area, rows[ii], cols[jj], dim)[np.arange(64), np.arange(64)]
         approx = np.einsum("ik,ik->i", U[ii], V[jj])
         if np.max(np.abs(exact - approx)) > 10.0 * eps * np.max(np.abs(exact)):
             fallbacks += 1
@@ -219,7 +233,7 @@ def build_problem(r, leaf, eta, eps, nrhs=1, seed=0, axes=None, cache=True, verb
     rng = np.random.default_rng(seed)
     b = np.asfortranarray(rng.standard_normal((nrhs, n)).T)
     p = Problem(n=n, r=r, leaf=leaf, eta=float(eta), eps=float(eps), nrhs=nrhs, seed=seed,
-                axes=axes, tree=tree, row_cl=bl.row_cl, col_cl=bl.col_cl, kind=kind,
+                axes=axes, dim=int(dim), tree=tree, row_cl=bl.row_cl, col_cl=bl.col_cl, kind=kind,
                 rank=rank, offset=offset, data=data, b=b, centroid=centroid, area=area,
                 aca_fallbacks=fallbacks, build_seconds=time.time() - t0)
     if verbose:
@@ -231,7 +245,7 @@ def build_problem(r, leaf, eta, eps, nrhs=1, seed=0, axes=None, cache=True, verb
 
 _ARRAYS = ("row_cl", "col_cl", "kind", "rank", "offset", "data", "b", "centroid", "area")
 _TREE = ("begin", "size", "son0", "son1", "level", "bmin", "bmax", "perm")
-_SCAL = ("n", "r", "leaf", "eta", "eps", "nrhs", "seed", "aca_fallbacks", "build_seconds")
+_SCAL = ("n", "r", "leaf", "eta", "eps", "nrhs", "seed", "aca_fallbacks", "build_seconds", "dim")
 
 
 def _save(path, p):
@@ -250,7 +264,8 @@ def _load(path):
     kw = {k: z[k] for k in _ARRAYS}
     kw["b"] = np.asfortranarray(kw["b"])
     for k in _SCAL:
-        kw[k] = z["s_" + k].item()
+        if "s_" + k in z:
+            kw[k] = z["s_" + k].item()
     ax = z["s_axes"]
     kw["axes"] = None if ax.size == 0 else tuple(ax.tolist())
     return Problem(tree=tree, **kw)

@@ -32,6 +32,8 @@ METRIC = "H-LU GFLOP/s & solves/s to 1e-10 residual, FP32-TC+IR vs FP64; p50/p99
 WORKLOAD = "sphere20480"  # icosphere r=5, n=20480, leaf 64, eta=2, eps=1e-4, 16 rhs
 TOL = 1e-10
 KIND_NAMES = ("getrf", "trsm", "project", "accum", "radd", "split")
+GEOMETRY = {3: "unit-sphere surface, kernel 1/(4 pi r),", 2: "circle of radius 1/2, kernel -log(r)/(2 pi),",
+            1: "interval [0, 1], kernel -log(r),"}
 
 
 def parse():
@@ -416,7 +418,7 @@ def run_native(args):
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 truncation cores and residual)",
             "data": "synthetic",
-            "config": {"workload": f"{args.workload}: icosphere r={w['r']}, n={p.n}, leaf {w['leaf']}, "
+            "config": {"workload": f"{args.workload}: {GEOMETRY[w.get('dim', 3)]} n={p.n}, leaf {w['leaf']}, "
                                    f"eta={w['eta']:g}, eps={w['eps']:g}, {p.nrhs} rhs ~ N(0,1) seed 0, tol 1e-10",
                        "n": p.n, "leaves": p.n_leaves, "nrhs": p.nrhs, "l2": "inputs larger than L2 (factor arena "
                        f"{st32['device_bytes'] / 1e9:.1f} GB)", "parallelism": f"replicas x{world}",
@@ -683,8 +685,8 @@ def run_serve(args):
                 time.sleep(nxt - now)
             pending -= len(srv.step())
         makespan = srv.clock()
+        srv.close()  # adds the kernel launches of the handles it releases
         st = dict(srv.stats)
-        srv.close()
         lat = sorted((r.done - r.arrival) * 1e3 for r in reqs)
         return makespan, lat, st, reqs
 

@@ -121,6 +121,23 @@ def test_factor_parity_5120():
     h.close()
 
 
+@pytest.mark.parametrize("dim,eta", [(1, 0.25), (1, 1.0), (2, 0.5)])
+def test_factor_parity_log_kernels(dim, eta):
+    """d = 1, 2 log-kernel problems (Sec. 6.1) with the eta values of Table 1: factors equal
+    the oracle's, and the GPU solve is as accurate as the oracle's."""
+    p = build_problem(3, 32, eta, 1e-4, nrhs=2, dim=dim)
+    o = HLUOracle(p, p.eps).factor()
+    h = gpu_factor(p)
+    _check_factor_parity(p, h, o)
+    b = _dev(p.b)
+    h.solve(b)
+    A = build_hmatrix(p)
+    xo = lu_solve(o.A, p.b_perm())
+    e_gpu = solve_error(A, b.cpu().numpy()[p.tree.perm], p.b_perm())
+    assert np.all(e_gpu <= 2 * solve_error(A, xo, p.b_perm()))
+    h.close()
+
+
 def test_all_dense_structure_is_dense_lu():
     """eta = 0: every block dense; the GPU result is the unique unpivoted LU."""
     p = build_problem(3, 32, 0.0, 1e-4, nrhs=1)

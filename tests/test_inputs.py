@@ -124,3 +124,33 @@ def test_hmatrix_approximates_dense(prob1280):
 def test_rhs_is_seeded_normal(prob320):
     b = np.random.default_rng(0).standard_normal((2, prob320.n)).T
     assert np.array_equal(prob320.b, b)
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_log_kernel_entries_and_self_term(dim):
+    """d = 1, 2 (Sec. 6.1): off-diagonal entries a_j g(c_i, c_j) with g = -log r (d = 1) or
+    -log r / (2 pi) (d = 2); the self-term equals the integral of g over the element itself,
+    computed here by adaptive quadrature (scipy) of -log|t| on both halves."""
+    from scipy.integrate import quad
+    from bem_inputs.mesh import ellipse_panels, interval_cells
+    c, a, lo, hi = interval_cells(40) if dim == 1 else ellipse_panels(40)
+    idx = np.arange(40)
+    A = kernel_block(c, a, idx, idx, dim)
+    scale = 1.0 if dim == 1 else 1.0 / (2 * np.pi)
+    i, j = 3, 17
+    assert np.isclose(A[i, j], -a[j] * np.log(np.linalg.norm(c[i] - c[j])) * scale, rtol=1e-14)
+    h = a[5]
+    half = quad(lambda t: -np.log(t), 0.0, h / 2)[0]
+    assert np.isclose(A[5, 5], 2 * half * scale, rtol=1e-10)
+    assert np.all(lo <= c) and np.all(c <= hi)
+
+
+def test_curve_and_interval_geometry():
+    from bem_inputs.mesh import ellipse_panels, interval_cells
+    c, a, _, _ = interval_cells(64)
+    assert np.isclose(a.sum(), 1.0) and np.allclose(c[:, 1:], 0.0)
+    # inscribed polygon of the circle of radius 1/2: perimeter -> pi from below, O(1/n^2)
+    p1 = ellipse_panels(64)[1].sum()
+    p2 = ellipse_panels(128)[1].sum()
+    assert p1 < p2 < np.pi
+    assert np.isclose((np.pi - p1) / (np.pi - p2), 4.0, rtol=1e-2)

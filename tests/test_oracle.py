@@ -194,3 +194,16 @@ def test_planted_truncation_off_by_one_is_caught(prob320, monkeypatch):
                         lambda self, sig: max(0, int(np.count_nonzero(sig > self.eps * sig[0])) - 1))
     with pytest.raises(AssertionError):
         test_rounded_addition_eckart_young(prob320)
+
+
+@pytest.mark.parametrize("dim,eta", [(1, 0.25), (1, 1.0), (2, 0.5)])
+def test_factor_quality_log_kernels(dim, eta):
+    """The d = 1, 2 log-kernel problems of Sec. 6.1 with the eta values of Table 1: the oracle's
+    factors and solve stay at the truncation level, as for the d = 3 problems."""
+    p = build_problem(3, 32, eta, 1e-4, nrhs=1, dim=dim)
+    assert (p.kind == 1).any() and (p.kind == 0).any()
+    A = build_hmatrix(p)
+    o = HLUOracle(p, p.eps).factor()
+    assert o.c.min_pivot > 0.0
+    assert factor_error(A, o.A, p.n) <= 10 * p.eps
+    assert np.all(solve_error(A, lu_solve(o.A, p.b_perm()), p.b_perm()) <= 10 * p.eps)
