@@ -99,6 +99,13 @@ typedef struct {
     int64_t mem_budget;  /* bytes of device memory the handle may allocate; 0 -> no limit */
     double timeout_s;    /* limit for any device-side wait; 0 -> 10 s.  On expiry the
                             call returns HLU_ETIMEOUT and the device is left usable */
+    int32_t inv_block;   /* solve by inverse blocks: the largest diagonal blocks of order
+                            <= inv_block (at least the largest leaf) are inverted at the end
+                            of hlu_factor, and the solve applies those inverses as dense
+                            products above the block substitution of Sec. 3.1 (fewer
+                            sequential steps); 0 -> 1024, < 0 -> plain block substitution.
+                            The inverses are not counted in the model flops */
+    int32_t reserved_;   /* set to 0 */
 } hlu_opts;
 
 typedef struct hlu_ctx *hlu_t;

@@ -447,6 +447,7 @@ static int create_impl(const hlu_tree *tree, const hlu_blocks *blocks, const hlu
         h->mem_budget = opts->mem_budget;
         h->schedule = opts->schedule;
         if (opts->timeout_s > 0.0) h->timeout_ns = (unsigned long long)(opts->timeout_s * 1e9);
+        if (opts->inv_block != 0) po.inv_block = opts->inv_block < 0 ? 0 : opts->inv_block;
     }
     if ((h->precision != HLU_FP64 && h->precision != HLU_FP32) ||
         (h->schedule != HLU_SCHED_DATAFLOW && h->schedule != HLU_SCHED_WAVES)) {

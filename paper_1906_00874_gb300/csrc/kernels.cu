@@ -188,11 +188,12 @@ __device__ __forceinline__ void trsm_group16(const T *L, const T *dinv, T *A, co
 
 template <class T>
 __device__ void dev_trsm(const TTrsm &t, const LaunchArgs &a, unsigned char *smem_raw) {
+    const int mode = t.mode & 0xff;
     const int m = t.m, mm = m * m;
     T *L = reinterpret_cast<T *>(smem_raw);
     T *dinv = L + mm + kTrsmSlack;
     const T *g = reinterpret_cast<const T *>(a.arena) + t.L_off;
-    if (t.mode == TR_UPPER_TRANS)  // L = U^T
+    if (mode == TR_UPPER_TRANS)  // L = U^T
         block_copy<T>(mm, [&](int e) { return g[e]; }, [&](int e, T v) {
             const int j = e / m;
             L[j + (e - j * m) * m] = v;
@@ -201,12 +202,12 @@ __device__ void dev_trsm(const TTrsm &t, const LaunchArgs &a, unsigned char *sme
         block_copy<T>(mm, [&](int e) { return g[e]; }, [&](int e, T v) { L[e] = v; });
     for (int e = mm + threadIdx.x; e < mm + kTrsmSlack; e += blockDim.x) L[e] = T(0);
     __syncthreads();
-    const bool unit = t.mode == TR_LOWER_UNIT;
+    const bool unit = mode == TR_LOWER_UNIT;
     for (int i = threadIdx.x; i < m; i += blockDim.x) dinv[i] = unit ? T(1) : T(1) / L[i + i * m];
     T *A = reinterpret_cast<T *>(a.arena);
     const int p = dim_c(t.P, a.kdyn);
-    if (threadIdx.x == 0) add_flops(a, K_TRSM, (double)m * m * p);
-    const bool forward = t.mode != TR_UPPER;
+    if (threadIdx.x == 0 && !(t.mode & kTrsmNoFlops)) add_flops(a, K_TRSM, (double)m * m * p);
+    const bool forward = mode != TR_UPPER;
     __syncthreads();
     if (m <= 32)
         trsm_group16<T, 2>(L, dinv, A, t.P, m, p, forward);
@@ -231,7 +232,7 @@ __device__ void dev_project(const TProject &t, const LaunchArgs &a, unsigned cha
     T *A = reinterpret_cast<T *>(a.arena);
     T *red = reinterpret_cast<T *>(smem_raw);
     const int len = dim_r(t.F, a.kdyn), k = dim_c(t.F, a.kdyn), p = dim_c(t.X, a.kdyn);
-    if (threadIdx.x == 0) add_flops(a, K_PROJECT, 2.0 * len * k * p);
+    if (threadIdx.x == 0 && !t.no_flops) add_flops(a, K_PROJECT, 2.0 * len * k * p);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int ta = (k + 3) >> 2, tb = (p + 3) >> 2, ntile = ta * tb;
     if (ntile == 0) return;
@@ -393,7 +394,8 @@ __device__ void dev_accum(const TAccum &t, const Term *terms, const LaunchArgs &
             }
             __syncthreads();
             const int Ltot = sP[nq];
-            if (b0 == 0 && threadIdx.x == 0) add_flops(a, K_ACCUM, 2.0 * m * (double)Ltot * p);
+            if (b0 == 0 && q0 == 0 && threadIdx.x == 0 && t.credit > 0.0f) add_flops(a, K_ACCUM, (double)t.credit * p);
+            if (b0 == 0 && threadIdx.x == 0 && t.credit == 0.0f) add_flops(a, K_ACCUM, 2.0 * m * (double)Ltot * p);
             for (int c0 = 0; c0 < Ltot; c0 += Lcap) {
                 const int L = min(Lcap, Ltot - c0);
                 if (c0 > 0) __syncthreads();  // the previous batch is consumed

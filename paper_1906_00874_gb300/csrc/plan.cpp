@@ -287,7 +287,7 @@ void Planner::hmm(const View &out, double alpha, bool overwrite, Block *M, bool 
         View Xs = rows(X, trans ? m->t : m->s);
         int32_t krows = F.p.cslot >= 0 ? s.cap : F.p.cols;
         View T = new_temp(-1, krows, X.p.cols, F.p.cslot, X.p.cslot);
-        TProject tp{F.p, Xs.p, T.p, -1, -1, -1, -1};
+        TProject tp{F.p, Xs.p, T.p, -1, -1, -1, -1, no_flops ? 1 : 0, 0};
         P->project.push_back(tp);
         emit(K_PROJECT, {&F, &Xs}, {&T});
         Tv[i] = T;
@@ -349,7 +349,7 @@ void Planner::hmm(const View &out, double alpha, bool overwrite, Block *M, bool 
                 ++cnt;
             }
             const bool ow = overwrite && first;
-            P->accum.push_back(TAccum{o.p, alpha, ow ? 1 : 0, t0, cnt, wdst, wsrc, 0});
+            P->accum.push_back(TAccum{o.p, alpha, ow ? 1 : 0, t0, cnt, wdst, wsrc, no_flops ? -1.0f : 0.0f});
             if (!ow) rd.push_back(&o);
             emit(K_ACCUM, rd, {&o});
         }
@@ -402,7 +402,7 @@ void Planner::add_into(Block *C, double alpha, const Prod &p) {
             int32_t q = lc_ids[cl[C->t].lc_first + qi];
             View o = rows(D, q);
             View A = rows(p.U, q);
-            P->accum.push_back(TAccum{o.p, alpha, 0, int32_t(P->terms.size()), 1, -1, -1, 0});
+            P->accum.push_back(TAccum{o.p, alpha, 0, int32_t(P->terms.size()), 1, -1, -1, 0.0f});
             P->terms.push_back(Term{A.p, Vt.p});
             emit(K_ACCUM, {&A, &Vt, &o}, {&o});
         }
@@ -532,6 +532,196 @@ void Planner::solve_upper(Block *F, const View &Y) {
     solve_upper(F->son[1][1], rows(Y, t1));
     hmm(rows(Y, t0), -1.0, false, F->son[0][1], false, rows(Y, t1));
     solve_upper(F->son[0][0], rows(Y, t0));
+}
+
+// ------------------------------------------------------ inverse-block solve
+// The block forward substitution of Sec. 3.1 (solve(F00); y1 -= F10 x0; solve(F11)) is kept above
+// a chosen level of diagonal blocks (c, c); below it, x_c = L_cc^{-1} y_c and x_c = U_cc^{-1} z_c are
+// applied as dense products.  The inverses are formed at the end of the factorisation by the same
+// substitution applied to the identity, one leaf cluster of columns at a time (n_c / leaf
+// independent chains per block, all off the factorisation's own path).  The solve's chain then has
+// one product per inverse block instead of one triangular solve and one update per leaf cluster.
+
+// Whether the block-tree leaf that covers rows of cluster q and columns of cluster j is dense.
+bool Planner::leaf_is_dense(int32_t q, int32_t j) const {
+    const Block *B = root;
+    while (B->kind == B_PART) {
+        const int32_t r0 = cl[B->t].son0, c0 = cl[B->s].son0;
+        const int i = cl[q].begin < cl[r0].begin + cl[r0].size ? 0 : 1;
+        const int k = cl[j].begin < cl[c0].begin + cl[c0].size ? 0 : 1;
+        B = B->son[i][k];
+    }
+    return B->kind == B_DENSE;
+}
+
+// The largest clusters of order <= bound under t.
+void Planner::choose_inverses(int32_t t, int32_t bound) {
+    if (cl[t].size <= bound || cl[t].son0 < 0) {
+        inv_index[t] = int32_t(inv_cl.size());
+        inv_cl.push_back(t);
+        return;
+    }
+    choose_inverses(cl[t].son0, bound);
+    choose_inverses(cl[t].son1, bound);
+}
+
+// Y (rows of F->t) := L^{-1} Y where Y is zero in the rows before s0: parts of the recursion that
+// only touch those rows are skipped (their result is zero).
+void Planner::inv_solve_lower(Block *F, const View &Y, int32_t s0) {
+    if (cl[F->t].begin + cl[F->t].size <= s0) return;
+    if (F->kind == B_DENSE) {
+        Store &s = st(F);
+        View D = viewD(F);
+        P->trsm.push_back(TTrsm{s.D_off, s.m, TR_LOWER_UNIT | kTrsmNoFlops, Y.p});
+        emit(K_TRSM, {&D}, {&Y});
+        return;
+    }
+    const int32_t t0 = cl[F->t].son0, t1 = cl[F->t].son1;
+    inv_solve_lower(F->son[0][0], rows(Y, t0), s0);
+    if (cl[t0].begin + cl[t0].size > s0) hmm(rows(Y, t1), -1.0, false, F->son[1][0], false, rows(Y, t0));
+    inv_solve_lower(F->son[1][1], rows(Y, t1), s0);
+}
+
+// Y := U^{-1} Y where Y is zero in the rows from e0 on.
+void Planner::inv_solve_upper(Block *F, const View &Y, int32_t e0) {
+    if (cl[F->t].begin >= e0) return;
+    if (F->kind == B_DENSE) {
+        Store &s = st(F);
+        View D = viewD(F);
+        P->trsm.push_back(TTrsm{s.D_off, s.m, TR_UPPER | kTrsmNoFlops, Y.p});
+        emit(K_TRSM, {&D}, {&Y});
+        return;
+    }
+    const int32_t t0 = cl[F->t].son0, t1 = cl[F->t].son1;
+    inv_solve_upper(F->son[1][1], rows(Y, t1), e0);
+    if (cl[t1].begin < e0) hmm(rows(Y, t0), -1.0, false, F->son[0][1], false, rows(Y, t1));
+    inv_solve_upper(F->son[0][0], rows(Y, t0), e0);
+}
+
+// Forms L_cc^{-1} and U_cc^{-1} of every inverse block (factorisation plan, after lu(root)).
+void Planner::plan_inverses() {
+    no_flops = true;
+    inv_L_off.assign(inv_cl.size(), 0);
+    inv_U_off.assign(inv_cl.size(), 0);
+    inv_objL.assign(inv_cl.size(), -1);
+    inv_objU.assign(inv_cl.size(), -1);
+    for (size_t i = 0; i < inv_cl.size(); ++i) {
+        const int32_t c = inv_cl[i], nc = cl[c].size, b0 = cl[c].begin;
+        // the diagonal block (c, c) of the block tree
+        Block *F = root;
+        while (F->t != c) {
+            const int32_t s0 = cl[F->t].son0;
+            const int side = cl[c].begin < cl[s0].begin + cl[s0].size ? 0 : 1;
+            F = F->son[side][side];
+        }
+        for (int up = 0; up < 2; ++up) {
+            const int64_t off = *arena;
+            *arena = align8(*arena + int64_t(nc) * nc);
+            const int32_t obj = new_obj(c, c);
+            (up ? inv_U_off : inv_L_off)[i] = off;
+            (up ? inv_objU : inv_objL)[i] = obj;
+            for (int32_t k = 0; k < cl[c].lc_count; ++k) {
+                const int32_t q = lc_ids[cl[c].lc_first + k], mq = cl[q].size, bq = cl[q].begin;
+                View Y;
+                Y.p = Panel{off + int64_t(bq - b0) * nc, nc, mq, -1, -1, 1, nc};
+                Y.obj = obj;
+                Y.r_cl = c;
+                Y.c_cl = q;
+                Y.trans = false;
+                // Y = the columns of the identity for the rows of q: one overwrite per leaf cluster
+                // of rows (an ACCUM output has at most a leaf cluster's rows), the identity at q
+                for (int32_t kk = 0; kk < cl[c].lc_count; ++kk) {
+                    const int32_t r = lc_ids[cl[c].lc_first + kk];
+                    View Yr = rows(Y, r);
+                    if (r == q) {
+                        View I = ident(q);
+                        P->terms.push_back(Term{I.p, I.p});
+                        P->accum.push_back(TAccum{Yr.p, 1.0, 1, int32_t(P->terms.size() - 1), 1, -1, -1, -1.0f});
+                        emit(K_ACCUM, {&I}, {&Yr});
+                    } else {
+                        P->accum.push_back(TAccum{Yr.p, 1.0, 1, int32_t(P->terms.size()), 0, -1, -1, -1.0f});
+                        emit(K_ACCUM, {}, {&Yr});
+                    }
+                }
+                if (up)
+                    inv_solve_upper(F, Y, bq + mq);
+                else
+                    inv_solve_lower(F, Y, bq);
+            }
+        }
+    }
+    no_flops = false;
+}
+
+// out (rows of c) = L_cc^{-1} in or U_cc^{-1} in: one product per leaf cluster q of c over the
+// triangle's columns (those of c up to q's end, or from q's start).  The model flops credited are
+// the method's own for that row of the substitution: the triangular solve with q's diagonal leaf
+// (m_q^2 per column) and the products with the dense leaves of the row inside the block (the
+// low-rank ones, of run-time rank, are not credited).
+void Planner::apply_inverse(int32_t idx, bool upper, const View &in, const View &out) {
+    const int32_t c = inv_cl[idx], nc = cl[c].size, b0 = cl[c].begin, e0 = b0 + nc;
+    const int64_t base = upper ? inv_U_off[idx] : inv_L_off[idx];
+    const int32_t obj = upper ? inv_objU[idx] : inv_objL[idx];
+    std::vector<View> keep;
+    std::vector<const View *> rd;
+    for (int32_t k = 0; k < cl[c].lc_count; ++k) {
+        const int32_t q = lc_ids[cl[c].lc_first + k], mq = cl[q].size, bq = cl[q].begin;
+        const int32_t j0 = upper ? bq : b0, j1 = upper ? e0 : bq + mq;  // columns [j0, j1)
+        Panel A{base + int64_t(bq - b0) + int64_t(j0 - b0) * nc, mq, j1 - j0, -1, -1, 1, nc};
+        Panel X = in.p;
+        X.off += int64_t(j0 - b0) * in.p.rs;
+        X.rows = j1 - j0;
+        X.rslot = -1;
+        keep.clear();
+        const int32_t k0 = upper ? k : 0, k1 = upper ? cl[c].lc_count : k + 1;
+        keep.reserve(2 * (k1 - k0));
+        double credit = double(mq) * mq;
+        for (int32_t kk = k0; kk < k1; ++kk) {
+            const int32_t j = lc_ids[cl[c].lc_first + kk];
+            View Lv;
+            Lv.p = A;
+            Lv.obj = obj;
+            Lv.r_cl = q;
+            Lv.c_cl = j;
+            Lv.trans = false;
+            keep.push_back(Lv);
+            keep.push_back(rows(in, j));
+            if (j != q && leaf_is_dense(q, j)) credit += 2.0 * mq * cl[j].size;
+        }
+        rd.clear();
+        for (const View &v : keep) rd.push_back(&v);
+        View o = rows(out, q);
+        P->terms.push_back(Term{A, X});
+        P->accum.push_back(TAccum{o.p, 1.0, 1, int32_t(P->terms.size() - 1), 1, -1, -1, float(credit)});
+        emit(K_ACCUM, rd, {&o});
+    }
+}
+
+// x = L^{-1} y from Y into Z (Z's rows of F->t are written, Y's are updated in place above the
+// inverse level).
+void Planner::solve_lower_pp(Block *F, const View &Y, const View &Z) {
+    const int32_t idx = inv_index[F->t];
+    if (idx >= 0) {
+        apply_inverse(idx, false, Y, Z);
+        return;
+    }
+    const int32_t t0 = cl[F->t].son0, t1 = cl[F->t].son1;
+    solve_lower_pp(F->son[0][0], rows(Y, t0), rows(Z, t0));
+    hmm(rows(Y, t1), -1.0, false, F->son[1][0], false, rows(Z, t0));
+    solve_lower_pp(F->son[1][1], rows(Y, t1), rows(Z, t1));
+}
+
+// x = U^{-1} z from Z into Y.
+void Planner::solve_upper_pp(Block *F, const View &Z, const View &Y) {
+    const int32_t idx = inv_index[F->t];
+    if (idx >= 0) {
+        apply_inverse(idx, true, Z, Y);
+        return;
+    }
+    const int32_t t0 = cl[F->t].son0, t1 = cl[F->t].son1;
+    solve_upper_pp(F->son[1][1], rows(Z, t1), rows(Y, t1));
+    hmm(rows(Z, t0), -1.0, false, F->son[0][1], false, rows(Y, t1));
+    solve_upper_pp(F->son[0][0], rows(Z, t0), rows(Y, t0));
 }
 
 // --------------------------------------------------------- plan bookkeeping
@@ -920,6 +1110,12 @@ int Planner::plan_all() {
     nrhs_slot = new_slot(0);
     begin_plan(fplan, false, &f_elems);
     lu(root);
+    inv_cl.clear();
+    inv_index.assign(cl.size(), -1);
+    if (opt.inv_block > 0) {
+        choose_inverses(0, std::max(opt.inv_block, max_leaf));
+        plan_inverses();
+    }
     finalize(fplan, &f_elems);
     f_solve_off = f_elems;
     f_elems = align8(f_elems + int64_t(n) * opt.nrhs_max);
@@ -931,8 +1127,18 @@ int Planner::plan_all() {
     Y.trans = false;
     begin_plan(splan, false, &f_elems);
     split_accum = true;
-    solve_lower(root, Y);
-    solve_upper(root, Y);
+    if (!inv_cl.empty()) {
+        f_z_off = f_elems;
+        f_elems = align8(f_elems + int64_t(n) * opt.nrhs_max);
+        View Z = Y;
+        Z.p.off = f_z_off;
+        Z.obj = new_obj(0, -1);
+        solve_lower_pp(root, Y, Z);
+        solve_upper_pp(root, Z, Y);
+    } else {
+        solve_lower(root, Y);
+        solve_upper(root, Y);
+    }
     split_accum = false;
     finalize(splan, &f_elems);
     layout_a_arena();
@@ -949,6 +1155,13 @@ int Planner::plan_all() {
     hmm(Yo, 1.0, true, root, false, X);
     finalize(mplan, &a_elems);
     P = nullptr;
+    // the ACCUM kernel keeps one output row per thread slot (at most 1024 rows)
+    for (const Plan *pp : {&fplan, &splan, &mplan})
+        for (const TAccum &t : pp->accum)
+            if (t.out.rows > 1024) {
+                error = "internal: product output with more than 1024 rows";
+                return HLU_EINVAL;
+            }
     return HLU_OK;
 }
 

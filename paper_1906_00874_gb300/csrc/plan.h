@@ -95,6 +95,9 @@ struct PlanOptions {
     int32_t nrhs_max = 64;
     int32_t kmax_core = 96;  // largest stacked rank a rounded addition handles (at most 128: the
                              // truncation core keeps a column of its right factor in one warp)
+    int32_t inv_block = 1024; // the largest diagonal blocks of at most this order (at least the
+                             // largest leaf) are inverted after the factorisation, and the solve
+                             // applies the inverses as products; 0: plain block substitution
 };
 
 class Planner {
@@ -129,6 +132,11 @@ public:
     int32_t nrhs_slot = -1;      // solve / matvec panel width
     int64_t f_solve_off = 0;     // n x nrhs_max panel (factor arena)
     int64_t a_x_off = 0, a_y_off = 0;  // n x nrhs_max panels (A_H arena)
+    int64_t f_z_off = -1;        // second n x nrhs_max solve panel (inverse-block solve only)
+    // inverse blocks: the diagonal blocks (c, c) whose inverses L_cc^{-1}, U_cc^{-1} (dense,
+    // n_c x n_c, column-major) the factorisation forms for the solve
+    std::vector<int32_t> inv_cl, inv_index;  // clusters; per cluster its inverse block or -1
+    std::vector<int64_t> inv_L_off, inv_U_off;
 
     Plan fplan, splan, mplan;    // factorisation, solve, matvec
 
@@ -157,6 +165,8 @@ private:
     std::vector<int32_t> pred_mark;  // per task: the last task that listed it as a predecessor
     std::vector<int32_t> rpool_task, rpool_next;
     int32_t ident_obj = -1;
+    bool no_flops = false;  // emitted tasks are not counted in the model flops
+    std::vector<int32_t> inv_objL, inv_objU;
 
     int32_t new_obj(int32_t row_cl, int32_t col_cl, int32_t nr_if_none = 1);
     int32_t new_slot(int32_t init);
@@ -189,6 +199,15 @@ private:
     void radd(Block *C, bool include_self, const std::vector<Piece> &pcs, const std::vector<View> &pviews);
     void solve_lower(Block *F, const View &Y);
     void solve_upper(Block *F, const View &Y);
+    // inverse-block solve
+    bool leaf_is_dense(int32_t q, int32_t j) const;
+    void choose_inverses(int32_t t, int32_t bound);
+    void plan_inverses();
+    void inv_solve_lower(Block *F, const View &Y, int32_t s0);
+    void inv_solve_upper(Block *F, const View &Y, int32_t e0);
+    void apply_inverse(int32_t idx, bool upper, const View &in, const View &out);
+    void solve_lower_pp(Block *F, const View &Y, const View &Z);
+    void solve_upper_pp(Block *F, const View &Z, const View &Y);
 
     int build_tree();
     void layout_factor_arena();

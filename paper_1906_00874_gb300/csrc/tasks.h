@@ -41,6 +41,9 @@ enum TrsmMode : int32_t {
     TR_UPPER_TRANS = 1,  // P := U^{-T} P, U upper part of the leaf (X U^{-1} on X^T)
     TR_UPPER = 2         // P := U^{-1} P (backward substitution of the solve)
 };
+// Flag or-ed into TTrsm::mode: the task is not counted in the model flops (work the method itself
+// does not do, such as forming the inverses of diagonal blocks for the solve).
+constexpr int32_t kTrsmNoFlops = 0x100;
 
 struct TGetrf {
     int64_t off;   // m x m column-major, ld = m
@@ -60,17 +63,21 @@ struct TTrsm {
 struct TProject {
     Panel F, X, T;
     int32_t dst0, src0, dst1, src1;
+    int32_t no_flops;  // 1: not counted in the model flops
+    int32_t pad_;
 };
 
 // out (rows x p) = beta*out + alpha * sum_t A_t X_t, with A_t: rows x inner_t,
 // X_t: inner_t x p.  beta = 0 when overwrite.  kdyn[dst] = kdyn[src] if dst >= 0.
+// Model flops: 2 rows inner p when credit == 0; credit * p when credit > 0 (a product that stands
+// in for other operations of the method: those operations' count); none when credit < 0.
 struct TAccum {
     Panel out;
     double alpha;
     int32_t overwrite;
     int32_t term0, nterms;
     int32_t dst, src;
-    int32_t pad_;
+    float credit;
 };
 
 struct Term {

@@ -51,7 +51,8 @@ class _Blocks(ctypes.Structure):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("rank_cap", ctypes.c_int32), ("nrhs_max", ctypes.c_int32),
-                ("schedule", ctypes.c_int32), ("mem_budget", ctypes.c_int64), ("timeout_s", ctypes.c_double)]
+                ("schedule", ctypes.c_int32), ("mem_budget", ctypes.c_int64), ("timeout_s", ctypes.c_double),
+                ("inv_block", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -194,16 +195,17 @@ class HLU:
 
     def __init__(self, n, perm, begin, size, son0, son1, row_cl, col_cl, kind, rank, offset, data,
                  precision=HLU_FP64, rank_cap=0, nrhs_max=0, mem_budget=0, stream=None,
-                 schedule=SCHED_DATAFLOW, timeout_s=0.0):
+                 schedule=SCHED_DATAFLOW, timeout_s=0.0, inv_block=0):
         tree, blocks, keep = _describe(n, perm, begin, size, son0, son1, row_cl, col_cl, kind, rank, offset, data)
         self._open(1, ctypes.byref(tree), ctypes.byref(blocks), [int(n)], int(blocks.n_leaves), precision, rank_cap,
-                   nrhs_max, mem_budget, stream, schedule, timeout_s)
+                   nrhs_max, mem_budget, stream, schedule, timeout_s, inv_block)
 
     def _open(self, count, trees, blocks, sizes, n_leaves, precision, rank_cap, nrhs_max, mem_budget, stream,
-              schedule, timeout_s):
+              schedule, timeout_s, inv_block=0):
         lib = load()
         self._h = ctypes.c_void_p()
-        opts = _Opts(int(precision), int(rank_cap), int(nrhs_max), int(schedule), int(mem_budget), float(timeout_s))
+        opts = _Opts(int(precision), int(rank_cap), int(nrhs_max), int(schedule), int(mem_budget), float(timeout_s),
+                     int(inv_block), 0)
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
@@ -222,7 +224,7 @@ class HLU:
 
     @classmethod
     def batch(cls, problems, precision=HLU_FP64, rank_cap=0, nrhs_max=0, mem_budget=0, stream=None,
-              schedule=SCHED_DATAFLOW, timeout_s=0.0):
+              schedule=SCHED_DATAFLOW, timeout_s=0.0, inv_block=0):
         """One handle for several independent problems (hlu_create_batch): the block-diagonal
         system whose rows are the problems' rows in turn (offsets of self.sizes)."""
         descs = [_describe(p.n, p.tree.perm, p.tree.begin, p.tree.size, p.tree.son0, p.tree.son1, p.row_cl,
@@ -233,7 +235,7 @@ class HLU:
         blocks = (_Blocks * len(descs))(*[d[1] for d in descs])
         self = cls.__new__(cls)
         self._open(len(descs), trees, blocks, [p.n for p in problems], sum(int(d[1].n_leaves) for d in descs),
-                   precision, rank_cap, nrhs_max, mem_budget, stream, schedule, timeout_s)
+                   precision, rank_cap, nrhs_max, mem_budget, stream, schedule, timeout_s, inv_block)
         return self
 
     @property

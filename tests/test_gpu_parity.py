@@ -138,6 +138,21 @@ def test_factor_parity_log_kernels(dim, eta):
     h.close()
 
 
+@pytest.mark.parametrize("inv_block", [-1, 64, 256, 2048])
+def test_inverse_block_solve_equals_substitution(case1280, inv_block):
+    """The solve by inverse blocks (the diagonal blocks of order <= inv_block inverted at the end of
+    the factorisation and applied as products) gives the oracle's block substitution; -1 is the
+    plain substitution.  The factors do not depend on it."""
+    p, o = case1280
+    h = gpu_factor(p, inv_block=inv_block)
+    _check_factor_parity(p, h, o)
+    b = _dev(p.b)
+    h.solve(b)
+    xo = _to_orig(p, lu_solve(o.A, p.b_perm()))
+    assert np.max(np.abs(b.cpu().numpy() - xo)) / np.max(np.abs(xo)) <= 1e-10
+    h.close()
+
+
 def test_all_dense_structure_is_dense_lu():
     """eta = 0: every block dense; the GPU result is the unique unpivoted LU."""
     p = build_problem(3, 32, 0.0, 1e-4, nrhs=1)
