@@ -570,6 +570,28 @@ __device__ void warp_apply_q(const T *W, int m, int kk, const T *tau, T *y) {
     }
 }
 
+// y := Q y with Q = H_0 ... H_{kk-1} from group_householder_qr (reflector j in column j of W,
+// leading dimension ld, entries below row j for rows < len, v_j[j] = 1), for one column held in
+// the registers of a warp: row i = lane + 32 k in y[k] (len <= kVRows).
+template <class T>
+__device__ __forceinline__ void reg_apply_q(const T *W, int ld, int len, int kk, const T *tau, T (&y)[kVRows / 32]) {
+    const int lane = threadIdx.x & 31;
+    for (int j = kk - 1; j >= 0; --j) {
+        const T *x = W + (int64_t)j * ld;
+        T xv[kVRows / 32];
+        T d = T(0);
+#pragma unroll
+        for (int k = 0; k < kVRows / 32; ++k) {
+            const int i = lane + 32 * k;
+            xv[k] = i == j ? T(1) : (i > j && i < len ? x[i] : T(0));
+            d += xv[k] * y[k];
+        }
+        d = warp_sum_t(d) * tau[j];
+#pragma unroll
+        for (int k = 0; k < kVRows / 32; ++k) y[k] -= d * xv[k];
+    }
+}
+
 // Jacobi rotation (c, s) that makes columns x, y with x.x = aa, y.y = bb,
 // x.y = gg orthogonal: t = tan(theta) is the smaller root of
 // t^2 + 2 zeta t - 1 = 0, zeta = (bb - aa) / (2 gg) (Rutishauser's form), and
@@ -1215,8 +1237,22 @@ __device__ bool radd_small(const TRadd &t, const Piece *pieces, const LaunchArgs
     const int knew = core_finish<T>(b, m, n, r, t, a, 0, ph);
     // the target's own factors were read above; every row of V is covered by P
     core_write_v<T, T>(b, m, n, r, knew, A + t.V_off, n);
-    core_form_u<T>(b, m, r, knew);
-    for (int e = threadIdx.x; e < m * knew; e += blockDim.x) A[t.U_off + e] = b.C[e];
+    // U = Q_M [B_sel; 0], one warp per column in registers (m <= 128)
+    for (int c = threadIdx.x >> 5; c < knew; c += blockDim.x >> 5) {
+        const T *bc = b.B + (size_t)b.order[c] * r;
+        T y[kVRows / 32];
+#pragma unroll
+        for (int k = 0; k < kVRows / 32; ++k) {
+            const int i = (threadIdx.x & 31) + 32 * k;
+            y[k] = i < r ? bc[i] : T(0);
+        }
+        reg_apply_q<T>(b.M, m, m, r, b.tauM, y);
+#pragma unroll
+        for (int k = 0; k < kVRows / 32; ++k) {
+            const int i = (threadIdx.x & 31) + 32 * k;
+            if (i < m) A[t.U_off + i + (int64_t)c * m] = y[k];
+        }
+    }
     if (threadIdx.x == 0) kd[t.kslot] = knew;
     phase_mark(a, 5, ph);
     return true;
@@ -1298,24 +1334,58 @@ __device__ void dev_radd(const TRadd &t, const Piece *pieces, const LaunchArgs &
     const int knew = core_truncate<T>(b, ku, kv, delta, t, a, &r, 8, ph);
     T *Uc = A + t.U_off;
     T *Vc = A + t.V_off;
-    // ---- V = Q_v [P R'^T B_sel Sigma^{-2}; 0]
+    // ---- V = Q_v [core right factor; 0] (rows < kv written here)
     core_write_v<T, T>(b, ku, kv, r, knew, Vc, n);
-    for (int e = threadIdx.x; e < (n - kv) * knew; e += blockDim.x) {
-        const int i = kv + e % (n - kv), c = e / (n - kv);
-        Vc[i + (int64_t)c * n] = T(0);
-    }
-    // ---- U = Q_u [Q_M [B_sel; 0]; 0]
-    core_form_u<T>(b, ku, r, knew);
-    for (int e = threadIdx.x; e < m * knew; e += blockDim.x) {
-        const int i = e % m, c = e / m;
-        Uc[e] = i < ku ? b.C[i + (size_t)c * ku] : T(0);
-    }
-    __syncthreads();
-    for (int c = threadIdx.x >> 5; c < 2 * knew; c += blockDim.x >> 5) {  // U and V columns together
-        if (c < knew)
-            warp_apply_q(WU, m, ku, b.tauU, Uc + (int64_t)c * m);
-        else
-            warp_apply_q(WV, n, kv, b.tauV, Vc + (int64_t)(c - knew) * n);
+    if (m <= kVRows && n <= kVRows) {
+        // ---- U = Q_u [Q_M [B_sel; 0]; 0] and V: one warp per column, the column in registers
+        __syncthreads();  // the core rows of V are written
+        const int lane = threadIdx.x & 31;
+        for (int c = threadIdx.x >> 5; c < 2 * knew; c += blockDim.x >> 5) {
+            T y[kVRows / 32];
+            if (c < knew) {
+                const T *bc = b.B + (size_t)b.order[c] * r;
+#pragma unroll
+                for (int k = 0; k < kVRows / 32; ++k) {
+                    const int i = lane + 32 * k;
+                    y[k] = i < r ? bc[i] : T(0);
+                }
+                reg_apply_q<T>(b.M, ku, ku, r, b.tauM, y);
+                reg_apply_q<T>(WU, m, m, ku, b.tauU, y);
+                T *dst = Uc + (int64_t)c * m;
+#pragma unroll
+                for (int k = 0; k < kVRows / 32; ++k)
+                    if (lane + 32 * k < m) dst[lane + 32 * k] = y[k];
+            } else {
+                T *vc = Vc + (int64_t)(c - knew) * n;
+#pragma unroll
+                for (int k = 0; k < kVRows / 32; ++k) {
+                    const int i = lane + 32 * k;
+                    y[k] = i < kv ? vc[i] : T(0);
+                }
+                reg_apply_q<T>(WV, n, n, kv, b.tauV, y);
+#pragma unroll
+                for (int k = 0; k < kVRows / 32; ++k)
+                    if (lane + 32 * k < n) vc[lane + 32 * k] = y[k];
+            }
+        }
+    } else {
+        for (int e = threadIdx.x; e < (n - kv) * knew; e += blockDim.x) {
+            const int i = kv + e % (n - kv), c = e / (n - kv);
+            Vc[i + (int64_t)c * n] = T(0);
+        }
+        // ---- U = Q_u [Q_M [B_sel; 0]; 0]
+        core_form_u<T>(b, ku, r, knew);
+        for (int e = threadIdx.x; e < m * knew; e += blockDim.x) {
+            const int i = e % m, c = e / m;
+            Uc[e] = i < ku ? b.C[i + (size_t)c * ku] : T(0);
+        }
+        __syncthreads();
+        for (int c = threadIdx.x >> 5; c < 2 * knew; c += blockDim.x >> 5) {  // U and V columns together
+            if (c < knew)
+                warp_apply_q(WU, m, ku, b.tauU, Uc + (int64_t)c * m);
+            else
+                warp_apply_q(WV, n, kv, b.tauV, Vc + (int64_t)(c - knew) * n);
+        }
     }
     if (threadIdx.x == 0) {
         kd[t.kslot] = knew;
