@@ -519,25 +519,48 @@ __device__ void group_householder_qr(T *W, int m, int K, T *tau, T *nrm, int w0,
             inv = T(1) / (x0 - alpha);
             tj = (alpha - x0) / alpha;
         }
-        for (int c = j + 1 + warp; c < K; c += nw) {
-            T *y = W + (int64_t)c * m;
-            T d = T(0);
-            for (int i = j + 1 + lane; i < m; i += 32) d += (x[i] * inv) * y[i];
-            d = warp_sum_t(d);
-            d = (d + y[j]) * tj;
+        // each warp updates its columns c = j + 1 + warp + nw t four at a time (overlapping the
+        // shuffle reductions); the warp that holds column j + 1 also leaves its norm below row j
+        for (int c0 = j + 1 + warp; c0 < K; c0 += 4 * nw) {
+            T *y[4];
+            T d[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int c = c0 + q * nw;
+                y[q] = W + (int64_t)(c < K ? c : j) * m;  // column j stands in (read only)
+                d[q] = T(0);
+            }
+            for (int i = j + 1 + lane; i < m; i += 32) {
+                const T xi = x[i] * inv;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (c0 + q * nw < K) d[q] += xi * y[q][i];
+            }
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) d[q] += __shfl_xor_sync(kFull, d[q], o);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) d[q] = (d[q] + y[q][j]) * tj;
             __syncwarp();
-            if (lane == 0) y[j] -= d;
-            if (c == j + 1 && c < kk) {  // next pivot column: leave its norm below row j
-                T t2 = T(0);
-                for (int i = j + 1 + lane; i < m; i += 32) {
-                    const T yi = y[i] - d * (x[i] * inv);
-                    y[i] = yi;
-                    t2 += yi * yi;
-                }
+            if (lane == 0)
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (c0 + q * nw < K) y[q][j] -= d[q];
+            const bool pivot = c0 == j + 1 && c0 < kk;  // q = 0 is the next pivot column
+            T t2 = T(0);
+            for (int i = j + 1 + lane; i < m; i += 32) {
+                const T xi = x[i] * inv;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (c0 + q * nw < K) {
+                        const T yi = y[q][i] - d[q] * xi;
+                        y[q][i] = yi;
+                        if (q == 0) t2 += yi * yi;
+                    }
+            }
+            if (pivot) {
                 t2 = warp_sum_t(t2);
-                if (lane == 0) nrm[c] = t2;
-            } else {
-                for (int i = j + 1 + lane; i < m; i += 32) y[i] -= d * (x[i] * inv);
+                if (lane == 0) nrm[c0] = t2;
             }
         }
         bar_sync(bar, nthr);
@@ -873,21 +896,51 @@ __device__ int block_qrcp(R *M, int mr, int nc, R *tau, R *cn, int *perm, double
         __syncthreads();
         if (iflag[1] < 0) break;  // uniform: every thread reads the same flag
         const R tj = tau[j];
-        for (int c = j + 1 + warp; c < nc; c += nw) {
-            R *y = M + (size_t)c * mr;
-            R d = R(0);
-            for (int i = j + 1 + lane; i < mr; i += 32) d += x[i] * y[i];
-            d = warp_sum_t(d);
-            d = (d + y[j]) * tj;
-            __syncwarp();
-            if (lane == 0) y[j] -= d;
-            R t2 = R(0);
-            for (int i = j + 1 + lane; i < mr; i += 32) {
-                y[i] -= d * x[i];
-                t2 += y[i] * y[i];
+        // each warp updates its columns c = j + 1 + warp + nw t four at a time, so that the four
+        // shuffle reductions overlap
+        for (int c0 = j + 1 + warp; c0 < nc; c0 += 4 * nw) {
+            R *y[4];
+            R d[4], t2[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int c = c0 + q * nw;
+                y[q] = M + (size_t)(c < nc ? c : j) * mr;  // column j stands in (read only)
+                d[q] = R(0);
+                t2[q] = R(0);
             }
-            t2 = warp_sum_t(t2);
-            if (lane == 0) cn[c] = t2;
+            for (int i = j + 1 + lane; i < mr; i += 32) {
+                const R xi = x[i];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (c0 + q * nw < nc) d[q] += xi * y[q][i];
+            }
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) d[q] += __shfl_xor_sync(kFull, d[q], o);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) d[q] = (d[q] + y[q][j]) * tj;
+            __syncwarp();
+            if (lane == 0)
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (c0 + q * nw < nc) y[q][j] -= d[q];
+            for (int i = j + 1 + lane; i < mr; i += 32) {
+                const R xi = x[i];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (c0 + q * nw < nc) {
+                        const R yi = y[q][i] - d[q] * xi;
+                        y[q][i] = yi;
+                        t2[q] += yi * yi;
+                    }
+            }
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) t2[q] += __shfl_xor_sync(kFull, t2[q], o);
+            if (lane == 0)
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (c0 + q * nw < nc) cn[c0 + q * nw] = t2[q];
         }
         __syncthreads();
         r = j + 1;
