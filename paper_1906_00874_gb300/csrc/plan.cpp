@@ -738,18 +738,19 @@ void Planner::begin_plan(Plan &p, bool astore_mode, int64_t *bump) {
     rpool_next.clear();
 }
 
-// Sorts a kind's tasks by wave (stable); returns new position of every old index.
+// Sorts a kind's tasks by wave (stable counting sort: waves are small integers); returns the new
+// position of every old index.
 template <class T>
-static std::vector<int32_t> permute_by_wave(std::vector<T> &v, std::vector<int32_t> &w) {
-    std::vector<int32_t> idx(v.size());
-    for (size_t i = 0; i < idx.size(); ++i) idx[i] = int32_t(i);
-    std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) { return w[a] < w[b]; });
+static std::vector<int32_t> permute_by_wave(std::vector<T> &v, std::vector<int32_t> &w, int32_t n_waves) {
+    std::vector<int32_t> start(size_t(n_waves) + 1, 0), where(v.size());
+    for (int32_t x : w) start[x + 1]++;
+    for (int32_t k = 0; k < n_waves; ++k) start[k + 1] += start[k];
+    for (size_t i = 0; i < v.size(); ++i) where[i] = start[w[i]]++;
     std::vector<T> nv(v.size());
-    std::vector<int32_t> nw(w.size()), where(v.size());
-    for (size_t i = 0; i < idx.size(); ++i) {
-        nv[i] = v[idx[i]];
-        nw[i] = w[idx[i]];
-        where[idx[i]] = int32_t(i);
+    std::vector<int32_t> nw(w.size());
+    for (size_t i = 0; i < v.size(); ++i) {
+        nv[where[i]] = v[i];
+        nw[where[i]] = w[i];
     }
     v.swap(nv);
     w.swap(nw);
@@ -758,12 +759,12 @@ static std::vector<int32_t> permute_by_wave(std::vector<T> &v, std::vector<int32
 
 void Planner::finalize(Plan &p, int64_t *bump) {
     std::vector<int32_t> where[K_NKINDS];
-    where[K_GETRF] = permute_by_wave(p.getrf, p.wave[K_GETRF]);
-    where[K_TRSM] = permute_by_wave(p.trsm, p.wave[K_TRSM]);
-    where[K_PROJECT] = permute_by_wave(p.project, p.wave[K_PROJECT]);
-    where[K_ACCUM] = permute_by_wave(p.accum, p.wave[K_ACCUM]);
-    where[K_RADD] = permute_by_wave(p.radd, p.wave[K_RADD]);
-    where[K_SPLIT] = permute_by_wave(p.split, p.wave[K_SPLIT]);
+    where[K_GETRF] = permute_by_wave(p.getrf, p.wave[K_GETRF], p.n_waves);
+    where[K_TRSM] = permute_by_wave(p.trsm, p.wave[K_TRSM], p.n_waves);
+    where[K_PROJECT] = permute_by_wave(p.project, p.wave[K_PROJECT], p.n_waves);
+    where[K_ACCUM] = permute_by_wave(p.accum, p.wave[K_ACCUM], p.n_waves);
+    where[K_RADD] = permute_by_wave(p.radd, p.wave[K_RADD], p.n_waves);
+    where[K_SPLIT] = permute_by_wave(p.split, p.wave[K_SPLIT], p.n_waves);
     // task codes follow the permutation; successors from the predecessor lists
     for (int32_t &c : p.task_code) {
         const int32_t k = c >> kCodeShift, i = c & kCodeMask;
@@ -1096,11 +1097,18 @@ int Planner::build(int32_t n_, int32_t n_clusters, const int32_t *perm_, const i
             error = "leaf data outside the data array";
             return HLU_EINVAL;
         }
-        for (int64_t i = 0; i < len; ++i)
-            if (!std::isfinite(data[leaf_offset[l] + i])) {
-                error = "non-finite input value";
-                return HLU_EINVAL;
-            }
+        // an exponent field of all ones is an infinity or a NaN (a vectorisable scan)
+        const double *dl = data + leaf_offset[l];
+        uint64_t bad = 0;
+        for (int64_t i = 0; i < len; ++i) {
+            uint64_t bits;
+            std::memcpy(&bits, dl + i, sizeof(bits));
+            bad |= uint64_t((bits & 0x7ff0000000000000ull) == 0x7ff0000000000000ull);
+        }
+        if (bad) {
+            error = "non-finite input value";
+            return HLU_EINVAL;
+        }
     }
     return build_tree();
 }
