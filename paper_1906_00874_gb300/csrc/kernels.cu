@@ -538,9 +538,11 @@ __device__ void group_householder_qr(T *W, int m, int K, T *tau, T *nrm, int w0,
             }
             for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) d[q] += __shfl_xor_sync(kFull, d[q], o);
+                for (int q = 0; q < 4; ++q)
+                    if (sizeof(T) != 8 || c0 + q * nw < K) d[q] += __shfl_xor_sync(kFull, d[q], o);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) d[q] = (d[q] + y[q][j]) * tj;
+            for (int q = 0; q < 4; ++q)
+                if (sizeof(T) != 8 || c0 + q * nw < K) d[q] = (d[q] + y[q][j]) * tj;
             __syncwarp();
             if (lane == 0)
 #pragma unroll
@@ -596,22 +598,47 @@ __device__ void warp_apply_q(const T *W, int m, int kk, const T *tau, T *y) {
 // y := Q y with Q = H_0 ... H_{kk-1} from group_householder_qr (reflector j in column j of W,
 // leading dimension ld, entries below row j for rows < len, v_j[j] = 1), for one column held in
 // the registers of a warp: row i = lane + 32 k in y[k] (len <= kVRows).
-template <class T>
-__device__ __forceinline__ void reg_apply_q(const T *W, int ld, int len, int kk, const T *tau, T (&y)[kVRows / 32]) {
+template <class T, int NK>
+__device__ __forceinline__ void reg_apply_q_n(const T *W, int ld, int len, int kk, const T *tau, T (&y)[kVRows / 32]) {
     const int lane = threadIdx.x & 31;
     for (int j = kk - 1; j >= 0; --j) {
         const T *x = W + (int64_t)j * ld;
-        T xv[kVRows / 32];
+        T xv[NK];
         T d = T(0);
 #pragma unroll
-        for (int k = 0; k < kVRows / 32; ++k) {
+        for (int k = 0; k < NK; ++k) {
             const int i = lane + 32 * k;
             xv[k] = i == j ? T(1) : (i > j && i < len ? x[i] : T(0));
             d += xv[k] * y[k];
         }
         d = warp_sum_t(d) * tau[j];
 #pragma unroll
-        for (int k = 0; k < kVRows / 32; ++k) y[k] -= d * xv[k];
+        for (int k = 0; k < NK; ++k) y[k] -= d * xv[k];
+    }
+}
+
+// In double precision only the register rows that hold rows < len take part (no arithmetic on the
+// zero rows: on the FP64 pipe of this part every operation counts).
+template <class T>
+__device__ __forceinline__ void reg_apply_q(const T *W, int ld, int len, int kk, const T *tau, T (&y)[kVRows / 32]) {
+    if constexpr (sizeof(T) != 8) {  // single precision: one code path (smaller kernel) is faster
+        reg_apply_q_n<T, 4>(W, ld, len, kk, tau, y);
+        return;
+    }
+    switch ((len + 31) >> 5) {
+        case 0:
+            break;
+        case 1:
+            reg_apply_q_n<T, 1>(W, ld, len, kk, tau, y);
+            break;
+        case 2:
+            reg_apply_q_n<T, 2>(W, ld, len, kk, tau, y);
+            break;
+        case 3:
+            reg_apply_q_n<T, 3>(W, ld, len, kk, tau, y);
+            break;
+        default:
+            reg_apply_q_n<T, 4>(W, ld, len, kk, tau, y);
     }
 }
 
@@ -916,9 +943,11 @@ __device__ int block_qrcp(R *M, int mr, int nc, R *tau, R *cn, int *perm, double
             }
             for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) d[q] += __shfl_xor_sync(kFull, d[q], o);
+                for (int q = 0; q < 4; ++q)
+                    if (sizeof(R) != 8 || c0 + q * nw < nc) d[q] += __shfl_xor_sync(kFull, d[q], o);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) d[q] = (d[q] + y[q][j]) * tj;
+            for (int q = 0; q < 4; ++q)
+                if (sizeof(R) != 8 || c0 + q * nw < nc) d[q] = (d[q] + y[q][j]) * tj;
             __syncwarp();
             if (lane == 0)
 #pragma unroll
@@ -936,7 +965,8 @@ __device__ int block_qrcp(R *M, int mr, int nc, R *tau, R *cn, int *perm, double
             }
             for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) t2[q] += __shfl_xor_sync(kFull, t2[q], o);
+                for (int q = 0; q < 4; ++q)
+                    if (sizeof(R) != 8 || c0 + q * nw < nc) t2[q] += __shfl_xor_sync(kFull, t2[q], o);
             if (lane == 0)
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
