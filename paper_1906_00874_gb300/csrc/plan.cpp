@@ -76,13 +76,12 @@ void Planner::cells_of(const View &v, std::vector<int64_t> &out) const {
         for (int32_t c = c0; c < c1; ++c) out.push_back(o.cell_base + int64_t(r) * o.nc + c);
 }
 
-int32_t Planner::emit(Kind k, const std::vector<const View *> &reads,
-                      const std::vector<const View *> &writes) {
+int32_t Planner::emit_views(Kind k, const View *const *reads, size_t nr, const View *const *writes, size_t nw) {
     static thread_local std::vector<int64_t> rc, wc;
     rc.clear();
     wc.clear();
-    for (const View *v : reads) cells_of(*v, rc);
-    for (const View *v : writes) cells_of(*v, wc);
+    for (size_t i = 0; i < nr; ++i) cells_of(*reads[i], rc);
+    for (size_t i = 0; i < nw; ++i) cells_of(*writes[i], wc);
     int32_t dep = -1;
     for (int64_t c : rc) dep = std::max(dep, cell_write_wave[c]);
     for (int64_t c : wc) dep = std::max(dep, std::max(cell_write_wave[c], cell_read_wave[c]));
@@ -276,9 +275,17 @@ void Planner::trsm_u_panel(Block *U, const View &Pv) {
 // contributions of all leaves covering one leaf cluster of the output rows.
 void Planner::hmm(const View &out, double alpha, bool overwrite, Block *M, bool trans, const View &X,
                   int32_t wdst, int32_t wsrc) {
-    std::vector<Block *> lv;
+    // scratch reused across calls (hmm does not recurse)
+    static thread_local std::vector<Block *> lv;
+    static thread_local std::vector<View> Tv;
+    static thread_local std::vector<std::vector<int32_t>> seg;
+    static thread_local std::vector<View> keep;
+    static thread_local std::vector<const View *> rd;
+    static thread_local std::vector<int32_t> depth, group;
+    static thread_local std::vector<int64_t> cells;
+    lv.clear();
     collect_leaves(M, lv);
-    std::vector<View> Tv(lv.size());
+    Tv.assign(lv.size(), View{});
     for (size_t i = 0; i < lv.size(); ++i) {
         Block *m = lv[i];
         if (m->kind != B_LOWRANK) continue;
@@ -294,16 +301,13 @@ void Planner::hmm(const View &out, double alpha, bool overwrite, Block *M, bool 
     }
     int32_t oc = out.r_cl;
     int32_t lc0 = cl[oc].lc_first, nseg = cl[oc].lc_count;
-    std::vector<std::vector<int32_t>> seg(nseg);
+    if ((int32_t)seg.size() < nseg) seg.resize(nseg);
+    for (int32_t qi = 0; qi < nseg; ++qi) seg[qi].clear();
     for (size_t i = 0; i < lv.size(); ++i) {
         int32_t rm = trans ? lv[i]->s : lv[i]->t;
         for (int32_t q = cl[rm].lc_first; q < cl[rm].lc_first + cl[rm].lc_count; ++q)
             seg[q - lc0].push_back(int32_t(i));
     }
-    std::vector<View> keep;
-    std::vector<const View *> rd;
-    std::vector<int32_t> depth, group;
-    std::vector<int64_t> cells;
     for (int32_t qi = 0; qi < nseg; ++qi) {
         if (seg[qi].empty() && !overwrite) continue;
         int32_t q = lc_ids[lc0 + qi];
@@ -435,7 +439,8 @@ void Planner::radd(Block *C, bool include_self, const std::vector<Piece> &pcs,
     P->radd.push_back(tr);
     P->max_kcap = std::max(P->max_kcap, kcap);
     View U = viewU(C), V = viewV(C);
-    std::vector<const View *> rd;
+    static thread_local std::vector<const View *> rd;
+    rd.clear();
     for (const View &v : pviews) rd.push_back(&v);
     if (include_self) {
         rd.push_back(&U);
@@ -757,7 +762,27 @@ static std::vector<int32_t> permute_by_wave(std::vector<T> &v, std::vector<int32
     return where;
 }
 
-void Planner::finalize(Plan &p, int64_t *bump) {
+// Rounded-addition scratch: the tasks of one wave get disjoint regions of the arena, waves reuse
+// them (the regions are assigned in emission order within each wave).
+void Planner::finalize_alloc(Plan &p, int64_t *bump) const {
+    const int64_t base = align8(*bump);
+    std::vector<int64_t> woff(size_t(std::max(p.n_waves, 1)), 0);
+    int64_t maxw = 0;
+    for (size_t i = 0; i < p.radd.size(); ++i) {
+        TRadd &r = p.radd[i];
+        int64_t &off = woff[p.wave[K_RADD][i]];
+        r.scratch_off = base + off;
+        const int32_t kc = std::min(r.Kcap, opt.kmax_core);
+        off = align8(off + int64_t(r.m + r.n) * std::max(kc, 1));
+        maxw = std::max(maxw, off);
+    }
+    p.scratch_base = base;
+    p.scratch_elems = maxw;
+    *bump = base + maxw;
+}
+
+// Orders the tasks by wave, builds the successor lists and priorities and the wave launches.
+void Planner::finalize_graph(Plan &p) const {
     std::vector<int32_t> where[K_NKINDS];
     where[K_GETRF] = permute_by_wave(p.getrf, p.wave[K_GETRF], p.n_waves);
     where[K_TRSM] = permute_by_wave(p.trsm, p.wave[K_TRSM], p.n_waves);
@@ -810,25 +835,6 @@ void Planner::finalize(Plan &p, int64_t *bump) {
             if (p.indeg[g] == 0) p.roots.push_back(int32_t(g));
         std::sort(p.roots.begin(), p.roots.end(), by_priority);
     }
-    // rounded-addition scratch: tasks of one wave get disjoint regions, waves reuse them
-    int64_t base = align8(*bump), maxw = 0;
-    {
-        size_t i = 0;
-        while (i < p.radd.size()) {
-            int32_t w = p.wave[K_RADD][i];
-            int64_t off = 0;
-            for (; i < p.radd.size() && p.wave[K_RADD][i] == w; ++i) {
-                TRadd &r = p.radd[i];
-                r.scratch_off = base + off;
-                int32_t kc = std::min(r.Kcap, opt.kmax_core);
-                off = align8(off + int64_t(r.m + r.n) * std::max(kc, 1));
-            }
-            maxw = std::max(maxw, off);
-        }
-    }
-    p.scratch_base = base;
-    p.scratch_elems = maxw;
-    *bump = base + maxw;
     // launches: for each wave, one launch per kind present
     size_t pos[K_NKINDS] = {0, 0, 0, 0, 0, 0};
     for (int32_t w = 0; w < p.n_waves; ++w) {
@@ -1124,7 +1130,8 @@ int Planner::plan_all() {
         choose_inverses(0, std::max(opt.inv_block, max_leaf));
         plan_inverses();
     }
-    finalize(fplan, &f_elems);
+    finalize_alloc(fplan, &f_elems);
+    finalize_graph(fplan);
     f_solve_off = f_elems;
     f_elems = align8(f_elems + int64_t(n) * opt.nrhs_max);
     View Y;
@@ -1148,7 +1155,8 @@ int Planner::plan_all() {
         solve_upper(root, Y);
     }
     split_accum = false;
-    finalize(splan, &f_elems);
+    finalize_alloc(splan, &f_elems);
+    finalize_graph(splan);
     layout_a_arena();
     a_x_off = a_elems;
     a_elems = align8(a_elems + int64_t(n) * opt.nrhs_max);
@@ -1161,7 +1169,8 @@ int Planner::plan_all() {
     Yo.obj = new_obj(0, -1);
     begin_plan(mplan, true, &a_elems);
     hmm(Yo, 1.0, true, root, false, X);
-    finalize(mplan, &a_elems);
+    finalize_alloc(mplan, &a_elems);
+    finalize_graph(mplan);
     P = nullptr;
     // the ACCUM kernel keeps one output row per thread slot (at most 1024 rows)
     for (const Plan *pp : {&fplan, &splan, &mplan})

@@ -17,6 +17,7 @@
 #pragma once
 #include <stdint.h>
 
+#include <initializer_list>
 #include <string>
 #include <vector>
 
@@ -172,7 +173,13 @@ private:
     int32_t new_slot(int32_t init);
     View new_temp(int32_t row_cl, int32_t rows, int32_t cols, int32_t rslot, int32_t cslot);
     void cells_of(const View &v, std::vector<int64_t> &out) const;
-    int32_t emit(Kind k, const std::vector<const View *> &reads, const std::vector<const View *> &writes);
+    int32_t emit_views(Kind k, const View *const *reads, size_t nr, const View *const *writes, size_t nw);
+    int32_t emit(Kind k, std::initializer_list<const View *> reads, std::initializer_list<const View *> writes) {
+        return emit_views(k, reads.begin(), reads.size(), writes.begin(), writes.size());
+    }
+    int32_t emit(Kind k, const std::vector<const View *> &reads, std::initializer_list<const View *> writes) {
+        return emit_views(k, reads.data(), reads.size(), writes.begin(), writes.size());
+    }
 
     Store &st(const Block *b) { return use_astore ? astore[b->id] : fstore[b->id]; }
     View viewD(const Block *b);
@@ -212,7 +219,8 @@ private:
     int build_tree();
     void layout_factor_arena();
     void layout_a_arena();
-    void finalize(Plan &p, int64_t *bump);
+    void finalize_alloc(Plan &p, int64_t *bump) const;
+    void finalize_graph(Plan &p) const;
     void begin_plan(Plan &p, bool astore_mode, int64_t *bump);
 };
 
