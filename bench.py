@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--solver", default="ir", choices=("ir", "gmres"),
                     help="FP64 iteration preconditioned by the factors: refinement or GMRES(restart)")
     ap.add_argument("--restart", type=int, default=30)
+    ap.add_argument("--construct", action="store_true",
+                    help="time the construction of the workload's H-matrix on the GPU (hlu_bem_build)")
     return ap.parse_args()
 
 
@@ -733,8 +735,47 @@ def run_serve(args):
         print(json.dumps(line), flush=True)
 
 
+def run_construct(args):
+    """Construction of the workload's H-matrix leaves on the GPU (dense blocks, ACA + truncation of
+    the admissible blocks) against the host generator that built the same matrix (Python + NumPy,
+    one process). The block tree and the leaf kinds are the host's; the GPU computes the data."""
+    import numpy as np
+    import torch
+
+    from bem_inputs import WORKLOADS, build_problem
+    from paper_1906_00874_gb300 import build
+    from paper_1906_00874_gb300.hlu import BEMBuild
+
+    w = dict(WORKLOADS[args.workload])
+    p = build_problem(cache=False, **w)
+    torch.cuda.set_device(0)
+    build.build()
+    for _ in range(max(1, args.warmup)):
+        BEMBuild.from_problem(p).close()
+    times = []
+    for _ in range(max(1, args.steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g = BEMBuild.from_problem(p)
+        times.append(time.perf_counter() - t0)
+    ranks = g.rank[p.kind == 1]
+    same = float(np.mean(ranks == p.rank[p.kind == 1]))
+    g.close()
+    sec = sorted(times)[len(times) // 2]
+    print(json.dumps({
+        "metric": "H-matrix construction time (leaf data of a given block tree)", "value": sec * 1e3, "unit": "ms",
+        "higher_is_better": False, "n_gpus": 1, "steps": len(times), "warmup": args.warmup, "data": "synthetic",
+        "config": {"workload": f"{args.workload}: n={p.n}, {p.n_leaves} leaves "
+                               f"({int((p.kind == 1).sum())} low rank), eps={p.eps:g}"},
+        "host_generator_s": p.build_seconds, "speedup_vs_host_generator": p.build_seconds / sec,
+        "low_rank_rank_equal_to_host": same, "data_doubles": int(g.data_len)}), flush=True)
+
+
 def main():
     args = parse()
+    if args.construct:
+        run_construct(args)
+        return
     from bem_inputs import BATCHES, STREAMS
     if args.impl == "reference":
         run_reference(args)

@@ -150,6 +150,51 @@ int hlu_factor_batch(hlu_t h, const double *eps);
  * hlu_create, 0 for a NULL handle. */
 int hlu_batch_count(hlu_t h);
 
+/* ------------------------------------------------ construction on the GPU */
+/* Inputs of hlu_bem_build (host pointers): the Laplace kernel of Sec. 6.1 in
+ * dimension dim (3: 1/(4 pi r); 2: -log(r)/(2 pi); 1: -log r), in collocation
+ * form with one element per degree of freedom: centroid (n x 3, row major,
+ * original order; unused coordinates 0) and size (area or length, n values).
+ * The cluster tree and the leaves of the block tree (row_cl, col_cl, kind:
+ * 0 dense, 1 low rank) are as for hlu_create; the data are computed here.
+ * Low-rank leaves: adaptive cross approximation with partial pivoting to the
+ * relative tolerance eps, at most aca_cap cross vectors (0 -> 48, at most 64),
+ * then truncated at eps by the rounded addition (Sec. 3.1). */
+typedef struct {
+    int32_t dim;
+    const double *centroid;
+    const double *size;
+    const hlu_tree *tree;
+    int64_t n_leaves;
+    const int32_t *row_cl;
+    const int32_t *col_cl;
+    const int8_t *kind;
+    double eps;
+    int32_t aca_cap;
+    int32_t reserved_;   /* set to 0 */
+} hlu_bem_input;
+
+typedef struct hlu_bem *hlu_bem_t;
+
+/* Build the leaf data on the device (stream order, synchronised on return).
+ * HLU_ERANKCAP when a cross approximation does not reach eps within aca_cap
+ * vectors (the block should be stored dense or partitioned).  On failure *out
+ * is NULL. */
+int hlu_bem_build(const hlu_bem_input *in, void *cuda_stream, hlu_bem_t *out);
+
+/* The result in the layout of hlu_blocks: rank and offset (host arrays of
+ * n_leaves, copied out when non-NULL), the total number of doubles, and the
+ * DEVICE pointer to the data (owned by the builder). */
+int hlu_bem_result(hlu_bem_t b, int32_t *rank, int64_t *offset, int64_t *data_len, const double **data_dev);
+
+/* Copy the data to host memory (data_len doubles). */
+int hlu_bem_copy_data(hlu_bem_t b, double *host);
+
+/* hlu_create on the builder's matrix (its tree, leaves and data). */
+int hlu_create_bem(hlu_bem_t b, const hlu_opts *opts, void *cuda_stream, hlu_t *out);
+
+void hlu_bem_destroy(hlu_bem_t b);
+
 /* Solve A x = b with the factors: forward substitution with the unit lower
  * factor, then backward substitution with the upper factor (Sec. 3.1).
  * b is a DEVICE pointer to n x nrhs FP64 values, column-major with leading

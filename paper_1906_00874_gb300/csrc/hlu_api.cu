@@ -15,10 +15,7 @@
 #include "kernels.cuh"
 #include "plan.h"
 
-namespace hlu {
-template <class T>
-bool set_kernel_attributes();
-}
+
 
 using namespace hlu;
 

@@ -25,6 +25,10 @@ template <class T>
 void launch_kind(int kind, const void *tasks, const Term *terms, const Piece *pieces, int start,
                  int count, int kcap, const LaunchArgs &a, cudaStream_t s);
 
+// Opt the task kernels of precision T into the device's largest dynamic shared memory.
+template <class T>
+bool set_kernel_attributes();
+
 // Persistent data-flow execution of a whole plan (one launch).
 struct FlowArgs {
     const int32_t *code;       // per task: (kind << kCodeShift) | index in the kind's array

@@ -26,7 +26,8 @@ EXPORTS = ("hlu_create", "hlu_factor", "hlu_solve", "hlu_matvec", "hlu_solve_ref
            "hlu_factor_doubles",
            "hlu_get_factors", "hlu_get_stats", "hlu_set_profiling", "hlu_destroy", "hlu_strerror",
            "hlu_last_error_detail", "hlu_last_cuda_error", "hlu_probe_alu_peaks", "hlu_inject_stall",
-           "hlu_create_batch", "hlu_factor_batch", "hlu_batch_count")
+           "hlu_create_batch", "hlu_factor_batch", "hlu_batch_count", "hlu_bem_build", "hlu_bem_result",
+           "hlu_bem_copy_data", "hlu_create_bem", "hlu_bem_destroy")
 KINDS = ("getrf", "trsm", "project", "accum", "radd", "split", "dataflow_factor", "dataflow_solve",
          "dataflow_matvec")
 
@@ -53,6 +54,13 @@ class _Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("rank_cap", ctypes.c_int32), ("nrhs_max", ctypes.c_int32),
                 ("schedule", ctypes.c_int32), ("mem_budget", ctypes.c_int64), ("timeout_s", ctypes.c_double),
                 ("inv_block", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
+
+
+class _BemInput(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("centroid", ctypes.c_void_p), ("size", ctypes.c_void_p),
+                ("tree", ctypes.POINTER(_Tree)), ("n_leaves", ctypes.c_int64), ("row_cl", ctypes.c_void_p),
+                ("col_cl", ctypes.c_void_p), ("kind", ctypes.c_void_p), ("eps", ctypes.c_double),
+                ("aca_cap", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -107,6 +115,12 @@ def load(path=LIB_PATH):
     lib.hlu_create.argtypes = [ctypes.POINTER(_Tree), ctypes.POINTER(_Blocks), ctypes.POINTER(_Opts), vp,
                                ctypes.POINTER(vp)]
     lib.hlu_factor.argtypes = [vp, dbl]
+    lib.hlu_bem_build.argtypes = [ctypes.POINTER(_BemInput), vp, ctypes.POINTER(vp)]
+    lib.hlu_bem_result.argtypes = [vp, vp, vp, ctypes.POINTER(i64), ctypes.POINTER(vp)]
+    lib.hlu_bem_copy_data.argtypes = [vp, vp]
+    lib.hlu_create_bem.argtypes = [vp, ctypes.POINTER(_Opts), vp, ctypes.POINTER(vp)]
+    lib.hlu_bem_destroy.argtypes = [vp]
+    lib.hlu_bem_destroy.restype = None
     lib.hlu_create_batch.argtypes = [i32, ctypes.POINTER(_Tree), ctypes.POINTER(_Blocks), ctypes.POINTER(_Opts), vp,
                                      ctypes.POINTER(vp)]
     lib.hlu_factor_batch.argtypes = [vp, ctypes.POINTER(dbl)]
@@ -353,3 +367,77 @@ class HLU:
 
     def __exit__(self, *a):
         self.close()
+
+
+class BEMBuild:
+    """The leaves of an H-matrix built on the GPU (hlu_bem_build): the Laplace kernel of dimension
+    `dim` on the elements (centroid, size) for the given cluster tree and block-tree leaves."""
+
+    def __init__(self, dim, centroid, size, perm, begin, csize, son0, son1, row_cl, col_cl, kind, eps,
+                 aca_cap=0, stream=None):
+        lib = load()
+        keep = [np.ascontiguousarray(a, dtype=t) for a, t in (
+            (centroid, np.float64), (size, np.float64), (perm, np.int32), (begin, np.int32), (csize, np.int32),
+            (son0, np.int32), (son1, np.int32), (row_cl, np.int32), (col_cl, np.int32), (kind, np.int8))]
+        c_, a_, perm_, begin_, size_, s0_, s1_, r_, cc_, k_ = keep
+        self.n, self.n_leaves = int(a_.shape[0]), int(r_.shape[0])
+        tree = _Tree(self.n, int(begin_.shape[0]), _ptr(perm_), _ptr(begin_), _ptr(size_), _ptr(s0_), _ptr(s1_))
+        inp = _BemInput(int(dim), _ptr(c_), _ptr(a_), ctypes.pointer(tree), self.n_leaves, _ptr(r_), _ptr(cc_),
+                        _ptr(k_), float(eps), int(aca_cap), 0)
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self._b = ctypes.c_void_p()
+        st = lib.hlu_bem_build(ctypes.byref(inp), ctypes.c_void_p(stream), ctypes.byref(self._b))
+        if st != 0:
+            self._b = ctypes.c_void_p()
+            raise HLUError(st, "hlu_bem_build")
+        self.rank = np.zeros(self.n_leaves, dtype=np.int32)
+        self.offset = np.zeros(self.n_leaves, dtype=np.int64)
+        n_data = ctypes.c_int64()
+        dev = ctypes.c_void_p()
+        lib.hlu_bem_result(self._b, _ptr(self.rank), _ptr(self.offset), ctypes.byref(n_data), ctypes.byref(dev))
+        self.data_len = n_data.value
+
+    @classmethod
+    def from_problem(cls, p, eps=None, **kw):
+        """The GPU build of a problem's matrix: its geometry, trees and leaf kinds."""
+        t = p.tree
+        return cls(getattr(p, "dim", 3), p.centroid, p.area, t.perm, t.begin, t.size, t.son0, t.son1, p.row_cl,
+                   p.col_cl, p.kind, p.eps if eps is None else eps, **kw)
+
+    def data(self):
+        """The leaf data copied to host memory (layout of hlu_blocks)."""
+        out = np.empty(max(self.data_len, 1))
+        st = load().hlu_bem_copy_data(self._b, _ptr(out))
+        if st != 0:
+            raise HLUError(st, "hlu_bem_copy_data")
+        return out[:self.data_len]
+
+    def create(self, precision=HLU_FP64, rank_cap=0, nrhs_max=0, mem_budget=0, stream=None,
+               schedule=SCHED_DATAFLOW, timeout_s=0.0, inv_block=0):
+        """An HLU handle on this matrix (hlu_create_bem)."""
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        opts = _Opts(int(precision), int(rank_cap), int(nrhs_max), int(schedule), int(mem_budget), float(timeout_s),
+                     int(inv_block), 0)
+        h = HLU.__new__(HLU)
+        h._h = ctypes.c_void_p()
+        h.n, h.sizes, h.n_leaves, h.precision = self.n, (self.n,), self.n_leaves, int(precision)
+        st = load().hlu_create_bem(self._b, ctypes.byref(opts), ctypes.c_void_p(stream), ctypes.byref(h._h))
+        if st != 0:
+            h._h = ctypes.c_void_p()
+            raise HLUError(st, "hlu_create_bem")
+        return h
+
+    def close(self):
+        if self._b:
+            load().hlu_bem_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
