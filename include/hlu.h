@@ -150,6 +150,27 @@ int hlu_factor_batch(hlu_t h, const double *eps);
  * hlu_create, 0 for a NULL handle. */
 int hlu_batch_count(hlu_t h);
 
+/* ------------------------------------------------ plan without a device */
+/* Validation and planning only (host, no CUDA call): the sizes of the task
+ * graphs hlu_create would build for these inputs and options. */
+typedef struct {
+    int64_t factor_tasks;    /* tasks of the factorisation graph */
+    int64_t factor_edges;    /* dependencies between them */
+    int64_t factor_levels;   /* longest dependency chain (tasks) */
+    int64_t solve_tasks;     /* tasks of one solve pass (forward and backward) */
+    int64_t solve_levels;
+    int64_t matvec_tasks;
+    int64_t inverse_blocks;  /* diagonal blocks inverted for the solve (hlu_opts.inv_block) */
+    int64_t factor_elems;    /* elements of the factor arena */
+    double plan_ms;          /* host time of the planning */
+} hlu_plan_info;
+
+int hlu_plan_info_get(const hlu_tree *tree, const hlu_blocks *blocks, const hlu_opts *opts, hlu_plan_info *out);
+
+/* The same for the batch of hlu_create_batch. */
+int hlu_plan_info_batch(int32_t count, const hlu_tree *trees, const hlu_blocks *blocks, const hlu_opts *opts,
+                        hlu_plan_info *out);
+
 /* ------------------------------------------------ construction on the GPU */
 /* Inputs of hlu_bem_build (host pointers): the Laplace kernel of Sec. 6.1 in
  * dimension dim (3: 1/(4 pi r); 2: -log(r)/(2 pi); 1: -log r), in collocation

@@ -502,10 +502,23 @@ int hlu_create(const hlu_tree *tree, const hlu_blocks *blocks, const hlu_opts *o
     return create_impl(tree, blocks, opts, cuda_stream, out, nullptr, 0);
 }
 
-int hlu_create_batch(int32_t count, const hlu_tree *trees, const hlu_blocks *blocks, const hlu_opts *opts,
-                     void *cuda_stream, hlu_t *out) {
-    if (!out) return HLU_EINVAL;
-    *out = nullptr;
+}  // extern "C"
+
+namespace {
+
+// Several problems as one block-diagonal H-matrix: count - 1 clusters above the problems (cluster 0
+// is the root), then every problem's clusters with indices and ranges shifted; leaves, offsets and
+// data concatenated.  inst[c] is the problem of cluster c (-1 above the problems).
+struct Forest {
+    std::vector<int32_t> perm, begin, size, son0, son1, inst, rc, cc, rk;
+    std::vector<int8_t> kd;
+    std::vector<int64_t> off;
+    std::vector<double> data;
+    hlu_tree t{};
+    hlu_blocks b{};
+};
+
+int make_forest(int32_t count, const hlu_tree *trees, const hlu_blocks *blocks, Forest &f) {
     if (count < 1 || !trees || !blocks) return HLU_EINVAL;
     int64_t N = 0, ncl = count - 1, nl = 0, dl = 0;
     for (int32_t i = 0; i < count; ++i) {
@@ -522,11 +535,23 @@ int hlu_create_batch(int32_t count, const hlu_tree *trees, const hlu_blocks *blo
     if (N > INT32_MAX || ncl > INT32_MAX) return HLU_EINVAL;
     // clusters: count - 1 clusters above the instances first (cluster 0 is the root), then every
     // instance's own clusters, indices and ranges shifted; leaves, offsets and data concatenated
-    std::vector<int32_t> perm(N), begin(ncl), size(ncl), son0(ncl), son1(ncl), inst(ncl, -1);
-    std::vector<int32_t> rc(nl), cc(nl), rk(nl);
-    std::vector<int8_t> kd(nl);
-    std::vector<int64_t> off(nl), cl_off(count);
-    std::vector<double> data(dl);
+    f.perm.assign(N, 0);
+    f.begin.assign(ncl, 0);
+    f.size.assign(ncl, 0);
+    f.son0.assign(ncl, -1);
+    f.son1.assign(ncl, -1);
+    f.inst.assign(ncl, -1);
+    f.rc.assign(nl, 0);
+    f.cc.assign(nl, 0);
+    f.rk.assign(nl, 0);
+    f.kd.assign(nl, 0);
+    f.off.assign(nl, 0);
+    f.data.assign(dl, 0.0);
+    std::vector<int32_t> &perm = f.perm, &begin = f.begin, &size = f.size, &son0 = f.son0, &son1 = f.son1,
+                         &inst = f.inst, &rc = f.rc, &cc = f.cc, &rk = f.rk;
+    std::vector<int8_t> &kd = f.kd;
+    std::vector<int64_t> &off = f.off, cl_off(count);
+    std::vector<double> &data = f.data;
     int64_t no = 0, co = count - 1, lo = 0, dof = 0;
     for (int32_t i = 0; i < count; ++i) {
         const hlu_tree &t = trees[i];
@@ -566,9 +591,73 @@ int hlu_create_batch(int32_t count, const hlu_tree *trees, const hlu_blocks *blo
         return v;
     };
     make(0, count);
-    const hlu_tree t{int32_t(N), int32_t(ncl), perm.data(), begin.data(), size.data(), son0.data(), son1.data()};
-    const hlu_blocks b{nl, rc.data(), cc.data(), kd.data(), rk.data(), off.data(), data.data(), dl};
-    return create_impl(&t, &b, opts, cuda_stream, out, inst.data(), count);
+    f.t = hlu_tree{int32_t(N), int32_t(ncl), perm.data(), begin.data(), size.data(), son0.data(), son1.data()};
+    f.b = hlu_blocks{nl, rc.data(), cc.data(), kd.data(), rk.data(), off.data(), data.data(), dl};
+    return HLU_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+}  // extern "C"
+
+namespace {
+
+int plan_only(const hlu_tree *tree, const hlu_blocks *blocks, const hlu_opts *opts, const int32_t *inst,
+              int32_t n_inst, hlu_plan_info *out) {
+    if (!out || !tree || !blocks) return HLU_EINVAL;
+    std::memset(out, 0, sizeof(*out));
+    const auto t0 = std::chrono::steady_clock::now();
+    PlanOptions po;
+    if (opts) {
+        if (opts->rank_cap > 0) po.rank_cap = opts->rank_cap;
+        if (opts->nrhs_max > 0) po.nrhs_max = opts->nrhs_max;
+        if (opts->inv_block != 0) po.inv_block = opts->inv_block < 0 ? 0 : opts->inv_block;
+    }
+    Planner pl;
+    int st = pl.build(tree->n, tree->n_clusters, tree->perm, tree->begin, tree->size, tree->son0, tree->son1,
+                      blocks->n_leaves, blocks->row_cl, blocks->col_cl, blocks->kind, blocks->rank, blocks->offset,
+                      blocks->data, blocks->data_len, po, inst, n_inst);
+    if (st == HLU_OK && pl.max_leaf > 128) st = HLU_EINVAL;
+    if (st == HLU_OK) st = pl.plan_all();
+    if (st) return st;
+    out->factor_tasks = pl.fplan.n_tasks;
+    out->factor_edges = pl.fplan.n_edges;
+    out->factor_levels = pl.fplan.n_waves;
+    out->solve_tasks = pl.splan.n_tasks;
+    out->solve_levels = pl.splan.n_waves;
+    out->matvec_tasks = pl.mplan.n_tasks;
+    out->inverse_blocks = (int64_t)pl.inv_cl.size();
+    out->factor_elems = pl.f_elems;
+    out->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return HLU_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hlu_plan_info_get(const hlu_tree *tree, const hlu_blocks *blocks, const hlu_opts *opts, hlu_plan_info *out) {
+    return plan_only(tree, blocks, opts, nullptr, 0, out);
+}
+
+int hlu_plan_info_batch(int32_t count, const hlu_tree *trees, const hlu_blocks *blocks, const hlu_opts *opts,
+                        hlu_plan_info *out) {
+    Forest f;
+    const int st = make_forest(count, trees, blocks, f);
+    if (st) return st;
+    return plan_only(&f.t, &f.b, opts, f.inst.data(), count, out);
+}
+
+int hlu_create_batch(int32_t count, const hlu_tree *trees, const hlu_blocks *blocks, const hlu_opts *opts,
+                     void *cuda_stream, hlu_t *out) {
+    if (!out) return HLU_EINVAL;
+    *out = nullptr;
+    Forest f;
+    const int st = make_forest(count, trees, blocks, f);
+    if (st) return st;
+    return create_impl(&f.t, &f.b, opts, cuda_stream, out, f.inst.data(), count);
 }
 
 int hlu_factor(hlu_t h, double eps) {

@@ -559,9 +559,11 @@ bool Planner::leaf_is_dense(int32_t q, int32_t j) const {
     return B->kind == B_DENSE;
 }
 
-// The largest clusters of order <= bound under t.
+// The largest clusters of order <= bound under t (in a batch, clusters of one problem only: a block
+// over several problems would couple their solves through its zero blocks).
 void Planner::choose_inverses(int32_t t, int32_t bound) {
-    if (cl[t].size <= bound || cl[t].son0 < 0) {
+    const bool one_problem = inst.empty() || inst[t] >= 0;
+    if ((cl[t].size <= bound && one_problem) || cl[t].son0 < 0) {
         inv_index[t] = int32_t(inv_cl.size());
         inv_cl.push_back(t);
         return;

@@ -27,7 +27,7 @@ EXPORTS = ("hlu_create", "hlu_factor", "hlu_solve", "hlu_matvec", "hlu_solve_ref
            "hlu_get_factors", "hlu_get_stats", "hlu_set_profiling", "hlu_destroy", "hlu_strerror",
            "hlu_last_error_detail", "hlu_last_cuda_error", "hlu_probe_alu_peaks", "hlu_inject_stall",
            "hlu_create_batch", "hlu_factor_batch", "hlu_batch_count", "hlu_bem_build", "hlu_bem_result",
-           "hlu_bem_copy_data", "hlu_create_bem", "hlu_bem_destroy")
+           "hlu_bem_copy_data", "hlu_create_bem", "hlu_bem_destroy", "hlu_plan_info_get", "hlu_plan_info_batch")
 KINDS = ("getrf", "trsm", "project", "accum", "radd", "split", "dataflow_factor", "dataflow_solve",
          "dataflow_matvec")
 
@@ -54,6 +54,33 @@ class _Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("rank_cap", ctypes.c_int32), ("nrhs_max", ctypes.c_int32),
                 ("schedule", ctypes.c_int32), ("mem_budget", ctypes.c_int64), ("timeout_s", ctypes.c_double),
                 ("inv_block", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
+
+
+class _PlanInfo(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in ("factor_tasks", "factor_edges", "factor_levels", "solve_tasks",
+                                              "solve_levels", "matvec_tasks", "inverse_blocks", "factor_elems")] + \
+               [("plan_ms", ctypes.c_double)]
+
+
+def plan_info(problems, rank_cap=0, nrhs_max=0, inv_block=0):
+    """Sizes of the task graphs hlu_create (one problem) or hlu_create_batch (a list) would build:
+    validation and planning on the host only (hlu_plan_info_get / hlu_plan_info_batch)."""
+    lib = load()
+    many = isinstance(problems, (list, tuple))
+    descs = [_describe(p.n, p.tree.perm, p.tree.begin, p.tree.size, p.tree.son0, p.tree.son1, p.row_cl, p.col_cl,
+                       p.kind, p.rank, p.offset, p.data) for p in (problems if many else [problems])]
+    opts = _Opts(0, int(rank_cap), int(nrhs_max), 0, 0, 0.0, int(inv_block), 0)
+    info = _PlanInfo()
+    if many:
+        trees = (_Tree * len(descs))(*[d[0] for d in descs])
+        blocks = (_Blocks * len(descs))(*[d[1] for d in descs])
+        st = lib.hlu_plan_info_batch(len(descs), trees, blocks, ctypes.byref(opts), ctypes.byref(info))
+    else:
+        st = lib.hlu_plan_info_get(ctypes.byref(descs[0][0]), ctypes.byref(descs[0][1]), ctypes.byref(opts),
+                                   ctypes.byref(info))
+    if st != 0:
+        raise HLUError(st, "hlu_plan_info")
+    return {f: getattr(info, f) for f, _ in info._fields_}
 
 
 class _BemInput(ctypes.Structure):
@@ -115,6 +142,10 @@ def load(path=LIB_PATH):
     lib.hlu_create.argtypes = [ctypes.POINTER(_Tree), ctypes.POINTER(_Blocks), ctypes.POINTER(_Opts), vp,
                                ctypes.POINTER(vp)]
     lib.hlu_factor.argtypes = [vp, dbl]
+    lib.hlu_plan_info_get.argtypes = [ctypes.POINTER(_Tree), ctypes.POINTER(_Blocks), ctypes.POINTER(_Opts),
+                                      ctypes.POINTER(_PlanInfo)]
+    lib.hlu_plan_info_batch.argtypes = [i32, ctypes.POINTER(_Tree), ctypes.POINTER(_Blocks), ctypes.POINTER(_Opts),
+                                        ctypes.POINTER(_PlanInfo)]
     lib.hlu_bem_build.argtypes = [ctypes.POINTER(_BemInput), vp, ctypes.POINTER(vp)]
     lib.hlu_bem_result.argtypes = [vp, vp, vp, ctypes.POINTER(i64), ctypes.POINTER(vp)]
     lib.hlu_bem_copy_data.argtypes = [vp, vp]
