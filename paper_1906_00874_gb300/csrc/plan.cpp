@@ -28,12 +28,7 @@ int32_t Planner::new_obj(int32_t row_cl, int32_t col_cl, int32_t nr_if_none) {
     o.cell_base = objs.empty() ? 0 : objs.back().cell_base + int64_t(objs.back().nr) * objs.back().nc;
     objs.push_back(o);
     int64_t need = o.cell_base + int64_t(o.nr) * o.nc;
-    if ((int64_t)cell_write_wave.size() < need) {
-        cell_write_wave.resize(need, -1);
-        cell_read_wave.resize(need, -1);
-        cell_writer.resize(need, -1);
-        cell_rhead.resize(need, -1);
-    }
+    if ((int64_t)cell.size() < need) cell.resize(need, CellState{-1, -1, -1, -1});
     return int32_t(objs.size() - 1);
 }
 
@@ -83,13 +78,13 @@ int32_t Planner::emit_views(Kind k, const View *const *reads, size_t nr, const V
     for (size_t i = 0; i < nr; ++i) cells_of(*reads[i], rc);
     for (size_t i = 0; i < nw; ++i) cells_of(*writes[i], wc);
     int32_t dep = -1;
-    for (int64_t c : rc) dep = std::max(dep, cell_write_wave[c]);
-    for (int64_t c : wc) dep = std::max(dep, std::max(cell_write_wave[c], cell_read_wave[c]));
+    for (int64_t c : rc) dep = std::max(dep, cell[c].write_wave);
+    for (int64_t c : wc) dep = std::max(dep, std::max(cell[c].write_wave, cell[c].read_wave));
     int32_t w = dep + 1;
-    for (int64_t c : rc) cell_read_wave[c] = std::max(cell_read_wave[c], w);
+    for (int64_t c : rc) cell[c].read_wave = std::max(cell[c].read_wave, w);
     for (int64_t c : wc) {
-        cell_write_wave[c] = w;
-        cell_read_wave[c] = -1;
+        cell[c].write_wave = w;
+        cell[c].read_wave = -1;
     }
     // explicit edges: read-after-write, write-after-write, write-after-read; each predecessor is
     // listed once (pred_mark[t] == g once t is in this task's list), in the order first met
@@ -102,20 +97,20 @@ int32_t Planner::emit_views(Kind k, const View *const *reads, size_t nr, const V
             P->pred_idx.push_back(t);
         }
     };
-    for (int64_t c : rc) add(cell_writer[c]);
+    for (int64_t c : rc) add(cell[c].writer);
     for (int64_t c : wc) {
-        add(cell_writer[c]);
-        for (int32_t e = cell_rhead[c]; e >= 0; e = rpool_next[e]) add(rpool_task[e]);
+        add(cell[c].writer);
+        for (int32_t e = cell[c].rhead; e >= 0; e = rpool_next[e]) add(rpool_task[e]);
     }
     P->pred_ptr.push_back(int32_t(P->pred_idx.size()));
     for (int64_t c : rc) {
         rpool_task.push_back(g);
-        rpool_next.push_back(cell_rhead[c]);
-        cell_rhead[c] = int32_t(rpool_task.size() - 1);
+        rpool_next.push_back(cell[c].rhead);
+        cell[c].rhead = int32_t(rpool_task.size() - 1);
     }
     for (int64_t c : wc) {
-        cell_writer[c] = g;
-        cell_rhead[c] = -1;
+        cell[c].writer = g;
+        cell[c].rhead = -1;
     }
     P->task_code.push_back((int32_t(k) << kCodeShift) | int32_t(P->wave[k].size()));
     P->wave[k].push_back(w);
@@ -328,7 +323,7 @@ void Planner::hmm(const View &out, double alpha, bool overwrite, Block *M, bool 
             cells.clear();
             cells_of(keep[2 * ti], cells);
             cells_of(keep[2 * ti + 1], cells);
-            for (int64_t c : cells) depth[ti] = std::max(depth[ti], cell_write_wave[c]);
+            for (int64_t c : cells) depth[ti] = std::max(depth[ti], cell[c].write_wave);
         }
         // In the solve, the terms whose inputs are ready at the deepest level (the part of the
         // update that waits on the latest solved segment) get their own ACCUM; the others are
@@ -737,10 +732,7 @@ void Planner::begin_plan(Plan &p, bool astore_mode, int64_t *bump) {
     P = &p;
     use_astore = astore_mode;
     arena = bump;
-    std::fill(cell_write_wave.begin(), cell_write_wave.end(), -1);
-    std::fill(cell_read_wave.begin(), cell_read_wave.end(), -1);
-    std::fill(cell_writer.begin(), cell_writer.end(), -1);
-    std::fill(cell_rhead.begin(), cell_rhead.end(), -1);
+    std::fill(cell.begin(), cell.end(), CellState{-1, -1, -1, -1});
     rpool_task.clear();
     rpool_next.clear();
 }

@@ -160,9 +160,13 @@ private:
     bool split_accum = false;  // solve plan: split each ACCUM into its early and its latest terms
     int64_t *arena = nullptr;  // bump pointer of the current arena
     std::vector<Obj> objs;
-    std::vector<int32_t> cell_write_wave, cell_read_wave;
-    // per cell: last writer and the readers since (singly linked lists in a pool)
-    std::vector<int32_t> cell_writer, cell_rhead;
+    // per cell: the wave of its last writer, the latest wave that read it since, the last writer
+    // task, and the readers since (head of a singly linked list in a pool); one record per cell so
+    // that the dependency analysis touches one cache line per cell
+    struct CellState {
+        int32_t write_wave, read_wave, writer, rhead;
+    };
+    std::vector<CellState> cell;
     std::vector<int32_t> pred_mark;  // per task: the last task that listed it as a predecessor
     std::vector<int32_t> rpool_task, rpool_next;
     int32_t ident_obj = -1;

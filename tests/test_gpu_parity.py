@@ -266,3 +266,25 @@ def test_solve_refined_matches_manual_refinement(case1280):
     st = h.stats()
     assert st["solve_flops"] > 0 and st["model_flops"] > 0
     h.close()
+
+
+@pytest.mark.parametrize("n", [1, 2, 127])
+@pytest.mark.parametrize("inv_block", [-1, 0])
+def test_single_dense_leaf_degenerate_sizes(n, inv_block):
+    """Degenerate H-matrices: one dense leaf of order 1, 2 or 127 (no low-rank block, one task of each
+    kind).  The factorisation is the unpivoted LU (oracle), the solve the dense solve."""
+    from paper_1906_00874_gb300 import HLU
+    g = np.random.default_rng(n)
+    a = g.standard_normal((n, n)) + 2.0 * n * np.eye(n)
+    b = g.standard_normal((n, 3))
+    h = HLU(n, np.arange(n), [0], [n], [-1], [-1], [0], [0], [0], [0], [0], a.ravel(order="F"), inv_block=inv_block)
+    h.factor(1e-4)
+    _, _, data = h.get_factors()
+    f = a.copy()
+    lu_nopiv(f)
+    assert np.max(np.abs(data[:n * n].reshape((n, n), order="F") - f)) <= 1e-13 * np.max(np.abs(f))
+    bd = _dev(b)
+    h.solve(bd)
+    x = np.linalg.solve(a, b)
+    assert np.max(np.abs(bd.cpu().numpy() - x)) <= 1e-12 * np.max(np.abs(x))
+    h.close()
