@@ -319,11 +319,13 @@ void Planner::hmm(const View &out, double alpha, bool overwrite, Block *M, bool 
                 keep[2 * ti] = rows(trans ? viewV(m) : viewU(m), q);
                 keep[2 * ti + 1] = Tv[seg[qi][ti]];
             }
-            // depth of the term: the latest dependency level among the cells it reads
-            cells.clear();
-            cells_of(keep[2 * ti], cells);
-            cells_of(keep[2 * ti + 1], cells);
-            for (int64_t c : cells) depth[ti] = std::max(depth[ti], cell[c].write_wave);
+            // depth of the term (solve plan only): the latest dependency level among the cells it reads
+            if (split_accum) {
+                cells.clear();
+                cells_of(keep[2 * ti], cells);
+                cells_of(keep[2 * ti + 1], cells);
+                for (int64_t c : cells) depth[ti] = std::max(depth[ti], cell[c].write_wave);
+            }
         }
         // In the solve, the terms whose inputs are ready at the deepest level (the part of the
         // update that waits on the latest solved segment) get their own ACCUM; the others are
