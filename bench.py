@@ -52,6 +52,42 @@ def parse():
     return ap.parse_args()
 
 
+class RankOps:
+    """Barrier and max / sum over the replicas of a multi-GPU run (one rank per GPU, each rank an
+    independent H-LU: no collective on the data path, only these scalar reductions of the timing and
+    the work). `device` is where the scalar lives: "cuda" for NCCL, "cpu" for gloo."""
+
+    def __init__(self, world, device):
+        self.world, self.device = world, device
+
+    def barrier(self):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def _reduce(self, v, op):
+        if self.world == 1:
+            return v
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([v], dtype=torch.float64, device=self.device)
+        dist.all_reduce(t, op=op)
+        return t.item()
+
+    def max(self, v):
+        import torch.distributed as dist
+        return self._reduce(v, dist.ReduceOp.MAX) if self.world > 1 else v
+
+    def sum(self, v):
+        import torch.distributed as dist
+        return self._reduce(v, dist.ReduceOp.SUM) if self.world > 1 else v
+
+
+def aggregate(total_ms_per_rank_max, work_per_rank_sum):
+    """Whole-job throughput of weak-scaled replicas: the work of all ranks over the slowest rank's time."""
+    return work_per_rank_sum / (total_ms_per_rank_max * 1e-3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -266,26 +302,8 @@ def run_native(args):
     b = to_device_panel(p.b)
     x = torch.zeros_like(b)
 
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
-    def max_over_ranks(v):
-        if world == 1:
-            return v
-        import torch.distributed as dist
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return t.item()
-
-    def sum_over_ranks(v):
-        if world == 1:
-            return v
-        import torch.distributed as dist
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return t.item()
+    ranks = RankOps(world, "cuda")
+    barrier, max_over_ranks, sum_over_ranks = ranks.barrier, ranks.max, ranks.sum
 
     def step(h):
         h.factor(p.eps)
@@ -329,7 +347,7 @@ def run_native(args):
     f32, st32 = flops_per_step(h32)
     t_ms = max_over_ranks(arm32["total_ms"])
     total_flops = sum_over_ranks(f32 * args.steps)
-    value = total_flops / (t_ms * 1e-3) / 1e9
+    value = aggregate(t_ms, total_flops) / 1e9
     per = sorted(arm32["per_step_ms"])
 
     def pct(a, q):
@@ -521,18 +539,8 @@ def run_batch(args):
     bn = [float(np.linalg.norm(p.b)) for p in probs]
     tol_stack = TOL * min(bn) / float(np.linalg.norm(bn))
 
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
-    def max_over_ranks(v):
-        if world == 1:
-            return v
-        import torch.distributed as dist
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return t.item()
+    ranks = RankOps(world, "cuda")
+    barrier, max_over_ranks = ranks.barrier, ranks.max
 
     def timed(fn, steps, warmup):
         for _ in range(warmup):
