@@ -140,3 +140,21 @@ def test_batch_rejects_bad_count_and_bad_problem(lib, prob1280):
     with pytest.raises(HLUError) as e:
         HLU.batch([prob1280, bad], stream=0)
     assert e.value.status == 1
+
+
+def test_bem_build_validates_before_any_device_call(lib, prob1280):
+    """hlu_bem_build rejects a bad dimension, a cross-approximation capacity above 64, a bad
+    permutation and a non-positive element size on the host."""
+    from paper_1906_00874_gb300.hlu import BEMBuild, HLUError
+    p = prob1280
+    t = p.tree
+    good = dict(dim=3, centroid=p.centroid, size=p.area, perm=t.perm, begin=t.begin, csize=t.size, son0=t.son0,
+                son1=t.son1, row_cl=p.row_cl, col_cl=p.col_cl, kind=p.kind, eps=1e-4, stream=0)
+    bad_perm = t.perm.copy()
+    bad_perm[0] = p.n
+    bad_size = p.area.copy()
+    bad_size[3] = 0.0
+    for mut in (dict(dim=4), dict(aca_cap=65), dict(perm=bad_perm), dict(size=bad_size), dict(eps=-1.0)):
+        with pytest.raises(HLUError) as e:
+            BEMBuild(**{**good, **mut})
+        assert e.value.status == 1, mut
