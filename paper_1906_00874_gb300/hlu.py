@@ -191,17 +191,20 @@ def _ptr(a):
 
 def _dev_ptr_and_ld(t, n, what):
     """(pointer, nrhs, ld) of a CUDA float64 tensor holding an n x nrhs column-major panel:
-    shape (n,) or (n, nrhs) with stride(0) == 1."""
+    shape (n,) or (n, nrhs) with stride(0) == 1 (any stride(0) when n == 1: one row)."""
     import torch
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64):
         raise TypeError(f"{what} must be a CUDA float64 tensor")
     if t.dim() == 1:
-        if t.shape[0] != n or t.stride(0) != 1:
+        if t.shape[0] != n or (n > 1 and t.stride(0) != 1):
             raise ValueError(f"{what}: expected a contiguous vector of length {n}")
         return t.data_ptr(), 1, n
-    if t.dim() != 2 or t.shape[0] != n or t.stride(0) != 1:
+    if t.dim() != 2 or t.shape[0] != n or (n > 1 and t.stride(0) != 1):
         raise ValueError(f"{what}: expected shape ({n}, nrhs) in column-major layout (stride(0) == 1)")
-    return t.data_ptr(), t.shape[1], max(t.stride(1), n)
+    ld = n if t.shape[1] <= 1 else t.stride(1)
+    if ld < n:
+        raise ValueError(f"{what}: columns overlap (stride(1) < {n})")
+    return t.data_ptr(), t.shape[1], ld
 
 
 def to_device_panel(a, device="cuda"):
