@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <thread>
 #include <utility>
 
 #include "../../include/hlu.h"
@@ -1099,18 +1100,39 @@ int Planner::build(int32_t n_, int32_t n_clusters, const int32_t *perm_, const i
             error = "leaf data outside the data array";
             return HLU_EINVAL;
         }
-        // an exponent field of all ones is an infinity or a NaN (a vectorisable scan)
-        const double *dl = data + leaf_offset[l];
+    }
+    // every value a leaf covers must be finite: an exponent field of all ones is an infinity or a
+    // NaN.  A vectorisable scan, split over host threads by leaves (the data can be GBs).
+    auto scan = [&](int64_t l0, int64_t l1) {
         uint64_t bad = 0;
-        for (int64_t i = 0; i < len; ++i) {
-            uint64_t bits;
-            std::memcpy(&bits, dl + i, sizeof(bits));
-            bad |= uint64_t((bits & 0x7ff0000000000000ull) == 0x7ff0000000000000ull);
+        for (int64_t l = l0; l < l1; ++l) {
+            const int32_t m = cl[leaf_row[l]].size, nn = cl[leaf_col[l]].size;
+            const int64_t len = leaf_kind[l] == 0 ? int64_t(m) * nn : int64_t(m + nn) * leaf_rank[l];
+            const double *dl = data + leaf_offset[l];
+            for (int64_t i = 0; i < len; ++i) {
+                uint64_t bits;
+                std::memcpy(&bits, dl + i, sizeof(bits));
+                bad |= uint64_t((bits & 0x7ff0000000000000ull) == 0x7ff0000000000000ull);
+            }
         }
-        if (bad) {
-            error = "non-finite input value";
-            return HLU_EINVAL;
-        }
+        return bad != 0;
+    };
+    const int nthreads = int(std::min<int64_t>(std::max(1u, std::min(8u, std::thread::hardware_concurrency())),
+                                                std::max<int64_t>(1, n_leaves / 256)));
+    bool bad = false;
+    if (nthreads <= 1) {
+        bad = scan(0, n_leaves);
+    } else {
+        std::vector<std::thread> pool;
+        std::vector<char> flag(nthreads, 0);
+        for (int q = 0; q < nthreads; ++q)
+            pool.emplace_back([&, q] { flag[q] = scan(n_leaves * q / nthreads, n_leaves * (q + 1) / nthreads); });
+        for (std::thread &th : pool) th.join();
+        for (char f : flag) bad = bad || f;
+    }
+    if (bad) {
+        error = "non-finite input value";
+        return HLU_EINVAL;
     }
     return build_tree();
 }
