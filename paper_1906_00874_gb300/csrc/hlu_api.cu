@@ -452,6 +452,7 @@ static int create_impl(const hlu_tree *tree, const hlu_blocks *blocks, const hlu
         return HLU_EINVAL;
     }
     h->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    po.wave_order = h->schedule == HLU_SCHED_WAVES;
     int st = h->pl.build(tree->n, tree->n_clusters, tree->perm, tree->begin, tree->size, tree->son0, tree->son1,
                          blocks->n_leaves, blocks->row_cl, blocks->col_cl, blocks->kind, blocks->rank,
                          blocks->offset, blocks->data, blocks->data_len, po, inst, n_inst);
@@ -614,6 +615,9 @@ int plan_only(const hlu_tree *tree, const hlu_blocks *blocks, const hlu_opts *op
         if (opts->rank_cap > 0) po.rank_cap = opts->rank_cap;
         if (opts->nrhs_max > 0) po.nrhs_max = opts->nrhs_max;
         if (opts->inv_block != 0) po.inv_block = opts->inv_block < 0 ? 0 : opts->inv_block;
+        po.wave_order = opts->schedule == HLU_SCHED_WAVES;
+    } else {
+        po.wave_order = false;
     }
     Planner pl;
     int st = pl.build(tree->n, tree->n_clusters, tree->perm, tree->begin, tree->size, tree->son0, tree->son1,

@@ -781,17 +781,20 @@ void Planner::finalize_alloc(Plan &p, int64_t *bump) const {
 // Orders the tasks by wave, builds the successor lists and priorities and the wave launches.
 void Planner::finalize_graph(Plan &p) const {
     std::vector<int32_t> where[K_NKINDS];
-    where[K_GETRF] = permute_by_wave(p.getrf, p.wave[K_GETRF], p.n_waves);
-    where[K_TRSM] = permute_by_wave(p.trsm, p.wave[K_TRSM], p.n_waves);
-    where[K_PROJECT] = permute_by_wave(p.project, p.wave[K_PROJECT], p.n_waves);
-    where[K_ACCUM] = permute_by_wave(p.accum, p.wave[K_ACCUM], p.n_waves);
-    where[K_RADD] = permute_by_wave(p.radd, p.wave[K_RADD], p.n_waves);
-    where[K_SPLIT] = permute_by_wave(p.split, p.wave[K_SPLIT], p.n_waves);
-    // task codes follow the permutation; successors from the predecessor lists
-    for (int32_t &c : p.task_code) {
-        const int32_t k = c >> kCodeShift, i = c & kCodeMask;
-        c = (k << kCodeShift) | where[k][i];
+    if (opt.wave_order) {
+        where[K_GETRF] = permute_by_wave(p.getrf, p.wave[K_GETRF], p.n_waves);
+        where[K_TRSM] = permute_by_wave(p.trsm, p.wave[K_TRSM], p.n_waves);
+        where[K_PROJECT] = permute_by_wave(p.project, p.wave[K_PROJECT], p.n_waves);
+        where[K_ACCUM] = permute_by_wave(p.accum, p.wave[K_ACCUM], p.n_waves);
+        where[K_RADD] = permute_by_wave(p.radd, p.wave[K_RADD], p.n_waves);
+        where[K_SPLIT] = permute_by_wave(p.split, p.wave[K_SPLIT], p.n_waves);
+        // task codes follow the permutation
+        for (int32_t &c : p.task_code) {
+            const int32_t k = c >> kCodeShift, i = c & kCodeMask;
+            c = (k << kCodeShift) | where[k][i];
+        }
     }
+    // successors from the predecessor lists
     const int64_t nt = p.n_tasks;
     if (p.pred_ptr.empty()) p.pred_ptr.push_back(0);
     p.indeg.assign(nt, 0);
@@ -832,7 +835,8 @@ void Planner::finalize_graph(Plan &p) const {
             if (p.indeg[g] == 0) p.roots.push_back(int32_t(g));
         std::sort(p.roots.begin(), p.roots.end(), by_priority);
     }
-    // launches: for each wave, one launch per kind present
+    // launches: for each wave, one launch per kind present (wave order only)
+    if (!opt.wave_order) return;
     size_t pos[K_NKINDS] = {0, 0, 0, 0, 0, 0};
     for (int32_t w = 0; w < p.n_waves; ++w) {
         for (int k = 0; k < K_NKINDS; ++k) {

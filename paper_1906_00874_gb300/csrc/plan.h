@@ -96,6 +96,8 @@ struct PlanOptions {
     int32_t nrhs_max = 64;
     int32_t kmax_core = 96;  // largest stacked rank a rounded addition handles (at most 128: the
                              // truncation core keeps a column of its right factor in one warp)
+    bool wave_order = true;   // sort each kind's tasks by wave and list the wave launches (only the
+                              // wave schedule needs them; the data-flow schedule runs any order)
     int32_t inv_block = 1024; // the largest diagonal blocks of at most this order (at least the
                              // largest leaf) are inverted after the factorisation, and the solve
                              // applies the inverses as products; 0: plain block substitution
