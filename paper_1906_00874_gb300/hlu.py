@@ -62,14 +62,14 @@ class _PlanInfo(ctypes.Structure):
                [("plan_ms", ctypes.c_double)]
 
 
-def plan_info(problems, rank_cap=0, nrhs_max=0, inv_block=0):
+def plan_info(problems, rank_cap=0, nrhs_max=0, inv_block=0, schedule=SCHED_DATAFLOW):
     """Sizes of the task graphs hlu_create (one problem) or hlu_create_batch (a list) would build:
     validation and planning on the host only (hlu_plan_info_get / hlu_plan_info_batch)."""
     lib = load()
     many = isinstance(problems, (list, tuple))
     descs = [_describe(p.n, p.tree.perm, p.tree.begin, p.tree.size, p.tree.son0, p.tree.son1, p.row_cl, p.col_cl,
                        p.kind, p.rank, p.offset, p.data) for p in (problems if many else [problems])]
-    opts = _Opts(0, int(rank_cap), int(nrhs_max), 0, 0, 0.0, int(inv_block), 0)
+    opts = _Opts(0, int(rank_cap), int(nrhs_max), int(schedule), 0, 0.0, int(inv_block), 0)
     info = _PlanInfo()
     if many:
         trees = (_Tree * len(descs))(*[d[0] for d in descs])

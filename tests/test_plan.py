@@ -35,3 +35,28 @@ def test_batch_plans_only_its_problems_tasks(inv_block):
         assert batch[key] == sum(o[key] for o in one), key
     for key in ("factor_levels", "solve_levels"):
         assert batch[key] == max(o[key] for o in one), key
+
+
+def test_wave_order_does_not_change_the_graph(prob1280):
+    """The wave schedule sorts each kind's tasks by wave; the data-flow schedule keeps emission order.
+    Both plan the same graph."""
+    from paper_1906_00874_gb300.hlu import SCHED_WAVES, plan_info
+    a = plan_info(prob1280)
+    b = plan_info(prob1280, schedule=SCHED_WAVES)
+    for key in ("factor_tasks", "factor_edges", "factor_levels", "solve_tasks", "solve_levels", "matvec_tasks",
+                "inverse_blocks", "factor_elems"):
+        assert a[key] == b[key], key
+
+
+@pytest.mark.parametrize("case", [dict(r=3, leaf=32, eta=0.5, eps=1e-4, dim=1),
+                                  dict(r=3, leaf=32, eta=1.0, eps=1e-4, dim=2),
+                                  dict(r=3, leaf=32, eta=0.0, eps=1e-4)])
+def test_variants_plan(case):
+    """The d = 1, 2 problems and the dense-only structure (eta = 0: every leaf dense) plan on the
+    host, with inverse blocks for the solve."""
+    from paper_1906_00874_gb300.hlu import plan_info
+    p = build_problem(nrhs=1, **case)
+    info = plan_info(p)
+    assert info["factor_tasks"] > 0 and info["inverse_blocks"] >= 1
+    if case["eta"] == 0.0:
+        assert (p.kind == 0).all()
