@@ -163,6 +163,10 @@ typedef struct {
     int64_t inverse_blocks;  /* diagonal blocks inverted for the solve (hlu_opts.inv_block) */
     int64_t factor_elems;    /* elements of the factor arena */
     double plan_ms;          /* host time of the planning */
+    double factor_critical_us;  /* longest dependency path of the factorisation and of one solve
+                                   pass under fixed per-kind task latencies (model, microseconds;
+                                   the same weights order the executor's ready tasks) */
+    double solve_critical_us;
 } hlu_plan_info;
 
 int hlu_plan_info_get(const hlu_tree *tree, const hlu_blocks *blocks, const hlu_opts *opts, hlu_plan_info *out);

@@ -635,6 +635,8 @@ int plan_only(const hlu_tree *tree, const hlu_blocks *blocks, const hlu_opts *op
     out->inverse_blocks = (int64_t)pl.inv_cl.size();
     out->factor_elems = pl.f_elems;
     out->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    out->factor_critical_us = pl.fplan.critical_us;
+    out->solve_critical_us = pl.splan.critical_us;
     return HLU_OK;
 }
 

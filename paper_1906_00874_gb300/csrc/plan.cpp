@@ -831,8 +831,12 @@ void Planner::finalize_graph(Plan &p) const {
         }
         auto by_priority = [&](int32_t x, int32_t y) { return bl[x] > bl[y] || (bl[x] == bl[y] && x < y); };
         p.roots.clear();
+        p.critical_us = 0.0;
         for (int64_t g = 0; g < nt; ++g)
-            if (p.indeg[g] == 0) p.roots.push_back(int32_t(g));
+            if (p.indeg[g] == 0) {
+                p.roots.push_back(int32_t(g));
+                p.critical_us = std::max(p.critical_us, double(bl[g]));
+            }
         std::sort(p.roots.begin(), p.roots.end(), by_priority);
     }
     // launches: for each wave, one launch per kind present (wave order only)

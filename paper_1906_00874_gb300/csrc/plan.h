@@ -89,6 +89,7 @@ struct Plan {
     int64_t n_edges = 0;
     int64_t scratch_base = 0, scratch_elems = 0;
     int32_t max_kcap = 0;
+    double critical_us = 0.0;  // longest path of the graph under the per-kind task latencies (µs)
 };
 
 struct PlanOptions {

@@ -59,7 +59,8 @@ class _Opts(ctypes.Structure):
 class _PlanInfo(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in ("factor_tasks", "factor_edges", "factor_levels", "solve_tasks",
                                               "solve_levels", "matvec_tasks", "inverse_blocks", "factor_elems")] + \
-               [("plan_ms", ctypes.c_double)]
+               [("plan_ms", ctypes.c_double), ("factor_critical_us", ctypes.c_double),
+                ("solve_critical_us", ctypes.c_double)]
 
 
 def plan_info(problems, rank_cap=0, nrhs_max=0, inv_block=0, schedule=SCHED_DATAFLOW):

@@ -20,6 +20,8 @@ def test_inverse_blocks_shorten_the_solve(prob1280):
     small = plan_info(prob1280, inv_block=64)
     assert off["inverse_blocks"] == 0 and on["inverse_blocks"] >= 2 and small["inverse_blocks"] > on["inverse_blocks"]
     assert on["solve_levels"] < small["solve_levels"] < off["solve_levels"]
+    assert on["solve_critical_us"] < off["solve_critical_us"]
+    assert 0.0 < off["factor_critical_us"] <= on["factor_critical_us"]
     # the inverses are extra factorisation tasks; the factorisation itself is unchanged
     assert on["factor_tasks"] > off["factor_tasks"] and on["matvec_tasks"] == off["matvec_tasks"]
 
