@@ -32,7 +32,7 @@ def executor(tmp_path_factory):
     return lib
 
 
-def _run(lib, p, eps, inv_block, seed):
+def _run(lib, p, eps, inv_block, seed, inst=None):
     t = p.tree
     keep = []
 
@@ -51,7 +51,8 @@ def _run(lib, p, eps, inv_block, seed):
         ptr(p.offset, np.int64), ptr(p.data, np.float64), ctypes.c_int64(p.data.size), ctypes.c_double(eps),
         ctypes.c_int32(inv_block), ctypes.c_uint64(seed), out.ctypes.data_as(ctypes.c_void_p),
         off.ctypes.data_as(ctypes.c_void_p), rank.ctypes.data_as(ctypes.c_void_p), b.ctypes.data_as(ctypes.c_void_p),
-        ctypes.c_int32(b.shape[1]))
+        ctypes.c_int32(b.shape[1]), None if inst is None else ptr(inst, np.int32),
+        ctypes.c_int32(0 if inst is None else int(np.max(inst)) + 1))
     assert st == 0, st
     q = copy.copy(p)
     q.rank, q.offset, q.data = rank, off, out
@@ -73,3 +74,90 @@ def test_task_lists_reproduce_the_oracle(executor, prob1280, oracle1280, inv_blo
     assert np.max(np.abs(densify(build_hmatrix(q)) - densify(o.A))) <= 1e-12 * amax
     xo = lu_solve(o.A, p.b_perm())
     assert np.max(np.abs(x - xo)) <= 1e-12 * np.max(np.abs(xo))
+
+
+class _Forest:
+    """Several problems as one block-diagonal H-matrix: a balanced tree of count - 1 clusters above
+    the problems' roots (cluster 0 the root), then each problem's clusters, leaves and data shifted
+    (the layout hlu_create_batch builds)."""
+
+    def __init__(self, probs):
+        count = len(probs)
+        ncl = count - 1 + sum(p.tree.begin.size for p in probs)
+        self.n = sum(p.n for p in probs)
+        begin, size = np.zeros(ncl, np.int64), np.zeros(ncl, np.int64)
+        son0, son1 = -np.ones(ncl, np.int64), -np.ones(ncl, np.int64)
+        inst = -np.ones(ncl, np.int64)
+        perm, rows, cols, kinds, ranks, offs, datas = [], [], [], [], [], [], []
+        co, no, do, cl_off = count - 1, 0, 0, []
+        for i, p in enumerate(probs):
+            t = p.tree
+            k = t.begin.size
+            cl_off.append(co)
+            begin[co:co + k] = t.begin + no
+            size[co:co + k] = t.size
+            son0[co:co + k] = np.where(t.son0 >= 0, t.son0 + co, -1)
+            son1[co:co + k] = np.where(t.son1 >= 0, t.son1 + co, -1)
+            inst[co:co + k] = i
+            perm.append(t.perm + no)
+            rows.append(p.row_cl + co)
+            cols.append(p.col_cl + co)
+            kinds.append(p.kind)
+            ranks.append(p.rank)
+            offs.append(p.offset + do)
+            datas.append(p.data)
+            co, no, do = co + k, no + p.n, do + p.data.size
+        nxt = [0]
+
+        def make(i0, i1):
+            if i1 - i0 == 1:
+                return cl_off[i0]
+            v = nxt[0]
+            nxt[0] += 1
+            mid = (i0 + i1) // 2
+            a, b = make(i0, mid), make(mid, i1)
+            begin[v], size[v], son0[v], son1[v] = begin[a], size[a] + size[b], a, b
+            return v
+        make(0, count)
+
+        class T:
+            pass
+        self.tree = T()
+        self.tree.perm, self.tree.begin, self.tree.size = np.concatenate(perm), begin, size
+        self.tree.son0, self.tree.son1 = son0, son1
+        self.tree.n_clusters = ncl
+        self.row_cl, self.col_cl = np.concatenate(rows), np.concatenate(cols)
+        self.kind, self.rank = np.concatenate(kinds), np.concatenate(ranks)
+        self.offset, self.data = np.concatenate(offs), np.concatenate(datas)
+        self.n_leaves = self.row_cl.size
+        self.inst = inst
+        self._b = np.concatenate([p.b_perm() for p in probs], axis=0)
+        self.leaf0 = np.cumsum([0] + [p.n_leaves for p in probs])
+
+    def b_perm(self):
+        return self._b
+
+
+def test_batch_task_lists_equal_the_problems_own(executor):
+    """A batch's task lists, executed, give every problem exactly the factors and solve of its own
+    task lists (no task couples two problems), with and without the inverse blocks."""
+    from bem_inputs import build_problem
+    probs = [build_problem(3, 32, 2.0, 1e-4, nrhs=2), build_problem(2, 32, 2.0, 1e-4, nrhs=2, seed=1,
+                                                                    axes=(1.0, 0.6, 0.4)),
+             build_problem(2, 32, 2.0, 1e-4, nrhs=2, seed=2, axes=(1.0, 0.8, 0.5))]
+    f = _Forest(probs)
+    for inv_block in (-1, 0):
+        qb, xb = _run(executor, f, 1e-4, inv_block, 7, inst=f.inst)
+        row = 0
+        for i, p in enumerate(probs):
+            q, x = _run(executor, p, 1e-4, inv_block, 11 + i)
+            lo = f.leaf0[i]
+            assert np.array_equal(qb.rank[lo:lo + p.n_leaves], q.rank)
+            for l in range(p.n_leaves):
+                m, n = p.leaf_shape(l)
+                k = int(q.rank[l])
+                ln = m * n if p.kind[l] == 0 else (m + n) * k
+                a = qb.data[qb.offset[lo + l]:qb.offset[lo + l] + ln]
+                assert np.array_equal(a, q.data[q.offset[l]:q.offset[l] + ln]), (i, l)
+            assert np.array_equal(xb[row:row + p.n], x)
+            row += p.n
