@@ -672,7 +672,8 @@ def run_serve(args):
     rank, world, local = dist_env()
     w = dict(STREAMS[args.workload])
     stream, specs = stream_specs(**w)
-    with __import__("multiprocessing").get_context("spawn").Pool(min(len(specs), os.cpu_count() or 1)) as pool:
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(len(specs), os.cpu_count() or 1)) as pool:
         probs = pool.map(_build_one, specs)
     torch.cuda.set_device(local)
     build.build()
