@@ -120,3 +120,20 @@ def test_group_too_large_is_split_and_hopeless_problem_raises():
     s.submit(Request("big", big, np.ones((20, 1)), rid=5))
     with pytest.raises(HLUError):
         s.step(now=1.0)
+
+
+def test_new_problems_are_grouped_by_max_group():
+    """Problems arriving together are admitted as groups of at most max_group problems; each group
+    is one handle, factorised once, and every request is answered from its own problem's rows."""
+    probs = {k: _Prob(4 + k, k) for k in range(5)}
+    s = _server(max_group=2)
+    g = np.random.default_rng(1)
+    reqs = [Request(k, probs[k], g.standard_normal((probs[k].n, 1)), rid=k) for k in range(5)]
+    for r in reqs:
+        s.submit(r)
+    out = s.step(now=0.0)
+    assert len(out) == 5 and len(_FakeHLU.created) == 3
+    assert sorted(len(h.probs) for h in _FakeHLU.created) == [1, 2, 2]
+    assert s.stats["groups_created"] == 3 and s.stats["solves"] == 3
+    for r in reqs:
+        assert np.allclose(probs[r.key].A @ r.x, r.b, atol=1e-10)
