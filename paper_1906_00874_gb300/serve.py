@@ -106,7 +106,10 @@ class Server:
     # ------------------------------------------------------------ admission
     def _admit(self, problems: dict, keep: set):
         """Factorise the new problems as groups of at most max_group, evicting LRU groups (never one
-        in `keep`, which this step still solves on) to fit the budget."""
+        in `keep`, which this step still solves on) to fit the budget.  A group created here joins
+        `keep` at once and is stamped with the current tick, so a later group of the same step never
+        evicts it (its requests are still to be solved)."""
+        keep = set(keep)
         keys = list(problems)
         while keys:
             part, keys = keys[:self.max_group], keys[self.max_group:]
@@ -125,6 +128,8 @@ class Server:
                         part = part[:len(part) // 2]
                     else:
                         raise
+            g.last_used = self._tick
+            keep.update(g.keys)
             self.groups.append(g)
             for k in g.keys:
                 self.where[k] = g

@@ -137,3 +137,24 @@ def test_new_problems_are_grouped_by_max_group():
     assert s.stats["groups_created"] == 3 and s.stats["solves"] == 3
     for r in reqs:
         assert np.allclose(probs[r.key].A @ r.x, r.b, atol=1e-10)
+
+
+def test_groups_admitted_in_one_step_are_not_evicted_by_later_groups():
+    """Three new problems admitted one group each (max_group=1) under a budget for three problems, with
+    one idle old group resident: the old group is the one evicted, never a group created earlier in
+    the same step, and every request is answered."""
+    probs = {k: _Prob(10, k) for k in range(4)}   # 800 bytes each
+    s = _server(budget=2500, max_group=1)         # room for three problems
+    s.submit(Request("old", probs[3], np.ones((10, 1)), rid=0))
+    s.step(now=0.0)
+    assert s.resident("old")
+    g = np.random.default_rng(3)
+    reqs = [Request(k, probs[k], g.standard_normal((10, 1)), arrival=1.0, rid=1 + k) for k in range(3)]
+    for r in reqs:
+        s.submit(r)
+    out = s.step(now=1.0)
+    assert len(out) == 3
+    assert not s.resident("old") and all(s.resident(k) for k in range(3))
+    assert s.stats["evicted_groups"] == 1
+    for r in reqs:
+        assert np.allclose(probs[r.key].A @ r.x, r.b, atol=1e-10)
