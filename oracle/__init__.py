@@ -4,7 +4,7 @@ This package is the independent reference that the GPU library is checked
 against.  Only the tests, the package's smoke check and the benchmark's CPU
 baseline use it; the GPU library neither imports it nor shares any code with
 it.  It is written for clarity, not speed: numpy arrays, recursion over the
-block tree in the order of the paper's operation sequence (Sec. 3.1, O1.1-O5.5),
+block tree as the recursive 2 x 2 block LU of Sec. 3.1,
 and library primitives (matmul, QR, SVD, triangular solve) as single steps.
 
 Modules

@@ -1,17 +1,16 @@
-"""The H-LU factorisation as the paper states it (test infrastructure only).
+"""The H-LU factorisation of Sec. 3.1, written as the textbook recursive block
+LU (test infrastructure only).
 
-Recursion (Sec. 3.1, operation sequence O1.1-O5.5; the same five steps at
-every partitioned diagonal block):
-
-    lu(A):   A dense -> unpivoted LU in place                          (O1.1)
-             else    lu(A00); trsm_l(A00, A01); trsm_u(A00, A10);      (O1.1-O1.3)
-                     addmul(A11, -1, A10, A01); lu(A11)                (O1.4, O1.5)
-
-Triangular solves on a target X (Sec. 3.1 "Low-rank blocks", and the
-decomposition of O2 into O2.1-O2.6 in Sec. 5.2):
-    X low rank  -> solve only on its factor (U for L^{-1} X, V for X U^{-1});
-    X dense     -> forward / backward substitution through the H-structure of L or U;
-    X partitioned -> X0j := L00^{-1} X0j; X1j -= L10 X0j; X1j := L11^{-1} X1j.
+A partitioned diagonal block [[A00, A01], [A10, A11]] is factorised by the
+standard 2 x 2 block LU recursion: factor A00, solve the two off-diagonal
+panels with its triangular factors (L00^{-1} A01 and A10 U00^{-1}), subtract
+the Schur product L10 U01 from A11 and factor what remains.  A dense leaf is
+factorised by unpivoted LU.  The triangular solves recurse the same way
+through the structure of the solved block: a low-rank block is solved on one
+of its factors only (U for L^{-1} X, V for X U^{-1}), a dense block by
+substitution through the H-structure of the triangular factor, and a
+partitioned block by the block substitution first son, Schur update, second
+son.
 
 Products and additions (Sec. 3.1): a product with a low-rank factor stays
 factorised, Z (U V^T) = (Z U) V^T and (U V^T) Z = U (Z^T V)^T.  Adding to a
@@ -30,7 +29,10 @@ Readings where the paper is silent (each one is listed in the design notes):
   * a low-rank target C with two partitioned factors is split into a temporary
     2 x 2 block of low-rank sons (restrictions of its factors), the recursion
     continues on the sons, and the sons are merged back into C by one rounded
-    addition of their zero-padded factors;
+    addition of their zero-padded factors ("split" reading, the default);
+  * the same target under the plain definition (reading="plain"): the exact
+    product A B is formed densely, restricted to C, and C := T_eps(C + alpha A B)
+    is the truncated SVD of the exact dense sum, one truncation per target leaf;
   * the factor Sigma of a truncated block is kept in U (U <- Q_u X Sigma, V <- Q_v Y).
 """
 from __future__ import annotations
@@ -69,9 +71,12 @@ class HLUOracle:
     L (strictly below the diagonal, unit diagonal implied) and U (on and above)
     in the block structure of the input."""
 
-    def __init__(self, problem, eps, hm=None):
+    def __init__(self, problem, eps, hm=None, reading="split"):
+        if reading not in ("split", "plain"):
+            raise ValueError(f"unknown reading {reading!r}")
         self.problem = problem
         self.eps = float(eps)
+        self.reading = reading
         self.A = build_hmatrix(problem) if hm is None else hm
         self.c = Counters()
 
@@ -93,11 +98,11 @@ class HLUOracle:
         if b.kind != "part":
             raise ValueError("low-rank diagonal block")
         (a00, a01), (a10, a11) = b.sons
-        self.lu(a00)                     # O1.1
-        self.trsm_l(a00, a01)            # O1.2
-        self.trsm_u(a00, a10)            # O1.3
-        self.addmul(a11, -1.0, a10, a01)  # O1.4
-        self.lu(a11)                     # O1.5
+        self.lu(a00)
+        self.trsm_l(a00, a01)
+        self.trsm_u(a00, a10)
+        self.addmul(a11, -1.0, a10, a01)
+        self.lu(a11)
 
     # ------------------------------------------------ triangular solves
     def trsm_l(self, L, X):
@@ -109,11 +114,11 @@ class HLUOracle:
         else:
             (l00, _), (l10, l11) = L.sons
             for j in (0, 1):
-                self.trsm_l(l00, X.sons[0][j])                      # O2.1, O2.2
+                self.trsm_l(l00, X.sons[0][j])
             for j in (0, 1):
-                self.addmul(X.sons[1][j], -1.0, l10, X.sons[0][j])  # O2.3, O2.4
+                self.addmul(X.sons[1][j], -1.0, l10, X.sons[0][j])
             for j in (0, 1):
-                self.trsm_l(l11, X.sons[1][j])                      # O2.5, O2.6
+                self.trsm_l(l11, X.sons[1][j])
 
     def trsm_u(self, U, X):
         """X := X U^{-1}, U the upper part of the factored diagonal block."""
@@ -199,6 +204,14 @@ class HLUOracle:
 
     def addmul(self, C, alpha, A, B):
         """C := C + alpha A B with truncation at low-rank leaves of C."""
+        if self.reading == "plain" and A.kind == "part" and B.kind == "part":
+            # plain definition: the exact product, formed densely, is distributed over the
+            # leaves of C; each low-rank leaf is truncated once, by the SVD of its exact sum
+            P = densify(A) @ densify(B)
+            self.c.flops["gemm"] += 2.0 * A.m * A.n * B.n
+            self.c.events["prod_dense_exact"] += 1
+            self.add_dense_into(C, alpha, P)
+            return
         if A.kind == "part" and B.kind == "part":
             if C.kind == "part":
                 for i in (0, 1):
@@ -250,6 +263,19 @@ class HLUOracle:
         self.c.events["merge"] += 1
         return self.rounded_add(np.hstack(us), np.hstack(vs))
 
+    def add_dense_into(self, C, alpha, P):
+        """C := C + alpha P for a dense C.m x C.n array P: added exactly to dense leaves, and to a
+        low-rank leaf as T_eps(C + alpha P) of the dense sum."""
+        if C.kind == "part":
+            for row in C.sons:
+                for s in row:
+                    self.add_dense_into(s, alpha, P[s.r0 - C.r0:s.r0 - C.r0 + s.m, s.c0 - C.c0:s.c0 - C.c0 + s.n])
+        elif C.kind == "dense":
+            C.D += alpha * P
+            self.c.events["add_dense"] += 1
+        else:
+            C.U, C.V = self.truncate_dense(C.U @ C.V.T + alpha * P)
+
     def add_into(self, C, alpha, P, r, c):
         """Add alpha * (U V^T)[r:r+C.m, c:c+C.n] to C (exact product restricted to C)."""
         U, V = P
@@ -272,6 +298,18 @@ class HLUOracle:
         if sig.size == 0 or sig[0] == 0.0:
             return 0
         return int(np.count_nonzero(sig > self.eps * sig[0]))
+
+    def truncate_dense(self, X):
+        """T_eps of a dense block by its SVD (the plain definition of the rounded addition):
+        X = Q_1 diag(sigma) Q_2^T, keep the sigma_i > eps * sigma_1, U = Q_1 Sigma, V = Q_2."""
+        m, n = X.shape
+        x, sig, yt = np.linalg.svd(X, full_matrices=False)
+        k = self._keep(sig)
+        self.c.flops["svd"] += 21.0 * max(m, n) * min(m, n) ** 2
+        self.c.events["truncate_dense"] += 1
+        self.c.trunc_K[min(m, n)] += 1
+        self.c.trunc_rank[k] += 1
+        return x[:, :k] * sig[:k], yt[:k].T.copy()
 
     def rounded_add(self, Us, Vs):
         """Truncated SVD of Us Vs^T from the stacked factors (Sec. 3.1):

@@ -195,7 +195,9 @@ void Planner::collect_leaves(Block *b, std::vector<Block *> &out) {
 }
 
 // ----------------------------------------------------- the H-LU recursion
-// lu: O1.1-O1.5 at a partitioned diagonal block, getrf at a dense leaf.
+// lu: the 2 x 2 block LU recursion of Sec. 3.1 at a partitioned diagonal block (factor the leading
+// block, solve both off-diagonal panels with its factors, Schur update, factor the trailing block),
+// getrf at a dense leaf.
 void Planner::lu(Block *b) {
     if (b->kind == B_DENSE) {
         Store &s = st(b);
@@ -204,11 +206,11 @@ void Planner::lu(Block *b) {
         emit(K_GETRF, {}, {&D});
         return;
     }
-    lu(b->son[0][0]);                                     // O1.1
-    trsm_l(b->son[0][0], b->son[0][1]);                   // O1.2
-    trsm_u(b->son[0][0], b->son[1][0]);                   // O1.3
-    addmul(b->son[1][1], -1.0, b->son[1][0], b->son[0][1]);  // O1.4
-    lu(b->son[1][1]);                                     // O1.5
+    lu(b->son[0][0]);
+    trsm_l(b->son[0][0], b->son[0][1]);
+    trsm_u(b->son[0][0], b->son[1][0]);
+    addmul(b->son[1][1], -1.0, b->son[1][0], b->son[0][1]);
+    lu(b->son[1][1]);
 }
 
 void Planner::trsm_l(Block *L, Block *X) {
@@ -217,7 +219,7 @@ void Planner::trsm_l(Block *L, Block *X) {
         trsm_l_panel(L, viewU(X));  // L^{-1} U V^T: solve on the k columns of U
     } else if (X->kind == B_DENSE) {
         trsm_l_panel(L, viewD(X));
-    } else {  // O2.1-O2.6
+    } else {  // block substitution: first block row, Schur update, second block row
         for (int j = 0; j < 2; ++j) trsm_l(L->son[0][0], X->son[0][j]);
         for (int j = 0; j < 2; ++j) addmul(X->son[1][j], -1.0, L->son[1][0], X->son[0][j]);
         for (int j = 0; j < 2; ++j) trsm_l(L->son[1][1], X->son[1][j]);

@@ -207,3 +207,88 @@ def test_factor_quality_log_kernels(dim, eta):
     assert o.c.min_pivot > 0.0
     assert factor_error(A, o.A, p.n) <= 10 * p.eps
     assert np.all(solve_error(A, lu_solve(o.A, p.b_perm()), p.b_perm()) <= 10 * p.eps)
+
+
+# ------------------------------------------- the error estimator against dense norms
+def _dense_factor_error(A, F):
+    """||A_H - L U||_2 / ||A_H||_2 with every matrix formed densely (SVD-based 2-norms)."""
+    a = densify(A)
+    f = densify(F)
+    L = np.tril(f, -1) + np.eye(a.shape[0])
+    U = np.triu(f)
+    return np.linalg.norm(a - L @ U, 2) / np.linalg.norm(a, 2)
+
+
+def _estimator_cases():
+    # n = 320 with leaf 16 (low-rank blocks at eta = 2, eps 1e-3) and the n = 1280 sphere at eps 1e-4
+    return [build_problem(2, 16, 2.0, 1e-3, nrhs=1), build_problem(3, 32, 2.0, 1e-4, nrhs=1)]
+
+
+@pytest.fixture(scope="module")
+def estimator_cases():
+    out = []
+    for p in _estimator_cases():
+        A = build_hmatrix(p)
+        o = HLUOracle(p, p.eps).factor()
+        out.append((p, A, o))
+    return out
+
+
+def test_factor_error_estimator_equals_dense_two_norm(estimator_cases):
+    """The power-iteration E_fac (M = A_H - L U applied through the block structure, transposes by
+    the transposed traversal) agrees with the 2-norms of the densified matrices to 1e-2."""
+    for p, A, o in estimator_cases:
+        ref = _dense_factor_error(A, o.A)
+        assert ref > 1e-8  # a case with real truncation, not rounding noise
+        est = factor_error(A, o.A, p.n)
+        assert abs(est - ref) <= 1e-2 * ref, (p.n, est, ref)
+
+
+def test_planted_missing_unit_diagonal_in_apply_lower_is_caught(estimator_cases, monkeypatch):
+    import oracle.errors as oe
+    orig = oe.apply_lower
+    monkeypatch.setattr(oe, "apply_lower", lambda F, x: orig(F, x) - x)  # L without its unit diagonal
+    p, A, o = estimator_cases[1]
+    ref = _dense_factor_error(A, o.A)
+    assert abs(factor_error(A, o.A, p.n) - ref) > 1e-2 * ref
+
+
+def test_planted_untransposed_apply_upper_t_is_caught(estimator_cases, monkeypatch):
+    import oracle.errors as oe
+    monkeypatch.setattr(oe, "apply_upper_t", lambda F, x: oe.apply_upper(F, x))  # U instead of U^T
+    p, A, o = estimator_cases[1]
+    ref = _dense_factor_error(A, o.A)
+    assert abs(factor_error(A, o.A, p.n) - ref) > 1e-2 * ref
+
+
+# ----------------------------------------------- the plain definition of addmul
+def test_plain_reading_meets_the_bound_and_agrees_untruncated(prob1280):
+    """The plain definition (the exact product formed densely, one truncated SVD of the exact sum per
+    low-rank target leaf) and the split/merge reading both meet E_fac <= 10 eps at n = 1280, and at
+    eps -> 0 both reproduce the unique unpivoted LU, so they agree to rounding."""
+    p = prob1280
+    A = build_hmatrix(p)
+    res = {}
+    for reading in ("split", "plain"):
+        o = HLUOracle(p, p.eps, reading=reading).factor()
+        assert o.c.min_pivot > 0.0
+        assert _dense_factor_error(A, o.A) <= 10 * p.eps
+        assert factor_error(A, o.A, p.n) <= 10 * p.eps
+        res[reading] = densify(HLUOracle(p, 1e-15, reading=reading).factor().A)
+    scale = np.max(np.abs(densify(A)))
+    assert np.max(np.abs(res["split"] - res["plain"])) <= 1e-12 * scale
+    assert HLUOracle(p, p.eps, reading="plain").factor().c.events["prod_dense_exact"] > 0
+
+
+def test_dense_truncation_eckart_young(prob320):
+    """truncate_dense (the plain rounded addition) keeps exactly sigma_i > eps sigma_1 of a block with
+    known singular values and leaves ||X - T(X)||_2 = sigma_{k+1}."""
+    rng = np.random.default_rng(5)
+    sig = np.array([2.0, 0.3, 4e-4, 1e-4, 3e-7])
+    q1, _ = np.linalg.qr(rng.standard_normal((25, 5)))
+    q2, _ = np.linalg.qr(rng.standard_normal((18, 5)))
+    X = q1 @ np.diag(sig) @ q2.T
+    o = HLUOracle(prob320, 1e-4, reading="plain")
+    U, V = o.truncate_dense(X)
+    assert U.shape[1] == 3  # 1e-4 * 2 = 2e-4 < 4e-4 kept, 1e-4 dropped
+    assert np.isclose(np.linalg.norm(X - U @ V.T, 2), sig[3], rtol=1e-8)
