@@ -348,9 +348,11 @@ const char *hlu_strerror(int status);
  * device's memory).  The k x nrhs intermediate V^T x lives in one fixed array
  * of 65536 doubles (512 KiB) inside the library, held on every GPU that loads
  * the library until the process exits; k * nrhs above 65536 returns
- * HLU_EINVAL.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress) with the device current; make that first
- * call before any stream capture.  Every call uses the same array, so calls
+ * HLU_EINVAL.  Every call looks up that array's device address in the
+ * current device's context (cudaGetSymbolAddress, with the device current),
+ * so no address outlives a context; the first call on a device also loads the
+ * library's module there, so make that first call before any stream capture.
+ * k = 0 sets y to zero.  Every call uses the same array, so calls
  * that overlap on the GPU (e.g. on two streams at once) race with each other;
  * each call clears the part it accumulates into.  Returns after queueing the
  * work (HLU_OK), HLU_EINVAL for bad sizes or pointers, HLU_ECUDA if a launch

@@ -9,8 +9,6 @@
 // memory that belongs to the library and exists on every GPU that loads it.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "../../include/hlu.h"
 
 namespace {
@@ -23,48 +21,59 @@ constexpr int64_t kStaticScratchDoubles = int64_t(1) << 16;
 // cudaGetSymbolAddress on the device in question.
 static __device__ __align__(256) double g_lowrank_scratch[kStaticScratchDoubles];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mutex;
-double *g_scratch_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device, looked up once
-// per device (with that device current).  Returns nullptr on failure.
+// Device address of the scratch array in the current device's context, looked
+// up on every call (a cheap query once the module is loaded), so that an
+// address never outlives the context it belongs to (cudaDeviceReset, a new
+// primary context).  The first lookup on a device loads the library's module
+// there, which is why the first call on a device must come before any stream
+// capture.  Returns nullptr on failure.
 double *scratch_on_current_device() {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_lowrank_scratch) != cudaSuccess) {
-            cudaGetLastError();
-            return nullptr;
-        }
-        g_scratch_addr[dev] = static_cast<double *>(p);
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_lowrank_scratch) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
     }
-    return g_scratch_addr[dev];
+    return static_cast<double *>(p);
 }
 
-// T (k x nrhs, zeroed by the caller) += V[rows]^T x[rows] over this CTA's row range.
-__global__ void k_project_rows(const double *V, int64_t ldv, const double *x, int64_t ldx, int n, int k, int nrhs,
-                               int rows_per_cta, double *T) {
-    const int r0 = blockIdx.x * rows_per_cta;
-    const int r1 = min(n, r0 + rows_per_cta);
-    for (int p = threadIdx.x; p < k * nrhs; p += blockDim.x) {
-        const int a = p % k, j = p / k;
+// T (k x nrhs, zeroed before the launch) += V[rows]^T x[rows].  CTA (bx, by,
+// bz) takes rows [128 bx, 128 bx + 128), the 16 columns a0 = 16 by of V and the
+// 16 columns j0 = 16 bz of x: both 128 x 16 slices are staged in shared memory
+// by coalesced loads (consecutive threads read consecutive rows of a column),
+// then thread t forms output (a0 + t % 16, j0 + t / 16) over the staged rows
+// and adds it to T with one atomicAdd per CTA and output.
+constexpr int kRowsPerCta = 128, kTile = 16;
+
+__global__ void __launch_bounds__(256) k_project_rows(const double *V, int64_t ldv, const double *x, int64_t ldx,
+                                                      int n, int k, int nrhs, double *T) {
+    __shared__ double sV[kTile][kRowsPerCta + 1], sX[kTile][kRowsPerCta + 1];
+    const int64_t r0 = (int64_t)blockIdx.x * kRowsPerCta;
+    const int a0 = blockIdx.y * kTile, j0 = blockIdx.z * kTile;
+    const int64_t left = (int64_t)n - r0;
+    const int rows = left < kRowsPerCta ? (int)left : kRowsPerCta;
+    const int ta = min(kTile, k - a0), tj = min(kTile, nrhs - j0);
+    for (int e = threadIdx.x; e < kTile * kRowsPerCta; e += blockDim.x) {
+        const int c = e / kRowsPerCta, i = e - c * kRowsPerCta;
+        sV[c][i] = (c < ta && i < rows) ? V[r0 + i + (int64_t)(a0 + c) * ldv] : 0.0;
+        sX[c][i] = (c < tj && i < rows) ? x[r0 + i + (int64_t)(j0 + c) * ldx] : 0.0;
+    }
+    __syncthreads();
+    const int ca = threadIdx.x % kTile, cj = threadIdx.x / kTile;
+    if (ca < ta && cj < tj) {
         double s = 0.0;
-        for (int r = r0; r < r1; ++r) s += V[r + a * ldv] * x[r + j * ldx];
-        atomicAdd(T + p, s);
+        for (int i = 0; i < rows; ++i) s = fma(sV[ca][i], sX[cj][i], s);
+        atomicAdd(T + (a0 + ca) + (int64_t)(j0 + cj) * k, s);
     }
 }
 
-// y (m x nrhs) = U (m x k) T (k x nrhs)
+// y (m x nrhs) = U (m x k) T (k x nrhs); consecutive threads take consecutive rows (coalesced U and y).
 __global__ void k_apply_rows(const double *U, int64_t ldu, const double *T, int m, int k, int nrhs, double *y,
                              int64_t ldy) {
     const int64_t tot = (int64_t)m * nrhs;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
-        const int i = int(e % m), j = int(e / m);
+        const int64_t i = e % m, j = e / m;
         double s = 0.0;
-        for (int a = 0; a < k; ++a) s += U[i + a * ldu] * T[a + (int64_t)j * k];
+        for (int a = 0; a < k; ++a) s = fma(U[i + a * ldu], T[a + j * k], s);
         y[i + j * ldy] = s;
     }
 }
@@ -82,15 +91,15 @@ extern "C" int hlu_lowrank_apply_noalloc(int32_t m, int32_t n, int32_t k, int32_
     double *T = scratch_on_current_device();
     if (!T) return HLU_ECUDA;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
-    // the array keeps the previous call's values: the accumulator starts from zero
+    // the array keeps the previous call's values: the accumulator starts from zero (k = 0: y = 0 below)
     if (k > 0 && cudaMemsetAsync(T, 0, sizeof(double) * (size_t)k * nrhs, s) != cudaSuccess) return HLU_ECUDA;
     if (k > 0 && n > 0) {
-        const int rows_per_cta = 256;
-        const int grid = (n + rows_per_cta - 1) / rows_per_cta;
-        k_project_rows<<<grid, 256, 0, s>>>(V, ldv, x, ldx, n, k, nrhs, rows_per_cta, T);
+        const int64_t gx = ((int64_t)n + kRowsPerCta - 1) / kRowsPerCta;  // <= 2^24 for int32 n
+        const dim3 grid((unsigned)gx, (unsigned)((k + kTile - 1) / kTile), (unsigned)((nrhs + kTile - 1) / kTile));
+        k_project_rows<<<grid, 256, 0, s>>>(V, ldv, x, ldx, n, k, nrhs, T);
     }
     const int64_t tot = (int64_t)m * nrhs;
-    const int grid = (int)((tot + 255) / 256 < 1024 ? (tot + 255) / 256 : 1024);
+    const int grid = (int)((tot + 255) / 256 < 1216 ? (tot + 255) / 256 : 1216);
     k_apply_rows<<<grid, 256, 0, s>>>(U, ldu, T, m, k, nrhs, y, ldy);
     return cudaGetLastError() == cudaSuccess ? HLU_OK : HLU_ECUDA;
 }

@@ -86,3 +86,47 @@ def test_noalloc_rejects_sizes_beyond_its_array(lib):
     st = lib.hlu_lowrank_apply_noalloc(1, 1, 300, 300, U.data_ptr(), 1, U.data_ptr(), 1, U.data_ptr(), 1,
                                        U.data_ptr(), 1, None)
     assert st == 1  # HLU_EINVAL: 300 x 300 > 65536
+
+
+def _ref(U, V, x):
+    return U @ (V.T @ x)
+
+
+@pytest.mark.parametrize("m,n,k,nrhs", [(3001, 2755, 9, 3), (517, 4099, 256, 256), (300, 200, 1, 65536),
+                                        (64, 129, 16, 4096)])
+def test_noalloc_several_ctas_and_the_largest_accepted_size(lib, m, n, k, nrhs):
+    """Several CTAs over the rows (n not a multiple of 128), output tiles with ragged edges and
+    k * nrhs at the largest accepted size 65536 (last three cases), against U (V^T x) in
+    float64 on the host, on two calls in a row."""
+    import torch
+    from paper_1906_00874_gb300.hlu import to_device_panel
+    rng = np.random.default_rng(m + n + k)
+    for _ in range(2):
+        U = rng.standard_normal((m, k))
+        V = rng.standard_normal((n, k))
+        x = rng.standard_normal((n, nrhs))
+        xd = to_device_panel(x)
+        got = _call(lib, U, V, xd, m, n, k, nrhs, row0=0, ld=n)
+        ref = _ref(U, V, x)
+        assert np.max(np.abs(got - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
+        torch.cuda.synchronize()
+
+
+def test_noalloc_rank_zero_clears_y(lib):
+    import torch
+    m, n, nrhs = 50, 40, 3
+    x = torch.ones((nrhs, n), dtype=torch.float64, device="cuda").t()
+    y = torch.full((nrhs, m), 7.0, dtype=torch.float64, device="cuda").t()
+    st = lib.hlu_lowrank_apply_noalloc(m, n, 0, nrhs, None, m, None, n, x.data_ptr(), n, y.data_ptr(), m,
+                                       torch.cuda.current_stream().cuda_stream)
+    assert st == 0
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(y).item() == 0
+
+
+def test_noalloc_rejects_one_past_the_limit(lib):
+    import torch
+    U = torch.zeros((1, 1), dtype=torch.float64, device="cuda")
+    st = lib.hlu_lowrank_apply_noalloc(1, 1, 1, 65537, U.data_ptr(), 1, U.data_ptr(), 1, U.data_ptr(), 1,
+                                       U.data_ptr(), 1, None)
+    assert st == 1  # HLU_EINVAL: 65537 > 65536, rejected before any work is queued
