@@ -3,8 +3,11 @@
 
 One step = hlu_factor (the whole H-LU task graph) + hlu_solve_refined (solves
 with the factors, FP64 residual H-matvec, update, until every column reaches
-||b - A_H x|| <= 1e-10 ||b||).  The headline arm factorises in FP32 (FP64
-truncation cores); the FP64 arm is timed beside it.  Inputs (the H-matrix and
+||b - A_H x|| <= 1e-10 ||b||).  The headline arm stores and computes the
+factors in FP32 and runs the SVD of every truncation core (QR of R'^T and the
+one-sided Jacobi) in FP64; the FP64 arm and the variant with an FP32 Jacobi
+are timed beside it, and the factorisation error E_fac of every arm's factors
+is estimated on the device (hlu_factor_error).  Inputs (the H-matrix and
 b) are resident in HBM when the timed region starts; the working set (factor
 arena >= 4 GB) is far larger than the 129 MB L2, so no L2 flush is needed.
 
@@ -286,7 +289,7 @@ def run_native(args):
     import torch
 
     from bem_inputs import WORKLOADS, build_problem
-    from paper_1906_00874_gb300 import HLU_FP32, HLU_FP64, build
+    from paper_1906_00874_gb300 import HLU_FP32, HLU_FP32_CORE32, HLU_FP64, build
     from paper_1906_00874_gb300.hlu import probe_alu_peaks, to_device_panel
 
     rank, world, local = dist_env()
@@ -362,18 +365,27 @@ def run_native(args):
     h32.set_profiling(False)
     nprof = max(1, min(args.steps, 3))
 
-    # ---------------- FP64 arm
-    arm64 = None
-    if not args.no_fp64:
-        h64 = make_handle(p, HLU_FP64, sptr)
-        a64 = timed_arm(h64, max(2, args.steps // 3), max(1, args.warmup // 2))
-        f64, st64 = flops_per_step(h64)
-        n64 = len(a64["per_step_ms"])
-        t64 = max_over_ranks(a64["total_ms"]) / n64
-        arm64 = {"time_to_1e10_ms": t64, "gflops": f64 / (t64 * 1e-3) / 1e9, "ir_iters": a64["iters"][-1],
-                 "resid": a64["resid"][-1], "factor_model_gflop": st64["model_flops"] / 1e9,
-                 "max_rank": st64["max_rank"], "steps": n64}
-        h64.close()
+    # factorisation error of the headline factors (device power iteration, FP64 sums)
+    step(h32)
+    torch.cuda.synchronize()
+    efac32 = h32.factor_error()[0]
+
+    def side_arm(precision):
+        """A comparison arm on its own handle: time to 1e-10 over a few steps, E_fac of its factors."""
+        h = make_handle(p, precision, sptr)
+        a = timed_arm(h, max(2, args.steps // 3), max(1, args.warmup // 2))
+        fl, st = flops_per_step(h)
+        k = len(a["per_step_ms"])
+        t = max_over_ranks(a["total_ms"]) / k
+        out = {"time_to_1e10_ms": t, "gflops": fl / (t * 1e-3) / 1e9, "ir_iters": a["iters"][-1],
+               "resid": a["resid"][-1], "factor_model_gflop": st["model_flops"] / 1e9,
+               "max_rank": st["max_rank"], "steps": k, "efac": h.factor_error()[0]}
+        h.close()
+        return out
+
+    # ---------------- FP64 arm, and FP32 factors with an FP32 Jacobi in the truncation cores
+    arm64 = None if args.no_fp64 else side_arm(HLU_FP64)
+    core32 = side_arm(HLU_FP32_CORE32)
 
     # ---------------- end to end through the public API with host buffers
     e2e = e2e_arm(p, HLU_FP32, sptr, min(args.steps, 3), f32, args.solver, args.restart)
@@ -436,7 +448,8 @@ def run_native(args):
         line = {
             "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 truncation cores and residual)",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 factors; f64 SVD of every truncation core (QR of R'^T + Jacobi), f64 residual and solution",
             "data": "synthetic",
             "config": {"workload": f"{args.workload}: {GEOMETRY[w.get('dim', 3)]} n={p.n}, leaf {w['leaf']}, "
                                    f"eta={w['eta']:g}, eps={w['eps']:g}, {p.nrhs} rhs ~ N(0,1) seed 0, tol 1e-10",
@@ -448,7 +461,9 @@ def run_native(args):
             "rank_hist": rank_hist(st32),
             "resid": max(arm32["resid"]), "factor_model_gflop": st32["model_flops"] / 1e9,
             "step_model_gflop": f32 / 1e9, "max_rank": st32["max_rank"],
-            "fp64_arm": arm64, "e2e": e2e, "gpu_launches": arm32["launches"], "clocks": clk.summary(),
+            "efac_fp32": efac32, "efac_note": "||A_H - L U||_2 / ||A_H||_2 of each arm's factors, device power "
+                                                  "iteration (hlu_factor_error), bound 10 eps",
+            "fp64_arm": arm64, "fp32_core32_arm": core32, "e2e": e2e, "gpu_launches": arm32["launches"], "clocks": clk.summary(),
             "roofline": roof, "cpu_baseline": cpu,
             "alu_peaks_tflops": {"fp64": fp64_peak, "fp32": fp32_peak},
             "plan": {"tasks": st32["n_tasks"], "waves": st32["n_waves"], "launches_per_factor": st32["n_launches"]},
@@ -631,7 +646,7 @@ def run_batch(args):
             "metric": "batched H-LU: problems factorised and solved to 1e-10 per second", "value": B * world / (t32 * 1e-3),
             "unit": "problems/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t32,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 (FP64 truncation cores and residual)", "data": "synthetic",
+            "dtype": "f32 factors; f64 truncation-core SVD, residual and solution", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {B} ellipsoids, n in {ns}, leaf 32, eta 2, eps per problem "
                                    f"in {sorted(set(eps))}, 1 rhs each, tol 1e-10 per problem",
                        "n_total": int(sum(p.n for p in probs)), "leaves": int(sum(p.n_leaves for p in probs)),
@@ -725,7 +740,7 @@ def run_serve(args):
             "metric": "H-LU serving: requests solved to 1e-10 per second, p50/p99 latency", "unit": "requests/s",
             "value": len(stream) * len(runs) / mk, "n_gpus": world, "steps": len(runs), "warmup": args.warmup,
             "ms_per_step": mk / len(runs) * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 (FP64 truncation cores and residual)", "data": "synthetic",
+            "dtype": "f32 factors; f64 truncation-core SVD, residual and solution", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {len(stream)} requests, {len(specs)} distinct ellipsoid problems "
                                    f"(n in {sorted({p.n for p in probs})}), {int(100 * w['repeat'])}% repeats, "
                                    f"nrhs uniform in {list(w['nrhs'])} ({nrhs} in all), Poisson arrivals at 0.8x "

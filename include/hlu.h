@@ -43,9 +43,14 @@ enum {
 
 /* ------------------------------------------------------------- precision */
 enum {
-    HLU_FP64 = 0,      /* factors stored and computed in FP64 */
-    HLU_FP32 = 1       /* factors stored and computed in FP32 (cores of the truncation
-                          SVD stay FP64); the original matrix and hlu_matvec stay FP64 */
+    HLU_FP64 = 0,        /* factors stored and computed in FP64 */
+    HLU_FP32 = 1,        /* factors stored and computed in FP32, except the SVD of every
+                            truncation core (the QR of R'^T and the one-sided Jacobi of the
+                            rounded addition, Sec. 3.1), which runs in FP64 on the FP32 data;
+                            the original matrix, hlu_matvec and the refinement stay FP64 */
+    HLU_FP32_CORE32 = 2  /* as HLU_FP32, but the truncation cores' Jacobi SVD runs in FP32
+                            with the rotations accumulated (faster, singular values to FP32
+                            accuracy) */
 };
 
 /* Cluster tree (Sec. 2, Algorithm 1), host pointers, clusters numbered so that
@@ -92,7 +97,7 @@ enum {
 };
 
 typedef struct {
-    int32_t precision;   /* HLU_FP64 or HLU_FP32 */
+    int32_t precision;   /* HLU_FP64, HLU_FP32 or HLU_FP32_CORE32 */
     int32_t rank_cap;    /* capacity of every low-rank block: min(m, n, rank_cap); 0 -> 32 */
     int32_t nrhs_max;    /* widest right-hand-side panel one solve pass takes; 0 -> 64 */
     int32_t schedule;    /* HLU_SCHED_DATAFLOW (default) or HLU_SCHED_WAVES */
@@ -313,6 +318,19 @@ typedef struct {
 } hlu_stats;
 
 int hlu_get_stats(hlu_t h, hlu_stats *out);
+
+/* Factorisation error of the last hlu_factor: E_fac = ||A_H - L U||_2 / ||A_H||_2
+ * (the error measure of the H-LU with truncation, Sec. 3.1), both 2-norms
+ * estimated by power iteration on M^T M (M = A_H - L U, then M = A_H) with M
+ * applied leaf by leaf in FP64 (the factors promoted exactly from their
+ * precision), never formed: x = x0 / |x0|, then z = M^T M x, lambda = |z|,
+ * x = z / lambda until |lambda - lambda_old| <= rtol lambda or iters products,
+ * ||M||_2 ~ sqrt(lambda).  x0: DEVICE pointer to n FP64 values in the original
+ * order, not all zero (the same start vector for both norms).  *efac receives
+ * the ratio, *norm_a (may be NULL) the estimate of ||A_H||_2.  The first call
+ * allocates a leaf table and 6 n + 1 doubles of work space (HLU_ENOMEM beyond
+ * opts.mem_budget).  HLU_ESTATE before a successful hlu_factor. */
+int hlu_factor_error(hlu_t h, const double *x0_dev, int32_t iters, double rtol, double *efac, double *norm_a);
 
 /* Failure injection for tests of the timeout path (no counterpart in the paper):
  * with on != 0, the next data-flow factorisation of the handle gets one task

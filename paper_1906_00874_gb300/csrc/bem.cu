@@ -395,6 +395,7 @@ int hlu_bem_build(const hlu_bem_input *in, void *cuda_stream, hlu_bem_t *out) {
         a.err = d_err;
         a.eps = in->eps;
         a.kmax = cap;
+        a.core64 = 0;
         launch_kind<double>(K_RADD, d_radd, nullptr, d_pieces, 0, (int)radd.size(), cap, a, s);
     }
     if ((st = cu(cudaGetLastError()))) return fail(st);

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "../../include/hlu.h"
+#include "errest.cuh"
 #include "gmres.cuh"
 #include "kernels.cuh"
 #include "plan.h"
@@ -65,7 +66,8 @@ struct Pending {
 
 struct hlu_ctx {
     Planner pl;
-    int precision = HLU_FP64;
+    int precision = HLU_FP64;   // storage precision of the factors: HLU_FP64 or HLU_FP32
+    bool core64 = true;         // FP32 factors: SVD of each truncation core in FP64 (HLU_FP32_CORE32: FP32)
     int schedule = HLU_SCHED_DATAFLOW;
     unsigned long long timeout_ns = 10000000000ull;
     cudaStream_t stream = nullptr;
@@ -102,6 +104,10 @@ struct hlu_ctx {
     double *eps_inst = nullptr;          // per-instance tolerances of a batch (device), used when eps_each
     bool eps_each = false;
     double create_ms[2] = {0.0, 0.0};    // host time of hlu_create: validation + planning, device set-up
+    // factorisation-error estimate (hlu_factor_error): leaf table and work vectors, made on first use
+    ErrLeaf *err_leaves = nullptr;
+    double *err_work = nullptr;
+    double *err_host = nullptr;
 };
 
 namespace {
@@ -175,7 +181,8 @@ int upload_plan(hlu_ctx *h, const Plan &p, DevPlan &d, int kmax) {
     d.scratch_stride = (stride + 31) & ~int64_t(31);
     const int elem = h->precision == HLU_FP64 ? 8 : 4;
     const bool dbl = &d == &h->mp || h->precision == HLU_FP64;
-    d.smem = dataflow_smem_bytes(h->pl.max_leaf, dbl ? 8 : elem, std::min(kc, kSmemCore));
+    const bool c64 = !dbl && h->core64;
+    d.smem = dataflow_smem_bytes(h->pl.max_leaf, dbl ? 8 : elem, std::min(kc, kSmemCore), c64);
     d.workers = dbl ? dataflow_workers<double>(d.smem) : dataflow_workers<float>(d.smem);
     if (!p.radd.empty()) {
         const size_t bytes = size_t(d.workers) * d.scratch_stride * (dbl ? 8 : elem);
@@ -183,7 +190,7 @@ int upload_plan(hlu_ctx *h, const Plan &p, DevPlan &d, int kmax) {
         if ((st = dalloc(h, &sp, bytes))) return st;
         d.scratch = sp;
         if (kc > kSmemCore) {
-            d.core_stride = (int64_t)((radd_smem_bytes(kc, dbl ? 8 : elem) + 255) & ~size_t(255));
+            d.core_stride = (int64_t)((radd_smem_bytes(kc, dbl ? 8 : elem, c64) + 255) & ~size_t(255));
             char *cp = nullptr;
             if ((st = dalloc(h, &cp, size_t(d.workers) * d.core_stride))) return st;
             d.core_scratch = cp;
@@ -239,6 +246,7 @@ void run_plan(hlu_ctx *h, const DevPlan &d, void *arena, double *flops) {
     a.flops = flops;
     a.phase = (h->profiling && &d == &h->fp) ? h->busy + 32 : nullptr;
     a.kmax = h->pl.opt.kmax_core;
+    a.core64 = h->core64 ? 1 : 0;
     const bool dbl = arena == (void *)h->aarena || h->precision == HLU_FP64;
     if (h->schedule == HLU_SCHED_DATAFLOW && d.n_tasks > 0) {
         FlowArgs f;
@@ -445,6 +453,10 @@ static int create_impl(const hlu_tree *tree, const hlu_blocks *blocks, const hlu
         h->schedule = opts->schedule;
         if (opts->timeout_s > 0.0) h->timeout_ns = (unsigned long long)(opts->timeout_s * 1e9);
         if (opts->inv_block != 0) po.inv_block = opts->inv_block < 0 ? 0 : opts->inv_block;
+    }
+    if (h->precision == HLU_FP32_CORE32) {  // FP32 factors, FP32 Jacobi in the truncation cores
+        h->precision = HLU_FP32;
+        h->core64 = false;
     }
     if ((h->precision != HLU_FP64 && h->precision != HLU_FP32) ||
         (h->schedule != HLU_SCHED_DATAFLOW && h->schedule != HLU_SCHED_WAVES)) {
@@ -1082,6 +1094,57 @@ int hlu_get_stats(hlu_t h, hlu_stats *o) {
     return HLU_OK;
 }
 
+int hlu_factor_error(hlu_t h, const double *x0, int32_t iters, double rtol, double *efac, double *norm_a) {
+    if (!h || !x0 || !efac || iters < 1 || !(rtol >= 0.0)) return HLU_EINVAL;
+    if (!h->factored) return HLU_ESTATE;
+    Planner &pl = h->pl;
+    const int64_t n = pl.n;
+    int st = HLU_OK;
+    if (!h->err_leaves) {
+        std::vector<ErrLeaf> lv(pl.n_leaves);
+        for (int64_t l = 0; l < pl.n_leaves; ++l) {
+            const Store &a = pl.astore[l], &f = pl.fstore[l];
+            ErrLeaf &e = lv[l];
+            e.r0 = pl.cl[a.t].begin;
+            e.c0 = pl.cl[a.s].begin;
+            e.m = a.m;
+            e.n = a.n;
+            e.kind = a.kind == B_DENSE ? 0 : 1;
+            e.a_off = a.kind == B_DENSE ? a.D_off : a.U_off;
+            e.a_voff = a.kind == B_DENSE ? 0 : a.V_off;
+            e.ak = a.kind == B_DENSE ? 0 : a.krank;
+            e.f_off = f.kind == B_DENSE ? f.D_off : f.U_off;
+            e.f_voff = f.kind == B_DENSE ? 0 : f.V_off;
+            e.kslot = f.kind == B_DENSE ? -1 : f.kslot;
+            e.side = e.r0 == e.c0 ? 0 : e.r0 < e.c0 ? 1 : 2;
+        }
+        if ((st = upload(h, &h->err_leaves, lv))) return st;
+        if ((st = dalloc(h, &h->err_work, 6 * n + 1))) return st;
+        if ((st = cuda_status(cudaMallocHost(reinterpret_cast<void **>(&h->err_host), sizeof(double))))) return st;
+    }
+    ErrEstimator e;
+    e.n = n;
+    e.n_leaves = pl.n_leaves;
+    e.leaves = h->err_leaves;
+    e.aarena = h->aarena;
+    e.farena = h->farena;
+    e.kdyn = h->kdyn;
+    e.fp64 = h->precision == HLU_FP64;
+    e.stream = h->stream;
+    e.x0c = h->err_work;
+    e.x = e.x0c + n;
+    e.z = e.x + n;
+    e.w1 = e.z + n;
+    e.w2 = e.w1 + n;
+    e.w3 = e.w2 + n;
+    e.dacc = e.w3 + n;
+    e.host_acc = h->err_host;
+    st = e.run(x0, h->perm, iters, rtol, efac, norm_a);
+    h->kernels_launched += e.launched;
+    if (st == HLU_OK) st = read_error(h);
+    return st;
+}
+
 int hlu_inject_stall(hlu_t h, int32_t on) {
     if (!h) return HLU_EINVAL;
     h->inject_stall = on != 0;
@@ -1110,6 +1173,7 @@ void hlu_destroy(hlu_t h) {
     for (void *p : h->allocs) cudaFree(p);
     if (h->ir_host) cudaFreeHost(h->ir_host);
     if (h->gm_host) cudaFreeHost(h->gm_host);
+    if (h->err_host) cudaFreeHost(h->err_host);
     delete h;
 }
 

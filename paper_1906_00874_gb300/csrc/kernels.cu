@@ -1,8 +1,11 @@
 // Device kernels of the H-LU task graph (sm_103a).  One CTA (256 threads)
 // executes one task; the launch of a wave passes the slice of the task array
 // that belongs to it.  T is the storage type of the factors (double or
-// float); the Jacobi SVD inside every rounded addition is always computed in
-// double.
+// float).  With double factors every step is double.  With float factors the
+// stacked QRs and the pivoted QR of each truncation core are single precision,
+// and the SVD of the core (the QR of R'^T and the one-sided Jacobi) is double
+// (LaunchArgs::core64, the default) or single precision (the HLU_FP32_CORE32
+// variant).
 #include <cuda_runtime.h>
 #include <float.h>
 #include <math.h>
@@ -989,27 +992,47 @@ struct CoreBufs {
     R *W;                                   // single precision: accumulated rotations (in D's space)
     R *tauU, *tauV, *nrmU, *nrmV;
     int *order, *perm, *iflag;
+    // single-precision cores with the SVD in double (core64): R'^T and its QR, reflector scalars,
+    // column norms and 1 / sigma in double (C, tauC and isg of precision R are not used then)
+    double *C64, *tauC64, *cn64, *isg64;
 };
 
+// core64 applies to single-precision cores only: their SVD (QR of R'^T, Jacobi) runs in double.
 template <class R>
-__host__ __device__ inline size_t core_bytes(int mr, int nc, bool stacked) {
-    const size_t rc = mr < nc ? mr : nc, mx = mr > nc ? mr : nc;
-    const size_t nr = (size_t)mr * nc + mx * rc + nc + 3 * rc + (sizeof(R) == 8 ? 0 : rc * rc) +
-                      (stacked ? 2 * ((size_t)mr + nc) : 0);
-    return 8 * (rc * rc + rc) + sizeof(R) * nr + 4 * (rc + nc + 8);
+__host__ __device__ constexpr bool core_in_double(bool core64) {
+    return sizeof(R) != 8 && core64;
 }
 
 template <class R>
-__device__ CoreBufs<R> carve_core(unsigned char *base, int mr, int nc, bool stacked) {
+__host__ __device__ inline size_t core_bytes(int mr, int nc, bool stacked, bool core64) {
+    const size_t rc = mr < nc ? mr : nc, mx = mr > nc ? mr : nc;
+    const bool c64 = core_in_double<R>(core64);
+    const size_t nr = (size_t)mr * nc + (c64 ? 0 : mx * rc) + nc + 3 * rc + (sizeof(R) == 8 ? 0 : rc * rc) +
+                      (stacked ? 2 * ((size_t)mr + nc) : 0);
+    return 8 * (rc * rc + rc + (c64 ? mx * rc + 3 * rc : 0)) + sizeof(R) * nr + 4 * (rc + nc + 8);
+}
+
+template <class R>
+__device__ CoreBufs<R> carve_core(unsigned char *base, int mr, int nc, bool stacked, bool core64) {
     const int rc = min(mr, nc), mx = max(mr, nc);
+    const bool c64 = core_in_double<R>(core64);
     CoreBufs<R> b;
     b.D = reinterpret_cast<double *>(base);
     b.sig = b.D + rc * rc;
-    R *x = reinterpret_cast<R *>(b.sig + rc);
+    double *dx = b.sig + rc;
+    b.C64 = b.tauC64 = b.cn64 = b.isg64 = nullptr;
+    if (c64) {
+        b.tauC64 = dx;
+        b.cn64 = dx + rc;
+        b.isg64 = dx + 2 * rc;
+        b.C64 = dx + 3 * rc;
+        dx += 3 * rc + (size_t)mx * rc;
+    }
+    R *x = reinterpret_cast<R *>(dx);
     b.M = x;
     x += (size_t)mr * nc;
-    b.C = x;
-    x += (size_t)mx * rc;
+    b.C = c64 ? nullptr : x;
+    x += c64 ? 0 : (size_t)mx * rc;
     b.cn = x;
     x += nc;
     b.tauM = x;
@@ -1062,15 +1085,39 @@ __device__ CoreBufs<R> carve_core(unsigned char *base, int mr, int nc, bool stac
 template <class R>
 __device__ int core_finish(const CoreBufs<R> &b, int mr, int nc, int r, const TRadd &t, const LaunchArgs &a,
                            int pb, unsigned long long &ph) {
-    for (int e = threadIdx.x; e < nc * r; e += blockDim.x) {
-        const int c = e % nc, i = e / nc;
-        b.C[e] = c >= i ? b.M[i + (size_t)c * mr] : R(0);
+    const bool c64 = core_in_double<R>(a.core64 != 0);
+    if (c64) {  // R'^T promoted to double (exact), its QR and the Jacobi in double
+        for (int e = threadIdx.x; e < nc * r; e += blockDim.x) {
+            const int c = e % nc, i = e / nc;
+            b.C64[e] = c >= i ? (double)b.M[i + (size_t)c * mr] : 0.0;
+        }
+    } else {
+        for (int e = threadIdx.x; e < nc * r; e += blockDim.x) {
+            const int c = e % nc, i = e / nc;
+            b.C[e] = c >= i ? b.M[i + (size_t)c * mr] : R(0);
+        }
     }
     if (threadIdx.x == 0) b.iflag[2] = 0;  // [0]: Jacobi flag, [1]: pivoted-QR flag
     __syncthreads();
-    group_householder_qr<R>(b.C, nc, r, b.tauC, b.cn, 0, blockDim.x >> 5, 0);
+    if (c64)
+        group_householder_qr<double>(b.C64, nc, r, b.tauC64, b.cn64, 0, blockDim.x >> 5, 0);
+    else
+        group_householder_qr<R>(b.C, nc, r, b.tauC, b.cn, 0, blockDim.x >> 5, 0);
     int sweeps;
-    if constexpr (sizeof(R) == 8) {
+    if (c64) {
+        for (int e = threadIdx.x; e < r * r; e += blockDim.x) {  // X = R_C^T
+            const int i = e % r, j = e / r;
+            b.D[e] = i >= j ? b.C64[j + (size_t)i * nc] : 0.0;
+        }
+        __syncthreads();
+        sweeps = block_jacobi(b.D, r, r, b.iflag);
+        for (int j = threadIdx.x; j < r; j += blockDim.x) {
+            double s = 0.0;
+            for (int i = 0; i < r; ++i) s += b.D[i + (size_t)j * r] * b.D[i + (size_t)j * r];
+            b.sig[j] = sqrt(s);
+        }
+        for (int e = threadIdx.x; e < r * r; e += blockDim.x) b.B[e] = R(b.D[e]);  // for the left factor
+    } else if constexpr (sizeof(R) == 8) {
         for (int e = threadIdx.x; e < r * r; e += blockDim.x) {  // X = R_C^T
             const int i = e % r, j = e / r;
             b.D[e] = i >= j ? b.C[j + (size_t)i * nc] : 0.0;
@@ -1118,7 +1165,10 @@ __device__ int core_finish(const CoreBufs<R> &b, int mr, int nc, int r, const TR
         int rk = 0;
         for (int l = 0; l < r; ++l) rk += (b.sig[l] > b.sig[j]) || (b.sig[l] == b.sig[j] && l < j);
         b.order[rk] = j;
-        b.isg[j] = b.sig[j] > 0.0 ? R(1.0 / b.sig[j]) : R(0);
+        if (c64)
+            b.isg64[j] = b.sig[j] > 0.0 ? 1.0 / b.sig[j] : 0.0;
+        else
+            b.isg[j] = b.sig[j] > 0.0 ? R(1.0 / b.sig[j]) : R(0);
     }
     __syncthreads();
     const double s1 = r > 0 ? b.sig[b.order[0]] : 0.0;
@@ -1155,7 +1205,20 @@ __device__ int core_truncate(const CoreBufs<R> &b, int mr, int nc, double delta,
 // sigma^2 for the nc rows of the core (V of type T, leading dimension ldv).
 template <class R, class T>
 __device__ void core_write_v(const CoreBufs<R> &b, int mr, int nc, int r, int knew, T *V, int64_t ldv) {
-    if constexpr (sizeof(R) == 8) {
+    if (b.C64) {
+        // double SVD of a single-precision core: V[perm[i], c] = (R'^T B)[i, order[c]] / sigma^2 in
+        // double, R' exact as promoted; B from the double Jacobi, so Sigma^{-2} amplifies only
+        // double rounding (the product sigma_j u_j v_j^T stays at that level relative to sigma_1)
+        for (int e = threadIdx.x; e < nc * knew; e += blockDim.x) {
+            const int c = e % knew, i = e / knew;
+            const int j = b.order[c];
+            const int lmax = min(i, r - 1);
+            const double *bj = b.D + (size_t)j * r;
+            double sacc = 0.0;
+            for (int l = 0; l <= lmax; ++l) sacc = fma((double)b.M[l + (size_t)i * mr], bj[l], sacc);
+            V[b.perm[i] + (int64_t)c * ldv] = T((sacc * b.isg64[j]) * b.isg64[j]);
+        }
+    } else if constexpr (sizeof(R) == 8) {
         for (int e = threadIdx.x; e < nc * knew; e += blockDim.x) {
             const int c = e % knew, i = e / knew;
             const int j = b.order[c];
@@ -1206,17 +1269,25 @@ __device__ void core_write_v(const CoreBufs<R> &b, int mr, int nc, int r, int kn
     }
 }
 
-// Left factor of the truncated core: b.C (mr x knew) := Q_M [B_sel; 0].
+// Output buffer of core_form_u: the buffer of R'^T in precision R, or its double copy (no longer
+// read once the Jacobi has started), which holds at least mr x knew values of precision R.
+template <class R>
+__device__ __forceinline__ R *core_out(const CoreBufs<R> &b) {
+    return b.C ? b.C : reinterpret_cast<R *>(b.C64);
+}
+
+// Left factor of the truncated core: core_out(b) (mr x knew) := Q_M [B_sel; 0].
 // Ends with a barrier.
 template <class R>
 __device__ void core_form_u(const CoreBufs<R> &b, int mr, int r, int knew) {
+    R *C = core_out(b);
     for (int e = threadIdx.x; e < mr * knew; e += blockDim.x) {
         const int i = e % mr, c = e / mr;
-        b.C[e] = i < r ? b.B[i + (size_t)b.order[c] * r] : R(0);
+        C[e] = i < r ? b.B[i + (size_t)b.order[c] * r] : R(0);
     }
     __syncthreads();
     for (int c = threadIdx.x >> 5; c < knew; c += blockDim.x >> 5)
-        warp_apply_q<R>(b.M, mr, r, b.tauM, b.C + (size_t)c * mr);
+        warp_apply_q<R>(b.M, mr, r, b.tauM, C + (size_t)c * mr);
     __syncthreads();
 }
 
@@ -1242,7 +1313,7 @@ __device__ void core_form_u(const CoreBufs<R> &b, int mr, int r, int knew) {
 // by the same core steps, which is the same T_eps of the same sum without the
 // two stacked QRs.  Shared memory is carved in two steps: X and the pivoted-QR
 // bookkeeping, then, with the rank r of the pivoted QR known, the rank-r
-// buffers; when those exceed kDensePost bytes the task falls back to the
+// buffers; when those exceed dense_post_cap bytes the task falls back to the
 // stacked route (nothing outside shared memory has been written yet).  Every
 // launch provides at least radd_dense_floor bytes, so the route depends on the
 // task alone.
@@ -1251,7 +1322,9 @@ __host__ __device__ constexpr int dense_max() {
     return 4096;
 }
 
-constexpr size_t kDensePost = 24576;
+// Rank-r budget of the dense route: larger when the core SVD of single-precision factors runs in
+// double (its R'^T copy and QR are double).
+__host__ __device__ constexpr size_t dense_post_cap(bool c64) { return c64 ? 40960 : 24576; }
 
 template <class R>
 __host__ __device__ inline size_t dense_pre_bytes(int m, int n) {
@@ -1260,8 +1333,10 @@ __host__ __device__ inline size_t dense_pre_bytes(int m, int n) {
 }
 
 template <class R>
-__host__ __device__ inline size_t dense_post_bytes(int m, int n, int r) {
+__host__ __device__ inline size_t dense_post_bytes(int m, int n, int r, bool c64) {
     const size_t mx = m > n ? m : n;
+    if (c64)  // D, sig, tauC64, cn64, isg64, C64 (double); B (precision R); order
+        return 8 * ((size_t)r * r + 4 * (size_t)r + mx * r) + sizeof(R) * (size_t)r * r + sizeof(int) * (size_t)r;
     return 8 * ((size_t)r * r + r) + sizeof(R) * (mx * r + 2 * (size_t)r + (sizeof(R) == 8 ? 0 : (size_t)r * r)) +
            sizeof(int) * (size_t)r;
 }
@@ -1301,10 +1376,22 @@ __device__ bool radd_small(const TRadd &t, const Piece *pieces, const LaunchArgs
     ph = phase_mark(a, 0, ph);
     const int r = block_qrcp<T>(b.M, m, n, b.tauM, b.cn, b.perm, delta, b.iflag);
     ph = phase_mark(a, 2, ph);
-    if (dense_post_bytes<T>(m, n, r) > kDensePost) return false;  // uniform over the CTA
+    const bool c64 = core_in_double<T>(a.core64 != 0);
+    if (dense_post_bytes<T>(m, n, r, c64) > dense_post_cap(c64)) return false;  // uniform over the CTA
     // rank-r buffers after X and the pivot bookkeeping
     b.D = reinterpret_cast<double *>(smem_raw + dense_pre_bytes<T>(m, n));
     b.sig = b.D + r * r;
+    b.C64 = b.tauC64 = b.cn64 = b.isg64 = nullptr;
+    if (c64) {
+        b.tauC64 = b.sig + r;
+        b.cn64 = b.tauC64 + r;
+        b.isg64 = b.cn64 + r;
+        b.C64 = b.isg64 + r;
+        b.C = b.tauC = b.isg = nullptr;
+        b.W = nullptr;
+        b.B = reinterpret_cast<T *>(b.C64 + (size_t)max(m, n) * r);
+        b.order = reinterpret_cast<int *>(b.B + r * r);
+    } else {
     b.C = reinterpret_cast<T *>(b.sig + r);
     b.tauC = b.C + (size_t)max(m, n) * r;
     b.isg = b.tauC + r;
@@ -1316,6 +1403,7 @@ __device__ bool radd_small(const TRadd &t, const Piece *pieces, const LaunchArgs
         b.B = b.isg + r;
         b.W = reinterpret_cast<T *>(b.D);  // r x r floats in the r x r doubles of D
         b.order = reinterpret_cast<int *>(b.B + r * r);
+    }
     }
     const int knew = core_finish<T>(b, m, n, r, t, a, 0, ph);
     // the target's own factors were read above; every row of V is covered by P
@@ -1371,7 +1459,8 @@ __device__ void dev_radd(const TRadd &t, const Piece *pieces, const LaunchArgs &
         return;
     }
     const int ku = min(m, K), kv = min(n, K);
-    const size_t cbytes = (core_bytes<T>(ku, kv, true) + 15) & ~size_t(15);
+    const bool c64 = core_in_double<T>(a.core64 != 0);
+    const size_t cbytes = (core_bytes<T>(ku, kv, true, c64) + 15) & ~size_t(15);
     const bool core_in_smem = cbytes <= smem_bytes;
     const size_t panel_bytes = (size_t)(m + n) * K * sizeof(T);
     T *WU = core_in_smem && cbytes + panel_bytes <= smem_bytes ? reinterpret_cast<T *>(smem_raw + cbytes) : scratch;
@@ -1397,7 +1486,7 @@ __device__ void dev_radd(const TRadd &t, const Piece *pieces, const LaunchArgs &
     }
     __syncthreads();
     ph = phase_mark(a, 8, ph);
-    const CoreBufs<T> b = carve_core<T>(core_in_smem ? smem_raw : core_scratch, ku, kv, true);
+    const CoreBufs<T> b = carve_core<T>(core_in_smem ? smem_raw : core_scratch, ku, kv, true, c64);
     // ---- QR of both stacks (one half of the CTA each), core M = R_u R_v^T
     const int half = (blockDim.x >> 5) / 2;
     if ((int)(threadIdx.x >> 5) < half)
@@ -1458,9 +1547,10 @@ __device__ void dev_radd(const TRadd &t, const Piece *pieces, const LaunchArgs &
         }
         // ---- U = Q_u [Q_M [B_sel; 0]; 0]
         core_form_u<T>(b, ku, r, knew);
+        const T *Cu = core_out(b);
         for (int e = threadIdx.x; e < m * knew; e += blockDim.x) {
             const int i = e % m, c = e / m;
-            Uc[e] = i < ku ? b.C[i + (size_t)c * ku] : T(0);
+            Uc[e] = i < ku ? Cu[i + (size_t)c * ku] : T(0);
         }
         __syncthreads();
         for (int c = threadIdx.x >> 5; c < 2 * knew; c += blockDim.x >> 5) {  // U and V columns together
@@ -1480,18 +1570,17 @@ __device__ void dev_radd(const TRadd &t, const Piece *pieces, const LaunchArgs &
 // Shared memory that every rounded-addition launch provides: the dense route's
 // worst case over m, n <= 128, m n <= dense_max, plus its rank-r budget.
 template <class R>
-size_t radd_dense_floor() {
-    static size_t s = 0;
-    if (s == 0)
-        for (int m = 1; m <= 128; ++m)
-            for (int n = 1; n <= 128 && m * n <= dense_max<R>(); ++n)
-                s = std::max(s, dense_pre_bytes<R>(m, n) + kDensePost);
+size_t radd_dense_floor(bool c64) {
+    size_t s = 0;
+    for (int m = 1; m <= 128; ++m)
+        for (int n = 1; n <= 128 && m * n <= dense_max<R>(); ++n)
+            s = std::max(s, dense_pre_bytes<R>(m, n) + dense_post_cap(c64));
     return s;
 }
 
-size_t radd_smem_bytes(int kc, int elem) {
-    if (elem == 8) return std::max(core_bytes<double>(kc, kc, true), radd_dense_floor<double>());
-    return std::max(core_bytes<float>(kc, kc, true), radd_dense_floor<float>());
+size_t radd_smem_bytes(int kc, int elem, bool core64) {
+    if (elem == 8) return std::max(core_bytes<double>(kc, kc, true, false), radd_dense_floor<double>(false));
+    return std::max(core_bytes<float>(kc, kc, true, core64), radd_dense_floor<float>(core64));
 }
 
 // ------------------------------------------------------------ wave kernels
@@ -1807,7 +1896,7 @@ void launch_kind(int kind, const void *tasks, const Term *terms, const Piece *pi
         case K_RADD: {
             // includes the dense route's worst case (radd_dense_floor), so that the
             // route a task takes does not depend on the schedule
-            const size_t smem = radd_smem_bytes(aux, sizeof(T));
+            const size_t smem = radd_smem_bytes(aux, sizeof(T), a.core64 != 0);
             k_radd<T><<<count, kThreads, smem, s>>>(reinterpret_cast<const TRadd *>(tasks) + start, pieces, a, aux,
                                                     smem);
             break;
@@ -1844,12 +1933,12 @@ bool set_kernel_attributes() {
     return ok;
 }
 
-size_t dataflow_smem_bytes(int max_leaf, int elem, int kc) {
+size_t dataflow_smem_bytes(int max_leaf, int elem, int kc, bool core64) {
     size_t s = getrf_smem_bytes(max_leaf, elem);
     s = std::max(s, trsm_smem_bytes(max_leaf, elem));
     s = std::max(s, project_smem_bytes(elem));
     s = std::max(s, accum_smem_bytes(elem));
-    s = std::max(s, radd_smem_bytes(kc, elem));
+    s = std::max(s, radd_smem_bytes(kc, elem, core64));
     return s;
 }
 

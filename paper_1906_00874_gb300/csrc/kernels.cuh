@@ -19,6 +19,7 @@ struct LaunchArgs {
     double *flops;      // model flops per task kind (K_NKINDS doubles), accumulated
     unsigned long long *phase;  // when profiling: rounded-addition phase counters (16), else null
     int32_t kmax;       // largest stacked rank the core buffers hold
+    int32_t core64;     // single-precision factors: SVD of each truncation core in double (1) or single (0)
 };
 
 template <class T>
@@ -58,7 +59,7 @@ struct FlowArgs {
                                // [16 + b] / [24 + b] the same for rounded additions of size class b; else null
 };
 
-size_t dataflow_smem_bytes(int max_leaf, int elem, int kc);
+size_t dataflow_smem_bytes(int max_leaf, int elem, int kc, bool core64);
 template <class T>
 int dataflow_workers(size_t smem);
 template <class T>
@@ -86,8 +87,9 @@ void launch_residual(const double *b, const double *ax, double *r, int64_t n, in
                      double *bn2, cudaStream_t s);
 
 // Shared memory of a rounded addition whose stacked rank is at most kcap, with
-// factors of elem bytes (also the dense route's worst case).
-size_t radd_smem_bytes(int kcap, int elem);
+// factors of elem bytes (also the dense route's worst case); core64: single-precision
+// factors whose truncation cores take their SVD in double.
+size_t radd_smem_bytes(int kcap, int elem, bool core64);
 size_t getrf_smem_bytes(int max_leaf, int elem);
 
 }  // namespace hlu

@@ -15,7 +15,8 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libhlu.so")
 
 HLU_FP64 = 0
-HLU_FP32 = 1
+HLU_FP32 = 1          # FP32 factors, FP64 SVD of every truncation core
+HLU_FP32_CORE32 = 2   # FP32 factors, FP32 Jacobi in the truncation cores
 SCHED_DATAFLOW = 0
 SCHED_WAVES = 1
 
@@ -27,7 +28,8 @@ EXPORTS = ("hlu_create", "hlu_factor", "hlu_solve", "hlu_matvec", "hlu_solve_ref
            "hlu_get_factors", "hlu_get_stats", "hlu_set_profiling", "hlu_destroy", "hlu_strerror",
            "hlu_last_error_detail", "hlu_last_cuda_error", "hlu_probe_alu_peaks", "hlu_inject_stall",
            "hlu_create_batch", "hlu_factor_batch", "hlu_batch_count", "hlu_bem_build", "hlu_bem_result",
-           "hlu_bem_copy_data", "hlu_create_bem", "hlu_bem_destroy", "hlu_plan_info_get", "hlu_plan_info_batch")
+           "hlu_bem_copy_data", "hlu_create_bem", "hlu_bem_destroy", "hlu_plan_info_get", "hlu_plan_info_batch",
+           "hlu_factor_error", "hlu_lowrank_apply_noalloc")
 KINDS = ("getrf", "trsm", "project", "accum", "radd", "split", "dataflow_factor", "dataflow_solve",
          "dataflow_matvec")
 
@@ -161,6 +163,7 @@ def load(path=LIB_PATH):
     lib.hlu_matvec.argtypes = [vp, vp, vp, i32, i64]
     lib.hlu_solve_refined.argtypes = [vp, vp, vp, i32, i64, dbl, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl)]
     lib.hlu_solve_gmres.argtypes = [vp, vp, vp, i32, i64, dbl, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl)]
+    lib.hlu_factor_error.argtypes = [vp, vp, i32, dbl, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
     lib.hlu_set_profiling.argtypes = [vp, i32]
     lib.hlu_inject_stall.argtypes = [vp, i32]
     lib.hlu_probe_alu_peaks.argtypes = [ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
@@ -357,6 +360,21 @@ class HLU:
                                            float(tol), int(restart), int(max_iter), ctypes.byref(it),
                                            ctypes.byref(res)), "hlu_solve_gmres")
         return it.value, res.value
+
+    def factor_error(self, x0=None, seed=1, iters=30, rtol=1e-3):
+        """E_fac = ||A_H - L U||_2 / ||A_H||_2 of the last factorisation, estimated on the device
+        (hlu_factor_error); x0: start vector in the original order (CUDA float64, n values), by
+        default N(0,1) from `seed`.  Returns (E_fac, estimate of ||A_H||_2)."""
+        import torch
+        if x0 is None:
+            x0 = torch.from_numpy(np.random.default_rng(seed).standard_normal(self.n)).to("cuda")
+        ptr, nrhs, _ = _dev_ptr_and_ld(x0, self.n, "x0")
+        if nrhs != 1:
+            raise ValueError("x0 must be one vector of n values")
+        e, a = ctypes.c_double(), ctypes.c_double()
+        self._check(load().hlu_factor_error(self._h, ctypes.c_void_p(ptr), int(iters), float(rtol), ctypes.byref(e),
+                                            ctypes.byref(a)), "hlu_factor_error")
+        return e.value, a.value
 
     def inject_stall(self, on=True):
         """Test hook: the next factorisation stalls on one task until the wait limit (HLU_ETIMEOUT)."""

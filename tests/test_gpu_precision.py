@@ -1,0 +1,145 @@
+"""GPU tests of the precision forms and of the device error estimate, against the CPU oracle.
+
+* eps = 1e-6 (the tolerance of the n = 81920 and half of the batched and serving workloads): FP64
+  factors equal the oracle's on spheres and ellipsoids at n = 1280 and 5120, with the tolerance rule
+  of the parity tests (rounding-level agreement when every truncation rank agrees, else 10 eps).
+* FP32 factors, with the truncation cores' SVD in FP64 (HLU_FP32) and in FP32 (HLU_FP32_CORE32):
+  their E_fac = ||A_H - L U||_2 / ||A_H||_2 measured by the oracle meets 10 eps, the error of the
+  densified factors against the FP64 oracle's is stated, and FP64 refinement reaches 1e-10.
+* The device estimate hlu_factor_error equals the oracle's power iteration on the same factors
+  (same start vector, same stopping rule) and the dense 2-norms at n = 1280.
+* The device model flop count of a factorisation equals the oracle's count of the same operations.
+"""
+import numpy as np
+import pytest
+
+from bem_inputs import build_problem
+from oracle import HLUOracle, build_hmatrix, densify
+from oracle.errors import factor_error, lu_solve, solve_error
+
+from gpu_helpers import factors_as_problem, gpu_factor, rank_agreement
+
+pytestmark = pytest.mark.gpu
+
+ELLIPSOID = (1.0, 0.7, 0.5)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    from paper_1906_00874_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def _dev(a):
+    from paper_1906_00874_gb300.hlu import to_device_panel
+    return to_device_panel(a)
+
+
+def _factor_diff(p, q, o):
+    amax = np.max(np.abs(densify(build_hmatrix(p))))
+    return np.max(np.abs(densify(build_hmatrix(q)) - densify(o.A))) / amax
+
+
+@pytest.mark.parametrize("r,axes", [(3, None), (3, ELLIPSOID), (4, None), (4, ELLIPSOID)])
+def test_factor_parity_eps_1e6(r, axes):
+    p = build_problem(r, 32, 2.0, 1e-6, nrhs=1, axes=axes)
+    o = HLUOracle(p, p.eps).factor()
+    h = gpu_factor(p)
+    q = factors_as_problem(p, h)
+    same, tot = rank_agreement(o, q)
+    err = _factor_diff(p, q, o)
+    if same == tot:
+        assert err <= 1e-10, err
+    else:
+        assert tot - same <= max(2, tot // 500), (same, tot)
+        assert err <= 10 * p.eps, err
+    A = build_hmatrix(p)
+    assert factor_error(A, build_hmatrix(q), p.n) <= 10 * p.eps
+    b = _dev(p.b)
+    h.solve(b)
+    xo = lu_solve(o.A, p.b_perm())
+    e_gpu = solve_error(A, b.cpu().numpy()[p.tree.perm], p.b_perm())
+    assert np.all(e_gpu <= 2 * solve_error(A, xo, p.b_perm()))
+    h.close()
+
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-6])
+@pytest.mark.parametrize("core", ["fp64", "fp32"])
+def test_fp32_factors_against_fp64_oracle(eps, core):
+    """FP32 factors on the n = 1280 ellipsoid: E_fac (oracle) <= 10 eps, the densified factors stay
+    within 1e-4 max|A_H| of the FP64 oracle's (FP32 rounding through the recursion, plus truncation
+    flips bounded by eps), and refinement reaches 1e-10 (checked with the oracle's H-matvec)."""
+    import torch
+    from paper_1906_00874_gb300 import HLU, HLU_FP32, HLU_FP32_CORE32
+    p = build_problem(3, 32, 2.0, eps, nrhs=2, axes=ELLIPSOID)
+    o = HLUOracle(p, p.eps).factor()
+    h = HLU.from_problem(p, precision=HLU_FP32 if core == "fp64" else HLU_FP32_CORE32)
+    h.factor(p.eps)
+    q = factors_as_problem(p, h)
+    A = build_hmatrix(p)
+    efac = factor_error(A, build_hmatrix(q), p.n)
+    assert efac <= 10 * p.eps, efac
+    assert _factor_diff(p, q, o) <= 1e-4
+    b = _dev(p.b)
+    x = torch.zeros_like(b)
+    it, res = h.solve_refined(b, x, tol=1e-10, max_iter=20)
+    assert res <= 1e-10 and it <= 8
+    xr = x.cpu().numpy()[p.tree.perm]
+    assert np.all(solve_error(A, xr, p.b_perm()) <= 2e-10)
+    h.close()
+
+
+def _oracle_start(p, seed=1):
+    """The oracle's start vector (cluster order) in the original order the C ABI takes."""
+    xc = np.random.default_rng(seed).standard_normal(p.n)
+    x = np.empty_like(xc)
+    x[p.tree.perm] = xc
+    return x
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_device_factor_error_equals_oracle_estimate(precision):
+    from paper_1906_00874_gb300 import HLU, HLU_FP32, HLU_FP64
+    p = build_problem(3, 32, 2.0, 1e-4, nrhs=1)
+    h = HLU.from_problem(p, precision=HLU_FP64 if precision == "fp64" else HLU_FP32)
+    h.factor(p.eps)
+    dev, norm_a = h.factor_error(x0=_dev(_oracle_start(p)))
+    q = factors_as_problem(p, h)
+    A = build_hmatrix(p)
+    F = build_hmatrix(q)
+    ref = factor_error(A, F, p.n)
+    assert abs(dev - ref) <= 1e-3 * ref, (dev, ref)
+    # and against the dense 2-norms of the same matrices
+    a = densify(A)
+    f = densify(F)
+    dense = np.linalg.norm(a - (np.tril(f, -1) + np.eye(p.n)) @ np.triu(f), 2) / np.linalg.norm(a, 2)
+    assert abs(dev - dense) <= 1e-2 * dense, (dev, dense)
+    assert abs(norm_a - np.linalg.norm(a, 2)) <= 1e-2 * np.linalg.norm(a, 2)
+    h.close()
+
+
+def test_device_factor_error_state():
+    from paper_1906_00874_gb300 import HLU, HLUError
+    p = build_problem(3, 32, 2.0, 1e-4, nrhs=1)
+    h = HLU.from_problem(p)
+    with pytest.raises(HLUError) as e:
+        h.factor_error()
+    assert e.value.status == 3  # before hlu_factor
+    h.close()
+
+
+def test_model_flops_equal_the_oracle_count():
+    """The device counts the model flops of the operations it runs with the oracle's formulas; on
+    the same problem (FP64, every truncation rank equal) the two totals agree."""
+    p = build_problem(3, 32, 2.0, 1e-4, nrhs=1)
+    o = HLUOracle(p, p.eps).factor()
+    h = gpu_factor(p)
+    q = factors_as_problem(p, h)
+    same, tot = rank_agreement(o, q)
+    assert same == tot
+    dev = h.stats()["model_flops"]
+    ref = o.c.total()
+    assert abs(dev - ref) <= 1e-9 * ref, (dev, ref, dict(o.c.flops), h.stats()["flops_by_kind"])
+    h.close()
