@@ -69,8 +69,10 @@ def test_factor_parity_eps_1e6(r, axes):
 @pytest.mark.parametrize("core", ["fp64", "fp32"])
 def test_fp32_factors_against_fp64_oracle(eps, core):
     """FP32 factors on the n = 1280 ellipsoid: E_fac (oracle) <= 10 eps, the densified factors stay
-    within 1e-4 max|A_H| of the FP64 oracle's (FP32 rounding through the recursion, plus truncation
-    flips bounded by eps), and refinement reaches 1e-10 (checked with the oracle's H-matvec)."""
+    within 10 eps + 1e-4 of max|A_H| from the FP64 oracle's (a singular value at the threshold may be
+    kept on one side and dropped on the other, which moves a block by up to about eps times its norm,
+    as in the FP64 parity rule; FP32 rounding carried through the recursion stays below 1e-4), and
+    refinement reaches 1e-10 (checked with the oracle's H-matvec)."""
     import torch
     from paper_1906_00874_gb300 import HLU, HLU_FP32, HLU_FP32_CORE32
     p = build_problem(3, 32, 2.0, eps, nrhs=2, axes=ELLIPSOID)
@@ -81,7 +83,7 @@ def test_fp32_factors_against_fp64_oracle(eps, core):
     A = build_hmatrix(p)
     efac = factor_error(A, build_hmatrix(q), p.n)
     assert efac <= 10 * p.eps, efac
-    assert _factor_diff(p, q, o) <= 1e-4
+    assert _factor_diff(p, q, o) <= 10 * p.eps + 1e-4
     b = _dev(p.b)
     x = torch.zeros_like(b)
     it, res = h.solve_refined(b, x, tol=1e-10, max_iter=20)
