@@ -110,8 +110,17 @@ typedef struct {
                             products above the block substitution of Sec. 3.1 (fewer
                             sequential steps); 0 -> 1024, < 0 -> plain block substitution.
                             The inverses are not counted in the model flops */
-    int32_t reserved_;   /* set to 0 */
+    int32_t flags;       /* HLU_FLAG_* bits; 0 for the defaults */
 } hlu_opts;
+
+/* hlu_opts.flags */
+enum {
+    HLU_FLAG_NO_TENSOR = 1  /* FP32 factors: compute the dense products of the factorisation
+                               (ACCUM tasks with >= 32 rows, >= 16 columns and >= 32 inner
+                               columns) on CUDA cores instead of the tensor cores (tcgen05,
+                               three TF32 products per FP32 product); the wave schedule never
+                               uses the tensor cores */
+};
 
 typedef struct hlu_ctx *hlu_t;
 

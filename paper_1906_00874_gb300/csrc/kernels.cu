@@ -344,9 +344,14 @@ __device__ __forceinline__ void cp_async_el(T *dst_smem, const T *src) {
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+struct TcState;
+__device__ bool dev_accum_tc(const TAccum &t, const Term *terms, const LaunchArgs &a, unsigned char *smem_raw,
+                             size_t smem_bytes, TcState &tc, int m, int p);
+__device__ __forceinline__ bool tc_on(const TcState *tc);
+
 template <class T>
 __device__ void dev_accum(const TAccum &t, const Term *terms, const LaunchArgs &a, unsigned char *smem_raw,
-                          size_t smem_bytes) {
+                          size_t smem_bytes, TcState *tc = nullptr) {
     T *A = reinterpret_cast<T *>(a.arena);
     Term *sT = reinterpret_cast<Term *>(smem_raw);
     int *sP = reinterpret_cast<int *>(sT + kAccTerms);  // exclusive prefix of the inner sizes
@@ -357,6 +362,12 @@ __device__ void dev_accum(const TAccum &t, const Term *terms, const LaunchArgs &
     const int p = t.dst >= 0 ? a.kdyn[t.src] : dim_c(t.out, a.kdyn);
     if (t.dst >= 0 && threadIdx.x == 0) a.kdyn[t.dst] = p;
     if (m == 0 || p == 0) return;
+    if constexpr (sizeof(T) == 4) {
+        // dense products with at least 32 rows and 16 columns go to the tensor cores
+        if (tc_on(tc) && m >= 32 && m <= kMaxLeafRows && p >= 16 &&
+            dev_accum_tc(t, terms, a, smem_raw, smem_bytes, *tc, m, p))
+            return;
+    }
     const T alpha = T(t.alpha);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     constexpr int kSlots = 4;  // (row, 4-column block) outputs per thread
@@ -466,6 +477,245 @@ __device__ void dev_accum(const TAccum &t, const Term *terms, const LaunchArgs &
             }
         }
     }
+}
+
+// ------------------------------------------------------ ACCUM on tensor cores
+// Dense products of the factorisation on the 5th-generation tensor cores (tcgen05), for
+// single-precision factors: one output tile of 128 rows (the leaf cluster, zero rows beyond m)
+// by Np <= 128 columns accumulates in tensor memory (TMEM, FP32) over the packed inner columns of
+// all terms.  Each operand value v is split into two TF32 parts, hi = tf32(v), lo = tf32(v - hi),
+// and the tile takes A_hi X_hi + A_hi X_lo + A_lo X_hi (three MMAs of kind::tf32 per K step of 8),
+// which keeps the products at FP32 accuracy (the dropped A_lo X_lo term is below 2^-21 of the
+// product).  Operands are staged in shared memory in the K-major, unswizzled layout of the MMA
+// descriptors: 8-row core matrices of 16 bytes per row, adjacent in K at 128 bytes (leading byte
+// offset) and in M / N at 256 bytes (stride byte offset), one block of rows x 8 per K step.  One
+// thread issues the MMAs and commits them to an mbarrier that every thread waits on (with a
+// deadline) before the staged operands are overwritten or the accumulator is read back with
+// tcgen05.ld (warp w reads TMEM lanes 32 (w % 4) ... and half (w / 4) of the columns).
+struct TcState {
+    uint32_t tmem;   // TMEM address of the accumulator (128 lanes x 128 columns)
+    uint32_t mbar;   // shared address of the MMA-completion mbarrier
+    uint32_t phase;  // parity of the mbarrier phase to wait for next
+    bool on;
+    unsigned long long timeout_ns;
+};
+
+constexpr int kTcRows = 128, kTcMaxCols = 128;
+
+__device__ __forceinline__ bool tc_on(const TcState *tc) { return tc && tc->on; }
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: K-major, no swizzle, LBO 128 B (K direction), SBO 256 B (M / N).
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) |
+           (1ull << 46);
+}
+
+// Instruction descriptor of kind::tf32: FP32 accumulator, TF32 A and B, both K-major, M x N.
+__device__ __forceinline__ uint32_t tc_idesc(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Byte offset of element (row, k) in a K-major tile of `rows` rows: [k / 8][row / 8][(k / 4) % 2][row % 8][k % 4].
+__device__ __forceinline__ uint32_t tc_off(int row, int k, int rows) {
+    return (uint32_t)((k >> 3) * rows * 32 + (row >> 3) * 256 + ((k >> 2) & 1) * 128 + (row & 7) * 16 + (k & 3) * 4);
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long tc_now() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait (every thread) for the MMAs committed last; false on timeout (error recorded).
+__device__ __forceinline__ bool tc_wait(TcState &tc, const LaunchArgs &a) {
+    const unsigned long long deadline = tc_now() + tc.timeout_ns;
+    uint32_t ok = 0;
+    for (;;) {
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(tc.mbar), "r"(tc.phase)
+            : "memory");
+        if (ok) break;
+        if (tc_now() > deadline) {
+            if (threadIdx.x == 0) set_error(a.err, DE_TIMEOUT, -1, 0.0);
+            return false;
+        }
+    }
+    tc.phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    return true;
+}
+
+// Inclusive scan of the inner sizes of a term batch into sP (exclusive prefix, sP[0] = 0), the
+// batch's descriptors into sT; returns the batch's packed inner size.  Ends with a barrier.
+__device__ __forceinline__ int accum_load_terms(const TAccum &t, const Term *terms, const LaunchArgs &a, Term *sT,
+                                                int *sP, int q0, int nq) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();  // the previous table and batch are no longer read
+    if ((int)threadIdx.x < nq) {
+        const Term tm = terms[t.term0 + q0 + threadIdx.x];
+        sT[threadIdx.x] = tm;
+        sP[threadIdx.x + 1] = dim_c(tm.A, a.kdyn);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        int carry = 0;
+        for (int base = 0; base < nq; base += 32) {
+            const int q = base + lane;
+            int v = q < nq ? sP[q + 1] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFull, v, o);
+                if (lane >= o) v += y;
+            }
+            if (q < nq) sP[q + 1] = v + carry;
+            carry += __shfl_sync(kFull, v, 31);
+        }
+        if (lane == 0) sP[0] = 0;
+    }
+    __syncthreads();
+    return sP[nq];
+}
+
+// The tensor-core form of dev_accum (single precision, m <= 128).  Returns false, before writing
+// anything, when the task is too small to gain (one term batch with fewer than 32 inner columns):
+// the caller then takes the CUDA-core form.
+__device__ bool dev_accum_tc(const TAccum &t, const Term *terms, const LaunchArgs &a, unsigned char *smem_raw,
+                             size_t smem_bytes, TcState &tc, int m, int p) {
+    float *A = reinterpret_cast<float *>(a.arena);
+    Term *sT = reinterpret_cast<Term *>(smem_raw);
+    int *sP = reinterpret_cast<int *>(sT + kAccTerms);
+    int *sC = sP + kAccTerms + 1;
+    unsigned char *data = smem_raw + accum_header_bytes();
+    const size_t dbytes = smem_bytes - accum_header_bytes();
+    const float alpha = float(t.alpha);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int b0 = 0; b0 < p; b0 += kTcMaxCols) {
+        const int pb = min(kTcMaxCols, p - b0), Np = (pb + 15) & ~15;
+        const int Lc = min(128, (int)(dbytes / (8 * (size_t)(kTcRows + Np))) & ~7);
+        if (Lc < 8) return b0 > 0;  // (not reached: every worker has room for 8 inner columns)
+        unsigned char *Ahi = data, *Alo = Ahi + (size_t)kTcRows * Lc * 4;
+        unsigned char *Xhi = Alo + (size_t)kTcRows * Lc * 4, *Xlo = Xhi + (size_t)Np * Lc * 4;
+        bool issued = false, pending = false;
+        for (int q0 = 0; q0 < t.nterms; q0 += kAccTerms) {
+            const int nq = min(kAccTerms, t.nterms - q0);
+            if (pending) {  // the staged operands of the last chunk are still read by the tensor cores
+                if (!tc_wait(tc, a)) return true;
+                pending = false;
+            }
+            const int Ltot = accum_load_terms(t, terms, a, sT, sP, q0, nq);
+            if (b0 == 0 && q0 == 0 && Ltot < 32 && t.nterms <= kAccTerms) return false;  // uniform
+            if (b0 == 0 && q0 == 0 && threadIdx.x == 0 && t.credit > 0.0f) add_flops(a, K_ACCUM, (double)t.credit * p);
+            if (b0 == 0 && threadIdx.x == 0 && t.credit == 0.0f) add_flops(a, K_ACCUM, 2.0 * m * (double)Ltot * p);
+            for (int c0 = 0; c0 < Ltot; c0 += Lc) {
+                const int L = min(Lc, Ltot - c0), Lp = (L + 7) & ~7;
+                if (pending) {
+                    if (!tc_wait(tc, a)) return true;
+                    pending = false;
+                }
+                for (int lb = threadIdx.x; lb < L; lb += blockDim.x) {
+                    const int gc = c0 + lb;
+                    int lo = 0, hi = nq - 1;  // largest q with sP[q] <= gc (a non-empty term)
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (sP[mid] <= gc)
+                            lo = mid;
+                        else
+                            hi = mid - 1;
+                    }
+                    sC[lb] = (lo << 16) | (gc - sP[lo]);
+                }
+                __syncthreads();
+                // A: 128 x Lp (rows beyond m and columns beyond L are zero); consecutive threads take
+                // consecutive rows of a column (coalesced for column-major panels)
+                for (int e = threadIdx.x; e < kTcRows * Lp; e += blockDim.x) {
+                    const int i = e & (kTcRows - 1), l = e >> 7;
+                    float v = 0.0f;
+                    if (i < m && l < L) {
+                        const int c = sC[l];
+                        const Panel &PA = sT[c >> 16].A;
+                        v = A[PA.off + (int64_t)i * PA.rs + (int64_t)(c & 0xffff) * PA.cs];
+                    }
+                    const float h = tf32_rna(v);
+                    const uint32_t o = tc_off(i, l, kTcRows);
+                    *reinterpret_cast<float *>(Ahi + o) = h;
+                    *reinterpret_cast<float *>(Alo + o) = tf32_rna(v - h);
+                }
+                // X^T: Np x Lp (row n = output column b0 + n), consecutive threads along the inner index
+                for (int e = threadIdx.x; e < Np * Lp; e += blockDim.x) {
+                    const int l = e % Lp, n = e / Lp;
+                    float v = 0.0f;
+                    if (n < pb && l < L) {
+                        const int c = sC[l];
+                        const Panel &PX = sT[c >> 16].X;
+                        v = A[PX.off + (int64_t)(c & 0xffff) * PX.rs + (int64_t)(b0 + n) * PX.cs];
+                    }
+                    const float h = tf32_rna(v);
+                    const uint32_t o = tc_off(n, l, Np);
+                    *reinterpret_cast<float *>(Xhi + o) = h;
+                    *reinterpret_cast<float *>(Xlo + o) = tf32_rna(v - h);
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t idesc = tc_idesc(kTcRows, Np);
+                    const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), xh = smem_u32(Xhi), xl = smem_u32(Xlo);
+                    for (int ks = 0; ks < Lp / 8; ++ks) {
+                        const uint32_t ao = ks * kTcRows * 32, xo = ks * Np * 32;
+                        tc_mma(tc.tmem, tc_desc(ah + ao), tc_desc(xh + xo), idesc, (issued || ks > 0) ? 1u : 0u);
+                        tc_mma(tc.tmem, tc_desc(ah + ao), tc_desc(xl + xo), idesc, 1u);
+                        tc_mma(tc.tmem, tc_desc(al + ao), tc_desc(xh + xo), idesc, 1u);
+                    }
+                    tc_commit(tc.mbar);
+                }
+                issued = true;
+                pending = true;
+            }
+        }
+        if (pending && !tc_wait(tc, a)) return true;
+        // epilogue: out = beta out + alpha acc over rows < m and columns < pb of the tile
+        const int row = 32 * (warp & 3) + lane, half = Np >> 1, cbeg = (warp >> 2) * half;
+        for (int c8 = cbeg; c8 < cbeg + half; c8 += 8) {
+            uint32_t v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            if (issued) {
+                const uint32_t ta = tc.tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c8;
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                               "=r"(v[7])
+                             : "r"(ta));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            }
+            if (row < m)
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (c8 + j < pb) {
+                        float &o = at(A, t.out, row, b0 + c8 + j);
+                        o = (t.overwrite ? 0.0f : o) + alpha * __uint_as_float(v[j]);
+                    }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();  // the accumulator is read before the next tile's MMAs overwrite it
+    }
+    return true;
 }
 
 // ------------------------------------------------------------------ SPLIT
@@ -1669,8 +1919,28 @@ template <class T>
 __global__ void __launch_bounds__(kThreads, 2) k_dataflow(FlowArgs f, LaunchArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_task, s_next, s_first;
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) unsigned long long s_mbar;
     T *scratch = reinterpret_cast<T *>(f.scratch) + (int64_t)blockIdx.x * f.scratch_stride;
     if (threadIdx.x == 0) s_next = -1;
+    // tensor cores (single precision, when enabled): this worker's TMEM accumulator (128 columns; at
+    // most two workers per SM, so 256 of the 512 columns) and the MMA-completion mbarrier
+    TcState tc{0u, 0u, 0u, false, f.timeout_ns};
+    const bool use_tc = sizeof(T) == 4 && f.tensor;
+    if (use_tc) {
+        if (threadIdx.x < 32) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                         "r"(kTcMaxCols));
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        }
+        if (threadIdx.x == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_mbar)));
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        tc.tmem = s_tmem;
+        tc.mbar = smem_u32(&s_mbar);
+        tc.on = true;
+    }
     for (;;) {
         if (threadIdx.x == 0) {
             int g = s_next;
@@ -1724,7 +1994,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dataflow(FlowArgs f, LaunchArgs
             }
             case K_ACCUM: {
                 const TAccum t = f.accum[idx];
-                dev_accum<T>(t, f.terms, a, smem_raw, f.smem_bytes);
+                dev_accum<T>(t, f.terms, a, smem_raw, f.smem_bytes, &tc);
                 break;
             }
             case K_RADD: {
@@ -1793,6 +2063,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_dataflow(FlowArgs f, LaunchArgs
             }
         }
         __syncthreads();
+    }
+    if (use_tc) {  // every path out of the loop comes here: the accumulator is given back
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x < 32)
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tc.tmem), "r"(kTcMaxCols));
     }
 }
 
