@@ -304,8 +304,10 @@ typedef struct {
                                  H-matrix products */
     int64_t kernel_launches[10];
     double task_busy_ms[8];   /* with profiling on, data-flow factorisations: summed time of the
-                                 tasks of each kind (concurrent tasks add up) */
-    int64_t task_count[8];
+                                 tasks of each kind (concurrent tasks add up); [6]: summed time the
+                                 workers waited for their tensor-memory allocation */
+    int64_t task_count[8];    /* the same, task counts; [7]: workers that ran at least one task,
+                                 summed over the profiled factorisations */
     double radd_busy_ms[8];   /* the same for rounded additions by target size m + n:
                                  < 128, < 256, < 512, ..., >= 8192 */
     int64_t radd_count[8];

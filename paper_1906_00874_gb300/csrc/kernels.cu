@@ -349,7 +349,9 @@ __device__ bool dev_accum_tc(const TAccum &t, const Term *terms, const LaunchArg
                              size_t smem_bytes, TcState &tc, int m, int p);
 __device__ __forceinline__ bool tc_on(const TcState *tc);
 
-template <class T>
+// TC: the kernel that calls this holds the tensor-core form (only the data-flow kernel does; a
+// kernel with tcgen05 code in it needs the TMEM permit handling of k_dataflow).
+template <class T, bool TC = false>
 __device__ void dev_accum(const TAccum &t, const Term *terms, const LaunchArgs &a, unsigned char *smem_raw,
                           size_t smem_bytes, TcState *tc = nullptr) {
     T *A = reinterpret_cast<T *>(a.arena);
@@ -362,7 +364,7 @@ __device__ void dev_accum(const TAccum &t, const Term *terms, const LaunchArgs &
     const int p = t.dst >= 0 ? a.kdyn[t.src] : dim_c(t.out, a.kdyn);
     if (t.dst >= 0 && threadIdx.x == 0) a.kdyn[t.dst] = p;
     if (m == 0 || p == 0) return;
-    if constexpr (sizeof(T) == 4) {
+    if constexpr (TC && sizeof(T) == 4) {
         // dense products with at least 32 rows and 16 columns go to the tensor cores
         if (tc_on(tc) && m >= 32 && m <= kMaxLeafRows && p >= 16 &&
             dev_accum_tc(t, terms, a, smem_raw, smem_bytes, *tc, m, p))
@@ -608,29 +610,33 @@ __device__ bool dev_accum_tc(const TAccum &t, const Term *terms, const LaunchArg
     const size_t dbytes = smem_bytes - accum_header_bytes();
     const float alpha = float(t.alpha);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int m8 = (m + 7) & ~7;
     for (int b0 = 0; b0 < p; b0 += kTcMaxCols) {
         const int pb = min(kTcMaxCols, p - b0), Np = (pb + 15) & ~15;
-        const int Lc = min(128, (int)(dbytes / (8 * (size_t)(kTcRows + Np))) & ~7);
+        // tiles hi / lo of A (128 x Lc) and X^T (Np x Lc), then the raw operands as copied: A (m x Lc,
+        // ld m) and X (Lc x pb, ld Lc)
+        const int Lc = min(128, (int)(dbytes / (4 * (size_t)(3 * kTcRows + 3 * Np))) & ~7);
         if (Lc < 8) return b0 > 0;  // (not reached: every worker has room for 8 inner columns)
         unsigned char *Ahi = data, *Alo = Ahi + (size_t)kTcRows * Lc * 4;
         unsigned char *Xhi = Alo + (size_t)kTcRows * Lc * 4, *Xlo = Xhi + (size_t)Np * Lc * 4;
+        float *rawA = reinterpret_cast<float *>(Xlo + (size_t)Np * Lc * 4);
+        float *rawX = rawA + (size_t)kTcRows * Lc;
         bool issued = false, pending = false;
+        // rows m8 .. 127 of the A tiles stay zero for the whole tile (the MMA always takes 128 rows)
+        for (int e = threadIdx.x; e < (kTcRows - m8) * Lc; e += blockDim.x) {
+            const int i = m8 + e % (kTcRows - m8), l = e / (kTcRows - m8);
+            const uint32_t o = tc_off(i, l, kTcRows);
+            *reinterpret_cast<float *>(Ahi + o) = 0.0f;
+            *reinterpret_cast<float *>(Alo + o) = 0.0f;
+        }
         for (int q0 = 0; q0 < t.nterms; q0 += kAccTerms) {
             const int nq = min(kAccTerms, t.nterms - q0);
-            if (pending) {  // the staged operands of the last chunk are still read by the tensor cores
-                if (!tc_wait(tc, a)) return true;
-                pending = false;
-            }
-            const int Ltot = accum_load_terms(t, terms, a, sT, sP, q0, nq);
+            const int Ltot = accum_load_terms(t, terms, a, sT, sP, q0, nq);  // (the MMAs read only the tiles)
             if (b0 == 0 && q0 == 0 && Ltot < 32 && t.nterms <= kAccTerms) return false;  // uniform
             if (b0 == 0 && q0 == 0 && threadIdx.x == 0 && t.credit > 0.0f) add_flops(a, K_ACCUM, (double)t.credit * p);
             if (b0 == 0 && threadIdx.x == 0 && t.credit == 0.0f) add_flops(a, K_ACCUM, 2.0 * m * (double)Ltot * p);
             for (int c0 = 0; c0 < Ltot; c0 += Lc) {
                 const int L = min(Lc, Ltot - c0), Lp = (L + 7) & ~7;
-                if (pending) {
-                    if (!tc_wait(tc, a)) return true;
-                    pending = false;
-                }
                 for (int lb = threadIdx.x; lb < L; lb += blockDim.x) {
                     const int gc = c0 + lb;
                     int lo = 0, hi = nq - 1;  // largest q with sP[q] <= gc (a non-empty term)
@@ -644,30 +650,35 @@ __device__ bool dev_accum_tc(const TAccum &t, const Term *terms, const LaunchArg
                     sC[lb] = (lo << 16) | (gc - sP[lo]);
                 }
                 __syncthreads();
-                // A: 128 x Lp (rows beyond m and columns beyond L are zero); consecutive threads take
-                // consecutive rows of a column (coalesced for column-major panels)
-                for (int e = threadIdx.x; e < kTcRows * Lp; e += blockDim.x) {
-                    const int i = e & (kTcRows - 1), l = e >> 7;
-                    float v = 0.0f;
-                    if (i < m && l < L) {
-                        const int c = sC[l];
-                        const Panel &PA = sT[c >> 16].A;
-                        v = A[PA.off + (int64_t)i * PA.rs + (int64_t)(c & 0xffff) * PA.cs];
-                    }
+                // raw operands by asynchronous copies (one packed column per warp and step, all copies
+                // of the chunk in flight), while the tensor cores may still read the previous tiles
+                for (int lb = warp; lb < L; lb += blockDim.x >> 5) {
+                    const int c = sC[lb], q = c >> 16, l = c & 0xffff;
+                    const Panel &PA = sT[q].A;
+                    const float *ca = A + PA.off + (int64_t)l * PA.cs;
+                    for (int i = lane; i < m; i += 32) cp_async_el(rawA + lb * m + i, ca + (int64_t)i * PA.rs);
+                    const Panel &PX = sT[q].X;
+                    const float *cx = A + PX.off + (int64_t)l * PX.rs + (int64_t)b0 * PX.cs;
+                    for (int j = lane; j < pb; j += 32) cp_async_el(rawX + lb + j * Lc, cx + (int64_t)j * PX.cs);
+                }
+                cp_async_wait_all();
+                if (pending) {
+                    if (!tc_wait(tc, a)) return true;
+                    pending = false;
+                }
+                __syncthreads();
+                // split into the TF32 tiles: A rows < m8, X^T rows < Np, inner columns < Lp (zero beyond)
+                for (int e = threadIdx.x; e < m8 * Lp; e += blockDim.x) {
+                    const int i = e % m8, l = e / m8;
+                    const float v = (i < m && l < L) ? rawA[i + l * m] : 0.0f;
                     const float h = tf32_rna(v);
                     const uint32_t o = tc_off(i, l, kTcRows);
                     *reinterpret_cast<float *>(Ahi + o) = h;
                     *reinterpret_cast<float *>(Alo + o) = tf32_rna(v - h);
                 }
-                // X^T: Np x Lp (row n = output column b0 + n), consecutive threads along the inner index
                 for (int e = threadIdx.x; e < Np * Lp; e += blockDim.x) {
                     const int l = e % Lp, n = e / Lp;
-                    float v = 0.0f;
-                    if (n < pb && l < L) {
-                        const int c = sC[l];
-                        const Panel &PX = sT[c >> 16].X;
-                        v = A[PX.off + (int64_t)(c & 0xffff) * PX.rs + (int64_t)(b0 + n) * PX.cs];
-                    }
+                    const float v = (n < pb && l < L) ? rawX[l + n * Lc] : 0.0f;
                     const float h = tf32_rna(v);
                     const uint32_t o = tc_off(n, l, Np);
                     *reinterpret_cast<float *>(Xhi + o) = h;
@@ -1924,10 +1935,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_dataflow(FlowArgs f, LaunchArgs
     T *scratch = reinterpret_cast<T *>(f.scratch) + (int64_t)blockIdx.x * f.scratch_stride;
     if (threadIdx.x == 0) s_next = -1;
     // tensor cores (single precision, when enabled): this worker's TMEM accumulator (128 columns; at
-    // most two workers per SM, so 256 of the 512 columns) and the MMA-completion mbarrier
+    // most two workers per SM, so 256 of the 512 columns) and the MMA-completion mbarrier.  A CTA of
+    // a kernel that holds tcgen05 code keeps the SM's TMEM allocation permit, and with it the SM
+    // from a second CTA, until it relinquishes the permit: every single-precision worker does so at
+    // once, after its allocation when the tensor cores are on.
     TcState tc{0u, 0u, 0u, false, f.timeout_ns};
     const bool use_tc = sizeof(T) == 4 && f.tensor;
+    int my_tasks = 0;  // tasks this worker ran (profiling: workers that ran any)
+    if constexpr (sizeof(T) == 4) {
+        if (!use_tc && threadIdx.x < 32) asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
     if (use_tc) {
+        const unsigned long long t_alloc = (f.busy && threadIdx.x == 0) ? global_ns() : 0ull;
         if (threadIdx.x < 32) {
             asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
                          "r"(kTcMaxCols));
@@ -1940,6 +1959,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dataflow(FlowArgs f, LaunchArgs
         tc.tmem = s_tmem;
         tc.mbar = smem_u32(&s_mbar);
         tc.on = true;
+        if (f.busy && threadIdx.x == 0) atomicAdd(f.busy + 6, global_ns() - t_alloc);  // TMEM allocation wait
     }
     for (;;) {
         if (threadIdx.x == 0) {
@@ -1975,6 +1995,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dataflow(FlowArgs f, LaunchArgs
         if (g < 0) break;
         const int code = f.code[g];
         const int kind = code >> kCodeShift, idx = code & kCodeMask;
+        ++my_tasks;
         const unsigned long long t_start = (f.busy && threadIdx.x == 0) ? global_ns() : 0ull;
         switch (kind) {
             case K_GETRF: {
@@ -1994,7 +2015,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dataflow(FlowArgs f, LaunchArgs
             }
             case K_ACCUM: {
                 const TAccum t = f.accum[idx];
-                dev_accum<T>(t, f.terms, a, smem_raw, f.smem_bytes, &tc);
+                dev_accum<T, true>(t, f.terms, a, smem_raw, f.smem_bytes, &tc);
                 break;
             }
             case K_RADD: {
@@ -2064,6 +2085,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dataflow(FlowArgs f, LaunchArgs
         }
         __syncthreads();
     }
+    if (f.busy && threadIdx.x == 0 && my_tasks > 0) atomicAdd(f.busy + 15, 1ull);  // active workers
     if (use_tc) {  // every path out of the loop comes here: the accumulator is given back
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
@@ -2218,14 +2240,29 @@ size_t dataflow_smem_bytes(int max_leaf, int elem, int kc, bool core64) {
     return s;
 }
 
+// Resident workers: the occupancy API counts one CTA per SM for a kernel that holds tcgen05 code
+// (it assumes the TMEM allocation permit is kept), but every worker relinquishes the permit at
+// start, so the count comes from the registers, the shared memory and the launch bound (two per
+// SM) directly; the TMEM of two workers (2 x 128 columns) fits the SM's 512.
 template <class T>
 int dataflow_workers(size_t smem) {
-    int dev = 0, sms = 0, per = 0;
+    int dev = 0, sms = 0, smem_sm = 0, reserved = 0, regs_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_dataflow<T>, kThreads, smem) != cudaSuccess || per < 1)
-        per = 1;
-    return sms * per;
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_dataflow<T>) != cudaSuccess) {
+        cudaGetLastError();
+        return sms;
+    }
+    const size_t per_cta = smem + fa.sharedSizeBytes + (size_t)reserved;
+    int per = 2;  // __launch_bounds__(kThreads, 2)
+    per = std::min<int>(per, (int)((size_t)smem_sm / std::max<size_t>(per_cta, 1)));
+    const int regs_cta = ((fa.numRegs * 32 + 255) / 256) * 256 * (kThreads / 32);  // 256-register warp granules
+    per = std::min(per, regs_sm / std::max(regs_cta, 1));
+    return sms * std::max(per, 1);
 }
 
 template <class T>
