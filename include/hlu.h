@@ -315,8 +315,9 @@ typedef struct {
     int64_t solve_task_count[8];
     double radd_phase[16];    /* rounded additions, summed ms per phase; [0, 8) dense route
                                  (small targets), [8, 16) stacked route: [0] sum formation or
-                                 stacking, [1] QR of the stacks and core product, [2] pivoted
-                                 QR of the core, [3] Jacobi SVD and truncation, [5] new
+                                 stacking, [1] QR of the stacks and core product (dense route:
+                                 the QR of R'^T of the core), [2] pivoted QR of the core, [3]
+                                 Jacobi SVD and truncation (stacked route: with the QR of R'^T), [5] new
                                  factors; counts: [4] Jacobi sweeps, [6] Jacobi sizes r,
                                  [7] tasks */
     int64_t kernels_launched; /* kernels this handle launched since it was created */

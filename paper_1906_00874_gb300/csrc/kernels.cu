@@ -906,6 +906,32 @@ __device__ __forceinline__ void reg_apply_q(const T *W, int ld, int len, int kk,
     }
 }
 
+// x 2^-k rounded toward zero to single precision, by integer operations on the bit pattern (they
+// run on the integer pipe; on this part a double-precision conversion instruction takes a slot of
+// the narrow FP64 pipe).  Zero, subnormal and underflowing values give a signed zero, values
+// above the single-precision range (and infinities) a signed infinity.
+__device__ __forceinline__ float dbl_to_flt_scaled(double x, int k) {
+    const int hi = __double2hiint(x);
+    const unsigned lo = (unsigned)__double2loint(x);
+    const unsigned sign = (unsigned)hi & 0x80000000u;
+    const int ex = (hi >> 20) & 0x7ff;
+    const int fe = ex - 1023 - k + 127;
+    if (ex == 0 || fe <= 0) return __uint_as_float(sign);
+    if (fe >= 255 || ex == 0x7ff) return __uint_as_float(sign | 0x7f800000u);
+    return __uint_as_float(sign | ((unsigned)fe << 23) | (((unsigned)hi & 0xfffffu) << 3) | (lo >> 29));
+}
+
+// A normal single-precision value in double precision (exact), by integer operations; zero and
+// subnormal values give a signed zero.
+__device__ __forceinline__ double flt_to_dbl(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned sign = u & 0x80000000u;
+    const int fe = (u >> 23) & 0xff;
+    if (fe == 0) return __hiloint2double((int)sign, 0);
+    const unsigned m = u & 0x7fffffu;
+    return __hiloint2double((int)(sign | ((unsigned)(fe - 127 + 1023) << 20) | (m >> 3)), (int)(m << 29));
+}
+
 // Jacobi rotation (c, s) that makes columns x, y with x.x = aa, y.y = bb,
 // x.y = gg orthogonal: t = tan(theta) is the smaller root of
 // t^2 + 2 zeta t - 1 = 0, zeta = (bb - aa) / (2 gg) (Rutishauser's form), and
@@ -917,11 +943,11 @@ __device__ __forceinline__ void reg_apply_q(const T *W, int ld, int len, int kk,
 // is orthogonal to double precision, and only its angle is single-precision
 // accurate, which the convergence test on the double dot products absorbs.
 __device__ __forceinline__ void jacobi_rotation(double aa, double bb, double gg, double &c, double &s) {
-    const double p = 2.0 * gg, q = bb - aa;
-    int e = (int)((__double2hiint(p) >> 20) & 0x7ff) - 1023;  // binary exponent of p
+    const double q = bb - aa;
+    // 2 gg and q scaled by 2^-e, e the binary exponent of 2 gg, as single-precision values
+    int e = (int)((__double2hiint(gg) >> 20) & 0x7ff) - 1023 + 1;
     e = max(-1000, min(1000, e));
-    const double sc = __hiloint2double((1023 - e) << 20, 0);  // 2^-e, exact
-    const float pf = (float)(p * sc), qf = (float)(q * sc);
+    const float pf = dbl_to_flt_scaled(gg, e - 1), qf = dbl_to_flt_scaled(q, e);
     const float z = qf / pf, az = fabsf(z);
     float t;
     if (!(az < 1e15f))
@@ -929,7 +955,7 @@ __device__ __forceinline__ void jacobi_rotation(double aa, double bb, double gg,
     else
         t = copysignf(1.0f, z) / (az + sqrtf(fmaf(z, z, 1.0f)));
     const float cf = rsqrtf(fmaf(t, t, 1.0f));
-    const double cd = (double)cf, sd = (double)(cf * t);
+    const double cd = flt_to_dbl(cf), sd = flt_to_dbl(cf * t);
     const double d = fma(cd, cd, fma(sd, sd, -1.0));
     const double f = fma(d, fma(0.375, d, -0.5), 1.0);
     c = cd * f;
@@ -1253,9 +1279,9 @@ struct CoreBufs {
     R *W;                                   // single precision: accumulated rotations (in D's space)
     R *tauU, *tauV, *nrmU, *nrmV;
     int *order, *perm, *iflag;
-    // single-precision cores with the SVD in double (core64): R'^T and its QR, reflector scalars,
-    // column norms and 1 / sigma in double (C, tauC and isg of precision R are not used then)
-    double *C64, *tauC64, *cn64, *isg64;
+    // single-precision cores with the Jacobi SVD in double (core64): 1 / sigma in double (isg of
+    // precision R is not used then); null otherwise
+    double *isg64;
 };
 
 // core64 applies to single-precision cores only: their SVD (QR of R'^T, Jacobi) runs in double.
@@ -1268,9 +1294,9 @@ template <class R>
 __host__ __device__ inline size_t core_bytes(int mr, int nc, bool stacked, bool core64) {
     const size_t rc = mr < nc ? mr : nc, mx = mr > nc ? mr : nc;
     const bool c64 = core_in_double<R>(core64);
-    const size_t nr = (size_t)mr * nc + (c64 ? 0 : mx * rc) + nc + 3 * rc + (sizeof(R) == 8 ? 0 : rc * rc) +
+    const size_t nr = (size_t)mr * nc + mx * rc + nc + 3 * rc + (sizeof(R) == 8 ? 0 : rc * rc) +
                       (stacked ? 2 * ((size_t)mr + nc) : 0);
-    return 8 * (rc * rc + rc + (c64 ? mx * rc + 3 * rc : 0)) + sizeof(R) * nr + 4 * (rc + nc + 8);
+    return 8 * (rc * rc + rc + (c64 ? rc : 0)) + sizeof(R) * nr + 4 * (rc + nc + 8);
 }
 
 template <class R>
@@ -1281,19 +1307,16 @@ __device__ CoreBufs<R> carve_core(unsigned char *base, int mr, int nc, bool stac
     b.D = reinterpret_cast<double *>(base);
     b.sig = b.D + rc * rc;
     double *dx = b.sig + rc;
-    b.C64 = b.tauC64 = b.cn64 = b.isg64 = nullptr;
+    b.isg64 = nullptr;
     if (c64) {
-        b.tauC64 = dx;
-        b.cn64 = dx + rc;
-        b.isg64 = dx + 2 * rc;
-        b.C64 = dx + 3 * rc;
-        dx += 3 * rc + (size_t)mx * rc;
+        b.isg64 = dx;
+        dx += rc;
     }
     R *x = reinterpret_cast<R *>(dx);
     b.M = x;
     x += (size_t)mr * nc;
-    b.C = c64 ? nullptr : x;
-    x += c64 ? 0 : (size_t)mx * rc;
+    b.C = x;
+    x += (size_t)mx * rc;
     b.cn = x;
     x += nc;
     b.tauM = x;
@@ -1347,28 +1370,20 @@ template <class R>
 __device__ int core_finish(const CoreBufs<R> &b, int mr, int nc, int r, const TRadd &t, const LaunchArgs &a,
                            int pb, unsigned long long &ph) {
     const bool c64 = core_in_double<R>(a.core64 != 0);
-    if (c64) {  // R'^T promoted to double (exact), its QR and the Jacobi in double
-        for (int e = threadIdx.x; e < nc * r; e += blockDim.x) {
-            const int c = e % nc, i = e / nc;
-            b.C64[e] = c >= i ? (double)b.M[i + (size_t)c * mr] : 0.0;
-        }
-    } else {
-        for (int e = threadIdx.x; e < nc * r; e += blockDim.x) {
-            const int c = e % nc, i = e / nc;
-            b.C[e] = c >= i ? b.M[i + (size_t)c * mr] : R(0);
-        }
+    for (int e = threadIdx.x; e < nc * r; e += blockDim.x) {
+        const int c = e % nc, i = e / nc;
+        b.C[e] = c >= i ? b.M[i + (size_t)c * mr] : R(0);
     }
     if (threadIdx.x == 0) b.iflag[2] = 0;  // [0]: Jacobi flag, [1]: pivoted-QR flag
     __syncthreads();
-    if (c64)
-        group_householder_qr<double>(b.C64, nc, r, b.tauC64, b.cn64, 0, blockDim.x >> 5, 0);
-    else
-        group_householder_qr<R>(b.C, nc, r, b.tauC, b.cn, 0, blockDim.x >> 5, 0);
+    group_householder_qr<R>(b.C, nc, r, b.tauC, b.cn, 0, blockDim.x >> 5, 0);
+    // profiling, dense route: the QR of R'^T goes to slot 1 (the stacked route keeps it in its slot 3)
+    if (pb == 0) ph = phase_mark(a, 1, ph);
     int sweeps;
-    if (c64) {
-        for (int e = threadIdx.x; e < r * r; e += blockDim.x) {  // X = R_C^T
+    if (c64) {  // the Jacobi SVD of X = R_C^T (single-precision values, exact in double) in double
+        for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
             const int i = e % r, j = e / r;
-            b.D[e] = i >= j ? b.C64[j + (size_t)i * nc] : 0.0;
+            b.D[e] = i >= j ? (double)b.C[j + (size_t)i * nc] : 0.0;
         }
         __syncthreads();
         sweeps = block_jacobi(b.D, r, r, b.iflag);
@@ -1466,10 +1481,13 @@ __device__ int core_truncate(const CoreBufs<R> &b, int mr, int nc, double delta,
 // sigma^2 for the nc rows of the core (V of type T, leading dimension ldv).
 template <class R, class T>
 __device__ void core_write_v(const CoreBufs<R> &b, int mr, int nc, int r, int knew, T *V, int64_t ldv) {
-    if (b.C64) {
-        // double SVD of a single-precision core: V[perm[i], c] = (R'^T B)[i, order[c]] / sigma^2 in
-        // double, R' exact as promoted; B from the double Jacobi, so Sigma^{-2} amplifies only
-        // double rounding (the product sigma_j u_j v_j^T stays at that level relative to sigma_1)
+    if (b.isg64) {
+        // double Jacobi SVD of a single-precision core: V[perm[i], c] = (R'^T B)[i, order[c]] /
+        // sigma^2 in double, R' exact as promoted.  B = X Z comes from the double Jacobi (Z
+        // orthogonal to double rounding), so the factor is M^T u_j / sigma_j for the left vectors
+        // u_j; its errors (double rounding of B, single-precision rounding of the QR of R'^T) enter
+        // the product sigma_j u_j v_j^T at their own level relative to sigma_1, not amplified by
+        // sigma_1 / sigma_j.
         for (int e = threadIdx.x; e < nc * knew; e += blockDim.x) {
             const int c = e % knew, i = e / knew;
             const int j = b.order[c];
@@ -1530,11 +1548,11 @@ __device__ void core_write_v(const CoreBufs<R> &b, int mr, int nc, int r, int kn
     }
 }
 
-// Output buffer of core_form_u: the buffer of R'^T in precision R, or its double copy (no longer
-// read once the Jacobi has started), which holds at least mr x knew values of precision R.
+// Output buffer of core_form_u: the buffer of R'^T (no longer read once the Jacobi has started),
+// which holds at least mr x knew values of precision R.
 template <class R>
 __device__ __forceinline__ R *core_out(const CoreBufs<R> &b) {
-    return b.C ? b.C : reinterpret_cast<R *>(b.C64);
+    return b.C;
 }
 
 // Left factor of the truncated core: core_out(b) (mr x knew) := Q_M [B_sel; 0].
@@ -1596,10 +1614,10 @@ __host__ __device__ inline size_t dense_pre_bytes(int m, int n) {
 template <class R>
 __host__ __device__ inline size_t dense_post_bytes(int m, int n, int r, bool c64) {
     const size_t mx = m > n ? m : n;
-    if (c64)  // D, sig, tauC64, cn64, isg64, C64 (double); B (precision R); order
-        return 8 * ((size_t)r * r + 4 * (size_t)r + mx * r) + sizeof(R) * (size_t)r * r + sizeof(int) * (size_t)r;
-    return 8 * ((size_t)r * r + r) + sizeof(R) * (mx * r + 2 * (size_t)r + (sizeof(R) == 8 ? 0 : (size_t)r * r)) +
-           sizeof(int) * (size_t)r;
+    // D, sig (and 1 / sigma of a double Jacobi in single-precision factors: c64) in double; C, tauC,
+    // isg (and B for single precision) in precision R; order
+    return 8 * ((size_t)r * r + r + (c64 ? r : 0)) +
+           sizeof(R) * (mx * r + 2 * (size_t)r + (sizeof(R) == 8 ? 0 : (size_t)r * r)) + sizeof(int) * (size_t)r;
 }
 
 template <class T>
@@ -1642,18 +1660,8 @@ __device__ bool radd_small(const TRadd &t, const Piece *pieces, const LaunchArgs
     // rank-r buffers after X and the pivot bookkeeping
     b.D = reinterpret_cast<double *>(smem_raw + dense_pre_bytes<T>(m, n));
     b.sig = b.D + r * r;
-    b.C64 = b.tauC64 = b.cn64 = b.isg64 = nullptr;
-    if (c64) {
-        b.tauC64 = b.sig + r;
-        b.cn64 = b.tauC64 + r;
-        b.isg64 = b.cn64 + r;
-        b.C64 = b.isg64 + r;
-        b.C = b.tauC = b.isg = nullptr;
-        b.W = nullptr;
-        b.B = reinterpret_cast<T *>(b.C64 + (size_t)max(m, n) * r);
-        b.order = reinterpret_cast<int *>(b.B + r * r);
-    } else {
-    b.C = reinterpret_cast<T *>(b.sig + r);
+    b.isg64 = c64 ? b.sig + r : nullptr;
+    b.C = reinterpret_cast<T *>(b.sig + r + (c64 ? r : 0));
     b.tauC = b.C + (size_t)max(m, n) * r;
     b.isg = b.tauC + r;
     if constexpr (sizeof(T) == 8) {
@@ -1664,7 +1672,6 @@ __device__ bool radd_small(const TRadd &t, const Piece *pieces, const LaunchArgs
         b.B = b.isg + r;
         b.W = reinterpret_cast<T *>(b.D);  // r x r floats in the r x r doubles of D
         b.order = reinterpret_cast<int *>(b.B + r * r);
-    }
     }
     const int knew = core_finish<T>(b, m, n, r, t, a, 0, ph);
     // the target's own factors were read above; every row of V is covered by P
