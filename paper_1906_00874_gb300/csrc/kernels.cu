@@ -611,24 +611,28 @@ __device__ bool dev_accum_tc(const TAccum &t, const Term *terms, const LaunchArg
     const float alpha = float(t.alpha);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int m8 = (m + 7) & ~7;
+    // tile rows: M = 64 when the leaf cluster fits (its accumulator row r sits in TMEM lane
+    // 32 (r / 16) + r % 16), else M = 128 (row r in lane r)
+    const int MT = m <= 64 ? 64 : kTcRows;
+    const int nw = blockDim.x >> 5;
     for (int b0 = 0; b0 < p; b0 += kTcMaxCols) {
         const int pb = min(kTcMaxCols, p - b0), Np = (pb + 15) & ~15;
-        // tiles hi / lo of A (128 x Lc) and X^T (Np x Lc), then the raw operands as copied: A (m x Lc,
+        // tiles hi / lo of A (MT x Lc) and X^T (Np x Lc), then the raw operands as copied: A (m x Lc,
         // ld m) and X (Lc x pb, ld Lc)
-        const int Lc = min(128, (int)(dbytes / (4 * (size_t)(3 * kTcRows + 3 * Np))) & ~7);
+        const int Lc = min(128, (int)(dbytes / (4 * (size_t)(3 * MT + 3 * Np))) & ~7);
         if (Lc < 8) return b0 > 0;  // (not reached: every worker has room for 8 inner columns)
-        unsigned char *Ahi = data, *Alo = Ahi + (size_t)kTcRows * Lc * 4;
-        unsigned char *Xhi = Alo + (size_t)kTcRows * Lc * 4, *Xlo = Xhi + (size_t)Np * Lc * 4;
+        unsigned char *Ahi = data, *Alo = Ahi + (size_t)MT * Lc * 4;
+        unsigned char *Xhi = Alo + (size_t)MT * Lc * 4, *Xlo = Xhi + (size_t)Np * Lc * 4;
         float *rawA = reinterpret_cast<float *>(Xlo + (size_t)Np * Lc * 4);
-        float *rawX = rawA + (size_t)kTcRows * Lc;
+        float *rawX = rawA + (size_t)MT * Lc;
         bool issued = false, pending = false;
-        // rows m8 .. 127 of the A tiles stay zero for the whole tile (the MMA always takes 128 rows)
-        for (int e = threadIdx.x; e < (kTcRows - m8) * Lc; e += blockDim.x) {
-            const int i = m8 + e % (kTcRows - m8), l = e / (kTcRows - m8);
-            const uint32_t o = tc_off(i, l, kTcRows);
-            *reinterpret_cast<float *>(Ahi + o) = 0.0f;
-            *reinterpret_cast<float *>(Alo + o) = 0.0f;
-        }
+        // rows m8 .. MT - 1 of the A tiles stay zero for the whole tile
+        for (int l = warp; l < Lc; l += nw)
+            for (int i = m8 + lane; i < MT; i += 32) {
+                const uint32_t o = tc_off(i, l, MT);
+                *reinterpret_cast<float *>(Ahi + o) = 0.0f;
+                *reinterpret_cast<float *>(Alo + o) = 0.0f;
+            }
         for (int q0 = 0; q0 < t.nterms; q0 += kAccTerms) {
             const int nq = min(kAccTerms, t.nterms - q0);
             const int Ltot = accum_load_terms(t, terms, a, sT, sP, q0, nq);  // (the MMAs read only the tiles)
@@ -652,7 +656,7 @@ __device__ bool dev_accum_tc(const TAccum &t, const Term *terms, const LaunchArg
                 __syncthreads();
                 // raw operands by asynchronous copies (one packed column per warp and step, all copies
                 // of the chunk in flight), while the tensor cores may still read the previous tiles
-                for (int lb = warp; lb < L; lb += blockDim.x >> 5) {
+                for (int lb = warp; lb < L; lb += nw) {
                     const int c = sC[lb], q = c >> 16, l = c & 0xffff;
                     const Panel &PA = sT[q].A;
                     const float *ca = A + PA.off + (int64_t)l * PA.cs;
@@ -668,30 +672,30 @@ __device__ bool dev_accum_tc(const TAccum &t, const Term *terms, const LaunchArg
                 }
                 __syncthreads();
                 // split into the TF32 tiles: A rows < m8, X^T rows < Np, inner columns < Lp (zero beyond)
-                for (int e = threadIdx.x; e < m8 * Lp; e += blockDim.x) {
-                    const int i = e % m8, l = e / m8;
-                    const float v = (i < m && l < L) ? rawA[i + l * m] : 0.0f;
-                    const float h = tf32_rna(v);
-                    const uint32_t o = tc_off(i, l, kTcRows);
-                    *reinterpret_cast<float *>(Ahi + o) = h;
-                    *reinterpret_cast<float *>(Alo + o) = tf32_rna(v - h);
-                }
-                for (int e = threadIdx.x; e < Np * Lp; e += blockDim.x) {
-                    const int l = e % Lp, n = e / Lp;
-                    const float v = (n < pb && l < L) ? rawX[l + n * Lc] : 0.0f;
-                    const float h = tf32_rna(v);
-                    const uint32_t o = tc_off(n, l, Np);
-                    *reinterpret_cast<float *>(Xhi + o) = h;
-                    *reinterpret_cast<float *>(Xlo + o) = tf32_rna(v - h);
-                }
+                for (int l = warp; l < Lp; l += nw)
+                    for (int i = lane; i < m8; i += 32) {
+                        const float v = (i < m && l < L) ? rawA[i + l * m] : 0.0f;
+                        const float h = tf32_rna(v);
+                        const uint32_t o = tc_off(i, l, MT);
+                        *reinterpret_cast<float *>(Ahi + o) = h;
+                        *reinterpret_cast<float *>(Alo + o) = tf32_rna(v - h);
+                    }
+                for (int n = warp; n < Np; n += nw)
+                    for (int l = lane; l < Lp; l += 32) {
+                        const float v = (n < pb && l < L) ? rawX[l + n * Lc] : 0.0f;
+                        const float h = tf32_rna(v);
+                        const uint32_t o = tc_off(n, l, Np);
+                        *reinterpret_cast<float *>(Xhi + o) = h;
+                        *reinterpret_cast<float *>(Xlo + o) = tf32_rna(v - h);
+                    }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncthreads();
                 if (threadIdx.x == 0) {
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t idesc = tc_idesc(kTcRows, Np);
+                    const uint32_t idesc = tc_idesc(MT, Np);
                     const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), xh = smem_u32(Xhi), xl = smem_u32(Xlo);
                     for (int ks = 0; ks < Lp / 8; ++ks) {
-                        const uint32_t ao = ks * kTcRows * 32, xo = ks * Np * 32;
+                        const uint32_t ao = ks * MT * 32, xo = ks * Np * 32;
                         tc_mma(tc.tmem, tc_desc(ah + ao), tc_desc(xh + xo), idesc, (issued || ks > 0) ? 1u : 0u);
                         tc_mma(tc.tmem, tc_desc(ah + ao), tc_desc(xl + xo), idesc, 1u);
                         tc_mma(tc.tmem, tc_desc(al + ao), tc_desc(xh + xo), idesc, 1u);
@@ -703,8 +707,10 @@ __device__ bool dev_accum_tc(const TAccum &t, const Term *terms, const LaunchArg
             }
         }
         if (pending && !tc_wait(tc, a)) return true;
-        // epilogue: out = beta out + alpha acc over rows < m and columns < pb of the tile
-        const int row = 32 * (warp & 3) + lane, half = Np >> 1, cbeg = (warp >> 2) * half;
+        // epilogue: out = beta out + alpha acc over rows < m and columns < pb of the tile; warp w reads
+        // TMEM lanes 32 (w % 4) .. + 31 and half w / 4 of the columns
+        const int row = MT == 64 ? (lane < 16 ? 16 * (warp & 3) + lane : kTcRows) : 32 * (warp & 3) + lane;
+        const int half = Np >> 1, cbeg = (warp >> 2) * half;
         for (int c8 = cbeg; c8 < cbeg + half; c8 += 8) {
             uint32_t v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             if (issued) {
