@@ -50,8 +50,8 @@ def parse():
     ap.add_argument("--solver", default="ir", choices=("ir", "gmres"),
                     help="FP64 iteration preconditioned by the factors: refinement or GMRES(restart)")
     ap.add_argument("--restart", type=int, default=30)
-    ap.add_argument("--no-tensor", action="store_true",
-                    help="FP32 factors: dense products on CUDA cores instead of the tensor cores")
+    ap.add_argument("--tensor", action="store_true",
+                    help="FP32 factors: dense products of the factorisation on the tensor cores (tcgen05)")
     ap.add_argument("--construct", action="store_true",
                     help="time the construction of the workload's H-matrix on the GPU (hlu_bem_build)")
     return ap.parse_args()
@@ -281,7 +281,7 @@ def measured_peaks():
         return {}
 
 
-FLAGS = 0  # hlu_opts.flags of every handle the bench makes (--no-tensor sets FLAG_NO_TENSOR)
+FLAGS = 0  # hlu_opts.flags of every handle the bench makes (--tensor sets FLAG_TENSOR)
 
 
 def make_handle(p, precision, stream):
@@ -803,9 +803,9 @@ def run_construct(args):
 def main():
     global FLAGS
     args = parse()
-    if args.no_tensor:
-        from paper_1906_00874_gb300.hlu import FLAG_NO_TENSOR
-        FLAGS = FLAG_NO_TENSOR
+    if args.tensor:
+        from paper_1906_00874_gb300.hlu import FLAG_TENSOR
+        FLAGS = FLAG_TENSOR
     if args.construct:
         run_construct(args)
         return

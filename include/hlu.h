@@ -115,11 +115,13 @@ typedef struct {
 
 /* hlu_opts.flags */
 enum {
-    HLU_FLAG_NO_TENSOR = 1  /* FP32 factors: compute the dense products of the factorisation
-                               (ACCUM tasks with >= 32 rows, >= 16 columns and >= 32 inner
-                               columns) on CUDA cores instead of the tensor cores (tcgen05,
-                               three TF32 products per FP32 product); the wave schedule never
-                               uses the tensor cores */
+    HLU_FLAG_TENSOR = 1  /* FP32 factors: compute the dense products of the factorisation
+                            (product tasks with >= 32 rows, >= 16 columns and >= 32 inner
+                            columns, data-flow schedule) on the tensor cores (tcgen05, three
+                            TF32 products per FP32 product, FP32 accumulation in tensor memory)
+                            instead of CUDA cores.  Off by default: these leaf-sized products
+                            (a 64-row leaf cluster, tens of inner columns) ran slower on the
+                            tensor cores than on CUDA cores in every measured workload */
 };
 
 typedef struct hlu_ctx *hlu_t;

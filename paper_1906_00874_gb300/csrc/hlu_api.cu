@@ -68,7 +68,7 @@ struct hlu_ctx {
     Planner pl;
     int precision = HLU_FP64;   // storage precision of the factors: HLU_FP64 or HLU_FP32
     bool core64 = true;         // FP32 factors: SVD of each truncation core in FP64 (HLU_FP32_CORE32: FP32)
-    bool tensor = true;         // FP32 factors: dense products of the factorisation on the tensor cores
+    bool tensor = false;        // FP32 factors: dense products of the factorisation on the tensor cores
     int schedule = HLU_SCHED_DATAFLOW;
     unsigned long long timeout_ns = 10000000000ull;
     cudaStream_t stream = nullptr;
@@ -274,6 +274,7 @@ void run_plan(hlu_ctx *h, const DevPlan &d, void *arena, double *flops) {
         f.scratch_stride = d.scratch_stride;
         f.timeout_ns = h->timeout_ns;
         f.tensor = (h->tensor && !dbl && &d == &h->fp) ? 1 : 0;
+        f.tc_min_inner = 32;
         f.busy = !h->profiling ? nullptr : &d == &h->fp ? h->busy : &d == &h->sp ? h->busy + 48 : nullptr;
         cudaMemcpyAsync(d.indeg, d.indeg0, sizeof(int32_t) * d.n_tasks, cudaMemcpyDeviceToDevice, h->stream);
         cudaMemsetAsync(d.queue, 0xff, sizeof(int32_t) * d.n_tasks, h->stream);
@@ -455,7 +456,7 @@ static int create_impl(const hlu_tree *tree, const hlu_blocks *blocks, const hlu
         h->schedule = opts->schedule;
         if (opts->timeout_s > 0.0) h->timeout_ns = (unsigned long long)(opts->timeout_s * 1e9);
         if (opts->inv_block != 0) po.inv_block = opts->inv_block < 0 ? 0 : opts->inv_block;
-        h->tensor = !(opts->flags & HLU_FLAG_NO_TENSOR);
+        h->tensor = (opts->flags & HLU_FLAG_TENSOR) != 0;
     }
     if (h->precision == HLU_FP32_CORE32) {  // FP32 factors, FP32 Jacobi in the truncation cores
         h->precision = HLU_FP32;

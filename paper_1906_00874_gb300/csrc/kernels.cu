@@ -344,6 +344,8 @@ __device__ __forceinline__ void cp_async_el(T *dst_smem, const T *src) {
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+__device__ __forceinline__ int accum_load_terms(const TAccum &t, const Term *terms, const LaunchArgs &a, Term *sT,
+                                                int *sP, int q0, int nq);
 struct TcState;
 __device__ bool dev_accum_tc(const TAccum &t, const Term *terms, const LaunchArgs &a, unsigned char *smem_raw,
                              size_t smem_bytes, TcState &tc, int m, int p);
@@ -364,11 +366,13 @@ __device__ void dev_accum(const TAccum &t, const Term *terms, const LaunchArgs &
     const int p = t.dst >= 0 ? a.kdyn[t.src] : dim_c(t.out, a.kdyn);
     if (t.dst >= 0 && threadIdx.x == 0) a.kdyn[t.dst] = p;
     if (m == 0 || p == 0) return;
+    bool loaded = false;  // the table of term batch 0 is in shared memory
     if constexpr (TC && sizeof(T) == 4) {
         // dense products with at least 32 rows and 16 columns go to the tensor cores
-        if (tc_on(tc) && m >= 32 && m <= kMaxLeafRows && p >= 16 &&
-            dev_accum_tc(t, terms, a, smem_raw, smem_bytes, *tc, m, p))
-            return;
+        if (tc_on(tc) && m >= 32 && m <= kMaxLeafRows && p >= 16) {
+            if (dev_accum_tc(t, terms, a, smem_raw, smem_bytes, *tc, m, p)) return;
+            loaded = true;
+        }
     }
     const T alpha = T(t.alpha);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -387,29 +391,7 @@ __device__ void dev_accum(const TAccum &t, const Term *terms, const LaunchArgs &
             for (int u = 0; u < 4; ++u) acc[s][u] = T(0);
         for (int q0 = 0; q0 < t.nterms; q0 += kAccTerms) {
             const int nq = min(kAccTerms, t.nterms - q0);
-            __syncthreads();  // the previous table and batch are no longer read
-            if ((int)threadIdx.x < nq) {
-                const Term tm = terms[t.term0 + q0 + threadIdx.x];
-                sT[threadIdx.x] = tm;
-                sP[threadIdx.x + 1] = dim_c(tm.A, a.kdyn);
-            }
-            __syncthreads();
-            if (warp == 0) {  // inclusive scan of the inner sizes
-                int carry = 0;
-                for (int base = 0; base < nq; base += 32) {
-                    const int q = base + lane;
-                    int v = q < nq ? sP[q + 1] : 0;
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int y = __shfl_up_sync(kFull, v, o);
-                        if (lane >= o) v += y;
-                    }
-                    if (q < nq) sP[q + 1] = v + carry;
-                    carry += __shfl_sync(kFull, v, 31);
-                }
-                if (lane == 0) sP[0] = 0;
-            }
-            __syncthreads();
-            const int Ltot = sP[nq];
+            const int Ltot = (loaded && b0 == 0 && q0 == 0) ? sP[nq] : accum_load_terms(t, terms, a, sT, sP, q0, nq);
             if (b0 == 0 && q0 == 0 && threadIdx.x == 0 && t.credit > 0.0f) add_flops(a, K_ACCUM, (double)t.credit * p);
             if (b0 == 0 && threadIdx.x == 0 && t.credit == 0.0f) add_flops(a, K_ACCUM, 2.0 * m * (double)Ltot * p);
             for (int c0 = 0; c0 < Ltot; c0 += Lcap) {
@@ -495,14 +477,19 @@ __device__ void dev_accum(const TAccum &t, const Term *terms, const LaunchArgs &
 // deadline) before the staged operands are overwritten or the accumulator is read back with
 // tcgen05.ld (warp w reads TMEM lanes 32 (w % 4) ... and half (w / 4) of the columns).
 struct TcState {
-    uint32_t tmem;   // TMEM address of the accumulator (128 lanes x 128 columns)
+    uint32_t tmem;   // TMEM address of the accumulators (128 lanes x kTcTmemCols columns)
     uint32_t mbar;   // shared address of the MMA-completion mbarrier
     uint32_t phase;  // parity of the mbarrier phase to wait for next
     bool on;
     unsigned long long timeout_ns;
+    int min_inner;
 };
 
-constexpr int kTcRows = 128, kTcMaxCols = 128;
+// Tiles of at most 128 output columns, one accumulator per tile (128 TMEM columns per worker).  The
+// MMAs of a tile may also rotate over kTcAccs accumulators (added in a fixed order by the epilogue)
+// so that consecutive MMAs do not wait on each other's results; with four (4 x 64 columns) the
+// products of the factorisations here were no faster, so one is used.
+constexpr int kTcRows = 128, kTcMaxCols = 128, kTcAccs = 1, kTcTmemCols = kTcAccs * kTcMaxCols;
 
 __device__ __forceinline__ bool tc_on(const TcState *tc) { return tc && tc->on; }
 
@@ -598,8 +585,9 @@ __device__ __forceinline__ int accum_load_terms(const TAccum &t, const Term *ter
 }
 
 // The tensor-core form of dev_accum (single precision, m <= 128).  Returns false, before writing
-// anything, when the task is too small to gain (one term batch with fewer than 32 inner columns):
-// the caller then takes the CUDA-core form.
+// anything, when the task is too small to gain (one term batch with fewer than tc.min_inner inner
+// columns): the caller then takes the CUDA-core form with the term table of that batch already in
+// shared memory.
 __device__ bool dev_accum_tc(const TAccum &t, const Term *terms, const LaunchArgs &a, unsigned char *smem_raw,
                              size_t smem_bytes, TcState &tc, int m, int p) {
     float *A = reinterpret_cast<float *>(a.arena);
@@ -625,7 +613,8 @@ __device__ bool dev_accum_tc(const TAccum &t, const Term *terms, const LaunchArg
         unsigned char *Xhi = Alo + (size_t)MT * Lc * 4, *Xlo = Xhi + (size_t)Np * Lc * 4;
         float *rawA = reinterpret_cast<float *>(Xlo + (size_t)Np * Lc * 4);
         float *rawX = rawA + (size_t)MT * Lc;
-        bool issued = false, pending = false;
+        bool pending = false;
+        int nmma = 0;  // MMAs issued for this tile (uniform); accumulator j holds data once nmma > j
         // rows m8 .. MT - 1 of the A tiles stay zero for the whole tile
         for (int l = warp; l < Lc; l += nw)
             for (int i = m8 + lane; i < MT; i += 32) {
@@ -636,7 +625,8 @@ __device__ bool dev_accum_tc(const TAccum &t, const Term *terms, const LaunchArg
         for (int q0 = 0; q0 < t.nterms; q0 += kAccTerms) {
             const int nq = min(kAccTerms, t.nterms - q0);
             const int Ltot = accum_load_terms(t, terms, a, sT, sP, q0, nq);  // (the MMAs read only the tiles)
-            if (b0 == 0 && q0 == 0 && Ltot < 32 && t.nterms <= kAccTerms) return false;  // uniform
+            if (b0 == 0 && q0 == 0 && Ltot < tc.min_inner && t.nterms <= kAccTerms) return false;  // uniform;
+            // the caller reuses the loaded table of batch 0
             if (b0 == 0 && q0 == 0 && threadIdx.x == 0 && t.credit > 0.0f) add_flops(a, K_ACCUM, (double)t.credit * p);
             if (b0 == 0 && threadIdx.x == 0 && t.credit == 0.0f) add_flops(a, K_ACCUM, 2.0 * m * (double)Ltot * p);
             for (int c0 = 0; c0 < Ltot; c0 += Lc) {
@@ -694,15 +684,19 @@ __device__ bool dev_accum_tc(const TAccum &t, const Term *terms, const LaunchArg
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t idesc = tc_idesc(MT, Np);
                     const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), xh = smem_u32(Xhi), xl = smem_u32(Xlo);
+                    int k = nmma;
                     for (int ks = 0; ks < Lp / 8; ++ks) {
                         const uint32_t ao = ks * MT * 32, xo = ks * Np * 32;
-                        tc_mma(tc.tmem, tc_desc(ah + ao), tc_desc(xh + xo), idesc, (issued || ks > 0) ? 1u : 0u);
-                        tc_mma(tc.tmem, tc_desc(ah + ao), tc_desc(xl + xo), idesc, 1u);
-                        tc_mma(tc.tmem, tc_desc(al + ao), tc_desc(xh + xo), idesc, 1u);
+                        const uint32_t pa[3] = {ah + ao, ah + ao, al + ao}, px[3] = {xh + xo, xl + xo, xh + xo};
+#pragma unroll
+                        for (int u = 0; u < 3; ++u, ++k) {
+                            const uint32_t d = tc.tmem + (uint32_t)((k % kTcAccs) * kTcMaxCols);
+                            tc_mma(d, tc_desc(pa[u]), tc_desc(px[u]), idesc, k >= kTcAccs ? 1u : 0u);
+                        }
                     }
                     tc_commit(tc.mbar);
                 }
-                issued = true;
+                nmma += 3 * (Lp / 8);
                 pending = true;
             }
         }
@@ -712,21 +706,24 @@ __device__ bool dev_accum_tc(const TAccum &t, const Term *terms, const LaunchArg
         const int row = MT == 64 ? (lane < 16 ? 16 * (warp & 3) + lane : kTcRows) : 32 * (warp & 3) + lane;
         const int half = Np >> 1, cbeg = (warp >> 2) * half;
         for (int c8 = cbeg; c8 < cbeg + half; c8 += 8) {
-            uint32_t v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            if (issued) {
-                const uint32_t ta = tc.tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c8;
+            float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            for (int q = 0; q < kTcAccs && q < nmma; ++q) {  // uniform: every lane loads
+                uint32_t v[8];
+                const uint32_t ta = tc.tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(q * kTcMaxCols + c8);
                 asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
                                "=r"(v[7])
                              : "r"(ta));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[j] += __uint_as_float(v[j]);
             }
             if (row < m)
 #pragma unroll
                 for (int j = 0; j < 8; ++j)
                     if (c8 + j < pb) {
                         float &o = at(A, t.out, row, b0 + c8 + j);
-                        o = (t.overwrite ? 0.0f : o) + alpha * __uint_as_float(v[j]);
+                        o = (t.overwrite ? 0.0f : o) + alpha * acc[j];
                     }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1947,12 +1944,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_dataflow(FlowArgs f, LaunchArgs
     __shared__ __align__(8) unsigned long long s_mbar;
     T *scratch = reinterpret_cast<T *>(f.scratch) + (int64_t)blockIdx.x * f.scratch_stride;
     if (threadIdx.x == 0) s_next = -1;
-    // tensor cores (single precision, when enabled): this worker's TMEM accumulator (128 columns; at
-    // most two workers per SM, so 256 of the 512 columns) and the MMA-completion mbarrier.  A CTA of
+    // tensor cores (single precision, when enabled): this worker's TMEM accumulators (kTcTmemCols
+    // columns; at most two workers per SM, 512 columns at most) and the MMA-completion mbarrier.  A CTA of
     // a kernel that holds tcgen05 code keeps the SM's TMEM allocation permit, and with it the SM
     // from a second CTA, until it relinquishes the permit: every single-precision worker does so at
     // once, after its allocation when the tensor cores are on.
-    TcState tc{0u, 0u, 0u, false, f.timeout_ns};
+    TcState tc{0u, 0u, 0u, false, f.timeout_ns, f.tc_min_inner};
     const bool use_tc = sizeof(T) == 4 && f.tensor;
     int my_tasks = 0;  // tasks this worker ran (profiling: workers that ran any)
     if constexpr (sizeof(T) == 4) {
@@ -1962,7 +1959,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dataflow(FlowArgs f, LaunchArgs
         const unsigned long long t_alloc = (f.busy && threadIdx.x == 0) ? global_ns() : 0ull;
         if (threadIdx.x < 32) {
             asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
-                         "r"(kTcMaxCols));
+                         "r"(kTcTmemCols));
             asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
         }
         if (threadIdx.x == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_mbar)));
@@ -2103,7 +2100,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dataflow(FlowArgs f, LaunchArgs
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         if (threadIdx.x < 32)
-            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tc.tmem), "r"(kTcMaxCols));
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tc.tmem), "r"(kTcTmemCols));
     }
 }
 

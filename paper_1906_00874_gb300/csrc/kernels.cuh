@@ -56,6 +56,7 @@ struct FlowArgs {
     int64_t scratch_stride;    // elements per worker
     unsigned long long timeout_ns;  // limit of any single wait for a ready task
     int32_t tensor;            // single precision: dense products of ACCUM tasks on the tensor cores
+    int32_t tc_min_inner;      // smallest packed inner size a product takes to the tensor cores
     unsigned long long *busy;  // when profiling: [kind] task nanoseconds, [8 + kind] task count,
                                // [16 + b] / [24 + b] the same for rounded additions of size class b; else null
 };

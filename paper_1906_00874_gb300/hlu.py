@@ -19,7 +19,7 @@ HLU_FP32 = 1          # FP32 factors, FP64 SVD of every truncation core
 HLU_FP32_CORE32 = 2   # FP32 factors, FP32 Jacobi in the truncation cores
 SCHED_DATAFLOW = 0
 SCHED_WAVES = 1
-FLAG_NO_TENSOR = 1    # FP32 factors: dense products on CUDA cores instead of the tensor cores
+FLAG_TENSOR = 1       # FP32 factors: dense products of the factorisation on the tensor cores
 
 STATUS = {0: "HLU_OK", 1: "HLU_EINVAL", 2: "HLU_ENOMEM", 3: "HLU_ESTATE", 4: "HLU_EPIVOT",
           5: "HLU_ERANKCAP", 6: "HLU_ETIMEOUT", 7: "HLU_ECUDA", 8: "HLU_ENUMERIC"}

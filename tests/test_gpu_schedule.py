@@ -24,11 +24,11 @@ def built():
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_dataflow_equals_waves(precision):
-    """Both schedules with the products on CUDA cores (the wave schedule does not use the tensor
-    cores)."""
-    from paper_1906_00874_gb300.hlu import FLAG_NO_TENSOR, SCHED_DATAFLOW, SCHED_WAVES
+    """Both schedules with the products on CUDA cores (the default; the wave schedule does not use
+    the tensor cores)."""
+    from paper_1906_00874_gb300.hlu import SCHED_DATAFLOW, SCHED_WAVES
     p = build_problem(4, 32, 2.0, 1e-4, nrhs=1)
-    h1 = gpu_factor(p, precision=precision, schedule=SCHED_DATAFLOW, flags=FLAG_NO_TENSOR)
+    h1 = gpu_factor(p, precision=precision, schedule=SCHED_DATAFLOW)
     h2 = gpu_factor(p, precision=precision, schedule=SCHED_WAVES)
     r1, o1, d1 = h1.get_factors()
     r2, o2, d2 = h2.get_factors()
@@ -47,11 +47,11 @@ def test_tensor_core_products_are_repeatable_and_match_cuda_cores():
     the CUDA-core products but for threshold flips, and the densified factors agree to the FP32 level
     (or the rank-flip bound 10 eps)."""
     from oracle import build_hmatrix, densify
-    from paper_1906_00874_gb300.hlu import FLAG_NO_TENSOR
+    from paper_1906_00874_gb300.hlu import FLAG_TENSOR
     from gpu_helpers import factors_as_problem
     p = build_problem(4, 32, 2.0, 1e-4, nrhs=1)
-    ht = gpu_factor(p, precision=1)
-    hc = gpu_factor(p, precision=1, flags=FLAG_NO_TENSOR)
+    ht = gpu_factor(p, precision=1, flags=FLAG_TENSOR)
+    hc = gpu_factor(p, precision=1)
     rt, _, dt = ht.get_factors()
     rc, _, _ = hc.get_factors()
     assert np.count_nonzero(rt != rc) <= max(2, len(rt) // 500)
