@@ -4,7 +4,7 @@ This package generates data only (mesh, cluster tree, block tree, compressed
 leaves, right-hand sides).  It holds none of the H-LU arithmetic and is the one
 module that both the CPU oracle and the GPU library consume.
 """
-from .problem import Problem, build_problem  # noqa: F401
+from .problem import Problem, build_problem, build_structure  # noqa: F401
 from .assemble import kernel_block  # noqa: F401
 from .mesh import icosphere, ellipsoid, triangle_data  # noqa: F401
 

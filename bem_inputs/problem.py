@@ -243,6 +243,34 @@ def build_problem(r, leaf, eta, eps, nrhs=1, seed=0, axes=None, cache=True, verb
     return p
 
 
+def build_structure(r, leaf, eta, eps, nrhs=1, seed=0, axes=None, dim=3):
+    """The problem of build_problem without leaf data: geometry, cluster tree (Algorithm 1), the
+    block-tree leaves of Algorithm 2 with every admissible block marked low rank (no cross
+    approximation is tried, so none falls back to a partitioned or dense block), and the
+    right-hand sides.  rank and offset are zero and data is empty: the leaves are to be computed
+    elsewhere (the GPU construction, hlu_bem_build)."""
+    t0 = time.time()
+    if dim == 3:
+        v, f = icosphere(r) if axes is None else ellipsoid(r, axes)
+        centroid, area, lo, hi = triangle_data(v, f)
+    elif dim == 2:
+        centroid, area, lo, hi = ellipse_panels(20 * 4 ** r, (0.5, 0.5) if axes is None else axes)
+    elif dim == 1:
+        centroid, area, lo, hi = interval_cells(20 * 4 ** r)
+    else:
+        raise ValueError(f"dim must be 1, 2 or 3, got {dim}")
+    n = centroid.shape[0]
+    tree = build_cluster_tree(centroid, lo, hi, leaf)
+    bl = build_block_leaves(tree, eta)
+    b = np.asfortranarray(np.random.default_rng(seed).standard_normal((nrhs, n)).T)
+    nl = len(bl)
+    return Problem(n=n, r=r, leaf=leaf, eta=float(eta), eps=float(eps), nrhs=nrhs, seed=seed,
+                   axes=None if axes is None else tuple(float(a) for a in axes), dim=int(dim), tree=tree,
+                   row_cl=bl.row_cl, col_cl=bl.col_cl, kind=bl.kind, rank=np.zeros(nl, dtype=np.int32),
+                   offset=np.zeros(nl, dtype=np.int64), data=np.zeros(0), b=b, centroid=centroid, area=area,
+                   aca_fallbacks=0, build_seconds=time.time() - t0)
+
+
 _ARRAYS = ("row_cl", "col_cl", "kind", "rank", "offset", "data", "b", "centroid", "area")
 _TREE = ("begin", "size", "son0", "son1", "level", "bmin", "bmax", "perm")
 _SCAL = ("n", "r", "leaf", "eta", "eps", "nrhs", "seed", "aca_fallbacks", "build_seconds", "dim")

@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--tensor", action="store_true",
                     help="FP32 factors: dense products of the factorisation on the tensor cores (tcgen05)")
+    ap.add_argument("--no-c3", action="store_true",
+                    help="skip the n = 81920 leg (GMRES(30), eps 1e-6, 64 rhs) reported in the sphere20480 line")
     ap.add_argument("--construct", action="store_true",
                     help="time the construction of the workload's H-matrix on the GPU (hlu_bem_build)")
     return ap.parse_args()
@@ -437,6 +439,14 @@ def run_native(args):
                                                for k, v in ph.items()}
                                        for route, ph in prof["radd_phase"].items()}}
 
+    # ---------------- the n = 81920 configuration (leaves built on the GPU), reported as one key
+    c3 = None
+    if args.workload == WORKLOAD and not args.no_c3:
+        try:
+            c3 = c3_leg(sptr, fp32_peak, steps=2)
+        except Exception as e:  # reported, not fatal
+            c3 = {"error": f"{type(e).__name__}: {e}"}
+
     cpu = None
     if rank == 0:
         try:
@@ -469,7 +479,7 @@ def run_native(args):
             "efac_fp32": efac32, "efac_note": "||A_H - L U||_2 / ||A_H||_2 of each arm's factors, device power "
                                                   "iteration (hlu_factor_error), bound 10 eps",
             "fp64_arm": arm64, "fp32_core32_arm": core32, "e2e": e2e, "gpu_launches": arm32["launches"], "clocks": clk.summary(),
-            "roofline": roof, "cpu_baseline": cpu,
+            "roofline": roof, "cpu_baseline": cpu, "c3_sphere81920": c3,
             "alu_peaks_tflops": {"fp64": fp64_peak, "fp32": fp32_peak},
             "plan": {"tasks": st32["n_tasks"], "waves": st32["n_waves"], "launches_per_factor": st32["n_launches"]},
         }
@@ -478,6 +488,69 @@ def run_native(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def c3_leg(sptr, fp32_peak, steps=2, restart=30):
+    """sphere81920: n = 81920, leaf 64, eta 2, eps 1e-6, 64 rhs.  The block structure is planned on
+    the host (mesh, Algorithms 1 and 2); the leaf data are computed on the GPU (hlu_bem_build: dense
+    leaves, cross approximation and truncation at eps).  One step = FP32 factorisation (FP64 Jacobi
+    SVD in every truncation core) + GMRES(30) in FP64 on A_H to a 1e-10 relative residual for all 64
+    right-hand sides; CUDA events around the steps."""
+    import torch
+
+    from bem_inputs import WORKLOADS, build_structure
+    from paper_1906_00874_gb300 import HLU_FP32
+    from paper_1906_00874_gb300.hlu import BEMBuild, to_device_panel
+    w = dict(WORKLOADS["sphere81920"])
+    t0 = time.perf_counter()
+    s = build_structure(**w)
+    structure_s = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = BEMBuild.from_problem(s)
+    torch.cuda.synchronize()
+    construct_ms = (time.perf_counter() - t0) * 1e3
+    h = g.create(precision=HLU_FP32, stream=sptr, flags=FLAGS)
+    create = h.stats()["create_ms"]
+    b = to_device_panel(s.b)
+    x = torch.zeros_like(b)
+
+    def step():
+        h.factor(w["eps"])
+        return h.solve_gmres(b, x, tol=TOL, restart=restart, max_iter=300)
+    step()
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    out = []
+    for i in range(steps):
+        out.append(step())
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+    st = h.stats()
+    fl = st["model_flops"] + st["solve_flops"]
+    efac = h.factor_error()[0]
+    h.set_profiling(True)
+    step()
+    torch.cuda.synchronize()
+    prof = h.stats()
+    h.set_profiling(False)
+    res = {"workload": "sphere81920: unit sphere, n=81920, leaf 64, eta 2, eps 1e-6, 64 rhs ~ N(0,1) seed 0, "
+                       "GMRES(30) to 1e-10, leaves built on the GPU",
+           "time_to_1e10_ms": sum(per) / len(per), "per_step_ms": per,
+           "factor_ms": prof["kernel_ms"]["dataflow_factor"],
+           "gmres_steps": out[-1][0], "resid": out[-1][1], "efac": efac,
+           "model_gflop_per_step": fl / 1e9, "gflops": fl / (sum(per) / len(per) * 1e-3) / 1e9,
+           "solves_per_s": 64 * steps / (sum(per) * 1e-3),
+           "rank_hist": rank_hist(st), "max_rank": st["max_rank"], "leaves": int(s.n_leaves),
+           "tasks": st["n_tasks"], "device_gb": st["device_bytes"] / 1e9,
+           "host_structure_s": structure_s, "gpu_construct_ms": construct_ms, "create_ms": create,
+           "classes": class_roofline(st, prof, 1, fp32_peak)}
+    h.close()
+    g.close()
+    return res
 
 
 def e2e_arm(p, precision, sptr, steps, flops_step, solver="ir", restart=30):
