@@ -31,12 +31,13 @@ BATCHES = {
 }
 
 
-def batch_specs(count, levels=(3, 4), eps=(1e-4, 1e-6), leaf=32, eta=2.0):
+def batch_specs(count, levels=(3, 4), eps=(1e-4, 1e-6), leaf=32, eta=2.0, leaf_large=64):
     """Keyword arguments of build_problem for each instance of a batch.
 
     Instance i uses default_rng(i): refinement r uniform in `levels`, tolerance
     uniform in `eps`, ellipsoid axes (1, a, b) with a, b uniform in [0.4, 1],
-    one right-hand side drawn from seed i."""
+    one right-hand side drawn from seed i.  Problems with r >= 5 (n >= 20480)
+    use the leaf size `leaf_large`, as the single-problem workloads of that size."""
     import numpy as np
     out = []
     for i in range(count):
@@ -44,13 +45,16 @@ def batch_specs(count, levels=(3, 4), eps=(1e-4, 1e-6), leaf=32, eta=2.0):
         r = int(g.choice(levels))
         e = float(g.choice(eps))
         a, b = (float(v) for v in g.uniform(0.4, 1.0, 2))
-        out.append(dict(r=r, leaf=leaf, eta=eta, eps=e, nrhs=1, seed=i, axes=(1.0, round(a, 6), round(b, 6))))
+        out.append(dict(r=r, leaf=leaf_large if r >= 5 else leaf, eta=eta, eps=e, nrhs=1, seed=i,
+                        axes=(1.0, round(a, 6), round(b, 6))))
     return out
 
 
 # Request streams for the serving loop.
 STREAMS = {
     "serve64": dict(requests=64, repeat=0.3, nrhs=(1, 64), levels=(3, 4), eps=(1e-4, 1e-6), leaf=32, eta=2.0),
+    # with n = 20480 problems too (r = 5, leaf 64 as the single-problem workloads of that size use)
+    "serve64r5": dict(requests=64, repeat=0.3, nrhs=(1, 64), levels=(3, 4, 5), eps=(1e-4, 1e-6), leaf=32, eta=2.0),
 }
 
 

@@ -772,40 +772,54 @@ def run_serve(args):
     build.build()
     rhs = [np.random.default_rng(sd).standard_normal((probs[k].n, c)) for k, c, sd in stream]
 
-    def replay(arrivals):
-        srv = Server(stream=torch.cuda.current_stream().cuda_stream)
+    def replay(arrivals, timeline=False):
+        srv = Server(timeline=timeline)  # a stream per group, half the workers per launch
         reqs = [Request(k, probs[k], b, arrival=float(t), rid=i)
                 for i, ((k, _, _), b, t) in enumerate(zip(stream, rhs, arrivals))]
-        for r in reqs:
-            srv.submit(r)
         torch.cuda.synchronize()
+        ref = torch.cuda.Event(enable_timing=True)
+        ref.record()
         t0 = time.perf_counter()
         srv.clock = lambda: time.perf_counter() - t0
-        pending = len(reqs)
-        while pending:
-            now = srv.clock()
-            nxt = min((r.arrival for r in srv.queue), default=now)
-            if nxt > now:
-                time.sleep(nxt - now)
-            pending -= len(srv.step())
+        srv.serve(reqs)
         makespan = srv.clock()
+        torch.cuda.synchronize()
+        ov = overlap(srv.events, ref) if timeline else None
         srv.close()  # adds the kernel launches of the handles it releases
         st = dict(srv.stats)
         lat = sorted((r.done - r.arrival) * 1e3 for r in reqs)
-        return makespan, lat, st, reqs
+        return makespan, lat, st, reqs, ov
+
+    def overlap(events, ref):
+        """Device time during which a factorisation and a solve of another group were both running,
+        over the factorisations' time (event timestamps on the groups' streams)."""
+        fac = [(ref.elapsed_time(a), ref.elapsed_time(b), g) for k, g, a, b in events if k == "factor"]
+        sol = [(ref.elapsed_time(a), ref.elapsed_time(b), g) for k, g, a, b in events if k == "solve"]
+        both = 0.0
+        for f0, f1, fg in fac:
+            segs = sorted((max(f0, s0), min(f1, s1)) for s0, s1, sg in sol if sg != fg and s0 < f1 and f0 < s1)
+            end = f0
+            for a, b in segs:
+                a = max(a, end)
+                if b > a:
+                    both += b - a
+                    end = b
+        tot = sum(f1 - f0 for f0, f1, _ in fac)
+        return {"factor_ms": tot, "factor_with_solve_ms": both, "fraction": both / tot if tot else 0.0,
+                "factorisations": len(fac), "solves": len(sol)}
 
     zero = np.zeros(len(stream))
     for _ in range(max(1, args.warmup // 3)):
-        cal_t, _, _, _ = replay(zero)
+        cal_t = replay(zero)[0]
     capacity = len(stream) / cal_t
     rate = 0.8 * capacity
     g = np.random.default_rng(0)
     runs = []
     with ClockSampler(local) as clk:
-        for _ in range(max(1, args.steps // 3)):
+        for i in range(max(1, args.steps // 3)):
             arrivals = np.cumsum(g.exponential(1.0 / rate, len(stream)))
             arrivals -= arrivals[0]
-            runs.append(replay(arrivals))
+            runs.append(replay(arrivals, timeline=(i == 0)))
     lat = sorted(x for r in runs for x in r[1])
     mk = sum(r[0] for r in runs)
     st = runs[-1][2]
@@ -826,7 +840,7 @@ def run_serve(args):
                        "parallelism": f"replicas x{world}", "l2": "inputs larger than L2"},
             "capacity_rps": capacity, "arrival_rate_rps": rate,
             "p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99), "mean_ms": float(np.mean(lat)),
-            "server": st, "gpu_launches": int(sum(r[2].get("kernels_launched", 0) for r in runs)),
+            "server": st, "device_overlap": runs[0][4], "gpu_launches": int(sum(r[2].get("kernels_launched", 0) for r in runs)),
             "e2e": {"value": len(stream) * len(runs) / mk, "unit": "requests/s",
                     "h2d_bytes_per_step": int(sum(b.nbytes for b in rhs) + sum(p.data.nbytes for p in probs)),
                     "d2h_bytes_per_step": int(sum(b.nbytes for b in rhs)),

@@ -111,6 +111,11 @@ typedef struct {
                             sequential steps); 0 -> 1024, < 0 -> plain block substitution.
                             The inverses are not counted in the model flops */
     int32_t flags;       /* HLU_FLAG_* bits; 0 for the defaults */
+    int32_t workers;     /* most worker CTAs of one data-flow launch of this handle; 0 -> as many
+                            as are resident on the GPU at once (two per SM).  A smaller number
+                            leaves room for the launches of other handles on other streams to
+                            run at the same time (the serving loop gives each group half) */
+    int32_t reserved_;   /* set to 0 */
 } hlu_opts;
 
 /* hlu_opts.flags */

@@ -69,6 +69,7 @@ struct hlu_ctx {
     int precision = HLU_FP64;   // storage precision of the factors: HLU_FP64 or HLU_FP32
     bool core64 = true;         // FP32 factors: SVD of each truncation core in FP64 (HLU_FP32_CORE32: FP32)
     bool tensor = false;        // FP32 factors: dense products of the factorisation on the tensor cores
+    int max_workers = 0;        // most worker CTAs per data-flow launch (0: all that are resident)
     int schedule = HLU_SCHED_DATAFLOW;
     unsigned long long timeout_ns = 10000000000ull;
     cudaStream_t stream = nullptr;
@@ -185,6 +186,7 @@ int upload_plan(hlu_ctx *h, const Plan &p, DevPlan &d, int kmax) {
     const bool c64 = !dbl && h->core64;
     d.smem = dataflow_smem_bytes(h->pl.max_leaf, dbl ? 8 : elem, std::min(kc, kSmemCore), c64);
     d.workers = dbl ? dataflow_workers<double>(d.smem) : dataflow_workers<float>(d.smem);
+    if (h->max_workers > 0) d.workers = std::min(d.workers, h->max_workers);
     if (!p.radd.empty()) {
         const size_t bytes = size_t(d.workers) * d.scratch_stride * (dbl ? 8 : elem);
         char *sp = nullptr;
@@ -457,6 +459,7 @@ static int create_impl(const hlu_tree *tree, const hlu_blocks *blocks, const hlu
         if (opts->timeout_s > 0.0) h->timeout_ns = (unsigned long long)(opts->timeout_s * 1e9);
         if (opts->inv_block != 0) po.inv_block = opts->inv_block < 0 ? 0 : opts->inv_block;
         h->tensor = (opts->flags & HLU_FLAG_TENSOR) != 0;
+        h->max_workers = std::max(0, opts->workers);
     }
     if (h->precision == HLU_FP32_CORE32) {  // FP32 factors, FP32 Jacobi in the truncation cores
         h->precision = HLU_FP32;

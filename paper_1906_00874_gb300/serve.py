@@ -1,26 +1,34 @@
 """Serving loop for H-LU solves: continuous batching of requests over resident factors.
 
 A request names a problem (an H-matrix, identified by a key) and carries right-hand sides. The server
-keeps factorised problems resident on the device in *groups*: one batched handle
-(hlu_create_batch) per set of problems that were admitted together. Every step
+keeps factorised problems resident on the device in *groups*: one batched handle (hlu_create_batch)
+per set of problems that were admitted together, each group with its own CUDA stream.
 
-1. takes all requests that have arrived;
-2. admits the problems that are not resident as one new group, factorised in one launch with each
-   problem's own eps (hlu_factor_batch); before that, least-recently-used groups are evicted until
-   the new group fits the device-memory budget (the handle's own mem_budget check enforces it);
-3. solves, per group, all its pending requests in one stacked solve (the block-diagonal system, each
-   request's columns in its problem's rows, zeros elsewhere), refined in FP64 to the tolerance for
-   every request on its own;
-4. returns every request's solution.
+Work runs on host threads that drive the library (its calls release the Python interpreter lock), so
+that the device holds several requests' work at once:
 
-Repeated requests for a resident problem therefore cost a solve, not a factorisation. Because the
-stacked system is block diagonal, a request's solution does not depend on the other requests in the
-step (up to the number of refinement steps the stacked tolerance takes).
+* one admission thread creates and factorises new groups in arrival order (each problem with its
+  own eps, hlu_factor_batch).  It evicts least-recently-used idle groups when the device-memory
+  budget is short; when nothing can be evicted yet it waits until a running solve ends and frees a
+  group, and it splits a group that cannot fit on its own;
+* solve threads run, per group, one stacked refined solve of the requests that have arrived for it
+  (the block-diagonal system, each request's columns in its problem's rows, zeros elsewhere, FP64
+  refinement to the tolerance for every request on its own).  A group runs one job at a time, in
+  order: its solves start once its factorisation is done.
+
+Every data-flow launch of a group uses at most `workers` worker CTAs (half of the resident slots by
+default), so a group's factorisation and another group's solve share the GPU instead of queueing
+behind each other. step() only dispatches and collects: requests that arrive while others are on the
+GPU are admitted at once, as slots and memory free up. Because the stacked system is block diagonal, a
+request's solution depends on the other requests of its solve only through the number of refinement
+steps, and every request meets its own residual tolerance.
 """
 from __future__ import annotations
 
 import collections
+import concurrent.futures
 import dataclasses
+import threading
 import time
 
 import numpy as np
@@ -43,38 +51,69 @@ class Request:
     x: np.ndarray | None = None
     done: float | None = None
     refactored: bool = False
+    iters: int = 0
 
 
 class _Group:
-    def __init__(self, handle, keys, sizes):
+    def __init__(self, handle, keys, sizes, stream):
         self.h = handle
         self.keys = list(keys)
         self.offset = dict(zip(keys, np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(int)))
         self.size = dict(zip(keys, sizes))
         self.n = int(sum(sizes))
         self.bytes = handle.stats()["device_bytes"]
+        self.stream = stream
         self.last_used = 0
+        self.busy = 0          # jobs queued or running on the group
+        self.tail = None       # future of its last job (jobs of a group run in order)
 
 
 class Server:
     """Continuous-batching H-LU server over resident factors (see the module docstring)."""
 
     def __init__(self, precision=HLU_FP32, mem_budget=150e9, tol=1e-10, max_iter=30, max_group=64,
-                 stream=None, clock=time.perf_counter, device="cuda", handle_type=HLU):
+                 stream=None, clock=time.perf_counter, device="cuda", handle_type=HLU, workers=None,
+                 solve_threads=2, stream_factory=None, timeline=False):
         self.precision = precision
         self.budget = int(mem_budget)
         self.tol = tol
         self.max_iter = max_iter
         self.max_group = max_group
-        self.stream = stream
         self.clock = clock
         self.device = device
         self.handle_type = handle_type
+        self.workers = self._default_workers() if workers is None else int(workers)
+        self.stream_factory = stream_factory or self._default_stream_factory(stream)
+        self.timeline = timeline
         self.groups: list[_Group] = []
         self.where: dict[object, _Group] = {}
+        self.admitting: dict[object, concurrent.futures.Future] = {}  # key -> future of its group
+        self.waiting: dict[object, list] = collections.defaultdict(list)  # key being admitted -> requests
         self.queue: collections.deque[Request] = collections.deque()
         self.stats = collections.Counter()
+        self.events = []           # (kind, group id, start event, end event) when timeline is on
         self._tick = 0
+        self._lock = threading.RLock()
+        self._freed = threading.Condition(self._lock)
+        self._done: list[Request] = []
+        self._errors: list[BaseException] = []
+        self._admit_pool = concurrent.futures.ThreadPoolExecutor(1, thread_name_prefix="hlu-admit")
+        self._solve_pool = concurrent.futures.ThreadPoolExecutor(solve_threads, thread_name_prefix="hlu-solve")
+
+    def _default_workers(self):
+        if self.device != "cuda":
+            return 0
+        import torch
+        return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+    def _default_stream_factory(self, stream):
+        if self.device != "cuda":
+            return lambda: None
+        import torch
+        if stream is not None:  # one given stream for every group: no device overlap between groups
+            given = stream if isinstance(stream, torch.cuda.Stream) else torch.cuda.ExternalStream(int(stream))
+            return lambda: given
+        return torch.cuda.Stream
 
     # ---------------------------------------------------------------- state
     @property
@@ -88,9 +127,24 @@ class Server:
         self.queue.append(req)
 
     def close(self):
+        self.drain()
+        self._admit_pool.shutdown(wait=True)
+        self._solve_pool.shutdown(wait=True)
         for g in self.groups:
             self._release(g)
         self.groups, self.where = [], {}
+
+    def drain(self):
+        """Wait until every dispatched job has finished; returns the requests completed since the
+        last step() or drain()."""
+        while True:
+            with self._lock:
+                futs = [f for f in self.admitting.values()] + [g.tail for g in self.groups if g.tail is not None]
+            pending = [f for f in futs if not f.done()]
+            if not pending:
+                break
+            concurrent.futures.wait(pending)
+        return self._collect()
 
     def _release(self, g):
         self.stats["kernels_launched"] += g.h.stats().get("kernels_launched", 0)
@@ -103,14 +157,26 @@ class Server:
         self._release(g)
         self.stats["evicted_groups"] += 1
 
+    def _stream_ptr(self, s):
+        if s is None:
+            return None
+        return getattr(s, "cuda_stream", s)
+
+    def _record(self, s):
+        if not self.timeline or s is None or self.device != "cuda" or not hasattr(s, "record_event"):
+            return None
+        import torch
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(s)
+        return e
+
     # ------------------------------------------------------------ admission
-    def _admit(self, problems: dict, keep: set):
-        """Factorise the new problems as groups of at most max_group, evicting LRU groups (never one
-        in `keep`, which this step still solves on) to fit the budget.  A group created here joins
-        `keep` at once and is stamped with the current tick, so a later group of the same step never
-        evicts it (its requests are still to be solved)."""
-        keep = set(keep)
-        keys = list(problems)
+    def _admit_job(self, keys, problems):
+        """Admission thread: create and factorise the groups of `keys` (at most max_group problems
+        each), evicting idle LRU groups to fit the budget, waiting for one to become idle when none
+        is, and halving a group that cannot fit by itself.  Returns the groups."""
+        out = []
+        keys = list(keys)
         while keys:
             part, keys = keys[:self.max_group], keys[self.max_group:]
             while True:
@@ -120,38 +186,87 @@ class Server:
                 except HLUError as e:
                     if e.status != ENOMEM:
                         raise
-                    victims = [v for v in self.groups if not (set(v.keys) & keep)]
-                    if victims:
-                        self._evict(min(victims, key=lambda v: v.last_used))
-                    elif len(part) > 1:  # nothing left to evict: admit fewer problems at a time
+                    with self._lock:
+                        idle = [v for v in self.groups if v.busy == 0]
+                        if idle:
+                            self._evict(min(idle, key=lambda v: v.last_used))
+                            continue
+                        if any(v.busy for v in self.groups):  # memory frees when a solve ends
+                            self._freed.wait(timeout=1.0)
+                            continue
+                    if len(part) > 1:  # nothing to evict and nothing running: fewer at a time
                         keys = part[len(part) // 2:] + keys
                         part = part[:len(part) // 2]
                     else:
                         raise
-            g.last_used = self._tick
-            keep.update(g.keys)
-            self.groups.append(g)
-            for k in g.keys:
-                self.where[k] = g
+            with self._lock:
+                self.groups.append(g)
+                g.last_used = self._tick
+                g.busy += 1  # held until its waiting requests are queued (_admitted)
+                for k in g.keys:
+                    self.where[k] = g
+            out.append(g)
+        return out
+
+    def _admitted(self, fut):
+        """Done-callback of an admission: queue the solves of the requests that waited for its
+        groups and release the groups' admission hold."""
+        if fut.exception() is not None:
+            return
+        with self._lock:
+            for g in fut.result():
+                reqs = []
+                for k in g.keys:
+                    reqs += self.waiting.pop(k, [])
+                    if self.admitting.get(k) is fut:
+                        del self.admitting[k]
+                if reqs:
+                    self._chain_solve(g, reqs)
+                g.busy -= 1
+                self._freed.notify_all()
 
     def _create(self, keys, problems):
         probs = [problems[k] for k in keys]
-        budget = self.budget - self.resident_bytes
+        with self._lock:
+            budget = self.budget - self.resident_bytes
         if budget <= 0:
             raise HLUError(ENOMEM, "device-memory budget exhausted")
-        kw = dict(precision=self.precision, mem_budget=budget, stream=self.stream)
+        stream = self.stream_factory()
+        kw = dict(precision=self.precision, mem_budget=budget, stream=self._stream_ptr(stream))
+        if self.workers:
+            kw["workers"] = self.workers
         H = self.handle_type
         h = H.batch(probs, **kw) if len(probs) > 1 else H.from_problem(probs[0], **kw)
+        e0 = self._record(stream)  # the factorisation's device work only (after the host planning)
         try:
             h.factor([p.eps for p in probs] if len(probs) > 1 else probs[0].eps)
         except Exception:
             h.close()
             raise
-        self.stats["factorised_problems"] += len(probs)
-        self.stats["groups_created"] += 1
-        return _Group(h, keys, [p.n for p in probs])
+        e1 = self._record(stream)
+        g = _Group(h, keys, [p.n for p in probs], stream)
+        with self._lock:
+            self.stats["factorised_problems"] += len(probs)
+            self.stats["groups_created"] += 1
+            if e0 is not None:
+                self.events.append(("factor", id(g), e0, e1))
+        return g
 
     # ---------------------------------------------------------------- solve
+    def _solve_job(self, g: _Group, reqs):
+        """Solve thread: one stacked refined solve of `reqs` on group g (its own stream)."""
+        try:
+            if self.device == "cuda":
+                import torch
+                with torch.cuda.stream(g.stream):
+                    self._solve_group(g, reqs)
+            else:
+                self._solve_group(g, reqs)
+        finally:
+            with self._lock:
+                g.busy -= 1
+                self._freed.notify_all()
+
     def _solve_group(self, g: _Group, reqs):
         import torch
 
@@ -175,40 +290,96 @@ class Server:
             ratio = own[own > 0] / colnorm[c:c + r.b.shape[1]][own > 0]
             if ratio.size:
                 tol = min(tol, self.tol * float(ratio.min()))
+        e0 = self._record(g.stream)
         b = to_device_panel(B, device=self.device)
         x = torch.zeros_like(b)
         it, res = g.h.solve_refined(b, x, tol=tol, max_iter=self.max_iter)
         X = x.cpu().numpy()
+        e1 = self._record(g.stream)
         now = self.clock()
         for r in reqs:
             o, c = g.offset[r.key], col0[id(r)]
             r.x = np.array(X[o:o + g.size[r.key], c:c + r.b.shape[1]])
+            r.iters = it
             r.done = now
-        self.stats["solves"] += 1
-        self.stats["refinement_steps"] += it
-        return it, res
+        with self._lock:
+            self.stats["solves"] += 1
+            self.stats["refinement_steps"] += it
+            if e0 is not None:
+                self.events.append(("solve", id(g), e0, e1))
+            self._done.extend(reqs)
+
+    # --------------------------------------------------------------- driver
+    def _on_error(self, fut):
+        e = fut.exception()
+        if e is not None:
+            with self._lock:
+                self._errors.append(e)
+
+    def _chain_solve(self, g: _Group, reqs, after=None):
+        """Queue a solve of reqs on g after the group's previous job (and `after`, a future)."""
+        prev = [f for f in (g.tail, after) if f is not None]
+
+        def run():
+            for f in prev:
+                f.result()
+            self._solve_job(g, reqs)
+        g.busy += 1
+        g.last_used = self._tick
+        g.tail = self._solve_pool.submit(run)
+        g.tail.add_done_callback(self._on_error)
+
+    def _collect(self):
+        with self._lock:
+            if self._errors:
+                e = self._errors.pop(0)
+                raise e
+            out, self._done = self._done, []
+        self.stats["requests"] += len(out)
+        return out
 
     def step(self, now=None):
-        """Serve every queued request that has arrived by `now` (default: the clock). Returns them."""
+        """Dispatch every queued request that has arrived by `now` (default: the clock) and return
+        the requests whose solutions are ready since the last call (without waiting)."""
         now = self.clock() if now is None else now
         ready = [r for r in self.queue if r.arrival <= now]
-        if not ready:
-            return []
-        self.queue = collections.deque(r for r in self.queue if r.arrival > now)
-        self._tick += 1
-        new = {}
-        for r in ready:
-            if r.key not in self.where and r.key not in new:
-                new[r.key] = r.problem
-                r.refactored = True
-        if new:
-            self._admit(new, keep={r.key for r in ready if r.key in self.where})
-        by_group = collections.defaultdict(list)
-        for r in ready:
-            by_group[id(self.where[r.key])].append(r)
-        for g in self.groups:
-            if id(g) in by_group:
-                g.last_used = self._tick
-                self._solve_group(g, by_group[id(g)])
-        self.stats["requests"] += len(ready)
-        return ready
+        if ready:
+            self.queue = collections.deque(r for r in self.queue if r.arrival > now)
+            with self._lock:
+                self._tick += 1
+                by_group = collections.defaultdict(list)
+                new = {}
+                for r in ready:
+                    if r.key in self.where:
+                        by_group[id(self.where[r.key])].append(r)
+                    else:  # solved once its group exists (the admission's done-callback)
+                        if r.key not in self.admitting and r.key not in new:
+                            new[r.key] = r.problem
+                            r.refactored = True
+                        self.waiting[r.key].append(r)
+                for g in self.groups:
+                    if id(g) in by_group:
+                        self._chain_solve(g, by_group[id(g)])
+                if new:
+                    fut = self._admit_pool.submit(self._admit_job, list(new), new)
+                    for k in new:
+                        self.admitting[k] = fut
+                    fut.add_done_callback(self._on_error)
+                    fut.add_done_callback(self._admitted)
+        return self._collect()
+
+    def serve(self, requests, poll=1e-4):
+        """Submit `requests` (their arrival times on the server clock) and serve them until every
+        one has its solution; returns them in completion order."""
+        for r in requests:
+            self.submit(r)
+        out = []
+        while len(out) < len(requests):
+            now = self.clock()
+            out += self.step(now)
+            if len(out) >= len(requests):
+                break
+            nxt = min((r.arrival for r in self.queue), default=None)
+            wait = poll if nxt is None else max(0.0, min(poll, nxt - now))
+            time.sleep(wait)
+        return out
