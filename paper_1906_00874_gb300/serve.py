@@ -7,10 +7,11 @@ per set of problems that were admitted together, each group with its own CUDA st
 Work runs on host threads that drive the library (its calls release the Python interpreter lock), so
 that the device holds several requests' work at once:
 
-* one admission thread creates and factorises new groups in arrival order (each problem with its
-  own eps, hlu_factor_batch).  It evicts least-recently-used idle groups when the device-memory
-  budget is short; when nothing can be evicted yet it waits until a running solve ends and frees a
-  group, and it splits a group that cannot fit on its own;
+* admission threads create and factorise new groups (each problem with its own eps,
+  hlu_factor_batch), several at once so that their host planning runs in parallel; the creations in
+  flight share the budget left free.  An admission evicts least-recently-used idle groups when the
+  device-memory budget is short; when nothing can be evicted yet it waits until a running job ends
+  and frees memory, and it splits a group that cannot fit on its own;
 * solve threads run, per group, one stacked refined solve of the requests that have arrived for it
   (the block-diagonal system, each request's columns in its problem's rows, zeros elsewhere, FP64
   refinement to the tolerance for every request on its own).  A group runs one job at a time, in
@@ -73,7 +74,7 @@ class Server:
 
     def __init__(self, precision=HLU_FP32, mem_budget=150e9, tol=1e-10, max_iter=30, max_group=64,
                  stream=None, clock=time.perf_counter, device="cuda", handle_type=HLU, workers=None,
-                 solve_threads=2, stream_factory=None, timeline=False):
+                 solve_threads=2, admit_threads=4, stream_factory=None, timeline=False):
         self.precision = precision
         self.budget = int(mem_budget)
         self.tol = tol
@@ -97,7 +98,9 @@ class Server:
         self._freed = threading.Condition(self._lock)
         self._done: list[Request] = []
         self._errors: list[BaseException] = []
-        self._admit_pool = concurrent.futures.ThreadPoolExecutor(1, thread_name_prefix="hlu-admit")
+        self._creating = 0         # creations in flight (they share the free budget)
+        self._reserved = 0         # bytes of budget handed to the creations in flight
+        self._admit_pool = concurrent.futures.ThreadPoolExecutor(admit_threads, thread_name_prefix="hlu-admit")
         self._solve_pool = concurrent.futures.ThreadPoolExecutor(solve_threads, thread_name_prefix="hlu-solve")
 
     def _default_workers(self):
@@ -187,6 +190,9 @@ class Server:
                     if e.status != ENOMEM:
                         raise
                     with self._lock:
+                        if self._creating > 0:  # another creation holds part of the budget
+                            self._freed.wait(timeout=1.0)
+                            continue
                         idle = [v for v in self.groups if v.busy == 0]
                         if idle:
                             self._evict(min(idle, key=lambda v: v.last_used))
@@ -226,11 +232,26 @@ class Server:
                 self._freed.notify_all()
 
     def _create(self, keys, problems):
+        """Create and factorise one group.  Creations run on several admission threads at once (the
+        host planning of one problem does not wait for another's); each takes an equal share of the
+        budget left free by the resident groups and the creations in flight."""
         probs = [problems[k] for k in keys]
         with self._lock:
-            budget = self.budget - self.resident_bytes
-        if budget <= 0:
-            raise HLUError(ENOMEM, "device-memory budget exhausted")
+            free = self.budget - self.resident_bytes - self._reserved
+            budget = free // (self._creating + 1)
+            if budget <= 0:
+                raise HLUError(ENOMEM, "device-memory budget exhausted")
+            self._creating += 1
+            self._reserved += budget
+        try:
+            return self._create_in(keys, probs, budget)
+        finally:
+            with self._lock:
+                self._creating -= 1
+                self._reserved -= budget
+                self._freed.notify_all()
+
+    def _create_in(self, keys, probs, budget):
         stream = self.stream_factory()
         kw = dict(precision=self.precision, mem_budget=budget, stream=self._stream_ptr(stream))
         if self.workers:
