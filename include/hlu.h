@@ -115,7 +115,10 @@ typedef struct {
                             as are resident on the GPU at once (two per SM).  A smaller number
                             leaves room for the launches of other handles on other streams to
                             run at the same time (the serving loop gives each group half) */
-    int32_t reserved_;   /* set to 0 */
+    int32_t temp_reuse;  /* product temporaries of one shape (per problem of a batch) share at most
+                            this many device regions, reused oldest first, the order between the
+                            uses of a region carried by the task graph; 0 -> 16, < 0 -> every
+                            temporary its own region (largest memory, no added dependencies) */
 } hlu_opts;
 
 /* hlu_opts.flags */
@@ -188,6 +191,8 @@ typedef struct {
                                    pass under fixed per-kind task latencies (model, microseconds;
                                    the same weights order the executor's ready tasks) */
     double solve_critical_us;
+    int64_t factor_temp_elems;       /* elements of the factorisation's product temporaries */
+    int64_t factor_temp_peak_elems;  /* largest sum of them in use at one dependency level */
 } hlu_plan_info;
 
 int hlu_plan_info_get(const hlu_tree *tree, const hlu_blocks *blocks, const hlu_opts *opts, hlu_plan_info *out);

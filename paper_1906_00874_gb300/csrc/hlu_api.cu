@@ -458,6 +458,7 @@ static int create_impl(const hlu_tree *tree, const hlu_blocks *blocks, const hlu
         h->schedule = opts->schedule;
         if (opts->timeout_s > 0.0) h->timeout_ns = (unsigned long long)(opts->timeout_s * 1e9);
         if (opts->inv_block != 0) po.inv_block = opts->inv_block < 0 ? 0 : opts->inv_block;
+        po.temp_reuse = opts->temp_reuse >= 0;
         h->tensor = (opts->flags & HLU_FLAG_TENSOR) != 0;
         h->max_workers = std::max(0, opts->workers);
     }
@@ -634,6 +635,7 @@ int plan_only(const hlu_tree *tree, const hlu_blocks *blocks, const hlu_opts *op
         if (opts->rank_cap > 0) po.rank_cap = opts->rank_cap;
         if (opts->nrhs_max > 0) po.nrhs_max = opts->nrhs_max;
         if (opts->inv_block != 0) po.inv_block = opts->inv_block < 0 ? 0 : opts->inv_block;
+        po.temp_reuse = opts->temp_reuse >= 0;
         po.wave_order = opts->schedule == HLU_SCHED_WAVES;
     } else {
         po.wave_order = false;
@@ -653,6 +655,8 @@ int plan_only(const hlu_tree *tree, const hlu_blocks *blocks, const hlu_opts *op
     out->matvec_tasks = pl.mplan.n_tasks;
     out->inverse_blocks = (int64_t)pl.inv_cl.size();
     out->factor_elems = pl.f_elems;
+    out->factor_temp_elems = pl.fplan.temp_elems;
+    out->factor_temp_peak_elems = pl.fplan.temp_peak_elems;
     out->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     out->factor_critical_us = pl.fplan.critical_us;
     out->solve_critical_us = pl.splan.critical_us;

@@ -2,12 +2,18 @@
 // H-LU recursion (Sec. 3.1) into tasks grouped in dependency waves.
 #include "plan.h"
 
+#include <climits>
+
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <map>
 #include <thread>
 #include <utility>
+#include <functional>
+#include <unordered_map>
+#include <queue>
 
 #include "../../include/hlu.h"
 
@@ -38,22 +44,229 @@ int32_t Planner::new_slot(int32_t init) {
     return n_slots++;
 }
 
-View Planner::new_temp(int32_t row_cl, int32_t rows, int32_t cols, int32_t rslot, int32_t cslot) {
+int64_t Planner::plan_alloc(int64_t elems, int32_t temp_obj) {
+    const int64_t off = *arena;
+    *arena = align8(*arena + elems);
+    plan_items.push_back(PlanItem{off, elems, temp_obj});
+    return off;
+}
+
+// A temporary panel (rows x cols, column-major), its own region of the arena while the plan is
+// emitted; relocate_temps later lets temporaries of the same shape and problem whose
+// dependency-level intervals do not overlap share regions.
+View Planner::new_temp(int32_t row_cl, int32_t rows, int32_t cols, int32_t rslot, int32_t cslot,
+                       int32_t owner_cl) {
     View v;
-    v.p.off = *arena;
     v.p.rows = rows;
     v.p.cols = cols;
     v.p.rslot = rslot;
     v.p.cslot = cslot;
     v.p.rs = 1;
     v.p.cs = rows;
-    *arena = align8(*arena + int64_t(rows) * std::max(cols, 1));
-    v.obj = new_obj(row_cl, -1);
     v.r_cl = row_cl;
     v.c_cl = -1;
     v.trans = false;
+    v.obj = new_obj(row_cl, -1);
+    const int64_t elems = int64_t(rows) * std::max(cols, 1);
+    v.p.off = plan_alloc(elems, v.obj);
+    if ((int64_t)temp_size.size() <= v.obj) {
+        temp_size.resize(v.obj + 1, 0);
+        temp_first.resize(v.obj + 1, INT32_MAX);
+        temp_last.resize(v.obj + 1, -1);
+        temp_shape.resize(v.obj + 1, {-1, -1, -1, -1});
+    }
+    temp_size[v.obj] = elems;
+    temp_shape[v.obj] = {owner_cl >= 0 && !inst.empty() ? inst[owner_cl] : -1, row_cl, rows, std::max(cols, 1)};
     return v;
 }
+
+// Lets the product temporaries of plan p share regions: the plan's other allocations (split blocks,
+// inverse blocks) are packed at the start of its range in their order, and the temporaries are laid
+// out after them by their dependency-level intervals (first writer's level to last reader's): in
+// order of first level, a temporary takes a free region of its exact size whose occupant's last
+// level is below its first level, else a new one.  Every offset in the plan's descriptors (and in
+// the stores and inverse blocks made during the plan) is moved accordingly, and for two temporaries
+// that share a region every task that touches the earlier one becomes a predecessor of every task
+// that writes the later one.  Those edges go from a lower level to a higher one, so the graph stays
+// acyclic with the same levels (no longer dependency chain in levels).
+void Planner::relocate_temps(Plan &p) {
+    const size_t ni = plan_items.size();
+    if (ni == 0) return;
+    std::vector<int64_t> noff(ni, -1);
+    int64_t pos = plan_begin;
+    std::vector<size_t> tmp;
+    for (size_t i = 0; i < ni; ++i) {
+        if (plan_items[i].temp_obj < 0) {
+            noff[i] = pos;
+            pos = align8(pos + plan_items[i].size);
+        } else {
+            tmp.push_back(i);
+        }
+    }
+    auto lev = [&](size_t i, bool last) {
+        const int32_t o = plan_items[i].temp_obj;
+        if (temp_last[o] < 0) return 0;  // never touched
+        return last ? temp_last[o] : temp_first[o];
+    };
+    std::stable_sort(tmp.begin(), tmp.end(), [&](size_t a, size_t b) { return lev(a, false) < lev(b, false); });
+    using Occ = std::pair<int32_t, size_t>;  // (last level, item)
+    std::priority_queue<Occ, std::vector<Occ>, std::greater<Occ>> active;
+    // free regions by shape (problem, row cluster, rows, cols): (offset, occupant)
+    std::map<std::array<int32_t, 4>, std::vector<std::pair<int64_t, int32_t>>> free_by_shape;
+    std::vector<std::pair<int32_t, int32_t>> order;  // (earlier temporary, later temporary) sharing a region
+    int64_t top = pos;
+    for (size_t i : tmp) {
+        const int32_t f = lev(i, false);
+        while (!active.empty() && active.top().first < f) {
+            const size_t j = active.top().second;
+            active.pop();
+            free_by_shape[temp_shape[plan_items[j].temp_obj]].emplace_back(noff[j], plan_items[j].temp_obj);
+        }
+        auto &fl = free_by_shape[temp_shape[plan_items[i].temp_obj]];
+        if (!fl.empty()) {
+            noff[i] = fl.back().first;
+            order.emplace_back(fl.back().second, plan_items[i].temp_obj);
+            fl.pop_back();
+        } else {
+            noff[i] = top;
+            top = align8(top + plan_items[i].size);
+        }
+        active.emplace(lev(i, true), i);
+    }
+    // offsets: an offset inside item k (items are in increasing offset order) keeps its distance
+    auto remap = [&](int64_t off) -> int64_t {
+        if (off < plan_begin) return off;
+        size_t lo = 0, hi = ni;
+        while (hi - lo > 1) {
+            const size_t mid = (lo + hi) / 2;
+            if (plan_items[mid].off <= off)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        return noff[lo] + (off - plan_items[lo].off);
+    };
+    for (TGetrf &t : p.getrf) t.off = remap(t.off);
+    for (TTrsm &t : p.trsm) {
+        t.L_off = remap(t.L_off);
+        t.P.off = remap(t.P.off);
+    }
+    for (TProject &t : p.project) {
+        t.F.off = remap(t.F.off);
+        t.X.off = remap(t.X.off);
+        t.T.off = remap(t.T.off);
+    }
+    for (TAccum &t : p.accum) t.out.off = remap(t.out.off);
+    for (Term &t : p.terms) {
+        t.A.off = remap(t.A.off);
+        t.X.off = remap(t.X.off);
+    }
+    for (TRadd &t : p.radd) {
+        t.U_off = remap(t.U_off);
+        t.V_off = remap(t.V_off);
+    }
+    for (Piece &t : p.pieces) {
+        t.U.off = remap(t.U.off);
+        t.V.off = remap(t.V.off);
+    }
+    for (TSplit &t : p.split) {
+        t.srcU.off = remap(t.srcU.off);
+        t.srcV.off = remap(t.srcV.off);
+        t.dstU = remap(t.dstU);
+        t.dstV = remap(t.dstV);
+    }
+    for (Store &st : fstore) {
+        st.D_off = remap(st.D_off);
+        st.U_off = remap(st.U_off);
+        st.V_off = remap(st.V_off);
+    }
+    for (int64_t &o : inv_L_off) o = remap(o);
+    for (int64_t &o : inv_U_off) o = remap(o);
+    *arena = top;
+    if (order.empty()) return;
+    // the touches of every temporary (counting sort by object; a task's touches are in cell order)
+    const size_t nobj = temp_size.size();
+    std::vector<int32_t> tptr(nobj + 1, 0), ttask(touch_obj.size()), tcell(touch_obj.size());
+    std::vector<uint8_t> twr(touch_obj.size());
+    for (int32_t o : touch_obj) tptr[o + 1]++;
+    for (size_t o = 0; o < nobj; ++o) tptr[o + 1] += tptr[o];
+    {
+        std::vector<int32_t> fill(tptr.begin(), tptr.end() - 1);
+        for (size_t e = 0; e < touch_obj.size(); ++e) {
+            const int32_t at = fill[touch_obj[e]]++;
+            ttask[at] = touch_task[e];
+            tcell[at] = touch_cell[e];
+            twr[at] = touch_write[e];
+        }
+    }
+    // per shared region, cell by cell (the two temporaries have the same shape, hence the same
+    // cells): every task that touched the earlier one's cell precedes every writer of the later one's
+    std::vector<std::pair<int32_t, int32_t>> extra;  // (task, predecessor)
+    std::vector<std::vector<int32_t>> by_cell;
+    for (const auto &pr : order) {
+        const int32_t a = pr.first, b = pr.second;
+        const int32_t ncell = objs[a].nr * objs[a].nc;
+        if ((int32_t)by_cell.size() < ncell) by_cell.resize(ncell);
+        for (int32_t c = 0; c < ncell; ++c) by_cell[c].clear();
+        for (int32_t e = tptr[a]; e < tptr[a + 1]; ++e) by_cell[tcell[e]].push_back(ttask[e]);
+        for (int32_t e = tptr[b]; e < tptr[b + 1]; ++e)
+            if (twr[e])
+                for (int32_t t : by_cell[tcell[e]]) extra.emplace_back(ttask[e], t);
+    }
+    // merge into the predecessor lists (CSR), each predecessor once per task (the extra edges
+    // grouped by task with a counting sort)
+    const int64_t nt = p.n_tasks;
+    std::vector<int32_t> xptr(nt + 1, 0), xidx(extra.size());
+    for (const auto &e : extra) xptr[e.first + 1]++;
+    for (int64_t g = 0; g < nt; ++g) xptr[g + 1] += xptr[g];
+    {
+        std::vector<int32_t> fill(xptr.begin(), xptr.end() - 1);
+        for (const auto &e : extra) xidx[fill[e.first]++] = e.second;
+    }
+    std::vector<int32_t> nptr(nt + 1, 0), nidx;
+    nidx.reserve(p.pred_idx.size() + extra.size());
+    std::vector<int32_t> mark(nt, -1);
+    for (int64_t g = 0; g < nt; ++g) {
+        for (int32_t e = p.pred_ptr[g]; e < p.pred_ptr[g + 1]; ++e) {
+            const int32_t t = p.pred_idx[e];
+            if (mark[t] != g) {
+                mark[t] = int32_t(g);
+                nidx.push_back(t);
+            }
+        }
+        for (int32_t e = xptr[g]; e < xptr[g + 1]; ++e) {
+            const int32_t t = xidx[e];
+            if (t != g && mark[t] != g) {
+                mark[t] = int32_t(g);
+                nidx.push_back(t);
+            }
+        }
+        nptr[g + 1] = int32_t(nidx.size());
+    }
+    p.pred_ptr.swap(nptr);
+    p.pred_idx.swap(nidx);
+}
+
+// The largest sum of temporary elements in use at one dependency level (the memory an allocation
+// of regions by non-overlapping level intervals would need; a lower bound for any that adds no level).
+void Planner::temp_levels(Plan &p) const {
+    std::vector<int64_t> delta(size_t(p.n_waves) + 2, 0);
+    int64_t tot = 0;
+    for (size_t o = 0; o < temp_size.size(); ++o) {
+        if (temp_size[o] == 0 || temp_last[o] < 0) continue;
+        tot += temp_size[o];
+        delta[temp_first[o]] += temp_size[o];
+        delta[temp_last[o] + 1] -= temp_size[o];
+    }
+    int64_t cur = 0, peak = 0;
+    for (int64_t d : delta) {
+        cur += d;
+        peak = std::max(peak, cur);
+    }
+    p.temp_elems = tot;
+    p.temp_peak_elems = peak;
+}
+
 
 void Planner::cells_of(const View &v, std::vector<int64_t> &out) const {
     const Obj &o = objs[v.obj];
@@ -74,14 +287,40 @@ void Planner::cells_of(const View &v, std::vector<int64_t> &out) const {
 
 int32_t Planner::emit_views(Kind k, const View *const *reads, size_t nr, const View *const *writes, size_t nw) {
     static thread_local std::vector<int64_t> rc, wc;
+    static thread_local std::vector<size_t> rend, wend;  // end of every view's cells in rc / wc
     rc.clear();
     wc.clear();
-    for (size_t i = 0; i < nr; ++i) cells_of(*reads[i], rc);
-    for (size_t i = 0; i < nw; ++i) cells_of(*writes[i], wc);
+    rend.clear();
+    wend.clear();
+    for (size_t i = 0; i < nr; ++i) {
+        cells_of(*reads[i], rc);
+        rend.push_back(rc.size());
+    }
+    for (size_t i = 0; i < nw; ++i) {
+        cells_of(*writes[i], wc);
+        wend.push_back(wc.size());
+    }
     int32_t dep = -1;
     for (int64_t c : rc) dep = std::max(dep, cell[c].write_wave);
     for (int64_t c : wc) dep = std::max(dep, std::max(cell[c].write_wave, cell[c].read_wave));
     int32_t w = dep + 1;
+    for (size_t i = 0; i < nr + nw; ++i) {  // the level interval and the cells of the temporaries touched
+        const bool wr = i >= nr;
+        const int32_t o = wr ? writes[i - nr]->obj : reads[i]->obj;
+        if (o < (int32_t)temp_size.size() && temp_size[o] > 0) {
+            temp_first[o] = std::min(temp_first[o], w);
+            temp_last[o] = std::max(temp_last[o], w);
+            const std::vector<int64_t> &cv = wr ? wc : rc;
+            const size_t j = wr ? i - nr : i;
+            const size_t b = j ? (wr ? wend : rend)[j - 1] : 0, e = (wr ? wend : rend)[j];
+            for (size_t k = b; k < e; ++k) {
+                touch_obj.push_back(o);
+                touch_cell.push_back(int32_t(cv[k] - objs[o].cell_base));
+                touch_task.push_back(int32_t(P->n_tasks));
+                touch_write.push_back(wr ? 1 : 0);
+            }
+        }
+    }
     for (int64_t c : rc) cell[c].read_wave = std::max(cell[c].read_wave, w);
     for (int64_t c : wc) {
         cell[c].write_wave = w;
@@ -291,7 +530,7 @@ void Planner::hmm(const View &out, double alpha, bool overwrite, Block *M, bool 
         View F = trans ? viewU(m) : viewV(m);
         View Xs = rows(X, trans ? m->t : m->s);
         int32_t krows = F.p.cslot >= 0 ? s.cap : F.p.cols;
-        View T = new_temp(-1, krows, X.p.cols, F.p.cslot, X.p.cslot);
+        View T = new_temp(-1, krows, X.p.cols, F.p.cslot, X.p.cslot, m->t);
         TProject tp{F.p, Xs.p, T.p, -1, -1, -1, -1, no_flops ? 1 : 0, 0};
         P->project.push_back(tp);
         emit(K_PROJECT, {&F, &Xs}, {&T});
@@ -364,14 +603,14 @@ Planner::Prod Planner::product(Block *A, Block *B) {
     if (A->kind == B_LOWRANK) {  // (U_a V_a^T) B = U_a (B^T V_a)^T
         Store &sa = st(A);
         int32_t ws = new_slot(0);
-        View W = new_temp(B->s, cl[B->s].size, sa.cap, -1, ws);
+        View W = new_temp(B->s, cl[B->s].size, sa.cap, -1, ws, B->s);
         hmm(W, 1.0, true, B, true, viewV(A), ws, sa.kslot);
         return Prod{viewU(A), W};
     }
     if (B->kind == B_LOWRANK) {  // A (U_b V_b^T) = (A U_b) V_b^T
         Store &sb = st(B);
         int32_t ws = new_slot(0);
-        View W = new_temp(A->t, cl[A->t].size, sb.cap, -1, ws);
+        View W = new_temp(A->t, cl[A->t].size, sb.cap, -1, ws, A->t);
         hmm(W, 1.0, true, A, false, viewU(B), ws, sb.kslot);
         return Prod{W, viewV(B)};
     }
@@ -380,12 +619,12 @@ Planner::Prod Planner::product(Block *A, Block *B) {
         return Prod{viewD(A), transpose(viewD(B))};  // factors of the product itself
     if (A->kind == B_DENSE && (B->kind == B_PART || tsz <= ssz)) {
         // A B = I_t (B^T A^T)^T with the leaf cluster t on the identity side
-        View W = new_temp(B->s, ssz, tsz, -1, -1);
+        View W = new_temp(B->s, ssz, tsz, -1, -1, B->s);
         hmm(W, 1.0, true, B, true, transpose(viewD(A)));
         return Prod{ident(A->t), W};
     }
     // A B = (A D_B) I_s^T with the leaf cluster s on the identity side
-    View W = new_temp(A->t, tsz, ssz, -1, -1);
+    View W = new_temp(A->t, tsz, ssz, -1, -1, A->t);
     hmm(W, 1.0, true, A, false, viewD(B));
     return Prod{W, ident(B->s)};
 }
@@ -474,10 +713,8 @@ void Planner::addmul(Block *C, double alpha, Block *A, Block *B) {
                 vs.m = cl[ti].size;
                 vs.n = cl[sj].size;
                 vs.cap = std::max(std::min(std::min(vs.m, vs.n), opt.rank_cap), cs.cap);
-                vs.U_off = *arena;
-                *arena = align8(*arena + int64_t(vs.m) * vs.cap);
-                vs.V_off = *arena;
-                *arena = align8(*arena + int64_t(vs.n) * vs.cap);
+                vs.U_off = plan_alloc(int64_t(vs.m) * vs.cap, -1);
+                vs.V_off = plan_alloc(int64_t(vs.n) * vs.cap, -1);
                 vs.kslot = new_slot(0);
                 vs.krank = 0;
                 vs.objU = new_obj(ti, -1);
@@ -622,8 +859,7 @@ void Planner::plan_inverses() {
             F = F->son[side][side];
         }
         for (int up = 0; up < 2; ++up) {
-            const int64_t off = *arena;
-            *arena = align8(*arena + int64_t(nc) * nc);
+            const int64_t off = plan_alloc(int64_t(nc) * nc, -1);
             const int32_t obj = new_obj(c, c);
             (up ? inv_U_off : inv_L_off)[i] = off;
             (up ? inv_objU : inv_objL)[i] = obj;
@@ -740,6 +976,16 @@ void Planner::begin_plan(Plan &p, bool astore_mode, int64_t *bump) {
     std::fill(cell.begin(), cell.end(), CellState{-1, -1, -1, -1});
     rpool_task.clear();
     rpool_next.clear();
+    plan_items.clear();  // every plan (and arena) has its own temporaries
+    plan_begin = *bump;
+    touch_obj.clear();
+    touch_cell.clear();
+    touch_task.clear();
+    touch_write.clear();
+    temp_shape.assign(objs.size(), {-1, -1, -1, -1});
+    temp_size.assign(objs.size(), 0);
+    temp_first.assign(objs.size(), INT32_MAX);
+    temp_last.assign(objs.size(), -1);
 }
 
 // Sorts a kind's tasks by wave (stable counting sort: waves are small integers); returns the new
@@ -1158,6 +1404,8 @@ int Planner::plan_all() {
         choose_inverses(0, std::max(opt.inv_block, max_leaf));
         plan_inverses();
     }
+    temp_levels(fplan);
+    if (opt.temp_reuse) relocate_temps(fplan);
     finalize_alloc(fplan, &f_elems);
     finalize_graph(fplan);
     f_solve_off = f_elems;

@@ -17,6 +17,7 @@
 #pragma once
 #include <stdint.h>
 
+#include <array>
 #include <initializer_list>
 #include <string>
 #include <vector>
@@ -90,6 +91,9 @@ struct Plan {
     int64_t scratch_base = 0, scratch_elems = 0;
     int32_t max_kcap = 0;
     double critical_us = 0.0;  // longest path of the graph under the per-kind task latencies (µs)
+    // product temporaries: elements in all, and the largest sum over one dependency level of the
+    // temporaries in use at that level (from their first writer's level to their last reader's)
+    int64_t temp_elems = 0, temp_peak_elems = 0;
 };
 
 struct PlanOptions {
@@ -102,6 +106,8 @@ struct PlanOptions {
     int32_t inv_block = 1024; // the largest diagonal blocks of at most this order (at least the
                              // largest leaf) are inverted after the factorisation, and the solve
                              // applies the inverses as products; 0: plain block substitution
+    bool temp_reuse = true;   // the factorisation's product temporaries share device regions by
+                             // dependency-level intervals (relocate_temps); false: each its own region
 };
 
 class Planner {
@@ -178,7 +184,27 @@ private:
 
     int32_t new_obj(int32_t row_cl, int32_t col_cl, int32_t nr_if_none = 1);
     int32_t new_slot(int32_t init);
-    View new_temp(int32_t row_cl, int32_t rows, int32_t cols, int32_t rslot, int32_t cslot);
+    // owner_cl: a cluster of the problem (of a batch) the temporary belongs to
+    View new_temp(int32_t row_cl, int32_t rows, int32_t cols, int32_t rslot, int32_t cslot, int32_t owner_cl);
+    // Allocations of the current plan in the arena, in bump order (temp_obj >= 0: a product
+    // temporary), and the tasks that touch each cell of each temporary (object, cell within the
+    // object, task, written).
+    struct PlanItem {
+        int64_t off, size;
+        int32_t temp_obj;
+    };
+    std::vector<PlanItem> plan_items;
+    int64_t plan_begin = 0;
+    std::vector<int32_t> touch_obj, touch_cell, touch_task;
+    std::vector<uint8_t> touch_write;
+    std::vector<std::array<int32_t, 4>> temp_shape;  // per temporary object: problem, row cluster, rows, cols
+    int64_t plan_alloc(int64_t elems, int32_t temp_obj);
+    // per object: its elements when it is a temporary of the current plan (else 0), and the first and
+    // last dependency level of a task that touches it
+    std::vector<int64_t> temp_size;
+    std::vector<int32_t> temp_first, temp_last;
+    void temp_levels(Plan &p) const;
+    void relocate_temps(Plan &p);
     void cells_of(const View &v, std::vector<int64_t> &out) const;
     int32_t emit_views(Kind k, const View *const *reads, size_t nr, const View *const *writes, size_t nw);
     int32_t emit(Kind k, std::initializer_list<const View *> reads, std::initializer_list<const View *> writes) {

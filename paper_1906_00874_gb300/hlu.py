@@ -57,24 +57,25 @@ class _Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("rank_cap", ctypes.c_int32), ("nrhs_max", ctypes.c_int32),
                 ("schedule", ctypes.c_int32), ("mem_budget", ctypes.c_int64), ("timeout_s", ctypes.c_double),
                 ("inv_block", ctypes.c_int32), ("flags", ctypes.c_int32), ("workers", ctypes.c_int32),
-                ("reserved_", ctypes.c_int32)]
+                ("temp_reuse", ctypes.c_int32)]
 
 
 class _PlanInfo(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in ("factor_tasks", "factor_edges", "factor_levels", "solve_tasks",
                                               "solve_levels", "matvec_tasks", "inverse_blocks", "factor_elems")] + \
                [("plan_ms", ctypes.c_double), ("factor_critical_us", ctypes.c_double),
-                ("solve_critical_us", ctypes.c_double)]
+                ("solve_critical_us", ctypes.c_double), ("factor_temp_elems", ctypes.c_int64),
+                ("factor_temp_peak_elems", ctypes.c_int64)]
 
 
-def plan_info(problems, rank_cap=0, nrhs_max=0, inv_block=0, schedule=SCHED_DATAFLOW):
+def plan_info(problems, rank_cap=0, nrhs_max=0, inv_block=0, schedule=SCHED_DATAFLOW, temp_reuse=0):
     """Sizes of the task graphs hlu_create (one problem) or hlu_create_batch (a list) would build:
     validation and planning on the host only (hlu_plan_info_get / hlu_plan_info_batch)."""
     lib = load()
     many = isinstance(problems, (list, tuple))
     descs = [_describe(p.n, p.tree.perm, p.tree.begin, p.tree.size, p.tree.son0, p.tree.son1, p.row_cl, p.col_cl,
                        p.kind, p.rank, p.offset, p.data) for p in (problems if many else [problems])]
-    opts = _Opts(0, int(rank_cap), int(nrhs_max), int(schedule), 0, 0.0, int(inv_block), 0, 0, 0)
+    opts = _Opts(0, int(rank_cap), int(nrhs_max), int(schedule), 0, 0.0, int(inv_block), 0, 0, int(temp_reuse))
     info = _PlanInfo()
     if many:
         trees = (_Tree * len(descs))(*[d[0] for d in descs])
@@ -249,17 +250,17 @@ class HLU:
 
     def __init__(self, n, perm, begin, size, son0, son1, row_cl, col_cl, kind, rank, offset, data,
                  precision=HLU_FP64, rank_cap=0, nrhs_max=0, mem_budget=0, stream=None,
-                 schedule=SCHED_DATAFLOW, timeout_s=0.0, inv_block=0, flags=0, workers=0):
+                 schedule=SCHED_DATAFLOW, timeout_s=0.0, inv_block=0, flags=0, workers=0, temp_reuse=0):
         tree, blocks, keep = _describe(n, perm, begin, size, son0, son1, row_cl, col_cl, kind, rank, offset, data)
         self._open(1, ctypes.byref(tree), ctypes.byref(blocks), [int(n)], int(blocks.n_leaves), precision, rank_cap,
-                   nrhs_max, mem_budget, stream, schedule, timeout_s, inv_block, flags, workers)
+                   nrhs_max, mem_budget, stream, schedule, timeout_s, inv_block, flags, workers, temp_reuse)
 
     def _open(self, count, trees, blocks, sizes, n_leaves, precision, rank_cap, nrhs_max, mem_budget, stream,
-              schedule, timeout_s, inv_block=0, flags=0, workers=0):
+              schedule, timeout_s, inv_block=0, flags=0, workers=0, temp_reuse=0):
         lib = load()
         self._h = ctypes.c_void_p()
         opts = _Opts(int(precision), int(rank_cap), int(nrhs_max), int(schedule), int(mem_budget), float(timeout_s),
-                     int(inv_block), int(flags), int(workers), 0)
+                     int(inv_block), int(flags), int(workers), int(temp_reuse))
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
@@ -278,7 +279,7 @@ class HLU:
 
     @classmethod
     def batch(cls, problems, precision=HLU_FP64, rank_cap=0, nrhs_max=0, mem_budget=0, stream=None,
-              schedule=SCHED_DATAFLOW, timeout_s=0.0, inv_block=0, flags=0, workers=0):
+              schedule=SCHED_DATAFLOW, timeout_s=0.0, inv_block=0, flags=0, workers=0, temp_reuse=0):
         """One handle for several independent problems (hlu_create_batch): the block-diagonal
         system whose rows are the problems' rows in turn (offsets of self.sizes)."""
         descs = [_describe(p.n, p.tree.perm, p.tree.begin, p.tree.size, p.tree.son0, p.tree.son1, p.row_cl,
@@ -289,7 +290,8 @@ class HLU:
         blocks = (_Blocks * len(descs))(*[d[1] for d in descs])
         self = cls.__new__(cls)
         self._open(len(descs), trees, blocks, [p.n for p in problems], sum(int(d[1].n_leaves) for d in descs),
-                   precision, rank_cap, nrhs_max, mem_budget, stream, schedule, timeout_s, inv_block, flags, workers)
+                   precision, rank_cap, nrhs_max, mem_budget, stream, schedule, timeout_s, inv_block, flags, workers,
+                   temp_reuse)
         return self
 
     @property
@@ -470,13 +472,13 @@ class BEMBuild:
         return out[:self.data_len]
 
     def create(self, precision=HLU_FP64, rank_cap=0, nrhs_max=0, mem_budget=0, stream=None,
-               schedule=SCHED_DATAFLOW, timeout_s=0.0, inv_block=0, flags=0, workers=0):
+               schedule=SCHED_DATAFLOW, timeout_s=0.0, inv_block=0, flags=0, workers=0, temp_reuse=0):
         """An HLU handle on this matrix (hlu_create_bem)."""
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
         opts = _Opts(int(precision), int(rank_cap), int(nrhs_max), int(schedule), int(mem_budget), float(timeout_s),
-                     int(inv_block), int(flags), int(workers), 0)
+                     int(inv_block), int(flags), int(workers), int(temp_reuse))
         h = HLU.__new__(HLU)
         h._h = ctypes.c_void_p()
         h.n, h.sizes, h.n_leaves, h.precision = self.n, (self.n,), self.n_leaves, int(precision)
