@@ -510,7 +510,7 @@ def c3_leg(sptr, fp32_peak, steps=2, restart=30):
     g = BEMBuild.from_problem(s)
     torch.cuda.synchronize()
     construct_ms = (time.perf_counter() - t0) * 1e3
-    h = g.create(precision=HLU_FP32, stream=sptr, flags=FLAGS)
+    h = g.create(precision=HLU_FP32, stream=sptr, flags=FLAGS, temp_reuse=1)
     create = h.stats()["create_ms"]
     b = to_device_panel(s.b)
     x = torch.zeros_like(b)

@@ -115,10 +115,12 @@ typedef struct {
                             as are resident on the GPU at once (two per SM).  A smaller number
                             leaves room for the launches of other handles on other streams to
                             run at the same time (the serving loop gives each group half) */
-    int32_t temp_reuse;  /* product temporaries of one shape (per problem of a batch) share at most
-                            this many device regions, reused oldest first, the order between the
-                            uses of a region carried by the task graph; 0 -> 16, < 0 -> every
-                            temporary its own region (largest memory, no added dependencies) */
+    int32_t temp_reuse;  /* > 0: the factorisation's product temporaries of one shape (and one
+                            problem of a batch) share device regions when their dependency-level
+                            intervals do not overlap (tasks of the earlier use precede writers of
+                            the later one, cell by cell; the graph keeps its levels).  About half
+                            the device memory at n = 20480, for a few percent of factorisation
+                            time and a longer planning.  0 (default): every temporary its own region */
 } hlu_opts;
 
 /* hlu_opts.flags */

@@ -116,6 +116,10 @@ namespace {
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? HLU_OK : HLU_ECUDA; }
 
+// Device-to-host copy ordered on the handle's stream (not the legacy default stream, which would
+// also wait for the work of other handles on other streams).
+cudaError_t d2h(hlu_ctx *h, void *dst, const void *src, size_t bytes);
+
 template <class X>
 int dalloc(hlu_ctx *h, X **p, size_t count) {
     *p = nullptr;
@@ -328,6 +332,12 @@ void run_plan(hlu_ctx *h, const DevPlan &d, void *arena, double *flops) {
     h->kernels_launched += (int64_t)d.launches.size();
 }
 
+cudaError_t d2h(hlu_ctx *h, void *dst, const void *src, size_t bytes) {
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return e;
+}
+
 int read_error(hlu_ctx *h) {
     cudaError_t e = cudaGetLastError();  // launch-time errors first
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -337,7 +347,7 @@ int read_error(hlu_ctx *h) {
     }
     if (h->profiling) collect_profile(h);
     long long w[4];
-    if (cudaMemcpy(w, h->err, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess) return HLU_ECUDA;
+    if (d2h(h, w, h->err, sizeof(w)) != cudaSuccess) return HLU_ECUDA;
     std::memcpy(h->last_err, w, sizeof(w));
     switch ((int)w[0]) {
         case DE_OK: return HLU_OK;
@@ -458,7 +468,7 @@ static int create_impl(const hlu_tree *tree, const hlu_blocks *blocks, const hlu
         h->schedule = opts->schedule;
         if (opts->timeout_s > 0.0) h->timeout_ns = (unsigned long long)(opts->timeout_s * 1e9);
         if (opts->inv_block != 0) po.inv_block = opts->inv_block < 0 ? 0 : opts->inv_block;
-        po.temp_reuse = opts->temp_reuse >= 0;
+        po.temp_reuse = opts->temp_reuse > 0;
         h->tensor = (opts->flags & HLU_FLAG_TENSOR) != 0;
         h->max_workers = std::max(0, opts->workers);
     }
@@ -635,7 +645,7 @@ int plan_only(const hlu_tree *tree, const hlu_blocks *blocks, const hlu_opts *op
         if (opts->rank_cap > 0) po.rank_cap = opts->rank_cap;
         if (opts->nrhs_max > 0) po.nrhs_max = opts->nrhs_max;
         if (opts->inv_block != 0) po.inv_block = opts->inv_block < 0 ? 0 : opts->inv_block;
-        po.temp_reuse = opts->temp_reuse >= 0;
+        po.temp_reuse = opts->temp_reuse > 0;
         po.wave_order = opts->schedule == HLU_SCHED_WAVES;
     } else {
         po.wave_order = false;
@@ -1008,7 +1018,7 @@ int hlu_get_factors(hlu_t h, int32_t *rank_out, int64_t *offsets_out, double *da
     std::vector<int32_t> kd(pl.n_slots);
     int st = cuda_status(cudaStreamSynchronize(h->stream));
     if (st) return st;
-    if ((st = cuda_status(cudaMemcpy(kd.data(), h->kdyn, sizeof(int32_t) * pl.n_slots, cudaMemcpyDeviceToHost))))
+    if ((st = cuda_status(d2h(h, kd.data(), h->kdyn, sizeof(int32_t) * pl.n_slots))))
         return st;
     int64_t leaf_end = 0;
     for (int64_t l = 0; l < pl.n_leaves; ++l) {
@@ -1018,10 +1028,10 @@ int hlu_get_factors(hlu_t h, int32_t *rank_out, int64_t *offsets_out, double *da
     }
     std::vector<double> buf(leaf_end);
     if (h->precision == HLU_FP64) {
-        st = cuda_status(cudaMemcpy(buf.data(), h->farena, sizeof(double) * leaf_end, cudaMemcpyDeviceToHost));
+        st = cuda_status(d2h(h, buf.data(), h->farena, sizeof(double) * leaf_end));
     } else {
         std::vector<float> fb(leaf_end);
-        st = cuda_status(cudaMemcpy(fb.data(), h->farena, sizeof(float) * leaf_end, cudaMemcpyDeviceToHost));
+        st = cuda_status(d2h(h, fb.data(), h->farena, sizeof(float) * leaf_end));
         for (int64_t i = 0; i < leaf_end; ++i) buf[i] = fb[i];
     }
     if (st) return st;
@@ -1072,14 +1082,14 @@ int hlu_get_stats(hlu_t h, hlu_stats *o) {
     }
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return HLU_ECUDA;
     double fl[16];
-    if (cudaMemcpy(fl, h->flops, sizeof(fl), cudaMemcpyDeviceToHost) != cudaSuccess) return HLU_ECUDA;
+    if (d2h(h, fl, h->flops, sizeof(fl)) != cudaSuccess) return HLU_ECUDA;
     for (int k = 0; k < 8; ++k) {
         o->flops_by_kind[k] = fl[k];
         o->model_flops += fl[k];
         o->solve_flops += fl[8 + k];
     }
     unsigned long long bz[kBusyWords];
-    if (cudaMemcpy(bz, h->busy, sizeof(bz), cudaMemcpyDeviceToHost) != cudaSuccess) return HLU_ECUDA;
+    if (d2h(h, bz, h->busy, sizeof(bz)) != cudaSuccess) return HLU_ECUDA;
     for (int k = 0; k < 8; ++k) {
         o->task_busy_ms[k] = bz[k] * 1e-6;
         o->task_count[k] = (int64_t)bz[8 + k];
@@ -1094,7 +1104,7 @@ int hlu_get_stats(hlu_t h, hlu_stats *o) {
     }
     if (h->factored) {
         std::vector<int32_t> kd(h->pl.n_slots);
-        if (cudaMemcpy(kd.data(), h->kdyn, sizeof(int32_t) * h->pl.n_slots, cudaMemcpyDeviceToHost) == cudaSuccess)
+        if (d2h(h, kd.data(), h->kdyn, sizeof(int32_t) * h->pl.n_slots) == cudaSuccess)
             for (int64_t l = 0; l < h->pl.n_leaves; ++l)
                 if (h->pl.fstore[l].kslot >= 0) {
                     const int32_t k = kd[h->pl.fstore[l].kslot];
@@ -1171,7 +1181,9 @@ int hlu_set_profiling(hlu_t h, int32_t on) {
         h->prof_ms[k] = 0.0;
         h->prof_count[k] = 0;
     }
-    if (cudaMemset(h->busy, 0, kBusyWords * sizeof(unsigned long long)) != cudaSuccess) return HLU_ECUDA;
+    if (cudaMemsetAsync(h->busy, 0, kBusyWords * sizeof(unsigned long long), h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return HLU_ECUDA;
     return HLU_OK;
 }
 

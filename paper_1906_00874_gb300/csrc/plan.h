@@ -106,7 +106,7 @@ struct PlanOptions {
     int32_t inv_block = 1024; // the largest diagonal blocks of at most this order (at least the
                              // largest leaf) are inverted after the factorisation, and the solve
                              // applies the inverses as products; 0: plain block substitution
-    bool temp_reuse = true;   // the factorisation's product temporaries share device regions by
+    bool temp_reuse = false;  // the factorisation's product temporaries share device regions by
                              // dependency-level intervals (relocate_temps); false: each its own region
 };
 

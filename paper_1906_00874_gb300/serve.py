@@ -254,6 +254,8 @@ class Server:
     def _create_in(self, keys, probs, budget):
         stream = self.stream_factory()
         kw = dict(precision=self.precision, mem_budget=budget, stream=self._stream_ptr(stream))
+        if self.device == "cuda":
+            kw["temp_reuse"] = 1  # resident groups: half the memory per problem
         if self.workers:
             kw["workers"] = self.workers
         H = self.handle_type

@@ -62,3 +62,18 @@ def test_variants_plan(case):
     assert info["factor_tasks"] > 0 and info["inverse_blocks"] >= 1
     if case["eta"] == 0.0:
         assert (p.kind == 0).all()
+
+
+def test_temporaries_sharing_regions_keep_the_levels_and_shrink_the_arena(prob1280):
+    """temp_reuse: product temporaries whose dependency-level intervals do not overlap share regions.
+    The graph keeps its number of levels (the added orderings go from a lower level to a higher
+    one), the factor arena shrinks, and the temporaries' level peak bounds what they need."""
+    from paper_1906_00874_gb300.hlu import plan_info
+    off = plan_info(prob1280)
+    on = plan_info(prob1280, temp_reuse=1)
+    assert on["factor_levels"] == off["factor_levels"] and on["factor_tasks"] == off["factor_tasks"]
+    assert on["factor_edges"] >= off["factor_edges"]
+    assert on["factor_elems"] < off["factor_elems"]
+    saved = off["factor_elems"] - on["factor_elems"]
+    assert 0 < off["factor_temp_peak_elems"] <= off["factor_temp_elems"]
+    assert saved <= off["factor_temp_elems"] - off["factor_temp_peak_elems"]

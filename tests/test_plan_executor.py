@@ -32,7 +32,7 @@ def executor(tmp_path_factory):
     return lib
 
 
-def _run(lib, p, eps, inv_block, seed, inst=None):
+def _run(lib, p, eps, inv_block, seed, inst=None, temp_reuse=0):
     t = p.tree
     keep = []
 
@@ -52,7 +52,7 @@ def _run(lib, p, eps, inv_block, seed, inst=None):
         ctypes.c_int32(inv_block), ctypes.c_uint64(seed), out.ctypes.data_as(ctypes.c_void_p),
         off.ctypes.data_as(ctypes.c_void_p), rank.ctypes.data_as(ctypes.c_void_p), b.ctypes.data_as(ctypes.c_void_p),
         ctypes.c_int32(b.shape[1]), None if inst is None else ptr(inst, np.int32),
-        ctypes.c_int32(0 if inst is None else int(np.max(inst)) + 1))
+        ctypes.c_int32(0 if inst is None else int(np.max(inst)) + 1), ctypes.c_int32(temp_reuse))
     assert st == 0, st
     q = copy.copy(p)
     q.rank, q.offset, q.data = rank, off, out
@@ -64,10 +64,12 @@ def oracle1280(prob1280):
     return HLUOracle(prob1280, prob1280.eps).factor()
 
 
-@pytest.mark.parametrize("inv_block,seed", [(-1, 1), (0, 2), (64, 3)])
-def test_task_lists_reproduce_the_oracle(executor, prob1280, oracle1280, inv_block, seed):
+@pytest.mark.parametrize("inv_block,seed,temp_reuse", [(-1, 1, 0), (0, 2, 0), (64, 3, 0), (0, 4, 1), (-1, 5, 1)])
+def test_task_lists_reproduce_the_oracle(executor, prob1280, oracle1280, inv_block, seed, temp_reuse):
+    """With temp_reuse the product temporaries share regions by dependency-level intervals; a missing
+    order between two uses of a region would corrupt the factors in some random order."""
     p, o = prob1280, oracle1280
-    q, x = _run(executor, p, p.eps, inv_block, seed)
+    q, x = _run(executor, p, p.eps, inv_block, seed, temp_reuse=temp_reuse)
     ranks_o = {l.leaf_id: l.rank for l in o.A.leaves() if l.kind == "lowrank"}
     assert all(int(q.rank[i]) == k for i, k in ranks_o.items())
     amax = np.max(np.abs(densify(build_hmatrix(p))))
@@ -146,11 +148,11 @@ def test_batch_task_lists_equal_the_problems_own(executor):
                                                                     axes=(1.0, 0.6, 0.4)),
              build_problem(2, 32, 2.0, 1e-4, nrhs=2, seed=2, axes=(1.0, 0.8, 0.5))]
     f = _Forest(probs)
-    for inv_block in (-1, 0):
-        qb, xb = _run(executor, f, 1e-4, inv_block, 7, inst=f.inst)
+    for inv_block, reuse in ((-1, 0), (0, 0), (0, 1)):
+        qb, xb = _run(executor, f, 1e-4, inv_block, 7, inst=f.inst, temp_reuse=reuse)
         row = 0
         for i, p in enumerate(probs):
-            q, x = _run(executor, p, 1e-4, inv_block, 11 + i)
+            q, x = _run(executor, p, 1e-4, inv_block, 11 + i, temp_reuse=reuse)
             lo = f.leaf0[i]
             assert np.array_equal(qb.rank[lo:lo + p.n_leaves], q.rank)
             for l in range(p.n_leaves):
