@@ -2217,6 +2217,12 @@ void launch_kind(int kind, const void *tasks, const Term *terms, const Piece *pi
     }
 }
 
+template <class K>
+static bool max_shared_carveout(K kernel) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                cudaSharedmemCarveoutMaxShared) == cudaSuccess;
+}
+
 // Lets a kernel use all of the opt-in shared memory beside its static share.
 template <class K>
 static bool allow_dynamic_smem(K kernel, int optin) {
@@ -2237,6 +2243,19 @@ bool set_kernel_attributes() {
     ok = allow_dynamic_smem(k_project<T>, optin) && ok;
     ok = allow_dynamic_smem(k_accum<T>, optin) && ok;
     ok = allow_dynamic_smem(k_dataflow<T>, optin) && ok;
+    // One split of the unified L1 (all of it as shared memory) for every kernel that runs between
+    // or beside data-flow launches: blocks of kernels with different splits do not share an SM, so a
+    // small kernel of one handle (permutation, refinement step) would otherwise wait until another
+    // handle's persistent launch on another stream has left the SMs.
+    ok = max_shared_carveout(k_dataflow<T>) && ok;
+    ok = max_shared_carveout(k_reset<T>) && ok;
+    ok = max_shared_carveout(k_to_work<T>) && ok;
+    ok = max_shared_carveout(k_add_from_work<T>) && ok;
+    ok = max_shared_carveout(k_permute<double, double>) && ok;
+    ok = max_shared_carveout(k_permute<double, float>) && ok;
+    ok = max_shared_carveout(k_permute<float, double>) && ok;
+    ok = max_shared_carveout(k_set_slot) && ok;
+    ok = max_shared_carveout(k_residual) && ok;
     cudaGetLastError();  // a failure is reported through the return value, not left pending
     return ok;
 }

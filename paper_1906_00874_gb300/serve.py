@@ -314,8 +314,8 @@ class Server:
             if ratio.size:
                 tol = min(tol, self.tol * float(ratio.min()))
         e0 = self._record(g.stream)
-        b = to_device_panel(B, device=self.device)
-        x = torch.zeros_like(b)
+        b = to_device_panel(B, device=self.device)  # a host-to-device copy, no kernel
+        x = torch.empty_like(b)  # written by the refinement (which starts from zero itself)
         it, res = g.h.solve_refined(b, x, tol=tol, max_iter=self.max_iter)
         X = x.cpu().numpy()
         e1 = self._record(g.stream)
