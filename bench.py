@@ -773,7 +773,7 @@ def run_serve(args):
     rhs = [np.random.default_rng(sd).standard_normal((probs[k].n, c)) for k, c, sd in stream]
 
     def replay(arrivals, timeline=False):
-        srv = Server(timeline=timeline)  # a stream per group, half the workers per launch
+        srv = Server(timeline=timeline)  # a stream per group, half the workers per launch, groups of <= 16
         reqs = [Request(k, probs[k], b, arrival=float(t), rid=i)
                 for i, ((k, _, _), b, t) in enumerate(zip(stream, rhs, arrivals))]
         torch.cuda.synchronize()

@@ -358,6 +358,14 @@ int hlu_get_stats(hlu_t h, hlu_stats *out);
  * opts.mem_budget).  HLU_ESTATE before a successful hlu_factor. */
 int hlu_factor_error(hlu_t h, const double *x0_dev, int32_t iters, double rtol, double *efac, double *norm_a);
 
+/* Launch settings of an existing handle (no re-planning): `workers` caps the worker CTAs of
+ * every data-flow launch (0 -> as many as the handle was created for; a larger value is
+ * clamped to that), `flags` takes HLU_FLAG_TENSOR (the other HLU_FLAG_* bits are ignored).
+ * Waits for the handle's stream.  The library's tuner (paper_1906_00874_gb300.autotune) times
+ * candidate settings with it.  hlu_get_launch reads the factorisation's settings back. */
+int hlu_set_launch(hlu_t h, int32_t workers, int32_t flags);
+int hlu_get_launch(hlu_t h, int32_t *workers, int32_t *flags);
+
 /* Failure injection for tests of the timeout path (no counterpart in the paper):
  * with on != 0, the next data-flow factorisation of the handle gets one task
  * (the last of its graph) whose in-degree is one more than its predecessors

@@ -41,7 +41,8 @@ struct DevPlan {
     int64_t scratch_stride = 0;
     void *core_scratch = nullptr;  // cores of rounded additions above kSmemCore (global)
     int64_t core_stride = 0;
-    int workers = 0;
+    int workers = 0;          // worker CTAs of a launch (at most workers_alloc)
+    int workers_alloc = 0;    // workers the per-worker scratch was allocated for
     size_t smem = 0;
 };
 
@@ -191,6 +192,7 @@ int upload_plan(hlu_ctx *h, const Plan &p, DevPlan &d, int kmax) {
     d.smem = dataflow_smem_bytes(h->pl.max_leaf, dbl ? 8 : elem, std::min(kc, kSmemCore), c64);
     d.workers = dbl ? dataflow_workers<double>(d.smem) : dataflow_workers<float>(d.smem);
     if (h->max_workers > 0) d.workers = std::min(d.workers, h->max_workers);
+    d.workers_alloc = d.workers;
     if (!p.radd.empty()) {
         const size_t bytes = size_t(d.workers) * d.scratch_stride * (dbl ? 8 : elem);
         char *sp = nullptr;
@@ -1164,6 +1166,22 @@ int hlu_factor_error(hlu_t h, const double *x0, int32_t iters, double rtol, doub
     h->kernels_launched += e.launched;
     if (st == HLU_OK) st = read_error(h);
     return st;
+}
+
+int hlu_set_launch(hlu_t h, int32_t workers, int32_t flags) {
+    if (!h || workers < 0) return HLU_EINVAL;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return HLU_ECUDA;
+    for (DevPlan *d : {&h->fp, &h->sp, &h->mp})
+        d->workers = workers > 0 ? std::min(workers, d->workers_alloc) : d->workers_alloc;
+    h->tensor = (flags & HLU_FLAG_TENSOR) != 0;
+    return HLU_OK;
+}
+
+int hlu_get_launch(hlu_t h, int32_t *workers, int32_t *flags) {
+    if (!h) return HLU_EINVAL;
+    if (workers) *workers = h->fp.workers;
+    if (flags) *flags = h->tensor ? HLU_FLAG_TENSOR : 0;
+    return HLU_OK;
 }
 
 int hlu_inject_stall(hlu_t h, int32_t on) {

@@ -69,15 +69,22 @@ View Planner::new_temp(int32_t row_cl, int32_t rows, int32_t cols, int32_t rslot
     v.obj = new_obj(row_cl, -1);
     const int64_t elems = int64_t(rows) * std::max(cols, 1);
     v.p.off = plan_alloc(elems, v.obj);
-    if ((int64_t)temp_size.size() <= v.obj) {
-        temp_size.resize(v.obj + 1, 0);
-        temp_first.resize(v.obj + 1, INT32_MAX);
-        temp_last.resize(v.obj + 1, -1);
-        temp_shape.resize(v.obj + 1, {-1, -1, -1, -1});
-    }
-    temp_size[v.obj] = elems;
-    temp_shape[v.obj] = {owner_cl >= 0 && !inst.empty() ? inst[owner_cl] : -1, row_cl, rows, std::max(cols, 1)};
+    note_temp(v.obj, elems, {owner_cl >= 0 && !inst.empty() ? inst[owner_cl] : -1, row_cl, rows, std::max(cols, 1)});
     return v;
+}
+
+// Registers object `obj` as a temporary of the current plan: its size and its shape (problem, row
+// cluster, rows, columns; split-block factors carry their capacity as a negative column count, so
+// that they share regions only with each other).
+void Planner::note_temp(int32_t obj, int64_t elems, const std::array<int32_t, 4> &shape) {
+    if ((int64_t)temp_size.size() <= obj) {
+        temp_size.resize(obj + 1, 0);
+        temp_first.resize(obj + 1, INT32_MAX);
+        temp_last.resize(obj + 1, -1);
+        temp_shape.resize(obj + 1, {-1, -1, -1, -1});
+    }
+    temp_size[obj] = elems;
+    temp_shape[obj] = shape;
 }
 
 // Lets the product temporaries of plan p share regions: the plan's other allocations (split blocks,
@@ -713,12 +720,15 @@ void Planner::addmul(Block *C, double alpha, Block *A, Block *B) {
                 vs.m = cl[ti].size;
                 vs.n = cl[sj].size;
                 vs.cap = std::max(std::min(std::min(vs.m, vs.n), opt.rank_cap), cs.cap);
-                vs.U_off = plan_alloc(int64_t(vs.m) * vs.cap, -1);
-                vs.V_off = plan_alloc(int64_t(vs.n) * vs.cap, -1);
                 vs.kslot = new_slot(0);
                 vs.krank = 0;
                 vs.objU = new_obj(ti, -1);
                 vs.objV = new_obj(sj, -1);
+                // the son's factors live from the split to the merge: temporaries of the plan
+                vs.U_off = plan_alloc(int64_t(vs.m) * vs.cap, vs.objU);
+                vs.V_off = plan_alloc(int64_t(vs.n) * vs.cap, vs.objV);
+                note_temp(vs.objU, int64_t(vs.m) * vs.cap, {ti >= 0 && !inst.empty() ? inst[ti] : -1, ti, vs.m, -vs.cap});
+                note_temp(vs.objV, int64_t(vs.n) * vs.cap, {sj >= 0 && !inst.empty() ? inst[sj] : -1, sj, vs.n, -vs.cap});
                 vs.objD = -1;
                 fstore.push_back(vs);
                 S[i][j] = v;
@@ -1007,10 +1017,18 @@ static std::vector<int32_t> permute_by_wave(std::vector<T> &v, std::vector<int32
     return where;
 }
 
-// Rounded-addition scratch: the tasks of one wave get disjoint regions of the arena, waves reuse
-// them (the regions are assigned in emission order within each wave).
+// Rounded-addition scratch of the wave schedule: the tasks of one wave get disjoint regions of the
+// arena, waves reuse them (the regions are assigned in emission order within each wave).  The
+// data-flow schedule gives every worker its own scratch instead, so nothing is laid out for it.
 void Planner::finalize_alloc(Plan &p, int64_t *bump) const {
     const int64_t base = align8(*bump);
+    if (!opt.wave_order) {
+        for (TRadd &r : p.radd) r.scratch_off = base;
+        p.scratch_base = base;
+        p.scratch_elems = 0;
+        *bump = base;
+        return;
+    }
     std::vector<int64_t> woff(size_t(std::max(p.n_waves, 1)), 0);
     int64_t maxw = 0;
     for (size_t i = 0; i < p.radd.size(); ++i) {

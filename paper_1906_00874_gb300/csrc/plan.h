@@ -205,6 +205,7 @@ private:
     std::vector<int32_t> temp_first, temp_last;
     void temp_levels(Plan &p) const;
     void relocate_temps(Plan &p);
+    void note_temp(int32_t obj, int64_t elems, const std::array<int32_t, 4> &shape);
     void cells_of(const View &v, std::vector<int64_t> &out) const;
     int32_t emit_views(Kind k, const View *const *reads, size_t nr, const View *const *writes, size_t nw);
     int32_t emit(Kind k, std::initializer_list<const View *> reads, std::initializer_list<const View *> writes) {

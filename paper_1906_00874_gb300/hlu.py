@@ -30,7 +30,7 @@ EXPORTS = ("hlu_create", "hlu_factor", "hlu_solve", "hlu_matvec", "hlu_solve_ref
            "hlu_last_error_detail", "hlu_last_cuda_error", "hlu_probe_alu_peaks", "hlu_inject_stall",
            "hlu_create_batch", "hlu_factor_batch", "hlu_batch_count", "hlu_bem_build", "hlu_bem_result",
            "hlu_bem_copy_data", "hlu_create_bem", "hlu_bem_destroy", "hlu_plan_info_get", "hlu_plan_info_batch",
-           "hlu_factor_error", "hlu_lowrank_apply_noalloc")
+           "hlu_factor_error", "hlu_lowrank_apply_noalloc", "hlu_set_launch", "hlu_get_launch")
 KINDS = ("getrf", "trsm", "project", "accum", "radd", "split", "dataflow_factor", "dataflow_solve",
          "dataflow_matvec")
 
@@ -167,6 +167,8 @@ def load(path=LIB_PATH):
     lib.hlu_solve_refined.argtypes = [vp, vp, vp, i32, i64, dbl, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl)]
     lib.hlu_solve_gmres.argtypes = [vp, vp, vp, i32, i64, dbl, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl)]
     lib.hlu_factor_error.argtypes = [vp, vp, i32, dbl, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
+    lib.hlu_set_launch.argtypes = [vp, i32, i32]
+    lib.hlu_get_launch.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.hlu_set_profiling.argtypes = [vp, i32]
     lib.hlu_inject_stall.argtypes = [vp, i32]
     lib.hlu_probe_alu_peaks.argtypes = [ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
@@ -379,6 +381,16 @@ class HLU:
         self._check(load().hlu_factor_error(self._h, ctypes.c_void_p(ptr), int(iters), float(rtol), ctypes.byref(e),
                                             ctypes.byref(a)), "hlu_factor_error")
         return e.value, a.value
+
+    def set_launch(self, workers=0, flags=0):
+        """Launch settings without re-planning (hlu_set_launch): worker cap and HLU_FLAG_TENSOR."""
+        self._check(load().hlu_set_launch(self._h, int(workers), int(flags)), "hlu_set_launch")
+
+    def get_launch(self):
+        """(workers of a factorisation launch, flags) of the handle (hlu_get_launch)."""
+        w, f = ctypes.c_int32(), ctypes.c_int32()
+        self._check(load().hlu_get_launch(self._h, ctypes.byref(w), ctypes.byref(f)), "hlu_get_launch")
+        return w.value, f.value
 
     def inject_stall(self, on=True):
         """Test hook: the next factorisation stalls on one task until the wait limit (HLU_ETIMEOUT)."""

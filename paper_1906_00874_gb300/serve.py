@@ -72,9 +72,9 @@ class _Group:
 class Server:
     """Continuous-batching H-LU server over resident factors (see the module docstring)."""
 
-    def __init__(self, precision=HLU_FP32, mem_budget=150e9, tol=1e-10, max_iter=30, max_group=64,
+    def __init__(self, precision=HLU_FP32, mem_budget=150e9, tol=1e-10, max_iter=30, max_group=16,
                  stream=None, clock=time.perf_counter, device="cuda", handle_type=HLU, workers=None,
-                 solve_threads=2, admit_threads=4, stream_factory=None, timeline=False):
+                 solve_threads=2, admit_threads=4, stream_factory=None, timeline=False, temp_reuse=0):
         self.precision = precision
         self.budget = int(mem_budget)
         self.tol = tol
@@ -86,6 +86,7 @@ class Server:
         self.workers = self._default_workers() if workers is None else int(workers)
         self.stream_factory = stream_factory or self._default_stream_factory(stream)
         self.timeline = timeline
+        self.temp_reuse = temp_reuse  # hlu_opts.temp_reuse of the groups (1: half the memory, slower planning)
         self.groups: list[_Group] = []
         self.where: dict[object, _Group] = {}
         self.admitting: dict[object, concurrent.futures.Future] = {}  # key -> future of its group
@@ -254,8 +255,8 @@ class Server:
     def _create_in(self, keys, probs, budget):
         stream = self.stream_factory()
         kw = dict(precision=self.precision, mem_budget=budget, stream=self._stream_ptr(stream))
-        if self.device == "cuda":
-            kw["temp_reuse"] = 1  # resident groups: half the memory per problem
+        if self.temp_reuse:
+            kw["temp_reuse"] = self.temp_reuse
         if self.workers:
             kw["workers"] = self.workers
         H = self.handle_type
@@ -383,9 +384,11 @@ class Server:
                 for g in self.groups:
                     if id(g) in by_group:
                         self._chain_solve(g, by_group[id(g)])
-                if new:
-                    fut = self._admit_pool.submit(self._admit_job, list(new), new)
-                    for k in new:
+                keys = list(new)
+                for c0 in range(0, len(keys), self.max_group):  # groups planned in parallel
+                    part = keys[c0:c0 + self.max_group]
+                    fut = self._admit_pool.submit(self._admit_job, part, {k: new[k] for k in part})
+                    for k in part:
                         self.admitting[k] = fut
                     fut.add_done_callback(self._on_error)
                     fut.add_done_callback(self._admitted)
