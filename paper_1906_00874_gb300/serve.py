@@ -101,6 +101,8 @@ class Server:
         self._errors: list[BaseException] = []
         self._creating = 0         # creations in flight (they share the free budget)
         self._reserved = 0         # bytes of budget handed to the creations in flight
+        self._jobs_active = 0      # admission jobs submitted and not finished
+        self.admit_threads = int(admit_threads)
         self._admit_pool = concurrent.futures.ThreadPoolExecutor(admit_threads, thread_name_prefix="hlu-admit")
         self._solve_pool = concurrent.futures.ThreadPoolExecutor(solve_threads, thread_name_prefix="hlu-solve")
 
@@ -177,79 +179,100 @@ class Server:
     # ------------------------------------------------------------ admission
     def _admit_job(self, keys, problems):
         """Admission thread: create and factorise the groups of `keys` (at most max_group problems
-        each), evicting idle LRU groups to fit the budget, waiting for one to become idle when none
-        is, and halving a group that cannot fit by itself.  Returns the groups."""
-        out = []
-        keys = list(keys)
-        while keys:
-            part, keys = keys[:self.max_group], keys[self.max_group:]
-            while True:
-                try:
-                    g = self._create(part, problems)
-                    break
-                except HLUError as e:
-                    if e.status != ENOMEM:
-                        raise
-                    with self._lock:
-                        if self._creating > 0:  # another creation holds part of the budget
-                            self._freed.wait(timeout=1.0)
-                            continue
-                        idle = [v for v in self.groups if v.busy == 0]
-                        if idle:
-                            self._evict(min(idle, key=lambda v: v.last_used))
-                            continue
-                        if any(v.busy for v in self.groups):  # memory frees when a solve ends
-                            self._freed.wait(timeout=1.0)
-                            continue
-                    if len(part) > 1:  # nothing to evict and nothing running: fewer at a time
-                        keys = part[len(part) // 2:] + keys
-                        part = part[:len(part) // 2]
-                    else:
-                        raise
+        each), evicting idle LRU groups to fit the budget, waiting for memory while other creations
+        or solves are running, and halving a group that cannot fit by itself.  Each group is
+        registered (and the solves of its waiting requests queued) as soon as it is factorised."""
+        try:
+            keys = list(keys)
+            while keys:
+                part, keys = keys[:self.max_group], keys[self.max_group:]
+                exclusive = False
+                while True:
+                    try:
+                        self._create(part, problems, exclusive)
+                        break
+                    except HLUError as e:
+                        if e.status != ENOMEM:
+                            raise
+                        with self._lock:
+                            if not exclusive:  # a share was not enough: next, all the free budget
+                                exclusive = True
+                                continue
+                            if self._creating > 0:  # another creation holds part of the budget
+                                self._freed.wait(timeout=1.0)
+                                continue
+                            idle = [v for v in self.groups if v.busy == 0]
+                            if idle:
+                                self._evict(min(idle, key=lambda v: v.last_used))
+                                continue
+                            if any(v.busy for v in self.groups):  # memory frees when a solve ends
+                                self._freed.wait(timeout=1.0)
+                                continue
+                        if len(part) > 1:  # nothing to evict and nothing running: fewer at a time
+                            keys = part[len(part) // 2:] + keys
+                            part = part[:len(part) // 2]
+                        else:
+                            raise
+        finally:
             with self._lock:
-                self.groups.append(g)
-                g.last_used = self._tick
-                g.busy += 1  # held until its waiting requests are queued (_admitted)
-                for k in g.keys:
-                    self.where[k] = g
-            out.append(g)
-        return out
-
-    def _admitted(self, fut):
-        """Done-callback of an admission: queue the solves of the requests that waited for its
-        groups and release the groups' admission hold."""
-        if fut.exception() is not None:
-            return
-        with self._lock:
-            for g in fut.result():
-                reqs = []
-                for k in g.keys:
-                    reqs += self.waiting.pop(k, [])
-                    if self.admitting.get(k) is fut:
-                        del self.admitting[k]
-                if reqs:
-                    self._chain_solve(g, reqs)
-                g.busy -= 1
+                self._jobs_active -= 1
                 self._freed.notify_all()
 
-    def _create(self, keys, problems):
-        """Create and factorise one group.  Creations run on several admission threads at once (the
-        host planning of one problem does not wait for another's); each takes an equal share of the
-        budget left free by the resident groups and the creations in flight."""
+    def _admit_failed(self, fut):
+        """Done-callback of an admission: on failure, forget the keys it did not admit (their
+        waiting requests are dropped; the error is raised by the next step())."""
+        if fut.exception() is None:
+            return
+        with self._lock:
+            for k in [k for k, f in self.admitting.items() if f is fut]:
+                del self.admitting[k]
+                self.waiting.pop(k, None)
+
+    def _register(self, g):
+        """Make a new group resident and queue the solves of the requests waiting for its keys
+        (called with the lock held)."""
+        self.groups.append(g)
+        g.last_used = self._tick
+        reqs = []
+        for k in g.keys:
+            self.where[k] = g
+            self.admitting.pop(k, None)
+            reqs += self.waiting.pop(k, [])
+        if reqs:
+            self._chain_solve(g, reqs)
+
+    def _create(self, keys, problems, exclusive=False):
+        """Create, factorise and register one group.  Creations run on several admission threads at
+        once (the host planning of one problem does not wait for another's).  The budget left free
+        by the resident groups and the creations in flight is split equally over the admissions
+        that still need a share (at most one per admission thread); an exclusive creation (a retry
+        after a share was too small) waits until no other creation is in flight and takes all of
+        it.  The group's registration and the release of its share happen under one lock, so that a
+        waiting admission never sees memory as neither reserved nor resident."""
         probs = [problems[k] for k in keys]
         with self._lock:
+            if exclusive:
+                while self._creating > 0:
+                    self._freed.wait(timeout=1.0)
+                claim = 1
+            else:
+                claim = max(1, min(self._jobs_active, self.admit_threads) - self._creating)
             free = self.budget - self.resident_bytes - self._reserved
-            budget = free // (self._creating + 1)
+            budget = free // claim
             if budget <= 0:
                 raise HLUError(ENOMEM, "device-memory budget exhausted")
             self._creating += 1
             self._reserved += budget
+        g = None
         try:
-            return self._create_in(keys, probs, budget)
+            g = self._create_in(keys, probs, budget)
+            return g
         finally:
             with self._lock:
                 self._creating -= 1
                 self._reserved -= budget
+                if g is not None:
+                    self._register(g)
                 self._freed.notify_all()
 
     def _create_in(self, keys, probs, budget):
@@ -387,11 +410,12 @@ class Server:
                 keys = list(new)
                 for c0 in range(0, len(keys), self.max_group):  # groups planned in parallel
                     part = keys[c0:c0 + self.max_group]
+                    self._jobs_active += 1
                     fut = self._admit_pool.submit(self._admit_job, part, {k: new[k] for k in part})
                     for k in part:
                         self.admitting[k] = fut
                     fut.add_done_callback(self._on_error)
-                    fut.add_done_callback(self._admitted)
+                    fut.add_done_callback(self._admit_failed)
         return self._collect()
 
     def serve(self, requests, poll=1e-4):

@@ -169,6 +169,23 @@ def test_groups_admitted_in_one_step_are_not_evicted_by_later_groups():
         assert np.allclose(probs[r.key].A @ r.x, r.b, atol=1e-10)
 
 
+def test_halved_group_admits_its_second_half_by_evicting_the_first():
+    """Two new problems that do not fit together (one at a time does): the group is halved, the
+    first half is solved as soon as it is factorised, then evicted to make room for the second
+    half, and both requests are answered."""
+    probs = {k: _Prob(10, k) for k in range(2)}   # 800 bytes each
+    s = _server(budget=1000, max_group=2)
+    g = np.random.default_rng(5)
+    reqs = [Request(k, probs[k], g.standard_normal((10, 1)), rid=k) for k in range(2)]
+    for r in reqs:
+        s.submit(r)
+    out = _step(s, 0.0)
+    assert sorted(r.rid for r in out) == [0, 1]
+    assert s.stats["groups_created"] == 2 and s.stats["evicted_groups"] == 1
+    for r in reqs:
+        assert np.allclose(probs[r.key].A @ r.x, r.b, atol=1e-10)
+
+
 class _SlowHLU(_FakeHLU):
     """A stand-in whose factorisation and solves take time (sleep, as a device call would block the
     calling thread without holding the interpreter lock)."""
