@@ -28,25 +28,33 @@ WORKLOADS = {
 # Batches of independent problems: `count` ellipsoids, instance i drawn from seed i.
 BATCHES = {
     "ellipsoids64": dict(count=64, levels=(3, 4), eps=(1e-4, 1e-6), leaf=32, eta=2.0),
+    # 256 ellipsoids refined 3 to 5 times (n = 1280 .. 20480), all three axes uniform in [0.5, 2],
+    # leaf 32 at every size
+    "ellipsoids256": dict(count=256, levels=(3, 4, 5), eps=(1e-4, 1e-6), leaf=32, eta=2.0, leaf_large=32,
+                          axes_range=(0.5, 2.0)),
 }
 
 
-def batch_specs(count, levels=(3, 4), eps=(1e-4, 1e-6), leaf=32, eta=2.0, leaf_large=64):
+def batch_specs(count, levels=(3, 4), eps=(1e-4, 1e-6), leaf=32, eta=2.0, leaf_large=64, axes_range=None):
     """Keyword arguments of build_problem for each instance of a batch.
 
     Instance i uses default_rng(i): refinement r uniform in `levels`, tolerance
-    uniform in `eps`, ellipsoid axes (1, a, b) with a, b uniform in [0.4, 1],
-    one right-hand side drawn from seed i.  Problems with r >= 5 (n >= 20480)
-    use the leaf size `leaf_large`, as the single-problem workloads of that size."""
+    uniform in `eps`, ellipsoid axes (1, a, b) with a, b uniform in [0.4, 1]
+    (or, with axes_range = (lo, hi), all three axes uniform in [lo, hi]), one
+    right-hand side drawn from seed i.  Problems with r >= 5 (n >= 20480) use
+    the leaf size `leaf_large`."""
     import numpy as np
     out = []
     for i in range(count):
         g = np.random.default_rng(i)
         r = int(g.choice(levels))
         e = float(g.choice(eps))
-        a, b = (float(v) for v in g.uniform(0.4, 1.0, 2))
-        out.append(dict(r=r, leaf=leaf_large if r >= 5 else leaf, eta=eta, eps=e, nrhs=1, seed=i,
-                        axes=(1.0, round(a, 6), round(b, 6))))
+        if axes_range is None:
+            a, b = (float(v) for v in g.uniform(0.4, 1.0, 2))
+            axes = (1.0, round(a, 6), round(b, 6))
+        else:
+            axes = tuple(round(float(v), 6) for v in g.uniform(axes_range[0], axes_range[1], 3))
+        out.append(dict(r=r, leaf=leaf_large if r >= 5 else leaf, eta=eta, eps=e, nrhs=1, seed=i, axes=axes))
     return out
 
 

@@ -15,7 +15,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libhlu.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "hlu_api.cu", "plan.cpp", "probe.cu", "noalloc.cu", "gmres.cu", "bem.cu", "errest.cu"]
+SOURCES = ["kernels.cu", "hlu_api.cu", "plan.cpp", "plan_batch.cpp", "probe.cu", "noalloc.cu", "gmres.cu", "bem.cu", "errest.cu"]
 
 
 def nvcc():

@@ -472,6 +472,7 @@ static int create_impl(const hlu_tree *tree, const hlu_blocks *blocks, const hlu
         if (opts->inv_block != 0) po.inv_block = opts->inv_block < 0 ? 0 : opts->inv_block;
         po.temp_reuse = opts->temp_reuse > 0;
         h->tensor = (opts->flags & HLU_FLAG_TENSOR) != 0;
+        if (opts->flags & HLU_FLAG_SERIAL_PLAN) po.batch_threads = -1;
         h->max_workers = std::max(0, opts->workers);
     }
     if (h->precision == HLU_FP32_CORE32) {  // FP32 factors, FP32 Jacobi in the truncation cores
@@ -649,6 +650,7 @@ int plan_only(const hlu_tree *tree, const hlu_blocks *blocks, const hlu_opts *op
         if (opts->inv_block != 0) po.inv_block = opts->inv_block < 0 ? 0 : opts->inv_block;
         po.temp_reuse = opts->temp_reuse > 0;
         po.wave_order = opts->schedule == HLU_SCHED_WAVES;
+        if (opts->flags & HLU_FLAG_SERIAL_PLAN) po.batch_threads = -1;
     } else {
         po.wave_order = false;
     }

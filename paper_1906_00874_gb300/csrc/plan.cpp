@@ -25,6 +25,30 @@ Planner::~Planner() {
     for (Block *b : blocks_owned) delete b;
 }
 
+void Planner::release_work() {
+    for (Block *b : blocks_owned) delete b;
+    std::vector<Block *>().swap(blocks_owned);
+    root = nullptr;
+    std::vector<Obj>().swap(objs);
+    std::vector<CellState>().swap(cell);
+    std::vector<int32_t>().swap(pred_mark);
+    std::vector<int32_t>().swap(rpool_task);
+    std::vector<int32_t>().swap(rpool_next);
+    std::vector<PlanItem>().swap(plan_items);
+    std::vector<int32_t>().swap(touch_obj);
+    std::vector<int32_t>().swap(touch_cell);
+    std::vector<int32_t>().swap(touch_task);
+    std::vector<uint8_t>().swap(touch_write);
+    std::vector<std::array<int32_t, 4>>().swap(temp_shape);
+    std::vector<int64_t>().swap(temp_size);
+    std::vector<int32_t>().swap(temp_first);
+    std::vector<int32_t>().swap(temp_last);
+    for (Plan *p : {&fplan, &splan, &mplan}) {  // the executors use the successor lists only
+        std::vector<int32_t>().swap(p->pred_ptr);
+        std::vector<int32_t>().swap(p->pred_idx);
+    }
+}
+
 // ------------------------------------------------------------------ objects
 int32_t Planner::new_obj(int32_t row_cl, int32_t col_cl, int32_t nr_if_none) {
     Obj o;
@@ -1104,6 +1128,8 @@ void Planner::finalize_graph(Plan &p) const {
                 p.critical_us = std::max(p.critical_us, double(bl[g]));
             }
         std::sort(p.roots.begin(), p.roots.end(), by_priority);
+        p.root_bl.resize(p.roots.size());
+        for (size_t r = 0; r < p.roots.size(); ++r) p.root_bl[r] = bl[p.roots[r]];
     }
     // launches: for each wave, one launch per kind present (wave order only)
     if (!opt.wave_order) return;
@@ -1408,10 +1434,15 @@ int Planner::build(int32_t n_, int32_t n_clusters, const int32_t *perm_, const i
         error = "non-finite input value";
         return HLU_EINVAL;
     }
+    if (n_inst > 1 && !opt.wave_order && opt.batch_threads >= 0) {
+        batch_deferred = true;  // every problem gets its own block tree in plan_batch
+        return HLU_OK;
+    }
     return build_tree();
 }
 
 int Planner::plan_all() {
+    if (batch_deferred) return plan_batch();
     layout_factor_arena();
     nrhs_slot = new_slot(0);
     begin_plan(fplan, false, &f_elems);

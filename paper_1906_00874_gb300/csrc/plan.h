@@ -87,6 +87,7 @@ struct Plan {
     std::vector<int32_t> pred_ptr, pred_idx;  // predecessors (CSR), built during emission
     std::vector<int32_t> succ_ptr, succ_idx;  // successors (CSR), built by finalize
     std::vector<int32_t> indeg, roots;
+    std::vector<float> root_bl;               // priority of every root (its longest path to the end, µs)
     int64_t n_edges = 0;
     int64_t scratch_base = 0, scratch_elems = 0;
     int32_t max_kcap = 0;
@@ -108,6 +109,9 @@ struct PlanOptions {
                              // applies the inverses as products; 0: plain block substitution
     bool temp_reuse = false;  // the factorisation's product temporaries share device regions by
                              // dependency-level intervals (relocate_temps); false: each its own region
+    int32_t batch_threads = 0;  // batch, data-flow schedule: the problems are planned on this many host
+                                // threads (0: all hardware threads) and their graphs joined
+                                // (plan_batch); < 0: one plan of the whole forest on one thread
 };
 
 class Planner {
@@ -163,6 +167,13 @@ public:
     int plan_all();
 
 private:
+    bool batch_deferred = false;  // a batch whose problems plan_all plans separately (plan_batch)
+    int plan_batch();
+    bool batch_layout(std::vector<int32_t> &cb, std::vector<int32_t> &ce, std::vector<int64_t> &lb,
+                      std::vector<int32_t> &rb) const;
+    // frees the emission state (cells, objects, block tree) once the plans are made
+    void release_work();
+
     // current plan being emitted
     Plan *P = nullptr;
     bool use_astore = false;

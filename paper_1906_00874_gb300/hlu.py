@@ -20,6 +20,7 @@ HLU_FP32_CORE32 = 2   # FP32 factors, FP32 Jacobi in the truncation cores
 SCHED_DATAFLOW = 0
 SCHED_WAVES = 1
 FLAG_TENSOR = 1       # FP32 factors: dense products of the factorisation on the tensor cores
+FLAG_SERIAL_PLAN = 2  # a batch planned as one H-matrix on one host thread (default: per problem, in parallel)
 
 STATUS = {0: "HLU_OK", 1: "HLU_EINVAL", 2: "HLU_ENOMEM", 3: "HLU_ESTATE", 4: "HLU_EPIVOT",
           5: "HLU_ERANKCAP", 6: "HLU_ETIMEOUT", 7: "HLU_ECUDA", 8: "HLU_ENUMERIC"}
@@ -68,14 +69,15 @@ class _PlanInfo(ctypes.Structure):
                 ("factor_temp_peak_elems", ctypes.c_int64)]
 
 
-def plan_info(problems, rank_cap=0, nrhs_max=0, inv_block=0, schedule=SCHED_DATAFLOW, temp_reuse=0):
+def plan_info(problems, rank_cap=0, nrhs_max=0, inv_block=0, schedule=SCHED_DATAFLOW, temp_reuse=0, flags=0):
     """Sizes of the task graphs hlu_create (one problem) or hlu_create_batch (a list) would build:
     validation and planning on the host only (hlu_plan_info_get / hlu_plan_info_batch)."""
     lib = load()
     many = isinstance(problems, (list, tuple))
     descs = [_describe(p.n, p.tree.perm, p.tree.begin, p.tree.size, p.tree.son0, p.tree.son1, p.row_cl, p.col_cl,
                        p.kind, p.rank, p.offset, p.data) for p in (problems if many else [problems])]
-    opts = _Opts(0, int(rank_cap), int(nrhs_max), int(schedule), 0, 0.0, int(inv_block), 0, 0, int(temp_reuse))
+    opts = _Opts(0, int(rank_cap), int(nrhs_max), int(schedule), 0, 0.0, int(inv_block), int(flags), 0,
+                 int(temp_reuse))
     info = _PlanInfo()
     if many:
         trees = (_Tree * len(descs))(*[d[0] for d in descs])

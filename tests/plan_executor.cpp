@@ -346,7 +346,9 @@ struct Exec {
 // Plans the H-matrix, runs the factorisation's tasks and then one solve pass on b (n x nrhs,
 // cluster order, overwritten by x), and returns the factors in the input leaf layout.  With inst
 // (the problem of every cluster, -1 above the problems), the H-matrix is a batch of n_inst problems
-// with one tolerance eps.  temp_reuse != 0: the product temporaries share regions (relocate_temps).
+// with one tolerance eps, planned per problem on batch_threads threads and joined (plan_batch; 0:
+// all hardware threads) or, with batch_threads < 0, as one forest.  temp_reuse != 0: the product
+// temporaries share regions (relocate_temps).
 // Status: 0, the planner's status, or -1 (not every task ran: a dependency cycle) / -2 (a task
 // failed: zero pivot or rank capacity).
 extern "C" int plan_execute(int32_t n, int32_t n_clusters, const int32_t *perm, const int32_t *begin,
@@ -354,9 +356,11 @@ extern "C" int plan_execute(int32_t n, int32_t n_clusters, const int32_t *perm, 
                             const int32_t *row_cl, const int32_t *col_cl, const int8_t *kind, const int32_t *rank,
                             const int64_t *offset, const double *data, int64_t data_len, double eps,
                             int32_t inv_block, uint64_t seed, double *out, int64_t *out_off, int32_t *out_rank,
-                            double *b, int32_t nrhs, const int32_t *inst, int32_t n_inst, int32_t temp_reuse) {
+                            double *b, int32_t nrhs, const int32_t *inst, int32_t n_inst, int32_t temp_reuse,
+                            int32_t batch_threads) {
     Planner pl;
     PlanOptions o;
+    o.batch_threads = batch_threads;  // batch: < 0 one plan of the forest, else per problem and joined
     if (inv_block != 0) o.inv_block = inv_block < 0 ? 0 : inv_block;  // 0: the default, < 0: off
     o.temp_reuse = temp_reuse != 0;  // temporaries sharing regions by dependency-level intervals
     o.wave_order = false;

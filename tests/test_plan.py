@@ -26,17 +26,21 @@ def test_inverse_blocks_shorten_the_solve(prob1280):
     assert on["factor_tasks"] > off["factor_tasks"] and on["matvec_tasks"] == off["matvec_tasks"]
 
 
+@pytest.mark.parametrize("serial", [False, True])
 @pytest.mark.parametrize("inv_block", [-1, 0])
-def test_batch_plans_only_its_problems_tasks(inv_block):
-    from paper_1906_00874_gb300.hlu import plan_info
+def test_batch_plans_only_its_problems_tasks(inv_block, serial):
+    """A batch plans each problem's tasks and dependencies and nothing else, whether the problems
+    are planned on their own threads and joined (default) or as one forest (FLAG_SERIAL_PLAN)."""
+    from paper_1906_00874_gb300.hlu import FLAG_SERIAL_PLAN, plan_info
     probs = [build_problem(3, 32, 2.0, 1e-4), build_problem(2, 32, 2.0, 1e-4, seed=1, axes=(1.0, 0.6, 0.4)),
              build_problem(2, 32, 2.0, 1e-4, seed=2, axes=(1.0, 0.8, 0.5))]
     one = [plan_info(p, inv_block=inv_block) for p in probs]
-    batch = plan_info(probs, inv_block=inv_block)
+    batch = plan_info(probs, inv_block=inv_block, flags=FLAG_SERIAL_PLAN if serial else 0)
     for key in ("factor_tasks", "factor_edges", "solve_tasks", "matvec_tasks", "inverse_blocks"):
         assert batch[key] == sum(o[key] for o in one), key
     for key in ("factor_levels", "solve_levels"):
         assert batch[key] == max(o[key] for o in one), key
+    assert batch["factor_critical_us"] == pytest.approx(max(o["factor_critical_us"] for o in one))
 
 
 def test_wave_order_does_not_change_the_graph(prob1280):

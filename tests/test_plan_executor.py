@@ -25,14 +25,15 @@ def executor(tmp_path_factory):
         pytest.skip("g++ not available")
     so = str(tmp_path_factory.mktemp("exec") / "plan_executor.so")
     subprocess.run([cxx, "-O2", "-std=c++17", "-pthread", "-fPIC", "-shared", "-I" + CSRC,
-                    os.path.join(ROOT, "tests", "plan_executor.cpp"), os.path.join(CSRC, "plan.cpp"), "-o", so],
+                    os.path.join(ROOT, "tests", "plan_executor.cpp"), os.path.join(CSRC, "plan.cpp"),
+                    os.path.join(CSRC, "plan_batch.cpp"), "-o", so],
                    check=True, capture_output=True)
     lib = ctypes.CDLL(so)
     lib.plan_execute.restype = ctypes.c_int
     return lib
 
 
-def _run(lib, p, eps, inv_block, seed, inst=None, temp_reuse=0):
+def _run(lib, p, eps, inv_block, seed, inst=None, temp_reuse=0, batch_threads=0):
     t = p.tree
     keep = []
 
@@ -52,7 +53,8 @@ def _run(lib, p, eps, inv_block, seed, inst=None, temp_reuse=0):
         ctypes.c_int32(inv_block), ctypes.c_uint64(seed), out.ctypes.data_as(ctypes.c_void_p),
         off.ctypes.data_as(ctypes.c_void_p), rank.ctypes.data_as(ctypes.c_void_p), b.ctypes.data_as(ctypes.c_void_p),
         ctypes.c_int32(b.shape[1]), None if inst is None else ptr(inst, np.int32),
-        ctypes.c_int32(0 if inst is None else int(np.max(inst)) + 1), ctypes.c_int32(temp_reuse))
+        ctypes.c_int32(0 if inst is None else int(np.max(inst)) + 1), ctypes.c_int32(temp_reuse),
+        ctypes.c_int32(batch_threads))
     assert st == 0, st
     q = copy.copy(p)
     q.rank, q.offset, q.data = rank, off, out
@@ -140,16 +142,18 @@ class _Forest:
         return self._b
 
 
-def test_batch_task_lists_equal_the_problems_own(executor):
+@pytest.mark.parametrize("batch_threads", [-1, 0, 2])
+def test_batch_task_lists_equal_the_problems_own(executor, batch_threads):
     """A batch's task lists, executed, give every problem exactly the factors and solve of its own
-    task lists (no task couples two problems), with and without the inverse blocks."""
+    task lists (no task couples two problems), with and without the inverse blocks, planned as one
+    forest (batch_threads < 0) or per problem on several threads and joined."""
     from bem_inputs import build_problem
     probs = [build_problem(3, 32, 2.0, 1e-4, nrhs=2), build_problem(2, 32, 2.0, 1e-4, nrhs=2, seed=1,
                                                                     axes=(1.0, 0.6, 0.4)),
              build_problem(2, 32, 2.0, 1e-4, nrhs=2, seed=2, axes=(1.0, 0.8, 0.5))]
     f = _Forest(probs)
     for inv_block, reuse in ((-1, 0), (0, 0), (0, 1)):
-        qb, xb = _run(executor, f, 1e-4, inv_block, 7, inst=f.inst, temp_reuse=reuse)
+        qb, xb = _run(executor, f, 1e-4, inv_block, 7, inst=f.inst, temp_reuse=reuse, batch_threads=batch_threads)
         row = 0
         for i, p in enumerate(probs):
             q, x = _run(executor, p, 1e-4, inv_block, 11 + i, temp_reuse=reuse)
