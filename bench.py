@@ -597,153 +597,334 @@ def _build_one(kw):
     return build_problem(**kw)
 
 
+def _structure_one(kw):
+    from bem_inputs import build_structure
+    return build_structure(**kw)
+
+
 def build_batch(name):
-    """The seeded problems of a named batch, built on all host cores (spawned workers, before any CUDA call)."""
+    """The seeded structures of a named batch (geometry, cluster tree, block-tree leaves and
+    right-hand sides; no leaf data), built on all host cores by spawned workers before any CUDA
+    call.  The leaf data are computed on the GPU afterwards (construct_leaves)."""
     import multiprocessing as mp
 
     from bem_inputs import BATCHES, batch_specs
     specs = batch_specs(**BATCHES[name])
     with mp.get_context("spawn").Pool(min(len(specs), os.cpu_count() or 1)) as pool:
-        return specs, pool.map(_build_one, specs)
+        return specs, pool.map(_structure_one, specs, chunksize=1)
+
+
+def construct_leaves(structs):
+    """Leaf data of every structure computed on the GPU (hlu_bem_build: dense leaves, cross
+    approximation and truncation at the problem's eps) and copied into the problem (host arrays,
+    the input layout of hlu_create_batch)."""
+    from paper_1906_00874_gb300.hlu import BEMBuild
+    for s in structs:
+        g = BEMBuild.from_problem(s)
+        s.rank, s.offset, s.data = g.rank.copy(), g.offset.copy(), g.data()
+        g.close()
+    return structs
+
+
+def _oracle_batch_worker(name, budget_s):
+    """Run in a single-threaded subprocess: the FP64 oracle's H-LU and solve of the batch's smallest
+    problems (host-built leaves), one after the other, until `budget_s` seconds are used."""
+    import numpy as np
+    from bem_inputs import BATCHES, batch_specs, build_problem
+    from oracle import HLUOracle
+    from oracle.errors import lu_solve
+    specs = sorted(batch_specs(**BATCHES[name]), key=lambda kw: kw["r"])
+    done, t_all, ns = 0, 0.0, []
+    for kw in specs:
+        p = build_problem(**kw)
+        t0 = time.perf_counter()
+        o = HLUOracle(p, p.eps).factor()
+        lu_solve(o.A, p.b_perm())
+        t_all += time.perf_counter() - t0
+        done += 1
+        ns.append(p.n)
+        if t_all >= budget_s:
+            break
+    print(json.dumps({"problems": done, "seconds": t_all, "n": sorted(set(ns)), "r": int(specs[0]["r"])}))
+
+
+def oracle_batch_sample(name, budget_s=12.0):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = ("import sys; sys.path.insert(0, %r); import bench; bench._oracle_batch_worker(%r, %r)"
+            % (ROOT, name, float(budget_s)))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError("oracle batch sample failed:\n" + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def _split_balanced(probs, parts):
+    """Problem indices in `parts` groups of about equal leaf counts (largest first, each to the
+    lightest group), every group in increasing index order."""
+    load, groups = [0] * parts, [[] for _ in range(parts)]
+    for i in sorted(range(len(probs)), key=lambda i: -probs[i].n_leaves):
+        g = load.index(min(load))
+        groups[g].append(i)
+        load[g] += probs[i].n_leaves
+    return [sorted(g) for g in groups if g]
 
 
 def run_batch(args):
-    """Batched H-LU of many independent problems in one handle (hlu_create_batch) against a loop of
-    per-problem FP64 handles.  One step = factorise every problem (its own eps) and solve its
-    right-hand side to a 1e-10 relative residual.  Metric: problems solved per second."""
+    """Batched H-LU of many independent problems in one handle (hlu_create_batch: the problems
+    planned in parallel on the host, one persistent data-flow launch per factorisation) against a
+    loop of per-problem FP64 handles.  One step = factorise every problem (its own eps) and solve its
+    right-hand side to a 1e-10 relative residual (FP64 refinement of the stacked block-diagonal
+    system).  The launch setting (worker count, product path) is chosen by the tuner on a sample of
+    the batch.  Metric: problems solved per second."""
+    import concurrent.futures
+
     import numpy as np
     import torch
 
+    from bem_inputs import BATCHES
     from paper_1906_00874_gb300 import HLU, HLU_FP32, HLU_FP64, build
-    from paper_1906_00874_gb300.hlu import to_device_panel
+    from paper_1906_00874_gb300.autotune import candidates, structure_key, tune
+    from paper_1906_00874_gb300.hlu import HLUError, probe_alu_peaks, to_device_panel
 
     rank, world, local = dist_env()
+    t0 = time.perf_counter()
     specs, probs = build_batch(args.workload)
+    structure_s = time.perf_counter() - t0
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    construct_leaves(probs)
+    construct_s = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
     sptr = stream.cuda_stream
+    B = len(probs)
     eps = [p.eps for p in probs]
-    bstack = to_device_panel(np.concatenate([p.b for p in probs], axis=0))
-    # stacked tolerance that bounds every problem's own relative residual by 1e-10
     bn = [float(np.linalg.norm(p.b)) for p in probs]
-    tol_stack = TOL * min(bn) / float(np.linalg.norm(bn))
-
     ranks = RankOps(world, "cuda")
     barrier, max_over_ranks = ranks.barrier, ranks.max
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
 
-    def timed(fn, steps, warmup):
-        for _ in range(warmup):
-            fn()
-        barrier()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    class Part:
+        """One batched handle over a subset of the problems, with its stacked b and x."""
+
+        def __init__(self, idx, precision, **kw):
+            self.idx = idx
+            sub = [probs[i] for i in idx]
+            self.h = HLU.batch(sub, precision=precision, stream=sptr, nrhs_max=1, **kw)
+            self.b = to_device_panel(np.concatenate([p.b for p in sub], axis=0))
+            self.x = torch.zeros_like(self.b)
+            nb = [bn[i] for i in idx]
+            # stacked tolerance that bounds every problem's own relative residual by 1e-10
+            self.tol = TOL * min(nb) / float(np.linalg.norm(nb))
+            self.eps = [eps[i] for i in idx]
+
+        def step(self):
+            self.h.factor(self.eps)
+            return self.h.solve_refined(self.b, self.x, tol=self.tol, max_iter=30)
+
+        def worst_resid(self):
+            y = torch.empty_like(self.x)
+            self.h.matvec(self.x, y)
+            r = (self.b - y).cpu().numpy()[:, 0]
+            o, worst = 0, 0.0
+            for i in self.idx:
+                n = probs[i].n
+                worst = max(worst, float(np.linalg.norm(r[o:o + n])) / bn[i])
+                o += n
+            return worst
+
+    def make_parts(precision, **kw):
+        """The whole batch in one handle; halves (balanced by leaves) while it does not fit."""
+        for parts in (1, 2, 4, 8):
+            made = []
+            try:
+                for idx in _split_balanced(probs, parts):
+                    made.append(Part(idx, precision, **kw))
+                return made
+            except HLUError as e:
+                for m in made:
+                    m.h.close()
+                del made
+                torch.cuda.empty_cache()
+                if e.status != 2:  # HLU_ENOMEM
+                    raise
+        raise RuntimeError("the batch does not fit the device even in eight handles")
+
+    # launch setting: tuner trials on a sample of the batch (every third problem, at most 32)
+    sample_idx = list(range(0, B, max(1, B // 32)))[:32]
+    sample = Part(sample_idx, HLU_FP32, temp_reuse=1)
+    cands = candidates(sms, tensor=True)
+    choice, trials, _ = tune(sample.h, sample.step, structure_key([probs[i] for i in sample_idx], HLU_FP32),
+                             cands, reps=2, use_cache=False)
+    sample.h.close()
+    del sample
+    torch.cuda.empty_cache()
+
+    t0 = time.perf_counter()
+    parts32 = make_parts(HLU_FP32, temp_reuse=1)
+    create_s = time.perf_counter() - t0
+    for part in parts32:
+        part.h.set_launch(choice["workers"], choice["flags"])
+
+    def step32():
+        return [part.step() for part in parts32]
+
+    l0 = sum(part.h.stats()["kernels_launched"] for part in parts32)
+    for _ in range(args.warmup):
+        step32()
+    barrier()
+    torch.cuda.synchronize()
+    l1 = sum(part.h.stats()["kernels_launched"] for part in parts32)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
         e0.record(stream)
-        out = [fn() for _ in range(steps)]
+        outs = [step32() for _ in range(args.steps)]
         e1.record(stream)
         torch.cuda.synchronize()
-        barrier()
-        return max_over_ranks(e0.elapsed_time(e1)) / steps, out
+    barrier()
+    t32 = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+    launches = (sum(part.h.stats()["kernels_launched"] for part in parts32) - l1) // args.steps
+    res32 = max(part.worst_resid() for part in parts32)
+    st = [part.h.stats() for part in parts32]
+    fl_factor = sum(s["model_flops"] for s in st)
+    dev_bytes = sum(s["device_bytes"] for s in st)
+    # one profiled factorisation: the data-flow kernel's share and the roofline
+    for part in parts32:
+        part.h.set_profiling(True)
+    step32()
+    torch.cuda.synchronize()
+    prof = [part.h.stats() for part in parts32]
+    for part in parts32:
+        part.h.set_profiling(False)
+    factor_ms = sum(p_["kernel_ms"]["dataflow_factor"] for p_ in prof)
+    efac_stacked = max(part.h.factor_error()[0] for part in parts32)
+    plan_ms = [part.h.stats()["create_ms"] for part in parts32]
+    its32 = max(o[0] for o in outs[-1])
+    for part in parts32:
+        part.h.close()
+    del parts32
+    torch.cuda.empty_cache()
 
-    def batched(precision):
-        h = HLU.batch(probs, precision=precision, stream=sptr)
-        x = torch.zeros_like(bstack)
+    # the comparison: one FP64 handle per problem, factor + refinement, one after the other; the
+    # handles are created ahead on host threads (each on its own stream), and only each problem's
+    # factor + refinement is timed (CUDA events on its stream)
+    def create64(i):
+        torch.cuda.set_device(local)
+        s = torch.cuda.Stream()
+        h = HLU.from_problem(probs[i], precision=HLU_FP64, stream=s.cuda_stream, nrhs_max=1)
+        return s, h
 
-        def step():
-            h.factor(eps)
-            return h.solve_refined(bstack, x, tol=tol_stack, max_iter=30)
-        return h, x, step
+    loop_ms, loop_its, loop_worst = [], 0, 0.0
+    tl0 = time.perf_counter()
+    with concurrent.futures.ThreadPoolExecutor(4) as ex:
+        ahead = 6
+        futs = {i: ex.submit(create64, i) for i in range(min(ahead, B))}
+        for i in range(B):
+            s, h = futs.pop(i).result()
+            if i + ahead < B:
+                futs[i + ahead] = ex.submit(create64, i + ahead)
+            with torch.cuda.stream(s):
+                b = to_device_panel(probs[i].b)
+                x = torch.zeros_like(b)
+                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0.record(s)
+                h.factor(probs[i].eps)
+                it, res = h.solve_refined(b, x, tol=TOL, max_iter=30)
+                a1.record(s)
+                a1.synchronize()
+            loop_ms.append(a0.elapsed_time(a1))
+            loop_its = max(loop_its, it)
+            loop_worst = max(loop_worst, res)
+            h.close()
+    loop_wall_s = time.perf_counter() - tl0
+    tloop = sum(loop_ms)
 
-    def per_problem_resid(h, x):
-        y = torch.empty_like(x)
-        h.matvec(x, y)
-        r = (bstack - y).cpu().numpy()[:, 0]
-        o, worst = 0, 0.0
-        for p, nb in zip(probs, bn):
-            worst = max(worst, float(np.linalg.norm(r[o:o + p.n])) / nb)
-            o += p.n
-        return worst
-
-    h32, x32, step32 = batched(HLU_FP32)
-    l0 = h32.stats()["kernels_launched"]
-    with ClockSampler(local) as clk:
-        t32, out32 = timed(step32, args.steps, args.warmup)
-    # every step launches the same kernels: the timed steps' share of the count since creation
-    launches = (h32.stats()["kernels_launched"] - l0) * args.steps // max(1, args.steps + args.warmup)
-    st32 = h32.stats()
-    res32 = per_problem_resid(h32, x32)
-    h64, x64, step64 = batched(HLU_FP64)
-    t64b, out64 = timed(step64, max(2, args.steps // 2), 1)
-    res64 = per_problem_resid(h64, x64)
-    h64.close()
-
-    # the comparison: one FP64 handle per problem, factor + refinement, one after the other
-    hs = [HLU.from_problem(p, precision=HLU_FP64, stream=sptr) for p in probs]
-    bs = [to_device_panel(p.b) for p in probs]
-    xs = [torch.zeros_like(b) for b in bs]
-
-    def loop():
-        its = 0
-        for h, p, b, x in zip(hs, probs, bs, xs):
-            h.factor(p.eps)
-            its = max(its, h.solve_refined(b, x, tol=TOL, max_iter=30)[0])
-        return its
-    tloop, outl = timed(loop, max(2, args.steps // 2), 1)
-    for h in hs:
-        h.close()
-
-    # end to end through the public API: hlu_create_batch from host arrays, factor, pinned b in, x out
-    b_host = torch.tensor(np.ascontiguousarray(bstack.cpu().numpy().T)).pin_memory()
+    # end to end through the public API: hlu_create_batch from host arrays (validation, parallel
+    # planning, upload), the tuned launch setting, factor, b from pinned host memory, x back
+    b_host = torch.tensor(np.ascontiguousarray(np.concatenate([p.b for p in probs], axis=0).T)).pin_memory()
     x_host = torch.empty_like(b_host).pin_memory()
     h2d = sum(p.data.nbytes + p.row_cl.nbytes + p.col_cl.nbytes + p.kind.nbytes + p.rank.nbytes + p.offset.nbytes
               + p.tree.perm.nbytes + p.tree.begin.nbytes + p.tree.size.nbytes + p.tree.son0.nbytes
               + p.tree.son1.nbytes for p in probs) + b_host.numel() * 8
-    e2e_t = []
-    for i in range(3):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        h = HLU.batch(probs, precision=HLU_FP32, stream=sptr)
-        h.factor(eps)
-        bd = b_host.to("cuda", non_blocking=True).t()
-        xd = torch.zeros_like(bd)
-        h.solve_refined(bd, xd, tol=tol_stack, max_iter=30)
-        x_host.copy_(xd.t(), non_blocking=True)
-        torch.cuda.synchronize()
-        e2e_t.append(time.perf_counter() - t0)
-        create = h.stats()["create_ms"]
-        h.close()
-    e2e_s = sum(e2e_t[1:]) / 2
+    torch.cuda.synchronize()
+    te0 = time.perf_counter()
+    parts = make_parts(HLU_FP32, temp_reuse=1)
+    bd = b_host.to("cuda", non_blocking=True).t()
+    xd = torch.zeros_like(bd)
+    row0 = np.cumsum([0] + [p.n for p in probs])
+    for part in parts:
+        part.h.set_launch(choice["workers"], choice["flags"])
+        part.h.factor(part.eps)
+        if len(parts) == 1:
+            part.h.solve_refined(bd, xd, tol=part.tol, max_iter=30)
+        else:  # a part's stacked rows are its problems' rows, in order
+            sel = torch.as_tensor(np.concatenate([np.arange(row0[i], row0[i + 1]) for i in part.idx]), device="cuda")
+            bi = bd[sel, 0].reshape(1, -1).t()
+            xi = torch.zeros_like(bi)
+            part.h.solve_refined(bi, xi, tol=part.tol, max_iter=30)
+            xd[sel, 0] = xi[:, 0]
+    x_host.copy_(xd.t(), non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - te0
+    for part in parts:
+        part.h.close()
 
-    B = len(probs)
+    fp64_peak, fp32_peak = probe_alu_peaks()
+    achieved = fl_factor / (factor_ms * 1e-3) / 1e12 if factor_ms else None
+    cpu = None
+    if rank == 0:
+        try:
+            o = oracle_batch_sample(args.workload)
+            cpu = {"value": o["problems"] / o["seconds"], "unit": "problems/s", "cores": 1, "kind": "oracle",
+                   "sample": f"FP64 oracle H-LU + solve of the batch's {o['problems']} smallest problems "
+                             f"(r = {o['r']}, n = {o['n']}, host-built leaves), {o['seconds']:.1f} s on 1 host "
+                             f"thread"}
+        except Exception as e:  # the baseline is context; the line stands without it
+            cpu = {"value": None, "unit": "problems/s", "cores": 1, "kind": "oracle", "error": str(e)[-300:]}
     if rank == 0:
         ns = sorted({p.n for p in probs})
+        w = BATCHES[args.workload]
         line = {
             "metric": "batched H-LU: problems factorised and solved to 1e-10 per second", "value": B * world / (t32 * 1e-3),
             "unit": "problems/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t32,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 factors; f64 truncation-core SVD, residual and solution", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {B} ellipsoids, n in {ns}, leaf 32, eta 2, eps per problem "
-                                   f"in {sorted(set(eps))}, 1 rhs each, tol 1e-10 per problem",
+            "config": {"workload": f"{args.workload}: {B} ellipsoids, refinement {w['levels']} (n in {ns}), "
+                                   f"leaf {w['leaf']}, eta {w['eta']}, eps per problem in {sorted(set(eps))}, "
+                                   f"axes {w.get('axes_range', '(1, U[0.4,1], U[0.4,1])')}, 1 rhs each, "
+                                   f"tol 1e-10 per problem; leaf data built on the GPU",
                        "n_total": int(sum(p.n for p in probs)), "leaves": int(sum(p.n_leaves for p in probs)),
-                       "parallelism": f"replicas x{world}",
-                       "l2": f"inputs larger than L2 (factor arena {st32['device_bytes'] / 1e9:.1f} GB)"},
-            "batched_fp32_ms": t32, "batched_fp64_ms": t64b, "loop_fp64_ms": tloop,
-            "speedup_vs_fp64_loop": tloop / t32, "batched_fp64_vs_fp64_loop": tloop / t64b,
-            "ir_iters": {"batched_fp32": out32[-1][0], "batched_fp64": out64[-1][0], "loop_fp64_max": outl[-1]},
-            "worst_problem_resid": {"batched_fp32": res32, "batched_fp64": res64},
-            "factor_model_gflop": st32["model_flops"] / 1e9, "max_rank": st32["max_rank"],
-            "plan": {"tasks": st32["n_tasks"], "launches_per_factor": st32["n_launches"]},
+                       "problems_by_n": {str(n): sum(p.n == n for p in probs) for n in ns},
+                       "parallelism": f"replicas x{world}", "handles": len(st),
+                       "l2": f"inputs larger than L2 (device memory {dev_bytes / 1e9:.1f} GB)"},
+            "batched_fp32_ms": t32, "loop_fp64_ms": tloop, "loop_fp64_wall_s": loop_wall_s,
+            "speedup_vs_fp64_loop": tloop / t32,
+            "ir_iters": {"batched_fp32": its32, "loop_fp64_max": loop_its},
+            "worst_problem_resid": {"batched_fp32": res32, "loop_fp64": loop_worst},
+            "efac_stacked_fp32": efac_stacked,
+            "factor_model_gflop": fl_factor / 1e9, "max_rank": max(s["max_rank"] for s in st),
+            "plan": {"tasks": sum(s["n_tasks"] for s in st), "create_ms": plan_ms},
+            "tuner": {"sample_problems": len(sample_idx), "choice": choice,
+                      "trials": [{"workers": c["workers"], "flags": c["flags"], "s": round(t, 4)} for c, t in trials]},
+            "host_structure_s": structure_s, "gpu_construct_s": construct_s, "create_s": create_s,
             "e2e": {"value": B / e2e_s, "unit": "problems/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(x_host.numel() * 8), "ms_per_step": e2e_s * 1e3,
-                    "create_ms_last": create,
-                    "includes": "hlu_create_batch (validation, planning, upload) + factor + refinement + copies"},
+                    "includes": "hlu_create_batch (validation, parallel planning, upload) + factor + refinement + "
+                                "copies, one step"},
+            "roofline": {"kernel": "k_dataflow<float> (factorisation)", "bound": "alu", "achieved": achieved,
+                         "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": achieved / fp32_peak if achieved and fp32_peak else None, "traffic": None,
+                         "peak_source": "measured FP32 FMA probe (hlu_probe_alu_peaks), of measured",
+                         "factor_kernel_ms": factor_ms},
+            "cpu_baseline": cpu,
             "gpu_launches": launches, "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
-    h32.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -111,42 +111,44 @@ struct Joined {
     }
 };
 
-void size_joined(Plan &q, const PlanBase &tot) {
-    q.getrf.resize(tot.kind[K_GETRF]);
-    q.trsm.resize(tot.kind[K_TRSM]);
-    q.project.resize(tot.kind[K_PROJECT]);
-    q.accum.resize(tot.kind[K_ACCUM]);
-    q.radd.resize(tot.kind[K_RADD]);
-    q.split.resize(tot.kind[K_SPLIT]);
-    for (int k = 0; k < K_NKINDS; ++k) q.wave[k].resize(tot.kind[k]);
-    q.terms.resize(tot.terms);
-    q.pieces.resize(tot.pieces);
-    q.task_code.resize(tot.tasks);
-    q.indeg.resize(tot.tasks);
-    q.succ_ptr.assign(tot.tasks + 1, 0);  // (the predecessor lists, used only while planning, are not kept)
-    q.succ_idx.resize(tot.edges);
-    q.roots.resize(tot.roots);
-    q.root_bl.resize(tot.roots);
+// Capacity for the joined plan; the problems' plans are appended in problem order (pages are
+// touched only as they are filled, while every problem's own plan is freed after its append, so
+// the host holds about one copy of the plans at any time).
+void reserve_joined(Plan &q, const PlanBase &tot) {
+    q.getrf.reserve(tot.kind[K_GETRF]);
+    q.trsm.reserve(tot.kind[K_TRSM]);
+    q.project.reserve(tot.kind[K_PROJECT]);
+    q.accum.reserve(tot.kind[K_ACCUM]);
+    q.radd.reserve(tot.kind[K_RADD]);
+    q.split.reserve(tot.kind[K_SPLIT]);
+    for (int k = 0; k < K_NKINDS; ++k) q.wave[k].reserve(tot.kind[k]);
+    q.terms.reserve(tot.terms);
+    q.pieces.reserve(tot.pieces);
+    q.task_code.reserve(tot.tasks);
+    q.indeg.reserve(tot.tasks);
+    q.succ_ptr.reserve(tot.tasks + 1);  // (the predecessor lists, used only while planning, are not kept)
+    q.succ_ptr.push_back(0);
+    q.succ_idx.reserve(tot.edges);
+    q.roots.reserve(tot.roots);
+    q.root_bl.reserve(tot.roots);
     q.n_tasks = tot.tasks;
     q.n_edges = tot.edges;
 }
 
-// Copies problem plan p into the joined plan q at bases b, shifting everything by s.
+// Appends problem plan p (bases b: the sizes of the joined arrays so far) to the joined plan q,
+// shifting everything by s.
 void join_plan(const Plan &p, const PlanBase &b, const Shift &s, Plan &q) {
-    for (size_t i = 0; i < p.getrf.size(); ++i) {
-        TGetrf t = p.getrf[i];
+    for (TGetrf t : p.getrf) {
         t.off = s.off(t.off);
         t.leaf = s.store(t.leaf);
-        q.getrf[b.kind[K_GETRF] + i] = t;
+        q.getrf.push_back(t);
     }
-    for (size_t i = 0; i < p.trsm.size(); ++i) {
-        TTrsm t = p.trsm[i];
+    for (TTrsm t : p.trsm) {
         t.L_off = s.off(t.L_off);
         s.panel(t.P);
-        q.trsm[b.kind[K_TRSM] + i] = t;
+        q.trsm.push_back(t);
     }
-    for (size_t i = 0; i < p.project.size(); ++i) {
-        TProject t = p.project[i];
+    for (TProject t : p.project) {
         s.panel(t.F);
         s.panel(t.X);
         s.panel(t.T);
@@ -154,24 +156,21 @@ void join_plan(const Plan &p, const PlanBase &b, const Shift &s, Plan &q) {
         t.src0 = s.slot_of(t.src0);
         t.dst1 = s.slot_of(t.dst1);
         t.src1 = s.slot_of(t.src1);
-        q.project[b.kind[K_PROJECT] + i] = t;
+        q.project.push_back(t);
     }
-    for (size_t i = 0; i < p.accum.size(); ++i) {
-        TAccum t = p.accum[i];
+    for (TAccum t : p.accum) {
         s.panel(t.out);
         t.term0 += int32_t(b.terms);
         t.dst = s.slot_of(t.dst);
         t.src = s.slot_of(t.src);
-        q.accum[b.kind[K_ACCUM] + i] = t;
+        q.accum.push_back(t);
     }
-    for (size_t i = 0; i < p.terms.size(); ++i) {
-        Term t = p.terms[i];
+    for (Term t : p.terms) {
         s.panel(t.A);
         s.panel(t.X);
-        q.terms[b.terms + i] = t;
+        q.terms.push_back(t);
     }
-    for (size_t i = 0; i < p.radd.size(); ++i) {
-        TRadd t = p.radd[i];
+    for (TRadd t : p.radd) {
         t.U_off = s.off(t.U_off);
         t.V_off = s.off(t.V_off);
         t.scratch_off = s.off(t.scratch_off);
@@ -179,36 +178,33 @@ void join_plan(const Plan &p, const PlanBase &b, const Shift &s, Plan &q) {
         t.piece0 += int32_t(b.pieces);
         t.target = s.store(t.target);
         t.inst = s.inst;
-        q.radd[b.kind[K_RADD] + i] = t;
+        q.radd.push_back(t);
     }
-    for (size_t i = 0; i < p.pieces.size(); ++i) {
-        Piece t = p.pieces[i];
+    for (Piece t : p.pieces) {
         s.panel(t.U);
         s.panel(t.V);
-        q.pieces[b.pieces + i] = t;
+        q.pieces.push_back(t);
     }
-    for (size_t i = 0; i < p.split.size(); ++i) {
-        TSplit t = p.split[i];
+    for (TSplit t : p.split) {
         s.panel(t.srcU);
         s.panel(t.srcV);
         t.dstU = s.off(t.dstU);
         t.dstV = s.off(t.dstV);
         t.src_kslot = s.slot_of(t.src_kslot);
         t.dst_kslot = s.slot_of(t.dst_kslot);
-        q.split[b.kind[K_SPLIT] + i] = t;
+        q.split.push_back(t);
     }
-    for (int k = 0; k < K_NKINDS; ++k)
-        std::copy(p.wave[k].begin(), p.wave[k].end(), q.wave[k].begin() + b.kind[k]);
+    for (int k = 0; k < K_NKINDS; ++k) q.wave[k].insert(q.wave[k].end(), p.wave[k].begin(), p.wave[k].end());
     for (int64_t g = 0; g < p.n_tasks; ++g) {
         const int32_t c = p.task_code[g], k = c >> kCodeShift;
-        q.task_code[b.tasks + g] = (k << kCodeShift) | int32_t((c & kCodeMask) + b.kind[k]);
-        q.indeg[b.tasks + g] = p.indeg[g];
-        q.succ_ptr[b.tasks + g + 1] = int32_t(p.succ_ptr[g + 1] + b.edges);
+        q.task_code.push_back((k << kCodeShift) | int32_t((c & kCodeMask) + b.kind[k]));
+        q.indeg.push_back(p.indeg[g]);
+        q.succ_ptr.push_back(int32_t(p.succ_ptr[g + 1] + b.edges));
     }
-    for (size_t e = 0; e < p.succ_idx.size(); ++e) q.succ_idx[b.edges + e] = int32_t(p.succ_idx[e] + b.tasks);
+    for (int32_t t : p.succ_idx) q.succ_idx.push_back(int32_t(t + b.tasks));
     for (size_t r = 0; r < p.roots.size(); ++r) {
-        q.roots[b.roots + r] = int32_t(p.roots[r] + b.tasks);
-        q.root_bl[b.roots + r] = p.root_bl[r];
+        q.roots.push_back(int32_t(p.roots[r] + b.tasks));
+        q.root_bl.push_back(p.root_bl[r]);
     }
 }
 
@@ -449,58 +445,47 @@ int Planner::plan_batch() {
         fplan = Plan();
         splan = Plan();
         mplan = Plan();
-        size_joined(fplan, ft);
-        size_joined(splan, st_);
-        size_joined(mplan, mt);
+        reserve_joined(fplan, ft);
+        reserve_joined(splan, st_);
+        reserve_joined(mplan, mt);
     } catch (const std::bad_alloc &) {
         error = "host memory exhausted while joining the plans";
         return HLU_ENOMEM;
     }
-    // join, one problem per thread at a time (disjoint ranges of the joined arrays)
-    next = 0;
-    auto joiner = [&] {
-        for (;;) {
-            const int32_t i = next.fetch_add(1);
-            if (i >= count) return;
-            Planner &q = *parts[i];
-            const Shift &f = fs[i], &a = as[i];
-            std::copy(q.slot_init.begin(), q.slot_init.end(), slot_init.begin() + f.slot);
-            for (size_t j = 0; j < q.fstore.size(); ++j) {
-                Store s = q.fstore[j];
-                s.t += f.cluster;
-                s.s += f.cluster;
-                s.D_off = f.off(s.D_off);
-                s.U_off = f.off(s.U_off);
-                s.V_off = f.off(s.V_off);
-                s.kslot = f.slot_of(s.kslot);
-                fstore[f.store(int32_t(j))] = s;
-            }
-            for (int64_t j = 0; j < q.n_leaves; ++j) {
-                Store s = q.astore[j];
-                s.t += a.cluster;
-                s.s += a.cluster;
-                s.D_off = a.off(s.D_off);
-                s.U_off = a.off(s.U_off);
-                s.V_off = a.off(s.V_off);
-                astore[a.leaf + j] = s;
-            }
-            for (size_t j = 0; j < q.inv_cl.size(); ++j) {
-                inv_cl[inv_base[i] + j] = q.inv_cl[j] + f.cluster;
-                inv_L_off[inv_base[i] + j] = f.off(q.inv_L_off[j]);
-                inv_U_off[inv_base[i] + j] = f.off(q.inv_U_off[j]);
-                inv_index[q.inv_cl[j] + f.cluster] = int32_t(inv_base[i] + j);
-            }
-            join_plan(q.fplan, fb[i], f, fplan);
-            join_plan(q.splan, sb[i], f, splan);
-            join_plan(q.mplan, mb[i], a, mplan);
-            parts[i].reset();  // its memory back before the next problem
+    // join in problem order, freeing every problem's plan after its append
+    for (int32_t i = 0; i < count; ++i) {
+        Planner &q = *parts[i];
+        const Shift &f = fs[i], &a = as[i];
+        std::copy(q.slot_init.begin(), q.slot_init.end(), slot_init.begin() + f.slot);
+        for (size_t j = 0; j < q.fstore.size(); ++j) {
+            Store s = q.fstore[j];
+            s.t += f.cluster;
+            s.s += f.cluster;
+            s.D_off = f.off(s.D_off);
+            s.U_off = f.off(s.U_off);
+            s.V_off = f.off(s.V_off);
+            s.kslot = f.slot_of(s.kslot);
+            fstore[f.store(int32_t(j))] = s;
         }
-    };
-    {
-        std::vector<std::thread> pool;
-        for (int32_t t = 1; t < nthreads; ++t) pool.emplace_back(joiner);
-        joiner();
-        for (std::thread &th : pool) th.join();
+        for (int64_t j = 0; j < q.n_leaves; ++j) {
+            Store s = q.astore[j];
+            s.t += a.cluster;
+            s.s += a.cluster;
+            s.D_off = a.off(s.D_off);
+            s.U_off = a.off(s.U_off);
+            s.V_off = a.off(s.V_off);
+            astore[a.leaf + j] = s;
+        }
+        for (size_t j = 0; j < q.inv_cl.size(); ++j) {
+            inv_cl[inv_base[i] + j] = q.inv_cl[j] + f.cluster;
+            inv_L_off[inv_base[i] + j] = f.off(q.inv_L_off[j]);
+            inv_U_off[inv_base[i] + j] = f.off(q.inv_U_off[j]);
+            inv_index[q.inv_cl[j] + f.cluster] = int32_t(inv_base[i] + j);
+        }
+        join_plan(q.fplan, fb[i], f, fplan);
+        join_plan(q.splan, sb[i], f, splan);
+        join_plan(q.mplan, mb[i], a, mplan);
+        parts[i].reset();
     }
     // graph-wide figures (the problems run side by side), and the roots of all problems in one
     // order of priority (longest remaining path first), as a single plan orders its own
