@@ -143,25 +143,84 @@ def oracle_sample(workload, level, reps):
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+def cpu_info():
+    """The host CPU as lscpu names it, and the hardware threads."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() in ("Model name", "Model"):
+                model = ln.split(":", 1)[1].strip()
+                if not model.isdigit():
+                    break
+    except Exception:
+        pass
+    return {"cpu_model": model, "nproc": os.cpu_count()}
+
+
+def _oracle_full_worker(workload):
+    """Run in a subprocess (its thread count set by the caller): the FP64 oracle's H-LU and solve of a
+    whole named workload."""
+    from bem_inputs import WORKLOADS, build_problem
+    from oracle import HLUOracle
+    from oracle.errors import lu_solve
+    p = build_problem(**WORKLOADS[workload])
+    t0 = time.perf_counter()
+    o = HLUOracle(p, p.eps).factor()
+    t1 = time.perf_counter()
+    lu_solve(o.A, p.b_perm())
+    t2 = time.perf_counter()
+    print(json.dumps({"n": p.n, "leaves": p.n_leaves, "factor_s": t1 - t0, "solve_s": t2 - t1,
+                      "flops": o.c.total()}))
+
+
+def oracle_full(workload, threads):
+    """The whole workload on the oracle: `threads` = 1 (one core) or the host's cores (numpy's BLAS
+    on all of them; the oracle's recursion itself is sequential)."""
+    t = str(int(threads))
+    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t, CUDA_VISIBLE_DEVICES="")
+    code = "import sys; sys.path.insert(0, %r); import bench; bench._oracle_full_worker(%r)" % (ROOT, workload)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError("oracle run failed:\n" + r.stderr[-2000:])
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    res["threads"] = int(threads)
+    res["gflops"] = res["flops"] / (res["factor_s"] + res["solve_s"]) / 1e9
+    return res
+
+
+def workload_config(args, w, p, world):
+    """The `config` of a single-problem line (the same for the native and the reference arm)."""
+    return {"workload": f"{args.workload}: {GEOMETRY[w.get('dim', 3)]} n={p.n}, leaf {w['leaf']}, "
+                        f"eta={w['eta']:g}, eps={w['eps']:g}, {p.nrhs} rhs ~ N(0,1) seed 0, tol 1e-10",
+            "n": p.n, "leaves": p.n_leaves, "nrhs": p.nrhs,
+            "l2": f"inputs larger than L2 (A_H leaf data {p.data.nbytes / 1e9:.2f} GB)",
+            "parallelism": f"replicas x{world}",
+            "solver": f"GMRES({args.restart})" if args.solver == "gmres" else "iterative refinement"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
     reps = args.warmup + args.steps
-    from bem_inputs import WORKLOADS
-    level = sample_level(20 * 4 ** WORKLOADS[args.workload]["r"], REF_SAMPLE_N)
+    from bem_inputs import WORKLOADS, build_problem
+    w = dict(WORKLOADS[args.workload])
+    p = build_problem(**w)  # the configuration's H-matrix (cached on disk after the first build)
+    level = sample_level(p.n, REF_SAMPLE_N)
     res = oracle_sample(args.workload, level, reps)
     ts = res["times"][args.warmup:]
     step = sum(ts) / len(ts)
     gflops = res["flops"] / step / 1e9
-    sample = (f"FP64 oracle H-LU of the leading level-{level} diagonal block (n={res['n']}, "
-              f"{res['leaves']} leaves) of the {args.workload} H-matrix per step, factor only, 1 thread")
+    sample = (f"each step: FP64 oracle H-LU of the leading level-{level} diagonal block (n={res['n']}, "
+              f"{res['leaves']} leaves) of this configuration's H-matrix, factor only, 1 thread")
     line = {
         "impl": "reference", "metric": METRIC, "value": gflops, "unit": "GFLOP/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "sample": sample},
-        "cpu_baseline": {"value": gflops, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "config": workload_config(args, w, p, args.gpus),
+        "cpu_baseline": dict({"value": gflops, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+                             **cpu_info()),
         "e2e": {"value": gflops, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -456,6 +515,14 @@ def run_native(args):
                    "sample": (f"FP64 oracle H-LU (factor only) of the leading level-{level} diagonal "
                               f"block, n={res['n']}, {res['leaves']} leaves, of the same H-matrix; "
                               f"{res['times'][0]:.1f} s on 1 host thread")}
+            cpu.update(cpu_info())
+            if args.workload == WORKLOAD and not args.no_c3:
+                # the whole n = 5120 configuration (factor + solve) on one core and on all of them
+                full = {}
+                for th in (1, os.cpu_count() or 1):
+                    r = oracle_full("sphere5120", th)
+                    full["threads_%d" % th] = {k: r[k] for k in ("n", "leaves", "factor_s", "solve_s", "gflops")}
+                cpu["full_sphere5120"] = full
         except Exception as e:  # reported, not fatal
             cpu = {"value": None, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
 
@@ -466,11 +533,8 @@ def run_native(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 factors; f64 SVD of every truncation core (QR of R'^T + Jacobi), f64 residual and solution",
             "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {GEOMETRY[w.get('dim', 3)]} n={p.n}, leaf {w['leaf']}, "
-                                   f"eta={w['eta']:g}, eps={w['eps']:g}, {p.nrhs} rhs ~ N(0,1) seed 0, tol 1e-10",
-                       "n": p.n, "leaves": p.n_leaves, "nrhs": p.nrhs, "l2": "inputs larger than L2 (factor arena "
-                       f"{st32['device_bytes'] / 1e9:.1f} GB)", "parallelism": f"replicas x{world}",
-                       "solver": f"GMRES({args.restart})" if args.solver == "gmres" else "iterative refinement"},
+            "config": workload_config(args, w, p, world),
+            "device_gb": st32["device_bytes"] / 1e9,
             "time_to_1e10_ms": t_ms / args.steps, "solves_per_s": p.nrhs * args.steps * world / (t_ms * 1e-3),
             "p50_ms": pct(per, 0.5), "p99_ms": pct(per, 0.99), "ir_iters": arm32["iters"][-1],
             "rank_hist": rank_hist(st32),
@@ -738,9 +802,40 @@ def run_batch(args):
                 o += n
             return worst
 
+    def host_available():
+        """Bytes of host memory this process may still use (MemAvailable, and the cgroup limit)."""
+        avail = None
+        try:
+            with open("/proc/meminfo") as f:
+                for ln in f:
+                    if ln.startswith("MemAvailable:"):
+                        avail = int(ln.split()[1]) * 1024
+        except OSError:
+            pass
+        try:
+            with open("/sys/fs/cgroup/memory.max") as f:
+                lim = f.read().strip()
+            with open("/sys/fs/cgroup/memory.current") as f:
+                cur = int(f.read().strip())
+            if lim != "max":
+                avail = min(avail or 1 << 62, int(lim) - cur)
+        except (OSError, ValueError):
+            pass
+        return avail
+
     def make_parts(precision, **kw):
-        """The whole batch in one handle; halves (balanced by leaves) while it does not fit."""
+        """The whole batch in one handle; halves (balanced by leaves) while it does not fit the
+        device.  Creating one handle holds, on the host, about 350 bytes per task while it plans (at
+        most about 95 tasks per leaf at leaf 32) and two copies of its leaf data while it uploads, so
+        the first split also keeps that within 70 % of the host memory available."""
+        avail = host_available()
+        need = sum(350 * 95 * p.n_leaves + 2 * p.data.nbytes for p in probs)
+        first = 1
+        while avail is not None and first < 8 and need / first > 0.7 * avail:
+            first *= 2
         for parts in (1, 2, 4, 8):
+            if parts < first:
+                continue
             made = []
             try:
                 for idx in _split_balanced(probs, parts):
@@ -912,6 +1007,7 @@ def run_batch(args):
             "tuner": {"sample_problems": len(sample_idx), "choice": choice,
                       "trials": [{"workers": c["workers"], "flags": c["flags"], "s": round(t, 4)} for c, t in trials]},
             "host_structure_s": structure_s, "gpu_construct_s": construct_s, "create_s": create_s,
+            "host_mem_available_gb": (host_available() or 0) / 1e9,
             "e2e": {"value": B / e2e_s, "unit": "problems/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(x_host.numel() * 8), "ms_per_step": e2e_s * 1e3,
                     "includes": "hlu_create_batch (validation, parallel planning, upload) + factor + refinement + "

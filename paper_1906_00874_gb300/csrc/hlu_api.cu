@@ -289,7 +289,7 @@ void run_plan(hlu_ctx *h, const DevPlan &d, void *arena, double *flops) {
         cudaMemcpyAsync(d.queue, d.roots, sizeof(int32_t) * d.n_roots, cudaMemcpyDeviceToDevice, h->stream);
         if (h->inject_stall && &d == &h->fp && d.n_tasks > 0) {  // test hook: the last task waits forever
             const int32_t last = d.n_tasks - 1;
-            launch_set_slot(d.indeg, last, h->pl.fplan.indeg[last] + 1, h->stream);
+            launch_set_slot(d.indeg, last, h->pl.fplan.last_indeg + 1, h->stream);
             h->inject_stall = false;
         }
         cudaMemsetAsync(d.counters, 0, 3 * sizeof(int32_t), h->stream);
@@ -520,6 +520,10 @@ static int create_impl(const hlu_tree *tree, const hlu_blocks *blocks, const hlu
     if (st == HLU_OK) st = upload_plan(h, h->pl.splan, h->sp, kmax);
     if (st == HLU_OK) st = upload_plan(h, h->pl.mplan, h->mp, kmax);
     if (st == HLU_OK) st = cuda_status(cudaStreamSynchronize(h->stream));
+    if (st == HLU_OK) {  // the device holds the graphs now: the host keeps the layout and the figures
+        h->pl.release_work();
+        for (Plan *p : {&h->pl.fplan, &h->pl.splan, &h->pl.mplan}) p->release_tasks();
+    }
     if (st != HLU_OK) {
         hlu_destroy(h);
         return st;
@@ -1070,12 +1074,7 @@ int hlu_get_stats(hlu_t h, hlu_stats *o) {
     o->solve_waves = s.n_waves;
     o->solve_launches = (int64_t)s.launches.size() + 3;
     o->device_bytes = h->device_bytes;
-    o->tasks_by_kind[0] = (int64_t)f.getrf.size();
-    o->tasks_by_kind[1] = (int64_t)f.trsm.size();
-    o->tasks_by_kind[2] = (int64_t)f.project.size();
-    o->tasks_by_kind[3] = (int64_t)f.accum.size();
-    o->tasks_by_kind[4] = (int64_t)f.radd.size();
-    o->tasks_by_kind[5] = (int64_t)f.split.size();
+    for (int k = 0; k < K_NKINDS; ++k) o->tasks_by_kind[k] = f.kind_count[k];
     o->max_stacked = f.max_kcap;
     o->kernels_launched = h->kernels_launched;
     o->create_ms[0] = h->create_ms[0];

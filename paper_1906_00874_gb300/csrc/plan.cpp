@@ -49,6 +49,28 @@ void Planner::release_work() {
     }
 }
 
+void Plan::release_tasks() {
+    kind_count[K_GETRF] = (int64_t)getrf.size();
+    kind_count[K_TRSM] = (int64_t)trsm.size();
+    kind_count[K_PROJECT] = (int64_t)project.size();
+    kind_count[K_ACCUM] = (int64_t)accum.size();
+    kind_count[K_RADD] = (int64_t)radd.size();
+    kind_count[K_SPLIT] = (int64_t)split.size();
+    last_indeg = indeg.empty() ? 0 : indeg.back();
+    std::vector<TGetrf>().swap(getrf);
+    std::vector<TTrsm>().swap(trsm);
+    std::vector<TProject>().swap(project);
+    std::vector<TAccum>().swap(accum);
+    std::vector<TRadd>().swap(radd);
+    std::vector<TSplit>().swap(split);
+    std::vector<Term>().swap(terms);
+    std::vector<Piece>().swap(pieces);
+    for (auto &w : wave) std::vector<int32_t>().swap(w);
+    for (std::vector<int32_t> *v : {&task_code, &pred_ptr, &pred_idx, &succ_ptr, &succ_idx, &indeg, &roots})
+        std::vector<int32_t>().swap(*v);
+    std::vector<float>().swap(root_bl);
+}
+
 // ------------------------------------------------------------------ objects
 int32_t Planner::new_obj(int32_t row_cl, int32_t col_cl, int32_t nr_if_none) {
     Obj o;

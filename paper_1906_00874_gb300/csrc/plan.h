@@ -95,6 +95,13 @@ struct Plan {
     // product temporaries: elements in all, and the largest sum over one dependency level of the
     // temporaries in use at that level (from their first writer's level to their last reader's)
     int64_t temp_elems = 0, temp_peak_elems = 0;
+    // tasks per kind and the in-degree of the last task, kept when the task arrays are released
+    int64_t kind_count[K_NKINDS] = {0, 0, 0, 0, 0, 0};
+    int32_t last_indeg = 0;
+
+    // Frees the task arrays and the graph (once they are on the device), keeping the figures above,
+    // the sizes and the wave launches.
+    void release_tasks();
 };
 
 struct PlanOptions {
@@ -166,13 +173,14 @@ public:
     // Lays out the arenas and emits the factorisation, solve and matvec plans.
     int plan_all();
 
+    // Frees the emission state (cells, objects, block tree, predecessor lists) once the plans are made.
+    void release_work();
+
 private:
     bool batch_deferred = false;  // a batch whose problems plan_all plans separately (plan_batch)
     int plan_batch();
     bool batch_layout(std::vector<int32_t> &cb, std::vector<int32_t> &ce, std::vector<int64_t> &lb,
                       std::vector<int32_t> &rb) const;
-    // frees the emission state (cells, objects, block tree) once the plans are made
-    void release_work();
 
     // current plan being emitted
     Plan *P = nullptr;
