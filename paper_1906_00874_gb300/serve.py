@@ -9,7 +9,9 @@ that the device holds several requests' work at once:
 
 * admission threads create and factorise new groups (each problem with its own eps,
   hlu_factor_batch), several at once so that their host planning runs in parallel; the creations in
-  flight share the budget left free.  An admission evicts least-recently-used idle groups when the
+  flight share the budget left free.  New problems wait in one queue, and a thread that starts takes
+  up to max_group of them as one group: problems that arrive while every admission thread is busy
+  are admitted together.  An admission evicts least-recently-used idle groups when the
   device-memory budget is short; when nothing can be evicted yet it waits until a running job ends
   and frees memory, and it splits a group that cannot fit on its own;
 * solve threads run, per group, one stacked refined solve of the requests that have arrived for it
@@ -89,7 +91,7 @@ class Server:
         self.temp_reuse = temp_reuse  # hlu_opts.temp_reuse of the groups (1: half the memory, slower planning)
         self.groups: list[_Group] = []
         self.where: dict[object, _Group] = {}
-        self.admitting: dict[object, concurrent.futures.Future] = {}  # key -> future of its group
+        self.admitting: set = set()  # keys dispatched for admission and not resident yet
         self.waiting: dict[object, list] = collections.defaultdict(list)  # key being admitted -> requests
         self.queue: collections.deque[Request] = collections.deque()
         self.stats = collections.Counter()
@@ -101,7 +103,9 @@ class Server:
         self._errors: list[BaseException] = []
         self._creating = 0         # creations in flight (they share the free budget)
         self._reserved = 0         # bytes of budget handed to the creations in flight
-        self._jobs_active = 0      # admission jobs submitted and not finished
+        self._pending: list = []   # keys dispatched and not yet taken by an admission job, in order
+        self._pending_probs: dict = {}
+        self._admit_futs: list = []
         self.admit_threads = int(admit_threads)
         self._admit_pool = concurrent.futures.ThreadPoolExecutor(admit_threads, thread_name_prefix="hlu-admit")
         self._solve_pool = concurrent.futures.ThreadPoolExecutor(solve_threads, thread_name_prefix="hlu-solve")
@@ -145,7 +149,8 @@ class Server:
         last step() or drain()."""
         while True:
             with self._lock:
-                futs = [f for f in self.admitting.values()] + [g.tail for g in self.groups if g.tail is not None]
+                self._admit_futs = [f for f in self._admit_futs if not f.done()]
+                futs = list(self._admit_futs) + [g.tail for g in self.groups if g.tail is not None]
             pending = [f for f in futs if not f.done()]
             if not pending:
                 break
@@ -177,56 +182,61 @@ class Server:
         return e
 
     # ------------------------------------------------------------ admission
-    def _admit_job(self, keys, problems):
-        """Admission thread: create and factorise the groups of `keys` (at most max_group problems
-        each), evicting idle LRU groups to fit the budget, waiting for memory while other creations
-        or solves are running, and halving a group that cannot fit by itself.  Each group is
-        registered (and the solves of its waiting requests queued) as soon as it is factorised."""
-        try:
-            keys = list(keys)
-            while keys:
-                part, keys = keys[:self.max_group], keys[self.max_group:]
-                exclusive = False
-                while True:
-                    try:
-                        self._create(part, problems, exclusive)
-                        break
-                    except HLUError as e:
-                        if e.status != ENOMEM:
-                            raise
-                        with self._lock:
-                            if not exclusive:  # a share was not enough: next, all the free budget
-                                exclusive = True
-                                continue
-                            if self._creating > 0:  # another creation holds part of the budget
-                                self._freed.wait(timeout=1.0)
-                                continue
-                            idle = [v for v in self.groups if v.busy == 0]
-                            if idle:
-                                self._evict(min(idle, key=lambda v: v.last_used))
-                                continue
-                            if any(v.busy for v in self.groups):  # memory frees when a solve ends
-                                self._freed.wait(timeout=1.0)
-                                continue
-                        if len(part) > 1:  # nothing to evict and nothing running: fewer at a time
-                            keys = part[len(part) // 2:] + keys
-                            part = part[:len(part) // 2]
-                        else:
-                            raise
-        finally:
-            with self._lock:
-                self._jobs_active -= 1
-                self._freed.notify_all()
-
-    def _admit_failed(self, fut):
-        """Done-callback of an admission: on failure, forget the keys it did not admit (their
-        waiting requests are dropped; the error is raised by the next step())."""
-        if fut.exception() is None:
-            return
+    def _admit_next(self):
+        """Admission thread: take the oldest dispatched keys that no job has taken yet (at most
+        max_group: the requests that arrived while every admission thread was busy are admitted
+        together, as one group) and admit them."""
         with self._lock:
-            for k in [k for k, f in self.admitting.items() if f is fut]:
-                del self.admitting[k]
-                self.waiting.pop(k, None)
+            part = self._pending[:self.max_group]
+            del self._pending[:len(part)]
+            problems = {k: self._pending_probs.pop(k) for k in part}
+        if not part:
+            return
+        try:
+            self._admit_job(part, problems)
+        except BaseException:
+            with self._lock:  # forget the keys it did not admit; their waiting requests are dropped
+                for k in part:
+                    if k not in self.where:
+                        self.admitting.discard(k)
+                        self.waiting.pop(k, None)
+            raise
+
+    def _admit_job(self, keys, problems):
+        """Create and factorise the groups of `keys` (at most max_group problems each), evicting idle
+        LRU groups to fit the budget, waiting for memory while other creations or solves are
+        running, and halving a group that cannot fit by itself.  Each group is registered (and the
+        solves of its waiting requests queued) as soon as it is factorised."""
+        keys = list(keys)
+        while keys:
+            part, keys = keys[:self.max_group], keys[self.max_group:]
+            exclusive = False
+            while True:
+                try:
+                    self._create(part, problems, exclusive)
+                    break
+                except HLUError as e:
+                    if e.status != ENOMEM:
+                        raise
+                    with self._lock:
+                        if not exclusive:  # a share was not enough: next, all the free budget
+                            exclusive = True
+                            continue
+                        if self._creating > 0:  # another creation holds part of the budget
+                            self._freed.wait(timeout=1.0)
+                            continue
+                        idle = [v for v in self.groups if v.busy == 0]
+                        if idle:
+                            self._evict(min(idle, key=lambda v: v.last_used))
+                            continue
+                        if any(v.busy for v in self.groups):  # memory frees when a solve ends
+                            self._freed.wait(timeout=1.0)
+                            continue
+                    if len(part) > 1:  # nothing to evict and nothing running: fewer at a time
+                        keys = part[len(part) // 2:] + keys
+                        part = part[:len(part) // 2]
+                    else:
+                        raise
 
     def _register(self, g):
         """Make a new group resident and queue the solves of the requests waiting for its keys
@@ -236,7 +246,7 @@ class Server:
         reqs = []
         for k in g.keys:
             self.where[k] = g
-            self.admitting.pop(k, None)
+            self.admitting.discard(k)
             reqs += self.waiting.pop(k, [])
         if reqs:
             self._chain_solve(g, reqs)
@@ -256,7 +266,9 @@ class Server:
                     self._freed.wait(timeout=1.0)
                 claim = 1
             else:
-                claim = max(1, min(self._jobs_active, self.admit_threads) - self._creating)
+                # this creation, those in flight, and the groups still to be taken from the queue
+                waiting_groups = -(-len(self._pending) // self.max_group)
+                claim = max(1, min(self.admit_threads, self._creating + 1 + waiting_groups) - self._creating)
             free = self.budget - self.resident_bytes - self._reserved
             budget = free // claim
             if budget <= 0:
@@ -399,7 +411,7 @@ class Server:
                 for r in ready:
                     if r.key in self.where:
                         by_group[id(self.where[r.key])].append(r)
-                    else:  # solved once its group exists (the admission's done-callback)
+                    else:  # solved once its group is registered (_register)
                         if r.key not in self.admitting and r.key not in new:
                             new[r.key] = r.problem
                             r.refactored = True
@@ -408,14 +420,13 @@ class Server:
                     if id(g) in by_group:
                         self._chain_solve(g, by_group[id(g)])
                 keys = list(new)
-                for c0 in range(0, len(keys), self.max_group):  # groups planned in parallel
-                    part = keys[c0:c0 + self.max_group]
-                    self._jobs_active += 1
-                    fut = self._admit_pool.submit(self._admit_job, part, {k: new[k] for k in part})
-                    for k in part:
-                        self.admitting[k] = fut
+                self._pending += keys
+                self._pending_probs.update(new)
+                self.admitting.update(keys)
+                for _ in range(-(-len(keys) // self.max_group)):  # one job per group of new keys
+                    fut = self._admit_pool.submit(self._admit_next)
                     fut.add_done_callback(self._on_error)
-                    fut.add_done_callback(self._admit_failed)
+                    self._admit_futs.append(fut)
         return self._collect()
 
     def serve(self, requests, poll=1e-4):

@@ -237,3 +237,27 @@ def test_admission_and_solves_run_concurrently_and_step_does_not_block():
     # the solve of the resident problem 0 overlaps the factorisation of problem 1
     assert any(a[1] < b[2] and b[1] < a[2] for a in fac for b in sol)
     s.close()
+
+
+def test_problems_arriving_while_admission_is_busy_are_admitted_together():
+    """With one admission thread busy on a first problem, three problems that arrive meanwhile wait
+    in the queue and are admitted by the next job as one group (one handle), and every request is
+    answered from its own problem's rows."""
+    _SlowHLU.spans = []
+    _FakeHLU.created = []
+    probs = {k: _Prob(5 + k, k) for k in range(4)}
+    s = Server(mem_budget=1e9, device="cpu", handle_type=_SlowHLU, admit_threads=1)
+    g = np.random.default_rng(6)
+    reqs = [Request(k, probs[k], g.standard_normal((probs[k].n, 1)), arrival=float(k > 0), rid=k) for k in range(4)]
+    for r in reqs:
+        s.submit(r)
+    out = s.step(now=0.0)          # problem 0: its admission starts (factorisation takes 0.2 s)
+    time.sleep(0.05)
+    out += s.step(now=1.0)         # problems 1-3 arrive while the only admission thread is busy
+    out += s.drain()
+    assert sorted(r.rid for r in out) == [0, 1, 2, 3]
+    assert sorted(len(h.probs) for h in _FakeHLU.created) == [1, 3]
+    assert s.stats["groups_created"] == 2
+    for r in reqs:
+        assert np.allclose(probs[r.key].A @ r.x, r.b, atol=1e-10)
+    s.close()
