@@ -945,7 +945,8 @@ __device__ __forceinline__ double flt_to_dbl(float f) {
 // (|d| ~ 1e-7, so the neglected term is below double rounding): the rotation
 // is orthogonal to double precision, and only its angle is single-precision
 // accurate, which the convergence test on the double dot products absorbs.
-__device__ __forceinline__ void jacobi_rotation(double aa, double bb, double gg, double &c, double &s) {
+__device__ __forceinline__ void jacobi_rotation(double aa, double bb, double gg, double &c, double &s,
+                                                double &tan_theta) {
     const double q = bb - aa;
     // 2 gg and q scaled by 2^-e, e the binary exponent of 2 gg, as single-precision values
     int e = (int)((__double2hiint(gg) >> 20) & 0x7ff) - 1023 + 1;
@@ -963,6 +964,7 @@ __device__ __forceinline__ void jacobi_rotation(double aa, double bb, double gg,
     const double f = fma(d, fma(0.375, d, -0.5), 1.0);
     c = cd * f;
     s = sd * f;
+    tan_theta = flt_to_dbl(t);
 }
 
 // One-sided (Hestenes) Jacobi on the columns of D (r x r, double, shared
@@ -974,8 +976,14 @@ __device__ __forceinline__ void jacobi_rotation(double aa, double bb, double gg,
 // of both columns; when all groups fit in one warp, the rounds run in that
 // warp alone with warp barriers.  A pair is rotated while
 // |x.y|^2 > tol^2 |x|^2 |y|^2 with tol = 4 r eps_double, the rounding level of
-// the dot product itself; at most 30 sweeps.  Returns the number of sweeps.
-__device__ int block_jacobi(double *D, int r, int ld, int *flag) {
+// the dot product itself; at most 30 sweeps.  The squared column norms are
+// computed exactly at the start of every sweep (nrm, r values of shared
+// memory) and carried through its rounds by the rotation's own update
+// (x.x - t x.y, y.y + t x.y, t = tan theta), so a round forms only the dot
+// product x.y: one reduction instead of three on the FP64 pipe.  The norms only
+// steer the rotations and the test; the singular values are formed from the
+// final columns by the caller.  Returns the number of sweeps.
+__device__ int block_jacobi(double *D, int r, int ld, int *flag, double *nrm) {
     if (r < 2) return 0;
     const int np = (r + 1) & ~1, P = np / 2;
     int g = 32;
@@ -988,6 +996,12 @@ __device__ int block_jacobi(double *D, int r, int ld, int *flag) {
     while (sweep < 30) {
         ++sweep;
         if (threadIdx.x == 0) *flag = 0;
+        for (int j = threadIdx.x; j < r; j += blockDim.x) {
+            const double *cj = D + (int64_t)j * ld;
+            double v = 0.0;
+            for (int i = 0; i < r; ++i) v = fma(cj[i], cj[i], v);
+            nrm[j] = v;
+        }
         __syncthreads();
         if (!one_warp || threadIdx.x < 32) {  // uniform per warp
             for (int rd = 0; rd < np - 1; ++rd) {
@@ -1006,28 +1020,25 @@ __device__ int block_jacobi(double *D, int r, int ld, int *flag) {
                 }
                 const bool active = gid < P && q < r;
                 double *cp = D + (int64_t)p * ld, *cq = D + (int64_t)q * ld;
-                double aa = 0.0, bb = 0.0, gg = 0.0;
+                double gg = 0.0;
                 if (active)
-                    for (int i = gl; i < r; i += g) {
-                        const double x = cp[i], y = cq[i];
-                        aa = fma(x, x, aa);
-                        bb = fma(y, y, bb);
-                        gg = fma(x, y, gg);
-                    }
-                for (int o = g >> 1; o > 0; o >>= 1) {  // every lane of the warp takes part
-                    aa += __shfl_xor_sync(kFull, aa, o);
-                    bb += __shfl_xor_sync(kFull, bb, o);
+                    for (int i = gl; i < r; i += g) gg = fma(cp[i], cq[i], gg);
+                for (int o = g >> 1; o > 0; o >>= 1)  // every lane of the warp takes part
                     gg += __shfl_xor_sync(kFull, gg, o);
-                }
                 // the butterfly leaves identical sums in every lane of a group
+                const double aa = active ? nrm[p] : 0.0, bb = active ? nrm[q] : 0.0;
                 if (active && gg * gg > tol2 * aa * bb) {
                     if (gl == 0) *flag = 1;
-                    double cs, sn;
-                    jacobi_rotation(aa, bb, gg, cs, sn);
+                    double cs, sn, tn;
+                    jacobi_rotation(aa, bb, gg, cs, sn, tn);
                     for (int i = gl; i < r; i += g) {
                         const double x = cp[i], y = cq[i];
                         cp[i] = cs * x - sn * y;
                         cq[i] = sn * x + cs * y;
+                    }
+                    if (gl == 0) {
+                        nrm[p] = fma(-tn, gg, aa);
+                        nrm[q] = fma(tn, gg, bb);
                     }
                 }
                 if (one_warp)
@@ -1389,7 +1400,7 @@ __device__ int core_finish(const CoreBufs<R> &b, int mr, int nc, int r, const TR
             b.D[e] = i >= j ? (double)b.C[j + (size_t)i * nc] : 0.0;
         }
         __syncthreads();
-        sweeps = block_jacobi(b.D, r, r, b.iflag);
+        sweeps = block_jacobi(b.D, r, r, b.iflag, b.sig);
         for (int j = threadIdx.x; j < r; j += blockDim.x) {
             double s = 0.0;
             for (int i = 0; i < r; ++i) s += b.D[i + (size_t)j * r] * b.D[i + (size_t)j * r];
@@ -1402,7 +1413,7 @@ __device__ int core_finish(const CoreBufs<R> &b, int mr, int nc, int r, const TR
             b.D[e] = i >= j ? b.C[j + (size_t)i * nc] : 0.0;
         }
         __syncthreads();
-        sweeps = block_jacobi(b.D, r, r, b.iflag);
+        sweeps = block_jacobi(b.D, r, r, b.iflag, b.sig);
         for (int j = threadIdx.x; j < r; j += blockDim.x) {
             double s = 0.0;
             for (int i = 0; i < r; ++i) s += b.D[i + (size_t)j * r] * b.D[i + (size_t)j * r];
