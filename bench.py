@@ -1050,6 +1050,9 @@ def run_serve(args):
     build.build()
     rhs = [np.random.default_rng(sd).standard_normal((probs[k].n, c)) for k, c, sd in stream]
 
+    def pct(a, q):
+        return a[min(len(a) - 1, int(round(q * (len(a) - 1))))]
+
     def replay(arrivals, timeline=False):
         srv = Server(timeline=timeline)  # a stream per group, half the workers per launch, groups of <= 16
         reqs = [Request(k, probs[k], b, arrival=float(t), rid=i)
@@ -1067,6 +1070,20 @@ def run_serve(args):
         st = dict(srv.stats)
         lat = sorted((r.done - r.arrival) * 1e3 for r in reqs)
         return makespan, lat, st, reqs, ov
+
+    def breakdown(reqs):
+        """p50 / p99 latency of the requests that waited for a factorisation of their problem and of
+        those served from resident factors, and by problem size."""
+        out = {}
+        groups = {"waited_for_admission": [r for r in reqs if r.waited],
+                  "resident": [r for r in reqs if not r.waited]}
+        for n in sorted({probs[r.key].n for r in reqs}):
+            groups[f"n={n}"] = [r for r in reqs if probs[r.key].n == n]
+        for name, rs in groups.items():
+            v = sorted((r.done - r.arrival) * 1e3 for r in rs)
+            if v:
+                out[name] = {"count": len(v), "p50_ms": pct(v, 0.5), "p99_ms": pct(v, 0.99)}
+        return out
 
     def overlap(events, ref):
         """Device time during which a factorisation and a solve of another group were both running,
@@ -1106,8 +1123,6 @@ def run_serve(args):
     mk = sum(r[0] for r in runs)
     st = runs[-1][2]
 
-    def pct(a, q):
-        return a[min(len(a) - 1, int(round(q * (len(a) - 1))))]
     if rank == 0:
         nrhs = sum(c for _, c, _ in stream)
         line = {
@@ -1122,7 +1137,8 @@ def run_serve(args):
                        "parallelism": f"replicas x{world}", "l2": "inputs larger than L2"},
             "capacity_rps": capacity, "capacity_burst_rps": burst, "arrival_rate_rps": rate,
             "p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99), "mean_ms": float(np.mean(lat)),
-            "server": st, "device_overlap": runs[0][4], "gpu_launches": int(sum(r[2].get("kernels_launched", 0) for r in runs)),
+            "server": st, "device_overlap": runs[0][4],
+            "latency_breakdown": breakdown([r for run in runs for r in run[3]]), "gpu_launches": int(sum(r[2].get("kernels_launched", 0) for r in runs)),
             "e2e": {"value": len(stream) * len(runs) / mk, "unit": "requests/s",
                     "h2d_bytes_per_step": int(sum(b.nbytes for b in rhs) + sum(p.data.nbytes for p in probs)),
                     "d2h_bytes_per_step": int(sum(b.nbytes for b in rhs)),

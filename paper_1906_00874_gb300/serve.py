@@ -53,7 +53,8 @@ class Request:
     rid: int = 0
     x: np.ndarray | None = None
     done: float | None = None
-    refactored: bool = False
+    refactored: bool = False   # this request's problem was (re)factorised for it
+    waited: bool = False       # it waited for the admission of its problem
     iters: int = 0
 
 
@@ -416,6 +417,7 @@ class Server:
                             new[r.key] = r.problem
                             r.refactored = True
                         self.waiting[r.key].append(r)
+                        r.waited = True
                 for g in self.groups:
                     if id(g) in by_group:
                         self._chain_solve(g, by_group[id(g)])
