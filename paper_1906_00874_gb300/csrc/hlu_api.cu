@@ -82,7 +82,8 @@ struct hlu_ctx {
     int32_t *perm = nullptr;
     int64_t *leaf_desc = nullptr;
     double *ir = nullptr;     // refinement work: b, x, r (n x nrhs_max each) and 2 x nrhs_max norms
-    double *ir_host = nullptr;  // pinned copy of the norms
+    double *ir_host = nullptr;  // host copy of the norms (pageable: a pinned allocation would
+                                // synchronise the device with the work of every other stream)
     // GMRES: Krylov bases V ((m + 1) panels) and Z = M^{-1} V (m panels) of n x nrhs_max, small state
     int gm_m = 0;
     double *gm_V = nullptr, *gm_Z = nullptr, *gm_small = nullptr, *gm_host = nullptr;
@@ -126,7 +127,9 @@ int dalloc(hlu_ctx *h, X **p, size_t count) {
     *p = nullptr;
     size_t bytes = std::max<size_t>(count, 1) * sizeof(X);
     if (h->mem_budget > 0 && h->device_bytes + (int64_t)bytes > h->mem_budget) return HLU_ENOMEM;
-    if (cudaMalloc(reinterpret_cast<void **>(p), bytes) != cudaSuccess) {
+    // stream-ordered allocation: a plain cudaMalloc is an implicit synchronisation point between
+    // streams, so creating one handle would wait for the kernels of every other handle
+    if (cudaMallocAsync(reinterpret_cast<void **>(p), bytes, h->stream) != cudaSuccess) {
         cudaGetLastError();
         return HLU_ENOMEM;
     }
@@ -512,7 +515,7 @@ static int create_impl(const hlu_tree *tree, const hlu_blocks *blocks, const hlu
         st = cuda_status(cudaMemsetAsync(h->busy, 0, kBusyWords * sizeof(unsigned long long), h->stream));
     if (st == HLU_OK) st = cuda_status(cudaMemsetAsync(h->flops, 0, 16 * sizeof(double), h->stream));
     if (st == HLU_OK) st = dalloc(h, &h->ir, 3 * n * w + 2 * w);
-    if (st == HLU_OK) st = cuda_status(cudaMallocHost(reinterpret_cast<void **>(&h->ir_host), 2 * w * sizeof(double)));
+    if (st == HLU_OK && !(h->ir_host = new (std::nothrow) double[2 * w])) st = HLU_ENOMEM;
     if (st == HLU_OK) st = clear_error(h);
     if (st == HLU_OK) st = upload(h, &h->perm, h->pl.perm);
     const int kmax = h->pl.opt.kmax_core;
@@ -900,9 +903,8 @@ int hlu_solve_gmres(hlu_t h, const double *b, double *x, int32_t nrhs, int64_t l
         if ((st = dalloc(h, &h->gm_V, size_t(m + 1) * n * w))) return st;
         if ((st = dalloc(h, &h->gm_Z, size_t(m) * n * w))) return st;
         if ((st = dalloc(h, &h->gm_small, size_t(small)))) return st;
-        if (!h->gm_host &&
-            (st = cuda_status(cudaMallocHost(reinterpret_cast<void **>(&h->gm_host), 2 * w * sizeof(double)))))
-            return st;
+        if (!h->gm_host) h->gm_host = new (std::nothrow) double[2 * w];
+        if (!h->gm_host) return HLU_ENOMEM;
         h->gm_m = m;
     }
     const int64_t vs = n * w;  // stride between basis panels
@@ -1144,7 +1146,7 @@ int hlu_factor_error(hlu_t h, const double *x0, int32_t iters, double rtol, doub
         }
         if ((st = upload(h, &h->err_leaves, lv))) return st;
         if ((st = dalloc(h, &h->err_work, 6 * n + 1))) return st;
-        if ((st = cuda_status(cudaMallocHost(reinterpret_cast<void **>(&h->err_host), sizeof(double))))) return st;
+        if (!(h->err_host = new (std::nothrow) double[1])) return HLU_ENOMEM;
     }
     ErrEstimator e;
     e.n = n;
@@ -1212,10 +1214,16 @@ void hlu_destroy(hlu_t h) {
     else cudaDeviceSynchronize();
     collect_profile(h);
     for (cudaEvent_t e : h->free_events) cudaEventDestroy(e);
-    for (void *p : h->allocs) cudaFree(p);
-    if (h->ir_host) cudaFreeHost(h->ir_host);
-    if (h->gm_host) cudaFreeHost(h->gm_host);
-    if (h->err_host) cudaFreeHost(h->err_host);
+    for (void *p : h->allocs)
+        if (cudaFreeAsync(p, h->stream) != cudaSuccess) {  // e.g. the caller's stream is gone already
+            cudaGetLastError();
+            cudaFree(p);
+        }
+    cudaStreamSynchronize(h->stream);  // the memory is back in the pool (and released) on return
+    cudaGetLastError();
+    delete[] h->ir_host;
+    delete[] h->gm_host;
+    delete[] h->err_host;
     delete h;
 }
 
