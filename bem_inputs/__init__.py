@@ -63,6 +63,10 @@ STREAMS = {
     "serve64": dict(requests=64, repeat=0.3, nrhs=(1, 64), levels=(3, 4), eps=(1e-4, 1e-6), leaf=32, eta=2.0),
     # with n = 20480 problems too (r = 5, leaf 64 as the single-problem workloads of that size use)
     "serve64r5": dict(requests=64, repeat=0.3, nrhs=(1, 64), levels=(3, 4, 5), eps=(1e-4, 1e-6), leaf=32, eta=2.0),
+    # n from 1280 to 81920 (r uniform in 3..6), all three axes uniform in [0.5, 2]; the groups share
+    # their product temporaries (temp_reuse) so that n = 81920 problems fit the budget several at a time
+    "serve64r6": dict(requests=64, repeat=0.3, nrhs=(1, 64), levels=(3, 4, 5, 6), eps=(1e-4, 1e-6), leaf=32,
+                      eta=2.0, axes_range=(0.5, 2.0), temp_reuse=1),
 }
 
 

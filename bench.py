@@ -656,11 +656,6 @@ def e2e_arm(p, precision, sptr, steps, flops_step, solver="ir", restart=30):
                         f"{'GMRES' if solver == 'gmres' else 'refinement'} + copies"}
 
 
-def _build_one(kw):
-    from bem_inputs import build_problem
-    return build_problem(**kw)
-
-
 def _structure_one(kw):
     from bem_inputs import build_structure
     return build_structure(**kw)
@@ -1042,19 +1037,23 @@ def run_serve(args):
 
     rank, world, local = dist_env()
     w = dict(STREAMS[args.workload])
+    temp_reuse = w.pop("temp_reuse", 0)
     stream, specs = stream_specs(**w)
+    # structures on all host cores (before any CUDA call), leaf data on the GPU
     import multiprocessing as mp
     with mp.get_context("spawn").Pool(min(len(specs), os.cpu_count() or 1)) as pool:
-        probs = pool.map(_build_one, specs)
+        probs = pool.map(_structure_one, specs, chunksize=1)
     torch.cuda.set_device(local)
     build.build()
+    construct_leaves(probs)
     rhs = [np.random.default_rng(sd).standard_normal((probs[k].n, c)) for k, c, sd in stream]
 
     def pct(a, q):
         return a[min(len(a) - 1, int(round(q * (len(a) - 1))))]
 
     def replay(arrivals, timeline=False):
-        srv = Server(timeline=timeline)  # a stream per group, half the workers per launch, groups of <= 16
+        # a stream per group, half the workers per launch, groups of <= 16
+        srv = Server(timeline=timeline, temp_reuse=temp_reuse)
         reqs = [Request(k, probs[k], b, arrival=float(t), rid=i)
                 for i, ((k, _, _), b, t) in enumerate(zip(stream, rhs, arrivals))]
         torch.cuda.synchronize()
@@ -1068,6 +1067,11 @@ def run_serve(args):
         ov = overlap(srv.events, ref) if timeline else None
         srv.close()  # adds the kernel launches of the handles it releases
         st = dict(srv.stats)
+        adm = sorted(srv.admissions, key=lambda a: -(a[2] + a[3]))
+        st["slowest_admissions"] = [{"problems": a[0], "n": a[1], "create_s": round(a[2], 3),
+                                     "factor_s": round(a[3], 3)} for a in adm[:5]]
+        st["admission_create_s"] = round(sum(a[2] for a in adm), 3)
+        st["admission_factor_s"] = round(sum(a[3] for a in adm), 3)
         lat = sorted((r.done - r.arrival) * 1e3 for r in reqs)
         return makespan, lat, st, reqs, ov
 
@@ -1083,6 +1087,13 @@ def run_serve(args):
             v = sorted((r.done - r.arrival) * 1e3 for r in rs)
             if v:
                 out[name] = {"count": len(v), "p50_ms": pct(v, 0.5), "p99_ms": pct(v, 0.99)}
+        # where the time goes: arrival -> group resident -> solve start -> solution
+        for name, a, b in (("to_resident", "arrival", "resident_at"), ("resident_to_solve", "resident_at", "solve_at"),
+                           ("solve", "solve_at", "done")):
+            v = sorted((getattr(r, b) - getattr(r, a)) * 1e3 for r in reqs
+                       if getattr(r, a) is not None and getattr(r, b) is not None)
+            if v:
+                out["phase_" + name] = {"p50_ms": pct(v, 0.5), "p99_ms": pct(v, 0.99), "max_ms": v[-1]}
         return out
 
     def overlap(events, ref):

@@ -55,6 +55,8 @@ class Request:
     done: float | None = None
     refactored: bool = False   # this request's problem was (re)factorised for it
     waited: bool = False       # it waited for the admission of its problem
+    resident_at: float | None = None  # server clock: its group resident (or the arrival if it was)
+    solve_at: float | None = None     # server clock: its stacked solve started
     iters: int = 0
 
 
@@ -97,6 +99,7 @@ class Server:
         self.queue: collections.deque[Request] = collections.deque()
         self.stats = collections.Counter()
         self.events = []           # (kind, group id, start event, end event) when timeline is on
+        self.admissions = []       # per created group: problems, unknowns, create s, factorise s
         self._tick = 0
         self._lock = threading.RLock()
         self._freed = threading.Condition(self._lock)
@@ -249,6 +252,9 @@ class Server:
             self.where[k] = g
             self.admitting.discard(k)
             reqs += self.waiting.pop(k, [])
+        now = self.clock()
+        for r in reqs:
+            r.resident_at = now
         if reqs:
             self._chain_solve(g, reqs)
 
@@ -296,7 +302,9 @@ class Server:
         if self.workers:
             kw["workers"] = self.workers
         H = self.handle_type
+        t0 = self.clock()
         h = H.batch(probs, **kw) if len(probs) > 1 else H.from_problem(probs[0], **kw)
+        t1 = self.clock()
         e0 = self._record(stream)  # the factorisation's device work only (after the host planning)
         try:
             h.factor([p.eps for p in probs] if len(probs) > 1 else probs[0].eps)
@@ -304,10 +312,13 @@ class Server:
             h.close()
             raise
         e1 = self._record(stream)
+        t2 = self.clock()
         g = _Group(h, keys, [p.n for p in probs], stream)
         with self._lock:
             self.stats["factorised_problems"] += len(probs)
             self.stats["groups_created"] += 1
+            # (problems, unknowns, seconds to create the handle, seconds to factorise)
+            self.admissions.append((len(probs), g.n, t1 - t0, t2 - t1))
             if e0 is not None:
                 self.events.append(("factor", id(g), e0, e1))
         return g
@@ -350,6 +361,9 @@ class Server:
             ratio = own[own > 0] / colnorm[c:c + r.b.shape[1]][own > 0]
             if ratio.size:
                 tol = min(tol, self.tol * float(ratio.min()))
+        t_solve = self.clock()
+        for r in reqs:
+            r.solve_at = t_solve
         e0 = self._record(g.stream)
         b = to_device_panel(B, device=self.device)  # a host-to-device copy, no kernel
         x = torch.empty_like(b)  # written by the refinement (which starts from zero itself)
@@ -412,6 +426,7 @@ class Server:
                 for r in ready:
                     if r.key in self.where:
                         by_group[id(self.where[r.key])].append(r)
+                        r.resident_at = now
                     else:  # solved once its group is registered (_register)
                         if r.key not in self.admitting and r.key not in new:
                             new[r.key] = r.problem
