@@ -9,9 +9,10 @@ that the device holds several requests' work at once:
 
 * admission threads create and factorise new groups (each problem with its own eps,
   hlu_factor_batch), several at once so that their host planning runs in parallel; the creations in
-  flight share the budget left free.  New problems wait in one queue, and a thread that starts takes
-  up to max_group of them as one group: problems that arrive while every admission thread is busy
-  are admitted together.  An admission evicts least-recently-used idle groups when the
+  flight share the budget left free (each asks for an estimate of its group's memory first).  New
+  problems wait in one queue, and a free thread takes the oldest as one group: up to max_group of
+  them while the group's unknowns stay within max_group_n, so problems that arrive while every
+  admission thread is busy are admitted together without small ones waiting for many large ones.  An admission evicts least-recently-used idle groups when the
   device-memory budget is short; when nothing can be evicted yet it waits until a running job ends
   and frees memory, and it splits a group that cannot fit on its own;
 * solve threads run, per group, one stacked refined solve of the requests that have arrived for it
@@ -79,12 +80,15 @@ class Server:
 
     def __init__(self, precision=HLU_FP32, mem_budget=150e9, tol=1e-10, max_iter=30, max_group=16,
                  stream=None, clock=time.perf_counter, device="cuda", handle_type=HLU, workers=None,
-                 solve_threads=2, admit_threads=4, stream_factory=None, timeline=False, temp_reuse=0):
+                 solve_threads=2, admit_threads=8, stream_factory=None, timeline=False, temp_reuse=0,
+                 max_group_n=65536, bytes_per_leaf=400e3):
         self.precision = precision
         self.budget = int(mem_budget)
         self.tol = tol
         self.max_iter = max_iter
         self.max_group = max_group
+        self.max_group_n = max_group_n      # a group takes more problems only while its unknowns stay below
+        self.bytes_per_leaf = bytes_per_leaf  # device-memory estimate of a new group, per leaf
         self.clock = clock
         self.device = device
         self.handle_type = handle_type
@@ -107,7 +111,7 @@ class Server:
         self._errors: list[BaseException] = []
         self._creating = 0         # creations in flight (they share the free budget)
         self._reserved = 0         # bytes of budget handed to the creations in flight
-        self._pending: list = []   # keys dispatched and not yet taken by an admission job, in order
+        self._pending = collections.deque()  # keys dispatched, not yet taken by an admission job
         self._pending_probs: dict = {}
         self._admit_futs: list = []
         self.admit_threads = int(admit_threads)
@@ -187,24 +191,32 @@ class Server:
 
     # ------------------------------------------------------------ admission
     def _admit_next(self):
-        """Admission thread: take the oldest dispatched keys that no job has taken yet (at most
-        max_group: the requests that arrived while every admission thread was busy are admitted
-        together, as one group) and admit them."""
-        with self._lock:
-            part = self._pending[:self.max_group]
-            del self._pending[:len(part)]
-            problems = {k: self._pending_probs.pop(k) for k in part}
-        if not part:
-            return
-        try:
-            self._admit_job(part, problems)
-        except BaseException:
-            with self._lock:  # forget the keys it did not admit; their waiting requests are dropped
-                for k in part:
-                    if k not in self.where:
-                        self.admitting.discard(k)
-                        self.waiting.pop(k, None)
-            raise
+        """Admission thread: take the oldest dispatched problems that no job has taken yet as one
+        group (the requests that arrived while every admission thread was busy are admitted
+        together: at most max_group problems, and more than one only while the group's unknowns
+        stay within max_group_n, so that a small problem does not wait for a long factorisation of
+        many large ones) and admit them; repeat while problems are queued."""
+        while True:
+            with self._lock:
+                part, total = [], 0
+                while self._pending and len(part) < self.max_group:
+                    nk = getattr(self._pending_probs[self._pending[0]], "n", 0)
+                    if part and total + nk > self.max_group_n:
+                        break
+                    part.append(self._pending.popleft())
+                    total += nk
+                problems = {k: self._pending_probs.pop(k) for k in part}
+            if not part:
+                return
+            try:
+                self._admit_job(part, problems)
+            except BaseException:
+                with self._lock:  # forget the keys it did not admit; their waiting requests are dropped
+                    for k in part:
+                        if k not in self.where:
+                            self.admitting.discard(k)
+                            self.waiting.pop(k, None)
+                raise
 
     def _admit_job(self, keys, problems):
         """Create and factorise the groups of `keys` (at most max_group problems each), evicting idle
@@ -267,6 +279,9 @@ class Server:
         it.  The group's registration and the release of its share happen under one lock, so that a
         waiting admission never sees memory as neither reserved nor resident."""
         probs = [problems[k] for k in keys]
+        est = None
+        if self.bytes_per_leaf and all(hasattr(p, "n_leaves") for p in probs):
+            est = int(self.bytes_per_leaf * sum(p.n_leaves for p in probs)) + (64 << 20)
         with self._lock:
             if exclusive:
                 while self._creating > 0:
@@ -277,7 +292,9 @@ class Server:
                 waiting_groups = -(-len(self._pending) // self.max_group)
                 claim = max(1, min(self.admit_threads, self._creating + 1 + waiting_groups) - self._creating)
             free = self.budget - self.resident_bytes - self._reserved
-            budget = free // claim
+            # the estimate of the group's memory when there is one (a first try; a group that needs
+            # more comes back exclusive), else an equal share of the free budget
+            budget = min(free, est) if est is not None and not exclusive else free // claim
             if budget <= 0:
                 raise HLUError(ENOMEM, "device-memory budget exhausted")
             self._creating += 1

@@ -261,3 +261,25 @@ def test_problems_arriving_while_admission_is_busy_are_admitted_together():
     for r in reqs:
         assert np.allclose(probs[r.key].A @ r.x, r.b, atol=1e-10)
     s.close()
+
+
+def test_a_group_takes_more_problems_only_within_its_unknowns_cap():
+    """Queued problems are grouped in arrival order while the group's unknowns stay within
+    max_group_n: two small problems form one group, the large one that follows its own."""
+    _SlowHLU.spans = []
+    _FakeHLU.created = []
+    probs = {0: _Prob(5, 0), 1: _Prob(5, 1), 2: _Prob(6, 2), 3: _Prob(30, 3)}
+    s = Server(mem_budget=1e9, device="cpu", handle_type=_SlowHLU, admit_threads=1, max_group_n=20)
+    g = np.random.default_rng(7)
+    reqs = [Request(k, probs[k], g.standard_normal((probs[k].n, 1)), arrival=float(k > 0), rid=k) for k in range(4)]
+    for r in reqs:
+        s.submit(r)
+    out = s.step(now=0.0)          # problem 0 alone keeps the only admission thread busy
+    time.sleep(0.05)
+    out += s.step(now=1.0)         # 1 and 2 (11 unknowns) are grouped; 3 (30) would pass the cap
+    out += s.drain()
+    assert sorted(r.rid for r in out) == [0, 1, 2, 3]
+    assert [sorted(p.n for p in h.probs) for h in _FakeHLU.created] == [[5], [5, 6], [30]]
+    for r in reqs:
+        assert np.allclose(probs[r.key].A @ r.x, r.b, atol=1e-10)
+    s.close()
