@@ -531,7 +531,7 @@ def run_native(args):
             "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 factors; f64 SVD of every truncation core (QR of R'^T + Jacobi), f64 residual and solution",
+            "dtype": "f32 factors; f64 Jacobi SVD of every truncation core, f64 residual and solution",
             "data": "synthetic",
             "config": workload_config(args, w, p, world),
             "device_gb": st32["device_bytes"] / 1e9,

@@ -45,9 +45,10 @@ enum {
 enum {
     HLU_FP64 = 0,        /* factors stored and computed in FP64 */
     HLU_FP32 = 1,        /* factors stored and computed in FP32, except the SVD of every
-                            truncation core (the QR of R'^T and the one-sided Jacobi of the
-                            rounded addition, Sec. 3.1), which runs in FP64 on the FP32 data;
-                            the original matrix, hlu_matvec and the refinement stay FP64 */
+                            truncation core (the one-sided Jacobi of the rounded addition,
+                            Sec. 3.1, and the right factor formed from it), which runs in FP64
+                            on the FP32 data; the original matrix, hlu_matvec and the
+                            refinement stay FP64 */
     HLU_FP32_CORE32 = 2  /* as HLU_FP32, but the truncation cores' Jacobi SVD runs in FP32
                             with the rotations accumulated (faster, singular values to FP32
                             accuracy) */
@@ -125,14 +126,12 @@ typedef struct {
 
 /* hlu_opts.flags */
 enum {
-    HLU_FLAG_TENSOR = 1  /* FP32 factors: compute the dense products of the factorisation
-                            (product tasks with >= 32 rows, >= 16 columns and >= 32 inner
-                            columns, data-flow schedule) on the tensor cores (tcgen05, three
-                            TF32 products per FP32 product, FP32 accumulation in tensor memory)
-                            instead of CUDA cores.  Off by default: these leaf-sized products
-                            (a 64-row leaf cluster, tens of inner columns) ran slower on the
-                            tensor cores than on CUDA cores in every measured workload */
-    ,
+    /* FP32 factors: compute the dense products of the factorisation (product tasks with >= 32
+       rows, >= 16 columns and >= 32 inner columns, data-flow schedule) on the tensor cores
+       (tcgen05, three TF32 products per FP32 product, FP32 accumulation in tensor memory) instead
+       of CUDA cores.  Off by default: these leaf-sized products (a 64-row leaf cluster, tens of
+       inner columns) ran slower on the tensor cores than on CUDA cores in every measured workload */
+    HLU_FLAG_TENSOR = 1,
     HLU_FLAG_SERIAL_PLAN = 2  /* hlu_create_batch / hlu_plan_info_batch with the data-flow
                                  schedule: plan the whole batch as one H-matrix on one host
                                  thread.  By default the problems are planned separately on all

@@ -2,8 +2,8 @@
 // executes one task; the launch of a wave passes the slice of the task array
 // that belongs to it.  T is the storage type of the factors (double or
 // float).  With double factors every step is double.  With float factors the
-// stacked QRs and the pivoted QR of each truncation core are single precision,
-// and the SVD of the core (the QR of R'^T and the one-sided Jacobi) is double
+// stacked QRs, the pivoted QR and the QR of R'^T of each truncation core are
+// single precision, and the one-sided Jacobi SVD of the core is double
 // (LaunchArgs::core64, the default) or single precision (the HLU_FP32_CORE32
 // variant).
 #include <cuda_runtime.h>
@@ -1298,7 +1298,7 @@ struct CoreBufs {
     double *isg64;
 };
 
-// core64 applies to single-precision cores only: their SVD (QR of R'^T, Jacobi) runs in double.
+// core64 applies to single-precision cores only: their Jacobi SVD runs in double.
 template <class R>
 __host__ __device__ constexpr bool core_in_double(bool core64) {
     return sizeof(R) != 8 && core64;
