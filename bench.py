@@ -490,6 +490,13 @@ def run_native(args):
                 "peak_gbs": hbm_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (fallback 6800)"},
             "kernel_ms_per_step": {k: v / nprof for k, v in ms.items()},
             "task_busy_ms_per_factor": {k: v / nprof for k, v in prof["task_busy_ms"].items() if v},
+            # summed over the workers of the factorisation launch: lifetime = tasks + waits on empty
+            # queue slots + the executor's own work (claims, successor release, barriers)
+            "worker_ms_per_factor": {
+                "life": prof["worker_life_ms"] / nprof, "queue_wait": prof["worker_wait_ms"] / nprof,
+                "tasks": sum(prof["task_busy_ms"].values()) / nprof,
+                "executor": (prof["worker_life_ms"] - prof["worker_wait_ms"]
+                             - sum(prof["task_busy_ms"].values())) / nprof},
             "classes": class_roofline(st32, prof, nprof, fp32_peak),
             "tasks_per_factor": {k: v // nprof for k, v in prof["task_count"].items() if v},
             "radd_busy_ms_by_size": {k: round(v / nprof, 1) for k, v in prof["radd_busy_ms"].items() if v},

@@ -36,7 +36,7 @@ struct DevPlan {
     // data-flow execution
     int32_t *code = nullptr, *succ_ptr = nullptr, *succ_idx = nullptr;
     int32_t *indeg0 = nullptr, *indeg = nullptr, *queue = nullptr, *roots = nullptr, *counters = nullptr;
-    int32_t n_tasks = 0, n_roots = 0, kc = 1;
+    int32_t n_tasks = 0, n_roots = 0, n_sinks = 0, kc = 1;
     void *scratch = nullptr;
     int64_t scratch_stride = 0;
     void *core_scratch = nullptr;  // cores of rounded additions above kSmemCore (global)
@@ -172,6 +172,8 @@ int upload_plan(hlu_ctx *h, const Plan &p, DevPlan &d, int kmax) {
     // data-flow graph and per-worker workspace
     d.n_tasks = (int32_t)p.n_tasks;
     d.n_roots = (int32_t)p.roots.size();
+    d.n_sinks = 0;
+    for (int64_t g = 0; g < p.n_tasks; ++g) d.n_sinks += p.succ_ptr[g + 1] == p.succ_ptr[g];
     if ((st = upload(h, &d.code, p.task_code))) return st;
     if ((st = upload(h, &d.succ_ptr, p.succ_ptr))) return st;
     if ((st = upload(h, &d.succ_idx, p.succ_idx))) return st;
@@ -269,6 +271,7 @@ void run_plan(hlu_ctx *h, const DevPlan &d, void *arena, double *flops) {
         f.queue = d.queue;
         f.counters = d.counters;
         f.n_tasks = d.n_tasks;
+        f.n_sinks = d.n_sinks;
         f.kc = d.kc;
         f.getrf = d.getrf;
         f.trsm = d.trsm;

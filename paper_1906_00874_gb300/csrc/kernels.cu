@@ -1963,6 +1963,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_dataflow(FlowArgs f, LaunchArgs
     TcState tc{0u, 0u, 0u, false, f.timeout_ns, f.tc_min_inner};
     const bool use_tc = sizeof(T) == 4 && f.tensor;
     int my_tasks = 0;  // tasks this worker ran (profiling: workers that ran any)
+    // profiling: the worker's lifetime (slot 14) and its waits on empty queue slots (slot 7); the rest
+    // of the lifetime outside the tasks is the executor's own overhead
+    const unsigned long long t_life = (f.busy && threadIdx.x == 0) ? global_ns() : 0ull;
     if constexpr (sizeof(T) == 4) {
         if (!use_tc && threadIdx.x < 32) asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
@@ -1988,7 +1991,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_dataflow(FlowArgs f, LaunchArgs
             if (g < 0) {
                 const int slot = atomicAdd(f.counters, 1);
                 if (slot < f.n_tasks) {
-                    const unsigned long long deadline = global_ns() + f.timeout_ns;
+                    const unsigned long long t_wait = global_ns();
+                    const unsigned long long deadline = t_wait + f.timeout_ns;
                     for (;;) {
                         g = ld_acquire(f.queue + slot);
                         if (g >= 0) break;
@@ -2007,6 +2011,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dataflow(FlowArgs f, LaunchArgs
                         }
                         __nanosleep(100);
                     }
+                    if (f.busy) atomicAdd(f.busy + 7, global_ns() - t_wait);
                 }
             }
             s_task = g;
@@ -2095,7 +2100,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_dataflow(FlowArgs f, LaunchArgs
         __syncthreads();
         if (threadIdx.x == 0) {
             s_next = s_first < ns ? f.succ_idx[e0 + s_first] : -1;
-            if (atomicAdd(f.counters + 2, 1) == f.n_tasks - 1) {
+            // only the sinks are counted: every task precedes a sink, so the last sink to complete is
+            // the last task (one global atomic per sink instead of per task)
+            if (ns == 0 && atomicAdd(f.counters + 2, 1) == f.n_sinks - 1) {
                 // the last task: wake the workers waiting on slots that will stay empty, and
                 // those that still claim one (each worker claims at most one more slot)
                 __threadfence();
@@ -2107,6 +2114,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dataflow(FlowArgs f, LaunchArgs
         __syncthreads();
     }
     if (f.busy && threadIdx.x == 0 && my_tasks > 0) atomicAdd(f.busy + 15, 1ull);  // active workers
+    if (f.busy && threadIdx.x == 0) atomicAdd(f.busy + 14, global_ns() - t_life);
     if (use_tc) {  // every path out of the loop comes here: the accumulator is given back
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();

@@ -38,8 +38,9 @@ struct FlowArgs {
     int32_t *indeg;            // working in-degrees (reset before every launch)
     int32_t *queue;            // n_tasks slots, -1 = empty
     int32_t *counters;         // [0] head (next slot to claim), [1] tail (next slot to fill),
-                               // [2] completed tasks
+                               // [2] completed sinks (tasks without successors)
     int32_t n_tasks;
+    int32_t n_sinks;           // every task is done once every sink is (each precedes a sink)
     int32_t kc;                // core capacity of rounded additions (shared memory)
     const TGetrf *getrf;
     const TTrsm *trsm;

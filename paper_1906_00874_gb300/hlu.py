@@ -129,6 +129,10 @@ class Stats(ctypes.Structure):
                                       "mean_jacobi_r": ph[b + 6] / max(ph[b + 7], 1), "tasks": ph[b + 7]}
         for f in per_kind:
             d[f] = dict(zip(KINDS, list(getattr(self, f))[:len(KINDS)]))
+        # profiling of the factorisation's workers (summed over workers): lifetime, and waits on
+        # queue slots that no ready task had filled yet
+        d["worker_life_ms"] = self.task_count[6] * 1e-6
+        d["worker_wait_ms"] = self.task_busy_ms[7]
         sizes = ("<128", "<256", "<512", "<1024", "<2048", "<4096", "<8192", ">=8192")
         for f in per_size:
             d[f] = dict(zip(sizes, list(getattr(self, f))))
