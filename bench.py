@@ -489,16 +489,18 @@ def run_native(args):
                 "achieved_gbs": alg_bytes / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else 0.0,
                 "peak_gbs": hbm_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (fallback 6800)"},
             "kernel_ms_per_step": {k: v / nprof for k, v in ms.items()},
-            "task_busy_ms_per_factor": {k: v / nprof for k, v in prof["task_busy_ms"].items() if v},
+            "task_busy_ms_per_factor": {k: prof["task_busy_ms"][k] / nprof for k in KIND_NAMES
+                                        if prof["task_busy_ms"][k]},
             # summed over the workers of the factorisation launch: lifetime = tasks + waits on empty
             # queue slots + the executor's own work (claims, successor release, barriers)
             "worker_ms_per_factor": {
                 "life": prof["worker_life_ms"] / nprof, "queue_wait": prof["worker_wait_ms"] / nprof,
-                "tasks": sum(prof["task_busy_ms"].values()) / nprof,
+                "tasks": sum(prof["task_busy_ms"][k] for k in KIND_NAMES) / nprof,
                 "executor": (prof["worker_life_ms"] - prof["worker_wait_ms"]
-                             - sum(prof["task_busy_ms"].values())) / nprof},
+                             - sum(prof["task_busy_ms"][k] for k in KIND_NAMES)) / nprof},
             "classes": class_roofline(st32, prof, nprof, fp32_peak),
-            "tasks_per_factor": {k: v // nprof for k, v in prof["task_count"].items() if v},
+            "tasks_per_factor": {k: prof["task_count"][k] // nprof for k in KIND_NAMES if prof["task_count"][k]},
+            "active_workers": prof["task_count"]["dataflow_solve"] // max(nprof, 1),
             "radd_busy_ms_by_size": {k: round(v / nprof, 1) for k, v in prof["radd_busy_ms"].items() if v},
             "radd_count_by_size": {k: v // nprof for k, v in prof["radd_count"].items() if v},
             "radd_phases_per_factor": {route: {k: (v if k.startswith("mean_") else v / nprof)

@@ -363,6 +363,7 @@ int32_t Planner::emit_views(Kind k, const View *const *reads, size_t nr, const V
         if (o < (int32_t)temp_size.size() && temp_size[o] > 0) {
             temp_first[o] = std::min(temp_first[o], w);
             temp_last[o] = std::max(temp_last[o], w);
+            if (!opt.temp_reuse) continue;  // the cell touches only order shared regions
             const std::vector<int64_t> &cv = wr ? wc : rc;
             const size_t j = wr ? i - nr : i;
             const size_t b = j ? (wr ? wend : rend)[j - 1] : 0, e = (wr ? wend : rend)[j];
