@@ -967,18 +967,6 @@ __device__ __forceinline__ void jacobi_rotation(double aa, double bb, double gg,
     tan_theta = flt_to_dbl(t);
 }
 
-// The warp of a CTA that runs the one-warp rounds of the Jacobi SVDs.  The two worker CTAs resident
-// on one SM would otherwise both use warp 0, and the first warps of both sit on the same SM
-// sub-partition, whose FP64 pipe they would share; k_dataflow gives the second CTA of an SM warp 2
-// (another sub-partition).  Any warp index of the CTA gives the same results.
-__shared__ int s_jacobi_warp;
-__device__ unsigned int g_sm_turn[1024];  // per SM: worker CTAs started there (parity = CTA slot)
-
-__device__ __forceinline__ int jacobi_warp() {
-    const int w = s_jacobi_warp;
-    return (w >= 0 && w < (int)(blockDim.x >> 5)) ? w : 0;
-}
-
 // One-sided (Hestenes) Jacobi on the columns of D (r x r, double, shared
 // memory, leading dimension ld), in place: D W = B with orthogonal columns
 // (W is not formed); the singular values of D are the column norms of B and
@@ -1003,9 +991,7 @@ __device__ int block_jacobi(double *D, int r, int ld, int *flag, double *nrm) {
     while (g > 1 && g * P > (int)blockDim.x) g >>= 1;
     while (g > 1 && (g >> 1) >= r) g >>= 1;
     const bool one_warp = g * P <= 32;
-    const int lead = jacobi_warp();
-    const int tl = one_warp ? (int)threadIdx.x - 32 * lead : (int)threadIdx.x;  // rank in the rounds
-    const int gid = tl / g, gl = tl % g;
+    const int gid = threadIdx.x / g, gl = threadIdx.x % g;
     const double tol = 4.0 * r * DBL_EPSILON, tol2 = tol * tol;
     int sweep = 0;
     while (sweep < 30) {
@@ -1018,7 +1004,7 @@ __device__ int block_jacobi(double *D, int r, int ld, int *flag, double *nrm) {
             nrm[j] = v;
         }
         __syncthreads();
-        if (!one_warp || (int)(threadIdx.x >> 5) == lead) {  // uniform per warp
+        if (!one_warp || threadIdx.x < 32) {  // uniform per warp
             for (int rd = 0; rd < np - 1; ++rd) {
                 int p, q;
                 if (gid == 0) {
@@ -1101,16 +1087,14 @@ __device__ int block_jacobi_f(float *X, float *W, int r, int *flag) {
     while (g > 1 && g * P > (int)blockDim.x) g >>= 1;
     while (g > 1 && (g >> 1) >= r) g >>= 1;
     const bool one_warp = g * P <= 32;
-    const int lead = jacobi_warp();
-    const int tl = one_warp ? (int)threadIdx.x - 32 * lead : (int)threadIdx.x;  // rank in the rounds
-    const int gid = tl / g, gl = tl % g;
+    const int gid = threadIdx.x / g, gl = threadIdx.x % g;
     const float tol = 4.0f * r * FLT_EPSILON;
     int sweep = 0;
     while (sweep < 30) {
         ++sweep;
         if (threadIdx.x == 0) *flag = 0;
         __syncthreads();
-        if (!one_warp || (int)(threadIdx.x >> 5) == lead) {  // uniform per warp
+        if (!one_warp || threadIdx.x < 32) {  // uniform per warp
             for (int rd = 0; rd < np - 1; ++rd) {
                 int p, q;
                 if (gid == 0) {
@@ -1927,8 +1911,6 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) k_radd(const TRadd *tasks, const Piece *pieces, LaunchArgs a, int kc,
                                                    size_t smem_bytes) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    if (threadIdx.x == 0) s_jacobi_warp = 0;
-    __syncthreads();
     const TRadd t = tasks[blockIdx.x];
     dev_radd<T>(t, pieces, a, kc, smem_raw, reinterpret_cast<T *>(a.arena) + t.scratch_off, smem_bytes, nullptr);
 }
@@ -1977,12 +1959,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dataflow(FlowArgs f, LaunchArgs
     __shared__ uint32_t s_tmem;
     __shared__ __align__(8) unsigned long long s_mbar;
     T *scratch = reinterpret_cast<T *>(f.scratch) + (int64_t)blockIdx.x * f.scratch_stride;
-    if (threadIdx.x == 0) {
-        s_next = -1;
-        unsigned smid;
-        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
-        s_jacobi_warp = (atomicAdd(&g_sm_turn[smid & 1023u], 1u) & 1u) ? 2 : 0;
-    }
+    if (threadIdx.x == 0) s_next = -1;
     // tensor cores (single precision, when enabled): this worker's TMEM accumulators (kTcTmemCols
     // columns; at most two workers per SM, 512 columns at most) and the MMA-completion mbarrier.  A CTA of
     // a kernel that holds tcgen05 code keeps the SM's TMEM allocation permit, and with it the SM
