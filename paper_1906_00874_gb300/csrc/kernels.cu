@@ -976,8 +976,7 @@ __device__ __forceinline__ void jacobi_rotation(double aa, double bb, double gg,
 // of both columns; when all groups fit in one warp, the rounds run in that
 // warp alone with warp barriers.  A pair is rotated while
 // |x.y|^2 > tol^2 |x|^2 |y|^2 with tol = 4 r eps_double, the rounding level of
-// the dot product itself; at most 30 sweeps, and no check sweep after one
-// whose rotations were all small (below).  The squared column norms are
+// the dot product itself; at most 30 sweeps.  The squared column norms are
 // computed exactly at the start of every sweep (nrm, r values of shared
 // memory) and carried through its rounds by the rotation's own update
 // (x.x - t x.y, y.y + t x.y, t = tan theta), so a round forms only the dot
@@ -1029,8 +1028,7 @@ __device__ int block_jacobi(double *D, int r, int ld, int *flag, double *nrm) {
                 // the butterfly leaves identical sums in every lane of a group
                 const double aa = active ? nrm[p] : 0.0, bb = active ? nrm[q] : 0.0;
                 if (active && gg * gg > tol2 * aa * bb) {
-                    // bit 0: a rotation; bit 1: a rotation of a pair with |x.y| > 1e-8 |x| |y|
-                    if (gl == 0) atomicOr(flag, gg * gg > 1e-16 * aa * bb ? 3 : 1);
+                    if (gl == 0) *flag = 1;
                     double cs, sn, tn;
                     jacobi_rotation(aa, bb, gg, cs, sn, tn);
                     for (int i = gl; i < r; i += g) {
@@ -1052,10 +1050,7 @@ __device__ int block_jacobi(double *D, int r, int ld, int *flag, double *nrm) {
         __syncthreads();
         const int f = *flag;
         __syncthreads();
-        // done when a sweep rotated nothing, or only pairs with cosines of at most 1e-8 between
-        // their columns: the convergence of cyclic Jacobi is quadratic, so the next sweep would
-        // meet cosines near 1e-16, below tol, and rotate nothing (the check sweep is saved)
-        if (!(f & 2)) break;
+        if (!f) break;
     }
     return sweep;
 }
