@@ -161,11 +161,24 @@ void Planner::relocate_temps(Plan &p) {
         if (temp_last[o] < 0) return 0;  // never touched
         return last ? temp_last[o] : temp_first[o];
     };
-    std::stable_sort(tmp.begin(), tmp.end(), [&](size_t a, size_t b) { return lev(a, false) < lev(b, false); });
+    {  // stable counting sort by first level (levels are below p.n_waves)
+        std::vector<size_t> start(size_t(std::max(p.n_waves, 1)) + 1, 0), sorted(tmp.size());
+        for (size_t i : tmp) start[lev(i, false) + 1]++;
+        for (size_t k = 1; k < start.size(); ++k) start[k] += start[k - 1];
+        for (size_t i : tmp) sorted[start[lev(i, false)]++] = i;
+        tmp.swap(sorted);
+    }
     using Occ = std::pair<int32_t, size_t>;  // (last level, item)
     std::priority_queue<Occ, std::vector<Occ>, std::greater<Occ>> active;
     // free regions by shape (problem, row cluster, rows, cols): (offset, occupant)
-    std::map<std::array<int32_t, 4>, std::vector<std::pair<int64_t, int32_t>>> free_by_shape;
+    struct ShapeHash {
+        size_t operator()(const std::array<int32_t, 4> &a) const {
+            uint64_t h = 0x9e3779b97f4a7c15ull;
+            for (int32_t v : a) h = (h ^ uint32_t(v)) * 0xbf58476d1ce4e5b9ull;
+            return size_t(h ^ (h >> 31));
+        }
+    };
+    std::unordered_map<std::array<int32_t, 4>, std::vector<std::pair<int64_t, int32_t>>, ShapeHash> free_by_shape;
     std::vector<std::pair<int32_t, int32_t>> order;  // (earlier temporary, later temporary) sharing a region
     int64_t top = pos;
     for (size_t i : tmp) {
@@ -186,18 +199,26 @@ void Planner::relocate_temps(Plan &p) {
         }
         active.emplace(lev(i, true), i);
     }
-    // offsets: an offset inside item k (items are in increasing offset order) keeps its distance
+    // offsets: an offset inside item k (items are in increasing offset order) keeps its distance.
+    // The item of an offset is found from a table of the first item of every 4096-element page of
+    // the plan's region, then a short forward scan (items are small: a few per page).
+    constexpr int kPageShift = 12;
+    const int64_t span = plan_items[ni - 1].off - plan_begin;
+    std::vector<int32_t> page_item(size_t(span >> kPageShift) + 1);
+    {
+        size_t it = 0;
+        for (size_t pg = 0; pg < page_item.size(); ++pg) {
+            const int64_t start = plan_begin + (int64_t(pg) << kPageShift);
+            while (it + 1 < ni && plan_items[it + 1].off <= start) ++it;
+            page_item[pg] = int32_t(it);
+        }
+    }
     auto remap = [&](int64_t off) -> int64_t {
         if (off < plan_begin) return off;
-        size_t lo = 0, hi = ni;
-        while (hi - lo > 1) {
-            const size_t mid = (lo + hi) / 2;
-            if (plan_items[mid].off <= off)
-                lo = mid;
-            else
-                hi = mid;
-        }
-        return noff[lo] + (off - plan_items[lo].off);
+        const size_t pg = std::min(size_t((off - plan_begin) >> kPageShift), page_item.size() - 1);
+        size_t i = size_t(page_item[pg]);
+        while (i + 1 < ni && plan_items[i + 1].off <= off) ++i;
+        return noff[i] + (off - plan_items[i].off);
     };
     for (TGetrf &t : p.getrf) t.off = remap(t.off);
     for (TTrsm &t : p.trsm) {
