@@ -16,7 +16,6 @@
 // recursion per problem, and no cell is written by two problems).
 #include <algorithm>
 #include <atomic>
-#include <cstring>
 #include <memory>
 #include <new>
 #include <thread>
