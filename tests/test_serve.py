@@ -283,3 +283,22 @@ def test_a_group_takes_more_problems_only_within_its_unknowns_cap():
     for r in reqs:
         assert np.allclose(probs[r.key].A @ r.x, r.b, atol=1e-10)
     s.close()
+
+
+def test_memory_estimate_first_then_the_free_budget():
+    """A creation first reserves its estimated memory (leaves x bytes_per_leaf + a margin), at most the
+    free budget: with a budget that one reservation fills, a second new problem waits for the first
+    creation and is then admitted with what is left; both requests are answered."""
+    probs = {k: _Prob(10, k) for k in range(2)}   # 800 bytes each
+    for p in probs.values():
+        p.n_leaves = 4
+    s = _server(budget=2000, max_group=1, admit_threads=2)
+    g = np.random.default_rng(9)
+    reqs = [Request(k, probs[k], g.standard_normal((10, 1)), rid=k) for k in range(2)]
+    for r in reqs:
+        s.submit(r)
+    out = _step(s, 0.0)
+    assert sorted(r.rid for r in out) == [0, 1]
+    assert s.stats["groups_created"] == 2 and s.stats.get("evicted_groups", 0) == 0
+    for r in reqs:
+        assert np.allclose(probs[r.key].A @ r.x, r.b, atol=1e-10)
