@@ -33,7 +33,7 @@ enum {
                           block, rank > min(m,n), leaf cluster above 128 indices,
                           non-finite input, bad argument */
     HLU_ENOMEM = 2,    /* cudaMalloc failed or the plan exceeds opts.mem_budget */
-    HLU_ESTATE = 3,    /* call out of order (solve before factor, factor twice) */
+    HLU_ESTATE = 3,    /* call out of order (a solve or an estimate before hlu_factor) */
     HLU_EPIVOT = 4,    /* zero or non-finite pivot u_kk in a dense diagonal leaf */
     HLU_ERANKCAP = 5,  /* a truncated rank or a stacked rank exceeded its capacity */
     HLU_ETIMEOUT = 6,  /* a device-side wait exceeded its limit */
