@@ -167,3 +167,38 @@ def test_batch_task_lists_equal_the_problems_own(executor, batch_threads):
                 assert np.array_equal(a, q.data[q.offset[l]:q.offset[l] + ln]), (i, l)
             assert np.array_equal(xb[row:row + p.n], x)
             row += p.n
+
+
+def test_batch_with_clusters_out_of_problem_order_is_planned_as_one_forest(executor):
+    """A forest whose clusters are numbered out of problem order (not the layout hlu_create_batch
+    builds, so the per-problem planning does not apply) is planned as one forest and gives the same
+    factors and solve as the forest in problem order."""
+    from bem_inputs import build_problem
+    probs = [build_problem(2, 32, 2.0, 1e-4, nrhs=1), build_problem(2, 32, 2.0, 1e-4, nrhs=1, seed=1,
+                                                                    axes=(1.0, 0.6, 0.4))]
+    f = _Forest(probs)
+    ref_q, ref_x = _run(executor, f, 1e-4, 0, 3, inst=f.inst)
+    # renumber every cluster but the root with a seeded permutation
+    ncl = f.tree.n_clusters
+    pi = np.concatenate([[0], 1 + np.random.default_rng(5).permutation(ncl - 1)])
+    g = copy.copy(f)
+    g.tree = copy.copy(f.tree)
+    for name in ("begin", "size"):
+        a = np.empty_like(getattr(f.tree, name))
+        a[pi] = getattr(f.tree, name)
+        setattr(g.tree, name, a)
+    for name in ("son0", "son1"):
+        src = getattr(f.tree, name)
+        a = np.empty_like(src)
+        a[pi] = np.where(src >= 0, pi[np.maximum(src, 0)], -1)
+        setattr(g.tree, name, a)
+    inst = np.empty_like(f.inst)
+    inst[pi] = f.inst
+    g.inst = inst
+    g.row_cl, g.col_cl = pi[f.row_cl], pi[f.col_cl]
+    q, x = _run(executor, g, 1e-4, 0, 4, inst=g.inst)
+    assert np.array_equal(q.rank, ref_q.rank)
+    for l in range(f.n_leaves):
+        assert q.offset[l] == ref_q.offset[l]
+    assert np.array_equal(q.data, ref_q.data)
+    assert np.array_equal(x, ref_x)
