@@ -169,7 +169,11 @@ int hlu_factor(hlu_t h, double eps);
  * problem i follow those of problems 0..i-1 (offsets sum_{j<i} n_j); every
  * other call (hlu_factor, hlu_solve, hlu_solve_refined, hlu_solve_gmres,
  * hlu_matvec, hlu_get_factors) sees the stacked system of that order.
- * count >= 1; on failure *out is NULL. */
+ * With the data-flow schedule the problems are planned on all host threads,
+ * one problem per planner, and their task graphs joined (the same tasks and
+ * dependencies as one plan of the whole matrix; HLU_FLAG_SERIAL_PLAN plans it
+ * as one on one thread).  The handle keeps no host copy of the task graphs
+ * after they are uploaded.  count >= 1; on failure *out is NULL. */
 int hlu_create_batch(int32_t count, const hlu_tree *trees, const hlu_blocks *blocks,
                      const hlu_opts *opts, void *cuda_stream, hlu_t *out);
 
