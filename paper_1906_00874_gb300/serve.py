@@ -12,9 +12,10 @@ that the device holds several requests' work at once:
   flight share the budget left free (each asks for an estimate of its group's memory first).  New
   problems wait in one queue, and a free thread takes the oldest as one group: up to max_group of
   them while the group's unknowns stay within max_group_n, so problems that arrive while every
-  admission thread is busy are admitted together without small ones waiting for many large ones.  An admission evicts least-recently-used idle groups when the
-  device-memory budget is short; when nothing can be evicted yet it waits until a running job ends
-  and frees memory, and it splits a group that cannot fit on its own;
+  admission thread is busy are admitted together without small ones waiting for many large ones.
+  An admission evicts least-recently-used idle groups when the device-memory budget is short; when
+  nothing can be evicted yet it waits until a running job ends and frees memory, and it splits a
+  group that cannot fit on its own;
 * solve threads run, per group, one stacked refined solve of the requests that have arrived for it
   (the block-diagonal system, each request's columns in its problem's rows, zeros elsewhere, FP64
   refinement to the tolerance for every request on its own).  A group runs one job at a time, in
