@@ -8,7 +8,10 @@
 #include <array>
 #include <cmath>
 #include <cstring>
+#include <new>
+#include <condition_variable>
 #include <map>
+#include <mutex>
 #include <thread>
 #include <utility>
 #include <functional>
@@ -30,19 +33,19 @@ void Planner::release_work() {
     std::vector<Block *>().swap(blocks_owned);
     root = nullptr;
     std::vector<Obj>().swap(objs);
-    std::vector<CellState>().swap(cell);
-    std::vector<int32_t>().swap(pred_mark);
-    std::vector<int32_t>().swap(rpool_task);
-    std::vector<int32_t>().swap(rpool_next);
+    std::vector<CellState>().swap(dep.cell);
+    std::vector<int32_t>().swap(dep.pred_mark);
+    std::vector<int32_t>().swap(dep.rpool_task);
+    std::vector<int32_t>().swap(dep.rpool_next);
     std::vector<PlanItem>().swap(plan_items);
-    std::vector<int32_t>().swap(touch_obj);
-    std::vector<int32_t>().swap(touch_cell);
-    std::vector<int32_t>().swap(touch_task);
-    std::vector<uint8_t>().swap(touch_write);
+    std::vector<int32_t>().swap(dep.touch_obj);
+    std::vector<int32_t>().swap(dep.touch_cell);
+    std::vector<int32_t>().swap(dep.touch_task);
+    std::vector<uint8_t>().swap(dep.touch_write);
     std::vector<std::array<int32_t, 4>>().swap(temp_shape);
     std::vector<int64_t>().swap(temp_size);
-    std::vector<int32_t>().swap(temp_first);
-    std::vector<int32_t>().swap(temp_last);
+    std::vector<int32_t>().swap(dep.temp_first);
+    std::vector<int32_t>().swap(dep.temp_last);
     for (Plan *p : {&fplan, &splan, &mplan}) {  // the executors use the successor lists only
         std::vector<int32_t>().swap(p->pred_ptr);
         std::vector<int32_t>().swap(p->pred_idx);
@@ -79,9 +82,7 @@ int32_t Planner::new_obj(int32_t row_cl, int32_t col_cl, int32_t nr_if_none) {
     o.nr = row_cl >= 0 ? cl[row_cl].lc_count : nr_if_none;
     o.nc = col_cl >= 0 ? cl[col_cl].lc_count : 1;
     o.cell_base = objs.empty() ? 0 : objs.back().cell_base + int64_t(objs.back().nr) * objs.back().nc;
-    objs.push_back(o);
-    int64_t need = o.cell_base + int64_t(o.nr) * o.nc;
-    if ((int64_t)cell.size() < need) cell.resize(need, CellState{-1, -1, -1, -1});
+    objs.push_back(o);  // its cells are made when a task first touches them (analyze)
     return int32_t(objs.size() - 1);
 }
 
@@ -123,10 +124,8 @@ View Planner::new_temp(int32_t row_cl, int32_t rows, int32_t cols, int32_t rslot
 // cluster, rows, columns; split-block factors carry their capacity as a negative column count, so
 // that they share regions only with each other).
 void Planner::note_temp(int32_t obj, int64_t elems, const std::array<int32_t, 4> &shape) {
-    if ((int64_t)temp_size.size() <= obj) {
+    if ((int64_t)temp_size.size() <= obj) {  // the level intervals grow in analyze
         temp_size.resize(obj + 1, 0);
-        temp_first.resize(obj + 1, INT32_MAX);
-        temp_last.resize(obj + 1, -1);
         temp_shape.resize(obj + 1, {-1, -1, -1, -1});
     }
     temp_size[obj] = elems;
@@ -158,8 +157,8 @@ void Planner::relocate_temps(Plan &p) {
     }
     auto lev = [&](size_t i, bool last) {
         const int32_t o = plan_items[i].temp_obj;
-        if (temp_last[o] < 0) return 0;  // never touched
-        return last ? temp_last[o] : temp_first[o];
+        if (dep.temp_last[o] < 0) return 0;  // never touched
+        return last ? dep.temp_last[o] : dep.temp_first[o];
     };
     {  // stable counting sort by first level (levels are below p.n_waves)
         std::vector<size_t> start(size_t(std::max(p.n_waves, 1)) + 1, 0), sorted(tmp.size());
@@ -260,17 +259,17 @@ void Planner::relocate_temps(Plan &p) {
     if (order.empty()) return;
     // the touches of every temporary (counting sort by object; a task's touches are in cell order)
     const size_t nobj = temp_size.size();
-    std::vector<int32_t> tptr(nobj + 1, 0), ttask(touch_obj.size()), tcell(touch_obj.size());
-    std::vector<uint8_t> twr(touch_obj.size());
-    for (int32_t o : touch_obj) tptr[o + 1]++;
+    std::vector<int32_t> tptr(nobj + 1, 0), ttask(dep.touch_obj.size()), tcell(dep.touch_obj.size());
+    std::vector<uint8_t> twr(dep.touch_obj.size());
+    for (int32_t o : dep.touch_obj) tptr[o + 1]++;
     for (size_t o = 0; o < nobj; ++o) tptr[o + 1] += tptr[o];
     {
         std::vector<int32_t> fill(tptr.begin(), tptr.end() - 1);
-        for (size_t e = 0; e < touch_obj.size(); ++e) {
-            const int32_t at = fill[touch_obj[e]]++;
-            ttask[at] = touch_task[e];
-            tcell[at] = touch_cell[e];
-            twr[at] = touch_write[e];
+        for (size_t e = 0; e < dep.touch_obj.size(); ++e) {
+            const int32_t at = fill[dep.touch_obj[e]]++;
+            ttask[at] = dep.touch_task[e];
+            tcell[at] = dep.touch_cell[e];
+            twr[at] = dep.touch_write[e];
         }
     }
     // per shared region, cell by cell (the two temporaries have the same shape, hence the same
@@ -327,10 +326,10 @@ void Planner::temp_levels(Plan &p) const {
     std::vector<int64_t> delta(size_t(p.n_waves) + 2, 0);
     int64_t tot = 0;
     for (size_t o = 0; o < temp_size.size(); ++o) {
-        if (temp_size[o] == 0 || temp_last[o] < 0) continue;
+        if (temp_size[o] == 0 || dep.temp_last[o] < 0) continue;
         tot += temp_size[o];
-        delta[temp_first[o]] += temp_size[o];
-        delta[temp_last[o] + 1] -= temp_size[o];
+        delta[dep.temp_first[o]] += temp_size[o];
+        delta[dep.temp_last[o] + 1] -= temp_size[o];
     }
     int64_t cur = 0, peak = 0;
     for (int64_t d : delta) {
@@ -342,95 +341,240 @@ void Planner::temp_levels(Plan &p) const {
 }
 
 
-void Planner::cells_of(const View &v, std::vector<int64_t> &out) const {
+void Planner::describe(const View &v, ViewRec &r) const {
     const Obj &o = objs[v.obj];
-    int32_t vr = v.trans ? v.c_cl : v.r_cl;  // cluster restricting object rows
-    int32_t vc = v.trans ? v.r_cl : v.c_cl;  // cluster restricting object columns
-    int32_t r0 = 0, r1 = o.nr, c0 = 0, c1 = o.nc;
+    const int32_t vr = v.trans ? v.c_cl : v.r_cl;  // cluster restricting object rows
+    const int32_t vc = v.trans ? v.r_cl : v.c_cl;  // cluster restricting object columns
+    r.base = o.cell_base;
+    r.nc = o.nc;
+    r.r0 = 0;
+    r.r1 = o.nr;
+    r.c0 = 0;
+    r.c1 = o.nc;
     if (o.row_cl >= 0 && vr >= 0) {
-        r0 = cl[vr].lc_first - cl[o.row_cl].lc_first;
-        r1 = r0 + cl[vr].lc_count;
+        r.r0 = cl[vr].lc_first - cl[o.row_cl].lc_first;
+        r.r1 = r.r0 + cl[vr].lc_count;
     }
     if (o.col_cl >= 0 && vc >= 0) {
-        c0 = cl[vc].lc_first - cl[o.col_cl].lc_first;
-        c1 = c0 + cl[vc].lc_count;
+        r.c0 = cl[vc].lc_first - cl[o.col_cl].lc_first;
+        r.c1 = r.c0 + cl[vc].lc_count;
     }
-    for (int32_t r = r0; r < r1; ++r)
-        for (int32_t c = c0; c < c1; ++c) out.push_back(o.cell_base + int64_t(r) * o.nc + c);
+    r.temp_obj = v.obj < (int32_t)temp_size.size() && temp_size[v.obj] > 0 ? v.obj : -1;
 }
 
-int32_t Planner::emit_views(Kind k, const View *const *reads, size_t nr, const View *const *writes, size_t nw) {
+void Planner::cells_of(const View &v, std::vector<int64_t> &out) const {
+    ViewRec r;
+    describe(v, r);
+    for (int32_t a = r.r0; a < r.r1; ++a)
+        for (int32_t c = r.c0; c < r.c1; ++c) out.push_back(r.base + int64_t(a) * r.nc + c);
+}
+
+int32_t Planner::analyze(Deps &d, std::vector<int32_t> &pred_ptr, std::vector<int32_t> &pred_idx, const ViewRec *v,
+                         size_t nr, size_t nw, int32_t g) const {
     static thread_local std::vector<int64_t> rc, wc;
     static thread_local std::vector<size_t> rend, wend;  // end of every view's cells in rc / wc
     rc.clear();
     wc.clear();
     rend.clear();
     wend.clear();
-    for (size_t i = 0; i < nr; ++i) {
-        cells_of(*reads[i], rc);
-        rend.push_back(rc.size());
-    }
-    for (size_t i = 0; i < nw; ++i) {
-        cells_of(*writes[i], wc);
-        wend.push_back(wc.size());
+    for (size_t i = 0; i < nr + nw; ++i) {
+        const ViewRec &r = v[i];
+        std::vector<int64_t> &out = i < nr ? rc : wc;
+        if (r.r1 > r.r0 && r.c1 > r.c0) {
+            const int64_t end = r.base + int64_t(r.r1 - 1) * r.nc + r.c1;  // cells are made on first use
+            if ((int64_t)d.cell.size() < end) d.cell.resize(end, CellState{-1, -1, -1, -1});
+            for (int32_t a = r.r0; a < r.r1; ++a)
+                for (int32_t c = r.c0; c < r.c1; ++c) out.push_back(r.base + int64_t(a) * r.nc + c);
+        }
+        (i < nr ? rend : wend).push_back(out.size());
     }
     int32_t dep = -1;
-    for (int64_t c : rc) dep = std::max(dep, cell[c].write_wave);
-    for (int64_t c : wc) dep = std::max(dep, std::max(cell[c].write_wave, cell[c].read_wave));
-    int32_t w = dep + 1;
+    for (int64_t c : rc) dep = std::max(dep, d.cell[c].write_wave);
+    for (int64_t c : wc) dep = std::max(dep, std::max(d.cell[c].write_wave, d.cell[c].read_wave));
+    const int32_t w = dep + 1;
     for (size_t i = 0; i < nr + nw; ++i) {  // the level interval and the cells of the temporaries touched
+        const int32_t o = v[i].temp_obj;
+        if (o < 0) continue;
+        if ((int32_t)d.temp_first.size() <= o) {
+            d.temp_first.resize(size_t(o) + 1, INT32_MAX);
+            d.temp_last.resize(size_t(o) + 1, -1);
+        }
+        d.temp_first[o] = std::min(d.temp_first[o], w);
+        d.temp_last[o] = std::max(d.temp_last[o], w);
+        if (!opt.temp_reuse) continue;  // the cell touches only order shared regions
         const bool wr = i >= nr;
-        const int32_t o = wr ? writes[i - nr]->obj : reads[i]->obj;
-        if (o < (int32_t)temp_size.size() && temp_size[o] > 0) {
-            temp_first[o] = std::min(temp_first[o], w);
-            temp_last[o] = std::max(temp_last[o], w);
-            if (!opt.temp_reuse) continue;  // the cell touches only order shared regions
-            const std::vector<int64_t> &cv = wr ? wc : rc;
-            const size_t j = wr ? i - nr : i;
-            const size_t b = j ? (wr ? wend : rend)[j - 1] : 0, e = (wr ? wend : rend)[j];
-            for (size_t k = b; k < e; ++k) {
-                touch_obj.push_back(o);
-                touch_cell.push_back(int32_t(cv[k] - objs[o].cell_base));
-                touch_task.push_back(int32_t(P->n_tasks));
-                touch_write.push_back(wr ? 1 : 0);
-            }
+        const std::vector<int64_t> &cv = wr ? wc : rc;
+        const size_t j = wr ? i - nr : i;
+        const size_t b = j ? (wr ? wend : rend)[j - 1] : 0, e = (wr ? wend : rend)[j];
+        for (size_t k = b; k < e; ++k) {
+            d.touch_obj.push_back(o);
+            d.touch_cell.push_back(int32_t(cv[k] - v[i].base));
+            d.touch_task.push_back(g);
+            d.touch_write.push_back(wr ? 1 : 0);
         }
     }
-    for (int64_t c : rc) cell[c].read_wave = std::max(cell[c].read_wave, w);
+    for (int64_t c : rc) d.cell[c].read_wave = std::max(d.cell[c].read_wave, w);
     for (int64_t c : wc) {
-        cell[c].write_wave = w;
-        cell[c].read_wave = -1;
+        d.cell[c].write_wave = w;
+        d.cell[c].read_wave = -1;
     }
     // explicit edges: read-after-write, write-after-write, write-after-read; each predecessor is
-    // listed once (pred_mark[t] == g once t is in this task's list), in the order first met
-    const int32_t g = int32_t(P->n_tasks);
-    if (P->pred_ptr.empty()) P->pred_ptr.push_back(0);
-    if ((int64_t)pred_mark.size() < (int64_t)g + 1) pred_mark.resize(std::max<int64_t>(2 * (int64_t)g, 1024), -1);
+    // listed once (d.pred_mark[t] == g once t is in this task's list), in the order first met
+    if (pred_ptr.empty()) pred_ptr.push_back(0);
+    if ((int64_t)d.pred_mark.size() < (int64_t)g + 1) d.pred_mark.resize(std::max<int64_t>(2 * (int64_t)g, 1024), -1);
     auto add = [&](int32_t t) {
-        if (t >= 0 && t != g && pred_mark[t] != g) {
-            pred_mark[t] = g;
-            P->pred_idx.push_back(t);
+        if (t >= 0 && t != g && d.pred_mark[t] != g) {
+            d.pred_mark[t] = g;
+            pred_idx.push_back(t);
         }
     };
-    for (int64_t c : rc) add(cell[c].writer);
+    for (int64_t c : rc) add(d.cell[c].writer);
     for (int64_t c : wc) {
-        add(cell[c].writer);
-        for (int32_t e = cell[c].rhead; e >= 0; e = rpool_next[e]) add(rpool_task[e]);
+        add(d.cell[c].writer);
+        for (int32_t e = d.cell[c].rhead; e >= 0; e = d.rpool_next[e]) add(d.rpool_task[e]);
     }
-    P->pred_ptr.push_back(int32_t(P->pred_idx.size()));
+    pred_ptr.push_back(int32_t(pred_idx.size()));
     for (int64_t c : rc) {
-        rpool_task.push_back(g);
-        rpool_next.push_back(cell[c].rhead);
-        cell[c].rhead = int32_t(rpool_task.size() - 1);
+        d.rpool_task.push_back(g);
+        d.rpool_next.push_back(d.cell[c].rhead);
+        d.cell[c].rhead = int32_t(d.rpool_task.size() - 1);
     }
     for (int64_t c : wc) {
-        cell[c].writer = g;
-        cell[c].rhead = -1;
+        d.cell[c].writer = g;
+        d.cell[c].rhead = -1;
+    }
+    return w;
+}
+
+// The hand-over between emission and analysis: a ring of chunks of task records (the number of
+// read and written views, then their cell rectangles), filled by the emitting thread and taken in
+// order by the analysing thread, which owns the cell states, the predecessor lists, the level
+// intervals of the temporaries and the waves until pipe_end.
+struct Planner::Pipe {
+    static constexpr size_t kRing = 4, kTasks = 2048;
+    struct Chunk {
+        std::vector<uint32_t> counts;  // per task: reads | writes << 16
+        std::vector<ViewRec> views;
+    };
+    Chunk ring[kRing];
+    alignas(64) size_t produced = 0, consumed = 0;  // chunks handed over / analysed
+    bool done = false, failed = false;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::thread th;
+    // the analysing thread's own (cache lines apart from what the emitting thread writes)
+    alignas(64) Deps d;
+    std::vector<int32_t> pred_ptr, pred_idx;
+    std::vector<int32_t> waves;  // per task from task g0 on
+    int32_t g0 = 0, n_waves = 0;
+    alignas(64) char end_ = 0;
+
+    Chunk &current() { return ring[produced % kRing]; }
+    // hands the current chunk over and waits until the next one in the ring has been analysed
+    void publish() {
+        std::unique_lock<std::mutex> lk(mu);
+        ++produced;
+        cv.notify_all();
+        cv.wait(lk, [&] { return produced - consumed < kRing; });
+        Chunk &c = current();
+        c.counts.clear();
+        c.views.clear();
+    }
+};
+
+void Planner::pipe_begin() {
+    pipe = new Pipe();
+    Pipe *q = pipe;
+    q->d.swap(dep);
+    q->pred_ptr.swap(P->pred_ptr);
+    q->pred_idx.swap(P->pred_idx);
+    q->g0 = int32_t(P->n_tasks);
+    q->th = std::thread([this, q] {
+        int32_t g = q->g0;
+        for (;;) {
+            size_t idx;
+            {
+                std::unique_lock<std::mutex> lk(q->mu);
+                q->cv.wait(lk, [&] { return q->consumed < q->produced || q->done; });
+                if (q->consumed == q->produced) return;
+                idx = q->consumed % Pipe::kRing;
+            }
+            const Pipe::Chunk &c = q->ring[idx];
+            if (!q->failed) {
+                try {
+                    size_t at = 0;
+                    for (uint32_t nrw : c.counts) {
+                        const size_t nr = nrw & 0xffffu, nw = nrw >> 16;
+                        const int32_t w = analyze(q->d, q->pred_ptr, q->pred_idx, c.views.data() + at, nr, nw, g++);
+                        q->waves.push_back(w);
+                        q->n_waves = std::max(q->n_waves, w + 1);
+                        at += nr + nw;
+                    }
+                } catch (const std::bad_alloc &) {
+                    q->failed = true;
+                }
+            }
+            std::lock_guard<std::mutex> lk(q->mu);
+            ++q->consumed;
+            q->cv.notify_all();
+        }
+    });
+}
+
+int Planner::pipe_end() {
+    Pipe *q = pipe;
+    pipe = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(q->mu);
+        if (!q->current().counts.empty()) ++q->produced;  // the last, partial chunk
+        q->done = true;
+        q->cv.notify_all();
+    }
+    q->th.join();
+    dep.swap(q->d);
+    P->pred_ptr.swap(q->pred_ptr);
+    P->pred_idx.swap(q->pred_idx);
+    const bool failed = q->failed;
+    if (!failed) {  // the waves into the kinds' lists, in emission order
+        for (size_t i = 0; i < q->waves.size(); ++i) {
+            const int32_t code = P->task_code[size_t(q->g0) + i];
+            P->wave[code >> kCodeShift][code & kCodeMask] = q->waves[i];
+        }
+        P->n_waves = std::max(P->n_waves, q->n_waves);
+    }
+    delete q;
+    if (failed) {
+        error = "out of host memory in the dependency analysis";
+        return HLU_ENOMEM;
+    }
+    return HLU_OK;
+}
+
+int32_t Planner::emit_views(Kind k, const View *const *reads, size_t nr, const View *const *writes, size_t nw) {
+    static thread_local std::vector<ViewRec> local;
+    ViewRec *v;
+    if (pipe) {
+        std::vector<ViewRec> &dst = pipe->current().views;
+        dst.resize(dst.size() + nr + nw);
+        v = dst.data() + dst.size() - (nr + nw);
+    } else {
+        local.resize(nr + nw);
+        v = local.data();
+    }
+    for (size_t i = 0; i < nr; ++i) describe(*reads[i], v[i]);
+    for (size_t i = 0; i < nw; ++i) describe(*writes[i], v[nr + i]);
+    int32_t w = 0;
+    if (pipe) {
+        Pipe::Chunk &c = pipe->current();
+        c.counts.push_back(uint32_t(nr) | uint32_t(nw) << 16);
+        if (c.counts.size() >= Pipe::kTasks) pipe->publish();
+    } else {
+        w = analyze(dep, P->pred_ptr, P->pred_idx, v, nr, nw, int32_t(P->n_tasks));
+        P->n_waves = std::max(P->n_waves, w + 1);
     }
     P->task_code.push_back((int32_t(k) << kCodeShift) | int32_t(P->wave[k].size()));
-    P->wave[k].push_back(w);
+    P->wave[k].push_back(w);  // the analysing thread's wave is filled in by pipe_end
     P->n_tasks++;
-    P->n_waves = std::max(P->n_waves, w + 1);
     return w;
 }
 
@@ -641,7 +785,8 @@ void Planner::hmm(const View &out, double alpha, bool overwrite, Block *M, bool 
                 cells.clear();
                 cells_of(keep[2 * ti], cells);
                 cells_of(keep[2 * ti + 1], cells);
-                for (int64_t c : cells) depth[ti] = std::max(depth[ti], cell[c].write_wave);
+                for (int64_t c : cells)
+                    if (c < (int64_t)dep.cell.size()) depth[ti] = std::max(depth[ti], dep.cell[c].write_wave);
             }
         }
         // In the solve, the terms whose inputs are ready at the deepest level (the part of the
@@ -1047,23 +1192,23 @@ void Planner::solve_upper_pp(Block *F, const View &Z, const View &Y) {
 
 // --------------------------------------------------------- plan bookkeeping
 void Planner::begin_plan(Plan &p, bool astore_mode, int64_t *bump) {
-    pred_mark.clear();
+    dep.pred_mark.clear();
     P = &p;
     use_astore = astore_mode;
     arena = bump;
-    std::fill(cell.begin(), cell.end(), CellState{-1, -1, -1, -1});
-    rpool_task.clear();
-    rpool_next.clear();
+    std::fill(dep.cell.begin(), dep.cell.end(), CellState{-1, -1, -1, -1});
+    dep.rpool_task.clear();
+    dep.rpool_next.clear();
     plan_items.clear();  // every plan (and arena) has its own temporaries
     plan_begin = *bump;
-    touch_obj.clear();
-    touch_cell.clear();
-    touch_task.clear();
-    touch_write.clear();
+    dep.touch_obj.clear();
+    dep.touch_cell.clear();
+    dep.touch_task.clear();
+    dep.touch_write.clear();
     temp_shape.assign(objs.size(), {-1, -1, -1, -1});
     temp_size.assign(objs.size(), 0);
-    temp_first.assign(objs.size(), INT32_MAX);
-    temp_last.assign(objs.size(), -1);
+    dep.temp_first.assign(objs.size(), INT32_MAX);
+    dep.temp_last.assign(objs.size(), -1);
 }
 
 // Sorts a kind's tasks by wave (stable counting sort: waves are small integers); returns the new
@@ -1485,22 +1630,91 @@ int Planner::build(int32_t n_, int32_t n_clusters, const int32_t *perm_, const i
     return build_tree();
 }
 
+// Capacity for the factorisation plan's lists from an estimate of its task count (about 7 to 10
+// tasks per leaf per level of the cluster tree on surface meshes), so that they are not copied as
+// they grow; capacity that is not used is never touched.
+void Planner::reserve_factorisation() {
+    int32_t depth = 1;
+    for (int64_t c = cl[0].lc_count; c > 1; c = (c + 1) / 2) ++depth;
+    const int64_t t = std::min<int64_t>(int64_t(n_leaves) * 10 * depth, int64_t(1) << 27);
+    Plan &p = fplan;
+    p.task_code.reserve(size_t(t));
+    p.getrf.reserve(size_t(cl[0].lc_count));
+    p.wave[K_GETRF].reserve(size_t(cl[0].lc_count));
+    const double share[K_NKINDS] = {0.0, 0.1, 0.3, 0.6, 0.25, 0.05};
+    for (int k = K_TRSM; k < K_NKINDS; ++k) p.wave[k].reserve(size_t(share[k] * double(t)));
+    p.trsm.reserve(size_t(share[K_TRSM] * double(t)));
+    p.project.reserve(size_t(share[K_PROJECT] * double(t)));
+    p.accum.reserve(size_t(share[K_ACCUM] * double(t)));
+    p.radd.reserve(size_t(share[K_RADD] * double(t)));
+    p.split.reserve(size_t(share[K_SPLIT] * double(t)));
+    p.terms.reserve(size_t(t));
+    p.pieces.reserve(size_t(0.25 * double(t)));
+    p.pred_ptr.reserve(size_t(t) + 1);
+    p.pred_idx.reserve(size_t(5 * t));
+    const size_t nobj = objs.size() + size_t(0.4 * double(t));
+    objs.reserve(nobj);
+    plan_items.reserve(size_t(0.4 * double(t)));
+    temp_size.reserve(nobj);
+    temp_shape.reserve(nobj);
+    dep.temp_first.reserve(nobj);
+    dep.temp_last.reserve(nobj);
+    dep.cell.reserve(2 * nobj);
+    dep.pred_mark.reserve(size_t(2 * t));
+    dep.rpool_task.reserve(size_t(6 * t));
+    dep.rpool_next.reserve(size_t(6 * t));
+}
+
 int Planner::plan_all() {
     if (batch_deferred) return plan_batch();
     layout_factor_arena();
     nrhs_slot = new_slot(0);
     begin_plan(fplan, false, &f_elems);
-    lu(root);
-    inv_cl.clear();
-    inv_index.assign(cl.size(), -1);
-    if (opt.inv_block > 0) {
-        choose_inverses(0, std::max(opt.inv_block, max_leaf));
-        plan_inverses();
+    auto emit_factorisation = [&] {
+        lu(root);
+        inv_cl.clear();
+        inv_index.assign(cl.size(), -1);
+        if (opt.inv_block > 0) {
+            choose_inverses(0, std::max(opt.inv_block, max_leaf));
+            plan_inverses();
+        }
+    };
+    reserve_factorisation();
+    // one plan of one piece: the dependency analysis of the factorisation on a second thread, and its
+    // graph finished (successors, priorities) while the solve and the matvec are emitted
+    const bool piped = opt.batch_threads >= 0 && std::thread::hardware_concurrency() > 1;
+    if (piped) {
+        pipe_begin();
+        bool oom = false;
+        try {
+            emit_factorisation();
+        } catch (const std::bad_alloc &) {
+            oom = true;
+        }
+        const int st = pipe_end();
+        if (oom) {
+            error = "out of host memory while emitting the factorisation";
+            return HLU_ENOMEM;
+        }
+        if (st != HLU_OK) return st;
+    } else {
+        emit_factorisation();
     }
+    dep.temp_first.resize(temp_size.size(), INT32_MAX);
+    dep.temp_last.resize(temp_size.size(), -1);
     temp_levels(fplan);
     if (opt.temp_reuse) relocate_temps(fplan);
     finalize_alloc(fplan, &f_elems);
-    finalize_graph(fplan);
+    struct Joiner {
+        std::thread th;
+        ~Joiner() {
+            if (th.joinable()) th.join();
+        }
+    } fgraph;
+    if (piped)
+        fgraph.th = std::thread([this] { finalize_graph(fplan); });
+    else
+        finalize_graph(fplan);
     f_solve_off = f_elems;
     f_elems = align8(f_elems + int64_t(n) * opt.nrhs_max);
     View Y;
@@ -1540,6 +1754,7 @@ int Planner::plan_all() {
     hmm(Yo, 1.0, true, root, false, X);
     finalize_alloc(mplan, &a_elems);
     finalize_graph(mplan);
+    if (fgraph.th.joinable()) fgraph.th.join();
     P = nullptr;
     // the ACCUM kernel keeps one output row per thread slot (at most 1024 rows)
     for (const Plan *pp : {&fplan, &splan, &mplan})

@@ -118,7 +118,9 @@ struct PlanOptions {
                              // dependency-level intervals (relocate_temps); false: each its own region
     int32_t batch_threads = 0;  // batch, data-flow schedule: the problems are planned on this many host
                                 // threads (0: all hardware threads) and their graphs joined
-                                // (plan_batch); < 0: one plan of the whole forest on one thread
+                                // (plan_batch); < 0: one plan of the whole forest on one thread.
+                                // Unless this is < 0, a factorisation plan that plan_all emits in
+                                // one piece has its dependency analysis on a second thread.
 };
 
 class Planner {
@@ -194,9 +196,30 @@ private:
     struct CellState {
         int32_t write_wave, read_wave, writer, rhead;
     };
-    std::vector<CellState> cell;
-    std::vector<int32_t> pred_mark;  // per task: the last task that listed it as a predecessor
-    std::vector<int32_t> rpool_task, rpool_next;
+    // The state of the dependency analysis (owned by the analysing thread while the emission is piped)
+    struct Deps {
+        std::vector<CellState> cell;
+        std::vector<int32_t> pred_mark;  // per task: the last task that listed it as a predecessor
+        std::vector<int32_t> rpool_task, rpool_next;
+        // the tasks that touch each cell of each temporary (object, cell within the object, task, written)
+        std::vector<int32_t> touch_obj, touch_cell, touch_task;
+        std::vector<uint8_t> touch_write;
+        // per temporary object: the first and last dependency level of a task that touches it
+        std::vector<int32_t> temp_first, temp_last;
+        void swap(Deps &o) {
+            cell.swap(o.cell);
+            pred_mark.swap(o.pred_mark);
+            rpool_task.swap(o.rpool_task);
+            rpool_next.swap(o.rpool_next);
+            touch_obj.swap(o.touch_obj);
+            touch_cell.swap(o.touch_cell);
+            touch_task.swap(o.touch_task);
+            touch_write.swap(o.touch_write);
+            temp_first.swap(o.temp_first);
+            temp_last.swap(o.temp_last);
+        }
+    };
+    Deps dep;
     int32_t ident_obj = -1;
     bool no_flops = false;  // emitted tasks are not counted in the model flops
     std::vector<int32_t> inv_objL, inv_objU;
@@ -206,26 +229,40 @@ private:
     // owner_cl: a cluster of the problem (of a batch) the temporary belongs to
     View new_temp(int32_t row_cl, int32_t rows, int32_t cols, int32_t rslot, int32_t cslot, int32_t owner_cl);
     // Allocations of the current plan in the arena, in bump order (temp_obj >= 0: a product
-    // temporary), and the tasks that touch each cell of each temporary (object, cell within the
-    // object, task, written).
+    // temporary).
     struct PlanItem {
         int64_t off, size;
         int32_t temp_obj;
     };
     std::vector<PlanItem> plan_items;
     int64_t plan_begin = 0;
-    std::vector<int32_t> touch_obj, touch_cell, touch_task;
-    std::vector<uint8_t> touch_write;
     std::vector<std::array<int32_t, 4>> temp_shape;  // per temporary object: problem, row cluster, rows, cols
     int64_t plan_alloc(int64_t elems, int32_t temp_obj);
-    // per object: its elements when it is a temporary of the current plan (else 0), and the first and
-    // last dependency level of a task that touches it
+    // per object: its elements when it is a temporary of the current plan (else 0)
     std::vector<int64_t> temp_size;
-    std::vector<int32_t> temp_first, temp_last;
     void temp_levels(Plan &p) const;
     void relocate_temps(Plan &p);
     void note_temp(int32_t obj, int64_t elems, const std::array<int32_t, 4> &shape);
     void cells_of(const View &v, std::vector<int64_t> &out) const;
+    // The cells a view covers: rows r0..r1-1 and columns c0..c1-1 of the cell grid of an object whose
+    // cells start at base with nc per row; temp_obj is the object when it is a temporary of the
+    // current plan, else -1.
+    struct ViewRec {
+        int64_t base;
+        int32_t nc, r0, r1, c0, c1, temp_obj;
+    };
+    void describe(const View &v, ViewRec &r) const;
+    // The dependency analysis of task g (reads first, then writes): its predecessors, its wave, the
+    // level interval of the temporaries it touches.  Returns the wave.
+    int32_t analyze(Deps &d, std::vector<int32_t> &pred_ptr, std::vector<int32_t> &pred_idx, const ViewRec *v,
+                    size_t nr, size_t nw, int32_t g) const;
+    // Factorisation emission with the analysis on a second host thread: emit_views hands the
+    // tasks' cells to it in chunks (pipe_begin / pipe_end around the recursion).
+    struct Pipe;
+    Pipe *pipe = nullptr;
+    void pipe_begin();
+    void reserve_factorisation();
+    int pipe_end();
     int32_t emit_views(Kind k, const View *const *reads, size_t nr, const View *const *writes, size_t nw);
     int32_t emit(Kind k, std::initializer_list<const View *> reads, std::initializer_list<const View *> writes) {
         return emit_views(k, reads.begin(), reads.size(), writes.begin(), writes.size());

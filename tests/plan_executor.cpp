@@ -408,3 +408,43 @@ extern "C" int plan_execute(int32_t n, int32_t n_clusters, const int32_t *perm, 
         for (int i = 0; i < n; ++i) b[i + int64_t(j) * n] = ex.A[pl.f_solve_off + i + int64_t(j) * n];
     return ex.err ? -2 : 0;
 }
+
+// Plans the H-matrix twice, with the factorisation's dependency analysis on a second thread
+// (batch_threads = 0) and all on one thread (batch_threads = -1), and compares the three plans'
+// graphs: task codes, waves, predecessor and successor lists, in-degrees, roots and their
+// priorities, and the arena sizes.  Returns 0 when they are equal, else 1 + the index of the first
+// array that differs (plan * 16 + array), or the planner's status.
+extern "C" int plan_graphs_equal(int32_t n, int32_t n_clusters, const int32_t *perm, const int32_t *begin,
+                                 const int32_t *size, const int32_t *son0, const int32_t *son1, int64_t n_leaves,
+                                 const int32_t *row_cl, const int32_t *col_cl, const int8_t *kind,
+                                 const int32_t *rank, const int64_t *offset, const double *data, int64_t data_len,
+                                 int32_t inv_block, int32_t temp_reuse) {
+    Planner pl[2];
+    for (int v = 0; v < 2; ++v) {
+        PlanOptions o;
+        o.batch_threads = v == 0 ? 0 : -1;
+        if (inv_block != 0) o.inv_block = inv_block < 0 ? 0 : inv_block;
+        o.temp_reuse = temp_reuse != 0;
+        o.wave_order = false;
+        int st = pl[v].build(n, n_clusters, perm, begin, size, son0, son1, n_leaves, row_cl, col_cl, kind, rank,
+                             offset, data, data_len, o);
+        if (st == 0) st = pl[v].plan_all();
+        if (st) return st;
+    }
+    if (pl[0].f_elems != pl[1].f_elems || pl[0].a_elems != pl[1].a_elems) return 1;
+    const Plan *a[3] = {&pl[0].fplan, &pl[0].splan, &pl[0].mplan}, *b[3] = {&pl[1].fplan, &pl[1].splan, &pl[1].mplan};
+    for (int q = 0; q < 3; ++q) {
+        const Plan &x = *a[q], &y = *b[q];
+        const int code = 2 + 16 * q;
+        if (x.n_tasks != y.n_tasks || x.n_waves != y.n_waves || x.n_edges != y.n_edges) return code;
+        if (x.temp_elems != y.temp_elems || x.temp_peak_elems != y.temp_peak_elems) return code + 1;
+        if (x.task_code != y.task_code) return code + 2;
+        for (int k = 0; k < K_NKINDS; ++k)
+            if (x.wave[k] != y.wave[k]) return code + 3;
+        if (x.pred_ptr != y.pred_ptr || x.pred_idx != y.pred_idx) return code + 4;
+        if (x.succ_ptr != y.succ_ptr || x.succ_idx != y.succ_idx) return code + 5;
+        if (x.indeg != y.indeg || x.roots != y.roots || x.root_bl != y.root_bl) return code + 6;
+        if (x.critical_us != y.critical_us) return code + 7;
+    }
+    return 0;
+}

@@ -202,3 +202,29 @@ def test_batch_with_clusters_out_of_problem_order_is_planned_as_one_forest(execu
         assert q.offset[l] == ref_q.offset[l]
     assert np.array_equal(q.data, ref_q.data)
     assert np.array_equal(x, ref_x)
+
+
+@pytest.mark.parametrize("inv_block,temp_reuse", [(-1, 0), (0, 0), (0, 1)])
+def test_piped_analysis_builds_the_serial_graphs(executor, inv_block, temp_reuse):
+    """The factorisation's dependency analysis on a second host thread (the default for one problem)
+    builds exactly the graphs of the one-thread planner: task codes, waves, predecessor and successor
+    lists, roots and priorities of the factorisation, solve and matvec plans, and the arena sizes."""
+    from bem_inputs import build_problem
+    lib = executor
+    lib.plan_graphs_equal.restype = ctypes.c_int
+    for p in (build_problem(3, 32, 2.0, 1e-4, nrhs=1),
+              build_problem(4, 32, 2.0, 1e-6, nrhs=1, seed=3, axes=(1.0, 0.7, 0.5))):
+        t = p.tree
+        keep = []
+
+        def ptr(a, tp):
+            x = np.ascontiguousarray(a, dtype=tp)
+            keep.append(x)
+            return x.ctypes.data_as(ctypes.c_void_p)
+        st = lib.plan_graphs_equal(
+            ctypes.c_int32(p.n), ctypes.c_int32(t.n_clusters), ptr(t.perm, np.int32), ptr(t.begin, np.int32),
+            ptr(t.size, np.int32), ptr(t.son0, np.int32), ptr(t.son1, np.int32), ctypes.c_int64(p.n_leaves),
+            ptr(p.row_cl, np.int32), ptr(p.col_cl, np.int32), ptr(p.kind, np.int8), ptr(p.rank, np.int32),
+            ptr(p.offset, np.int64), ptr(p.data, np.float64), ctypes.c_int64(p.data.size),
+            ctypes.c_int32(inv_block), ctypes.c_int32(temp_reuse))
+        assert st == 0, (p.n, st)
