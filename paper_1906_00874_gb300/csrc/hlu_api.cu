@@ -6,8 +6,10 @@
 #include <functional>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/hlu.h"
@@ -373,24 +375,47 @@ template <class T>
 int upload_arenas(hlu_ctx *h, const double *data) {
     Planner &pl = h->pl;
     // A_H arena: leaves exactly as given (FP64), then zeroed work panels
-    std::vector<double> a_leaves;
     int64_t a_leaf_end = 0;
     for (const Store &s : pl.astore) {
         int64_t end = s.kind == B_DENSE ? s.D_off + int64_t(s.m) * s.n : s.V_off + int64_t(s.n) * s.krank;
         a_leaf_end = std::max(a_leaf_end, end);
     }
-    a_leaves.assign(a_leaf_end, 0.0);
+    // the staging copy, split over host threads by leaves (panels are packed in leaf order, each
+    // followed by at most 7 elements of alignment that are zeroed)
+    std::unique_ptr<double[]> a_leaves(new (std::nothrow) double[std::max<int64_t>(a_leaf_end, 1)]);
+    if (!a_leaves) return HLU_ENOMEM;
+    auto stage = [&](int64_t l0, int64_t l1) {
+        auto put = [&](int64_t off, const double *src, int64_t len, int64_t next) {
+            std::memcpy(&a_leaves[off], src, sizeof(double) * len);
+            for (int64_t i = off + len; i < std::min(next, a_leaf_end); ++i) a_leaves[i] = 0.0;
+        };
+        for (int64_t l = l0; l < l1; ++l) {
+            const Store &s = pl.astore[l];
+            const double *src = data + pl.leaf_offset[l];
+            if (s.kind == B_DENSE) {
+                const int64_t len = int64_t(s.m) * s.n;
+                put(s.D_off, src, len, (s.D_off + len + 7) & ~int64_t(7));
+            } else {
+                const int64_t lu = int64_t(s.m) * s.krank, lv = int64_t(s.n) * s.krank;
+                put(s.U_off, src, lu, s.V_off);
+                put(s.V_off, src + lu, lv, (s.V_off + lv + 7) & ~int64_t(7));
+            }
+        }
+    };
+    const int nthreads = int(std::min<int64_t>(std::max(1u, std::min(8u, std::thread::hardware_concurrency())),
+                                                std::max<int64_t>(1, a_leaf_end >> 20)));
+    if (nthreads <= 1) {
+        stage(0, pl.n_leaves);
+    } else {
+        std::vector<std::thread> pool;
+        for (int q = 0; q < nthreads; ++q)
+            pool.emplace_back(stage, pl.n_leaves * q / nthreads, pl.n_leaves * (q + 1) / nthreads);
+        for (std::thread &th : pool) th.join();
+    }
     std::vector<int64_t> desc(kLeafDesc * pl.n_leaves);
     for (int64_t l = 0; l < pl.n_leaves; ++l) {
         const Store &s = pl.astore[l];
         const Store &f = pl.fstore[l];
-        const double *src = data + pl.leaf_offset[l];
-        if (s.kind == B_DENSE) {
-            std::memcpy(&a_leaves[s.D_off], src, sizeof(double) * s.m * s.n);
-        } else {
-            std::memcpy(&a_leaves[s.U_off], src, sizeof(double) * s.m * s.krank);
-            std::memcpy(&a_leaves[s.V_off], src + int64_t(s.m) * s.krank, sizeof(double) * s.n * s.krank);
-        }
         int64_t *d = &desc[kLeafDesc * l];
         d[0] = s.kind == B_DENSE ? 0 : 1;
         d[1] = s.m;
@@ -405,7 +430,7 @@ int upload_arenas(hlu_ctx *h, const double *data) {
     int st;
     if ((st = dalloc(h, &h->aarena, pl.a_elems))) return st;
     if ((st = cuda_status(cudaMemsetAsync(h->aarena, 0, sizeof(double) * pl.a_elems, h->stream)))) return st;
-    if ((st = cuda_status(cudaMemcpyAsync(h->aarena, a_leaves.data(), sizeof(double) * a_leaf_end,
+    if ((st = cuda_status(cudaMemcpyAsync(h->aarena, a_leaves.get(), sizeof(double) * a_leaf_end,
                                           cudaMemcpyHostToDevice, h->stream))))
         return st;
     if ((st = upload(h, &h->leaf_desc, desc))) return st;
