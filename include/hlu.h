@@ -132,12 +132,14 @@ enum {
        of CUDA cores.  Off by default: these leaf-sized products (a 64-row leaf cluster, tens of
        inner columns) ran slower on the tensor cores than on CUDA cores in every measured workload */
     HLU_FLAG_TENSOR = 1,
-    HLU_FLAG_SERIAL_PLAN = 2  /* hlu_create_batch / hlu_plan_info_batch with the data-flow
-                                 schedule: plan the whole batch as one H-matrix on one host
-                                 thread.  By default the problems are planned separately on all
-                                 host threads and their task graphs joined (the same tasks and
-                                 dependencies; each problem keeps its own unused copy of the
-                                 n x nrhs_max work panels in the arenas) */
+    HLU_FLAG_SERIAL_PLAN = 2  /* plan on one host thread.  hlu_create_batch / hlu_plan_info_batch
+                                 with the data-flow schedule: plan the whole batch as one H-matrix.
+                                 By default the problems are planned separately on all host threads
+                                 and their task graphs joined (the same tasks and dependencies; each
+                                 problem keeps its own unused copy of the n x nrhs_max work panels
+                                 in the arenas).  hlu_create / hlu_plan_info_get: by default the
+                                 dependency analysis of the factorisation runs on a second host
+                                 thread beside the expansion of the recursion (the same graph) */
 };
 
 typedef struct hlu_ctx *hlu_t;

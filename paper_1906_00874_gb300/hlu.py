@@ -20,7 +20,7 @@ HLU_FP32_CORE32 = 2   # FP32 factors, FP32 Jacobi in the truncation cores
 SCHED_DATAFLOW = 0
 SCHED_WAVES = 1
 FLAG_TENSOR = 1       # FP32 factors: dense products of the factorisation on the tensor cores
-FLAG_SERIAL_PLAN = 2  # a batch planned as one H-matrix on one host thread (default: per problem, in parallel)
+FLAG_SERIAL_PLAN = 2  # plan on one host thread (default: a batch per problem in parallel, one problem on two threads)
 
 STATUS = {0: "HLU_OK", 1: "HLU_EINVAL", 2: "HLU_ENOMEM", 3: "HLU_ESTATE", 4: "HLU_EPIVOT",
           5: "HLU_ERANKCAP", 6: "HLU_ETIMEOUT", 7: "HLU_ECUDA", 8: "HLU_ENUMERIC"}
