@@ -54,6 +54,9 @@ def parse():
                     help="FP32 factors: dense products of the factorisation on the tensor cores (tcgen05)")
     ap.add_argument("--no-c3", action="store_true",
                     help="skip the n = 81920 leg (GMRES(30), eps 1e-6, 64 rhs) reported in the sphere20480 line")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the batched (ellipsoids64) and serving (serve64r5) legs reported in the sphere20480 "
+                         "line")
     ap.add_argument("--construct", action="store_true",
                     help="time the construction of the workload's H-matrix on the GPU (hlu_bem_build)")
     return ap.parse_args()
@@ -350,6 +353,64 @@ def make_handle(p, precision, stream):
     return HLU.from_problem(p, precision=precision, stream=stream, flags=FLAGS)
 
 
+_T_START = time.time()
+
+
+def _pick(d, keys):
+    """The entries of d named by keys ("a.b" reaches into a nested dict); missing ones are left out."""
+    out = {}
+    for k in keys:
+        v, ok = d, True
+        for part in k.split("."):
+            ok = isinstance(v, dict) and part in v
+            if not ok:
+                break
+            v = v[part]
+        if ok:
+            out[k] = v
+    return out
+
+
+# The batched and serving workloads as they run alone (their own bench lines), summarised into the
+# headline line: each is a child process, so that a failure or a hang there cannot cost this line.
+EXTRA_LEGS = (
+    ("c4_ellipsoids64", ["--workload", "ellipsoids64", "--steps", "2", "--warmup", "3"],
+     ("config.workload", "value", "unit", "ms_per_step", "steps", "warmup", "loop_fp64_ms", "speedup_vs_fp64_loop",
+      "worst_problem_resid", "efac_stacked_fp32", "factor_model_gflop", "max_rank", "plan", "e2e.value",
+      "e2e.ms_per_step", "roofline.frac", "cpu_baseline.value", "cpu_baseline.unit", "cpu_baseline.sample",
+      "gpu_launches", "clocks")),
+    ("c5_serve64r5", ["--workload", "serve64r5"],
+     ("config.workload", "value", "unit", "p50_ms", "p99_ms", "mean_ms", "capacity_rps", "capacity_burst_rps",
+      "arrival_rate_rps", "device_overlap.fraction", "server.groups_created", "server.evicted_groups",
+      "latency_breakdown.resident", "latency_breakdown.waited_for_admission", "gpu_launches", "clocks")),
+)
+
+
+def extra_legs(budget_s=480.0, leg_cap_s=300.0):
+    """Runs EXTRA_LEGS while the whole bench stays within budget_s seconds of wall time."""
+    legs = {}
+    for key, argv, keys in EXTRA_LEGS:
+        left = min(leg_cap_s, budget_s - (time.time() - _T_START))
+        if left < 60.0:
+            legs[key] = {"skipped": "bench wall-time budget spent"}
+            continue
+        try:
+            t0 = time.time()
+            r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + argv, capture_output=True,
+                               text=True, timeout=left, cwd=ROOT)
+            line = next((ln for ln in reversed(r.stdout.splitlines()) if ln.startswith("{")), None)
+            if r.returncode != 0 or line is None:
+                legs[key] = {"error": f"exit {r.returncode}: " + " | ".join(r.stderr.strip().splitlines()[-3:])}
+            else:
+                legs[key] = _pick(json.loads(line), keys)
+                legs[key]["wall_s"] = round(time.time() - t0, 1)
+        except subprocess.TimeoutExpired:
+            legs[key] = {"error": f"timed out after {left:.0f} s"}
+        except Exception as e:  # reported, not fatal
+            legs[key] = {"error": f"{type(e).__name__}: {e}"}
+    return legs
+
+
 def run_native(args):
     import numpy as np
     import torch
@@ -535,6 +596,10 @@ def run_native(args):
         except Exception as e:  # reported, not fatal
             cpu = {"value": None, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
 
+    legs = None
+    if rank == 0 and world == 1 and args.workload == WORKLOAD and not args.no_c3 and not args.no_extra:
+        legs = extra_legs()
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
@@ -553,6 +618,7 @@ def run_native(args):
                                                   "iteration (hlu_factor_error), bound 10 eps",
             "fp64_arm": arm64, "fp32_core32_arm": core32, "e2e": e2e, "gpu_launches": arm32["launches"], "clocks": clk.summary(),
             "roofline": roof, "cpu_baseline": cpu, "c3_sphere81920": c3,
+            **(legs or {}),
             "alu_peaks_tflops": {"fp64": fp64_peak, "fp32": fp32_peak},
             "plan": {"tasks": st32["n_tasks"], "waves": st32["n_waves"], "launches_per_factor": st32["n_launches"]},
         }

@@ -35,3 +35,41 @@ def test_native_and_reference_arms_share_the_config():
     b = bench.workload_config(args, w, p, 1)
     assert a == b and a["n"] == 20480 and a["solver"] == "iterative refinement"
     assert "sphere20480" in a["workload"] and "1e-10" in a["workload"]
+
+
+def test_pick_reaches_into_nested_entries_and_skips_missing_ones():
+    d = {"a": 1, "b": {"c": 2, "d": {"e": 3}}, "x": None}
+    assert bench._pick(d, ("a", "b.c", "b.d.e", "b.z", "x", "q")) == {"a": 1, "b.c": 2, "b.d.e": 3, "x": None}
+
+
+def test_extra_legs_run_as_children_and_report_their_failure(monkeypatch):
+    """Each leg is a child process; a child that fails leaves an error entry, and once the wall-time
+    budget is spent the remaining legs are skipped without being started."""
+    calls = []
+
+    def fake_run(cmd, **kw):
+        calls.append(cmd)
+        return types.SimpleNamespace(returncode=1, stdout="", stderr="a\nb\nRuntimeError: no device\n")
+    monkeypatch.setattr(bench.subprocess, "run", fake_run)
+    monkeypatch.setattr(bench, "_T_START", bench.time.time())
+    legs = bench.extra_legs(budget_s=1000.0)
+    assert set(legs) == {k for k, _, _ in bench.EXTRA_LEGS}
+    assert all("no device" in v["error"] for v in legs.values())
+    assert len(calls) == len(bench.EXTRA_LEGS) and all("--workload" in c for c in calls)
+    calls.clear()
+    monkeypatch.setattr(bench, "_T_START", bench.time.time() - 990.0)
+    legs = bench.extra_legs(budget_s=1000.0)
+    assert not calls and all("skipped" in v for v in legs.values())
+
+
+def test_extra_legs_keep_the_summary_of_the_childs_line(monkeypatch):
+    line = {"value": 40.2, "unit": "problems/s", "config": {"workload": "w"}, "e2e": {"value": 15.0}, "big": [1] * 9}
+
+    def fake_run(cmd, **kw):
+        return types.SimpleNamespace(returncode=0, stdout="log line\n" + bench.json.dumps(line) + "\n", stderr="")
+    monkeypatch.setattr(bench.subprocess, "run", fake_run)
+    monkeypatch.setattr(bench, "_T_START", bench.time.time())
+    legs = bench.extra_legs(budget_s=1000.0)
+    c4 = legs["c4_ellipsoids64"]
+    assert c4["value"] == 40.2 and c4["config.workload"] == "w" and c4["e2e.value"] == 15.0
+    assert "big" not in c4 and "wall_s" in c4
