@@ -120,7 +120,8 @@ struct PlanOptions {
                                 // threads (0: all hardware threads) and their graphs joined
                                 // (plan_batch); < 0: one plan of the whole forest on one thread.
                                 // Unless this is < 0, a factorisation plan that plan_all emits in
-                                // one piece has its dependency analysis on a second thread.
+                                // one piece has its dependency analysis on a second thread (so do
+                                // the problems of a batch when the pool has two threads for each).
 };
 
 class Planner {

@@ -275,13 +275,18 @@ int Planner::plan_batch() {
         return st ? st : plan_all();
     }
     const int32_t count = n_inst;
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int32_t nthreads = std::max(1, std::min<int32_t>(count, opt.batch_threads > 0 ? opt.batch_threads
+                                                                                         : int32_t(hw)));
+    // a problem's own dependency analysis gets a second thread when the pool leaves one per problem
+    const int32_t part_threads = 2 * nthreads <= int32_t(hw) ? 0 : -1;
     std::vector<std::unique_ptr<Planner>> parts(count);
     for (int32_t i = 0; i < count; ++i) {
         parts[i].reset(new (std::nothrow) Planner());
         if (!parts[i]) return HLU_ENOMEM;
         Planner &q = *parts[i];
         q.opt = opt;
-        q.opt.batch_threads = -1;
+        q.opt.batch_threads = part_threads;
         q.n = rb[i + 1] - rb[i];
         q.n_inst = 1;
         const int32_t c0 = cb[i], lc0 = cl[c0].lc_first;
@@ -335,9 +340,6 @@ int Planner::plan_batch() {
             status[order[j]] = st;
         }
     };
-    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-    const int32_t nthreads = std::max(1, std::min<int32_t>(count, opt.batch_threads > 0 ? opt.batch_threads
-                                                                                         : int32_t(hw)));
     {
         std::vector<std::thread> pool;
         for (int32_t t = 1; t < nthreads; ++t) pool.emplace_back(worker);
