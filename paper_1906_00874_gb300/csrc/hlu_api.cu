@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <functional>
 #include <cmath>
@@ -582,7 +583,7 @@ struct Forest {
     std::vector<int32_t> perm, begin, size, son0, son1, inst, rc, cc, rk;
     std::vector<int8_t> kd;
     std::vector<int64_t> off;
-    std::vector<double> data;
+    std::unique_ptr<double[]> data;
     hlu_tree t{};
     hlu_blocks b{};
 };
@@ -615,12 +616,13 @@ int make_forest(int32_t count, const hlu_tree *trees, const hlu_blocks *blocks, 
     f.rk.assign(nl, 0);
     f.kd.assign(nl, 0);
     f.off.assign(nl, 0);
-    f.data.assign(dl, 0.0);
+    f.data.reset(new (std::nothrow) double[std::max<int64_t>(dl, 1)]);
+    if (!f.data) return HLU_ENOMEM;
     std::vector<int32_t> &perm = f.perm, &begin = f.begin, &size = f.size, &son0 = f.son0, &son1 = f.son1,
                          &inst = f.inst, &rc = f.rc, &cc = f.cc, &rk = f.rk;
     std::vector<int8_t> &kd = f.kd;
     std::vector<int64_t> &off = f.off, cl_off(count);
-    std::vector<double> &data = f.data;
+    std::vector<int64_t> data_at(count);  // where each problem's leaf data starts in the concatenation
     int64_t no = 0, co = count - 1, lo = 0, dof = 0;
     for (int32_t i = 0; i < count; ++i) {
         const hlu_tree &t = trees[i];
@@ -641,11 +643,25 @@ int make_forest(int32_t count, const hlu_tree *trees, const hlu_blocks *blocks, 
             rk[lo + l] = b.rank[l];
             off[lo + l] = b.offset[l] + dof;
         }
-        std::memcpy(data.data() + dof, b.data, sizeof(double) * b.data_len);
+        data_at[i] = dof;
         no += t.n;
         co += t.n_clusters;
         lo += b.n_leaves;
         dof += b.data_len;
+    }
+    // the leaf data, copied problem by problem on up to eight host threads
+    {
+        std::atomic<int32_t> next{0};
+        auto copy = [&] {
+            for (int32_t i; (i = next.fetch_add(1)) < count;)
+                std::memcpy(f.data.get() + data_at[i], blocks[i].data, sizeof(double) * blocks[i].data_len);
+        };
+        const int nthreads = int(std::min<int64_t>(std::max(1u, std::min(8u, std::thread::hardware_concurrency())),
+                                                    std::min<int64_t>(count, std::max<int64_t>(1, dl >> 20))));
+        std::vector<std::thread> pool;
+        for (int q = 1; q < nthreads; ++q) pool.emplace_back(copy);
+        copy();
+        for (std::thread &th : pool) th.join();
     }
     // a balanced binary tree of clusters over the instances, numbered from 0 (the root)
     int32_t next_v = 0;
@@ -661,7 +677,7 @@ int make_forest(int32_t count, const hlu_tree *trees, const hlu_blocks *blocks, 
     };
     make(0, count);
     f.t = hlu_tree{int32_t(N), int32_t(ncl), perm.data(), begin.data(), size.data(), son0.data(), son1.data()};
-    f.b = hlu_blocks{nl, rc.data(), cc.data(), kd.data(), rk.data(), off.data(), data.data(), dl};
+    f.b = hlu_blocks{nl, rc.data(), cc.data(), kd.data(), rk.data(), off.data(), f.data.get(), dl};
     return HLU_OK;
 }
 

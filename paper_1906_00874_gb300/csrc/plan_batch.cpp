@@ -134,76 +134,110 @@ void reserve_joined(Plan &q, const PlanBase &tot) {
     q.n_edges = tot.edges;
 }
 
-// Appends problem plan p (bases b: the sizes of the joined arrays so far) to the joined plan q,
-// shifting everything by s.
-void join_plan(const Plan &p, const PlanBase &b, const Shift &s, Plan &q) {
-    for (TGetrf t : p.getrf) {
-        t.off = s.off(t.off);
-        t.leaf = s.store(t.leaf);
-        q.getrf.push_back(t);
-    }
-    for (TTrsm t : p.trsm) {
-        t.L_off = s.off(t.L_off);
-        s.panel(t.P);
-        q.trsm.push_back(t);
-    }
-    for (TProject t : p.project) {
-        s.panel(t.F);
-        s.panel(t.X);
-        s.panel(t.T);
-        t.dst0 = s.slot_of(t.dst0);
-        t.src0 = s.slot_of(t.src0);
-        t.dst1 = s.slot_of(t.dst1);
-        t.src1 = s.slot_of(t.src1);
-        q.project.push_back(t);
-    }
-    for (TAccum t : p.accum) {
-        s.panel(t.out);
-        t.term0 += int32_t(b.terms);
-        t.dst = s.slot_of(t.dst);
-        t.src = s.slot_of(t.src);
-        q.accum.push_back(t);
-    }
-    for (Term t : p.terms) {
-        s.panel(t.A);
-        s.panel(t.X);
-        q.terms.push_back(t);
-    }
-    for (TRadd t : p.radd) {
-        t.U_off = s.off(t.U_off);
-        t.V_off = s.off(t.V_off);
-        t.scratch_off = s.off(t.scratch_off);
-        t.kslot = s.slot_of(t.kslot);
-        t.piece0 += int32_t(b.pieces);
-        t.target = s.store(t.target);
-        t.inst = s.inst;
-        q.radd.push_back(t);
-    }
-    for (Piece t : p.pieces) {
-        s.panel(t.U);
-        s.panel(t.V);
-        q.pieces.push_back(t);
-    }
-    for (TSplit t : p.split) {
-        s.panel(t.srcU);
-        s.panel(t.srcV);
-        t.dstU = s.off(t.dstU);
-        t.dstV = s.off(t.dstV);
-        t.src_kslot = s.slot_of(t.src_kslot);
-        t.dst_kslot = s.slot_of(t.dst_kslot);
-        q.split.push_back(t);
-    }
-    for (int k = 0; k < K_NKINDS; ++k) q.wave[k].insert(q.wave[k].end(), p.wave[k].begin(), p.wave[k].end());
-    for (int64_t g = 0; g < p.n_tasks; ++g) {
-        const int32_t c = p.task_code[g], k = c >> kCodeShift;
-        q.task_code.push_back((k << kCodeShift) | int32_t((c & kCodeMask) + b.kind[k]));
-        q.indeg.push_back(p.indeg[g]);
-        q.succ_ptr.push_back(int32_t(p.succ_ptr[g + 1] + b.edges));
-    }
-    for (int32_t t : p.succ_idx) q.succ_idx.push_back(int32_t(t + b.tasks));
-    for (size_t r = 0; r < p.roots.size(); ++r) {
-        q.roots.push_back(int32_t(p.roots[r] + b.tasks));
-        q.root_bl.push_back(p.root_bl[r]);
+// Appends one group of the arrays of problem plan p (bases b: the sizes of the joined arrays so far)
+// to the joined plan q, shifting everything by s, and frees them in p.  The groups touch disjoint
+// arrays, so they are joined on kJoinGroups threads at once: 0: GETRF, TRSM, PROJECT and SPLIT
+// tasks; 1: ACCUM tasks; 2: their terms; 3: RADD tasks and their pieces; 4: the graph (task codes,
+// in-degrees, successors, roots).
+constexpr int kJoinGroups = 5;
+
+template <class V>
+void release(V &v) {
+    V().swap(v);
+}
+
+void join_group(int group, Plan &p, const PlanBase &b, const Shift &s, Plan &q) {
+    auto waves = [&](int k) {
+        q.wave[k].insert(q.wave[k].end(), p.wave[k].begin(), p.wave[k].end());
+        release(p.wave[k]);
+    };
+    if (group == 0) {
+        for (TGetrf t : p.getrf) {
+            t.off = s.off(t.off);
+            t.leaf = s.store(t.leaf);
+            q.getrf.push_back(t);
+        }
+        for (TTrsm t : p.trsm) {
+            t.L_off = s.off(t.L_off);
+            s.panel(t.P);
+            q.trsm.push_back(t);
+        }
+        for (TProject t : p.project) {
+            s.panel(t.F);
+            s.panel(t.X);
+            s.panel(t.T);
+            t.dst0 = s.slot_of(t.dst0);
+            t.src0 = s.slot_of(t.src0);
+            t.dst1 = s.slot_of(t.dst1);
+            t.src1 = s.slot_of(t.src1);
+            q.project.push_back(t);
+        }
+        for (TSplit t : p.split) {
+            s.panel(t.srcU);
+            s.panel(t.srcV);
+            t.dstU = s.off(t.dstU);
+            t.dstV = s.off(t.dstV);
+            t.src_kslot = s.slot_of(t.src_kslot);
+            t.dst_kslot = s.slot_of(t.dst_kslot);
+            q.split.push_back(t);
+        }
+        release(p.getrf);
+        release(p.trsm);
+        release(p.project);
+        release(p.split);
+        for (int k : {K_GETRF, K_TRSM, K_PROJECT, K_SPLIT}) waves(k);
+    } else if (group == 1) {
+        for (TAccum t : p.accum) {
+            s.panel(t.out);
+            t.term0 += int32_t(b.terms);
+            t.dst = s.slot_of(t.dst);
+            t.src = s.slot_of(t.src);
+            q.accum.push_back(t);
+        }
+        release(p.accum);
+        waves(K_ACCUM);
+    } else if (group == 2) {
+        for (Term t : p.terms) {
+            s.panel(t.A);
+            s.panel(t.X);
+            q.terms.push_back(t);
+        }
+        release(p.terms);
+    } else if (group == 3) {
+        for (TRadd t : p.radd) {
+            t.U_off = s.off(t.U_off);
+            t.V_off = s.off(t.V_off);
+            t.scratch_off = s.off(t.scratch_off);
+            t.kslot = s.slot_of(t.kslot);
+            t.piece0 += int32_t(b.pieces);
+            t.target = s.store(t.target);
+            t.inst = s.inst;
+            q.radd.push_back(t);
+        }
+        for (Piece t : p.pieces) {
+            s.panel(t.U);
+            s.panel(t.V);
+            q.pieces.push_back(t);
+        }
+        release(p.radd);
+        release(p.pieces);
+        waves(K_RADD);
+    } else {
+        for (int64_t g = 0; g < p.n_tasks; ++g) {
+            const int32_t c = p.task_code[g], k = c >> kCodeShift;
+            q.task_code.push_back((k << kCodeShift) | int32_t((c & kCodeMask) + b.kind[k]));
+            q.indeg.push_back(p.indeg[g]);
+            q.succ_ptr.push_back(int32_t(p.succ_ptr[g + 1] + b.edges));
+        }
+        for (int32_t t : p.succ_idx) q.succ_idx.push_back(int32_t(t + b.tasks));
+        for (size_t r = 0; r < p.roots.size(); ++r) {
+            q.roots.push_back(int32_t(p.roots[r] + b.tasks));
+            q.root_bl.push_back(p.root_bl[r]);
+        }
+        release(p.task_code);
+        release(p.indeg);
+        release(p.succ_ptr);
+        release(p.succ_idx);
     }
 }
 
@@ -453,7 +487,18 @@ int Planner::plan_batch() {
         error = "host memory exhausted while joining the plans";
         return HLU_ENOMEM;
     }
-    // join in problem order, freeing every problem's plan after its append
+    // join in problem order: the plans' groups of arrays each on its own thread, freeing what it has
+    // appended, the stores and inverse blocks here
+    auto join_plans = [&](int group) {
+        for (int32_t i = 0; i < count; ++i) {
+            Planner &q = *parts[i];
+            join_group(group, q.fplan, fb[i], fs[i], fplan);
+            join_group(group, q.splan, sb[i], fs[i], splan);
+            join_group(group, q.mplan, mb[i], as[i], mplan);
+        }
+    };
+    std::vector<std::thread> joiners;
+    for (int group = 0; group < kJoinGroups; ++group) joiners.emplace_back(join_plans, group);
     for (int32_t i = 0; i < count; ++i) {
         Planner &q = *parts[i];
         const Shift &f = fs[i], &a = as[i];
@@ -483,11 +528,9 @@ int Planner::plan_batch() {
             inv_U_off[inv_base[i] + j] = f.off(q.inv_U_off[j]);
             inv_index[q.inv_cl[j] + f.cluster] = int32_t(inv_base[i] + j);
         }
-        join_plan(q.fplan, fb[i], f, fplan);
-        join_plan(q.splan, sb[i], f, splan);
-        join_plan(q.mplan, mb[i], a, mplan);
-        parts[i].reset();
     }
+    for (std::thread &th : joiners) th.join();
+    for (int32_t i = 0; i < count; ++i) parts[i].reset();
     // graph-wide figures (the problems run side by side), and the roots of all problems in one
     // order of priority (longest remaining path first), as a single plan orders its own
     for (int w = 0; w < 3; ++w) {
