@@ -408,10 +408,7 @@ int upload_arenas(hlu_ctx *h, const double *data) {
     if (nthreads <= 1) {
         stage(0, pl.n_leaves);
     } else {
-        std::vector<std::thread> pool;
-        for (int q = 0; q < nthreads; ++q)
-            pool.emplace_back(stage, pl.n_leaves * q / nthreads, pl.n_leaves * (q + 1) / nthreads);
-        for (std::thread &th : pool) th.join();
+        run_parts(nthreads, [&](int q) { stage(pl.n_leaves * q / nthreads, pl.n_leaves * (q + 1) / nthreads); });
     }
     std::vector<int64_t> desc(kLeafDesc * pl.n_leaves);
     for (int64_t l = 0; l < pl.n_leaves; ++l) {
@@ -658,10 +655,7 @@ int make_forest(int32_t count, const hlu_tree *trees, const hlu_blocks *blocks, 
         };
         const int nthreads = int(std::min<int64_t>(std::max(1u, std::min(8u, std::thread::hardware_concurrency())),
                                                     std::min<int64_t>(count, std::max<int64_t>(1, dl >> 20))));
-        std::vector<std::thread> pool;
-        for (int q = 1; q < nthreads; ++q) pool.emplace_back(copy);
-        copy();
-        for (std::thread &th : pool) th.join();
+        run_parts(nthreads, [&](int) { copy(); });
     }
     // a balanced binary tree of clusters over the instances, numbered from 0 (the root)
     int32_t next_v = 0;

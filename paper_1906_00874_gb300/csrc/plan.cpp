@@ -12,6 +12,7 @@
 #include <condition_variable>
 #include <map>
 #include <mutex>
+#include <system_error>
 #include <thread>
 #include <utility>
 #include <functional>
@@ -482,14 +483,14 @@ struct Planner::Pipe {
     }
 };
 
-void Planner::pipe_begin() {
+bool Planner::pipe_begin() {
     pipe = new Pipe();
     Pipe *q = pipe;
     q->d.swap(dep);
     q->pred_ptr.swap(P->pred_ptr);
     q->pred_idx.swap(P->pred_idx);
     q->g0 = int32_t(P->n_tasks);
-    q->th = std::thread([this, q] {
+    auto work = [this, q] {
         int32_t g = q->g0;
         for (;;) {
             size_t idx;
@@ -518,7 +519,18 @@ void Planner::pipe_begin() {
             ++q->consumed;
             q->cv.notify_all();
         }
-    });
+    };
+    try {
+        q->th = std::thread(work);
+    } catch (const std::system_error &) {  // no thread to be had: the analysis stays on this one
+        dep.swap(q->d);
+        P->pred_ptr.swap(q->pred_ptr);
+        P->pred_idx.swap(q->pred_idx);
+        delete q;
+        pipe = nullptr;
+        return false;
+    }
+    return true;
 }
 
 int Planner::pipe_end() {
@@ -1612,11 +1624,8 @@ int Planner::build(int32_t n_, int32_t n_clusters, const int32_t *perm_, const i
     if (nthreads <= 1) {
         bad = scan(0, n_leaves);
     } else {
-        std::vector<std::thread> pool;
         std::vector<char> flag(nthreads, 0);
-        for (int q = 0; q < nthreads; ++q)
-            pool.emplace_back([&, q] { flag[q] = scan(n_leaves * q / nthreads, n_leaves * (q + 1) / nthreads); });
-        for (std::thread &th : pool) th.join();
+        run_parts(nthreads, [&](int q) { flag[q] = scan(n_leaves * q / nthreads, n_leaves * (q + 1) / nthreads); });
         for (char f : flag) bad = bad || f;
     }
     if (bad) {
@@ -1682,9 +1691,8 @@ int Planner::plan_all() {
     reserve_factorisation();
     // one plan of one piece: the dependency analysis of the factorisation on a second thread, and its
     // graph finished (successors, priorities) while the solve and the matvec are emitted
-    const bool piped = opt.batch_threads >= 0 && std::thread::hardware_concurrency() > 1;
+    const bool piped = opt.batch_threads >= 0 && std::thread::hardware_concurrency() > 1 && pipe_begin();
     if (piped) {
-        pipe_begin();
         bool oom = false;
         try {
             emit_factorisation();
@@ -1711,10 +1719,15 @@ int Planner::plan_all() {
             if (th.joinable()) th.join();
         }
     } fgraph;
-    if (piped)
-        fgraph.th = std::thread([this] { finalize_graph(fplan); });
-    else
+    if (piped) {
+        try {
+            fgraph.th = std::thread([this] { finalize_graph(fplan); });
+        } catch (const std::system_error &) {
+            finalize_graph(fplan);
+        }
+    } else {
         finalize_graph(fplan);
+    }
     f_solve_off = f_elems;
     f_elems = align8(f_elems + int64_t(n) * opt.nrhs_max);
     View Y;

@@ -20,11 +20,32 @@
 #include <array>
 #include <initializer_list>
 #include <string>
+#include <system_error>
+#include <thread>
 #include <vector>
 
 #include "tasks.h"
 
 namespace hlu {
+
+// Runs part(q) for q = 0 .. n - 1: part 0 on the calling thread, the others on threads of their own,
+// and any part whose thread cannot be made on the calling thread too.
+template <class F>
+void run_parts(int n, const F &part) {
+    std::vector<std::thread> pool;
+    std::vector<int> here;
+    pool.reserve(size_t(n > 1 ? n - 1 : 0));
+    for (int q = 1; q < n; ++q) {
+        try {
+            pool.emplace_back(part, q);
+        } catch (const std::system_error &) {
+            here.push_back(q);
+        }
+    }
+    part(0);
+    for (int q : here) part(q);
+    for (std::thread &th : pool) th.join();
+}
 
 struct ClusterInfo {
     int32_t begin, size, son0, son1;
@@ -261,7 +282,7 @@ private:
     // tasks' cells to it in chunks (pipe_begin / pipe_end around the recursion).
     struct Pipe;
     Pipe *pipe = nullptr;
-    void pipe_begin();
+    bool pipe_begin();  // false (nothing started) when no thread can be made
     void reserve_factorisation();
     int pipe_end();
     int32_t emit_views(Kind k, const View *const *reads, size_t nr, const View *const *writes, size_t nw);

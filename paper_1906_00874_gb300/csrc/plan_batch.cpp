@@ -374,12 +374,7 @@ int Planner::plan_batch() {
             status[order[j]] = st;
         }
     };
-    {
-        std::vector<std::thread> pool;
-        for (int32_t t = 1; t < nthreads; ++t) pool.emplace_back(worker);
-        worker();
-        for (std::thread &th : pool) th.join();
-    }
+    run_parts(nthreads, [&](int) { worker(); });
     for (int32_t i = 0; i < count; ++i)
         if (status[i] != HLU_OK) {
             error = "problem " + std::to_string(i) + ": " + parts[i]->error;
@@ -487,8 +482,8 @@ int Planner::plan_batch() {
         error = "host memory exhausted while joining the plans";
         return HLU_ENOMEM;
     }
-    // join in problem order: the plans' groups of arrays each on its own thread, freeing what it has
-    // appended, the stores and inverse blocks here
+    // join in problem order: the stores and inverse blocks, then the plans' groups of arrays each on
+    // its own thread, freeing what it has appended
     auto join_plans = [&](int group) {
         for (int32_t i = 0; i < count; ++i) {
             Planner &q = *parts[i];
@@ -497,8 +492,6 @@ int Planner::plan_batch() {
             join_group(group, q.mplan, mb[i], as[i], mplan);
         }
     };
-    std::vector<std::thread> joiners;
-    for (int group = 0; group < kJoinGroups; ++group) joiners.emplace_back(join_plans, group);
     for (int32_t i = 0; i < count; ++i) {
         Planner &q = *parts[i];
         const Shift &f = fs[i], &a = as[i];
@@ -529,7 +522,7 @@ int Planner::plan_batch() {
             inv_index[q.inv_cl[j] + f.cluster] = int32_t(inv_base[i] + j);
         }
     }
-    for (std::thread &th : joiners) th.join();
+    run_parts(kJoinGroups, join_plans);
     for (int32_t i = 0; i < count; ++i) parts[i].reset();
     // graph-wide figures (the problems run side by side), and the roots of all problems in one
     // order of priority (longest remaining path first), as a single plan orders its own
