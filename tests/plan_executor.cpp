@@ -409,11 +409,70 @@ extern "C" int plan_execute(int32_t n, int32_t n_clusters, const int32_t *perm, 
     return ex.err ? -2 : 0;
 }
 
+namespace {
+
+bool same(const Panel &a, const Panel &b) {
+    return a.off == b.off && a.rows == b.rows && a.cols == b.cols && a.rslot == b.rslot && a.cslot == b.cslot &&
+           a.rs == b.rs && a.cs == b.cs;
+}
+
+// Every field of every task descriptor, term and piece of two plans.
+bool same_descriptors(const Plan &x, const Plan &y) {
+    if (x.getrf.size() != y.getrf.size() || x.trsm.size() != y.trsm.size() || x.project.size() != y.project.size() ||
+        x.accum.size() != y.accum.size() || x.radd.size() != y.radd.size() || x.split.size() != y.split.size() ||
+        x.terms.size() != y.terms.size() || x.pieces.size() != y.pieces.size())
+        return false;
+    for (size_t i = 0; i < x.getrf.size(); ++i) {
+        const TGetrf &a = x.getrf[i], &b = y.getrf[i];
+        if (a.off != b.off || a.m != b.m || a.leaf != b.leaf) return false;
+    }
+    for (size_t i = 0; i < x.trsm.size(); ++i) {
+        const TTrsm &a = x.trsm[i], &b = y.trsm[i];
+        if (a.L_off != b.L_off || a.m != b.m || a.mode != b.mode || !same(a.P, b.P)) return false;
+    }
+    for (size_t i = 0; i < x.project.size(); ++i) {
+        const TProject &a = x.project[i], &b = y.project[i];
+        if (!same(a.F, b.F) || !same(a.X, b.X) || !same(a.T, b.T) || a.dst0 != b.dst0 || a.src0 != b.src0 ||
+            a.dst1 != b.dst1 || a.src1 != b.src1 || a.no_flops != b.no_flops)
+            return false;
+    }
+    for (size_t i = 0; i < x.accum.size(); ++i) {
+        const TAccum &a = x.accum[i], &b = y.accum[i];
+        if (!same(a.out, b.out) || a.alpha != b.alpha || a.overwrite != b.overwrite || a.term0 != b.term0 ||
+            a.nterms != b.nterms || a.dst != b.dst || a.src != b.src || a.credit != b.credit)
+            return false;
+    }
+    for (size_t i = 0; i < x.terms.size(); ++i)
+        if (!same(x.terms[i].A, y.terms[i].A) || !same(x.terms[i].X, y.terms[i].X)) return false;
+    for (size_t i = 0; i < x.radd.size(); ++i) {
+        const TRadd &a = x.radd[i], &b = y.radd[i];
+        if (a.U_off != b.U_off || a.V_off != b.V_off || a.scratch_off != b.scratch_off || a.m != b.m || a.n != b.n ||
+            a.cap != b.cap || a.kslot != b.kslot || a.include_self != b.include_self || a.piece0 != b.piece0 ||
+            a.npieces != b.npieces || a.Kcap != b.Kcap || a.target != b.target || a.inst != b.inst)
+            return false;
+    }
+    for (size_t i = 0; i < x.pieces.size(); ++i) {
+        const Piece &a = x.pieces[i], &b = y.pieces[i];
+        if (a.coef != b.coef || !same(a.U, b.U) || !same(a.V, b.V) || a.roff != b.roff || a.coff != b.coff)
+            return false;
+    }
+    for (size_t i = 0; i < x.split.size(); ++i) {
+        const TSplit &a = x.split[i], &b = y.split[i];
+        if (!same(a.srcU, b.srcU) || !same(a.srcV, b.srcV) || a.dstU != b.dstU || a.dstV != b.dstV || a.mu != b.mu ||
+            a.nv != b.nv || a.src_kslot != b.src_kslot || a.dst_kslot != b.dst_kslot)
+            return false;
+    }
+    return true;
+}
+
+}  // namespace
+
 // Plans the H-matrix twice, with the factorisation's dependency analysis on a second thread
-// (batch_threads = 0) and all on one thread (batch_threads = -1), and compares the three plans'
-// graphs: task codes, waves, predecessor and successor lists, in-degrees, roots and their
-// priorities, and the arena sizes.  Returns 0 when they are equal, else 1 + the index of the first
-// array that differs (plan * 16 + array), or the planner's status.
+// (batch_threads = 0) and all on one thread (batch_threads = -1), and compares the three plans:
+// every task descriptor, term and piece, task codes, waves, predecessor and successor lists,
+// in-degrees, roots and their priorities, the dynamic-size slots, the leaves' stores and the
+// arena layout.  Returns 0 when they are equal, else 1 + the index of the first array that differs
+// (plan * 16 + array), or the planner's status.
 extern "C" int plan_graphs_equal(int32_t n, int32_t n_clusters, const int32_t *perm, const int32_t *begin,
                                  const int32_t *size, const int32_t *son0, const int32_t *son1, int64_t n_leaves,
                                  const int32_t *row_cl, const int32_t *col_cl, const int8_t *kind,
@@ -431,7 +490,16 @@ extern "C" int plan_graphs_equal(int32_t n, int32_t n_clusters, const int32_t *p
         if (st == 0) st = pl[v].plan_all();
         if (st) return st;
     }
-    if (pl[0].f_elems != pl[1].f_elems || pl[0].a_elems != pl[1].a_elems) return 1;
+    if (pl[0].f_elems != pl[1].f_elems || pl[0].a_elems != pl[1].a_elems || pl[0].f_solve_off != pl[1].f_solve_off ||
+        pl[0].f_z_off != pl[1].f_z_off || pl[0].a_x_off != pl[1].a_x_off || pl[0].a_y_off != pl[1].a_y_off ||
+        pl[0].slot_init != pl[1].slot_init || pl[0].nrhs_slot != pl[1].nrhs_slot ||
+        pl[0].inv_L_off != pl[1].inv_L_off || pl[0].inv_U_off != pl[1].inv_U_off)
+        return 1;
+    for (int64_t l = 0; l < n_leaves; ++l) {
+        const Store &a = pl[0].fstore[l], &b = pl[1].fstore[l];
+        if (a.D_off != b.D_off || a.U_off != b.U_off || a.V_off != b.V_off || a.kslot != b.kslot || a.cap != b.cap)
+            return 1;
+    }
     const Plan *a[3] = {&pl[0].fplan, &pl[0].splan, &pl[0].mplan}, *b[3] = {&pl[1].fplan, &pl[1].splan, &pl[1].mplan};
     for (int q = 0; q < 3; ++q) {
         const Plan &x = *a[q], &y = *b[q];
@@ -445,6 +513,7 @@ extern "C" int plan_graphs_equal(int32_t n, int32_t n_clusters, const int32_t *p
         if (x.succ_ptr != y.succ_ptr || x.succ_idx != y.succ_idx) return code + 5;
         if (x.indeg != y.indeg || x.roots != y.roots || x.root_bl != y.root_bl) return code + 6;
         if (x.critical_us != y.critical_us) return code + 7;
+        if (!same_descriptors(x, y)) return code + 8;
     }
     return 0;
 }
