@@ -17,7 +17,6 @@
 #include <utility>
 #include <functional>
 #include <unordered_map>
-#include <queue>
 
 #include "../../include/hlu.h"
 
@@ -168,9 +167,7 @@ void Planner::relocate_temps(Plan &p) {
         for (size_t i : tmp) sorted[start[lev(i, false)]++] = i;
         tmp.swap(sorted);
     }
-    using Occ = std::pair<int32_t, size_t>;  // (last level, item)
-    std::priority_queue<Occ, std::vector<Occ>, std::greater<Occ>> active;
-    // free regions by shape (problem, row cluster, rows, cols): (offset, occupant)
+    // every temporary's shape (problem, row cluster, rows, cols) as a small integer
     struct ShapeHash {
         size_t operator()(const std::array<int32_t, 4> &a) const {
             uint64_t h = 0x9e3779b97f4a7c15ull;
@@ -178,17 +175,34 @@ void Planner::relocate_temps(Plan &p) {
             return size_t(h ^ (h >> 31));
         }
     };
-    std::unordered_map<std::array<int32_t, 4>, std::vector<std::pair<int64_t, int32_t>>, ShapeHash> free_by_shape;
+    std::vector<int32_t> shape_of(ni, -1);
+    int32_t n_shapes = 0;
+    {
+        std::unordered_map<std::array<int32_t, 4>, int32_t, ShapeHash> ids;
+        ids.reserve(1024);
+        for (size_t i : tmp) {
+            auto it = ids.emplace(temp_shape[plan_items[i].temp_obj], n_shapes).first;
+            if (it->second == n_shapes) ++n_shapes;
+            shape_of[i] = it->second;
+        }
+    }
+    // the temporaries placed so far by their last level; those of the levels below the current
+    // temporary's first level are free again, released level by level and in item order
+    std::vector<std::vector<int32_t>> ending(size_t(std::max(p.n_waves, 1)));
+    int32_t released = 0;
+    // free regions by shape: (offset, occupant)
+    std::vector<std::vector<std::pair<int64_t, int32_t>>> free_by_shape(static_cast<size_t>(n_shapes));
     std::vector<std::pair<int32_t, int32_t>> order;  // (earlier temporary, later temporary) sharing a region
     int64_t top = pos;
     for (size_t i : tmp) {
         const int32_t f = lev(i, false);
-        while (!active.empty() && active.top().first < f) {
-            const size_t j = active.top().second;
-            active.pop();
-            free_by_shape[temp_shape[plan_items[j].temp_obj]].emplace_back(noff[j], plan_items[j].temp_obj);
+        for (; released < f; ++released) {
+            std::vector<int32_t> &done = ending[size_t(released)];
+            std::sort(done.begin(), done.end());
+            for (int32_t j : done) free_by_shape[shape_of[j]].emplace_back(noff[j], plan_items[j].temp_obj);
+            std::vector<int32_t>().swap(done);
         }
-        auto &fl = free_by_shape[temp_shape[plan_items[i].temp_obj]];
+        auto &fl = free_by_shape[shape_of[i]];
         if (!fl.empty()) {
             noff[i] = fl.back().first;
             order.emplace_back(fl.back().second, plan_items[i].temp_obj);
@@ -197,128 +211,178 @@ void Planner::relocate_temps(Plan &p) {
             noff[i] = top;
             top = align8(top + plan_items[i].size);
         }
-        active.emplace(lev(i, true), i);
+        ending[size_t(lev(i, true))].push_back(int32_t(i));
     }
-    // offsets: an offset inside item k (items are in increasing offset order) keeps its distance.
-    // The item of an offset is found from a table of the first item of every 4096-element page of
-    // the plan's region, then a short forward scan (items are small: a few per page).
-    constexpr int kPageShift = 12;
-    const int64_t span = plan_items[ni - 1].off - plan_begin;
-    std::vector<int32_t> page_item(size_t(span >> kPageShift) + 1);
-    {
-        size_t it = 0;
-        for (size_t pg = 0; pg < page_item.size(); ++pg) {
-            const int64_t start = plan_begin + (int64_t(pg) << kPageShift);
-            while (it + 1 < ni && plan_items[it + 1].off <= start) ++it;
-            page_item[pg] = int32_t(it);
-        }
-    }
-    auto remap = [&](int64_t off) -> int64_t {
-        if (off < plan_begin) return off;
-        const size_t pg = std::min(size_t((off - plan_begin) >> kPageShift), page_item.size() - 1);
-        size_t i = size_t(page_item[pg]);
-        while (i + 1 < ni && plan_items[i + 1].off <= off) ++i;
-        return noff[i] + (off - plan_items[i].off);
-    };
-    for (TGetrf &t : p.getrf) t.off = remap(t.off);
-    for (TTrsm &t : p.trsm) {
-        t.L_off = remap(t.L_off);
-        t.P.off = remap(t.P.off);
-    }
-    for (TProject &t : p.project) {
-        t.F.off = remap(t.F.off);
-        t.X.off = remap(t.X.off);
-        t.T.off = remap(t.T.off);
-    }
-    for (TAccum &t : p.accum) t.out.off = remap(t.out.off);
-    for (Term &t : p.terms) {
-        t.A.off = remap(t.A.off);
-        t.X.off = remap(t.X.off);
-    }
-    for (TRadd &t : p.radd) {
-        t.U_off = remap(t.U_off);
-        t.V_off = remap(t.V_off);
-    }
-    for (Piece &t : p.pieces) {
-        t.U.off = remap(t.U.off);
-        t.V.off = remap(t.V.off);
-    }
-    for (TSplit &t : p.split) {
-        t.srcU.off = remap(t.srcU.off);
-        t.srcV.off = remap(t.srcV.off);
-        t.dstU = remap(t.dstU);
-        t.dstV = remap(t.dstV);
-    }
-    for (Store &st : fstore) {
-        st.D_off = remap(st.D_off);
-        st.U_off = remap(st.U_off);
-        st.V_off = remap(st.V_off);
-    }
-    for (int64_t &o : inv_L_off) o = remap(o);
-    for (int64_t &o : inv_U_off) o = remap(o);
     *arena = top;
-    if (order.empty()) return;
-    // the touches of every temporary (counting sort by object; a task's touches are in cell order)
-    const size_t nobj = temp_size.size();
-    std::vector<int32_t> tptr(nobj + 1, 0), ttask(dep.touch_obj.size()), tcell(dep.touch_obj.size());
-    std::vector<uint8_t> twr(dep.touch_obj.size());
-    for (int32_t o : dep.touch_obj) tptr[o + 1]++;
-    for (size_t o = 0; o < nobj; ++o) tptr[o + 1] += tptr[o];
-    {
-        std::vector<int32_t> fill(tptr.begin(), tptr.end() - 1);
-        for (size_t e = 0; e < dep.touch_obj.size(); ++e) {
-            const int32_t at = fill[dep.touch_obj[e]]++;
-            ttask[at] = dep.touch_task[e];
-            tcell[at] = dep.touch_cell[e];
-            twr[at] = dep.touch_write[e];
-        }
-    }
-    // per shared region, cell by cell (the two temporaries have the same shape, hence the same
-    // cells): every task that touched the earlier one's cell precedes every writer of the later one's
-    std::vector<std::pair<int32_t, int32_t>> extra;  // (task, predecessor)
-    std::vector<std::vector<int32_t>> by_cell;
-    for (const auto &pr : order) {
-        const int32_t a = pr.first, b = pr.second;
-        const int32_t ncell = objs[a].nr * objs[a].nc;
-        if ((int32_t)by_cell.size() < ncell) by_cell.resize(ncell);
-        for (int32_t c = 0; c < ncell; ++c) by_cell[c].clear();
-        for (int32_t e = tptr[a]; e < tptr[a + 1]; ++e) by_cell[tcell[e]].push_back(ttask[e]);
-        for (int32_t e = tptr[b]; e < tptr[b + 1]; ++e)
-            if (twr[e])
-                for (int32_t t : by_cell[tcell[e]]) extra.emplace_back(ttask[e], t);
-    }
-    // merge into the predecessor lists (CSR), each predecessor once per task (the extra edges
-    // grouped by task with a counting sort)
-    const int64_t nt = p.n_tasks;
-    std::vector<int32_t> xptr(nt + 1, 0), xidx(extra.size());
-    for (const auto &e : extra) xptr[e.first + 1]++;
-    for (int64_t g = 0; g < nt; ++g) xptr[g + 1] += xptr[g];
-    {
-        std::vector<int32_t> fill(xptr.begin(), xptr.end() - 1);
-        for (const auto &e : extra) xidx[fill[e.first]++] = e.second;
-    }
-    std::vector<int32_t> nptr(nt + 1, 0), nidx;
-    nidx.reserve(p.pred_idx.size() + extra.size());
-    std::vector<int32_t> mark(nt, -1);
-    for (int64_t g = 0; g < nt; ++g) {
-        for (int32_t e = p.pred_ptr[g]; e < p.pred_ptr[g + 1]; ++e) {
-            const int32_t t = p.pred_idx[e];
-            if (mark[t] != g) {
-                mark[t] = int32_t(g);
-                nidx.push_back(t);
+    // the offsets in the plan move, and the shared regions add edges: the two on two threads
+    auto remap_offsets = [&] {
+        // offsets: an offset inside item k (items are in increasing offset order) keeps its distance.
+        // The item of an offset is found from a table of the first item of every 4096-element page of
+        // the plan's region, then a short forward scan (items are small: a few per page).
+        constexpr int kPageShift = 12;
+        const int64_t span = plan_items[ni - 1].off - plan_begin;
+        std::vector<int32_t> page_item(size_t(span >> kPageShift) + 1);
+        {
+            size_t it = 0;
+            for (size_t pg = 0; pg < page_item.size(); ++pg) {
+                const int64_t start = plan_begin + (int64_t(pg) << kPageShift);
+                while (it + 1 < ni && plan_items[it + 1].off <= start) ++it;
+                page_item[pg] = int32_t(it);
             }
         }
-        for (int32_t e = xptr[g]; e < xptr[g + 1]; ++e) {
-            const int32_t t = xidx[e];
-            if (t != g && mark[t] != g) {
-                mark[t] = int32_t(g);
-                nidx.push_back(t);
+        auto remap = [&](int64_t off) -> int64_t {
+            if (off < plan_begin) return off;
+            const size_t pg = std::min(size_t((off - plan_begin) >> kPageShift), page_item.size() - 1);
+            size_t i = size_t(page_item[pg]);
+            while (i + 1 < ni && plan_items[i + 1].off <= off) ++i;
+            return noff[i] + (off - plan_items[i].off);
+        };
+        for (TGetrf &t : p.getrf) t.off = remap(t.off);
+        for (TTrsm &t : p.trsm) {
+            t.L_off = remap(t.L_off);
+            t.P.off = remap(t.P.off);
+        }
+        for (TProject &t : p.project) {
+            t.F.off = remap(t.F.off);
+            t.X.off = remap(t.X.off);
+            t.T.off = remap(t.T.off);
+        }
+        for (TAccum &t : p.accum) t.out.off = remap(t.out.off);
+        for (Term &t : p.terms) {
+            t.A.off = remap(t.A.off);
+            t.X.off = remap(t.X.off);
+        }
+        for (TRadd &t : p.radd) {
+            t.U_off = remap(t.U_off);
+            t.V_off = remap(t.V_off);
+        }
+        for (Piece &t : p.pieces) {
+            t.U.off = remap(t.U.off);
+            t.V.off = remap(t.V.off);
+        }
+        for (TSplit &t : p.split) {
+            t.srcU.off = remap(t.srcU.off);
+            t.srcV.off = remap(t.srcV.off);
+            t.dstU = remap(t.dstU);
+            t.dstV = remap(t.dstV);
+        }
+        for (Store &st : fstore) {
+            st.D_off = remap(st.D_off);
+            st.U_off = remap(st.U_off);
+            st.V_off = remap(st.V_off);
+        }
+        for (int64_t &o : inv_L_off) o = remap(o);
+        for (int64_t &o : inv_U_off) o = remap(o);
+    };
+    auto add_edges = [&] {
+        if (order.empty()) return;
+        // the touches of every temporary (counting sort by object; a task's touches are in cell order)
+        const size_t nobj = temp_size.size();
+        std::vector<int32_t> tptr(nobj + 1, 0), ttask(dep.touch_obj.size()), tcell(dep.touch_obj.size());
+        std::vector<uint8_t> twr(dep.touch_obj.size());
+        for (int32_t o : dep.touch_obj) tptr[o + 1]++;
+        for (size_t o = 0; o < nobj; ++o) tptr[o + 1] += tptr[o];
+        {
+            std::vector<int32_t> fill(tptr.begin(), tptr.end() - 1);
+            for (size_t e = 0; e < dep.touch_obj.size(); ++e) {
+                const int32_t at = fill[dep.touch_obj[e]]++;
+                ttask[at] = dep.touch_task[e];
+                tcell[at] = dep.touch_cell[e];
+                twr[at] = dep.touch_write[e];
             }
         }
-        nptr[g + 1] = int32_t(nidx.size());
-    }
-    p.pred_ptr.swap(nptr);
-    p.pred_idx.swap(nidx);
+        // per shared region, cell by cell (the two temporaries have the same shape, hence the same
+        // cells): every task that touched the earlier one's cell precedes every writer of the later one's
+        // (split by ranges of region pairs over host threads, put side by side in pair order)
+        const int npairs = int(std::min<int64_t>(std::max(1u, std::min(8u, std::thread::hardware_concurrency())),
+                                                  int64_t(order.size()) / 16384 + 1));
+        std::vector<std::vector<std::pair<int32_t, int32_t>>> part_extra(static_cast<size_t>(npairs));
+        run_parts(npairs, [&](int q) {
+            std::vector<std::pair<int32_t, int32_t>> &extra = part_extra[size_t(q)];  // (task, predecessor)
+            std::vector<std::vector<int32_t>> by_cell;
+            const size_t k0 = order.size() * size_t(q) / size_t(npairs);
+            const size_t k1 = order.size() * size_t(q + 1) / size_t(npairs);
+            for (size_t k = k0; k < k1; ++k) {
+                const int32_t a = order[k].first, b = order[k].second;
+                const int32_t ncell = objs[a].nr * objs[a].nc;
+                if ((int32_t)by_cell.size() < ncell) by_cell.resize(ncell);
+                for (int32_t c = 0; c < ncell; ++c) by_cell[c].clear();
+                for (int32_t e = tptr[a]; e < tptr[a + 1]; ++e) by_cell[tcell[e]].push_back(ttask[e]);
+                for (int32_t e = tptr[b]; e < tptr[b + 1]; ++e)
+                    if (twr[e])
+                        for (int32_t t : by_cell[tcell[e]]) extra.emplace_back(ttask[e], t);
+            }
+        });
+        std::vector<std::pair<int32_t, int32_t>> extra;
+        {
+            size_t total = 0;
+            for (const auto &v : part_extra) total += v.size();
+            extra.reserve(total);
+            for (auto &v : part_extra) {
+                extra.insert(extra.end(), v.begin(), v.end());
+                std::vector<std::pair<int32_t, int32_t>>().swap(v);
+            }
+        }
+        // merge into the predecessor lists (CSR), each predecessor once per task (the extra edges
+        // grouped by task with a counting sort)
+        const int64_t nt = p.n_tasks;
+        std::vector<int32_t> xptr(nt + 1, 0), xidx(extra.size());
+        for (const auto &e : extra) xptr[e.first + 1]++;
+        for (int64_t g = 0; g < nt; ++g) xptr[g + 1] += xptr[g];
+        {
+            std::vector<int32_t> fill(xptr.begin(), xptr.end() - 1);
+            for (const auto &e : extra) xidx[fill[e.first]++] = e.second;
+        }
+        // the merge of a task depends on its own lists only: split by task ranges over host threads,
+        // each part merging into its own list, then the parts put side by side
+        const int nparts = int(std::min<int64_t>(std::max(1u, std::min(8u, std::thread::hardware_concurrency())),
+                                                  nt / 65536 + 1));
+        std::vector<std::vector<int32_t>> part_idx(static_cast<size_t>(nparts));
+        std::vector<int32_t> nptr(nt + 1, 0);  // first the merged length of every task
+        run_parts(nparts, [&](int q) {
+            const int64_t g0 = nt * q / nparts, g1 = nt * (q + 1) / nparts;
+            std::vector<int32_t> &out = part_idx[size_t(q)];
+            out.reserve(size_t(p.pred_ptr[g1] - p.pred_ptr[g0]) + size_t(xptr[g1] - xptr[g0]));
+            std::vector<int32_t> mark(nt, -1);
+            for (int64_t g = g0; g < g1; ++g) {
+                const size_t before = out.size();
+                if (xptr[g] == xptr[g + 1]) {  // no extra edge: the list as it is (already without repeats)
+                    out.insert(out.end(), p.pred_idx.begin() + p.pred_ptr[g], p.pred_idx.begin() + p.pred_ptr[g + 1]);
+                } else {
+                    for (int32_t e = p.pred_ptr[g]; e < p.pred_ptr[g + 1]; ++e) {
+                        const int32_t t = p.pred_idx[e];
+                        if (mark[t] != g) {
+                            mark[t] = int32_t(g);
+                            out.push_back(t);
+                        }
+                    }
+                    for (int32_t e = xptr[g]; e < xptr[g + 1]; ++e) {
+                        const int32_t t = xidx[e];
+                        if (t != g && mark[t] != g) {
+                            mark[t] = int32_t(g);
+                            out.push_back(t);
+                        }
+                    }
+                }
+                nptr[g + 1] = int32_t(out.size() - before);
+            }
+        });
+        for (int64_t g = 0; g < nt; ++g) nptr[g + 1] += nptr[g];
+        std::vector<int32_t> nidx(static_cast<size_t>(nptr[nt]));
+        run_parts(nparts, [&](int q) {
+            const int64_t g0 = nt * q / nparts;
+            std::copy(part_idx[size_t(q)].begin(), part_idx[size_t(q)].end(), nidx.begin() + nptr[g0]);
+            std::vector<int32_t>().swap(part_idx[size_t(q)]);
+        });
+        p.pred_ptr.swap(nptr);
+        p.pred_idx.swap(nidx);
+    };
+    run_parts(2, [&](int q) {
+        if (q == 0)
+            add_edges();
+        else
+            remap_offsets();
+    });
 }
 
 // The largest sum of temporary elements in use at one dependency level (the memory an allocation
