@@ -141,6 +141,12 @@ void Planner::note_temp(int32_t obj, int64_t elems, const std::array<int32_t, 4>
 // that share a region every task that touches the earlier one becomes a predecessor of every task
 // that writes the later one.  Those edges go from a lower level to a higher one, so the graph stays
 // acyclic with the same levels (no longer dependency chain in levels).
+int Planner::host_parts(int64_t limit) const {
+    if (opt.batch_threads < 0) return 1;  // one thread (or one of a batch's pool of problem planners)
+    const int64_t hw = std::max(1u, std::min(8u, std::thread::hardware_concurrency()));
+    return int(std::max<int64_t>(1, std::min(hw, limit)));
+}
+
 void Planner::relocate_temps(Plan &p) {
     const size_t ni = plan_items.size();
     if (ni == 0) return;
@@ -294,8 +300,7 @@ void Planner::relocate_temps(Plan &p) {
         // per shared region, cell by cell (the two temporaries have the same shape, hence the same
         // cells): every task that touched the earlier one's cell precedes every writer of the later one's
         // (split by ranges of region pairs over host threads, put side by side in pair order)
-        const int npairs = int(std::min<int64_t>(std::max(1u, std::min(8u, std::thread::hardware_concurrency())),
-                                                  int64_t(order.size()) / 16384 + 1));
+        const int npairs = host_parts(int64_t(order.size()) / 16384 + 1);
         std::vector<std::vector<std::pair<int32_t, int32_t>>> part_extra(static_cast<size_t>(npairs));
         run_parts(npairs, [&](int q) {
             std::vector<std::pair<int32_t, int32_t>> &extra = part_extra[size_t(q)];  // (task, predecessor)
@@ -335,8 +340,7 @@ void Planner::relocate_temps(Plan &p) {
         }
         // the merge of a task depends on its own lists only: split by task ranges over host threads,
         // each part merging into its own list, then the parts put side by side
-        const int nparts = int(std::min<int64_t>(std::max(1u, std::min(8u, std::thread::hardware_concurrency())),
-                                                  nt / 65536 + 1));
+        const int nparts = host_parts(nt / 65536 + 1);
         std::vector<std::vector<int32_t>> part_idx(static_cast<size_t>(nparts));
         std::vector<int32_t> nptr(nt + 1, 0);  // first the merged length of every task
         run_parts(nparts, [&](int q) {
@@ -377,11 +381,10 @@ void Planner::relocate_temps(Plan &p) {
         p.pred_ptr.swap(nptr);
         p.pred_idx.swap(nidx);
     };
-    run_parts(2, [&](int q) {
-        if (q == 0)
-            add_edges();
-        else
-            remap_offsets();
+    const int two = host_parts(2);
+    run_parts(two, [&](int q) {
+        if (q == 0) add_edges();
+        if (q == 1 || two == 1) remap_offsets();
     });
 }
 

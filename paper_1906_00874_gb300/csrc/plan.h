@@ -264,6 +264,9 @@ private:
     std::vector<int64_t> temp_size;
     void temp_levels(Plan &p) const;
     void relocate_temps(Plan &p);
+    // Host threads for a piece of planning work that splits into at most `limit` parts: up to eight,
+    // one when opt.batch_threads < 0.
+    int host_parts(int64_t limit) const;
     void note_temp(int32_t obj, int64_t elems, const std::array<int32_t, 4> &shape);
     void cells_of(const View &v, std::vector<int64_t> &out) const;
     // The cells a view covers: rows r0..r1-1 and columns c0..c1-1 of the cell grid of an object whose
