@@ -521,7 +521,7 @@ int32_t Planner::analyze(Deps &d, std::vector<int32_t> &pred_ptr, std::vector<in
 struct Planner::Pipe {
     static constexpr size_t kRing = 4, kTasks = 2048;
     struct Chunk {
-        std::vector<uint32_t> counts;  // per task: reads | writes << 16
+        std::vector<uint32_t> counts;  // per task: its reads, then its writes
         std::vector<ViewRec> views;
     };
     Chunk ring[kRing];
@@ -535,7 +535,7 @@ struct Planner::Pipe {
     std::vector<int32_t> pred_ptr, pred_idx;
     std::vector<int32_t> waves;  // per task from task g0 on
     int32_t g0 = 0, n_waves = 0;
-    alignas(64) char end_ = 0;
+    alignas(64) char pad_ = 0;  // keeps the fields above off the cache line of what follows
 
     Chunk &current() { return ring[produced % kRing]; }
     // hands the current chunk over and waits until the next one in the ring has been analysed
@@ -571,8 +571,8 @@ bool Planner::pipe_begin() {
             if (!q->failed) {
                 try {
                     size_t at = 0;
-                    for (uint32_t nrw : c.counts) {
-                        const size_t nr = nrw & 0xffffu, nw = nrw >> 16;
+                    for (size_t t = 0; t < c.counts.size(); t += 2) {
+                        const size_t nr = c.counts[t], nw = c.counts[t + 1];
                         const int32_t w = analyze(q->d, q->pred_ptr, q->pred_idx, c.views.data() + at, nr, nw, g++);
                         q->waves.push_back(w);
                         q->n_waves = std::max(q->n_waves, w + 1);
@@ -645,8 +645,9 @@ int32_t Planner::emit_views(Kind k, const View *const *reads, size_t nr, const V
     int32_t w = 0;
     if (pipe) {
         Pipe::Chunk &c = pipe->current();
-        c.counts.push_back(uint32_t(nr) | uint32_t(nw) << 16);
-        if (c.counts.size() >= Pipe::kTasks) pipe->publish();
+        c.counts.push_back(uint32_t(nr));
+        c.counts.push_back(uint32_t(nw));
+        if (c.counts.size() >= 2 * Pipe::kTasks) pipe->publish();
     } else {
         w = analyze(dep, P->pred_ptr, P->pred_idx, v, nr, nw, int32_t(P->n_tasks));
         P->n_waves = std::max(P->n_waves, w + 1);
