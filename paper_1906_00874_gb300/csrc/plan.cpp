@@ -1713,7 +1713,7 @@ int Planner::build(int32_t n_, int32_t n_clusters, const int32_t *perm_, const i
 void Planner::reserve_factorisation() {
     int32_t depth = 1;
     for (int64_t c = cl[0].lc_count; c > 1; c = (c + 1) / 2) ++depth;
-    const int64_t t = std::min<int64_t>(int64_t(n_leaves) * 10 * depth, int64_t(1) << 27);
+    const int64_t t = std::min<int64_t>(int64_t(n_leaves) * 10 * depth, int64_t(1) << 25);  // larger plans grow past it
     Plan &p = fplan;
     p.task_code.reserve(size_t(t));
     p.getrf.reserve(size_t(cl[0].lc_count));
