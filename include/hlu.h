@@ -2,7 +2,7 @@
  * hlu.h - LU factorisation of hierarchical matrices (H-LU) on one GB300 GPU.
  *
  * The operation is the H-LU of Sec. 3.1 of "Exploiting Nested Task-Parallelism
- * in the H-LU Factorization": the recursion O1.1-O5.5 (LU of the leading
+ * in the H-LU Factorization": the 2 x 2 block recursion (LU of the leading
  * diagonal block, triangular solves of the off-diagonal blocks, Schur update,
  * LU of the trailing block) applied at every partitioned diagonal block, with
  * low-rank blocks X = U V^T handled in H-arithmetic (triangular solves on one
@@ -152,7 +152,7 @@ typedef struct hlu_ctx *hlu_t;
 int hlu_create(const hlu_tree *tree, const hlu_blocks *blocks, const hlu_opts *opts,
                void *cuda_stream, hlu_t *out);
 
-/* H-LU in place (Sec. 3.1, O1.1-O5.5), truncating at relative tolerance eps
+/* H-LU in place (Sec. 3.1), truncating at relative tolerance eps
  * (singular values sigma_i <= eps * sigma_1 of each rounded addition are dropped).
  * Every call first restores the working copy from A_H on the device, so the
  * handle can be factorised again (e.g. with another eps).  Synchronises the

@@ -1,19 +1,20 @@
 // Host planner: expands the H-LU recursion into a task graph with dependency
 // waves, and lays out the device arenas.
 //
-// The recursion is the one of Sec. 3.1 (O1.1-O5.5 at every partitioned
-// diagonal block, with O2/O3 decomposed as O2.1-O2.6 of Sec. 5.2 when the
-// off-diagonal block is partitioned).  Dependencies between tasks are found
-// from the matrix regions they read and write, at the granularity of leaf
-// clusters: every stored object (a dense block, the U or V factor of a
-// low-rank block, a temporary panel) is cut into cells along the leaf clusters
-// of its row (and column) cluster.  This plays the role of the skeleton array
-// of Sec. 5.1 - a fixed table of representants, built once, that is decoupled
-// from the storage whose sizes change during the factorisation - and, because
-// all tasks of all recursion levels are analysed in one domain, it exposes the
-// cross-level parallelism that weak dependencies and early release give in
-// Sec. 5.2.  Tasks are grouped into waves (longest-path levels); the tasks of
-// one wave are independent.
+// The recursion is the 2 x 2 block LU of Sec. 3.1 at every partitioned diagonal
+// block (factor the leading block, solve the two off-diagonal blocks with its
+// factors, Schur update, factor the trailing block), each off-diagonal solve
+// broken into block substitution as in Sec. 5.2 when that block is partitioned.
+// Dependencies between tasks are found from the matrix regions they read and
+// write, at the granularity of leaf clusters: every stored object (a dense
+// block, the U or V factor of a low-rank block, a temporary panel) is cut into
+// cells along the leaf clusters of its row (and column) cluster.  This plays
+// the role of the skeleton array of Sec. 5.1 - a fixed table of representants,
+// built once, that is decoupled from the storage whose sizes change during the
+// factorisation - and, because all tasks of all recursion levels are analysed
+// in one domain, it exposes the cross-level parallelism that weak dependencies
+// and early release give in Sec. 5.2.  Tasks are grouped into waves
+// (longest-path levels); the tasks of one wave are independent.
 #pragma once
 #include <stdint.h>
 

@@ -1,8 +1,8 @@
 // Task descriptors shared by the host planner and the device kernels.
 //
-// The H-LU recursion of Sec. 3.1 (O1.1-O5.5, with the low-rank operations of
-// the "Low-rank blocks" paragraph) is expanded on the host into tasks of six
-// kinds.  Every matrix operand is a strided view ("Panel") into one device
+// The H-LU recursion of Sec. 3.1 (the 2 x 2 block LU at every partitioned
+// diagonal block, with the low-rank operations of the "Low-rank blocks"
+// paragraph) is expanded on the host into tasks of six kinds.  Every matrix operand is a strided view ("Panel") into one device
 // arena; dimensions that depend on ranks computed at run time are read from a
 // device array of dynamic dimensions (kdyn) through slot indices.
 #pragma once
@@ -23,8 +23,8 @@ struct Panel {
 constexpr int32_t kMaxLeafRows = 128;
 
 enum Kind : int32_t {
-    K_GETRF = 0,    // unpivoted LU of a dense diagonal leaf (O1.1, Sec. 3.1 "Dense blocks")
-    K_TRSM = 1,     // triangular solve of a panel with a dense diagonal leaf (O1.2/O1.3)
+    K_GETRF = 0,    // unpivoted LU of a dense diagonal leaf (Sec. 3.1 "Dense blocks")
+    K_TRSM = 1,     // triangular solve of a panel with a dense diagonal leaf (Sec. 3.1)
     K_PROJECT = 2,  // T = F^T X: first half of a low-rank leaf times a panel, y = U (V^T z)
     K_ACCUM = 3,    // out[seg] (+)= alpha * sum_j A_j X_j over the leaves that cover seg
     K_RADD = 4,     // rounded addition: stack factors, QR, SVD of the core, truncate
